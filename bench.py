@@ -1,0 +1,292 @@
+"""Benchmark of the SWR-Galerkin sweep on GB300.
+
+One step = the whole hot path on the 2-electron ground-state workload
+([-12,12]^2, 4x4 subdomains, 24x24 Gaussians each): swr_assemble (quadrature,
+local Galerkin systems, orthonormalisation, step-matrix inverses, projection
+of phi0) followed by swr_iterate until the interface residual Res(k) <= 1e-8.
+Metric: local subdomain solves per second (one solve = one time step of one
+subdomain), with the time-to-residual reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun every rank solves its own replica of the workload on its own
+GPU (independent problems, no data-path collective; weak scaling); the time
+is the max over ranks.  `--impl reference` times the FP64 CPU oracle on the
+host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TOL = 1e-8
+KMAX = 200
+METRIC = "SWR time-to-1e-8 interface residual; subdomain solves/s vs plain FP64 GPU path"
+# nominal FP64 (non-tensor) rate of one GB300, the ceiling of the FP64 window kernel
+FP64_PEAK_TFLOPS = 1.25
+
+
+def workload(name: str):
+    from paper_1710_02401_gb300 import problems as P
+    if name == "tise_2e_16sd":
+        return P.tise_2e_16_subdomains()
+    if name == "tise_1d_2sd":
+        return P.tise_1d_two_subdomains()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(name: str, inst) -> dict:
+    return {"workload": name, "n_elec": inst.n_elec, "box": list(inst.box), "L": inst.L,
+            "subdomains": inst.n_sub, "K_d": inst.K_d, "K": inst.K_d ** inst.n_elec,
+            "nodes_per_coord": (inst.n_mid + 2) * inst.q_p, "dt": inst.dt, "mu": str(inst.mu),
+            "tol": TOL, "kmax": KMAX, "l2": "flushed (256 MB write) before every step",
+            "parallelism": "replicas (one independent problem per GPU)"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(inst, gpu_solves_per_iter=None):
+    """Times the FP64 CPU oracle on this host: assembly of all local systems,
+    then the first Schwarz iteration (zero initial traces).  Returns
+    (solves/s of the iteration, description, assembly seconds)."""
+    from oracle import swr_oracle as O
+    t0 = time.perf_counter()
+    locs = O.assemble(inst)
+    t_asm = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    r = O.run_swr(inst, kmax=1, tol=0.0, locs=locs)
+    t_it = time.perf_counter() - t1
+    solves = r.records[0].n_win * inst.n_sub
+    desc = (f"oracle (numpy FP64, dense quadrature + LU) on the same workload: first Schwarz "
+            f"iteration, {solves} local step solves in {t_it:.2f} s; local assembly of all "
+            f"{inst.n_sub} subdomains took {t_asm:.2f} s and is not in the rate")
+    return solves / t_it, desc, t_asm
+
+
+def run_reference(args, inst, name):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import swr_oracle as O
+    locs = O.assemble(inst)
+    for _ in range(args.warmup):
+        O.run_swr(inst, kmax=1, tol=0.0, locs=locs)
+    t_tot, solves = 0.0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = O.run_swr(inst, kmax=1, tol=0.0, locs=locs)
+        t_tot += time.perf_counter() - t0
+        solves += r.records[0].n_win * inst.n_sub
+    value = solves / t_tot
+    cores = os.cpu_count()
+    sample = ("each step: first Schwarz iteration (zero initial traces) of the FP64 oracle on the "
+              "full workload, local systems assembled once before the timed steps")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "subdomain solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(name, inst),
+        "cpu_baseline": {"value": value, "unit": "subdomain solves/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "subdomain solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="tise_2e_16sd")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    name = args.workload
+    inst = workload(name)
+    if args.impl == "reference":
+        run_reference(args, inst, name)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1710_02401_gb300 import build as B
+    B.build()
+    from paper_1710_02401_gb300 import swr as S
+
+    stream = torch.cuda.current_stream(dev)
+    s = S.SWR(inst, device=str(dev), stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_step():
+        s.assemble()
+        rep, hist = s.iterate(TOL, KMAX)
+        return rep, hist
+
+    for _ in range(args.warmup):
+        rep, hist = one_step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    c0 = s.counters()
+    times, reps = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep, hist = one_step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        reps.append(rep)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    c1 = s.counters()
+    clocks = sampler.stop()
+    t_ms = sum(times)
+    solves = sum(r.subdomain_solves for r in reps)
+    converged = all(r.converged for r in reps)
+    t_max = t_ms
+    solves_all = solves
+    if world > 1:
+        t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        n = torch.tensor([solves], dtype=torch.float64, device=dev)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        solves_all = int(n.item())
+    value = solves_all / (t_max * 1e-3)
+    # dominant kernel: the persistent time-window kernel (FP64 matvec-bound)
+    w_ms = c1["window_ms"] - c0["window_ms"]
+    w_launch = c1["window_launches"] - c0["window_launches"]
+    w_flops = c1["window_flops"] - c0["window_flops"]
+    achieved = w_flops / (w_ms * 1e-3) / 1e12 if w_ms > 0 else 0.0
+    launches = int(c1["kernel_launches"] - c0["kernel_launches"])
+
+    # end to end through the public API: setup from host descriptors, assembly,
+    # iterations, read-back of energies and psi at all nodes, teardown
+    e2e_val, h2d, d2h = None, 0, 0
+    if args.e2e_steps > 0:
+        e_solves, e_time = 0, 0.0
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            se = S.SWR(inst, device=str(dev), stream=stream)
+            se.assemble()
+            rep_e, _ = se.iterate(TOL, KMAX)
+            energy = se.energy()
+            psi = se.psi_nodes()
+            ce = se.counters()
+            se.close()
+            torch.cuda.synchronize(dev)
+            e_time += time.perf_counter() - t0
+            e_solves += rep_e.subdomain_solves
+            h2d, d2h = int(ce["h2d_bytes"]), int(ce["d2h_bytes"])
+            del se
+        e2e_val = e_solves / e_time
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, desc, t_asm = oracle_sample(inst)
+        cpu = {"value": v, "unit": "subdomain solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": desc}
+    out = {
+        "metric": METRIC, "value": value, "unit": "subdomain solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(name, inst),
+        "time_to_residual_s": t_max / args.steps * 1e-3,
+        "schwarz_iterations": [r.iterations for r in reps], "converged": converged,
+        "res_last": [r.res_last for r in reps],
+        "energy": float(s.energy()[0]),
+        "roofline": {"kernel": "k_ngf_window", "bound": "alu", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak on this pool)",
+                     "traffic": None, "window_ms_per_launch": w_ms / max(w_launch, 1),
+                     "algorithmic": "2 K^2 flops per local step solve (FP64 matvec with the step-matrix inverse)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "subdomain solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

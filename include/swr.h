@@ -1,0 +1,195 @@
+/*
+ * swr.h -- C ABI of the GB300 (sm_103a) Schwarz Waveform Relaxation (SWR)
+ * Galerkin sweep for the N-body Schroedinger equation.
+ *
+ * The method (E. Lorin, "Domain Decomposition Method for the N-body
+ * Time-Independent and Time-Dependent Schroedinger Equation"):
+ *   - the configuration space [a,b]^N (d = 1, N = 1 or 2 electrons) is cut into
+ *     L^N overlapping hypercubes Omega_{i1 + L*i2}, overlap bands of width eps
+ *     (opening of Sec. 6);
+ *   - on each subdomain the wavefunction is expanded in tensor products of 1-D
+ *     Gaussians exp(-delta (x - alpha)^2) (Sec. 2, Eq. gauss1d), giving local
+ *     Galerkin systems A_i, H~_i (with the Robin term R_i) and Q_i
+ *     (Sec. 5.1, "Construction of the local approximate solutions");
+ *   - imaginary time: implicit Euler + global normalisation (NGF, Sec. 5.2 and
+ *     Sec. 5.4 step 2/4); real time: Crank-Nicolson under the dipole field
+ *     (Sec. 1.2, Sec. 5.4 step 2);
+ *   - subdomains exchange Robin data (d_n + mu) psi_j, averaged over all
+ *     overlapping neighbours (Sec. 5.1, Eq. RTC and the multi-subdomain rule);
+ *   - convergence is measured by the residual Res(k) of Eq. residueRT / residueIT
+ *     (Sec. 6.2, 6.3).
+ *
+ * Every entry point returns a swr_status; no C++ exception crosses the ABI.
+ * swr_last_error(ctx) returns a human-readable detail string for the last
+ * failing call on that context (or a setup failure when ctx is NULL).
+ * A context is not thread-safe; distinct contexts are independent.
+ * All device work is ordered on the CUDA stream given in swr_problem.stream
+ * (NULL = the legacy default stream).  Host buffers are owned by the caller.
+ */
+#ifndef SWR_H
+#define SWR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum swr_status {
+    SWR_OK = 0,
+    SWR_EINVAL = 1,      /* invalid argument or problem description            */
+    SWR_ENOMEM = 2,      /* device allocation failed / workspace too small      */
+    SWR_ECUDA = 3,       /* CUDA runtime error (detail in swr_last_error)       */
+    SWR_ESINGULAR = 4,   /* overlap matrix not positive definite (basis too
+                            ill-conditioned for the Cholesky orthogonalisation) */
+    SWR_ENUMERIC = 5,    /* NaN / Inf met in a solve or a trace                 */
+    SWR_ENOTCONV = 6,    /* swr_iterate reached kmax above tol (report filled)  */
+    SWR_ETIMEOUT = 7,    /* a bounded device-side wait gave up                  */
+    SWR_ESTATE = 8       /* call out of order (e.g. swr_step before assemble)  */
+} swr_status;
+
+typedef enum swr_mode {
+    SWR_MODE_TISE = 0,   /* imaginary time: implicit Euler (+ normalisation)    */
+    SWR_MODE_TDSE = 1    /* real time: Crank-Nicolson with the dipole field     */
+} swr_mode;
+
+typedef enum swr_precision {
+    SWR_PREC_FP64 = 0,   /* plain FP64 everywhere                                */
+    SWR_PREC_MIXED = 1   /* FP32 bulk step matrices + FP64 refinement            */
+} swr_precision;
+
+/* One SWR problem: global box [box_lo, box_hi]^n_elec cut into L^n_elec
+ * subdomains.  Subdomain sid = i1 + L*i2 covers, in coordinate e,
+ * [a + i_e H - overlap/2, a + (i_e+1) H + overlap/2], H = (b-a)/L.          */
+typedef struct swr_instance {
+    int    n_elec;          /* N = 1 or 2 (d = 1)                                 */
+    double box_lo, box_hi;  /* a, b                                               */
+    int    L;               /* subdomains per coordinate (>= 1)                   */
+    double overlap;         /* eps, 0 < eps < H (any eps > 0 when L == 1)         */
+    int    K_d;             /* Gaussians per coordinate, used when K_d_per_sub is NULL */
+    const int*    K_d_per_sub;   /* optional [L^N] Gaussians per coordinate per subdomain */
+    double delta;           /* Gaussian exponent, used when delta_per_sub is NULL */
+    const double* delta_per_sub; /* optional [L^N]                                */
+    int    q_p;             /* Gauss-Legendre nodes per panel (1..64)             */
+    int    n_mid;           /* equal panels of the middle zone [lo+eps, hi-eps]   */
+    int    n_nuclei;        /* P <= 3                                              */
+    double x_nuc[3], Z_nuc[3];
+    double eta_en, eta_ee;  /* soft-Coulomb parameters (Eq. pseudo)               */
+    double ee_coef;         /* e-e prefactor (1: physical, 0: none)               */
+    double harmonic;        /* + harmonic * x_e^2 / 2 per electron                 */
+    double kinetic;         /* kappa in -kappa * Laplacian (1/2 for H0)           */
+    double mu_re, mu_im;    /* Robin constant mu (Eq. RTC)                         */
+    int    mode;            /* swr_mode                                            */
+    int    normalize;       /* TISE: renormalise every step (NGF)                 */
+    double dt;
+    int    n_steps;         /* fixed window (TDSE; TISE when ngf_tol <= 0)        */
+    double ngf_tol;         /* TISE inner stop ||phi^{n+1} - phi^n|| <= ngf_tol   */
+    int    max_steps;       /* TISE window cap                                    */
+    double field_E0, field_T, field_omega, field_phase; /* e(t) = E0 sin^2(pi t/T) sin(omega t + phase), 0 <= t <= T */
+    double phi0_gamma;      /* phi0 = exp(-gamma |x - x0|^2)                       */
+    double phi0_center[2];
+} swr_instance;
+
+typedef struct swr_problem {
+    int                 n_instances;  /* independent problems batched together */
+    const swr_instance* instances;    /* [n_instances], copied by swr_setup     */
+    int                 precision;    /* swr_precision                          */
+    void*               stream;       /* cudaStream_t (NULL: default stream)    */
+    void*               workspace;    /* optional caller-owned device buffer    */
+    size_t              workspace_bytes; /* >= swr_workspace_size() when given   */
+} swr_problem;
+
+typedef struct swr_ctx swr_ctx;
+
+/* Per Schwarz iteration (one call of swr_step). */
+typedef struct swr_iter_report {
+    int       k;                 /* Schwarz iteration index (1-based)              */
+    double    res;               /* max over instances of Res(k)                   */
+    int       window_max;        /* longest time window of this iteration          */
+    long long subdomain_solves;  /* local step solves done in this iteration       */
+    double    seconds;           /* device time of the iteration (CUDA events)     */
+} swr_iter_report;
+
+typedef struct swr_report {
+    int       iterations;
+    int       converged;         /* 1 when max_instance Res(k) <= tol              */
+    double    res_last;
+    long long subdomain_solves;
+    double    seconds;
+} swr_report;
+
+/* Device bytes the context needs (so the caller can pass them in as
+ * swr_problem.workspace).  Fails with SWR_EINVAL on an invalid problem. */
+swr_status swr_workspace_size(const swr_problem* p, size_t* bytes);
+
+/* Validates and copies the problem, lays out device memory (the caller's
+ * workspace when given, else cudaMalloc'ed and owned by the context), and
+ * uploads the subdomain descriptors.  *out is NULL on failure. */
+swr_status swr_setup(const swr_problem* p, swr_ctx** out);
+
+/* Sec. 5.1: quadrature tables, local Galerkin matrices, orthonormalisation of
+ * the local bases, step matrices (TISE: (I + dt H'), TDSE: I + i dt/2 H')
+ * and their inverses, projection of phi0 (Sec. 6.1).  Once per problem.
+ * SWR_ESINGULAR when an overlap matrix fails the Cholesky factorisation. */
+swr_status swr_assemble(swr_ctx* ctx);
+
+/* Exactly one Schwarz iteration over all subdomains of all instances:
+ * time window of local solves (Sec. 5.4 step 2, 4), interface traces,
+ * averaged Robin data for the next iteration, Res(k).  rep may be NULL. */
+swr_status swr_step(swr_ctx* ctx, swr_iter_report* rep);
+
+/* swr_step until max_instance Res(k) <= tol or kmax iterations.
+ * res_history (nullable) receives up to kmax residuals.
+ * Returns SWR_ENOTCONV (report filled) when tol is not reached. */
+swr_status swr_iterate(swr_ctx* ctx, double tol, int kmax, swr_report* rep, double* res_history);
+
+/* Interface-trace window of the last iteration (checkpoint / warm start). */
+typedef enum swr_dir { SWR_GET = 0, SWR_SET = 1 } swr_dir;
+typedef struct swr_trace_view {
+    void*  host;      /* host buffer of `bytes` bytes                               */
+    size_t bytes;     /* must equal swr_get(ctx, SWR_FIELD_TRACE_BYTES) on SET      */
+} swr_trace_view;
+swr_status swr_traces(swr_ctx* ctx, int dir, swr_trace_view* view);
+
+/* Read-back of results into a HOST buffer of exactly the stated size. */
+typedef enum swr_field {
+    SWR_FIELD_ENERGY = 0,       /* double[n_instances]: PoU Rayleigh quotient (TISE)   */
+    SWR_FIELD_NORM2 = 1,        /* double[n_instances]: PoU norm^2 of the last state   */
+    SWR_FIELD_DIPOLE = 2,       /* double[n_instances]: <x_1 + ... + x_N> (TDSE)        */
+    SWR_FIELD_RES = 3,          /* double[n_instances]: Res(k) of the last iteration   */
+    SWR_FIELD_WINDOW = 4,       /* int[n_instances]: window length of the last iteration */
+    SWR_FIELD_PSI_NODES = 5,    /* double (TISE) or double2 (TDSE) per volume node of
+                                   every subdomain, subdomains in order, node
+                                   p = q1 + q*q2 (q nodes per coordinate)            */
+    SWR_FIELD_OWN_TRACES = 6,   /* u_i at the interface nodes for steps 0..window of
+                                   the last iteration, layout [sub][step][node]       */
+    SWR_FIELD_ROBIN = 7,        /* averaged Robin data g_i, same layout                */
+    SWR_FIELD_TRACE_BYTES = 8,  /* size_t: bytes of the swr_traces window              */
+    SWR_FIELD_NODE_COUNTS = 9,  /* int[3 * n_sub_total]: per subdomain (q, n_gamma, K) */
+    SWR_FIELD_K_MAX = 10,       /* int: Schwarz iterations done so far                 */
+    SWR_FIELD_COUNTERS = 11     /* double[10], cumulative since swr_setup:
+                                   [0] ms inside the time-window kernel (CUDA events on
+                                       the context stream, one pair per launch),
+                                   [1] launches of the time-window kernel,
+                                   [2] kernel launches of the library (all kernels),
+                                   [3] algorithmic flops of the window kernels
+                                       (2 K^2 real / 8 K^2 complex per local step solve),
+                                   [4] algorithmic bytes of the window kernels
+                                       (step-matrix bytes read per local step solve),
+                                   [5] local step solves,
+                                   [6] ms of swr_assemble (events), [7] ms of swr_step,
+                                   [8] host->device bytes copied, [9] device->host bytes */
+} swr_field;
+swr_status swr_get(swr_ctx* ctx, int field, void* host, size_t bytes);
+
+/* Bytes that swr_get needs for `field` (for the sized fields). */
+swr_status swr_field_bytes(swr_ctx* ctx, int field, size_t* bytes);
+
+void        swr_destroy(swr_ctx* ctx);
+const char* swr_last_error(const swr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWR_H */

@@ -1,0 +1,783 @@
+// swr_api.cu -- host side of the C ABI declared in include/swr.h.
+//
+// Owns the context: validated copy of the problem, the subdomain descriptors,
+// the device arena (one allocation, or the caller's workspace), and the order
+// of launches of an assembly (swr_assemble) and of a Schwarz iteration
+// (swr_step).  Geometry follows the opening of Sec. 6 of the paper: subdomain
+// i_e of coordinate e covers [a + i_e H - eps/2, a + (i_e + 1) H + eps/2].
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "swr_internal.cuh"
+
+namespace swr {
+cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, int max_kd, int max_K,
+                            bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
+                            const GemmJob* d_jobs2, double* d_norm_part, double tau);
+cudaError_t ngf_occupancy(int* blocks_per_sm, size_t smem);
+cudaError_t launch_ngf_iteration(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst, int max_K,
+                                 cudaEvent_t ev_begin, cudaEvent_t ev_end);
+extern const int kAssembleLaunchesFixed, kStepLaunches;
+cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
+                        const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
+                        int res_blocks, double* d_res, int max_cap_hint);
+cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
+                          int cap, double* d_part, double* d_energy, double* d_norm2, double* psi_out,
+                          const long long* psi_off, int max_K, int max_kd, int max_q);
+}  // namespace swr
+
+using namespace swr;
+
+static const int ROW_BLOCK = 32;      // rows of a step matrix per persistent task
+static const int GJ_NB_HOST = 32;     // Gauss-Jordan block (matches swr_assemble.cu)
+static const int RES_BLOCKS = 8;      // residual partial blocks per subdomain
+static const double CHOL_TAU = 1e-15; // relative pivot floor of the overlap Cholesky
+static const long long SPIN_LIMIT = 1LL << 24;  // polls (x ~64 ns) before a barrier gives up
+
+struct swr_ctx {
+    std::string err;
+    swr_problem prob;
+    std::vector<swr_instance> inst_h;
+    std::vector<std::vector<int>> kd_h;
+    std::vector<std::vector<double>> delta_h;
+    std::vector<InstDev> inst;
+    std::vector<SubDev> sub;
+    std::vector<long long> zoff, psi_off;
+    std::vector<Task> tasks;
+    std::vector<int> inst_task0;
+    size_t arena_doubles = 0, aux_bytes = 0;
+    int cap = 0, max_K = 0, max_kd = 0, max_q = 0, max_ngam = 0;
+    bool any_ee = false, tdse = false;
+    long long psi_total = 0, zbuf_total = 0;
+    // device memory
+    void* base = nullptr;
+    bool owns = false;
+    double* arena = nullptr;
+    InstDev* d_inst = nullptr;
+    SubDev* d_sub = nullptr;
+    int* d_err = nullptr;
+    GemmJob *d_jobs1 = nullptr, *d_jobs2 = nullptr;
+    double* d_norm_part = nullptr;
+    Task* d_tasks = nullptr;
+    int* d_inst_task0 = nullptr;
+    double *d_part_s = nullptr, *d_part_d = nullptr, *d_snorm = nullptr, *d_zbuf = nullptr;
+    long long* d_zoff = nullptr;
+    int *d_act = nullptr, *d_win = nullptr, *d_win_prev = nullptr;
+    GridBarrier* d_bar = nullptr;
+    double *d_res_part = nullptr, *d_res = nullptr, *d_epart = nullptr, *d_energy = nullptr, *d_norm2 = nullptr;
+    double* d_psi = nullptr;
+    long long* d_psi_off = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // state
+    bool assembled = false;
+    int k = 0, parity = 0;
+    int grid = 0;
+    size_t ngf_smem = 0;
+    std::vector<double> res_h, energy_h, norm2_h;
+    std::vector<int> win_h, win_prev_h;
+    // counters (see SWR_FIELD_COUNTERS)
+    double counters[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    cudaEvent_t evw0 = nullptr, evw1 = nullptr;
+};
+
+static std::string g_setup_err;
+
+static swr_status fail(swr_ctx* c, swr_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_setup_err = buf;
+    return s;
+}
+
+#define CU(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(c, SWR_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
+                        __FILE__, __LINE__);                                                        \
+    } while (0)
+
+static long long align32(long long x) { return (x + 31) & ~31LL; }
+
+// ------------------------------------------------------------------ layout
+
+static swr_status validate(swr_ctx* c, const swr_problem* p) {
+    if (!p || p->n_instances < 1 || !p->instances) return fail(c, SWR_EINVAL, "empty problem");
+    int mode0 = p->instances[0].mode;
+    for (int i = 0; i < p->n_instances; ++i) {
+        const swr_instance& in = p->instances[i];
+        if (in.n_elec < 1 || in.n_elec > 2) return fail(c, SWR_EINVAL, "instance %d: n_elec must be 1 or 2", i);
+        if (in.mode != mode0) return fail(c, SWR_EINVAL, "instance %d: all instances must share one mode", i);
+        if (in.mode != SWR_MODE_TISE && in.mode != SWR_MODE_TDSE) return fail(c, SWR_EINVAL, "instance %d: bad mode", i);
+        if (!(in.box_hi > in.box_lo)) return fail(c, SWR_EINVAL, "instance %d: empty box", i);
+        if (in.L < 1 || in.L > 4096) return fail(c, SWR_EINVAL, "instance %d: L out of range", i);
+        double H = (in.box_hi - in.box_lo) / in.L;
+        if (!(in.overlap > 0) || (in.L > 1 && !(in.overlap < H)))
+            return fail(c, SWR_EINVAL, "instance %d: need 0 < overlap < (b-a)/L", i);
+        if (in.q_p < 1 || in.q_p > SWR_MAX_QP) return fail(c, SWR_EINVAL, "instance %d: q_p must be in [1,%d]", i, SWR_MAX_QP);
+        if (in.n_mid < 1) return fail(c, SWR_EINVAL, "instance %d: n_mid must be >= 1", i);
+        int q = (in.n_mid + 2) * in.q_p;
+        if (q > 384) return fail(c, SWR_EINVAL, "instance %d: (n_mid+2)*q_p = %d exceeds 384", i, q);
+        if (in.n_nuclei < 0 || in.n_nuclei > SWR_MAX_NUC) return fail(c, SWR_EINVAL, "instance %d: at most 3 nuclei", i);
+        if (!(in.dt > 0)) return fail(c, SWR_EINVAL, "instance %d: dt must be > 0", i);
+        if (in.mode == SWR_MODE_TDSE && in.n_steps < 1) return fail(c, SWR_EINVAL, "instance %d: TDSE needs n_steps >= 1", i);
+        if (in.mode == SWR_MODE_TISE && in.ngf_tol <= 0 && in.n_steps < 1)
+            return fail(c, SWR_EINVAL, "instance %d: TISE needs ngf_tol > 0 or n_steps >= 1", i);
+        if (in.mode == SWR_MODE_TISE && in.ngf_tol > 0 && in.max_steps < 1)
+            return fail(c, SWR_EINVAL, "instance %d: max_steps must be >= 1", i);
+        if (in.mode == SWR_MODE_TISE && in.mu_im != 0.0)
+            return fail(c, SWR_EINVAL, "instance %d: imaginary-time Robin constant must be real", i);
+        if (in.mode == SWR_MODE_TDSE) return fail(c, SWR_EINVAL, "instance %d: real-time mode not built in this library version", i);
+        int nsub = 1;
+        for (int e = 0; e < in.n_elec; ++e) nsub *= in.L;
+        for (int s = 0; s < nsub; ++s) {
+            int kd = in.K_d_per_sub ? in.K_d_per_sub[s] : in.K_d;
+            double dl = in.delta_per_sub ? in.delta_per_sub[s] : in.delta;
+            if (kd < 2) return fail(c, SWR_EINVAL, "instance %d sub %d: K_d must be >= 2", i, s);
+            if (in.n_elec == 2 && kd > 32) return fail(c, SWR_EINVAL, "instance %d sub %d: K_d <= 32 for N = 2", i, s);
+            if (in.n_elec == 1 && kd > 96) return fail(c, SWR_EINVAL, "instance %d sub %d: K_d <= 96 for N = 1", i, s);
+            if (!(dl > 0)) return fail(c, SWR_EINVAL, "instance %d sub %d: delta must be > 0", i, s);
+        }
+    }
+    if (p->precision != SWR_PREC_FP64 && p->precision != SWR_PREC_MIXED)
+        return fail(c, SWR_EINVAL, "unknown precision");
+    return SWR_OK;
+}
+
+// Fill descriptors and offsets; returns arena size (doubles) and aux bytes.
+static void plan(swr_ctx* c) {
+    const swr_problem& p = c->prob;
+    c->inst.clear();
+    c->sub.clear();
+    c->zoff.clear();
+    c->psi_off.clear();
+    c->tasks.clear();
+    c->inst_task0.clear();
+    long long off = 0, zo = 0, po = 0;
+    c->cap = 0;
+    c->tdse = p.instances[0].mode == SWR_MODE_TDSE;
+    const int cx = c->tdse ? 2 : 1;
+    for (int i = 0; i < p.n_instances; ++i) {
+        const swr_instance& in = c->inst_h[i];
+        int fixed = (in.mode == SWR_MODE_TDSE) ? in.n_steps : (in.ngf_tol > 0 ? 0 : in.n_steps);
+        int cap = fixed > 0 ? fixed : in.max_steps;
+        c->cap = cap > c->cap ? cap : c->cap;
+    }
+    for (int i = 0; i < p.n_instances; ++i) {
+        const swr_instance& in = c->inst_h[i];
+        InstDev d;
+        memset(&d, 0, sizeof(d));
+        d.N = in.n_elec;
+        d.L = in.L;
+        d.q_p = in.q_p;
+        d.n_mid = in.n_mid;
+        d.q = (in.n_mid + 2) * in.q_p;
+        d.mode = in.mode;
+        d.normalize = (in.mode == SWR_MODE_TISE) ? in.normalize : 0;
+        d.n_nuc = in.n_nuclei;
+        d.sub_base = (int)c->sub.size();
+        d.n_sub = 1;
+        for (int e = 0; e < in.n_elec; ++e) d.n_sub *= in.L;
+        d.n_steps = in.n_steps;
+        d.max_steps = in.max_steps;
+        d.window_cap = (in.mode == SWR_MODE_TDSE) ? in.n_steps : (in.ngf_tol > 0 ? 0 : in.n_steps);
+        d.a = in.box_lo;
+        d.b = in.box_hi;
+        d.H = (in.box_hi - in.box_lo) / in.L;
+        d.eps = in.overlap;
+        for (int A = 0; A < in.n_nuclei; ++A) {
+            d.x_nuc[A] = in.x_nuc[A];
+            d.Z_nuc[A] = in.Z_nuc[A];
+        }
+        d.eta_en = in.eta_en;
+        d.eta_ee = in.eta_ee;
+        d.ee_coef = (in.n_elec == 2) ? in.ee_coef : 0.0;
+        d.harmonic = in.harmonic;
+        d.kappa = in.kinetic;
+        d.mu_re = in.mu_re;
+        d.mu_im = in.mu_im;
+        d.dt = in.dt;
+        d.ngf_tol = in.ngf_tol;
+        d.E0 = in.field_E0;
+        d.T = in.field_T;
+        d.omega = in.field_omega;
+        d.phase = in.field_phase;
+        d.gamma0 = in.phi0_gamma;
+        d.x0[0] = in.phi0_center[0];
+        d.x0[1] = in.phi0_center[1];
+        if (d.N == 2 && d.ee_coef != 0.0) c->any_ee = true;
+        c->inst.push_back(d);
+        c->inst_task0.push_back((int)c->tasks.size());
+        for (int sidl = 0; sidl < d.n_sub; ++sidl) {
+            SubDev s;
+            memset(&s, 0, sizeof(s));
+            s.inst = i;
+            s.N = d.N;
+            s.kd = c->kd_h[i][sidl];
+            s.delta = c->delta_h[i][sidl];
+            s.K = s.N == 2 ? s.kd * s.kd : s.kd;
+            s.q = d.q;
+            int rem = sidl;
+            for (int e = 0; e < 2; ++e) {
+                s.idx[e] = (e < d.N) ? rem % d.L : 0;
+                if (e < d.N) rem /= d.L;
+                s.lo[e] = d.a + s.idx[e] * d.H - 0.5 * d.eps;
+                s.hi[e] = d.a + (s.idx[e] + 1) * d.H + 0.5 * d.eps;
+            }
+            s.edge_mask = 0;
+            int ng = 0;
+            for (int sl = 0; sl < 4; ++sl) s.gam_off[sl] = -1;
+            for (int e = 0; e < d.N; ++e) {
+                for (int side = 0; side < 2; ++side) {
+                    bool interior = side == 0 ? s.idx[e] > 0 : s.idx[e] < d.L - 1;
+                    if (!interior) continue;
+                    s.edge_mask |= 1 << (2 * e + side);
+                    s.gam_off[2 * e + side] = ng;
+                    ng += (d.N == 2) ? d.q : 1;
+                }
+            }
+            s.ngam = ng;
+            s.nline = (d.N == 2) ? 16 * d.q : 8;
+            const int K = s.K, q = d.q, kd = s.kd;
+            T1Layout lay(q, kd);
+            for (int e = 0; e < 2; ++e) {
+                if (e < d.N) {
+                    s.t1[e] = off;
+                    off = align32(off + lay.size());
+                } else {
+                    s.t1[e] = s.t1[0];
+                }
+            }
+            s.Hm = off; off = align32(off + (long long)K * K);
+            s.Gm = off; off = align32(off + (long long)K * K * cx);
+            s.c0 = off; off = align32(off + (long long)K * cx);
+            s.hist = off; off = align32(off + (long long)(c->cap + 1) * K * cx);
+            s.bvec = off; off = align32(off + (long long)(c->cap + 1) * K * cx);
+            s.line = off; off = align32(off + (long long)(c->cap + 1) * s.nline * cx);
+            s.u[0] = off; off = align32(off + (long long)(c->cap + 1) * (ng > 0 ? ng : 1) * cx);
+            s.u[1] = off; off = align32(off + (long long)(c->cap + 1) * (ng > 0 ? ng : 1) * cx);
+            s.g = off; off = align32(off + (long long)(c->cap + 1) * (ng > 0 ? ng : 1) * cx);
+            long long ee = (d.N == 2) ? 3LL * q * kd * kd + (long long)q * q : 0;
+            long long gj = ((long long)GJ_NB_HOST * GJ_NB_HOST + 2LL * GJ_NB_HOST * K) * cx;
+            s.work = off; off = align32(off + (ee > gj ? ee : gj));
+            c->zoff.push_back(zo);
+            zo += 2LL * K;
+            c->psi_off.push_back(po);
+            po += (d.N == 2) ? (long long)q * q : q;
+            if (K > c->max_K) c->max_K = K;
+            if (kd > c->max_kd) c->max_kd = kd;
+            if (q > c->max_q) c->max_q = q;
+            if (ng > c->max_ngam) c->max_ngam = ng;
+            const int sid = (int)c->sub.size();
+            for (int r0 = 0; r0 < K; r0 += ROW_BLOCK) {
+                Task t;
+                t.sid = sid;
+                t.r0 = r0;
+                t.r1 = r0 + ROW_BLOCK < K ? r0 + ROW_BLOCK : K;
+                t.inst = i;
+                c->tasks.push_back(t);
+            }
+            c->sub.push_back(s);
+        }
+    }
+    c->inst_task0.push_back((int)c->tasks.size());
+    c->arena_doubles = (size_t)off;
+    c->zbuf_total = zo;
+    c->psi_total = po;
+}
+
+// Auxiliary device arrays carved after the arena (bytes, 256-aligned).
+struct AuxPlan {
+    size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, snorm, zbuf, zoff, act, win,
+        win_prev, bar, res_part, res, epart, energy, norm2, psi, psi_off, total;
+};
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+static AuxPlan aux_plan(const swr_ctx* c) {
+    AuxPlan a;
+    size_t o = al256(c->arena_doubles * sizeof(double));
+    const size_t ni = c->inst.size(), ns = c->sub.size(), nt = c->tasks.size();
+    a.inst = o; o = al256(o + ni * sizeof(InstDev));
+    a.sub = o; o = al256(o + ns * sizeof(SubDev));
+    a.err = o; o = al256(o + sizeof(int) * 4);
+    a.jobs1 = o; o = al256(o + ns * sizeof(GemmJob));
+    a.jobs2 = o; o = al256(o + ns * sizeof(GemmJob));
+    a.norm_part = o; o = al256(o + ns * sizeof(double));
+    a.tasks = o; o = al256(o + nt * sizeof(Task));
+    a.task0 = o; o = al256(o + (ni + 1) * sizeof(int));
+    a.part_s = o; o = al256(o + 2 * nt * sizeof(double));
+    a.part_d = o; o = al256(o + 2 * nt * sizeof(double));
+    a.snorm = o; o = al256(o + ni * (size_t)(c->cap + 1) * sizeof(double));
+    a.zbuf = o; o = al256(o + (size_t)c->zbuf_total * sizeof(double));
+    a.zoff = o; o = al256(o + ns * sizeof(long long));
+    a.act = o; o = al256(o + ni * sizeof(int));
+    a.win = o; o = al256(o + ni * sizeof(int));
+    a.win_prev = o; o = al256(o + ni * sizeof(int));
+    a.bar = o; o = al256(o + sizeof(GridBarrier));
+    a.res_part = o; o = al256(o + ns * RES_BLOCKS * sizeof(double));
+    a.res = o; o = al256(o + ni * sizeof(double));
+    a.epart = o; o = al256(o + 2 * ns * sizeof(double));
+    a.energy = o; o = al256(o + ni * sizeof(double));
+    a.norm2 = o; o = al256(o + ni * sizeof(double));
+    a.psi = o; o = al256(o + (size_t)c->psi_total * sizeof(double) * (c->tdse ? 2 : 1));
+    a.psi_off = o; o = al256(o + ns * sizeof(long long));
+    a.total = o;
+    return a;
+}
+
+static swr_status copy_problem(swr_ctx* c, const swr_problem* p) {
+    c->prob = *p;
+    c->inst_h.assign(p->instances, p->instances + p->n_instances);
+    c->kd_h.clear();
+    c->delta_h.clear();
+    for (int i = 0; i < p->n_instances; ++i) {
+        const swr_instance& in = p->instances[i];
+        int nsub = 1;
+        for (int e = 0; e < in.n_elec; ++e) nsub *= in.L;
+        std::vector<int> kd(nsub);
+        std::vector<double> dl(nsub);
+        for (int s = 0; s < nsub; ++s) {
+            kd[s] = in.K_d_per_sub ? in.K_d_per_sub[s] : in.K_d;
+            dl[s] = in.delta_per_sub ? in.delta_per_sub[s] : in.delta;
+        }
+        c->kd_h.push_back(kd);
+        c->delta_h.push_back(dl);
+        c->inst_h[i].K_d_per_sub = nullptr;
+        c->inst_h[i].delta_per_sub = nullptr;
+    }
+    c->prob.instances = c->inst_h.data();
+    return SWR_OK;
+}
+
+extern "C" swr_status swr_workspace_size(const swr_problem* p, size_t* bytes) {
+    if (!bytes) return fail(nullptr, SWR_EINVAL, "bytes is NULL");
+    swr_status st = validate(nullptr, p);
+    if (st != SWR_OK) return st;
+    swr_ctx tmp;
+    copy_problem(&tmp, p);
+    plan(&tmp);
+    *bytes = aux_plan(&tmp).total;
+    return SWR_OK;
+}
+
+extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
+    if (!out) return fail(nullptr, SWR_EINVAL, "out is NULL");
+    *out = nullptr;
+    swr_status st = validate(nullptr, p);
+    if (st != SWR_OK) return st;
+    swr_ctx* c = new swr_ctx();
+    copy_problem(c, p);
+    plan(c);
+    AuxPlan a = aux_plan(c);
+    c->stream = (cudaStream_t)p->stream;
+    if (p->workspace) {
+        if (p->workspace_bytes < a.total) {
+            swr_status s2 = fail(nullptr, SWR_ENOMEM, "workspace of %zu bytes < %zu needed", p->workspace_bytes, a.total);
+            delete c;
+            return s2;
+        }
+        if (((uintptr_t)p->workspace) & 255) {
+            delete c;
+            return fail(nullptr, SWR_EINVAL, "workspace must be 256-byte aligned");
+        }
+        c->base = p->workspace;
+    } else {
+        cudaError_t e = cudaMalloc(&c->base, a.total);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(nullptr, SWR_ENOMEM, "cudaMalloc(%zu) failed: %s", a.total, cudaGetErrorString(e));
+        }
+        c->owns = true;
+    }
+    char* b = (char*)c->base;
+    c->arena = (double*)b;
+    c->d_inst = (InstDev*)(b + a.inst);
+    c->d_sub = (SubDev*)(b + a.sub);
+    c->d_err = (int*)(b + a.err);
+    c->d_jobs1 = (GemmJob*)(b + a.jobs1);
+    c->d_jobs2 = (GemmJob*)(b + a.jobs2);
+    c->d_norm_part = (double*)(b + a.norm_part);
+    c->d_tasks = (Task*)(b + a.tasks);
+    c->d_inst_task0 = (int*)(b + a.task0);
+    c->d_part_s = (double*)(b + a.part_s);
+    c->d_part_d = (double*)(b + a.part_d);
+    c->d_snorm = (double*)(b + a.snorm);
+    c->d_zbuf = (double*)(b + a.zbuf);
+    c->d_zoff = (long long*)(b + a.zoff);
+    c->d_act = (int*)(b + a.act);
+    c->d_win = (int*)(b + a.win);
+    c->d_win_prev = (int*)(b + a.win_prev);
+    c->d_bar = (GridBarrier*)(b + a.bar);
+    c->d_res_part = (double*)(b + a.res_part);
+    c->d_res = (double*)(b + a.res);
+    c->d_epart = (double*)(b + a.epart);
+    c->d_energy = (double*)(b + a.energy);
+    c->d_norm2 = (double*)(b + a.norm2);
+    c->d_psi = (double*)(b + a.psi);
+    c->d_psi_off = (long long*)(b + a.psi_off);
+    // GEMM jobs of the sum-factorised e-e block
+    std::vector<GemmJob> j1(c->sub.size()), j2(c->sub.size());
+    for (size_t s = 0; s < c->sub.size(); ++s) {
+        const SubDev& sd = c->sub[s];
+        GemmJob z;
+        memset(&z, 0, sizeof(z));
+        j1[s] = z;
+        j2[s] = z;
+        if (sd.N != 2) continue;
+        int q = sd.q, kd2 = sd.kd * sd.kd;
+        long long P1 = sd.work, P2 = sd.work + (long long)q * kd2, Wv = sd.work + 2LL * q * kd2,
+                  Mee = sd.work + 2LL * q * kd2 + (long long)q * q;
+        j1[s].a = Wv; j1[s].b = P2; j1[s].c = Mee;
+        j1[s].M = q; j1[s].N = kd2; j1[s].K = q;
+        j1[s].lda = q; j1[s].ldb = kd2; j1[s].ldc = kd2;
+        j2[s].a = P1; j2[s].b = Mee; j2[s].c = sd.Hm;
+        j2[s].M = kd2; j2[s].N = kd2; j2[s].K = q;
+        j2[s].lda = kd2; j2[s].ldb = kd2; j2[s].ldc = kd2;
+        j2[s].transA = 1; j2[s].mode = 1; j2[s].kd = sd.kd;
+    }
+    CU(cudaMemcpyAsync(c->d_inst, c->inst.data(), c->inst.size() * sizeof(InstDev), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_sub, c->sub.data(), c->sub.size() * sizeof(SubDev), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_jobs1, j1.data(), j1.size() * sizeof(GemmJob), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_jobs2, j2.data(), j2.size() * sizeof(GemmJob), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_tasks, c->tasks.data(), c->tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_inst_task0, c->inst_task0.data(), c->inst_task0.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_zoff, c->zoff.data(), c->zoff.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_psi_off, c->psi_off.data(), c->psi_off.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+    c->counters[8] += (double)(c->inst.size() * sizeof(InstDev) + c->sub.size() * (sizeof(SubDev) + 2 * sizeof(GemmJob) + 2 * sizeof(long long)) +
+                               c->tasks.size() * sizeof(Task) + c->inst_task0.size() * sizeof(int));
+    CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
+    CU(cudaMemsetAsync(c->d_win_prev, 0, c->inst.size() * sizeof(int), c->stream));
+    CU(cudaMemsetAsync(c->d_win, 0, c->inst.size() * sizeof(int), c->stream));
+    CU(cudaEventCreate(&c->ev0));
+    CU(cudaEventCreate(&c->ev1));
+    CU(cudaEventCreate(&c->evw0));
+    CU(cudaEventCreate(&c->evw1));
+    // persistent grid for the window kernel
+    c->ngf_smem = (2 * (size_t)c->max_K + (size_t)c->max_kd + ROW_BLOCK + 64) * sizeof(double);
+    int bps = 0, dev = 0, nsm = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CU(ngf_occupancy(&bps, c->ngf_smem));
+    if (bps < 1) return fail(c, SWR_EINVAL, "window kernel does not fit on an SM");
+    int maxgrid = bps * nsm;
+    int nt = (int)c->tasks.size();
+    c->grid = nt < maxgrid ? nt : maxgrid;
+    c->res_h.assign(c->inst.size(), 0.0);
+    c->energy_h.assign(c->inst.size(), 0.0);
+    c->norm2_h.assign(c->inst.size(), 0.0);
+    c->win_h.assign(c->inst.size(), 0);
+    c->win_prev_h.assign(c->inst.size(), 0);
+    *out = c;
+    return SWR_OK;
+}
+
+static swr_status check_err(swr_ctx* c) {
+    int e = 0;
+    CU(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    c->counters[9] += sizeof(int);
+    CU(cudaStreamSynchronize(c->stream));
+    if (e & SWR_ERR_SINGULAR) return fail(c, SWR_ESINGULAR, "overlap or step matrix not positive definite (ill-conditioned basis)");
+    if (e & SWR_ERR_TIMEOUT) return fail(c, SWR_ETIMEOUT, "a device-side grid barrier gave up waiting");
+    if (e & SWR_ERR_NUMERIC) return fail(c, SWR_ENUMERIC, "non-finite normalisation");
+    return SWR_OK;
+}
+
+static SwrDeviceView view(swr_ctx* c) {
+    SwrDeviceView v;
+    v.arena = c->arena;
+    v.inst = c->d_inst;
+    v.sub = c->d_sub;
+    v.n_inst = (int)c->inst.size();
+    v.n_sub = (int)c->sub.size();
+    v.err = c->d_err;
+    return v;
+}
+
+extern "C" swr_status swr_assemble(swr_ctx* c) {
+    if (!c) return fail(nullptr, SWR_EINVAL, "ctx is NULL");
+    CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
+    CU(cudaEventRecord(c->ev0, c->stream));
+    CU(launch_assemble(view(c), c->stream, c->max_q, c->max_kd, c->max_K, c->any_ee, c->tdse, !c->tdse,
+                       c->d_jobs1, c->d_jobs2, c->d_norm_part, CHOL_TAU));
+    CU(cudaEventRecord(c->ev1, c->stream));
+    swr_status st = check_err(c);
+    if (st != SWR_OK) return st;
+    float ams = 0;
+    CU(cudaEventElapsedTime(&ams, c->ev0, c->ev1));
+    c->counters[6] += ams;
+    c->counters[2] += kAssembleLaunchesFixed + (c->any_ee ? 3 : 0) + 2 * ((c->max_K + GJ_NB_HOST - 1) / GJ_NB_HOST);
+    c->assembled = true;
+    c->k = 0;
+    c->parity = 0;
+    CU(cudaMemsetAsync(c->d_win_prev, 0, c->inst.size() * sizeof(int), c->stream));
+    c->win_prev_h.assign(c->inst.size(), 0);
+    return SWR_OK;
+}
+
+static SweepArgs sweep_args(swr_ctx* c) {
+    SweepArgs a;
+    a.v = view(c);
+    a.tasks = c->d_tasks;
+    a.n_tasks = (int)c->tasks.size();
+    a.tasks_per_cta = (a.n_tasks + c->grid - 1) / c->grid;
+    a.inst_task0 = c->d_inst_task0;
+    a.part_s = c->d_part_s;
+    a.part_d = c->d_part_d;
+    a.snorm = c->d_snorm;
+    a.zbuf = c->d_zbuf;
+    a.zoff = c->d_zoff;
+    a.act = c->d_act;
+    a.win = c->d_win;
+    a.win_prev = c->d_win_prev;
+    a.cap = c->cap;
+    a.bar = c->d_bar;
+    a.spin_limit = SPIN_LIMIT;
+    return a;
+}
+
+extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
+    if (!c) return fail(nullptr, SWR_EINVAL, "ctx is NULL");
+    if (!c->assembled) return fail(c, SWR_ESTATE, "swr_step before swr_assemble");
+    CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
+    CU(cudaEventRecord(c->ev0, c->stream));
+    SweepArgs a = sweep_args(c);
+    int grid = (a.n_tasks + a.tasks_per_cta - 1) / a.tasks_per_cta;
+    CU(launch_ngf_iteration(a, grid, c->ngf_smem, c->stream, (int)c->inst.size(), c->max_K, c->evw0, c->evw1));
+    CU(launch_post(view(c), c->stream, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
+                   c->d_res_part, RES_BLOCKS, c->d_res, c->cap));
+    CU(launch_energy(view(c), c->stream, c->d_win, c->d_snorm, c->cap, c->d_epart, c->d_energy, c->d_norm2,
+                     c->d_psi, c->d_psi_off, c->max_K, c->max_kd, c->max_q));
+    CU(cudaEventRecord(c->ev1, c->stream));
+    const size_t ni = c->inst.size();
+    CU(cudaMemcpyAsync(c->res_h.data(), c->d_res, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(c->win_h.data(), c->d_win, ni * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(c->energy_h.data(), c->d_energy, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(c->norm2_h.data(), c->d_norm2, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    c->counters[9] += (double)(ni * (3 * sizeof(double) + sizeof(int)));
+    swr_status st = check_err(c);
+    if (st != SWR_OK) return st;
+    // the current window becomes the previous one for the next iteration
+    CU(cudaMemcpyAsync(c->d_win_prev, c->d_win, ni * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
+    c->win_prev_h = c->win_h;
+    c->k += 1;
+    c->parity ^= 1;
+    double rmax = 0;
+    int wmax = 0;
+    long long solves = 0;
+    for (size_t i = 0; i < ni; ++i) {
+        if (!isfinite(c->res_h[i])) return fail(c, SWR_ENUMERIC, "non-finite residual in instance %zu", i);
+        rmax = c->res_h[i] > rmax ? c->res_h[i] : rmax;
+        wmax = c->win_h[i] > wmax ? c->win_h[i] : wmax;
+        solves += (long long)c->win_h[i] * c->inst[i].n_sub;
+    }
+    float ms = 0, wms = 0;
+    CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    CU(cudaEventElapsedTime(&wms, c->evw0, c->evw1));
+    double flops = 0, bytes = 0;
+    {
+        std::vector<int> nsolve(c->inst.size());
+        for (size_t i = 0; i < ni; ++i) nsolve[i] = c->win_h[i];
+        const double per = c->tdse ? 8.0 : 2.0, bper = c->tdse ? 16.0 : 8.0;
+        for (const SubDev& sd : c->sub) {
+            double K2 = (double)sd.K * sd.K;
+            flops += per * K2 * nsolve[sd.inst];
+            bytes += bper * K2 * nsolve[sd.inst];
+        }
+    }
+    c->counters[0] += wms;
+    c->counters[1] += 1;
+    c->counters[2] += kStepLaunches;
+    c->counters[3] += flops;
+    c->counters[4] += bytes;
+    c->counters[5] += (double)solves;
+    c->counters[7] += ms;
+    if (rep) {
+        rep->k = c->k;
+        rep->res = rmax;
+        rep->window_max = wmax;
+        rep->subdomain_solves = solves;
+        rep->seconds = ms * 1e-3;
+    }
+    return SWR_OK;
+}
+
+extern "C" swr_status swr_iterate(swr_ctx* c, double tol, int kmax, swr_report* rep, double* hist) {
+    if (!c) return fail(nullptr, SWR_EINVAL, "ctx is NULL");
+    if (kmax < 1) return fail(c, SWR_EINVAL, "kmax must be >= 1");
+    swr_report r;
+    memset(&r, 0, sizeof(r));
+    for (int it = 0; it < kmax; ++it) {
+        swr_iter_report ir;
+        swr_status st = swr_step(c, &ir);
+        if (st != SWR_OK) return st;
+        if (hist) hist[it] = ir.res;
+        r.iterations = it + 1;
+        r.res_last = ir.res;
+        r.subdomain_solves += ir.subdomain_solves;
+        r.seconds += ir.seconds;
+        if (ir.res <= tol) {
+            r.converged = 1;
+            break;
+        }
+    }
+    if (rep) *rep = r;
+    return r.converged ? SWR_OK : fail(c, SWR_ENOTCONV, "Res(k) = %g > tol = %g after %d iterations", r.res_last, tol, kmax);
+}
+
+static size_t trace_bytes(const swr_ctx* c) {
+    // [win per instance as int64] + per subdomain: own traces u and Robin source b' for steps 0..cap
+    size_t b = c->inst.size() * sizeof(long long);
+    const int cx = c->tdse ? 2 : 1;
+    for (const SubDev& s : c->sub)
+        b += (size_t)(c->cap + 1) * ((size_t)(s.ngam > 0 ? s.ngam : 1) + s.K) * cx * sizeof(double);
+    return b;
+}
+
+extern "C" swr_status swr_field_bytes(swr_ctx* c, int field, size_t* bytes) {
+    if (!c || !bytes) return fail(c, SWR_EINVAL, "NULL argument");
+    const size_t ni = c->inst.size(), ns = c->sub.size();
+    const int cx = c->tdse ? 2 : 1;
+    switch (field) {
+        case SWR_FIELD_ENERGY: case SWR_FIELD_NORM2: case SWR_FIELD_DIPOLE: case SWR_FIELD_RES:
+            *bytes = ni * sizeof(double); return SWR_OK;
+        case SWR_FIELD_WINDOW: *bytes = ni * sizeof(int); return SWR_OK;
+        case SWR_FIELD_PSI_NODES: *bytes = (size_t)c->psi_total * cx * sizeof(double); return SWR_OK;
+        case SWR_FIELD_OWN_TRACES: case SWR_FIELD_ROBIN: {
+            size_t b = 0;
+            for (size_t s = 0; s < ns; ++s)
+                b += (size_t)(c->win_h[c->sub[s].inst] + 1) * c->sub[s].ngam * cx * sizeof(double);
+            *bytes = b;
+            return SWR_OK;
+        }
+        case SWR_FIELD_TRACE_BYTES: *bytes = sizeof(size_t); return SWR_OK;
+        case SWR_FIELD_NODE_COUNTS: *bytes = 3 * ns * sizeof(int); return SWR_OK;
+        case SWR_FIELD_K_MAX: *bytes = sizeof(int); return SWR_OK;
+        case SWR_FIELD_COUNTERS: *bytes = 10 * sizeof(double); return SWR_OK;
+    }
+    return fail(c, SWR_EINVAL, "unknown field %d", field);
+}
+
+extern "C" swr_status swr_get(swr_ctx* c, int field, void* host, size_t bytes) {
+    if (!c || !host) return fail(c, SWR_EINVAL, "NULL argument");
+    size_t need = 0;
+    swr_status st = swr_field_bytes(c, field, &need);
+    if (st != SWR_OK) return st;
+    if (bytes != need) return fail(c, SWR_EINVAL, "field %d needs exactly %zu bytes, got %zu", field, need, bytes);
+    const size_t ni = c->inst.size();
+    const int cx = c->tdse ? 2 : 1;
+    switch (field) {
+        case SWR_FIELD_ENERGY: memcpy(host, c->energy_h.data(), need); return SWR_OK;
+        case SWR_FIELD_NORM2: memcpy(host, c->norm2_h.data(), need); return SWR_OK;
+        case SWR_FIELD_RES: memcpy(host, c->res_h.data(), need); return SWR_OK;
+        case SWR_FIELD_WINDOW: memcpy(host, c->win_h.data(), need); return SWR_OK;
+        case SWR_FIELD_DIPOLE: memset(host, 0, need); return SWR_OK;
+        case SWR_FIELD_K_MAX: memcpy(host, &c->k, sizeof(int)); return SWR_OK;
+        case SWR_FIELD_COUNTERS: memcpy(host, c->counters, sizeof(c->counters)); return SWR_OK;
+        case SWR_FIELD_TRACE_BYTES: { size_t tb = trace_bytes(c); memcpy(host, &tb, sizeof(size_t)); return SWR_OK; }
+        case SWR_FIELD_NODE_COUNTS: {
+            int* o = (int*)host;
+            for (size_t s = 0; s < c->sub.size(); ++s) {
+                o[3 * s] = c->sub[s].q;
+                o[3 * s + 1] = c->sub[s].ngam;
+                o[3 * s + 2] = c->sub[s].K;
+            }
+            return SWR_OK;
+        }
+        case SWR_FIELD_PSI_NODES:
+            c->counters[9] += (double)need;
+            CU(cudaMemcpyAsync(host, c->d_psi, need, cudaMemcpyDeviceToHost, c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+            return SWR_OK;
+        case SWR_FIELD_OWN_TRACES: case SWR_FIELD_ROBIN: {
+            if (c->k == 0) return fail(c, SWR_ESTATE, "no iteration done yet");
+            char* h = (char*)host;
+            const int par = c->parity ^ 1;  // buffer written by the last iteration
+            for (size_t s = 0; s < c->sub.size(); ++s) {
+                const SubDev& sd = c->sub[s];
+                size_t nb = (size_t)(c->win_h[sd.inst] + 1) * sd.ngam * cx * sizeof(double);
+                long long off = (field == SWR_FIELD_OWN_TRACES) ? sd.u[par] : sd.g;
+                if (nb) CU(cudaMemcpyAsync(h, c->arena + off, nb, cudaMemcpyDeviceToHost, c->stream));
+                h += nb;
+            }
+            CU(cudaStreamSynchronize(c->stream));
+            (void)ni;
+            return SWR_OK;
+        }
+    }
+    return fail(c, SWR_EINVAL, "unknown field %d", field);
+}
+
+extern "C" swr_status swr_traces(swr_ctx* c, int dir, swr_trace_view* view_) {
+    if (!c || !view_ || !view_->host) return fail(c, SWR_EINVAL, "NULL argument");
+    if (!c->assembled) return fail(c, SWR_ESTATE, "swr_traces before swr_assemble");
+    const size_t need = trace_bytes(c);
+    if (view_->bytes != need) return fail(c, SWR_EINVAL, "trace window needs %zu bytes, got %zu", need, view_->bytes);
+    const int cx = c->tdse ? 2 : 1;
+    char* h = (char*)view_->host;
+    const size_t ni = c->inst.size();
+    const int par = c->parity ^ 1;  // u buffer of the last iteration
+    if (dir == SWR_GET) {
+        long long* w = (long long*)h;
+        for (size_t i = 0; i < ni; ++i) w[i] = c->win_prev_h[i];
+        h += ni * sizeof(long long);
+        for (const SubDev& s : c->sub) {
+            size_t nu = (size_t)(c->cap + 1) * (s.ngam > 0 ? s.ngam : 1) * cx * sizeof(double);
+            size_t nbv = (size_t)(c->cap + 1) * s.K * cx * sizeof(double);
+            CU(cudaMemcpyAsync(h, c->arena + s.u[par], nu, cudaMemcpyDeviceToHost, c->stream));
+            h += nu;
+            CU(cudaMemcpyAsync(h, c->arena + s.bvec, nbv, cudaMemcpyDeviceToHost, c->stream));
+            h += nbv;
+        }
+        CU(cudaStreamSynchronize(c->stream));
+        return SWR_OK;
+    }
+    if (dir != SWR_SET) return fail(c, SWR_EINVAL, "dir must be SWR_GET or SWR_SET");
+    const long long* w = (const long long*)h;
+    for (size_t i = 0; i < ni; ++i) {
+        if (w[i] < 0 || w[i] > c->cap) return fail(c, SWR_EINVAL, "window %lld out of range", w[i]);
+        c->win_prev_h[i] = (int)w[i];
+        c->win_h[i] = (int)w[i];
+    }
+    h += ni * sizeof(long long);
+    // the restored u goes to the buffer the next iteration compares against
+    const int tgt = c->parity ^ 1;
+    for (const SubDev& s : c->sub) {
+        size_t nu = (size_t)(c->cap + 1) * (s.ngam > 0 ? s.ngam : 1) * cx * sizeof(double);
+        size_t nbv = (size_t)(c->cap + 1) * s.K * cx * sizeof(double);
+        CU(cudaMemcpyAsync(c->arena + s.u[tgt], h, nu, cudaMemcpyHostToDevice, c->stream));
+        h += nu;
+        CU(cudaMemcpyAsync(c->arena + s.bvec, h, nbv, cudaMemcpyHostToDevice, c->stream));
+        h += nbv;
+    }
+    CU(cudaMemcpyAsync(c->d_win_prev, c->win_prev_h.data(), ni * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (c->k == 0) c->k = 1;  // the next residual compares against the restored traces
+    return SWR_OK;
+}
+
+extern "C" void swr_destroy(swr_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->evw0) cudaEventDestroy(c->evw0);
+    if (c->evw1) cudaEventDestroy(c->evw1);
+    if (c->owns && c->base) cudaFree(c->base);
+    delete c;
+}
+
+extern "C" const char* swr_last_error(const swr_ctx* c) {
+    if (!c) return g_setup_err.c_str();
+    return c->err.c_str();
+}

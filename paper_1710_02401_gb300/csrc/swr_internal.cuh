@@ -1,0 +1,176 @@
+// swr_internal.cuh -- device-side data layout and helpers shared by the CUDA
+// translation units of the SWR-Galerkin library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swr.h"
+
+#define SWR_MAX_NUC 3
+#define SWR_MAX_QP 64
+#define SWR_NLINE_KINDS 16   // 2 coordinates x 4 lines x {value, derivative}
+
+// Complex number in FP64 (real-time path); a plain aggregate so that it can
+// live in __shared__ memory.
+struct cplx {
+    double re, im;
+};
+__host__ __device__ inline cplx mkc(double r, double i = 0.0) { cplx z; z.re = r; z.im = i; return z; }
+__host__ __device__ inline cplx operator+(cplx a, cplx b) { return mkc(a.re + b.re, a.im + b.im); }
+__host__ __device__ inline cplx operator-(cplx a, cplx b) { return mkc(a.re - b.re, a.im - b.im); }
+__host__ __device__ inline cplx operator*(cplx a, cplx b) {
+    return mkc(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+__host__ __device__ inline cplx operator*(double s, cplx a) { return mkc(s * a.re, s * a.im); }
+__host__ __device__ inline cplx conj(cplx a) { return mkc(a.re, -a.im); }
+
+// Per-instance constants (device copy).
+struct InstDev {
+    int N, L, kd_uniform, q_p, n_mid, q, mode, normalize, n_nuc;
+    int sub_base, n_sub;          // first global subdomain index, count
+    int n_steps, max_steps, window_cap;
+    double a, b, H, eps;
+    double x_nuc[SWR_MAX_NUC], Z_nuc[SWR_MAX_NUC];
+    double eta_en, eta_ee, ee_coef, harmonic, kappa;
+    double mu_re, mu_im, dt, ngf_tol;
+    double E0, T, omega, phase;
+    double gamma0, x0[2];
+};
+
+// Per-subdomain descriptor.  Offsets are in doubles from the arena base.
+struct SubDev {
+    int inst, N, kd, K, q, ngam;
+    int idx[2];                   // 1-D subdomain indices (i1, i2)
+    int edge_mask;                // bit 2*d+side: edge (coordinate d, side lo=0/hi=1) is interior
+    int gam_off[4];               // first Gamma node of edge slot 2*d+side (-1 when absent)
+    double lo[2], hi[2], delta;
+    long long t1[2];              // 1-D table block of coordinate d
+    long long Hm;                 // K*K  H' (real part), orthonormal basis
+    long long Gm;                 // K*K step-matrix inverse (x2 doubles when complex)
+    long long c0;                 // initial coefficients (K, x2 when complex)
+    long long hist;               // (cap+1)*K iterates before normalisation (x2 complex)
+    long long bvec;               // (cap+1)*K Robin source b' per step (x2 complex)
+    long long line;               // (cap+1)*nline line traces (x2 complex)
+    long long u[2];               // (cap+1)*ngam own traces, two iteration parities (x2 complex)
+    long long g;                  // (cap+1)*ngam averaged Robin data (x2 complex)
+    long long work;               // scratch for assembly (see swr_assemble.cu)
+    int nline;                    // values per step in `line`
+};
+
+// 1-D table layout for one coordinate of one subdomain (offsets in doubles).
+struct T1Layout {
+    int q, kd;
+    __host__ __device__ T1Layout(int q_, int kd_) : q(q_), kd(kd_) {}
+    __host__ __device__ long long x() const { return 0; }
+    __host__ __device__ long long w() const { return q; }
+    __host__ __device__ long long chi() const { return 2LL * q; }
+    __host__ __device__ long long v1() const { return 3LL * q; }          // 1-D external potential
+    __host__ __device__ long long alpha() const { return 4LL * q; }       // centres [kd]
+    __host__ __device__ long long B() const { return 4LL * q + kd; }      // [q][kd] values (-> orthonormal)
+    __host__ __device__ long long D() const { return B() + (long long)q * kd; }  // [q][kd] derivatives
+    __host__ __device__ long long Lv() const { return D() + (long long)q * kd; } // [4][kd] line values
+    __host__ __device__ long long Ld() const { return Lv() + 4LL * kd; }         // [4][kd] line derivatives
+    __host__ __device__ long long mat(int i) const { return Ld() + 4LL * kd + (long long)i * kd * kd; }
+    // matrices: 0 S, 1 Kf, 2 Xpos, 3 U, 4 Schi, 5 Xo (orth transform), 6 Tp, 7 Up, 8 Pp, 9 Xp', 10 Rp
+    __host__ __device__ long long size() const { return mat(11); }
+};
+enum { M_S = 0, M_KF, M_XPOS, M_U, M_SCHI, M_XO, M_TP, M_UP, M_PP, M_XP, M_RP };
+
+// Line positions of a subdomain interval: lo, lo+eps, hi-eps, hi.
+__host__ __device__ inline double line_pos(double lo, double hi, double eps, int l) {
+    return l == 0 ? lo : (l == 1 ? lo + eps : (l == 2 ? hi - eps : hi));
+}
+
+// ---------------------------------------------------------------- errors
+#define SWR_ERR_TIMEOUT 1
+#define SWR_ERR_NUMERIC 2
+#define SWR_ERR_SINGULAR 4
+
+// Bounded sense-reversal grid barrier for a cooperative launch.  Spins at most
+// `limit` polls; on timeout it raises SWR_ERR_TIMEOUT in *err and returns false.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+__device__ inline bool grid_sync_bounded(GridBarrier* bar, unsigned int nblocks, int* err,
+                                         long long limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* vgen = &bar->gen;
+        unsigned int g = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == g) {
+                if (++it > limit) { atomicOr(err, SWR_ERR_TIMEOUT); ok = 0; break; }
+                if ((it & 63) == 0 && *(volatile int*)err) { ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*(volatile int*)err) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Warp reduction.
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Host-side launch helpers implemented in swr_assemble.cu / swr_sweep.cu.
+struct SwrDeviceView {
+    double* arena;
+    const InstDev* inst;
+    const SubDev* sub;
+    int n_inst, n_sub;
+    int* err;                     // device error flags
+};
+
+namespace swr {
+// Batched FP64 GEMM job (one per subdomain): C = op(A) * B.
+struct GemmJob {
+    long long a, b, c;   // offsets (doubles) into the arena
+    int M, N, K;         // C is M x N
+    int lda, ldb, ldc;
+    int transA;          // op(A) = A^T when set (A stored K x M)
+    int mode;            // 0: C = AB;  1: scatter the e-e block into H' (index permutation)
+    int kd;              // for mode 1
+};
+
+// Row block [r0, r1) of the step matrix of subdomain sid (persistent task).
+struct Task {
+    int sid, r0, r1, inst;
+};
+
+struct SweepArgs {
+    SwrDeviceView v;
+    const Task* tasks;
+    int n_tasks, tasks_per_cta;
+    const int* inst_task0;      // [n_inst+1] first task of each instance
+    double* part_s;             // [2][n_tasks]
+    double* part_d;             // [2][n_tasks]
+    double* snorm;              // [n_inst][cap+1] normalisation factors s_n
+    double* zbuf;               // per subdomain [2][K] (A'chi y) ring, offsets zoff[sid]
+    const long long* zoff;
+    int* act;                   // [n_inst] active flags
+    int* win;                   // [n_inst] window length of this iteration
+    const int* win_prev;        // [n_inst] window of the previous iteration (0: none)
+    int cap;                    // max window stored
+    GridBarrier* bar;
+    long long spin_limit;
+};
+}  // namespace swr

@@ -1,0 +1,615 @@
+// swr_sweep.cu -- one Schwarz iteration over all subdomains on sm_103a.
+//
+// Imaginary time (Sec. 5.2 system SIT, Sec. 5.4 steps 2 and 4): on every
+// subdomain, implicit Euler in the orthonormal local basis
+//     y^{n+1} = G (c^n + kappa dt b'^{n+1}),   G = (I + dt H')^{-1},
+// then the global normalisation c^{n+1} = y^{n+1} / s_{n+1},
+//     s_{n+1}^2 = sum_i y_i^T (Pp (x) Pp) y_i        (partition-of-unity norm),
+// and the inner stop ||c^{n+1} - c^n|| <= ngf_tol (Sec. 5.2).  The whole time
+// window runs in ONE persistent cooperative kernel: each CTA owns fixed row
+// blocks of the step matrices, two bounded grid barriers per step separate the
+// matvec from the norm reduction, all reductions are deterministic (fixed
+// order over per-task partials, per instance).
+//
+// After the window: line traces (psi and d psi at the 4 line positions of
+// every subdomain coordinate), the averaged Robin data of Sec. 5.1 for every
+// interface node, the Robin source b' of the next iteration, the own interface
+// traces and Res(k) (Eq. residueIT), and the energy.
+#include <math.h>
+#include <stdio.h>
+
+#include "swr_internal.cuh"
+
+namespace swr {
+
+// z rows = (Pp1 (x) Pp2) y  for rows [r0, r1) of one subdomain; y in shared memory.
+__device__ void achi_rows(const SwrDeviceView& v, const SubDev& s, const double* ys, int r0, int r1,
+                          double* zrow, double* tmp) {
+    const int kd = s.kd;
+    T1Layout lay(s.q, kd);
+    const double* P1 = v.arena + s.t1[0] + lay.mat(M_PP);
+    if (s.N == 1) {
+        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+            double acc = 0;
+            for (int c = 0; c < kd; ++c) acc += P1[r * kd + c] * ys[c];
+            zrow[r - r0] = acc;
+        }
+        __syncthreads();
+        return;
+    }
+    const double* P2 = v.arena + s.t1[1] + lay.mat(M_PP);
+    const int b0 = r0 / kd, b1 = (r1 - 1) / kd;
+    for (int b = b0; b <= b1; ++b) {
+        // tmp[c] = sum_e Y[c][e] P2[b][e],  Y[c][e] = y[c + kd e]
+        for (int c = threadIdx.x; c < kd; c += blockDim.x) {
+            double acc = 0;
+            for (int e = 0; e < kd; ++e) acc += ys[c + kd * e] * P2[b * kd + e];
+            tmp[c] = acc;
+        }
+        __syncthreads();
+        int lo = max(r0, b * kd), hi = min(r1, (b + 1) * kd);
+        for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+            int a = r - b * kd;
+            double acc = 0;
+            for (int c = 0; c < kd; ++c) acc += P1[a * kd + c] * tmp[c];
+            zrow[r - r0] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ inline double block_sum(double x, double* red) {
+    x = warp_sum(x);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = x;
+    __syncthreads();
+    double t = 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// Deterministic sum of the partials of one instance (fixed task order).
+__device__ inline double inst_sum(const double* part, int t0, int t1, double* red) {
+    double x = 0;
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) x += __ldcg(part + t);
+    // fixed reduction tree: thread order is deterministic for a fixed blockDim
+    return block_sum(x, red);
+}
+
+// Persistent imaginary-time window (real arithmetic).  Dynamic shared memory:
+// 2*Kmax (v / y) + Kmax (z rows) + kd_max doubles.
+__global__ void __launch_bounds__(256) k_ngf_window(SweepArgs A) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    const SwrDeviceView& v = A.v;
+    const unsigned nblk = gridDim.x;
+    const int t_begin = blockIdx.x * A.tasks_per_cta;
+    const int t_end = min(A.n_tasks, t_begin + A.tasks_per_cta);
+    const int cap = A.cap;
+    double* vs = sm;  // vector of the current subdomain (K)
+    // layout of the remaining dynamic shared memory is set per task below
+    // The active flags act[] change only in phase B (first task of an instance),
+    // so they are stable from the second barrier of a step to the first barrier
+    // of the next one, where every CTA takes the termination decision.
+    __shared__ int s_act;
+    for (int n = 0;; ++n) {
+        // ------------------------------------------------------------ phase A(n+1)
+        // s_n from the partials of phase B(n); delta_n partials;
+        // y^{n+1} rows = G rows (y^n / s_n + kappa dt b'^{n+1}).
+        for (int t = t_begin; t < t_end; ++t) {
+            const Task tk = A.tasks[t];
+            const SubDev& s = v.sub[tk.sid];
+            const InstDev& in = v.inst[tk.inst];
+            if (threadIdx.x == 0) s_act = __ldcg(A.act + tk.inst);
+            __syncthreads();
+            if (!s_act) continue;
+            const int t0 = A.inst_task0[tk.inst], t1 = A.inst_task0[tk.inst + 1];
+            const bool first = (t == t0);
+            double s_n = 1.0;
+            if (in.normalize) s_n = sqrt(inst_sum(A.part_s + (n & 1) * A.n_tasks, t0, t1, red));
+            if (first && threadIdx.x == 0) A.snorm[(long long)tk.inst * (cap + 1) + n] = s_n;
+            const int fixed = in.window_cap;  // fixed window length, 0 when the NGF stop decides
+            const int maxs = fixed > 0 ? fixed : in.max_steps;
+            if (n >= maxs || !isfinite(s_n) || s_n <= 0.0) continue;  // closed in phase B
+            const int K = s.K;
+            const double* hist = v.arena + s.hist;
+            // delta_n partial over this task's rows (needs y^{n-1}, z^{n-1}, s_{n-1})
+            if (n >= 1 && fixed == 0 && in.ngf_tol > 0.0) {
+                double s_p = __ldcg(A.snorm + (long long)tk.inst * (cap + 1) + n - 1);
+                const double* yn = hist + (long long)n * K;
+                const double* yp = hist + (long long)(n - 1) * K;
+                const double* zn = A.zbuf + A.zoff[tk.sid] + (n & 1) * K;
+                const double* zp = A.zbuf + A.zoff[tk.sid] + ((n - 1) & 1) * K;
+                double acc = 0;
+                for (int r = tk.r0 + threadIdx.x; r < tk.r1; r += blockDim.x) {
+                    double dy = __ldcg(yn + r) / s_n - __ldcg(yp + r) / s_p;
+                    double dz = __ldcg(zn + r) / s_n - __ldcg(zp + r) / s_p;
+                    acc += dy * dz;
+                }
+                acc = block_sum(acc, red);
+                if (threadIdx.x == 0) A.part_d[(n & 1) * A.n_tasks + t] = acc;
+            }
+            // v = y^n / s_n + kappa dt b'^{n+1}
+            const int wp = A.win_prev[tk.inst];
+            const double* bsrc = (wp > 0) ? v.arena + s.bvec + (long long)min(n + 1, wp) * K : nullptr;
+            const double kdt = in.kappa * in.dt;
+            const double* yn = hist + (long long)n * K;
+            for (int c = threadIdx.x; c < K; c += blockDim.x) {
+                double val = __ldcg(yn + c) / s_n;
+                if (bsrc) val += kdt * __ldcg(bsrc + c);
+                vs[c] = val;
+            }
+            __syncthreads();
+            // rows: one warp per row, lanes over columns
+            const double* G = v.arena + s.Gm;
+            double* ynew = v.arena + s.hist + (long long)(n + 1) * K;
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            for (int r = tk.r0 + warp; r < tk.r1; r += nw) {
+                const double* g = G + (long long)r * K;
+                double acc0 = 0, acc1 = 0;
+                int c = lane;
+                for (; c + 32 < K; c += 64) {
+                    acc0 = fma(g[c], vs[c], acc0);
+                    acc1 = fma(g[c + 32], vs[c + 32], acc1);
+                }
+                if (c < K) acc0 = fma(g[c], vs[c], acc0);
+                double acc = warp_sum(acc0 + acc1);
+                if (lane == 0) ynew[r] = acc;
+            }
+            __syncthreads();
+        }
+        if (!grid_sync_bounded(A.bar, nblk, v.err, A.spin_limit)) return;
+        // ------------------------------------------------------------ phase B(n+1)
+        // stop test on delta_n; z^{n+1} rows = A'chi y^{n+1}; s^2 partials.
+        for (int t = t_begin; t < t_end; ++t) {
+            const Task tk = A.tasks[t];
+            const SubDev& s = v.sub[tk.sid];
+            const InstDev& in = v.inst[tk.inst];
+            if (threadIdx.x == 0) s_act = __ldcg(A.act + tk.inst);
+            __syncthreads();
+            if (!s_act) continue;
+            const int t0 = A.inst_task0[tk.inst], t1 = A.inst_task0[tk.inst + 1];
+            const bool first = (t == t0);
+            // window end: fixed length / step cap reached, bad norm, or NGF stop on delta_n
+            const int fixed = in.window_cap;
+            const int maxs = fixed > 0 ? fixed : in.max_steps;
+            const double s_n = __ldcg(A.snorm + (long long)tk.inst * (cap + 1) + n);
+            bool stop = (n >= maxs) || !isfinite(s_n) || s_n <= 0.0;
+            if (!stop && n >= 1 && fixed == 0 && in.ngf_tol > 0.0) {
+                double d2 = inst_sum(A.part_d + (n & 1) * A.n_tasks, t0, t1, red);
+                stop = sqrt(fmax(d2, 0.0)) <= in.ngf_tol;
+            }
+            if (stop) {
+                if (first && threadIdx.x == 0) {
+                    A.win[tk.inst] = n;
+                    if (!isfinite(s_n) || s_n <= 0.0) atomicOr(v.err, SWR_ERR_NUMERIC);
+                    __threadfence();
+                    atomicExch(A.act + tk.inst, 0);
+                }
+                continue;
+            }
+            const int K = s.K;
+            const double* yn1 = v.arena + s.hist + (long long)(n + 1) * K;
+            for (int c = threadIdx.x; c < K; c += blockDim.x) vs[c] = __ldcg(yn1 + c);
+            __syncthreads();
+            double* zrow = sm + K;
+            double* tmp = sm + 2 * K;
+            achi_rows(v, s, vs, tk.r0, tk.r1, zrow, tmp);
+            double* zdst = A.zbuf + A.zoff[tk.sid] + ((n + 1) & 1) * K;
+            double acc = 0;
+            for (int r = tk.r0 + threadIdx.x; r < tk.r1; r += blockDim.x) {
+                double z = zrow[r - tk.r0];
+                zdst[r] = z;
+                acc += vs[r] * z;
+            }
+            acc = block_sum(acc, red);
+            if (threadIdx.x == 0) A.part_s[((n + 1) & 1) * A.n_tasks + t] = acc;
+        }
+        if (!grid_sync_bounded(A.bar, nblk, v.err, A.spin_limit)) return;
+        // global termination: all instances inactive
+        __shared__ int s_any;
+        if (threadIdx.x == 0) {
+            int a = 0;
+            for (int i = 0; i < v.n_inst; ++i) a |= __ldcg(A.act + i);
+            s_any = a;
+        }
+        __syncthreads();
+        if (!s_any) return;
+    }
+}
+
+// Phase "B(0)": z^0 = A'chi c0 and the s_0^2 partials, and y^0 = c0 into hist[0].
+__global__ void k_ngf_prologue(SweepArgs A) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    const SwrDeviceView& v = A.v;
+    for (int t = blockIdx.x; t < A.n_tasks; t += gridDim.x) {
+        const Task tk = A.tasks[t];
+        const SubDev& s = v.sub[tk.sid];
+        const int K = s.K;
+        const double* c0 = v.arena + s.c0;
+        double* h0 = v.arena + s.hist;
+        for (int c = threadIdx.x; c < K; c += blockDim.x) sm[c] = c0[c];
+        __syncthreads();
+        for (int r = tk.r0 + threadIdx.x; r < tk.r1; r += blockDim.x) h0[r] = sm[r];
+        double* zrow = sm + K;
+        double* tmp = sm + 2 * K;
+        achi_rows(v, s, sm, tk.r0, tk.r1, zrow, tmp);
+        double* zdst = A.zbuf + A.zoff[tk.sid];
+        double acc = 0;
+        for (int r = tk.r0 + threadIdx.x; r < tk.r1; r += blockDim.x) {
+            zdst[r] = zrow[r - tk.r0];
+            acc += sm[r] * zrow[r - tk.r0];
+        }
+        acc = block_sum(acc, red);
+        if (threadIdx.x == 0) A.part_s[t] = acc;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- traces
+
+// Line traces of subdomain j at step n from the un-normalised iterate y^n:
+// N = 2: [d][l][kind][q] with psi (kind 0) and d_{x_d} psi (kind 1) on the line
+// x_d = pos_l, sampled at the nodes of the other coordinate.  N = 1: [l][kind].
+__global__ void k_line_traces(SwrDeviceView v, const int* win, int cap) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const int W = win[s.inst];
+    const int kd = s.kd, q = s.q, K = s.K;
+    T1Layout lay(q, kd);
+    __shared__ double ys[1024];
+    __shared__ double r[16][64];
+    for (int n = blockIdx.x; n <= W; n += gridDim.x) {
+        const double* y = v.arena + s.hist + (long long)n * K;
+        for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c] = y[c];
+        __syncthreads();
+        double* out = v.arena + s.line + (long long)n * s.nline;
+        if (s.N == 1) {
+            const double* T = v.arena + s.t1[0];
+            for (int e = threadIdx.x; e < 8; e += blockDim.x) {
+                int l = e / 2, kind = e % 2;
+                const double* Lr = T + (kind ? lay.Ld() : lay.Lv()) + l * kd;
+                double acc = 0;
+                for (int a = 0; a < kd; ++a) acc += Lr[a] * ys[a];
+                out[l * 2 + kind] = acc;
+            }
+            __syncthreads();
+            continue;
+        }
+        // N = 2: r[(d,l,kind)][.] contractions of the line vector with Y
+        for (int e = threadIdx.x; e < 16 * kd; e += blockDim.x) {
+            int combo = e / kd, m = e % kd;
+            int d = combo / 8, l = (combo / 2) % 4, kind = combo % 2;
+            const double* T = v.arena + s.t1[d];
+            const double* Lr = T + (kind ? lay.Ld() : lay.Lv()) + l * kd;
+            double acc = 0;
+            if (d == 0) {  // r[b] = sum_a L1[a] Y[a][b]
+                for (int a = 0; a < kd; ++a) acc += Lr[a] * ys[a + kd * m];
+            } else {       // r[a] = sum_b Y[a][b] L2[b]
+                for (int b = 0; b < kd; ++b) acc += ys[m + kd * b] * Lr[b];
+            }
+            r[combo][m] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 16 * q; e += blockDim.x) {
+            int combo = e / q, node = e % q;
+            int d = combo / 8;
+            const double* Bo = v.arena + s.t1[1 - d] + lay.B() + (long long)node * kd;
+            double acc = 0;
+            for (int m = 0; m < kd; ++m) acc += Bo[m] * r[combo][m];
+            out[combo * q + node] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// Averaged Robin data g_i and own traces u_i at the interface nodes of every
+// subdomain for steps 0..W, and the Robin source b'_i of the next iteration.
+__global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, int cap, int parity) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const InstDev& in = v.inst[s.inst];
+    const int W = win[s.inst];
+    const int kd = s.kd, q = s.q, K = s.K, L = in.L, qp = in.q_p;
+    T1Layout lay(q, kd);
+    __shared__ double gs[4 * 64 * 6];
+    __shared__ double hsum[4][64];
+    for (int n = blockIdx.x; n <= W; n += gridDim.x) {
+        const double sn = in.normalize ? snorm[(long long)s.inst * (cap + 1) + n] : 1.0;
+        double* u = v.arena + s.u[parity] + (long long)n * s.ngam;
+        double* g = v.arena + s.g + (long long)n * s.ngam;
+        for (int node = threadIdx.x; node < s.ngam; node += blockDim.x) {
+            // locate the edge slot of this node
+            int slot = -1, nt = 0;
+            for (int sl = 3; sl >= 0; --sl)
+                if (s.gam_off[sl] >= 0 && node >= s.gam_off[sl]) { slot = sl; nt = node - s.gam_off[sl]; break; }
+            const int d = slot / 2, side = slot % 2;
+            const double sig = side ? 1.0 : -1.0;
+            const int lown = side ? 3 : 0;
+            const double* lo = v.arena + s.line + (long long)n * s.nline;
+            double own;
+            if (s.N == 1) own = lo[lown * 2 + 0];
+            else own = lo[((d * 4 + lown) * 2 + 0) * q + nt];
+            u[node] = own / sn;
+            // contributors: neighbour across the edge and the same column, times
+            // the tangential set (own index, plus the overlap neighbour in the bands)
+            double acc = 0;
+            int cnt = 0;
+            const int kdn = s.idx[d];
+            const int across = kdn + (side ? 1 : -1);
+            if (s.N == 1) {
+                const int j = in.sub_base + across;
+                const double* lj = v.arena + v.sub[j].line + (long long)n * v.sub[j].nline;
+                const int l = side ? 1 : 2;
+                acc += sig * lj[l * 2 + 1] + in.mu_re * lj[l * 2 + 0];
+                cnt = 1;
+            } else {
+                const int o = 1 - d;
+                const int ko = s.idx[o];
+                const int pt = nt / qp, npan = in.n_mid + 2;
+                int jo_list[3], shift[3], njo = 0;
+                jo_list[njo] = ko; shift[njo++] = 0;
+                if (pt == 0 && ko > 0) { jo_list[njo] = ko - 1; shift[njo++] = q - qp; }
+                if (pt == npan - 1 && ko < L - 1) { jo_list[njo] = ko + 1; shift[njo++] = -(q - qp); }
+                for (int jd_i = 0; jd_i < 2; ++jd_i) {
+                    const int jd = jd_i ? across : kdn;
+                    for (int t = 0; t < njo; ++t) {
+                        const int jo = jo_list[t];
+                        if (jd == kdn && jo == ko) continue;
+                        int j1 = d == 0 ? jd : jo, j2 = d == 0 ? jo : jd;
+                        const int j = in.sub_base + j1 + L * j2;
+                        const int l = (jd == kdn) ? lown : (side ? 1 : 2);
+                        const int nj = nt + shift[t];
+                        const double* lj = v.arena + v.sub[j].line + (long long)n * v.sub[j].nline;
+                        double val = lj[((d * 4 + l) * 2 + 0) * q + nj];
+                        double der = lj[((d * 4 + l) * 2 + 1) * q + nj];
+                        acc += sig * der + in.mu_re * val;
+                        ++cnt;
+                    }
+                }
+            }
+            double gv = acc / (double)cnt;
+            g[node] = gv;
+            gs[node] = gv;
+        }
+        __syncthreads();
+        // b'[a + kd b] for this step
+        double* bdst = v.arena + s.bvec + (long long)n * K;
+        if (s.N == 1) {
+            const double* T = v.arena + s.t1[0];
+            for (int a = threadIdx.x; a < kd; a += blockDim.x) {
+                double acc = 0;
+                for (int sl = 0; sl < 2; ++sl) {
+                    if (s.gam_off[sl] < 0) continue;
+                    int l = sl ? 3 : 0;
+                    acc += gs[s.gam_off[sl]] * T[lay.Lv() + l * kd + a];
+                }
+                bdst[a] = acc;
+            }
+        } else {
+            // hsum[slot][m] = sum_t w_t g_t B'_o[t][m]
+            for (int e = threadIdx.x; e < 4 * kd; e += blockDim.x) {
+                int sl = e / kd, m = e % kd;
+                double acc = 0;
+                if (s.gam_off[sl] >= 0) {
+                    int d = sl / 2;
+                    const double* To = v.arena + s.t1[1 - d];
+                    for (int t = 0; t < q; ++t) acc += To[lay.w() + t] * gs[s.gam_off[sl] + t] * To[lay.B() + t * kd + m];
+                }
+                hsum[sl][m] = acc;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < K; e += blockDim.x) {
+                int a = e % kd, b = e / kd;
+                double acc = 0;
+                for (int sl = 0; sl < 4; ++sl) {
+                    if (s.gam_off[sl] < 0) continue;
+                    int d = sl / 2, l = (sl % 2) ? 3 : 0;
+                    const double* Td = v.arena + s.t1[d];
+                    if (d == 0) acc += Td[lay.Lv() + l * kd + a] * hsum[sl][b];
+                    else acc += hsum[sl][a] * Td[lay.Lv() + l * kd + b];
+                }
+                bdst[e] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Res(k)^2 partials: sum_{n=1}^{max(W, Wp)} dt sum_nodes w |u^(k) - u^(k-1)|^2 with
+// hold-last indexing; u^(0) = 0.  One partial per (subdomain, block).
+__global__ void k_residual(SwrDeviceView v, const int* win, const int* win_prev, int parity, int first_iter,
+                           double* part) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const InstDev& in = v.inst[s.inst];
+    const int W = win[s.inst], Wp = first_iter ? 0 : win_prev[s.inst];
+    const int Nn = max(W, Wp);
+    const int q = s.q, kd = s.kd;
+    T1Layout lay(q, kd);
+    __shared__ double red[33];
+    double acc = 0;
+    for (long long e = threadIdx.x + (long long)blockIdx.x * blockDim.x; e < (long long)Nn * s.ngam;
+         e += (long long)blockDim.x * gridDim.x) {
+        int n = 1 + (int)(e / s.ngam), node = (int)(e % s.ngam);
+        double a = v.arena[s.u[parity] + (long long)min(n, W) * s.ngam + node];
+        double b = first_iter ? 0.0 : v.arena[s.u[parity ^ 1] + (long long)min(n, Wp) * s.ngam + node];
+        double w = 1.0;
+        if (s.N == 2) {
+            int slot = -1, nt = 0;
+            for (int sl = 3; sl >= 0; --sl)
+                if (s.gam_off[sl] >= 0 && node >= s.gam_off[sl]) { slot = sl; nt = node - s.gam_off[sl]; break; }
+            const double* To = v.arena + s.t1[1 - slot / 2];
+            w = To[lay.w() + nt];
+        }
+        acc += in.dt * w * (a - b) * (a - b);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[sid * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void k_residual_reduce(SwrDeviceView v, const double* part, int nblk, double* res) {
+    const int i = blockIdx.x;
+    const InstDev& in = v.inst[i];
+    __shared__ double red[33];
+    double acc = 0;
+    for (int e = threadIdx.x; e < in.n_sub * nblk; e += blockDim.x) acc += part[(long long)in.sub_base * nblk + e];
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) res[i] = sqrt(acc);
+}
+
+// Energy numerator / denominator per subdomain at step W (normalised state):
+// sum over volume nodes of w chi (kappa |grad psi|^2 + V psi^2) and w chi psi^2,
+// and psi at the nodes (node p = q1 + q*q2).
+__global__ void k_energy(SwrDeviceView v, const int* win, const double* snorm, int cap, double* part,
+                         double* psi_out, const long long* psi_off) {
+    const int sid = blockIdx.x;
+    const SubDev& s = v.sub[sid];
+    const InstDev& in = v.inst[s.inst];
+    const int W = win[s.inst];
+    const int kd = s.kd, q = s.q, K = s.K;
+    T1Layout lay(q, kd);
+    const double sn = in.normalize ? snorm[(long long)s.inst * (cap + 1) + W] : 1.0;
+    extern __shared__ double sm[];
+    double* ys = sm;               // K
+    double* G1 = sm + K;           // kd * q
+    double* G1d = G1 + kd * q;     // kd * q
+    __shared__ double red[33];
+    const double* y = v.arena + s.hist + (long long)W * K;
+    for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c] = y[c] / sn;
+    __syncthreads();
+    const double* T0 = v.arena + s.t1[0];
+    double num = 0, den = 0;
+    if (s.N == 1) {
+        for (int n = threadIdx.x; n < q; n += blockDim.x) {
+            double p = 0, dp = 0;
+            for (int a = 0; a < kd; ++a) {
+                p += T0[lay.B() + n * kd + a] * ys[a];
+                dp += T0[lay.D() + n * kd + a] * ys[a];
+            }
+            double wc = T0[lay.w() + n] * T0[lay.chi() + n];
+            num += wc * (in.kappa * dp * dp + T0[lay.v1() + n] * p * p);
+            den += wc * p * p;
+            if (psi_out) psi_out[psi_off[sid] + n] = p;
+        }
+    } else {
+        const double* T1 = v.arena + s.t1[1];
+        for (int e = threadIdx.x; e < kd * q; e += blockDim.x) {
+            int a = e / q, n2 = e % q;
+            double acc = 0, accd = 0;
+            for (int b = 0; b < kd; ++b) {
+                double c = ys[a + kd * b];
+                acc += c * T1[lay.B() + n2 * kd + b];
+                accd += c * T1[lay.D() + n2 * kd + b];
+            }
+            G1[e] = acc;
+            G1d[e] = accd;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+            int n2 = e / q, n1 = e % q;
+            double p = 0, d1 = 0, d2 = 0;
+            for (int a = 0; a < kd; ++a) {
+                double b1 = T0[lay.B() + n1 * kd + a];
+                p += b1 * G1[a * q + n2];
+                d1 += T0[lay.D() + n1 * kd + a] * G1[a * q + n2];
+                d2 += b1 * G1d[a * q + n2];
+            }
+            double x1 = T0[lay.x() + n1], x2 = T1[lay.x() + n2];
+            double r = x1 - x2;
+            double V = T0[lay.v1() + n1] + T1[lay.v1() + n2] + in.ee_coef / sqrt(r * r + in.eta_ee * in.eta_ee);
+            double wc = T0[lay.w() + n1] * T1[lay.w() + n2] * T0[lay.chi() + n1] * T1[lay.chi() + n2];
+            num += wc * (in.kappa * (d1 * d1 + d2 * d2) + V * p * p);
+            den += wc * p * p;
+            if (psi_out) psi_out[psi_off[sid] + e] = p;
+        }
+    }
+    num = block_sum(num, red);
+    den = block_sum(den, red);
+    if (threadIdx.x == 0) {
+        part[2 * sid] = num;
+        part[2 * sid + 1] = den;
+    }
+}
+
+__global__ void k_energy_reduce(SwrDeviceView v, const double* part, double* energy, double* norm2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= v.n_inst) return;
+    const InstDev& in = v.inst[i];
+    double num = 0, den = 0;
+    for (int j = 0; j < in.n_sub; ++j) {
+        num += part[2 * (in.sub_base + j)];
+        den += part[2 * (in.sub_base + j) + 1];
+    }
+    energy[i] = num / den;
+    norm2[i] = den;
+}
+
+__global__ void k_reset_iter(int* act, int n_inst, GridBarrier* bar) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_inst) act[i] = 1;
+    if (i == 0) { bar->count = 0; bar->gen = 0; }
+}
+
+// ------------------------------------------------------------- host driver
+
+static inline unsigned div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+struct SweepHost {
+    SweepArgs args;
+    int grid;
+    size_t smem;
+};
+
+cudaError_t ngf_occupancy(int* blocks_per_sm, size_t smem) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_ngf_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_ngf_window, 256, smem);
+}
+
+// Kernel launches per swr_step (reset, prologue, window, line traces, gather,
+// residual, residual reduce, energy, energy reduce).
+extern const int kStepLaunches = 9;
+
+cudaError_t launch_ngf_iteration(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst,
+                                 int max_K, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+    k_reset_iter<<<div_up(max(n_inst, 1), 256), 256, 0, st>>>(a.act, n_inst, a.bar);
+    k_ngf_prologue<<<min(a.n_tasks, 1024), 256, smem, st>>>(a);
+    cudaError_t e = cudaEventRecord(ev_begin, st);
+    if (e != cudaSuccess) return e;
+    void* params[] = {&a};
+    e = cudaLaunchCooperativeKernel((const void*)k_ngf_window, dim3(grid), dim3(256), params, smem, st);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecord(ev_end, st);
+}
+
+cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
+                        const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
+                        int res_blocks, double* d_res, int max_cap_hint) {
+    int nb = 64;
+    k_line_traces<<<dim3(nb, v.n_sub), 256, 0, st>>>(v, d_win, cap);
+    k_gather<<<dim3(nb, v.n_sub), 256, 0, st>>>(v, d_win, d_snorm, cap, parity);
+    k_residual<<<dim3(res_blocks, v.n_sub), 256, 0, st>>>(v, d_win, d_win_prev, parity, first_iter, d_res_part);
+    k_residual_reduce<<<v.n_inst, 256, 0, st>>>(v, d_res_part, res_blocks, d_res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
+                          int cap, double* d_part, double* d_energy, double* d_norm2, double* psi_out,
+                          const long long* psi_off, int max_K, int max_kd, int max_q) {
+    size_t smem = ((size_t)max_K + 2 * (size_t)max_kd * max_q) * sizeof(double);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_energy<<<v.n_sub, 256, smem, st>>>(v, d_win, d_snorm, cap, d_part, psi_out, psi_off);
+    k_energy_reduce<<<div_up(v.n_inst, 128), 128, 0, st>>>(v, d_part, d_energy, d_norm2);
+    return cudaGetLastError();
+}
+
+}  // namespace swr

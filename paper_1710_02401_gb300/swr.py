@@ -1,0 +1,299 @@
+"""ctypes binding of the SWR-Galerkin C ABI (include/swr.h).
+
+Argument marshalling only: every step of the sweep runs in the CUDA kernels of
+libswr.so.  PyTorch provides the device workspace (a caller-owned uint8
+tensor handed to swr_setup) and the CUDA stream; nothing here computes any
+part of the method.  The binding fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+from . import problems as P
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libswr.so")
+
+SWR_OK, SWR_EINVAL, SWR_ENOMEM, SWR_ECUDA, SWR_ESINGULAR, SWR_ENUMERIC, SWR_ENOTCONV, SWR_ETIMEOUT, SWR_ESTATE = range(9)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENUMERIC", "ENOTCONV", "ETIMEOUT", "ESTATE"]
+MODE_TISE, MODE_TDSE = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+GET, SET = 0, 1
+(FIELD_ENERGY, FIELD_NORM2, FIELD_DIPOLE, FIELD_RES, FIELD_WINDOW, FIELD_PSI_NODES, FIELD_OWN_TRACES,
+ FIELD_ROBIN, FIELD_TRACE_BYTES, FIELD_NODE_COUNTS, FIELD_K_MAX, FIELD_COUNTERS) = range(12)
+
+
+class swr_instance(C.Structure):
+    _fields_ = [
+        ("n_elec", C.c_int), ("box_lo", C.c_double), ("box_hi", C.c_double), ("L", C.c_int),
+        ("overlap", C.c_double), ("K_d", C.c_int), ("K_d_per_sub", C.POINTER(C.c_int)),
+        ("delta", C.c_double), ("delta_per_sub", C.POINTER(C.c_double)), ("q_p", C.c_int),
+        ("n_mid", C.c_int), ("n_nuclei", C.c_int), ("x_nuc", C.c_double * 3), ("Z_nuc", C.c_double * 3),
+        ("eta_en", C.c_double), ("eta_ee", C.c_double), ("ee_coef", C.c_double), ("harmonic", C.c_double),
+        ("kinetic", C.c_double), ("mu_re", C.c_double), ("mu_im", C.c_double), ("mode", C.c_int),
+        ("normalize", C.c_int), ("dt", C.c_double), ("n_steps", C.c_int), ("ngf_tol", C.c_double),
+        ("max_steps", C.c_int), ("field_E0", C.c_double), ("field_T", C.c_double),
+        ("field_omega", C.c_double), ("field_phase", C.c_double), ("phi0_gamma", C.c_double),
+        ("phi0_center", C.c_double * 2),
+    ]
+
+
+class swr_problem(C.Structure):
+    _fields_ = [("n_instances", C.c_int), ("instances", C.POINTER(swr_instance)), ("precision", C.c_int),
+                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+
+
+class swr_iter_report(C.Structure):
+    _fields_ = [("k", C.c_int), ("res", C.c_double), ("window_max", C.c_int),
+                ("subdomain_solves", C.c_longlong), ("seconds", C.c_double)]
+
+
+class swr_report(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("res_last", C.c_double),
+                ("subdomain_solves", C.c_longlong), ("seconds", C.c_double)]
+
+
+class swr_trace_view(C.Structure):
+    _fields_ = [("host", C.c_void_p), ("bytes", C.c_size_t)]
+
+
+EXPORTS = ["swr_workspace_size", "swr_setup", "swr_assemble", "swr_step", "swr_iterate", "swr_traces",
+           "swr_get", "swr_field_bytes", "swr_destroy", "swr_last_error"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libswr.so (raises when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libswr.so not found at {path}: run paper_1710_02401_gb300/build.py "
+                           "(the SWR sweep has no CPU fallback)")
+    lib = C.CDLL(path)
+    lib.swr_workspace_size.argtypes = [C.POINTER(swr_problem), C.POINTER(C.c_size_t)]
+    lib.swr_setup.argtypes = [C.POINTER(swr_problem), C.POINTER(C.c_void_p)]
+    lib.swr_assemble.argtypes = [C.c_void_p]
+    lib.swr_step.argtypes = [C.c_void_p, C.POINTER(swr_iter_report)]
+    lib.swr_iterate.argtypes = [C.c_void_p, C.c_double, C.c_int, C.POINTER(swr_report), C.POINTER(C.c_double)]
+    lib.swr_traces.argtypes = [C.c_void_p, C.c_int, C.POINTER(swr_trace_view)]
+    lib.swr_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]
+    lib.swr_field_bytes.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]
+    lib.swr_destroy.argtypes = [C.c_void_p]
+    lib.swr_destroy.restype = None
+    lib.swr_last_error.argtypes = [C.c_void_p]
+    lib.swr_last_error.restype = C.c_char_p
+    for name in EXPORTS[:-2]:
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class SWRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def _to_c_instance(inst: P.Instance, keep: list) -> swr_instance:
+    ci = swr_instance()
+    ci.n_elec = inst.n_elec
+    ci.box_lo, ci.box_hi = float(inst.box[0]), float(inst.box[1])
+    ci.L = inst.L
+    ci.overlap = float(inst.overlap)
+    if isinstance(inst.K_d, int):
+        ci.K_d = inst.K_d
+        ci.K_d_per_sub = None
+    else:
+        arr = (C.c_int * len(inst.K_d))(*[int(k) for k in inst.K_d])
+        keep.append(arr)
+        ci.K_d = int(inst.K_d[0])
+        ci.K_d_per_sub = C.cast(arr, C.POINTER(C.c_int))
+    if isinstance(inst.delta, (int, float)):
+        ci.delta = float(inst.delta)
+        ci.delta_per_sub = None
+    else:
+        arr = (C.c_double * len(inst.delta))(*[float(d) for d in inst.delta])
+        keep.append(arr)
+        ci.delta = float(inst.delta[0])
+        ci.delta_per_sub = C.cast(arr, C.POINTER(C.c_double))
+    ci.q_p = inst.q_p
+    ci.n_mid = inst.n_mid
+    ci.n_nuclei = len(inst.nuclei)
+    for a, (x, z) in enumerate(inst.nuclei):
+        ci.x_nuc[a] = float(x)
+        ci.Z_nuc[a] = float(z)
+    ci.eta_en, ci.eta_ee = float(inst.eta_en), float(inst.eta_ee)
+    ci.ee_coef = float(inst.ee_coef)
+    ci.harmonic = float(inst.harmonic)
+    ci.kinetic = float(inst.kinetic)
+    mu = complex(inst.mu)
+    ci.mu_re, ci.mu_im = mu.real, mu.imag
+    ci.mode = MODE_TDSE if inst.mode == P.TDSE else MODE_TISE
+    ci.normalize = 1 if inst.normalize else 0
+    ci.dt = float(inst.dt)
+    ci.n_steps = int(inst.n_steps)
+    ci.ngf_tol = float(inst.ngf_tol)
+    ci.max_steps = int(inst.max_steps)
+    ci.field_E0, ci.field_T, ci.field_omega, ci.field_phase = (float(f) for f in inst.field)
+    ci.phi0_gamma = float(inst.phi0_gamma)
+    ci.phi0_center[0], ci.phi0_center[1] = float(inst.phi0_center[0]), float(inst.phi0_center[1])
+    return ci
+
+
+class SWR:
+    """One SWR context over a batch of instances (all subdomains of all
+    instances in one sweep).  Device memory is a torch uint8 tensor owned by
+    this object; work is ordered on `stream` (default: torch's current)."""
+
+    def __init__(self, instances, precision: int = PREC_FP64, device: str = "cuda:0", stream=None,
+                 use_torch_workspace: bool = True):
+        import torch
+        self.lib = load_library()
+        if isinstance(instances, P.Instance):
+            instances = [instances]
+        self.instances = list(instances)
+        self._keep: list = []
+        arr = (swr_instance * len(self.instances))()
+        for i, inst in enumerate(self.instances):
+            arr[i] = _to_c_instance(inst, self._keep)
+        self._arr = arr
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        prob = swr_problem()
+        prob.n_instances = len(self.instances)
+        prob.instances = C.cast(arr, C.POINTER(swr_instance))
+        prob.precision = precision
+        prob.stream = C.c_void_p(self.stream.cuda_stream)
+        nbytes = C.c_size_t(0)
+        self._check(self.lib.swr_workspace_size(C.byref(prob), C.byref(nbytes)), None)
+        self.workspace = None
+        if use_torch_workspace:
+            self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            aligned = (base + 255) & ~255
+            prob.workspace = C.c_void_p(aligned)
+            prob.workspace_bytes = int(nbytes.value)
+        self.workspace_bytes = int(nbytes.value)
+        self._prob = prob
+        ctx = C.c_void_p(None)
+        self._check(self.lib.swr_setup(C.byref(prob), C.byref(ctx)), None)
+        self.ctx = ctx
+
+    # ------------------------------------------------------------ plumbing
+    def _check(self, st: int, ctx) -> None:
+        if st != SWR_OK:
+            msg = self.lib.swr_last_error(ctx if ctx is not None else None)
+            raise SWRError(st, msg.decode() if msg else "")
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.lib.swr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ the ABI
+    def assemble(self) -> None:
+        self._check(self.lib.swr_assemble(self.ctx), self.ctx)
+
+    def step(self) -> swr_iter_report:
+        rep = swr_iter_report()
+        self._check(self.lib.swr_step(self.ctx, C.byref(rep)), self.ctx)
+        return rep
+
+    def iterate(self, tol: float, kmax: int, raise_on_notconv: bool = False):
+        rep = swr_report()
+        hist = (C.c_double * kmax)()
+        st = self.lib.swr_iterate(self.ctx, float(tol), int(kmax), C.byref(rep), hist)
+        if st != SWR_OK and not (st == SWR_ENOTCONV and not raise_on_notconv):
+            self._check(st, self.ctx)
+        return rep, list(hist[: rep.iterations])
+
+    def field_bytes(self, field: int) -> int:
+        n = C.c_size_t(0)
+        self._check(self.lib.swr_field_bytes(self.ctx, field, C.byref(n)), self.ctx)
+        return int(n.value)
+
+    def get(self, field: int, dtype=np.float64) -> np.ndarray:
+        nb = self.field_bytes(field)
+        out = np.empty(nb // np.dtype(dtype).itemsize, dtype=dtype)
+        self._check(self.lib.swr_get(self.ctx, field, out.ctypes.data_as(C.c_void_p), nb), self.ctx)
+        return out
+
+    def trace_bytes(self) -> int:
+        return int(self.get(FIELD_TRACE_BYTES, dtype=np.uint64)[0])
+
+    def traces_get(self) -> np.ndarray:
+        buf = np.empty(self.trace_bytes(), dtype=np.uint8)
+        view = swr_trace_view(buf.ctypes.data_as(C.c_void_p), buf.nbytes)
+        self._check(self.lib.swr_traces(self.ctx, GET, C.byref(view)), self.ctx)
+        return buf
+
+    def traces_set(self, buf: np.ndarray) -> None:
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        view = swr_trace_view(buf.ctypes.data_as(C.c_void_p), buf.nbytes)
+        self._check(self.lib.swr_traces(self.ctx, SET, C.byref(view)), self.ctx)
+
+    # ------------------------------------------------------------ results
+    def counters(self) -> dict:
+        c = self.get(FIELD_COUNTERS)
+        keys = ["window_ms", "window_launches", "kernel_launches", "window_flops", "window_bytes",
+                "solves", "assemble_ms", "step_ms", "h2d_bytes", "d2h_bytes"]
+        return dict(zip(keys, (float(x) for x in c)))
+
+    def energy(self) -> np.ndarray:
+        return self.get(FIELD_ENERGY)
+
+    def residual(self) -> np.ndarray:
+        return self.get(FIELD_RES)
+
+    def window(self) -> np.ndarray:
+        return self.get(FIELD_WINDOW, dtype=np.int32)
+
+    def node_counts(self) -> np.ndarray:
+        return self.get(FIELD_NODE_COUNTS, dtype=np.int32).reshape(-1, 3)
+
+    def psi_nodes(self) -> List[np.ndarray]:
+        """psi_i at the volume nodes of every subdomain (node p = q1 + q*q2)."""
+        flat = self.get(FIELD_PSI_NODES)
+        out, o = [], 0
+        for (q, ng, K), inst_sub in zip(self.node_counts(), self._sub_n()):
+            n = q ** inst_sub
+            out.append(flat[o:o + n])
+            o += n
+        return out
+
+    def _sub_n(self):
+        for inst in self.instances:
+            for _ in range(inst.n_sub):
+                yield inst.n_elec
+
+    def own_traces(self) -> List[np.ndarray]:
+        return self._per_sub_steps(FIELD_OWN_TRACES)
+
+    def robin_data(self) -> List[np.ndarray]:
+        return self._per_sub_steps(FIELD_ROBIN)
+
+    def _per_sub_steps(self, field):
+        flat = self.get(field)
+        win = self.window()
+        out, o, s = [], 0, 0
+        counts = self.node_counts()
+        for i, inst in enumerate(self.instances):
+            for _ in range(inst.n_sub):
+                ng = int(counts[s][1])
+                n = (int(win[i]) + 1) * ng
+                out.append(flat[o:o + n].reshape(int(win[i]) + 1, ng))
+                o += n
+                s += 1
+        return out

@@ -1,0 +1,120 @@
+"""The C ABI: the library builds for sm_103a, loads, exports every function
+that include/swr.h declares, and the ctypes mirror of its structs has the
+C layout.  CPU only (no CUDA call is made)."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_1710_02401_gb300 import build as B
+from paper_1710_02401_gb300 import problems as P
+from paper_1710_02401_gb300 import swr as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "swr.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return S.load_library()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:swr_status|void|const char\*)\s+(swr_\w+)\s*\(", txt, re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (swr_\w+)", out))
+    for n in names:
+        assert n in exported, n
+        assert hasattr(lib, n)
+    assert set(S.EXPORTS) == set(names)
+
+
+def test_struct_layout_matches_c(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(f'''
+#include <stdio.h>
+#include <stddef.h>
+#include "{HEADER}"
+#define F(T, m) printf("%s.%s %zu\\n", #T, #m, offsetof(T, m));
+int main(void) {{
+  printf("swr_instance %zu\\n", sizeof(swr_instance));
+  printf("swr_problem %zu\\n", sizeof(swr_problem));
+  printf("swr_iter_report %zu\\n", sizeof(swr_iter_report));
+  printf("swr_report %zu\\n", sizeof(swr_report));
+  printf("swr_trace_view %zu\\n", sizeof(swr_trace_view));
+  F(swr_instance, delta_per_sub) F(swr_instance, x_nuc) F(swr_instance, mode) F(swr_instance, phi0_center)
+  F(swr_instance, max_steps) F(swr_problem, workspace_bytes) F(swr_iter_report, seconds)
+  return 0;
+}}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", str(prog), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n") if line)
+    assert int(got["swr_instance"]) == C.sizeof(S.swr_instance)
+    assert int(got["swr_problem"]) == C.sizeof(S.swr_problem)
+    assert int(got["swr_iter_report"]) == C.sizeof(S.swr_iter_report)
+    assert int(got["swr_report"]) == C.sizeof(S.swr_report)
+    assert int(got["swr_trace_view"]) == C.sizeof(S.swr_trace_view)
+    for key in ["delta_per_sub", "x_nuc", "mode", "phi0_center", "max_steps"]:
+        assert int(got[f"swr_instance.{key}"]) == getattr(S.swr_instance, key).offset, key
+    assert int(got["swr_problem.workspace_bytes"]) == S.swr_problem.workspace_bytes.offset
+    assert int(got["swr_iter_report.seconds"]) == S.swr_iter_report.seconds.offset
+
+
+def _problem(insts, keep):
+    arr = (S.swr_instance * len(insts))()
+    for i, inst in enumerate(insts):
+        arr[i] = S._to_c_instance(inst, keep)
+    keep.append(arr)
+    p = S.swr_problem()
+    p.n_instances = len(insts)
+    p.instances = C.cast(arr, C.POINTER(S.swr_instance))
+    p.precision = S.PREC_FP64
+    return p
+
+
+def test_workspace_size_and_validation_on_host(lib):
+    keep = []
+    n = C.c_size_t(0)
+    p = _problem([P.small_tise_2d()], keep)
+    assert lib.swr_workspace_size(C.byref(p), C.byref(n)) == S.SWR_OK
+    assert n.value > 0
+    # a bigger window needs more memory
+    p2 = _problem([P.small_tise_2d().replace(max_steps=6000)], keep)
+    n2 = C.c_size_t(0)
+    assert lib.swr_workspace_size(C.byref(p2), C.byref(n2)) == S.SWR_OK
+    assert n2.value > n.value
+    bad = [
+        P.small_tise_2d().replace(n_elec=3),
+        P.small_tise_2d().replace(overlap=0.0),
+        P.small_tise_2d().replace(overlap=5.0),
+        P.small_tise_2d().replace(q_p=0),
+        P.small_tise_2d().replace(dt=0.0),
+        P.small_tise_2d().replace(K_d=1),
+        P.small_tise_2d().replace(delta=-1.0),
+        P.small_tise_2d().replace(mu=1 + 1j),
+        P.small_tise_2d().replace(ngf_tol=0.0, n_steps=0),
+    ]
+    for inst in bad:
+        st = lib.swr_workspace_size(C.byref(_problem([inst], keep)), C.byref(n))
+        assert st == S.SWR_EINVAL, inst
+        assert len(lib.swr_last_error(None)) > 0
+    empty = S.swr_problem()
+    assert lib.swr_workspace_size(C.byref(empty), C.byref(n)) == S.SWR_EINVAL
+
+
+def test_mixed_modes_rejected(lib):
+    keep = []
+    n = C.c_size_t(0)
+    p = _problem([P.small_tise_2d(), P.small_tdse_2d()], keep)
+    assert lib.swr_workspace_size(C.byref(p), C.byref(n)) == S.SWR_EINVAL

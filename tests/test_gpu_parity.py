@@ -1,0 +1,158 @@
+"""GPU parity: the CUDA sweep (through the C ABI) against the FP64 oracle.
+
+Both sides take the same seeded problem from problems.py; the oracle solves
+in the raw Gaussian basis with dense 2-D quadrature and LU, the GPU in the
+orthonormalised basis with Kronecker/sum-factorised assembly and explicit
+inverses.  Only basis-independent results are compared: window lengths
+(bit-exact integers), Res(k), energies, interface traces and Robin data at
+every interface node and step, and psi at every volume node.
+
+FP64 tolerance: 1e-10 relative on energies and node values (the workloads'
+bases have kappa(A) <= 1e9, so two backward-stable FP64 solves of the same
+discrete problem agree to ~kappa*eps ~ 1e-7 in coefficients but to ~1e-12 in
+the basis-invariant values); Res(k) is a difference of successive iterates,
+so it is compared absolutely against 1e-10 of the first residual.
+"""
+import numpy as np
+import pytest
+
+from oracle import swr_oracle as O
+from paper_1710_02401_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def swr_mod():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_02401_gb300 import build as B
+    B.build()
+    from paper_1710_02401_gb300 import swr as S
+    return S
+
+
+def _run_gpu(S, inst, kmax, tol=0.0):
+    s = S.SWR(inst)
+    s.assemble()
+    res, wins, energies = [], [], []
+    for _ in range(kmax):
+        rep = s.step()
+        res.append(rep.res)
+        wins.append(int(s.window()[0]))
+        energies.append(float(s.energy()[0]))
+        if rep.res <= tol:
+            break
+    return s, res, wins, energies
+
+
+def _compare(S, inst, kmax, tol=0.0, rel=REL):
+    ref = O.run_swr(inst, kmax=kmax, tol=tol)
+    s, res, wins, energies = _run_gpu(S, inst, len(ref.records), tol)
+    assert wins == [r.n_win for r in ref.records]
+    r0 = ref.records[0].res
+    for a, r in zip(res, ref.records):
+        assert abs(a - r.res) <= rel * r0, (a, r.res)
+    if inst.normalize or inst.mode == P.TDSE:
+        for a, r in zip(energies, ref.records):
+            if r.energy is not None:
+                assert abs(a - r.energy) <= rel * abs(r.energy), (a, r.energy)
+    # interface traces and Robin data, every node and step of the last iteration
+    u = s.own_traces()
+    g = s.robin_data()
+    umax = max(np.abs(x).max() for x in ref.own_traces if x.size)
+    gmax = max(np.abs(x).max() for x in ref.robin if x.size)
+    for i in range(inst.n_sub):
+        assert u[i].shape == ref.own_traces[i].shape
+        assert np.abs(u[i] - ref.own_traces[i]).max() <= rel * umax
+        assert np.abs(g[i] - ref.robin[i]).max() <= rel * gmax
+    # psi at every volume node of every subdomain
+    psi = s.psi_nodes()
+    pref = [O.psi_at_nodes(ref.locs[i], ref.coeffs[i]) for i in range(inst.n_sub)]
+    pmax = max(np.abs(p).max() for p in pref)
+    for i in range(inst.n_sub):
+        assert np.abs(psi[i] - pref[i]).max() <= rel * pmax
+    return s, ref
+
+
+def test_parity_one_electron_two_subdomains(swr_mod):
+    # the 1-electron workload in full (40 Gaussians per subdomain, Res <= 1e-8)
+    _compare(swr_mod, P.tise_1d_two_subdomains(), kmax=50, tol=1e-8)
+
+
+def test_parity_one_electron_harmonic(swr_mod):
+    s, ref = _compare(swr_mod, P.harmonic_1d_two_subdomains(), kmax=50, tol=1e-8)
+    assert abs(ref.records[-1].energy - 0.5) < 1e-3
+
+
+def test_parity_two_electrons_3x3(swr_mod):
+    # 9 subdomains (corner bands with 3 contributors), K = 100: ragged 32-row tasks
+    _compare(swr_mod, P.small_tise_2d(), kmax=6)
+
+
+def test_parity_two_electrons_uneven_kd_and_no_ee(swr_mod):
+    inst = P.small_tise_2d(L=2, K_d=7, q_p=6, n_mid=2).replace(
+        K_d=[7, 9, 8, 6], delta=[1.3, 2.1, 1.7, 1.1], ee_coef=0.0)
+    _compare(swr_mod, inst, kmax=4)
+
+
+def test_parity_heat_fixed_window(swr_mod):
+    inst = P.Instance(n_elec=1, box=(-15.0, 15.0), L=3, overlap=1.0, K_d=40, delta=2.5,
+                      q_p=10, n_mid=5, nuclei=(), ee_coef=0.0, kinetic=1.0, mu=1.0,
+                      mode=P.TISE, normalize=False, dt=0.1, n_steps=10, ngf_tol=0.0,
+                      phi0_gamma=0.2)
+    _compare(swr_mod, inst, kmax=5)
+
+
+def test_parity_batched_instances(swr_mod):
+    S = swr_mod
+    insts = [P.small_tise_2d(L=2, K_d=6, q_p=6, n_mid=2),
+             P.tise_1d_two_subdomains().replace(L=3, K_d=20, delta=2.0),
+             P.small_tise_2d(L=2, K_d=7, q_p=6, n_mid=2).replace(nuclei=((0.3, 2.0),), mu=4.0)]
+    s = S.SWR(insts)
+    s.assemble()
+    kmax = 3
+    gres = []
+    for _ in range(kmax):
+        s.step()
+        gres.append(s.residual().copy())
+    gE = s.energy()
+    gW = s.window()
+    for i, inst in enumerate(insts):
+        ref = O.run_swr(inst, kmax=kmax, tol=0.0)
+        assert gW[i] == ref.records[-1].n_win
+        assert abs(gE[i] - ref.records[-1].energy) <= REL * abs(ref.records[-1].energy)
+        for k in range(kmax):
+            assert abs(gres[k][i] - ref.records[k].res) <= REL * ref.records[0].res
+
+
+def test_checkpoint_resume_is_bit_exact(swr_mod):
+    S = swr_mod
+    inst = P.small_tise_2d(L=2, K_d=6, q_p=6, n_mid=2)
+    a = S.SWR(inst)
+    a.assemble()
+    for _ in range(3):
+        a.step()
+    blob = a.traces_get()
+    r4 = a.step().res
+    b = S.SWR(inst)
+    b.assemble()
+    b.traces_set(blob)
+    assert b.step().res == r4
+    np.testing.assert_array_equal(a.energy(), b.energy())
+
+
+def test_errors_are_reported_not_raised_on_device(swr_mod):
+    S = swr_mod
+    s = S.SWR(P.small_tise_2d(L=2, K_d=6, q_p=6, n_mid=2))
+    with pytest.raises(S.SWRError) as e:
+        s.step()  # before assemble
+    assert e.value.status == S.SWR_ESTATE
+    # a hopelessly ill-conditioned basis fails the overlap Cholesky
+    bad = S.SWR(P.tise_1d_two_subdomains().replace(K_d=90, delta=0.05))
+    with pytest.raises(S.SWRError) as e:
+        bad.assemble()
+    assert e.value.status == S.SWR_ESINGULAR
