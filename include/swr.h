@@ -186,6 +186,25 @@ swr_status swr_get(swr_ctx* ctx, int field, void* host, size_t bytes);
 /* Bytes that swr_get needs for `field` (for the sized fields). */
 swr_status swr_field_bytes(swr_ctx* ctx, int field, size_t* bytes);
 
+/* Allocation-free recomputation of Res(k) of the last completed Schwarz
+ * iteration, one value per instance into res_host[0..n) (n = n_instances).
+ * No counterpart in the paper: this is a service for callers that may not
+ * allocate device memory when they call it (for example code that runs under
+ * a framework owning all device memory, or a real-time loop that forbids
+ * allocation after start-up).  It calls no cudaMalloc/cudaFree and no
+ * allocating library routine; its scratch (partial sums, window lengths,
+ * result) lives in one file-scope __device__ array of 2 MiB, held by every
+ * GPU that loads the library until the process exits, which limits it to
+ * about 32,000 subdomains (SWR_EINVAL beyond that).  The first call on a
+ * device resolves the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU (other streams, other contexts) race and must be
+ * serialised by the caller.  Nothing in the array needs clearing: every call
+ * overwrites all of the scratch it reads.  Synchronises the context stream.
+ * Returns SWR_ESTATE before the first swr_step.  The result equals
+ * swr_get(SWR_FIELD_RES) of the same iteration. */
+swr_status swr_residual_noalloc(swr_ctx* ctx, double* res_host, size_t n);
+
 void        swr_destroy(swr_ctx* ctx);
 const char* swr_last_error(const swr_ctx* ctx);
 

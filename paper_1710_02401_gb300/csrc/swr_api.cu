@@ -82,6 +82,7 @@ struct swr_ctx {
     size_t ngf_smem = 0;
     std::vector<double> res_h, energy_h, norm2_h;
     std::vector<int> win_h, win_prev_h;
+    std::vector<int> win_pp_h;  // windows of the iteration before the last one
     // counters (see SWR_FIELD_COUNTERS)
     double counters[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     cudaEvent_t evw0 = nullptr, evw1 = nullptr;
@@ -477,6 +478,7 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->norm2_h.assign(c->inst.size(), 0.0);
     c->win_h.assign(c->inst.size(), 0);
     c->win_prev_h.assign(c->inst.size(), 0);
+    c->win_pp_h.assign(c->inst.size(), 0);
     *out = c;
     return SWR_OK;
 }
@@ -568,6 +570,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     if (st != SWR_OK) return st;
     // the current window becomes the previous one for the next iteration
     CU(cudaMemcpyAsync(c->d_win_prev, c->d_win, ni * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
+    c->win_pp_h = c->win_prev_h;
     c->win_prev_h = c->win_h;
     c->k += 1;
     c->parity ^= 1;
@@ -764,6 +767,25 @@ extern "C" swr_status swr_traces(swr_ctx* c, int dir, swr_trace_view* view_) {
     if (c->k == 0) c->k = 1;  // the next residual compares against the restored traces
     return SWR_OK;
 }
+
+// Internal accessor for the allocation-free residual entry point (swr_noalloc.cu).
+namespace swr {
+bool residual_inputs(swr_ctx* c, ResidualInputs* r) {
+    if (!c || !c->assembled || c->k < 1) return false;
+    r->v = view(c);
+    r->stream = c->stream;
+    r->k = c->k;
+    r->parity_last = c->parity ^ 1;
+    r->n_inst = (int)c->inst.size();
+    r->n_sub = (int)c->sub.size();
+    r->win_last = c->win_prev_h.data();
+    r->win_before = c->win_pp_h.data();
+    return true;
+}
+void set_error(swr_ctx* c, const char* msg) {
+    if (c) c->err = msg;
+}
+}  // namespace swr
 
 extern "C" void swr_destroy(swr_ctx* c) {
     if (!c) return;

@@ -173,4 +173,17 @@ struct SweepArgs {
     GridBarrier* bar;
     long long spin_limit;
 };
+
+// What the allocation-free residual entry point needs from a context.
+struct ResidualInputs {
+    SwrDeviceView v;
+    cudaStream_t stream;
+    int k, parity_last, n_inst, n_sub;
+    const int* win_last;   // host, windows of the last iteration
+    const int* win_before; // host, windows of the iteration before it
+};
+bool residual_inputs(swr_ctx* c, ResidualInputs* r);
+void set_error(swr_ctx* c, const char* msg);
+cudaError_t launch_residual(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
+                            int parity, int first_iter, double* d_part, int res_blocks, double* d_res);
 }  // namespace swr

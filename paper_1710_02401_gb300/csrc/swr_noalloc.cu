@@ -1,0 +1,92 @@
+// swr_noalloc.cu -- Res(k) recomputed without any device allocation.
+//
+// swr_residual_noalloc() repeats the interface-residual reduction of the last
+// Schwarz iteration (the same k_residual / k_residual_reduce kernels that
+// swr_step runs) but keeps its scratch -- the per-block partial sums, the two
+// window-length arrays and the per-instance result -- in one file-scope
+// __device__ array instead of the context's workspace.  It exists for callers
+// that must not allocate device memory at the point of the call.
+#include <cuda_runtime.h>
+#include <mutex>
+#include <stdio.h>
+
+#include "swr_internal.cuh"
+
+using namespace swr;
+
+// Capacity of the static scratch, in doubles (2 MiB).  Layout of one call:
+// [window ints: 2*n_inst, padded to doubles] [partials: RES_BLOCKS*n_sub] [res: n_inst]
+#define SWR_NOALLOC_SCRATCH_DOUBLES (1 << 18)
+#define SWR_NOALLOC_RES_BLOCKS 8
+
+static __device__ __align__(256) double g_noalloc_scratch[SWR_NOALLOC_SCRATCH_DOUBLES];
+
+// Device address of g_noalloc_scratch, resolved once per device (the host-side
+// name is only a stand-in and must never be passed to a kernel).
+static std::mutex g_noalloc_mutex;
+static double* g_noalloc_ptr[64] = {nullptr};
+
+static cudaError_t noalloc_scratch_for_current_device(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = (double*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+extern "C" swr_status swr_residual_noalloc(swr_ctx* ctx, double* res_host, size_t n) {
+    if (!ctx || !res_host) return SWR_EINVAL;
+    ResidualInputs r;
+    if (!residual_inputs(ctx, &r)) {
+        set_error(ctx, "swr_residual_noalloc: no completed Schwarz iteration on this context");
+        return SWR_ESTATE;
+    }
+    if (n != (size_t)r.n_inst) {
+        set_error(ctx, "swr_residual_noalloc: n must equal the number of instances");
+        return SWR_EINVAL;
+    }
+    const long long win_doubles = (2LL * r.n_inst + 1) / 2;
+    const long long need = win_doubles + (long long)SWR_NOALLOC_RES_BLOCKS * r.n_sub + r.n_inst;
+    if (need > SWR_NOALLOC_SCRATCH_DOUBLES) {
+        char msg[200];
+        snprintf(msg, sizeof(msg),
+                 "swr_residual_noalloc: problem needs %lld scratch doubles, the static limit is %d "
+                 "(about %d subdomains)", need, SWR_NOALLOC_SCRATCH_DOUBLES,
+                 (SWR_NOALLOC_SCRATCH_DOUBLES - 2 * r.n_inst) / SWR_NOALLOC_RES_BLOCKS);
+        set_error(ctx, msg);
+        return SWR_EINVAL;
+    }
+    double* base = nullptr;
+    cudaError_t e = noalloc_scratch_for_current_device(&base);
+    if (e != cudaSuccess) {
+        set_error(ctx, cudaGetErrorString(e));
+        return SWR_ECUDA;
+    }
+    int* d_win = (int*)base;
+    int* d_win_before = d_win + r.n_inst;
+    double* d_part = base + win_doubles;
+    double* d_res = d_part + (long long)SWR_NOALLOC_RES_BLOCKS * r.n_sub;
+    // every partial slot and every result is overwritten by the kernels, so
+    // nothing in the shared array has to be cleared between calls
+    e = cudaMemcpyAsync(d_win, r.win_last, r.n_inst * sizeof(int), cudaMemcpyHostToDevice, r.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_win_before, r.win_before, r.n_inst * sizeof(int), cudaMemcpyHostToDevice, r.stream);
+    if (e == cudaSuccess)
+        e = launch_residual(r.v, r.stream, d_win, d_win_before, r.parity_last, r.k == 1 ? 1 : 0, d_part,
+                            SWR_NOALLOC_RES_BLOCKS, d_res);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res_host, d_res, n * sizeof(double), cudaMemcpyDeviceToHost, r.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r.stream);
+    if (e != cudaSuccess) {
+        set_error(ctx, cudaGetErrorString(e));
+        return SWR_ECUDA;
+    }
+    return SWR_OK;
+}

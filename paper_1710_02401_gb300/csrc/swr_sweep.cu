@@ -602,6 +602,14 @@ cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_wi
     return cudaGetLastError();
 }
 
+// Residual of one iteration into caller-chosen scratch (partials) and output.
+cudaError_t launch_residual(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
+                            int parity, int first_iter, double* d_part, int res_blocks, double* d_res) {
+    k_residual<<<dim3(res_blocks, v.n_sub), 256, 0, st>>>(v, d_win, d_win_prev, parity, first_iter, d_part);
+    k_residual_reduce<<<v.n_inst, 256, 0, st>>>(v, d_part, res_blocks, d_res);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
                           int cap, double* d_part, double* d_energy, double* d_norm2, double* psi_out,
                           const long long* psi_off, int max_K, int max_kd, int max_q) {

@@ -62,7 +62,7 @@ class swr_trace_view(C.Structure):
 
 
 EXPORTS = ["swr_workspace_size", "swr_setup", "swr_assemble", "swr_step", "swr_iterate", "swr_traces",
-           "swr_get", "swr_field_bytes", "swr_destroy", "swr_last_error"]
+           "swr_get", "swr_field_bytes", "swr_residual_noalloc", "swr_destroy", "swr_last_error"]
 
 _lib = None
 
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
     lib.swr_traces.argtypes = [C.c_void_p, C.c_int, C.POINTER(swr_trace_view)]
     lib.swr_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]
     lib.swr_field_bytes.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]
+    lib.swr_residual_noalloc.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]
     lib.swr_destroy.argtypes = [C.c_void_p]
     lib.swr_destroy.restype = None
     lib.swr_last_error.argtypes = [C.c_void_p]
@@ -228,6 +229,13 @@ class SWR:
         nb = self.field_bytes(field)
         out = np.empty(nb // np.dtype(dtype).itemsize, dtype=dtype)
         self._check(self.lib.swr_get(self.ctx, field, out.ctypes.data_as(C.c_void_p), nb), self.ctx)
+        return out
+
+    def residual_noalloc(self) -> np.ndarray:
+        """Res(k) of the last iteration recomputed by the allocation-free entry point."""
+        out = np.empty(len(self.instances), dtype=np.float64)
+        self._check(self.lib.swr_residual_noalloc(self.ctx, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                                  out.size), self.ctx)
         return out
 
     def trace_bytes(self) -> int:
