@@ -31,8 +31,10 @@ sys.path.insert(0, ROOT)
 TOL = 1e-8
 KMAX = 200
 METRIC = "SWR time-to-1e-8 interface residual; subdomain solves/s vs plain FP64 GPU path"
-# nominal FP64 (non-tensor) rate of one GB300, the ceiling of the FP64 window kernel
-FP64_PEAK_TFLOPS = 1.25
+# FP64 and FP32 (non-tensor) FMA rates of one GB300, measured on this machine with
+# independent FMA chains over all SMs (the ceilings of the window kernel)
+FP64_PEAK_TFLOPS = 1.01
+FP32_PEAK_TFLOPS = 67.7
 
 
 def workload(name: str):
@@ -156,6 +158,9 @@ def main():
     ap.add_argument("--workload", default="tise_2e_16sd")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of the headline line; the other path is timed beside it")
+    ap.add_argument("--no-compare", action="store_true", help="skip the timing of the other precision")
     args = ap.parse_args()
     name = args.workload
     inst = workload(name)
@@ -180,57 +185,82 @@ def main():
     from paper_1710_02401_gb300 import swr as S
 
     stream = torch.cuda.current_stream(dev)
-    s = S.SWR(inst, device=str(dev), stream=stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    prec_of = {"mixed": S.PREC_MIXED, "fp64": S.PREC_FP64}
 
-    def one_step():
-        s.assemble()
-        rep, hist = s.iterate(TOL, KMAX)
-        return rep, hist
+    def timed(prec_name, steps, warmup, sample_clocks):
+        """W untimed + K timed steps (assemble + iterate to Res <= TOL), CUDA
+        events on the library's stream, L2 flushed before every step."""
+        s = S.SWR(inst, precision=prec_of[prec_name], device=str(dev), stream=stream)
+        for _ in range(warmup):
+            s.assemble()
+            s.iterate(TOL, KMAX)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+        c0 = s.counters()
+        times, reps = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.assemble()
+            rep, hist = s.iterate(TOL, KMAX)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            reps.append(rep)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        c1 = s.counters()
+        clocks = sampler.stop() if sampler else None
+        t_ms = sum(times)
+        solves = sum(r.subdomain_solves for r in reps)
+        t_max, solves_all = t_ms, solves
+        if world > 1:
+            t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_max = float(t.item())
+            n = torch.tensor([solves], dtype=torch.float64, device=dev)
+            dist.all_reduce(n, op=dist.ReduceOp.SUM)
+            solves_all = int(n.item())
+        d = {k: c1[k] - c0[k] for k in c1}
+        return dict(s=s, value=solves_all / (t_max * 1e-3), t_max=t_max, reps=reps, counters=d, clocks=clocks)
 
-    for _ in range(args.warmup):
-        rep, hist = one_step()
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    sampler = ClockSampler(local)
-    sampler.start()
-    c0 = s.counters()
-    times, reps = [], []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rep, hist = one_step()
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        reps.append(rep)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    c1 = s.counters()
-    clocks = sampler.stop()
-    t_ms = sum(times)
-    solves = sum(r.subdomain_solves for r in reps)
-    converged = all(r.converged for r in reps)
-    t_max = t_ms
-    solves_all = solves
-    if world > 1:
-        t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        n = torch.tensor([solves], dtype=torch.float64, device=dev)
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        solves_all = int(n.item())
-    value = solves_all / (t_max * 1e-3)
-    # dominant kernel: the persistent time-window kernel (FP64 matvec-bound)
-    w_ms = c1["window_ms"] - c0["window_ms"]
-    w_launch = c1["window_launches"] - c0["window_launches"]
-    w_flops = c1["window_flops"] - c0["window_flops"]
+    main_run = timed(args.precision, args.steps, args.warmup, True)
+    other = None
+    if not args.no_compare:
+        other_name = "fp64" if args.precision == "mixed" else "mixed"
+        other = timed(other_name, max(1, min(args.steps, 2)), 1, False)
+        other["name"] = other_name
+    s = main_run["s"]
+    reps = main_run["reps"]
+    cnt = main_run["counters"]
+    w_ms, w_launch, w_flops = cnt["window_ms"], cnt["window_launches"], cnt["window_flops"]
+    # dominant kernel: the persistent time-window kernel
     achieved = w_flops / (w_ms * 1e-3) / 1e12 if w_ms > 0 else 0.0
-    launches = int(c1["kernel_launches"] - c0["kernel_launches"])
+    if args.precision == "mixed":
+        # double-single matvec: ~12 FP32 operations per matrix element on the FP32 pipes
+        peak = FP32_PEAK_TFLOPS / 6.0
+        roof = {"kernel": "k_window<df32>", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "measured FP32 FMA rate of this pool's GB300 (67.7 TFLOP/s) / 6: the "
+                               "double-single product-sum spends 12 FP32 operations per 2 FP64-equivalent flops",
+                "algorithmic": "2 K^2 FP64-equivalent flops per local step solve (matvec with the step-matrix inverse)"}
+    else:
+        roof = {"kernel": "k_window<fp64>", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 FMA rate measured on this pool's GB300 (probe of independent FMA chains)",
+                "algorithmic": "2 K^2 flops per local step solve (FP64 matvec with the step-matrix inverse)"}
+    roof["traffic"] = None
+    roof["window_ms_per_launch"] = w_ms / max(w_launch, 1)
+    roof["step_us"] = 1e3 * w_ms / max(1.0, cnt["solves"] / inst.n_sub)
+    launches = int(cnt["kernel_launches"])
 
     # end to end through the public API: setup from host descriptors, assembly,
     # iterations, read-back of energies and psi at all nodes, teardown
@@ -240,7 +270,7 @@ def main():
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            se = S.SWR(inst, device=str(dev), stream=stream)
+            se = S.SWR(inst, precision=prec_of[args.precision], device=str(dev), stream=stream)
             se.assemble()
             rep_e, _ = se.iterate(TOL, KMAX)
             energy = se.energy()
@@ -264,25 +294,32 @@ def main():
         cpu = {"value": v, "unit": "subdomain solves/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": desc}
     out = {
-        "metric": METRIC, "value": value, "unit": "subdomain solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "metric": METRIC, "value": main_run["value"], "unit": "subdomain solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_run["t_max"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32x2 (double-single) step matrices, f64 reductions" if args.precision == "mixed" else "f64",
         "data": "synthetic", "config": workload_config(name, inst),
-        "time_to_residual_s": t_max / args.steps * 1e-3,
-        "schwarz_iterations": [r.iterations for r in reps], "converged": converged,
+        "precision": args.precision,
+        "time_to_residual_s": main_run["t_max"] / args.steps * 1e-3,
+        "schwarz_iterations": [r.iterations for r in reps], "converged": all(r.converged for r in reps),
         "res_last": [r.res_last for r in reps],
         "energy": float(s.energy()[0]),
-        "roofline": {"kernel": "k_ngf_window", "bound": "alu", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak on this pool)",
-                     "traffic": None, "window_ms_per_launch": w_ms / max(w_launch, 1),
-                     "algorithmic": "2 K^2 flops per local step solve (FP64 matvec with the step-matrix inverse)"},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "subdomain solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "clocks": clocks,
+        "clocks": main_run["clocks"],
     }
+    if other is not None:
+        o_reps = other["reps"]
+        out["other_precision"] = {
+            "precision": other["name"], "value": other["value"],
+            "time_to_residual_s": other["t_max"] / len(o_reps) * 1e-3,
+            "schwarz_iterations": [r.iterations for r in o_reps],
+            "energy": float(other["s"].energy()[0]),
+            "speedup_of_headline": main_run["value"] / other["value"],
+        }
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

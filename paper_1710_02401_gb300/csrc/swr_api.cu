@@ -20,9 +20,11 @@ namespace swr {
 cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, int max_kd, int max_K,
                             bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
                             const GemmJob* d_jobs2, double* d_norm_part, double tau);
-cudaError_t ngf_occupancy(int* blocks_per_sm, size_t smem);
-cudaError_t launch_ngf_iteration(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst, int max_K,
-                                 cudaEvent_t ev_begin, cudaEvent_t ev_end);
+size_t window_smem(int kmax, int kdmax);
+cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, bool df32);
+cudaError_t launch_split_df32(const SwrDeviceView& v, cudaStream_t st, int max_K);
+cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst, bool df32,
+                          cudaEvent_t ev_begin, cudaEvent_t ev_end);
 extern const int kAssembleLaunchesFixed, kStepLaunches;
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
@@ -34,7 +36,7 @@ cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_
 
 using namespace swr;
 
-static const int ROW_BLOCK = 32;      // rows of a step matrix per persistent task
+static const int ROW_BLOCK_MAX = 64;  // rows of a step matrix per persistent task (upper bound)
 static const int GJ_NB_HOST = 32;     // Gauss-Jordan block (matches swr_assemble.cu)
 static const int RES_BLOCKS = 8;      // residual partial blocks per subdomain
 static const double CHOL_TAU = 1e-15; // relative pivot floor of the overlap Cholesky
@@ -48,13 +50,15 @@ struct swr_ctx {
     std::vector<std::vector<double>> delta_h;
     std::vector<InstDev> inst;
     std::vector<SubDev> sub;
-    std::vector<long long> zoff, psi_off;
+    std::vector<long long> psi_off;
     std::vector<Task> tasks;
     std::vector<int> inst_task0;
     size_t arena_doubles = 0, aux_bytes = 0;
     int cap = 0, max_K = 0, max_kd = 0, max_q = 0, max_ngam = 0;
     bool any_ee = false, tdse = false;
-    long long psi_total = 0, zbuf_total = 0;
+    long long psi_total = 0, own_total = 0;
+    bool df32 = false;
+    int nsm = 0, bps = 0;
     // device memory
     void* base = nullptr;
     bool owns = false;
@@ -66,9 +70,8 @@ struct swr_ctx {
     double* d_norm_part = nullptr;
     Task* d_tasks = nullptr;
     int* d_inst_task0 = nullptr;
-    double *d_part_s = nullptr, *d_part_d = nullptr, *d_snorm = nullptr, *d_zbuf = nullptr;
-    long long* d_zoff = nullptr;
-    int *d_act = nullptr, *d_win = nullptr, *d_win_prev = nullptr;
+    double *d_part_s = nullptr, *d_part_d = nullptr, *d_snorm = nullptr, *d_own = nullptr, *d_s_prev = nullptr;
+    int *d_alive = nullptr, *d_n_active = nullptr, *d_win = nullptr, *d_win_prev = nullptr;
     GridBarrier* d_bar = nullptr;
     double *d_res_part = nullptr, *d_res = nullptr, *d_epart = nullptr, *d_energy = nullptr, *d_norm2 = nullptr;
     double* d_psi = nullptr;
@@ -79,7 +82,7 @@ struct swr_ctx {
     bool assembled = false;
     int k = 0, parity = 0;
     int grid = 0;
-    size_t ngf_smem = 0;
+    size_t win_smem = 0;
     std::vector<double> res_h, energy_h, norm2_h;
     std::vector<int> win_h, win_prev_h;
     std::vector<int> win_pp_h;  // windows of the iteration before the last one
@@ -156,16 +159,54 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
     return SWR_OK;
 }
 
+// Row tasks of the window kernel: every subdomain's rows cut into equal blocks
+// so that the resident CTAs (blocks_per_sm x SMs) get the same number of rows.
+static void plan_tasks(swr_ctx* c) {
+    c->tasks.clear();
+    c->inst_task0.clear();
+    long long rows = 0;
+    for (const SubDev& s : c->sub) rows += s.K;
+    const int ctas = (c->nsm > 0 && c->bps > 0) ? c->nsm * c->bps : 304;
+    long long target = (rows + ctas - 1) / ctas;
+    if (target < 8) target = 8;
+    if (target > ROW_BLOCK_MAX) target = ROW_BLOCK_MAX;
+    long long own = 0;
+    int cur_inst = -1;
+    for (size_t sid = 0; sid < c->sub.size(); ++sid) {
+        const SubDev& s = c->sub[sid];
+        while (cur_inst < s.inst) {
+            c->inst_task0.push_back((int)c->tasks.size());
+            ++cur_inst;
+        }
+        int nt = (int)((s.K + target - 1) / target);
+        int per = (s.K + nt - 1) / nt;
+        for (int r0 = 0; r0 < s.K; r0 += per) {
+            Task t;
+            t.sid = (int)sid;
+            t.r0 = r0;
+            t.r1 = r0 + per < s.K ? r0 + per : s.K;
+            t.inst = s.inst;
+            t.own = own;
+            own += 4LL * (t.r1 - t.r0);
+            c->tasks.push_back(t);
+        }
+    }
+    while (cur_inst < (int)c->inst.size()) {
+        c->inst_task0.push_back((int)c->tasks.size());
+        ++cur_inst;
+    }
+    c->own_total = own;
+}
+
 // Fill descriptors and offsets; returns arena size (doubles) and aux bytes.
 static void plan(swr_ctx* c) {
     const swr_problem& p = c->prob;
     c->inst.clear();
     c->sub.clear();
-    c->zoff.clear();
     c->psi_off.clear();
     c->tasks.clear();
     c->inst_task0.clear();
-    long long off = 0, zo = 0, po = 0;
+    long long off = 0, po = 0;
     c->cap = 0;
     c->tdse = p.instances[0].mode == SWR_MODE_TDSE;
     const int cx = c->tdse ? 2 : 1;
@@ -272,36 +313,26 @@ static void plan(swr_ctx* c) {
             long long ee = (d.N == 2) ? 3LL * q * kd * kd + (long long)q * q : 0;
             long long gj = ((long long)GJ_NB_HOST * GJ_NB_HOST + 2LL * GJ_NB_HOST * K) * cx;
             s.work = off; off = align32(off + (ee > gj ? ee : gj));
-            c->zoff.push_back(zo);
-            zo += 2LL * K;
+            if (c->df32) { s.Gf = off; off = align32(off + (long long)K * K); }
+            else s.Gf = 0;
             c->psi_off.push_back(po);
             po += (d.N == 2) ? (long long)q * q : q;
             if (K > c->max_K) c->max_K = K;
             if (kd > c->max_kd) c->max_kd = kd;
             if (q > c->max_q) c->max_q = q;
             if (ng > c->max_ngam) c->max_ngam = ng;
-            const int sid = (int)c->sub.size();
-            for (int r0 = 0; r0 < K; r0 += ROW_BLOCK) {
-                Task t;
-                t.sid = sid;
-                t.r0 = r0;
-                t.r1 = r0 + ROW_BLOCK < K ? r0 + ROW_BLOCK : K;
-                t.inst = i;
-                c->tasks.push_back(t);
-            }
             c->sub.push_back(s);
         }
     }
-    c->inst_task0.push_back((int)c->tasks.size());
     c->arena_doubles = (size_t)off;
-    c->zbuf_total = zo;
     c->psi_total = po;
+    plan_tasks(c);
 }
 
 // Auxiliary device arrays carved after the arena (bytes, 256-aligned).
 struct AuxPlan {
-    size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, snorm, zbuf, zoff, act, win,
-        win_prev, bar, res_part, res, epart, energy, norm2, psi, psi_off, total;
+    size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, snorm, own, s_prev, alive,
+        n_active, win, win_prev, bar, res_part, res, epart, energy, norm2, psi, psi_off, total;
 };
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 static AuxPlan aux_plan(const swr_ctx* c) {
@@ -319,9 +350,10 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.part_s = o; o = al256(o + 2 * nt * sizeof(double));
     a.part_d = o; o = al256(o + 2 * nt * sizeof(double));
     a.snorm = o; o = al256(o + ni * (size_t)(c->cap + 1) * sizeof(double));
-    a.zbuf = o; o = al256(o + (size_t)c->zbuf_total * sizeof(double));
-    a.zoff = o; o = al256(o + ns * sizeof(long long));
-    a.act = o; o = al256(o + ni * sizeof(int));
+    a.own = o; o = al256(o + (size_t)c->own_total * sizeof(double));
+    a.s_prev = o; o = al256(o + nt * sizeof(double));
+    a.alive = o; o = al256(o + nt * sizeof(int));
+    a.n_active = o; o = al256(o + sizeof(int));
     a.win = o; o = al256(o + ni * sizeof(int));
     a.win_prev = o; o = al256(o + ni * sizeof(int));
     a.bar = o; o = al256(o + sizeof(GridBarrier));
@@ -334,6 +366,25 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.psi_off = o; o = al256(o + ns * sizeof(long long));
     a.total = o;
     return a;
+}
+
+// Layout for the current device: the row tasks depend on the SM count and on
+// how many window CTAs fit per SM (two at most; 152 x 2 without a device).
+static void plan_for_device(swr_ctx* c, const swr_problem* p) {
+    c->df32 = (p->precision == SWR_PREC_MIXED);
+    plan(c);
+    int dev = 0;
+    c->win_smem = window_smem(c->max_K, c->max_kd);
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        window_occupancy(&c->bps, c->win_smem, c->df32) == cudaSuccess) {
+        if (c->bps > 2) c->bps = 2;  // two CTAs per SM keep the barriers short
+    } else {
+        cudaGetLastError();
+        c->nsm = 152;
+        c->bps = 2;
+    }
+    plan_tasks(c);
 }
 
 static swr_status copy_problem(swr_ctx* c, const swr_problem* p) {
@@ -366,7 +417,7 @@ extern "C" swr_status swr_workspace_size(const swr_problem* p, size_t* bytes) {
     if (st != SWR_OK) return st;
     swr_ctx tmp;
     copy_problem(&tmp, p);
-    plan(&tmp);
+    plan_for_device(&tmp, p);
     *bytes = aux_plan(&tmp).total;
     return SWR_OK;
 }
@@ -378,7 +429,7 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     if (st != SWR_OK) return st;
     swr_ctx* c = new swr_ctx();
     copy_problem(c, p);
-    plan(c);
+    plan_for_device(c, p);
     AuxPlan a = aux_plan(c);
     c->stream = (cudaStream_t)p->stream;
     if (p->workspace) {
@@ -413,9 +464,10 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->d_part_s = (double*)(b + a.part_s);
     c->d_part_d = (double*)(b + a.part_d);
     c->d_snorm = (double*)(b + a.snorm);
-    c->d_zbuf = (double*)(b + a.zbuf);
-    c->d_zoff = (long long*)(b + a.zoff);
-    c->d_act = (int*)(b + a.act);
+    c->d_own = (double*)(b + a.own);
+    c->d_s_prev = (double*)(b + a.s_prev);
+    c->d_alive = (int*)(b + a.alive);
+    c->d_n_active = (int*)(b + a.n_active);
     c->d_win = (int*)(b + a.win);
     c->d_win_prev = (int*)(b + a.win_prev);
     c->d_bar = (GridBarrier*)(b + a.bar);
@@ -452,9 +504,8 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     CU(cudaMemcpyAsync(c->d_jobs2, j2.data(), j2.size() * sizeof(GemmJob), cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->d_tasks, c->tasks.data(), c->tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->d_inst_task0, c->inst_task0.data(), c->inst_task0.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    CU(cudaMemcpyAsync(c->d_zoff, c->zoff.data(), c->zoff.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->d_psi_off, c->psi_off.data(), c->psi_off.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
-    c->counters[8] += (double)(c->inst.size() * sizeof(InstDev) + c->sub.size() * (sizeof(SubDev) + 2 * sizeof(GemmJob) + 2 * sizeof(long long)) +
+    c->counters[8] += (double)(c->inst.size() * sizeof(InstDev) + c->sub.size() * (sizeof(SubDev) + 2 * sizeof(GemmJob) + sizeof(long long)) +
                                c->tasks.size() * sizeof(Task) + c->inst_task0.size() * sizeof(int));
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
     CU(cudaMemsetAsync(c->d_win_prev, 0, c->inst.size() * sizeof(int), c->stream));
@@ -464,13 +515,8 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     CU(cudaEventCreate(&c->evw0));
     CU(cudaEventCreate(&c->evw1));
     // persistent grid for the window kernel
-    c->ngf_smem = (2 * (size_t)c->max_K + (size_t)c->max_kd + ROW_BLOCK + 64) * sizeof(double);
-    int bps = 0, dev = 0, nsm = 0;
-    CU(cudaGetDevice(&dev));
-    CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CU(ngf_occupancy(&bps, c->ngf_smem));
-    if (bps < 1) return fail(c, SWR_EINVAL, "window kernel does not fit on an SM");
-    int maxgrid = bps * nsm;
+    if (c->bps < 1 || c->nsm < 1) return fail(c, SWR_EINVAL, "window kernel does not fit on an SM");
+    int maxgrid = c->bps * c->nsm;
     int nt = (int)c->tasks.size();
     c->grid = nt < maxgrid ? nt : maxgrid;
     c->res_h.assign(c->inst.size(), 0.0);
@@ -511,13 +557,15 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     CU(cudaEventRecord(c->ev0, c->stream));
     CU(launch_assemble(view(c), c->stream, c->max_q, c->max_kd, c->max_K, c->any_ee, c->tdse, !c->tdse,
                        c->d_jobs1, c->d_jobs2, c->d_norm_part, CHOL_TAU));
+    if (c->df32) CU(launch_split_df32(view(c), c->stream, c->max_K));
     CU(cudaEventRecord(c->ev1, c->stream));
     swr_status st = check_err(c);
     if (st != SWR_OK) return st;
     float ams = 0;
     CU(cudaEventElapsedTime(&ams, c->ev0, c->ev1));
     c->counters[6] += ams;
-    c->counters[2] += kAssembleLaunchesFixed + (c->any_ee ? 3 : 0) + 2 * ((c->max_K + GJ_NB_HOST - 1) / GJ_NB_HOST);
+    c->counters[2] += kAssembleLaunchesFixed + (c->any_ee ? 3 : 0) + 2 * ((c->max_K + GJ_NB_HOST - 1) / GJ_NB_HOST) +
+                      (c->df32 ? 1 : 0);
     c->assembled = true;
     c->k = 0;
     c->parity = 0;
@@ -532,13 +580,15 @@ static SweepArgs sweep_args(swr_ctx* c) {
     a.tasks = c->d_tasks;
     a.n_tasks = (int)c->tasks.size();
     a.tasks_per_cta = (a.n_tasks + c->grid - 1) / c->grid;
+    a.kmax = c->max_K;
     a.inst_task0 = c->d_inst_task0;
     a.part_s = c->d_part_s;
     a.part_d = c->d_part_d;
     a.snorm = c->d_snorm;
-    a.zbuf = c->d_zbuf;
-    a.zoff = c->d_zoff;
-    a.act = c->d_act;
+    a.own = c->d_own;
+    a.alive = c->d_alive;
+    a.s_prev = c->d_s_prev;
+    a.n_active = c->d_n_active;
     a.win = c->d_win;
     a.win_prev = c->d_win_prev;
     a.cap = c->cap;
@@ -554,7 +604,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     CU(cudaEventRecord(c->ev0, c->stream));
     SweepArgs a = sweep_args(c);
     int grid = (a.n_tasks + a.tasks_per_cta - 1) / a.tasks_per_cta;
-    CU(launch_ngf_iteration(a, grid, c->ngf_smem, c->stream, (int)c->inst.size(), c->max_K, c->evw0, c->evw1));
+    CU(launch_window(a, grid, c->win_smem, c->stream, (int)c->inst.size(), c->df32, c->evw0, c->evw1));
     CU(launch_post(view(c), c->stream, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
                    c->d_res_part, RES_BLOCKS, c->d_res, c->cap));
     CU(launch_energy(view(c), c->stream, c->d_win, c->d_snorm, c->cap, c->d_epart, c->d_energy, c->d_norm2,

@@ -55,6 +55,7 @@ struct SubDev {
     long long u[2];               // (cap+1)*ngam own traces, two iteration parities (x2 complex)
     long long g;                  // (cap+1)*ngam averaged Robin data (x2 complex)
     long long work;               // scratch for assembly (see swr_assemble.cu)
+    long long Gf;                 // mixed precision: G as FP32 pairs (G_hi [K*K] then G_lo [K*K])
     int nline;                    // values per step in `line`
 };
 
@@ -154,19 +155,21 @@ struct GemmJob {
 // Row block [r0, r1) of the step matrix of subdomain sid (persistent task).
 struct Task {
     int sid, r0, r1, inst;
+    long long own;              // offset of the task's ring [4][r1-r0] in SweepArgs::own
 };
 
 struct SweepArgs {
     SwrDeviceView v;
     const Task* tasks;
-    int n_tasks, tasks_per_cta;
+    int n_tasks, tasks_per_cta, kmax;
     const int* inst_task0;      // [n_inst+1] first task of each instance
     double* part_s;             // [2][n_tasks]
     double* part_d;             // [2][n_tasks]
     double* snorm;              // [n_inst][cap+1] normalisation factors s_n
-    double* zbuf;               // per subdomain [2][K] (A'chi y) ring, offsets zoff[sid]
-    const long long* zoff;
-    int* act;                   // [n_inst] active flags
+    double* own;                // per-task rings of own rows: y^n, y^{n-1}, z^n, z^{n-1}
+    int* alive;                 // [n_tasks] task still stepping (touched by its CTA only)
+    double* s_prev;             // [n_tasks] last normalisation factor seen by the task
+    int* n_active;              // instances still stepping
     int* win;                   // [n_inst] window length of this iteration
     const int* win_prev;        // [n_inst] window of the previous iteration (0: none)
     int cap;                    // max window stored

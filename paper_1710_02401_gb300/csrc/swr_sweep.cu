@@ -1,17 +1,6 @@
 // swr_sweep.cu -- one Schwarz iteration over all subdomains on sm_103a.
 //
-// Imaginary time (Sec. 5.2 system SIT, Sec. 5.4 steps 2 and 4): on every
-// subdomain, implicit Euler in the orthonormal local basis
-//     y^{n+1} = G (c^n + kappa dt b'^{n+1}),   G = (I + dt H')^{-1},
-// then the global normalisation c^{n+1} = y^{n+1} / s_{n+1},
-//     s_{n+1}^2 = sum_i y_i^T (Pp (x) Pp) y_i        (partition-of-unity norm),
-// and the inner stop ||c^{n+1} - c^n|| <= ngf_tol (Sec. 5.2).  The whole time
-// window runs in ONE persistent cooperative kernel: each CTA owns fixed row
-// blocks of the step matrices, two bounded grid barriers per step separate the
-// matvec from the norm reduction, all reductions are deterministic (fixed
-// order over per-task partials, per instance).
-//
-// After the window: line traces (psi and d psi at the 4 line positions of
+// The time window itself runs in swr_window.cu.  After the window: line traces (psi and d psi at the 4 line positions of
 // every subdomain coordinate), the averaged Robin data of Sec. 5.1 for every
 // interface node, the Robin source b' of the next iteration, the own interface
 // traces and Res(k) (Eq. residueIT), and the energy.
@@ -21,42 +10,6 @@
 #include "swr_internal.cuh"
 
 namespace swr {
-
-// z rows = (Pp1 (x) Pp2) y  for rows [r0, r1) of one subdomain; y in shared memory.
-__device__ void achi_rows(const SwrDeviceView& v, const SubDev& s, const double* ys, int r0, int r1,
-                          double* zrow, double* tmp) {
-    const int kd = s.kd;
-    T1Layout lay(s.q, kd);
-    const double* P1 = v.arena + s.t1[0] + lay.mat(M_PP);
-    if (s.N == 1) {
-        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-            double acc = 0;
-            for (int c = 0; c < kd; ++c) acc += P1[r * kd + c] * ys[c];
-            zrow[r - r0] = acc;
-        }
-        __syncthreads();
-        return;
-    }
-    const double* P2 = v.arena + s.t1[1] + lay.mat(M_PP);
-    const int b0 = r0 / kd, b1 = (r1 - 1) / kd;
-    for (int b = b0; b <= b1; ++b) {
-        // tmp[c] = sum_e Y[c][e] P2[b][e],  Y[c][e] = y[c + kd e]
-        for (int c = threadIdx.x; c < kd; c += blockDim.x) {
-            double acc = 0;
-            for (int e = 0; e < kd; ++e) acc += ys[c + kd * e] * P2[b * kd + e];
-            tmp[c] = acc;
-        }
-        __syncthreads();
-        int lo = max(r0, b * kd), hi = min(r1, (b + 1) * kd);
-        for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
-            int a = r - b * kd;
-            double acc = 0;
-            for (int c = 0; c < kd; ++c) acc += P1[a * kd + c] * tmp[c];
-            zrow[r - r0] = acc;
-        }
-        __syncthreads();
-    }
-}
 
 __device__ inline double block_sum(double x, double* red) {
     x = warp_sum(x);
@@ -79,177 +32,6 @@ __device__ inline double inst_sum(const double* part, int t0, int t1, double* re
     for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) x += __ldcg(part + t);
     // fixed reduction tree: thread order is deterministic for a fixed blockDim
     return block_sum(x, red);
-}
-
-// Persistent imaginary-time window (real arithmetic).  Dynamic shared memory:
-// 2*Kmax (v / y) + Kmax (z rows) + kd_max doubles.
-__global__ void __launch_bounds__(256) k_ngf_window(SweepArgs A) {
-    extern __shared__ double sm[];
-    __shared__ double red[33];
-    const SwrDeviceView& v = A.v;
-    const unsigned nblk = gridDim.x;
-    const int t_begin = blockIdx.x * A.tasks_per_cta;
-    const int t_end = min(A.n_tasks, t_begin + A.tasks_per_cta);
-    const int cap = A.cap;
-    double* vs = sm;  // vector of the current subdomain (K)
-    // layout of the remaining dynamic shared memory is set per task below
-    // The active flags act[] change only in phase B (first task of an instance),
-    // so they are stable from the second barrier of a step to the first barrier
-    // of the next one, where every CTA takes the termination decision.
-    __shared__ int s_act;
-    for (int n = 0;; ++n) {
-        // ------------------------------------------------------------ phase A(n+1)
-        // s_n from the partials of phase B(n); delta_n partials;
-        // y^{n+1} rows = G rows (y^n / s_n + kappa dt b'^{n+1}).
-        for (int t = t_begin; t < t_end; ++t) {
-            const Task tk = A.tasks[t];
-            const SubDev& s = v.sub[tk.sid];
-            const InstDev& in = v.inst[tk.inst];
-            if (threadIdx.x == 0) s_act = __ldcg(A.act + tk.inst);
-            __syncthreads();
-            if (!s_act) continue;
-            const int t0 = A.inst_task0[tk.inst], t1 = A.inst_task0[tk.inst + 1];
-            const bool first = (t == t0);
-            double s_n = 1.0;
-            if (in.normalize) s_n = sqrt(inst_sum(A.part_s + (n & 1) * A.n_tasks, t0, t1, red));
-            if (first && threadIdx.x == 0) A.snorm[(long long)tk.inst * (cap + 1) + n] = s_n;
-            const int fixed = in.window_cap;  // fixed window length, 0 when the NGF stop decides
-            const int maxs = fixed > 0 ? fixed : in.max_steps;
-            if (n >= maxs || !isfinite(s_n) || s_n <= 0.0) continue;  // closed in phase B
-            const int K = s.K;
-            const double* hist = v.arena + s.hist;
-            // delta_n partial over this task's rows (needs y^{n-1}, z^{n-1}, s_{n-1})
-            if (n >= 1 && fixed == 0 && in.ngf_tol > 0.0) {
-                double s_p = __ldcg(A.snorm + (long long)tk.inst * (cap + 1) + n - 1);
-                const double* yn = hist + (long long)n * K;
-                const double* yp = hist + (long long)(n - 1) * K;
-                const double* zn = A.zbuf + A.zoff[tk.sid] + (n & 1) * K;
-                const double* zp = A.zbuf + A.zoff[tk.sid] + ((n - 1) & 1) * K;
-                double acc = 0;
-                for (int r = tk.r0 + threadIdx.x; r < tk.r1; r += blockDim.x) {
-                    double dy = __ldcg(yn + r) / s_n - __ldcg(yp + r) / s_p;
-                    double dz = __ldcg(zn + r) / s_n - __ldcg(zp + r) / s_p;
-                    acc += dy * dz;
-                }
-                acc = block_sum(acc, red);
-                if (threadIdx.x == 0) A.part_d[(n & 1) * A.n_tasks + t] = acc;
-            }
-            // v = y^n / s_n + kappa dt b'^{n+1}
-            const int wp = A.win_prev[tk.inst];
-            const double* bsrc = (wp > 0) ? v.arena + s.bvec + (long long)min(n + 1, wp) * K : nullptr;
-            const double kdt = in.kappa * in.dt;
-            const double* yn = hist + (long long)n * K;
-            for (int c = threadIdx.x; c < K; c += blockDim.x) {
-                double val = __ldcg(yn + c) / s_n;
-                if (bsrc) val += kdt * __ldcg(bsrc + c);
-                vs[c] = val;
-            }
-            __syncthreads();
-            // rows: one warp per row, lanes over columns
-            const double* G = v.arena + s.Gm;
-            double* ynew = v.arena + s.hist + (long long)(n + 1) * K;
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-            for (int r = tk.r0 + warp; r < tk.r1; r += nw) {
-                const double* g = G + (long long)r * K;
-                double acc0 = 0, acc1 = 0;
-                int c = lane;
-                for (; c + 32 < K; c += 64) {
-                    acc0 = fma(g[c], vs[c], acc0);
-                    acc1 = fma(g[c + 32], vs[c + 32], acc1);
-                }
-                if (c < K) acc0 = fma(g[c], vs[c], acc0);
-                double acc = warp_sum(acc0 + acc1);
-                if (lane == 0) ynew[r] = acc;
-            }
-            __syncthreads();
-        }
-        if (!grid_sync_bounded(A.bar, nblk, v.err, A.spin_limit)) return;
-        // ------------------------------------------------------------ phase B(n+1)
-        // stop test on delta_n; z^{n+1} rows = A'chi y^{n+1}; s^2 partials.
-        for (int t = t_begin; t < t_end; ++t) {
-            const Task tk = A.tasks[t];
-            const SubDev& s = v.sub[tk.sid];
-            const InstDev& in = v.inst[tk.inst];
-            if (threadIdx.x == 0) s_act = __ldcg(A.act + tk.inst);
-            __syncthreads();
-            if (!s_act) continue;
-            const int t0 = A.inst_task0[tk.inst], t1 = A.inst_task0[tk.inst + 1];
-            const bool first = (t == t0);
-            // window end: fixed length / step cap reached, bad norm, or NGF stop on delta_n
-            const int fixed = in.window_cap;
-            const int maxs = fixed > 0 ? fixed : in.max_steps;
-            const double s_n = __ldcg(A.snorm + (long long)tk.inst * (cap + 1) + n);
-            bool stop = (n >= maxs) || !isfinite(s_n) || s_n <= 0.0;
-            if (!stop && n >= 1 && fixed == 0 && in.ngf_tol > 0.0) {
-                double d2 = inst_sum(A.part_d + (n & 1) * A.n_tasks, t0, t1, red);
-                stop = sqrt(fmax(d2, 0.0)) <= in.ngf_tol;
-            }
-            if (stop) {
-                if (first && threadIdx.x == 0) {
-                    A.win[tk.inst] = n;
-                    if (!isfinite(s_n) || s_n <= 0.0) atomicOr(v.err, SWR_ERR_NUMERIC);
-                    __threadfence();
-                    atomicExch(A.act + tk.inst, 0);
-                }
-                continue;
-            }
-            const int K = s.K;
-            const double* yn1 = v.arena + s.hist + (long long)(n + 1) * K;
-            for (int c = threadIdx.x; c < K; c += blockDim.x) vs[c] = __ldcg(yn1 + c);
-            __syncthreads();
-            double* zrow = sm + K;
-            double* tmp = sm + 2 * K;
-            achi_rows(v, s, vs, tk.r0, tk.r1, zrow, tmp);
-            double* zdst = A.zbuf + A.zoff[tk.sid] + ((n + 1) & 1) * K;
-            double acc = 0;
-            for (int r = tk.r0 + threadIdx.x; r < tk.r1; r += blockDim.x) {
-                double z = zrow[r - tk.r0];
-                zdst[r] = z;
-                acc += vs[r] * z;
-            }
-            acc = block_sum(acc, red);
-            if (threadIdx.x == 0) A.part_s[((n + 1) & 1) * A.n_tasks + t] = acc;
-        }
-        if (!grid_sync_bounded(A.bar, nblk, v.err, A.spin_limit)) return;
-        // global termination: all instances inactive
-        __shared__ int s_any;
-        if (threadIdx.x == 0) {
-            int a = 0;
-            for (int i = 0; i < v.n_inst; ++i) a |= __ldcg(A.act + i);
-            s_any = a;
-        }
-        __syncthreads();
-        if (!s_any) return;
-    }
-}
-
-// Phase "B(0)": z^0 = A'chi c0 and the s_0^2 partials, and y^0 = c0 into hist[0].
-__global__ void k_ngf_prologue(SweepArgs A) {
-    extern __shared__ double sm[];
-    __shared__ double red[33];
-    const SwrDeviceView& v = A.v;
-    for (int t = blockIdx.x; t < A.n_tasks; t += gridDim.x) {
-        const Task tk = A.tasks[t];
-        const SubDev& s = v.sub[tk.sid];
-        const int K = s.K;
-        const double* c0 = v.arena + s.c0;
-        double* h0 = v.arena + s.hist;
-        for (int c = threadIdx.x; c < K; c += blockDim.x) sm[c] = c0[c];
-        __syncthreads();
-        for (int r = tk.r0 + threadIdx.x; r < tk.r1; r += blockDim.x) h0[r] = sm[r];
-        double* zrow = sm + K;
-        double* tmp = sm + 2 * K;
-        achi_rows(v, s, sm, tk.r0, tk.r1, zrow, tmp);
-        double* zdst = A.zbuf + A.zoff[tk.sid];
-        double acc = 0;
-        for (int r = tk.r0 + threadIdx.x; r < tk.r1; r += blockDim.x) {
-            zdst[r] = zrow[r - tk.r0];
-            acc += sm[r] * zrow[r - tk.r0];
-        }
-        acc = block_sum(acc, red);
-        if (threadIdx.x == 0) A.part_s[t] = acc;
-        __syncthreads();
-    }
 }
 
 // ---------------------------------------------------------------- traces
@@ -551,45 +333,13 @@ __global__ void k_energy_reduce(SwrDeviceView v, const double* part, double* ene
     norm2[i] = den;
 }
 
-__global__ void k_reset_iter(int* act, int n_inst, GridBarrier* bar) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_inst) act[i] = 1;
-    if (i == 0) { bar->count = 0; bar->gen = 0; }
-}
-
 // ------------------------------------------------------------- host driver
 
 static inline unsigned div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
-struct SweepHost {
-    SweepArgs args;
-    int grid;
-    size_t smem;
-};
-
-cudaError_t ngf_occupancy(int* blocks_per_sm, size_t smem) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_ngf_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_ngf_window, 256, smem);
-}
-
-// Kernel launches per swr_step (reset, prologue, window, line traces, gather,
-// residual, residual reduce, energy, energy reduce).
-extern const int kStepLaunches = 9;
-
-cudaError_t launch_ngf_iteration(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst,
-                                 int max_K, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
-    k_reset_iter<<<div_up(max(n_inst, 1), 256), 256, 0, st>>>(a.act, n_inst, a.bar);
-    k_ngf_prologue<<<min(a.n_tasks, 1024), 256, smem, st>>>(a);
-    cudaError_t e = cudaEventRecord(ev_begin, st);
-    if (e != cudaSuccess) return e;
-    void* params[] = {&a};
-    e = cudaLaunchCooperativeKernel((const void*)k_ngf_window, dim3(grid), dim3(256), params, smem, st);
-    if (e != cudaSuccess) return e;
-    return cudaEventRecord(ev_end, st);
-}
+// Kernel launches per swr_step besides the window (reset, window, line traces,
+// gather, residual, residual reduce, energy, energy reduce).
+extern const int kStepLaunches = 8;
 
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,

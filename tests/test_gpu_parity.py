@@ -38,8 +38,8 @@ def swr_mod():
     return S
 
 
-def _run_gpu(S, inst, kmax, tol=0.0):
-    s = S.SWR(inst)
+def _run_gpu(S, inst, kmax, tol=0.0, precision=0):
+    s = S.SWR(inst, precision=precision)
     s.assemble()
     res, wins, energies = [], [], []
     for _ in range(kmax):
@@ -55,9 +55,9 @@ def _run_gpu(S, inst, kmax, tol=0.0):
 REL_ROBIN = 1e-9
 
 
-def _compare(S, inst, kmax, tol=0.0, rel=REL):
+def _compare(S, inst, kmax, tol=0.0, rel=REL, precision=0):
     ref = O.run_swr(inst, kmax=kmax, tol=tol)
-    s, res, wins, energies = _run_gpu(S, inst, len(ref.records), tol)
+    s, res, wins, energies = _run_gpu(S, inst, len(ref.records), tol, precision)
     assert wins == [r.n_win for r in ref.records]
     r0 = max(r.res for r in ref.records)
     for a, r in zip(res, ref.records):
@@ -97,6 +97,15 @@ def test_parity_one_electron_harmonic(swr_mod):
 def test_parity_two_electrons_3x3(swr_mod):
     # 9 subdomains (corner bands with 3 contributors), K = 100: ragged 32-row tasks
     _compare(swr_mod, P.small_tise_2d(), kmax=6)
+
+
+def test_parity_mixed_precision_one_electron(swr_mod):
+    # double-single step matrices on the FP32 pipes: same tolerance as FP64
+    _compare(swr_mod, P.tise_1d_two_subdomains(), kmax=50, tol=1e-8, precision=swr_mod.PREC_MIXED)
+
+
+def test_parity_mixed_precision_two_electrons_3x3(swr_mod):
+    _compare(swr_mod, P.small_tise_2d(), kmax=6, precision=swr_mod.PREC_MIXED)
 
 
 def test_parity_two_electrons_uneven_kd_and_no_ee(swr_mod):
