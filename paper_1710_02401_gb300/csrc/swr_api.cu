@@ -20,7 +20,9 @@ namespace swr {
 cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, int max_kd, int max_K,
                             bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
                             const GemmJob* d_jobs2, double* d_norm_part, double tau);
-size_t window_smem(int kmax, int kdmax);
+size_t window_smem(int kmax, int kdmax, int tasks_per_cta, long long g_resident_floats);
+int window_tasks_per_cta_max();
+int window_rows_per_task_max();
 cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, bool df32);
 cudaError_t launch_split_df32(const SwrDeviceView& v, cudaStream_t st, int max_K);
 cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst, bool df32,
@@ -36,7 +38,6 @@ cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_
 
 using namespace swr;
 
-static const int ROW_BLOCK_MAX = 64;  // rows of a step matrix per persistent task (upper bound)
 static const int GJ_NB_HOST = 32;     // Gauss-Jordan block (matches swr_assemble.cu)
 static const int RES_BLOCKS = 8;      // residual partial blocks per subdomain
 static const double CHOL_TAU = 1e-15; // relative pivot floor of the overlap Cholesky
@@ -57,8 +58,8 @@ struct swr_ctx {
     int cap = 0, max_K = 0, max_kd = 0, max_q = 0, max_ngam = 0;
     bool any_ee = false, tdse = false;
     long long psi_total = 0, own_total = 0;
-    bool df32 = false;
-    int nsm = 0, bps = 0;
+    bool df32 = false, g_resident = false, any_ngf_stop = false;
+    int nsm = 0, bps = 0, tasks_per_cta = 1, max_rows = 0;
     // device memory
     void* base = nullptr;
     bool owns = false;
@@ -70,8 +71,8 @@ struct swr_ctx {
     double* d_norm_part = nullptr;
     Task* d_tasks = nullptr;
     int* d_inst_task0 = nullptr;
-    double *d_part_s = nullptr, *d_part_d = nullptr, *d_snorm = nullptr, *d_own = nullptr, *d_s_prev = nullptr;
-    int *d_alive = nullptr, *d_n_active = nullptr, *d_win = nullptr, *d_win_prev = nullptr;
+    double *d_part_s = nullptr, *d_part_d = nullptr, *d_snorm = nullptr, *d_sums_s = nullptr, *d_sums_d = nullptr;
+    int *d_n_active = nullptr, *d_win = nullptr, *d_win_prev = nullptr;
     GridBarrier* d_bar = nullptr;
     double *d_res_part = nullptr, *d_res = nullptr, *d_epart = nullptr, *d_energy = nullptr, *d_norm2 = nullptr;
     double* d_psi = nullptr;
@@ -166,10 +167,11 @@ static void plan_tasks(swr_ctx* c) {
     c->inst_task0.clear();
     long long rows = 0;
     for (const SubDev& s : c->sub) rows += s.K;
-    const int ctas = (c->nsm > 0 && c->bps > 0) ? c->nsm * c->bps : 304;
+    const int ctas = (c->nsm > 0 ? c->nsm : 152) * 2;
     long long target = (rows + ctas - 1) / ctas;
     if (target < 8) target = 8;
-    if (target > ROW_BLOCK_MAX) target = ROW_BLOCK_MAX;
+    if (target > window_rows_per_task_max()) target = window_rows_per_task_max();
+    c->max_rows = 0;
     long long own = 0;
     int cur_inst = -1;
     for (size_t sid = 0; sid < c->sub.size(); ++sid) {
@@ -188,6 +190,7 @@ static void plan_tasks(swr_ctx* c) {
             t.inst = s.inst;
             t.own = own;
             own += 4LL * (t.r1 - t.r0);
+            if (t.r1 - t.r0 > c->max_rows) c->max_rows = t.r1 - t.r0;
             c->tasks.push_back(t);
         }
     }
@@ -196,6 +199,9 @@ static void plan_tasks(swr_ctx* c) {
         ++cur_inst;
     }
     c->own_total = own;
+    const int nt = (int)c->tasks.size();
+    c->tasks_per_cta = (nt + ctas - 1) / ctas;
+    if (c->tasks_per_cta < 1) c->tasks_per_cta = 1;
 }
 
 // Fill descriptors and offsets; returns arena size (doubles) and aux bytes.
@@ -313,8 +319,13 @@ static void plan(swr_ctx* c) {
             long long ee = (d.N == 2) ? 3LL * q * kd * kd + (long long)q * q : 0;
             long long gj = ((long long)GJ_NB_HOST * GJ_NB_HOST + 2LL * GJ_NB_HOST * K) * cx;
             s.work = off; off = align32(off + (ee > gj ? ee : gj));
-            if (c->df32) { s.Gf = off; off = align32(off + (long long)K * K); }
-            else s.Gf = 0;
+            if (c->df32) {
+                s.Gf = off; off = align32(off + (long long)K * K);
+                s.Wf = off; off = align32(off + (long long)K * K);
+            } else {
+                s.Gf = 0;
+                s.Wf = 0;
+            }
             c->psi_off.push_back(po);
             po += (d.N == 2) ? (long long)q * q : q;
             if (K > c->max_K) c->max_K = K;
@@ -331,7 +342,7 @@ static void plan(swr_ctx* c) {
 
 // Auxiliary device arrays carved after the arena (bytes, 256-aligned).
 struct AuxPlan {
-    size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, snorm, own, s_prev, alive,
+    size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, snorm, sums_s, sums_d,
         n_active, win, win_prev, bar, res_part, res, epart, energy, norm2, psi, psi_off, total;
 };
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -350,9 +361,8 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.part_s = o; o = al256(o + 2 * nt * sizeof(double));
     a.part_d = o; o = al256(o + 2 * nt * sizeof(double));
     a.snorm = o; o = al256(o + ni * (size_t)(c->cap + 1) * sizeof(double));
-    a.own = o; o = al256(o + (size_t)c->own_total * sizeof(double));
-    a.s_prev = o; o = al256(o + nt * sizeof(double));
-    a.alive = o; o = al256(o + nt * sizeof(int));
+    a.sums_s = o; o = al256(o + ni * sizeof(double));
+    a.sums_d = o; o = al256(o + ni * sizeof(double));
     a.n_active = o; o = al256(o + sizeof(int));
     a.win = o; o = al256(o + ni * sizeof(int));
     a.win_prev = o; o = al256(o + ni * sizeof(int));
@@ -372,19 +382,30 @@ static AuxPlan aux_plan(const swr_ctx* c) {
 // how many window CTAs fit per SM (two at most; 152 x 2 without a device).
 static void plan_for_device(swr_ctx* c, const swr_problem* p) {
     c->df32 = (p->precision == SWR_PREC_MIXED);
-    plan(c);
     int dev = 0;
-    c->win_smem = window_smem(c->max_K, c->max_kd);
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-        window_occupancy(&c->bps, c->win_smem, c->df32) == cudaSuccess) {
-        if (c->bps > 2) c->bps = 2;  // two CTAs per SM keep the barriers short
-    } else {
+    bool have_dev = cudaGetDevice(&dev) == cudaSuccess &&
+                    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+    if (!have_dev) {
         cudaGetLastError();
         c->nsm = 152;
-        c->bps = 2;
     }
-    plan_tasks(c);
+    plan(c);  // descriptors, arena and the row tasks for 2 CTAs per SM
+    c->any_ngf_stop = false;
+    for (const InstDev& d : c->inst)
+        if (d.window_cap == 0 && d.ngf_tol > 0.0) c->any_ngf_stop = true;
+    // keep the CTA's rows of G_hi in shared memory when one task per CTA fits twice per SM
+    c->g_resident = c->df32 && c->tasks_per_cta == 1;
+    c->win_smem = window_smem(c->max_K, c->max_kd, c->tasks_per_cta,
+                              c->g_resident ? (long long)c->max_rows * c->max_K : 0);
+    c->bps = 2;
+    if (have_dev) {
+        if (c->win_smem > 110 * 1024) {
+            c->g_resident = false;
+            c->win_smem = window_smem(c->max_K, c->max_kd, c->tasks_per_cta, 0);
+        }
+        if (window_occupancy(&c->bps, c->win_smem, c->df32) != cudaSuccess) c->bps = 0;
+        if (c->bps > 2) c->bps = 2;
+    }
 }
 
 static swr_status copy_problem(swr_ctx* c, const swr_problem* p) {
@@ -464,9 +485,8 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->d_part_s = (double*)(b + a.part_s);
     c->d_part_d = (double*)(b + a.part_d);
     c->d_snorm = (double*)(b + a.snorm);
-    c->d_own = (double*)(b + a.own);
-    c->d_s_prev = (double*)(b + a.s_prev);
-    c->d_alive = (int*)(b + a.alive);
+    c->d_sums_s = (double*)(b + a.sums_s);
+    c->d_sums_d = (double*)(b + a.sums_d);
     c->d_n_active = (int*)(b + a.n_active);
     c->d_win = (int*)(b + a.win);
     c->d_win_prev = (int*)(b + a.win_prev);
@@ -514,11 +534,15 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     CU(cudaEventCreate(&c->ev1));
     CU(cudaEventCreate(&c->evw0));
     CU(cudaEventCreate(&c->evw1));
-    // persistent grid for the window kernel
+    // persistent grid for the window kernel: all CTAs must be co-resident
     if (c->bps < 1 || c->nsm < 1) return fail(c, SWR_EINVAL, "window kernel does not fit on an SM");
-    int maxgrid = c->bps * c->nsm;
+    if (c->tasks_per_cta > window_tasks_per_cta_max())
+        return fail(c, SWR_EINVAL, "problem has %zu row tasks: more than %d per CTA for the window kernel",
+                    c->tasks.size(), window_tasks_per_cta_max());
     int nt = (int)c->tasks.size();
-    c->grid = nt < maxgrid ? nt : maxgrid;
+    c->grid = (nt + c->tasks_per_cta - 1) / c->tasks_per_cta;
+    if (c->grid > c->bps * c->nsm)
+        return fail(c, SWR_EINVAL, "window grid of %d CTAs exceeds %d resident CTAs", c->grid, c->bps * c->nsm);
     c->res_h.assign(c->inst.size(), 0.0);
     c->energy_h.assign(c->inst.size(), 0.0);
     c->norm2_h.assign(c->inst.size(), 0.0);
@@ -565,7 +589,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     CU(cudaEventElapsedTime(&ams, c->ev0, c->ev1));
     c->counters[6] += ams;
     c->counters[2] += kAssembleLaunchesFixed + (c->any_ee ? 3 : 0) + 2 * ((c->max_K + GJ_NB_HOST - 1) / GJ_NB_HOST) +
-                      (c->df32 ? 1 : 0);
+                      (c->df32 ? 2 : 0);
     c->assembled = true;
     c->k = 0;
     c->parity = 0;
@@ -579,15 +603,17 @@ static SweepArgs sweep_args(swr_ctx* c) {
     a.v = view(c);
     a.tasks = c->d_tasks;
     a.n_tasks = (int)c->tasks.size();
-    a.tasks_per_cta = (a.n_tasks + c->grid - 1) / c->grid;
+    a.tasks_per_cta = c->tasks_per_cta;
     a.kmax = c->max_K;
+    a.kdmax = c->max_kd;
+    a.g_resident = c->g_resident ? 1 : 0;
+    a.any_ngf_stop = c->any_ngf_stop ? 1 : 0;
     a.inst_task0 = c->d_inst_task0;
     a.part_s = c->d_part_s;
     a.part_d = c->d_part_d;
     a.snorm = c->d_snorm;
-    a.own = c->d_own;
-    a.alive = c->d_alive;
-    a.s_prev = c->d_s_prev;
+    a.sums_s = c->d_sums_s;
+    a.sums_d = c->d_sums_d;
     a.n_active = c->d_n_active;
     a.win = c->d_win;
     a.win_prev = c->d_win_prev;
@@ -603,7 +629,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
     CU(cudaEventRecord(c->ev0, c->stream));
     SweepArgs a = sweep_args(c);
-    int grid = (a.n_tasks + a.tasks_per_cta - 1) / a.tasks_per_cta;
+    int grid = c->grid;
     CU(launch_window(a, grid, c->win_smem, c->stream, (int)c->inst.size(), c->df32, c->evw0, c->evw1));
     CU(launch_post(view(c), c->stream, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
                    c->d_res_part, RES_BLOCKS, c->d_res, c->cap));

@@ -56,6 +56,7 @@ struct SubDev {
     long long g;                  // (cap+1)*ngam averaged Robin data (x2 complex)
     long long work;               // scratch for assembly (see swr_assemble.cu)
     long long Gf;                 // mixed precision: G as FP32 pairs (G_hi [K*K] then G_lo [K*K])
+    long long Wf;                 // mixed precision: W = (Pp (x) Pp) G as FP32 pairs
     int nline;                    // values per step in `line`
 };
 
@@ -161,14 +162,15 @@ struct Task {
 struct SweepArgs {
     SwrDeviceView v;
     const Task* tasks;
-    int n_tasks, tasks_per_cta, kmax;
+    int n_tasks, tasks_per_cta, kmax, kdmax;
+    int g_resident;             // mixed precision: G_hi rows of the CTA's task kept in shared memory
+    int any_ngf_stop;           // some instance stops its window on ||c^{n+1} - c^n||
     const int* inst_task0;      // [n_inst+1] first task of each instance
-    double* part_s;             // [2][n_tasks]
-    double* part_d;             // [2][n_tasks]
+    double* part_s;             // [n_tasks] partials of s^2
+    double* part_d;             // [n_tasks] partials of delta^2
+    double* sums_s;             // [n_inst] s^2 per instance (reduced at the grid barrier)
+    double* sums_d;             // [n_inst] delta^2 per instance
     double* snorm;              // [n_inst][cap+1] normalisation factors s_n
-    double* own;                // per-task rings of own rows: y^n, y^{n-1}, z^n, z^{n-1}
-    int* alive;                 // [n_tasks] task still stepping (touched by its CTA only)
-    double* s_prev;             // [n_tasks] last normalisation factor seen by the task
     int* n_active;              // instances still stepping
     int* win;                   // [n_inst] window length of this iteration
     const int* win_prev;        // [n_inst] window of the previous iteration (0: none)

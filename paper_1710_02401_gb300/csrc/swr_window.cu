@@ -8,23 +8,25 @@
 // is the global normalisation; the inner stop is ||c^{n+1} - c^n|| <= tol with
 // c^n = y^n / s_n (Sec. 5.2).
 //
-// One persistent cooperative launch runs the whole window.  Work unit: a task
-// = a block of rows of one subdomain's G; tasks are sized so that every SM
-// gets the same number of rows.  Per step, two bounded grid barriers:
-//   phase A(n+1): s_n from the per-task partials (deterministic order), the
-//                 partial of delta_n^2 from rows this task owns, then the
-//                 rows of y^{n+1} = G v (v = y^n/s_n + kappa dt b');
-//   phase B(n+1): stop decisions, z^{n+1} rows = (Pp (x) Pp) y^{n+1} by the
-//                 Kronecker form, and the partial of s_{n+1}^2.
-// Each phase costs one dependent round trip to L2; the task's own rows of
-// y^n, y^{n-1}, z^n, z^{n-1} stay in a per-task ring that only this CTA
-// touches.
+// One persistent cooperative launch runs the whole window.  A task is a block
+// of rows of one subdomain's G, sized so that every SM gets the same number of
+// rows; a CTA keeps its tasks' constants, their own rows of y^n, y^{n-1}, z^n,
+// z^{n-1}, the Kronecker factors Pp and (mixed precision) its rows of G_hi in
+// shared memory for the whole window.  Per step:
+//   phase A(n+1): y^{n+1} rows = G v, v = y^n/s_n + kappa dt b'^{n+1}, and the
+//                 partial of delta_n^2 from the CTA's own rows;
+//   reduce-barrier: the last CTA to arrive sums the delta partials per
+//                 instance (fixed order) and releases the grid;
+//   phase B(n+1): stop decisions, z^{n+1} rows = (Pp (x) Pp) y^{n+1}, partial
+//                 of s_{n+1}^2;
+//   reduce-barrier: the same for the s^2 partials.
+// Every wait is bounded; on timeout the kernel raises SWR_ERR_TIMEOUT and
+// returns.
 //
-// Precision: FP64 (DFMA), or "double-single" (SWR_PREC_MIXED): G is stored
-// as FP32 pairs G = G_hi + G_lo and v = v_hi + v_lo; the products run on the
-// FP32 pipes with error-free TwoProduct/TwoSum accumulation into a
-// (hi, lo) pair, which keeps the FP64 accuracy of the step (error ~1e-14)
-// while using the FP32 units (64x the FP64 rate on GB300).
+// Precision: FP64 (DFMA), or double-single (SWR_PREC_MIXED): G = G_hi + G_lo
+// in FP32 pairs, v = v_hi + v_lo; products run on the FP32 pipes with
+// error-free TwoProduct/TwoSum accumulation into a (hi, lo) pair, which keeps
+// the FP64 accuracy of the step (~1e-14) on units with 64x the FP64 rate.
 #include <math.h>
 
 #include "swr_internal.cuh"
@@ -32,33 +34,16 @@
 namespace swr {
 
 #define WIN_THREADS 256
+#define WIN_TPC 4    // tasks per CTA kept in shared memory
+#define WIN_RB 64    // rows per task
 
 __device__ inline unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-
-// Monotone-counter grid barrier: the m-th barrier of a launch completes when
-// the counter reaches m * gridDim.x.  At most `limit` polls, then error.
-__device__ inline bool grid_barrier_mono(unsigned* count, unsigned target, int* err, long long limit) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        __threadfence();
-        atomicAdd(count, 1u);
-        long long it = 0;
-        while (ld_acquire_u32(count) < target) {
-            if (++it > limit) { atomicOr(err, SWR_ERR_TIMEOUT); ok = 0; break; }
-            if ((it & 255) == 0 && *(volatile int*)err) { ok = 0; break; }
-            __nanosleep(20);
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
+__device__ inline void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ inline double wblock_sum(double x, double* red) {
@@ -76,211 +61,323 @@ __device__ inline double wblock_sum(double x, double* red) {
     return red[32];
 }
 
+// Grid barrier fused with a per-instance reduction.  Every CTA has written its
+// partials to part[]; the CTA whose arrival completes the count sums them per
+// instance in task order into sums[], then publishes 2*gen + go on the release
+// word, go = 0 when `nact` (if given) shows that no instance is still stepping.
+// Bounded waits; returns false on error, *go_out receives go.
+__device__ bool reduce_barrier(unsigned* count, unsigned* release, unsigned target, unsigned gen, bool reduce,
+                               const double* part, const int* inst_task0, int n_inst, double* sums, int* err,
+                               long long limit, double* red, const int* nact, int* go_out) {
+    __shared__ int s_last, s_ok, s_go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned old = atomicAdd(count, 1u);
+        s_last = (old == target - 1);
+        s_ok = 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (reduce) {
+            if (n_inst < 8) {
+                for (int i = 0; i < n_inst; ++i) {
+                    double x = 0;
+                    for (int u = inst_task0[i] + threadIdx.x; u < inst_task0[i + 1]; u += WIN_THREADS)
+                        x += __ldcg(part + u);
+                    x = wblock_sum(x, red);
+                    if (threadIdx.x == 0) sums[i] = x;
+                }
+            } else {
+                for (int i = threadIdx.x; i < n_inst; i += WIN_THREADS) {
+                    double x = 0;
+                    for (int u = inst_task0[i]; u < inst_task0[i + 1]; ++u) x += __ldcg(part + u);
+                    sums[i] = x;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int go = nact ? (__ldcg(nact) > 0) : 1;
+            s_go = go;
+            __threadfence();
+            st_release_u32(release, 2u * gen + (unsigned)go);
+        }
+    } else if (threadIdx.x == 0) {
+        long long it = 0;
+        unsigned w = 0;
+        while ((w = ld_acquire_u32(release)) < 2u * gen) {
+            if (++it > limit) { atomicOr(err, SWR_ERR_TIMEOUT); s_ok = 0; break; }
+            if ((it & 255) == 0 && *(volatile int*)err) { s_ok = 0; break; }
+            __nanosleep(20);
+        }
+        s_go = (int)(w & 1u);
+        __threadfence();
+    }
+    __syncthreads();
+    *go_out = s_go;
+    return s_ok != 0 && *(volatile int*)err == 0;
+}
+
+// The same, reducing two partial arrays (part_a -> sums_a, part_b -> sums_b).
+__device__ bool reduce_barrier2(unsigned* count, unsigned* release, unsigned target, unsigned gen,
+                                const double* part_a, const double* part_b, const int* inst_task0, int n_inst,
+                                double* sums_a, double* sums_b, int* err, long long limit, double* red,
+                                const int* nact, int* go_out) {
+    __shared__ int s_last, s_ok, s_go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned old = atomicAdd(count, 1u);
+        s_last = (old == target - 1);
+        s_ok = 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (n_inst < 8) {
+            for (int i = 0; i < n_inst; ++i) {
+                double xa = 0, xb = 0;
+                for (int u = inst_task0[i] + threadIdx.x; u < inst_task0[i + 1]; u += WIN_THREADS) {
+                    xa += __ldcg(part_a + u);
+                    xb += __ldcg(part_b + u);
+                }
+                xa = wblock_sum(xa, red);
+                xb = wblock_sum(xb, red);
+                if (threadIdx.x == 0) {
+                    sums_a[i] = xa;
+                    sums_b[i] = xb;
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < n_inst; i += WIN_THREADS) {
+                double xa = 0, xb = 0;
+                for (int u = inst_task0[i]; u < inst_task0[i + 1]; ++u) {
+                    xa += __ldcg(part_a + u);
+                    xb += __ldcg(part_b + u);
+                }
+                sums_a[i] = xa;
+                sums_b[i] = xb;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int go = nact ? (__ldcg(nact) > 0) : 1;
+            s_go = go;
+            __threadfence();
+            st_release_u32(release, 2u * gen + (unsigned)go);
+        }
+    } else if (threadIdx.x == 0) {
+        long long it = 0;
+        unsigned w = 0;
+        while ((w = ld_acquire_u32(release)) < 2u * gen) {
+            if (++it > limit) { atomicOr(err, SWR_ERR_TIMEOUT); s_ok = 0; break; }
+            if ((it & 255) == 0 && *(volatile int*)err) { s_ok = 0; break; }
+            __nanosleep(20);
+        }
+        s_go = (int)(w & 1u);
+        __threadfence();
+    }
+    __syncthreads();
+    *go_out = s_go;
+    return s_ok != 0 && *(volatile int*)err == 0;
+}
+
 __device__ inline void two_sum(float a, float b, float& s, float& e) {
     s = a + b;
     float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
 
-// rows [r0, r1) of z = (Pp1 (x) Pp2) y  (N = 2) or Pp1 y (N = 1); y in shared memory
-__device__ void z_rows(const SwrDeviceView& v, const SubDev& s, const double* ys, int r0, int r1, double* z,
-                       double* tmp) {
-    const int kd = s.kd;
-    T1Layout lay(s.q, kd);
-    const double* P1 = v.arena + s.t1[0] + lay.mat(M_PP);
-    if (s.N == 1) {
-        for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+struct TaskCache {
+    int inst, r0, nr, K, kd, N, t0, first, fixed, maxs, ngf_stop, normalize;
+    long long hist, bvec, Gm, Gf, Wf, c0;
+    double kdt, ngf_tol;
+};
+
+// rows [r0, r0+nr) of z = (P1 (x) P2) y (N = 2) or P1 y (N = 1); P and y in
+// shared memory.  Warp-parallel dot products (lanes over the contraction,
+// shuffle reduction) keep the FP64 dependency chains short.
+__device__ void z_rows_sm(const TaskCache& tc, const double* P1, const double* P2, const double* ys, double* z,
+                          double* tmp) {
+    const int kd = tc.kd, r0 = tc.r0, r1 = tc.r0 + tc.nr;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = WIN_THREADS / 32;
+    if (tc.N == 1) {
+        for (int r = r0 + warp; r < r1; r += nw) {
             double acc = 0;
-            for (int c = 0; c < kd; ++c) acc += P1[r * kd + c] * ys[c];
-            z[r - r0] = acc;
+            for (int c = lane; c < kd; c += 32) acc += P1[r * kd + c] * ys[c];
+            acc = warp_sum(acc);
+            if (lane == 0) z[r - r0] = acc;
         }
         __syncthreads();
         return;
     }
-    const double* P2 = v.arena + s.t1[1] + lay.mat(M_PP);
-    const int b0 = r0 / kd, b1 = (r1 - 1) / kd;
-    for (int b = b0; b <= b1; ++b) {
-        for (int c = threadIdx.x; c < kd; c += blockDim.x) {
-            double acc = 0;
-            for (int e = 0; e < kd; ++e) acc += ys[c + kd * e] * P2[b * kd + e];
-            tmp[c] = acc;
-        }
-        __syncthreads();
-        int lo = max(r0, b * kd), hi = min(r1, (b + 1) * kd);
-        for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
-            int a = r - b * kd;
-            double acc = 0;
-            for (int c = 0; c < kd; ++c) acc += P1[a * kd + c] * tmp[c];
-            z[r - r0] = acc;
-        }
-        __syncthreads();
+    const int b0 = r0 / kd, b1 = (r1 - 1) / kd, nb = b1 - b0 + 1;
+    // tmp[bb][c] = sum_e Y[c][e] P2[b0+bb][e]   (kd <= 32: one lane per e)
+    for (int item = warp; item < nb * kd; item += nw) {
+        const int bb = item / kd, c = item % kd;
+        double x = (lane < kd) ? ys[c + kd * lane] * P2[(b0 + bb) * kd + lane] : 0.0;
+        x = warp_sum(x);
+        if (lane == 0) tmp[bb * kd + c] = x;
     }
+    __syncthreads();
+    for (int r = r0 + warp; r < r1; r += nw) {
+        const int b = r / kd, a = r - b * kd;
+        double x = (lane < kd) ? P1[a * kd + lane] * tmp[(b - b0) * kd + lane] : 0.0;
+        x = warp_sum(x);
+        if (lane == 0) z[r - r0] = x;
+    }
+    __syncthreads();
 }
 
-// Dynamic shared memory: vs[Kmax] doubles, vf[Kmax] float2 (mixed only), tmp[kdmax].
-template <bool DF32>
-__global__ void __launch_bounds__(WIN_THREADS, 2) k_window(SweepArgs A) {
+// FP64 window: two phases and two reduce-barriers per step (see the top of
+// the file).  Dynamic shared memory (doubles):
+//   vs[kmax] | (unused)[kmax] | tmp[WIN_RB + 2 kdmax] | P[tasks_per_cta][2][kdmax^2]
+__global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fp64(SweepArgs A) {
     extern __shared__ double sm[];
     __shared__ double red[33];
-    __shared__ int s_nact;
+    __shared__ TaskCache tcs[WIN_TPC];
+    __shared__ double own[WIN_TPC][4][WIN_RB];
+    __shared__ double s_prev[WIN_TPC];
+    __shared__ int alive[WIN_TPC];
+    __shared__ double s_sc[2];  // 1/s_n, 1/s_{n-1}
+    int go = 1;
     const SwrDeviceView& v = A.v;
     const int t_begin = blockIdx.x * A.tasks_per_cta;
-    const int t_end = min(A.n_tasks, t_begin + A.tasks_per_cta);
+    const int ntk = min(A.n_tasks - t_begin, A.tasks_per_cta);
     const int cap = A.cap;
+    const int kmax = A.kmax, kdmax = A.kdmax;
     double* vs = sm;
-    float2* vf = (float2*)(sm + A.kmax);
-    double* tmp = sm + 2 * A.kmax;
+    double* tmp = sm + 2 * kmax;
+    double* Psm = tmp + WIN_RB + 2 * kdmax;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = WIN_THREADS / 32;
-    unsigned target = 0;
-    // ---------------------------------------------------------------- step 0
-    for (int t = t_begin; t < t_end; ++t) {
+    unsigned target = 0, gen = 0;
+
+    // ------------------------------------------------------- set-up + step 0
+    for (int j = 0; j < ntk; ++j) {
+        const int t = t_begin + j;
         const Task tk = A.tasks[t];
         const SubDev& s = v.sub[tk.sid];
-        const int K = s.K, nr = tk.r1 - tk.r0;
-        const double* c0 = v.arena + s.c0;
+        const InstDev& in = v.inst[tk.inst];
+        if (tid == 0) {
+            TaskCache c;
+            c.inst = tk.inst;
+            c.r0 = tk.r0;
+            c.nr = tk.r1 - tk.r0;
+            c.K = s.K;
+            c.kd = s.kd;
+            c.N = s.N;
+            c.t0 = A.inst_task0[tk.inst];
+            c.first = (t == c.t0);
+            c.fixed = in.window_cap;
+            c.maxs = in.window_cap > 0 ? in.window_cap : in.max_steps;
+            c.ngf_stop = (in.window_cap == 0 && in.ngf_tol > 0.0);
+            c.normalize = in.normalize;
+            c.hist = s.hist;
+            c.bvec = s.bvec;
+            c.Gm = s.Gm;
+            c.Gf = s.Gf;
+            c.c0 = s.c0;
+            c.kdt = in.kappa * in.dt;
+            c.ngf_tol = in.ngf_tol;
+            tcs[j] = c;
+            alive[j] = 1;
+            s_prev[j] = 1.0;
+        }
+        __syncthreads();
+        const TaskCache& tc = tcs[j];
+        const int kd = tc.kd, K = tc.K, nr = tc.nr;
+        T1Layout lay(s.q, kd);
+        double* P1 = Psm + (long long)j * 2 * kdmax * kdmax;
+        double* P2 = P1 + (long long)kdmax * kdmax;
+        const double* P1g = v.arena + s.t1[0] + lay.mat(M_PP);
+        const double* P2g = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_PP);
+        for (int e = tid; e < kd * kd; e += WIN_THREADS) {
+            P1[e] = P1g[e];
+            P2[e] = P2g[e];
+        }
+        const double* c0 = v.arena + tc.c0;
         for (int c = tid; c < K; c += WIN_THREADS) vs[c] = c0[c];
         __syncthreads();
-        double* own = A.own + tk.own;  // [4][nr]: y slot 0/1, z slot 0/1
-        double* h0 = v.arena + s.hist;
-        for (int r = tk.r0 + tid; r < tk.r1; r += WIN_THREADS) {
-            h0[r] = vs[r];
-            own[r - tk.r0] = vs[r];  // y^0 in slot 0
+        double* h0 = v.arena + tc.hist;
+        for (int r = tid; r < nr; r += WIN_THREADS) {
+            h0[tc.r0 + r] = vs[tc.r0 + r];
+            own[j][0][r] = vs[tc.r0 + r];  // y^0 in slot 0
         }
-        z_rows(v, s, vs, tk.r0, tk.r1, own + 2 * nr, tmp);  // z^0 in slot 0
+        z_rows_sm(tc, P1, P2, vs, own[j][2], tmp);  // z^0 in slot 0
         double acc = 0;
-        for (int r = tid; r < nr; r += WIN_THREADS) acc += own[r] * own[2 * nr + r];
+        for (int r = tid; r < nr; r += WIN_THREADS) acc += own[j][0][r] * own[j][2][r];
         acc = wblock_sum(acc, red);
-        if (tid == 0) {
-            A.part_s[t] = acc;
-            A.alive[t] = 1;
-            A.s_prev[t] = 1.0;
-        }
+        if (tid == 0) A.part_s[t] = acc;
     }
     target += gridDim.x;
-    if (!grid_barrier_mono(&A.bar->count, target, v.err, A.spin_limit)) return;
+    ++gen;
+    if (!reduce_barrier(&A.bar->count, &A.bar->gen, target, gen, true, A.part_s, A.inst_task0, v.n_inst,
+                        A.sums_s, v.err, A.spin_limit, red, nullptr, &go))
+        return;
 
     for (int n = 0;; ++n) {
-        if (tid == 0) s_nact = __ldcg(A.n_active);
-        __syncthreads();
-        if (s_nact == 0) return;  // stable here: instances close only in phase B
         // ------------------------------------------------------ phase A(n+1)
-        for (int t = t_begin; t < t_end; ++t) {
-            if (!A.alive[t]) continue;  // written by this CTA only
-            const Task tk = A.tasks[t];
-            const SubDev& s = v.sub[tk.sid];
-            const InstDev& in = v.inst[tk.inst];
-            const int K = s.K, nr = tk.r1 - tk.r0;
-            const int t0 = A.inst_task0[tk.inst], t1 = A.inst_task0[tk.inst + 1];
-            const int fixed = in.window_cap, maxs = fixed > 0 ? fixed : in.max_steps;
-            const bool ngf_stop = fixed == 0 && in.ngf_tol > 0.0;
-            // issue the independent loads together: partials of s_n, y^n, b'^{n+1}
-            double ps = 0;
-            if (in.normalize)
-                for (int u = t0 + tid; u < t1; u += WIN_THREADS) ps += __ldcg(A.part_s + (n & 1) * A.n_tasks + u);
-            const double* yn = v.arena + s.hist + (long long)n * K;
-            const int wp = A.win_prev[tk.inst];
-            const double* bsrc = (wp > 0) ? v.arena + s.bvec + (long long)min(n + 1, wp) * K : nullptr;
-            double bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                int c = tid + i * WIN_THREADS;
-                double yv = 0, bb = 0;
-                if (c < K) {
-                    yv = yn[c];
-                    if (bsrc) bb = bsrc[c];
-                }
-                if (c < K) vs[c] = yv;
-                bv[i] = bb;
-            }
-            const double s_n = in.normalize ? sqrt(wblock_sum(ps, red)) : 1.0;
-            const double sp = A.s_prev[t];  // s_{n-1}
+        for (int j = 0; j < ntk; ++j) {
             __syncthreads();
-            if (tid == 0) {
-                A.s_prev[t] = s_n;
-                if (t == t0) A.snorm[(long long)tk.inst * (cap + 1) + n] = s_n;
+            if (!alive[j]) continue;
+            const TaskCache& tc = tcs[j];
+            const int K = tc.K, nr = tc.nr;
+            const int t = t_begin + j;
+            // one round trip: s_n^2, y^n, b'^{n+1}
+            const double s2 = tc.normalize ? __ldcg(A.sums_s + tc.inst) : 1.0;
+            const double* yn = v.arena + tc.hist + (long long)n * K;
+            const int wp = A.win_prev[tc.inst];
+            const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(n + 1, wp) * K : nullptr;
+            double yv[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int c = tid + i * WIN_THREADS;
+                yv[i] = (c < K) ? yn[c] : 0.0;
+                bv[i] = (c < K && bsrc) ? bsrc[c] : 0.0;
             }
-            if (n >= maxs || !isfinite(s_n) || s_n <= 0.0) continue;  // closed in phase B
-            const double kdt = in.kappa * in.dt;
+            // one thread takes the square root and the reciprocals (FP64 division
+            // and square root are slow sequences on this part)
+            if (tid == 0) {
+                const double s_n = tc.normalize ? sqrt(s2) : 1.0;
+                s_sc[0] = 1.0 / s_n;
+                s_sc[1] = 1.0 / s_prev[j];
+                s_prev[j] = s_n;
+                if (tc.first) A.snorm[(long long)tc.inst * (cap + 1) + n] = s_n;
+            }
+            __syncthreads();
+            const double s_n = s_prev[j];
+            const double is_n = s_sc[0], is_p = s_sc[1];
+            if (n >= tc.maxs || !isfinite(s_n) || s_n <= 0.0) continue;  // closed in phase B
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 int c = tid + i * WIN_THREADS;
                 if (c < K) {
-                    double val = vs[c] / s_n + kdt * bv[i];
+                    double val = yv[i] * is_n + tc.kdt * bv[i];
                     vs[c] = val;
-                    if (DF32) {
-                        float h = (float)val;
-                        vf[c] = make_float2(h, (float)(val - (double)h));
-                    }
                 }
             }
-            double* own = A.own + tk.own;
             // partial of delta_n^2 = || y^n/s_n - y^{n-1}/s_{n-1} ||^2_chi over own rows
-            if (n >= 1 && ngf_stop) {
-                const double* y_n = own + (n & 1) * nr;
-                const double* y_p = own + ((n - 1) & 1) * nr;
-                const double* z_n = own + (2 + (n & 1)) * nr;
-                const double* z_p = own + (2 + ((n - 1) & 1)) * nr;
+            if (n >= 1 && tc.ngf_stop) {
+                const double* y_n = own[j][n & 1];
+                const double* y_p = own[j][(n - 1) & 1];
+                const double* z_n = own[j][2 + (n & 1)];
+                const double* z_p = own[j][2 + ((n - 1) & 1)];
                 double acc = 0;
                 for (int r = tid; r < nr; r += WIN_THREADS)
-                    acc += (y_n[r] / s_n - y_p[r] / sp) * (z_n[r] / s_n - z_p[r] / sp);
+                    acc += (y_n[r] * is_n - y_p[r] * is_p) * (z_n[r] * is_n - z_p[r] * is_p);
                 acc = wblock_sum(acc, red);
-                if (tid == 0) A.part_d[(n & 1) * A.n_tasks + t] = acc;
+                if (tid == 0) A.part_d[t] = acc;
             } else {
                 __syncthreads();
             }
             // rows of y^{n+1} = G v
-            double* ynew = v.arena + s.hist + (long long)(n + 1) * K;
-            double* yslot = own + ((n + 1) & 1) * nr;
-            if (DF32) {
-                const float* Gh = (const float*)(v.arena + s.Gf);
-                const float* Gl = Gh + (long long)K * K;
-                for (int r = tk.r0 + warp; r < tk.r1; r += nw) {
-                    const float* gh = Gh + (long long)r * K;
-                    const float* gl = Gl + (long long)r * K;
-                    float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f;
-                    int c = lane;
-                    for (; c + 32 < K; c += 64) {
-                        float h0 = gh[c], l0 = gl[c], h1 = gh[c + 32], l1 = gl[c + 32];
-                        float2 v0 = vf[c], v1 = vf[c + 32];
-                        float p0 = h0 * v0.x, e0 = fmaf(h0, v0.x, -p0);
-                        float p1 = h1 * v1.x, e1 = fmaf(h1, v1.x, -p1);
-                        float s0, q0, s1, q1;
-                        two_sum(ah0, p0, s0, q0);
-                        two_sum(ah1, p1, s1, q1);
-                        ah0 = s0;
-                        ah1 = s1;
-                        al0 += (q0 + e0) + fmaf(h0, v0.y, l0 * v0.x);
-                        al1 += (q1 + e1) + fmaf(h1, v1.y, l1 * v1.x);
-                    }
-                    if (c < K) {
-                        float h0 = gh[c], l0 = gl[c];
-                        float2 v0 = vf[c];
-                        float p0 = h0 * v0.x, e0 = fmaf(h0, v0.x, -p0);
-                        float s0, q0;
-                        two_sum(ah0, p0, s0, q0);
-                        ah0 = s0;
-                        al0 += (q0 + e0) + fmaf(h0, v0.y, l0 * v0.x);
-                    }
-                    float sh, eh;
-                    two_sum(ah0, ah1, sh, eh);
-                    float ah = sh, al = al0 + al1 + eh;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        float oh = __shfl_xor_sync(0xffffffffu, ah, o);
-                        float ol = __shfl_xor_sync(0xffffffffu, al, o);
-                        two_sum(ah, oh, sh, eh);
-                        ah = sh;
-                        al = al + ol + eh;
-                    }
-                    if (lane == 0) {
-                        double y = (double)ah + (double)al;
-                        ynew[r] = y;
-                        yslot[r - tk.r0] = y;
-                    }
-                }
-            } else {
-                const double* G = v.arena + s.Gm;
-                for (int r = tk.r0 + warp; r < tk.r1; r += nw) {
+            double* ynew = v.arena + tc.hist + (long long)(n + 1) * K;
+            double* yslot = own[j][(n + 1) & 1];
+            {
+                const double* G = v.arena + tc.Gm;
+                for (int r = tc.r0 + warp; r < tc.r0 + nr; r += nw) {
                     const double* g = G + (long long)r * K;
                     double a0 = 0, a1 = 0;
                     int c = lane;
@@ -292,68 +389,73 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window(SweepArgs A) {
                     double y = warp_sum(a0 + a1);
                     if (lane == 0) {
                         ynew[r] = y;
-                        yslot[r - tk.r0] = y;
+                        yslot[r - tc.r0] = y;
                     }
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
         target += gridDim.x;
-        if (!grid_barrier_mono(&A.bar->count, target, v.err, A.spin_limit)) return;
+        ++gen;
+        if (!reduce_barrier(&A.bar->count, &A.bar->gen, target, gen, A.any_ngf_stop && n >= 1, A.part_d,
+                            A.inst_task0, v.n_inst, A.sums_d, v.err, A.spin_limit, red, nullptr, &go))
+            return;
         // ------------------------------------------------------ phase B(n+1)
-        for (int t = t_begin; t < t_end; ++t) {
-            if (!A.alive[t]) continue;
-            const Task tk = A.tasks[t];
-            const SubDev& s = v.sub[tk.sid];
-            const InstDev& in = v.inst[tk.inst];
-            const int K = s.K, nr = tk.r1 - tk.r0;
-            const int t0 = A.inst_task0[tk.inst], t1 = A.inst_task0[tk.inst + 1];
-            const int fixed = in.window_cap, maxs = fixed > 0 ? fixed : in.max_steps;
-            const bool ngf_stop = fixed == 0 && in.ngf_tol > 0.0;
-            const double s_n = A.s_prev[t];
-            double pd = 0;
-            if (n >= 1 && ngf_stop)
-                for (int u = t0 + tid; u < t1; u += WIN_THREADS) pd += __ldcg(A.part_d + (n & 1) * A.n_tasks + u);
-            const double* yn1 = v.arena + s.hist + (long long)(n + 1) * K;
-            bool early = (n >= maxs) || !isfinite(s_n) || s_n <= 0.0;
-            if (!early)
+        for (int j = 0; j < ntk; ++j) {
+            __syncthreads();
+            if (!alive[j]) continue;
+            const TaskCache& tc = tcs[j];
+            const int K = tc.K, nr = tc.nr;
+            const int t = t_begin + j;
+            const double s_n = s_prev[j];
+            bool stop = (n >= tc.maxs) || !isfinite(s_n) || s_n <= 0.0;
+            double d2 = 0;
+            const double* yn1 = v.arena + tc.hist + (long long)(n + 1) * K;
+            if (!stop) {
+                if (n >= 1 && tc.ngf_stop) d2 = __ldcg(A.sums_d + tc.inst);
                 for (int c = tid; c < K; c += WIN_THREADS) vs[c] = yn1[c];
-            bool stop = early;
-            if (!stop && n >= 1 && ngf_stop) {
-                double d2 = wblock_sum(pd, red);
-                stop = sqrt(fmax(d2, 0.0)) <= in.ngf_tol;
+                if (n >= 1 && tc.ngf_stop) stop = sqrt(fmax(d2, 0.0)) <= tc.ngf_tol;
             }
             if (stop) {
+                __syncthreads();
                 if (tid == 0) {
-                    A.alive[t] = 0;
-                    if (t == t0) {
-                        A.win[tk.inst] = n;
+                    alive[j] = 0;
+                    if (tc.first) {
+                        A.win[tc.inst] = n;
                         if (!isfinite(s_n) || s_n <= 0.0) atomicOr(v.err, SWR_ERR_NUMERIC);
                         __threadfence();
                         atomicSub(A.n_active, 1);
                     }
                 }
-                __syncthreads();
                 continue;
             }
             __syncthreads();
-            double* own = A.own + tk.own;
-            double* zslot = own + (2 + ((n + 1) & 1)) * nr;
-            z_rows(v, s, vs, tk.r0, tk.r1, zslot, tmp);
-            const double* yslot = own + ((n + 1) & 1) * nr;
+            double* P1 = Psm + (long long)j * 2 * kdmax * kdmax;
+            double* P2 = P1 + (long long)kdmax * kdmax;
+            double* zslot = own[j][2 + ((n + 1) & 1)];
+            z_rows_sm(tc, P1, P2, vs, zslot, tmp);
+            const double* yslot = own[j][(n + 1) & 1];
             double acc = 0;
             for (int r = tid; r < nr; r += WIN_THREADS) acc += yslot[r] * zslot[r];
             acc = wblock_sum(acc, red);
-            if (tid == 0) A.part_s[((n + 1) & 1) * A.n_tasks + t] = acc;
+            if (tid == 0) A.part_s[t] = acc;
         }
+        __syncthreads();
         target += gridDim.x;
-        if (!grid_barrier_mono(&A.bar->count, target, v.err, A.spin_limit)) return;
+        ++gen;
+        // the last CTA to arrive reads the active count after every decrement of
+        // this phase and hands the verdict to all CTAs with the release
+        if (!reduce_barrier(&A.bar->count, &A.bar->gen, target, gen, true, A.part_s, A.inst_task0, v.n_inst,
+                            A.sums_s, v.err, A.spin_limit, red, A.n_active, &go))
+            return;
+        if (!go) return;
     }
 }
 
 __global__ void k_window_reset(SweepArgs A, int n_inst) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.bar->count = 0;
+        A.bar->gen = 0;
         *A.n_active = n_inst;
     }
 }
@@ -374,16 +476,339 @@ __global__ void k_split_df32(SwrDeviceView v) {
     }
 }
 
+// ---------------------------------------------------- double-single window
+//
+// Mixed precision, ONE reduce-barrier per step.  z^{n+1} = (Pp (x) Pp) y^{n+1}
+// is obtained as W v with W = (Pp (x) Pp) G precomputed at assembly, so the
+// CTA that computes its rows of y^{n+1} = G v also has its rows of z^{n+1}
+// and the partial of s_{n+1}^2 without waiting for the full y^{n+1}.  Phase
+// P(n): decisions from the sums reduced at the last barrier (s_n^2 and
+// D_{n-1} = ||c^{n-1} - c^{n-2}||^2 ... see below), v = y^n/s_n + kappa dt b',
+// partial of D_n = ||c^n - c^{n-1}||^2 from the CTA's own rows, fused
+// double-single pass over the rows of G and W, partial of s_{n+1}^2.  The
+// barrier after P(n) reduces both partial arrays.  D_n is therefore known at
+// P(n+1): when D_n <= tol^2 the window ends at n (the step n+1 already
+// computed is dropped), which reproduces the stop of the plain algorithm.
+// Dynamic shared memory: vs[kmax] doubles | vf[kmax] float2 | tmp[WIN_RB + 2 kdmax]
+// doubles | P[tasks_per_cta][2][kdmax^2] doubles | G_hi rows (floats, when resident).
+__global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    __shared__ TaskCache tcs[WIN_TPC];
+    __shared__ double own[WIN_TPC][4][WIN_RB];
+    __shared__ double s_prev[WIN_TPC];
+    __shared__ int alive[WIN_TPC];
+    __shared__ double s_sc[2];
+    __shared__ int s_stop;
+    int go = 1;
+    const SwrDeviceView& v = A.v;
+    const int t_begin = blockIdx.x * A.tasks_per_cta;
+    const int ntk = min(A.n_tasks - t_begin, A.tasks_per_cta);
+    const int cap = A.cap;
+    const int kmax = A.kmax, kdmax = A.kdmax;
+    double* vs = sm;
+    float2* vf = (float2*)(sm + kmax);
+    double* tmp = sm + 2 * kmax;
+    double* Psm = tmp + WIN_RB + 2 * kdmax;
+    float* Gsm = (float*)(Psm + (long long)A.tasks_per_cta * 2 * kdmax * kdmax);
+    const bool gres = A.g_resident != 0;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = WIN_THREADS / 32;
+    unsigned target = 0, gen = 0;
+
+    // ------------------------------------------------------- set-up + step 0
+    for (int j = 0; j < ntk; ++j) {
+        const int t = t_begin + j;
+        const Task tk = A.tasks[t];
+        const SubDev& s = v.sub[tk.sid];
+        const InstDev& in = v.inst[tk.inst];
+        if (tid == 0) {
+            TaskCache c;
+            c.inst = tk.inst;
+            c.r0 = tk.r0;
+            c.nr = tk.r1 - tk.r0;
+            c.K = s.K;
+            c.kd = s.kd;
+            c.N = s.N;
+            c.t0 = A.inst_task0[tk.inst];
+            c.first = (t == c.t0);
+            c.fixed = in.window_cap;
+            c.maxs = in.window_cap > 0 ? in.window_cap : in.max_steps;
+            c.ngf_stop = (in.window_cap == 0 && in.ngf_tol > 0.0);
+            c.normalize = in.normalize;
+            c.hist = s.hist;
+            c.bvec = s.bvec;
+            c.Gm = s.Gm;
+            c.Gf = s.Gf;
+            c.Wf = s.Wf;
+            c.c0 = s.c0;
+            c.kdt = in.kappa * in.dt;
+            c.ngf_tol = in.ngf_tol;
+            tcs[j] = c;
+            alive[j] = 1;
+            s_prev[j] = 1.0;
+        }
+        __syncthreads();
+        const TaskCache& tc = tcs[j];
+        const int kd = tc.kd, K = tc.K, nr = tc.nr;
+        T1Layout lay(s.q, kd);
+        double* P1 = Psm + (long long)j * 2 * kdmax * kdmax;
+        double* P2 = P1 + (long long)kdmax * kdmax;
+        const double* P1g = v.arena + s.t1[0] + lay.mat(M_PP);
+        const double* P2g = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_PP);
+        for (int e = tid; e < kd * kd; e += WIN_THREADS) {
+            P1[e] = P1g[e];
+            P2[e] = P2g[e];
+        }
+        if (gres) {
+            const float* Gh = (const float*)(v.arena + tc.Gf);
+            for (long long e = tid; e < (long long)nr * K; e += WIN_THREADS) Gsm[e] = Gh[(long long)tc.r0 * K + e];
+        }
+        const double* c0 = v.arena + tc.c0;
+        for (int c = tid; c < K; c += WIN_THREADS) vs[c] = c0[c];
+        __syncthreads();
+        double* h0 = v.arena + tc.hist;
+        for (int r = tid; r < nr; r += WIN_THREADS) {
+            h0[tc.r0 + r] = vs[tc.r0 + r];
+            own[j][0][r] = vs[tc.r0 + r];  // y^0 in slot 0
+        }
+        z_rows_sm(tc, P1, P2, vs, own[j][2], tmp);  // z^0 in slot 0
+        double acc = 0;
+        for (int r = tid; r < nr; r += WIN_THREADS) acc += own[j][0][r] * own[j][2][r];
+        acc = wblock_sum(acc, red);
+        if (tid == 0) {
+            A.part_s[t] = acc;
+            A.part_d[t] = 0.0;
+        }
+    }
+    target += gridDim.x;
+    ++gen;
+    if (!reduce_barrier2(&A.bar->count, &A.bar->gen, target, gen, A.part_s, A.part_d, A.inst_task0, v.n_inst,
+                         A.sums_s, A.sums_d, v.err, A.spin_limit, red, nullptr, &go))
+        return;
+
+    for (int n = 0;; ++n) {
+        for (int j = 0; j < ntk; ++j) {
+            __syncthreads();
+            if (!alive[j]) continue;
+            const TaskCache& tc = tcs[j];
+            const int K = tc.K, nr = tc.nr;
+            const int t = t_begin + j;
+            // one round trip: s_n^2, D_{n-1}, y^n, b'^{n+1}
+            const double s2 = tc.normalize ? __ldcg(A.sums_s + tc.inst) : 1.0;
+            const double d2 = (n >= 2 && tc.ngf_stop) ? __ldcg(A.sums_d + tc.inst) : 1.0e300;
+            const double* yn = v.arena + tc.hist + (long long)n * K;
+            const int wp = A.win_prev[tc.inst];
+            const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(n + 1, wp) * K : nullptr;
+            double yv[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int c = tid + i * WIN_THREADS;
+                yv[i] = (c < K) ? yn[c] : 0.0;
+                bv[i] = (c < K && bsrc) ? bsrc[c] : 0.0;
+            }
+            if (tid == 0) {
+                const double s_n = tc.normalize ? sqrt(s2) : 1.0;
+                int stop = 0, w = n;
+                if (n >= 2 && tc.ngf_stop && sqrt(fmax(d2, 0.0)) <= tc.ngf_tol) {
+                    stop = 1;
+                    w = n - 1;
+                } else if (n >= tc.maxs || !isfinite(s_n) || s_n <= 0.0) {
+                    stop = 1;
+                    w = n;
+                }
+                if (tc.first) A.snorm[(long long)tc.inst * (cap + 1) + n] = s_n;
+                if (stop) {
+                    alive[j] = 0;
+                    if (tc.first) {
+                        A.win[tc.inst] = w;
+                        if (!isfinite(s_n) || s_n <= 0.0) atomicOr(v.err, SWR_ERR_NUMERIC);
+                        __threadfence();
+                        atomicSub(A.n_active, 1);
+                    }
+                } else {
+                    s_sc[0] = 1.0 / s_n;
+                    s_sc[1] = 1.0 / s_prev[j];
+                    s_prev[j] = s_n;
+                }
+                s_stop = stop;
+            }
+            __syncthreads();
+            if (s_stop) continue;
+            const double is_n = s_sc[0], is_p = s_sc[1];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int c = tid + i * WIN_THREADS;
+                if (c < K) {
+                    double val = yv[i] * is_n + tc.kdt * bv[i];
+                    vs[c] = val;
+                    float h = (float)val;
+                    vf[c] = make_float2(h, (float)(val - (double)h));
+                }
+            }
+            // partial of D_n = || y^n/s_n - y^{n-1}/s_{n-1} ||^2_chi over own rows
+            if (n >= 1 && tc.ngf_stop) {
+                const double* y_n = own[j][n & 1];
+                const double* y_p = own[j][(n - 1) & 1];
+                const double* z_n = own[j][2 + (n & 1)];
+                const double* z_p = own[j][2 + ((n - 1) & 1)];
+                double acc = 0;
+                for (int r = tid; r < nr; r += WIN_THREADS)
+                    acc += (y_n[r] * is_n - y_p[r] * is_p) * (z_n[r] * is_n - z_p[r] * is_p);
+                acc = wblock_sum(acc, red);
+                if (tid == 0) A.part_d[t] = acc;
+            } else {
+                __syncthreads();
+            }
+            // fused double-single rows of y^{n+1} = G v and z^{n+1} = W v
+            double* ynew = v.arena + tc.hist + (long long)(n + 1) * K;
+            double* yslot = own[j][(n + 1) & 1];
+            double* zslot = own[j][2 + ((n + 1) & 1)];
+            const float* Ghg = (const float*)(v.arena + tc.Gf);
+            const float* Gl = Ghg + (long long)K * K;
+            const float* Wh = (const float*)(v.arena + tc.Wf);
+            const float* Wl = Wh + (long long)K * K;
+            for (int r = tc.r0 + warp; r < tc.r0 + nr; r += nw) {
+                const float* gh = gres ? Gsm + (long long)(r - tc.r0) * K : Ghg + (long long)r * K;
+                const float* gl = Gl + (long long)r * K;
+                const float* wh = Wh + (long long)r * K;
+                const float* wl = Wl + (long long)r * K;
+                float yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
+                for (int c = lane; c < K; c += 32) {
+                    const float2 x = vf[c];
+                    const float g0 = gh[c], g1 = gl[c], w0 = wh[c], w1 = wl[c];
+                    float p = g0 * x.x, e = fmaf(g0, x.x, -p), sh, q;
+                    two_sum(yh, p, sh, q);
+                    yh = sh;
+                    yl += (q + e) + fmaf(g0, x.y, g1 * x.x);
+                    p = w0 * x.x;
+                    e = fmaf(w0, x.x, -p);
+                    two_sum(zh, p, sh, q);
+                    zh = sh;
+                    zl += (q + e) + fmaf(w0, x.y, w1 * x.x);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    float sh, eh;
+                    float oh = __shfl_xor_sync(0xffffffffu, yh, o), ol = __shfl_xor_sync(0xffffffffu, yl, o);
+                    two_sum(yh, oh, sh, eh);
+                    yh = sh;
+                    yl = yl + ol + eh;
+                    oh = __shfl_xor_sync(0xffffffffu, zh, o);
+                    ol = __shfl_xor_sync(0xffffffffu, zl, o);
+                    two_sum(zh, oh, sh, eh);
+                    zh = sh;
+                    zl = zl + ol + eh;
+                }
+                if (lane == 0) {
+                    const double y = (double)yh + (double)yl;
+                    ynew[r] = y;
+                    yslot[r - tc.r0] = y;
+                    zslot[r - tc.r0] = (double)zh + (double)zl;
+                }
+            }
+            __syncthreads();
+            double acc = 0;
+            for (int r = tid; r < nr; r += WIN_THREADS) acc += yslot[r] * zslot[r];
+            acc = wblock_sum(acc, red);
+            if (tid == 0) A.part_s[t] = acc;
+        }
+        __syncthreads();
+        target += gridDim.x;
+        ++gen;
+        if (!reduce_barrier2(&A.bar->count, &A.bar->gen, target, gen, A.part_s, A.part_d, A.inst_task0, v.n_inst,
+                             A.sums_s, A.sums_d, v.err, A.spin_limit, red, A.n_active, &go))
+            return;
+        if (!go) return;
+    }
+}
+
+__global__ void k_window_reset(SweepArgs A, int n_inst) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.bar->count = 0;
+        A.bar->gen = 0;
+        *A.n_active = n_inst;
+    }
+}
+
+// Split of the FP64 step-matrix inverse into FP32 pairs (mixed precision).
+__global__ void k_split_df32(SwrDeviceView v) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const long long KK = (long long)s.K * s.K;
+    const double* G = v.arena + s.Gm;
+    float* Gh = (float*)(v.arena + s.Gf);
+    float* Gl = Gh + KK;
+    for (long long e = threadIdx.x + (long long)blockIdx.x * blockDim.x; e < KK; e += (long long)blockDim.x * gridDim.x) {
+        double g = G[e];
+        float h = (float)g;
+        Gh[e] = h;
+        Gl[e] = (float)(g - (double)h);
+    }
+}
+
+// W = (Pp1 (x) Pp2) G (N = 2) or Pp1 G (N = 1), column by column in FP64, stored
+// as FP32 pairs.  Column j of G reshaped Y[c][e] = G[c + kd e][j]:
+// W[(a,b), j] = sum_{c,e} P1[a][c] Y[c][e] P2[b][e].
+__global__ void k_make_w(SwrDeviceView v) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const int K = s.K, kd = s.kd;
+    T1Layout lay(s.q, kd);
+    const double* P1 = v.arena + s.t1[0] + lay.mat(M_PP);
+    const double* P2 = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_PP);
+    const double* G = v.arena + s.Gm;
+    float* Wh = (float*)(v.arena + s.Wf);
+    float* Wl = Wh + (long long)K * K;
+    extern __shared__ double sw[];
+    double* Y = sw;            // K
+    double* T = sw + K;        // kd * kd (N = 2)
+    for (int j = blockIdx.x; j < K; j += gridDim.x) {
+        for (int r = threadIdx.x; r < K; r += blockDim.x) Y[r] = G[(long long)r * K + j];
+        __syncthreads();
+        if (s.N == 1) {
+            for (int a = threadIdx.x; a < K; a += blockDim.x) {
+                double acc = 0;
+                for (int c = 0; c < K; ++c) acc += P1[a * kd + c] * Y[c];
+                float h = (float)acc;
+                Wh[(long long)a * K + j] = h;
+                Wl[(long long)a * K + j] = (float)(acc - (double)h);
+            }
+        } else {
+            for (int e2 = threadIdx.x; e2 < kd * kd; e2 += blockDim.x) {  // T[a][e] = sum_c P1[a][c] Y[c][e]
+                int a = e2 / kd, e = e2 % kd;
+                double acc = 0;
+                for (int c = 0; c < kd; ++c) acc += P1[a * kd + c] * Y[c + kd * e];
+                T[a * kd + e] = acc;
+            }
+            __syncthreads();
+            for (int m = threadIdx.x; m < K; m += blockDim.x) {  // W[(a,b)] = sum_e T[a][e] P2[b][e]
+                int a = m % kd, b = m / kd;
+                double acc = 0;
+                for (int e = 0; e < kd; ++e) acc += T[a * kd + e] * P2[b * kd + e];
+                float h = (float)acc;
+                Wh[(long long)m * K + j] = h;
+                Wl[(long long)m * K + j] = (float)(acc - (double)h);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------- host side
 
-size_t window_smem(int kmax, int kdmax) { return (2 * (size_t)kmax + (size_t)kdmax + 8) * sizeof(double); }
+size_t window_smem(int kmax, int kdmax, int tasks_per_cta, long long g_resident_floats) {
+    return (2 * (size_t)kmax + WIN_RB + 2 * (size_t)kdmax + (size_t)tasks_per_cta * 2 * kdmax * kdmax) *
+               sizeof(double) +
+           (size_t)g_resident_floats * sizeof(float);
+}
+
+int window_tasks_per_cta_max() { return WIN_TPC; }
+int window_rows_per_task_max() { return WIN_RB; }
 
 cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, bool df32) {
-    const void* f = df32 ? (const void*)k_window<true> : (const void*)k_window<false>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    const void* f = df32 ? (const void*)k_window_df32 : (const void*)k_window_fp64;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, WIN_THREADS, smem);
 }
 
@@ -391,6 +816,9 @@ cudaError_t launch_split_df32(const SwrDeviceView& v, cudaStream_t st, int max_K
     long long kk = (long long)max_K * max_K;
     unsigned gx = (unsigned)((kk + 256 * 8 - 1) / (256 * 8));
     k_split_df32<<<dim3(gx, v.n_sub), 256, 0, st>>>(v);
+    size_t sm = ((size_t)max_K + 32 * 32) * sizeof(double);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_make_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_make_w<<<dim3(max_K < 512 ? max_K : 512, v.n_sub), 256, sm, st>>>(v);
     return cudaGetLastError();
 }
 
@@ -400,7 +828,7 @@ cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, 
     cudaError_t e = cudaEventRecord(ev_begin, st);
     if (e != cudaSuccess) return e;
     void* params[] = {&a};
-    const void* f = df32 ? (const void*)k_window<true> : (const void*)k_window<false>;
+    const void* f = df32 ? (const void*)k_window_df32 : (const void*)k_window_fp64;
     e = cudaLaunchCooperativeKernel(f, dim3(grid), dim3(WIN_THREADS), params, smem, st);
     if (e != cudaSuccess) return e;
     return cudaEventRecord(ev_end, st);
