@@ -452,30 +452,6 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fp64(SweepArgs A) {
     }
 }
 
-__global__ void k_window_reset(SweepArgs A, int n_inst) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        A.bar->count = 0;
-        A.bar->gen = 0;
-        *A.n_active = n_inst;
-    }
-}
-
-// Split of the FP64 step-matrix inverse into FP32 pairs (mixed precision).
-__global__ void k_split_df32(SwrDeviceView v) {
-    const int sid = blockIdx.y;
-    const SubDev& s = v.sub[sid];
-    const long long KK = (long long)s.K * s.K;
-    const double* G = v.arena + s.Gm;
-    float* Gh = (float*)(v.arena + s.Gf);
-    float* Gl = Gh + KK;
-    for (long long e = threadIdx.x + (long long)blockIdx.x * blockDim.x; e < KK; e += (long long)blockDim.x * gridDim.x) {
-        double g = G[e];
-        float h = (float)g;
-        Gh[e] = h;
-        Gl[e] = (float)(g - (double)h);
-    }
-}
-
 // ---------------------------------------------------- double-single window
 //
 // Mixed precision, ONE reduce-barrier per step.  z^{n+1} = (Pp (x) Pp) y^{n+1}
