@@ -471,8 +471,8 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
     extern __shared__ double sm[];
     __shared__ double red[33];
     __shared__ TaskCache tcs[WIN_TPC];
-    __shared__ double own[WIN_TPC][4][WIN_RB];
-    __shared__ double s_prev[WIN_TPC];
+    __shared__ double own[WIN_TPC][6][WIN_RB];  // y slots 0..2, z slots 3..5 (ring of 3)
+    __shared__ double s_prev[WIN_TPC], is_prev[WIN_TPC];
     __shared__ int alive[WIN_TPC];
     __shared__ double s_sc[2];
     __shared__ int s_stop;
@@ -522,6 +522,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
             tcs[j] = c;
             alive[j] = 1;
             s_prev[j] = 1.0;
+            is_prev[j] = 1.0;
         }
         __syncthreads();
         const TaskCache& tc = tcs[j];
@@ -547,9 +548,9 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
             h0[tc.r0 + r] = vs[tc.r0 + r];
             own[j][0][r] = vs[tc.r0 + r];  // y^0 in slot 0
         }
-        z_rows_sm(tc, P1, P2, vs, own[j][2], tmp);  // z^0 in slot 0
+        z_rows_sm(tc, P1, P2, vs, own[j][3], tmp);  // z^0 in slot 3
         double acc = 0;
-        for (int r = tid; r < nr; r += WIN_THREADS) acc += own[j][0][r] * own[j][2][r];
+        for (int r = tid; r < nr; r += WIN_THREADS) acc += own[j][0][r] * own[j][3][r];
         acc = wblock_sum(acc, red);
         if (tid == 0) {
             A.part_s[t] = acc;
@@ -583,7 +584,8 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
                 bv[i] = (c < K && bsrc) ? bsrc[c] : 0.0;
             }
             if (tid == 0) {
-                const double s_n = tc.normalize ? sqrt(s2) : 1.0;
+                const double is_n = tc.normalize ? rsqrt(s2) : 1.0;
+                const double s_n = tc.normalize ? s2 * is_n : 1.0;
                 int stop = 0, w = n;
                 if (n >= 2 && tc.ngf_stop && sqrt(fmax(d2, 0.0)) <= tc.ngf_tol) {
                     stop = 1;
@@ -602,9 +604,10 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
                         atomicSub(A.n_active, 1);
                     }
                 } else {
-                    s_sc[0] = 1.0 / s_n;
-                    s_sc[1] = 1.0 / s_prev[j];
+                    s_sc[0] = is_n;
+                    s_sc[1] = is_prev[j];
                     s_prev[j] = s_n;
+                    is_prev[j] = is_n;
                 }
                 s_stop = stop;
             }
@@ -621,24 +624,11 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
                     vf[c] = make_float2(h, (float)(val - (double)h));
                 }
             }
-            // partial of D_n = || y^n/s_n - y^{n-1}/s_{n-1} ||^2_chi over own rows
-            if (n >= 1 && tc.ngf_stop) {
-                const double* y_n = own[j][n & 1];
-                const double* y_p = own[j][(n - 1) & 1];
-                const double* z_n = own[j][2 + (n & 1)];
-                const double* z_p = own[j][2 + ((n - 1) & 1)];
-                double acc = 0;
-                for (int r = tid; r < nr; r += WIN_THREADS)
-                    acc += (y_n[r] * is_n - y_p[r] * is_p) * (z_n[r] * is_n - z_p[r] * is_p);
-                acc = wblock_sum(acc, red);
-                if (tid == 0) A.part_d[t] = acc;
-            } else {
-                __syncthreads();
-            }
+            __syncthreads();
             // fused double-single rows of y^{n+1} = G v and z^{n+1} = W v
             double* ynew = v.arena + tc.hist + (long long)(n + 1) * K;
-            double* yslot = own[j][(n + 1) & 1];
-            double* zslot = own[j][2 + ((n + 1) & 1)];
+            double* yslot = own[j][(n + 1) % 3];
+            double* zslot = own[j][3 + (n + 1) % 3];
             const float* Ghg = (const float*)(v.arena + tc.Gf);
             const float* Gl = Ghg + (long long)K * K;
             const float* Wh = (const float*)(v.arena + tc.Wf);
@@ -648,7 +638,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
                 const float* gl = Gl + (long long)r * K;
                 const float* wh = Wh + (long long)r * K;
                 const float* wl = Wl + (long long)r * K;
-                float yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
+                float yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f, eh;
                 for (int c = lane; c < K; c += 32) {
                     const float2 x = vf[c];
                     const float g0 = gh[c], g1 = gl[c], w0 = wh[c], w1 = wl[c];
@@ -664,7 +654,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    float sh, eh;
+                    float sh;
                     float oh = __shfl_xor_sync(0xffffffffu, yh, o), ol = __shfl_xor_sync(0xffffffffu, yl, o);
                     two_sum(yh, oh, sh, eh);
                     yh = sh;
@@ -683,10 +673,33 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
                 }
             }
             __syncthreads();
-            double acc = 0;
-            for (int r = tid; r < nr; r += WIN_THREADS) acc += yslot[r] * zslot[r];
-            acc = wblock_sum(acc, red);
-            if (tid == 0) A.part_s[t] = acc;
+            // partials of s_{n+1}^2 and of D_n = ||y^n/s_n - y^{n-1}/s_{n-1}||^2_chi (own rows)
+            const bool dn = (n >= 1 && tc.ngf_stop);
+            const double* y_n = own[j][n % 3];
+            const double* y_p = own[j][(n + 2) % 3];
+            const double* z_n = own[j][3 + n % 3];
+            const double* z_p = own[j][3 + (n + 2) % 3];
+            double acc = 0, accd = 0;
+            for (int r = tid; r < nr; r += WIN_THREADS) {
+                acc += yslot[r] * zslot[r];
+                if (dn) accd += (y_n[r] * is_n - y_p[r] * is_p) * (z_n[r] * is_n - z_p[r] * is_p);
+            }
+            acc = warp_sum(acc);
+            accd = warp_sum(accd);
+            if (lane == 0) {
+                red[warp] = acc;
+                red[16 + warp] = accd;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double a = 0, b = 0;
+                for (int i = 0; i < nw; ++i) {
+                    a += red[i];
+                    b += red[16 + i];
+                }
+                A.part_s[t] = a;
+                if (dn) A.part_d[t] = b;
+            }
         }
         __syncthreads();
         target += gridDim.x;
