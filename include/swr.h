@@ -56,7 +56,9 @@ typedef enum swr_mode {
 
 typedef enum swr_precision {
     SWR_PREC_FP64 = 0,   /* plain FP64 everywhere                                */
-    SWR_PREC_MIXED = 1   /* FP32 bulk step matrices + FP64 refinement            */
+    SWR_PREC_MIXED = 1   /* imaginary time: step matrices as FP32 hi/lo pairs with
+                            error-free FP32 accumulation (FP64-level accuracy on
+                            the FP32 pipes), FP64 reductions; real time: FP64     */
 } swr_precision;
 
 /* One SWR problem: global box [box_lo, box_hi]^n_elec cut into L^n_elec

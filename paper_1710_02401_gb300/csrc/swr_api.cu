@@ -32,8 +32,10 @@ cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_wi
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
                         int res_blocks, double* d_res, int max_cap_hint);
 cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
-                          int cap, double* d_part, double* d_energy, double* d_norm2, double* psi_out,
-                          const long long* psi_off, int max_K, int max_kd, int max_q);
+                          int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
+                          double* psi_out, const long long* psi_off, int max_K, int max_kd, int max_q);
+cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const long long* d_boff, const int* d_win_prev,
+                               int n_steps, int iters, int max_K, int max_kd, long long* launches);
 }  // namespace swr
 
 using namespace swr;
@@ -59,6 +61,11 @@ struct swr_ctx {
     bool any_ee = false, tdse = false;
     long long psi_total = 0, own_total = 0;
     bool df32 = false, g_resident = false, any_ngf_stop = false;
+    int cn_iters = 0;
+    std::vector<long long> boff;  // real time: per subdomain r, u, x work vectors
+    long long* d_boff = nullptr;
+    double* d_dipole = nullptr;
+    std::vector<double> dipole_h;
     int nsm = 0, bps = 0, tasks_per_cta = 1, max_rows = 0;
     // device memory
     void* base = nullptr;
@@ -115,6 +122,21 @@ static swr_status fail(swr_ctx* c, swr_status s, const char* fmt, ...) {
 
 static long long align32(long long x) { return (x + 31) & ~31LL; }
 
+// Bound of the contraction of the Crank-Nicolson fixed point x <- G0 (r - i theta Q' x):
+// ||G0|| <= 1 and ||Q'|| <= max over the domain of |x_1 + ... + x_N|.
+static double cn_contraction(const swr_instance& in) {
+    double xm = fmax(fabs(in.box_lo - 0.5 * in.overlap), fabs(in.box_hi + 0.5 * in.overlap));
+    return 0.5 * in.dt * fabs(in.field_E0) * in.n_elec * xm;
+}
+
+// Fixed-point iterations after x0 = G0 r so that rho^(m+1) <= 1e-17.
+static int cn_iterations(const swr_instance& in) {
+    double rho = cn_contraction(in);
+    if (!(rho > 0.0)) return 0;
+    int m = (int)ceil(log(1e-17) / log(rho)) - 1;
+    return m < 0 ? 0 : m;
+}
+
 // ------------------------------------------------------------------ layout
 
 static swr_status validate(swr_ctx* c, const swr_problem* p) {
@@ -143,7 +165,13 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
             return fail(c, SWR_EINVAL, "instance %d: max_steps must be >= 1", i);
         if (in.mode == SWR_MODE_TISE && in.mu_im != 0.0)
             return fail(c, SWR_EINVAL, "instance %d: imaginary-time Robin constant must be real", i);
-        if (in.mode == SWR_MODE_TDSE) return fail(c, SWR_EINVAL, "instance %d: real-time mode not built in this library version", i);
+        if (in.mode == SWR_MODE_TDSE) {
+            if (in.mu_im > 0.0)
+                return fail(c, SWR_EINVAL, "instance %d: real-time Robin constant needs Im(mu) <= 0 (absorbing)", i);
+            if (cn_contraction(in) >= 0.5)
+                return fail(c, SWR_EINVAL, "instance %d: dt/2 * |E0| * max|x_1+..+x_N| = %g >= 0.5: field too "
+                                           "strong for the fixed-point Crank-Nicolson solve", i, cn_contraction(in));
+        }
         int nsub = 1;
         for (int e = 0; e < in.n_elec; ++e) nsub *= in.L;
         for (int s = 0; s < nsub; ++s) {
@@ -210,6 +238,12 @@ static void plan(swr_ctx* c) {
     c->inst.clear();
     c->sub.clear();
     c->psi_off.clear();
+    c->boff.clear();
+    c->cn_iters = 0;
+    for (int i = 0; i < p.n_instances; ++i) {
+        int m = cn_iterations(c->inst_h[i]);
+        if (c->inst_h[i].mode == SWR_MODE_TDSE && m > c->cn_iters) c->cn_iters = m;
+    }
     c->tasks.clear();
     c->inst_task0.clear();
     long long off = 0, po = 0;
@@ -319,6 +353,12 @@ static void plan(swr_ctx* c) {
             long long ee = (d.N == 2) ? 3LL * q * kd * kd + (long long)q * q : 0;
             long long gj = ((long long)GJ_NB_HOST * GJ_NB_HOST + 2LL * GJ_NB_HOST * K) * cx;
             s.work = off; off = align32(off + (ee > gj ? ee : gj));
+            if (c->tdse) {
+                for (int b3 = 0; b3 < 3; ++b3) {
+                    c->boff.push_back(off);
+                    off = align32(off + 2LL * K);
+                }
+            }
             if (c->df32) {
                 s.Gf = off; off = align32(off + (long long)K * K);
                 s.Wf = off; off = align32(off + (long long)K * K);
@@ -343,7 +383,7 @@ static void plan(swr_ctx* c) {
 // Auxiliary device arrays carved after the arena (bytes, 256-aligned).
 struct AuxPlan {
     size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, snorm, sums_s, sums_d,
-        n_active, win, win_prev, bar, res_part, res, epart, energy, norm2, psi, psi_off, total;
+        n_active, win, win_prev, bar, res_part, res, epart, energy, norm2, dipole, boff, psi, psi_off, total;
 };
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 static AuxPlan aux_plan(const swr_ctx* c) {
@@ -369,9 +409,11 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.bar = o; o = al256(o + sizeof(GridBarrier));
     a.res_part = o; o = al256(o + ns * RES_BLOCKS * sizeof(double));
     a.res = o; o = al256(o + ni * sizeof(double));
-    a.epart = o; o = al256(o + 2 * ns * sizeof(double));
+    a.epart = o; o = al256(o + 3 * ns * sizeof(double));
     a.energy = o; o = al256(o + ni * sizeof(double));
     a.norm2 = o; o = al256(o + ni * sizeof(double));
+    a.dipole = o; o = al256(o + ni * sizeof(double));
+    a.boff = o; o = al256(o + (c->boff.size() + 1) * sizeof(long long));
     a.psi = o; o = al256(o + (size_t)c->psi_total * sizeof(double) * (c->tdse ? 2 : 1));
     a.psi_off = o; o = al256(o + ns * sizeof(long long));
     a.total = o;
@@ -496,6 +538,8 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->d_epart = (double*)(b + a.epart);
     c->d_energy = (double*)(b + a.energy);
     c->d_norm2 = (double*)(b + a.norm2);
+    c->d_dipole = (double*)(b + a.dipole);
+    c->d_boff = (long long*)(b + a.boff);
     c->d_psi = (double*)(b + a.psi);
     c->d_psi_off = (long long*)(b + a.psi_off);
     // GEMM jobs of the sum-factorised e-e block
@@ -525,6 +569,8 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     CU(cudaMemcpyAsync(c->d_tasks, c->tasks.data(), c->tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->d_inst_task0, c->inst_task0.data(), c->inst_task0.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->d_psi_off, c->psi_off.data(), c->psi_off.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+    if (!c->boff.empty())
+        CU(cudaMemcpyAsync(c->d_boff, c->boff.data(), c->boff.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
     c->counters[8] += (double)(c->inst.size() * sizeof(InstDev) + c->sub.size() * (sizeof(SubDev) + 2 * sizeof(GemmJob) + sizeof(long long)) +
                                c->tasks.size() * sizeof(Task) + c->inst_task0.size() * sizeof(int));
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
@@ -549,6 +595,7 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->win_h.assign(c->inst.size(), 0);
     c->win_prev_h.assign(c->inst.size(), 0);
     c->win_pp_h.assign(c->inst.size(), 0);
+    c->dipole_h.assign(c->inst.size(), 0.0);
     *out = c;
     return SWR_OK;
 }
@@ -581,7 +628,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     CU(cudaEventRecord(c->ev0, c->stream));
     CU(launch_assemble(view(c), c->stream, c->max_q, c->max_kd, c->max_K, c->any_ee, c->tdse, !c->tdse,
                        c->d_jobs1, c->d_jobs2, c->d_norm_part, CHOL_TAU));
-    if (c->df32) CU(launch_split_df32(view(c), c->stream, c->max_K));
+    if (c->df32 && !c->tdse) CU(launch_split_df32(view(c), c->stream, c->max_K));
     CU(cudaEventRecord(c->ev1, c->stream));
     swr_status st = check_err(c);
     if (st != SWR_OK) return st;
@@ -589,7 +636,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     CU(cudaEventElapsedTime(&ams, c->ev0, c->ev1));
     c->counters[6] += ams;
     c->counters[2] += kAssembleLaunchesFixed + (c->any_ee ? 3 : 0) + 2 * ((c->max_K + GJ_NB_HOST - 1) / GJ_NB_HOST) +
-                      (c->df32 ? 2 : 0);
+                      (c->df32 && !c->tdse ? 2 : 0);
     c->assembled = true;
     c->k = 0;
     c->parity = 0;
@@ -628,20 +675,37 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     if (!c->assembled) return fail(c, SWR_ESTATE, "swr_step before swr_assemble");
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
     CU(cudaEventRecord(c->ev0, c->stream));
-    SweepArgs a = sweep_args(c);
-    int grid = c->grid;
-    CU(launch_window(a, grid, c->win_smem, c->stream, (int)c->inst.size(), c->df32, c->evw0, c->evw1));
+    long long win_launches = 1;
+    if (c->tdse) {
+        // real time: fixed window of n_steps Crank-Nicolson steps, launched from the host
+        std::vector<int> wfix(c->inst.size());
+        int nmax = 0;
+        for (size_t i = 0; i < c->inst.size(); ++i) {
+            wfix[i] = c->inst[i].window_cap;
+            nmax = wfix[i] > nmax ? wfix[i] : nmax;
+        }
+        CU(cudaEventRecord(c->evw0, c->stream));
+        CU(launch_tdse_window(view(c), c->stream, c->d_boff, c->d_win_prev, nmax, c->cn_iters, c->max_K, c->max_kd,
+                              &win_launches));
+        CU(cudaEventRecord(c->evw1, c->stream));
+        CU(cudaMemcpyAsync(c->d_win, wfix.data(), wfix.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    } else {
+        SweepArgs a = sweep_args(c);
+        int grid = c->grid;
+        CU(launch_window(a, grid, c->win_smem, c->stream, (int)c->inst.size(), c->df32, c->evw0, c->evw1));
+    }
     CU(launch_post(view(c), c->stream, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
                    c->d_res_part, RES_BLOCKS, c->d_res, c->cap));
     CU(launch_energy(view(c), c->stream, c->d_win, c->d_snorm, c->cap, c->d_epart, c->d_energy, c->d_norm2,
-                     c->d_psi, c->d_psi_off, c->max_K, c->max_kd, c->max_q));
+                     c->d_dipole, c->d_psi, c->d_psi_off, c->max_K, c->max_kd, c->max_q));
     CU(cudaEventRecord(c->ev1, c->stream));
     const size_t ni = c->inst.size();
     CU(cudaMemcpyAsync(c->res_h.data(), c->d_res, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(c->win_h.data(), c->d_win, ni * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(c->energy_h.data(), c->d_energy, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(c->norm2_h.data(), c->d_norm2, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    c->counters[9] += (double)(ni * (3 * sizeof(double) + sizeof(int)));
+    CU(cudaMemcpyAsync(c->dipole_h.data(), c->d_dipole, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    c->counters[9] += (double)(ni * (4 * sizeof(double) + sizeof(int)));
     swr_status st = check_err(c);
     if (st != SWR_OK) return st;
     // the current window becomes the previous one for the next iteration
@@ -675,7 +739,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     }
     c->counters[0] += wms;
     c->counters[1] += 1;
-    c->counters[2] += kStepLaunches;
+    c->counters[2] += kStepLaunches - 1 + win_launches;
     c->counters[3] += flops;
     c->counters[4] += bytes;
     c->counters[5] += (double)solves;
@@ -759,7 +823,7 @@ extern "C" swr_status swr_get(swr_ctx* c, int field, void* host, size_t bytes) {
         case SWR_FIELD_NORM2: memcpy(host, c->norm2_h.data(), need); return SWR_OK;
         case SWR_FIELD_RES: memcpy(host, c->res_h.data(), need); return SWR_OK;
         case SWR_FIELD_WINDOW: memcpy(host, c->win_h.data(), need); return SWR_OK;
-        case SWR_FIELD_DIPOLE: memset(host, 0, need); return SWR_OK;
+        case SWR_FIELD_DIPOLE: memcpy(host, c->dipole_h.data(), need); return SWR_OK;
         case SWR_FIELD_K_MAX: memcpy(host, &c->k, sizeof(int)); return SWR_OK;
         case SWR_FIELD_COUNTERS: memcpy(host, c->counters, sizeof(c->counters)); return SWR_OK;
         case SWR_FIELD_TRACE_BYTES: { size_t tb = trace_bytes(c); memcpy(host, &tb, sizeof(size_t)); return SWR_OK; }

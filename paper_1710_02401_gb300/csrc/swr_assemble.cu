@@ -537,14 +537,19 @@ __global__ void k_gj_panel(SwrDeviceView v, int kb) {
     }
 }
 
-// Rank-nb update of the whole matrix for block column kb (64x64 tiles).
+// Rank-nb update of the whole matrix for block column kb (TILE x TILE tiles:
+// 64 for real, 32 for complex so that the staged panels stay under 48 KB).
+template <typename T> struct GjTile { static const int v = 64; };
+template <> struct GjTile<cplx> { static const int v = 32; };
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gj_update(SwrDeviceView v, int kb) {
+    constexpr int TL = GjTile<T>::v;
     const int sid = blockIdx.z;
     const SubDev& s = v.sub[sid];
     const int K = s.K, k0 = kb * GJ_NB;
     if (k0 >= K) return;
-    const int tm = blockIdx.y * 64, tn = blockIdx.x * 64;
+    const int tm = blockIdx.y * TL, tn = blockIdx.x * TL;
     if (tm >= K || tn >= K) return;
     const int nb = min(GJ_NB, K - k0);
     double* M = v.arena + s.Gm;
@@ -552,15 +557,15 @@ __global__ void __launch_bounds__(256) k_gj_update(SwrDeviceView v, int kb) {
     const double* Pinv = W;
     const double* Rp = W + (sizeof(T) / 8) * GJ_NB * GJ_NB;
     const double* Cp = Rp + (sizeof(T) / 8) * (long long)GJ_NB * K;
-    __shared__ T Cs[64][GJ_NB + 1];
-    __shared__ T Rs[GJ_NB][64 + 1];
-    for (int e = threadIdx.x; e < 64 * GJ_NB; e += 256) {
+    __shared__ T Cs[TL][GJ_NB + 1];
+    __shared__ T Rs[GJ_NB][TL + 1];
+    for (int e = threadIdx.x; e < TL * GJ_NB; e += 256) {
         int i = e / GJ_NB, t = e % GJ_NB;
         int gi = tm + i;
         Cs[i][t] = (gi < K && t < nb) ? ld_el<T>(Cp, (long long)gi * GJ_NB + t) : zero_el(T());
     }
-    for (int e = threadIdx.x; e < GJ_NB * 64; e += 256) {
-        int t = e / 64, j = e % 64;
+    for (int e = threadIdx.x; e < GJ_NB * TL; e += 256) {
+        int t = e / TL, j = e % TL;
         int gj = tn + j;
         T r = zero_el(T());
         if (gj < K && t < nb) {
@@ -570,8 +575,8 @@ __global__ void __launch_bounds__(256) k_gj_update(SwrDeviceView v, int kb) {
         Rs[t][j] = r;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 64 * 64; e += 256) {
-        int i = e / 64, j = e % 64;
+    for (int e = threadIdx.x; e < TL * TL; e += 256) {
+        int i = e / TL, j = e % TL;
         int gi = tm + i, gj = tn + j;
         if (gi >= K || gj >= K) continue;
         bool ri = gi >= k0 && gi < k0 + nb, cj = gj >= k0 && gj < k0 + nb;
@@ -624,8 +629,8 @@ __global__ void k_project(SwrDeviceView v, double* norm_part) {
     const bool cpx = in.mode == SWR_MODE_TDSE;
     for (int m = threadIdx.x; m < s.K; m += blockDim.x) {
         double val = (s.N == 1) ? u[0][m] : u[0][m % kd] * u[1][m / kd];
-        if (cpx) { c0[2 * m] = val; c0[2 * m + 1] = 0.0; }
-        else c0[m] = val;
+        c0[m] = val;                 // planar: real block ...
+        if (cpx) c0[s.K + m] = 0.0;  // ... then imaginary block
     }
     if (threadIdx.x == 0) norm_part[sid] = (s.N == 1) ? nrm[0] : nrm[0] * nrm[1];
 }
@@ -678,12 +683,13 @@ cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, 
     k_symmetrize<<<ge, 256, 0, st>>>(v);
     k_step_matrix<<<ge, 256, 0, st>>>(v);
     int nkb = (max_K + GJ_NB - 1) / GJ_NB;
-    dim3 gu(div_up(max_K, 64), div_up(max_K, 64), v.n_sub);
     for (int kb = 0; kb < nkb; ++kb) {
         if (any_tdse) {
+            dim3 gu(div_up(max_K, 32), div_up(max_K, 32), v.n_sub);
             k_gj_panel<cplx><<<v.n_sub, 256, 0, st>>>(v, kb);
             k_gj_update<cplx><<<gu, 256, 0, st>>>(v, kb);
         } else {
+            dim3 gu(div_up(max_K, 64), div_up(max_K, 64), v.n_sub);
             k_gj_panel<double><<<v.n_sub, 256, 0, st>>>(v, kb);
             k_gj_update<double><<<gu, 256, 0, st>>>(v, kb);
         }

@@ -35,6 +35,13 @@ __device__ inline double inst_sum(const double* part, int t0, int t1, double* re
 }
 
 // ---------------------------------------------------------------- traces
+//
+// Per-step vectors are planar over nch channels: nch = 1 (imaginary time,
+// real) or 2 (real time: real plane then imaginary plane).  Everything below
+// is linear in the coefficients, so the complex case runs the real arithmetic
+// on each plane and combines the planes only where mu is complex.
+
+__device__ inline int n_channels(const InstDev& in) { return in.mode == SWR_MODE_TDSE ? 2 : 1; }
 
 // Line traces of subdomain j at step n from the un-normalised iterate y^n:
 // N = 2: [d][l][kind][q] with psi (kind 0) and d_{x_d} psi (kind 1) on the line
@@ -42,16 +49,18 @@ __device__ inline double inst_sum(const double* part, int t0, int t1, double* re
 __global__ void k_line_traces(SwrDeviceView v, const int* win, int cap) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
-    const int W = win[s.inst];
+    const InstDev& in = v.inst[s.inst];
+    const int W = win[s.inst], nch = n_channels(in);
     const int kd = s.kd, q = s.q, K = s.K;
     T1Layout lay(q, kd);
     __shared__ double ys[1024];
     __shared__ double r[16][64];
-    for (int n = blockIdx.x; n <= W; n += gridDim.x) {
-        const double* y = v.arena + s.hist + (long long)n * K;
+    for (int item = blockIdx.x; item <= W * nch + nch - 1; item += gridDim.x) {
+        const int n = item / nch, ch = item % nch;
+        const double* y = v.arena + s.hist + ((long long)n * nch + ch) * K;
         for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c] = y[c];
         __syncthreads();
-        double* out = v.arena + s.line + (long long)n * s.nline;
+        double* out = v.arena + s.line + ((long long)n * nch + ch) * s.nline;
         if (s.N == 1) {
             const double* T = v.arena + s.t1[0];
             for (int e = threadIdx.x; e < 8; e += blockDim.x) {
@@ -64,7 +73,6 @@ __global__ void k_line_traces(SwrDeviceView v, const int* win, int cap) {
             __syncthreads();
             continue;
         }
-        // N = 2: r[(d,l,kind)][.] contractions of the line vector with Y
         for (int e = threadIdx.x; e < 16 * kd; e += blockDim.x) {
             int combo = e / kd, m = e % kd;
             int d = combo / 8, l = (combo / 2) % 4, kind = combo % 2;
@@ -91,45 +99,55 @@ __global__ void k_line_traces(SwrDeviceView v, const int* win, int cap) {
     }
 }
 
+// Edge slot (2*d + side) and tangential node of interface node `node`.
+__device__ inline void gamma_slot(const SubDev& s, int node, int& slot, int& nt) {
+    slot = -1;
+    nt = 0;
+    for (int sl = 3; sl >= 0; --sl)
+        if (s.gam_off[sl] >= 0 && node >= s.gam_off[sl]) {
+            slot = sl;
+            nt = node - s.gam_off[sl];
+            return;
+        }
+}
+
 // Averaged Robin data g_i and own traces u_i at the interface nodes of every
 // subdomain for steps 0..W, and the Robin source b'_i of the next iteration.
 __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, int cap, int parity) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
     const InstDev& in = v.inst[s.inst];
-    const int W = win[s.inst];
+    const int W = win[s.inst], nch = n_channels(in);
     const int kd = s.kd, q = s.q, K = s.K, L = in.L, qp = in.q_p;
     T1Layout lay(q, kd);
-    __shared__ double gs[4 * 64 * 6];
+    __shared__ double gs[2][4 * 384];
     __shared__ double hsum[4][64];
     for (int n = blockIdx.x; n <= W; n += gridDim.x) {
         const double sn = in.normalize ? snorm[(long long)s.inst * (cap + 1) + n] : 1.0;
-        double* u = v.arena + s.u[parity] + (long long)n * s.ngam;
-        double* g = v.arena + s.g + (long long)n * s.ngam;
         for (int node = threadIdx.x; node < s.ngam; node += blockDim.x) {
-            // locate the edge slot of this node
-            int slot = -1, nt = 0;
-            for (int sl = 3; sl >= 0; --sl)
-                if (s.gam_off[sl] >= 0 && node >= s.gam_off[sl]) { slot = sl; nt = node - s.gam_off[sl]; break; }
+            int slot, nt;
+            gamma_slot(s, node, slot, nt);
             const int d = slot / 2, side = slot % 2;
             const double sig = side ? 1.0 : -1.0;
             const int lown = side ? 3 : 0;
-            const double* lo = v.arena + s.line + (long long)n * s.nline;
-            double own;
-            if (s.N == 1) own = lo[lown * 2 + 0];
-            else own = lo[((d * 4 + lown) * 2 + 0) * q + nt];
-            u[node] = own / sn;
-            // contributors: neighbour across the edge and the same column, times
-            // the tangential set (own index, plus the overlap neighbour in the bands)
-            double acc = 0;
+            double val[2] = {0, 0}, der[2] = {0, 0}, own[2] = {0, 0};
             int cnt = 0;
+            for (int ch = 0; ch < nch; ++ch) {
+                const double* lo = v.arena + s.line + ((long long)n * nch + ch) * s.nline;
+                own[ch] = (s.N == 1) ? lo[lown * 2 + 0] : lo[((d * 4 + lown) * 2 + 0) * q + nt];
+            }
+            // contributors: the neighbour across the edge and the same column, times
+            // the tangential set (own index, plus the overlap neighbour in the bands)
             const int kdn = s.idx[d];
             const int across = kdn + (side ? 1 : -1);
             if (s.N == 1) {
                 const int j = in.sub_base + across;
-                const double* lj = v.arena + v.sub[j].line + (long long)n * v.sub[j].nline;
                 const int l = side ? 1 : 2;
-                acc += sig * lj[l * 2 + 1] + in.mu_re * lj[l * 2 + 0];
+                for (int ch = 0; ch < nch; ++ch) {
+                    const double* lj = v.arena + v.sub[j].line + ((long long)n * nch + ch) * v.sub[j].nline;
+                    val[ch] += lj[l * 2 + 0];
+                    der[ch] += lj[l * 2 + 1];
+                }
                 cnt = 1;
             } else {
                 const int o = 1 - d;
@@ -148,59 +166,69 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
                         const int j = in.sub_base + j1 + L * j2;
                         const int l = (jd == kdn) ? lown : (side ? 1 : 2);
                         const int nj = nt + shift[t];
-                        const double* lj = v.arena + v.sub[j].line + (long long)n * v.sub[j].nline;
-                        double val = lj[((d * 4 + l) * 2 + 0) * q + nj];
-                        double der = lj[((d * 4 + l) * 2 + 1) * q + nj];
-                        acc += sig * der + in.mu_re * val;
+                        for (int ch = 0; ch < nch; ++ch) {
+                            const double* lj = v.arena + v.sub[j].line + ((long long)n * nch + ch) * v.sub[j].nline;
+                            val[ch] += lj[((d * 4 + l) * 2 + 0) * q + nj];
+                            der[ch] += lj[((d * 4 + l) * 2 + 1) * q + nj];
+                        }
                         ++cnt;
                     }
                 }
             }
-            double gv = acc / (double)cnt;
-            g[node] = gv;
-            gs[node] = gv;
+            const double inv = 1.0 / (double)cnt;
+            // g = (n.grad + mu) psi_j averaged; complex mu mixes the planes
+            double gre = (sig * der[0] + in.mu_re * val[0] - in.mu_im * val[1]) * inv;
+            double gim = (sig * der[1] + in.mu_re * val[1] + in.mu_im * val[0]) * inv;
+            for (int ch = 0; ch < nch; ++ch) {
+                const double gv = ch ? gim : gre;
+                v.arena[s.u[parity] + ((long long)n * nch + ch) * s.ngam + node] = own[ch] / sn;
+                v.arena[s.g + ((long long)n * nch + ch) * s.ngam + node] = gv;
+                gs[ch][node] = gv;
+            }
         }
         __syncthreads();
-        // b'[a + kd b] for this step
-        double* bdst = v.arena + s.bvec + (long long)n * K;
-        if (s.N == 1) {
-            const double* T = v.arena + s.t1[0];
-            for (int a = threadIdx.x; a < kd; a += blockDim.x) {
-                double acc = 0;
-                for (int sl = 0; sl < 2; ++sl) {
-                    if (s.gam_off[sl] < 0) continue;
-                    int l = sl ? 3 : 0;
-                    acc += gs[s.gam_off[sl]] * T[lay.Lv() + l * kd + a];
+        // b'[a + kd b] for this step, one plane per channel
+        for (int ch = 0; ch < nch; ++ch) {
+            double* bdst = v.arena + s.bvec + ((long long)n * nch + ch) * K;
+            if (s.N == 1) {
+                const double* T = v.arena + s.t1[0];
+                for (int a = threadIdx.x; a < kd; a += blockDim.x) {
+                    double acc = 0;
+                    for (int sl = 0; sl < 2; ++sl) {
+                        if (s.gam_off[sl] < 0) continue;
+                        int l = sl ? 3 : 0;
+                        acc += gs[ch][s.gam_off[sl]] * T[lay.Lv() + l * kd + a];
+                    }
+                    bdst[a] = acc;
                 }
-                bdst[a] = acc;
-            }
-        } else {
-            // hsum[slot][m] = sum_t w_t g_t B'_o[t][m]
-            for (int e = threadIdx.x; e < 4 * kd; e += blockDim.x) {
-                int sl = e / kd, m = e % kd;
-                double acc = 0;
-                if (s.gam_off[sl] >= 0) {
-                    int d = sl / 2;
-                    const double* To = v.arena + s.t1[1 - d];
-                    for (int t = 0; t < q; ++t) acc += To[lay.w() + t] * gs[s.gam_off[sl] + t] * To[lay.B() + t * kd + m];
+            } else {
+                for (int e = threadIdx.x; e < 4 * kd; e += blockDim.x) {
+                    int sl = e / kd, m = e % kd;
+                    double acc = 0;
+                    if (s.gam_off[sl] >= 0) {
+                        int d = sl / 2;
+                        const double* To = v.arena + s.t1[1 - d];
+                        for (int t = 0; t < q; ++t)
+                            acc += To[lay.w() + t] * gs[ch][s.gam_off[sl] + t] * To[lay.B() + t * kd + m];
+                    }
+                    hsum[sl][m] = acc;
                 }
-                hsum[sl][m] = acc;
+                __syncthreads();
+                for (int e = threadIdx.x; e < K; e += blockDim.x) {
+                    int a = e % kd, b = e / kd;
+                    double acc = 0;
+                    for (int sl = 0; sl < 4; ++sl) {
+                        if (s.gam_off[sl] < 0) continue;
+                        int d = sl / 2, l = (sl % 2) ? 3 : 0;
+                        const double* Td = v.arena + s.t1[d];
+                        if (d == 0) acc += Td[lay.Lv() + l * kd + a] * hsum[sl][b];
+                        else acc += hsum[sl][a] * Td[lay.Lv() + l * kd + b];
+                    }
+                    bdst[e] = acc;
+                }
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < K; e += blockDim.x) {
-                int a = e % kd, b = e / kd;
-                double acc = 0;
-                for (int sl = 0; sl < 4; ++sl) {
-                    if (s.gam_off[sl] < 0) continue;
-                    int d = sl / 2, l = (sl % 2) ? 3 : 0;
-                    const double* Td = v.arena + s.t1[d];
-                    if (d == 0) acc += Td[lay.Lv() + l * kd + a] * hsum[sl][b];
-                    else acc += hsum[sl][a] * Td[lay.Lv() + l * kd + b];
-                }
-                bdst[e] = acc;
-            }
         }
-        __syncthreads();
     }
 }
 
@@ -211,6 +239,7 @@ __global__ void k_residual(SwrDeviceView v, const int* win, const int* win_prev,
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
     const InstDev& in = v.inst[s.inst];
+    const int nch = n_channels(in);
     const int W = win[s.inst], Wp = first_iter ? 0 : win_prev[s.inst];
     const int Nn = max(W, Wp);
     const int q = s.q, kd = s.kd;
@@ -220,17 +249,19 @@ __global__ void k_residual(SwrDeviceView v, const int* win, const int* win_prev,
     for (long long e = threadIdx.x + (long long)blockIdx.x * blockDim.x; e < (long long)Nn * s.ngam;
          e += (long long)blockDim.x * gridDim.x) {
         int n = 1 + (int)(e / s.ngam), node = (int)(e % s.ngam);
-        double a = v.arena[s.u[parity] + (long long)min(n, W) * s.ngam + node];
-        double b = first_iter ? 0.0 : v.arena[s.u[parity ^ 1] + (long long)min(n, Wp) * s.ngam + node];
         double w = 1.0;
         if (s.N == 2) {
-            int slot = -1, nt = 0;
-            for (int sl = 3; sl >= 0; --sl)
-                if (s.gam_off[sl] >= 0 && node >= s.gam_off[sl]) { slot = sl; nt = node - s.gam_off[sl]; break; }
+            int slot, nt;
+            gamma_slot(s, node, slot, nt);
             const double* To = v.arena + s.t1[1 - slot / 2];
             w = To[lay.w() + nt];
         }
-        acc += in.dt * w * (a - b) * (a - b);
+        for (int ch = 0; ch < nch; ++ch) {
+            double a = v.arena[s.u[parity] + ((long long)min(n, W) * nch + ch) * s.ngam + node];
+            double b = first_iter ? 0.0
+                                  : v.arena[s.u[parity ^ 1] + ((long long)min(n, Wp) * nch + ch) * s.ngam + node];
+            acc += in.dt * w * (a - b) * (a - b);
+        }
     }
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) part[sid * gridDim.x + blockIdx.x] = acc;
@@ -246,15 +277,15 @@ __global__ void k_residual_reduce(SwrDeviceView v, const double* part, int nblk,
     if (threadIdx.x == 0) res[i] = sqrt(acc);
 }
 
-// Energy numerator / denominator per subdomain at step W (normalised state):
-// sum over volume nodes of w chi (kappa |grad psi|^2 + V psi^2) and w chi psi^2,
-// and psi at the nodes (node p = q1 + q*q2).
+// Per subdomain at step W (normalised state): sums over the volume nodes of
+// w chi (kappa |grad psi|^2 + V |psi|^2), w chi |psi|^2 and w chi (x_1+..+x_N)|psi|^2,
+// and psi at the nodes (node p = q1 + q*q2; re, im interleaved in real time).
 __global__ void k_energy(SwrDeviceView v, const int* win, const double* snorm, int cap, double* part,
                          double* psi_out, const long long* psi_off) {
     const int sid = blockIdx.x;
     const SubDev& s = v.sub[sid];
     const InstDev& in = v.inst[s.inst];
-    const int W = win[s.inst];
+    const int W = win[s.inst], nch = n_channels(in);
     const int kd = s.kd, q = s.q, K = s.K;
     T1Layout lay(q, kd);
     const double sn = in.normalize ? snorm[(long long)s.inst * (cap + 1) + W] : 1.0;
@@ -263,74 +294,83 @@ __global__ void k_energy(SwrDeviceView v, const int* win, const double* snorm, i
     double* G1 = sm + K;           // kd * q
     double* G1d = G1 + kd * q;     // kd * q
     __shared__ double red[33];
-    const double* y = v.arena + s.hist + (long long)W * K;
-    for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c] = y[c] / sn;
-    __syncthreads();
     const double* T0 = v.arena + s.t1[0];
-    double num = 0, den = 0;
-    if (s.N == 1) {
-        for (int n = threadIdx.x; n < q; n += blockDim.x) {
-            double p = 0, dp = 0;
-            for (int a = 0; a < kd; ++a) {
-                p += T0[lay.B() + n * kd + a] * ys[a];
-                dp += T0[lay.D() + n * kd + a] * ys[a];
+    double num = 0, den = 0, dip = 0;
+    for (int ch = 0; ch < nch; ++ch) {
+        const double* y = v.arena + s.hist + ((long long)W * nch + ch) * K;
+        for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c] = y[c] / sn;
+        __syncthreads();
+        if (s.N == 1) {
+            for (int n = threadIdx.x; n < q; n += blockDim.x) {
+                double p = 0, dp = 0;
+                for (int a = 0; a < kd; ++a) {
+                    p += T0[lay.B() + n * kd + a] * ys[a];
+                    dp += T0[lay.D() + n * kd + a] * ys[a];
+                }
+                double wc = T0[lay.w() + n] * T0[lay.chi() + n];
+                num += wc * (in.kappa * dp * dp + T0[lay.v1() + n] * p * p);
+                den += wc * p * p;
+                dip += wc * T0[lay.x() + n] * p * p;
+                if (psi_out) psi_out[(psi_off[sid] + n) * nch + ch] = p;
             }
-            double wc = T0[lay.w() + n] * T0[lay.chi() + n];
-            num += wc * (in.kappa * dp * dp + T0[lay.v1() + n] * p * p);
-            den += wc * p * p;
-            if (psi_out) psi_out[psi_off[sid] + n] = p;
-        }
-    } else {
-        const double* T1 = v.arena + s.t1[1];
-        for (int e = threadIdx.x; e < kd * q; e += blockDim.x) {
-            int a = e / q, n2 = e % q;
-            double acc = 0, accd = 0;
-            for (int b = 0; b < kd; ++b) {
-                double c = ys[a + kd * b];
-                acc += c * T1[lay.B() + n2 * kd + b];
-                accd += c * T1[lay.D() + n2 * kd + b];
+        } else {
+            const double* T1 = v.arena + s.t1[1];
+            for (int e = threadIdx.x; e < kd * q; e += blockDim.x) {
+                int a = e / q, n2 = e % q;
+                double acc = 0, accd = 0;
+                for (int b = 0; b < kd; ++b) {
+                    double c = ys[a + kd * b];
+                    acc += c * T1[lay.B() + n2 * kd + b];
+                    accd += c * T1[lay.D() + n2 * kd + b];
+                }
+                G1[e] = acc;
+                G1d[e] = accd;
             }
-            G1[e] = acc;
-            G1d[e] = accd;
+            __syncthreads();
+            for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+                int n2 = e / q, n1 = e % q;
+                double p = 0, d1 = 0, d2 = 0;
+                for (int a = 0; a < kd; ++a) {
+                    double b1 = T0[lay.B() + n1 * kd + a];
+                    p += b1 * G1[a * q + n2];
+                    d1 += T0[lay.D() + n1 * kd + a] * G1[a * q + n2];
+                    d2 += b1 * G1d[a * q + n2];
+                }
+                double x1 = T0[lay.x() + n1], x2 = T1[lay.x() + n2];
+                double r = x1 - x2;
+                double V = T0[lay.v1() + n1] + T1[lay.v1() + n2] + in.ee_coef / sqrt(r * r + in.eta_ee * in.eta_ee);
+                double wc = T0[lay.w() + n1] * T1[lay.w() + n2] * T0[lay.chi() + n1] * T1[lay.chi() + n2];
+                num += wc * (in.kappa * (d1 * d1 + d2 * d2) + V * p * p);
+                den += wc * p * p;
+                dip += wc * (x1 + x2) * p * p;
+                if (psi_out) psi_out[(psi_off[sid] + e) * nch + ch] = p;
+            }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
-            int n2 = e / q, n1 = e % q;
-            double p = 0, d1 = 0, d2 = 0;
-            for (int a = 0; a < kd; ++a) {
-                double b1 = T0[lay.B() + n1 * kd + a];
-                p += b1 * G1[a * q + n2];
-                d1 += T0[lay.D() + n1 * kd + a] * G1[a * q + n2];
-                d2 += b1 * G1d[a * q + n2];
-            }
-            double x1 = T0[lay.x() + n1], x2 = T1[lay.x() + n2];
-            double r = x1 - x2;
-            double V = T0[lay.v1() + n1] + T1[lay.v1() + n2] + in.ee_coef / sqrt(r * r + in.eta_ee * in.eta_ee);
-            double wc = T0[lay.w() + n1] * T1[lay.w() + n2] * T0[lay.chi() + n1] * T1[lay.chi() + n2];
-            num += wc * (in.kappa * (d1 * d1 + d2 * d2) + V * p * p);
-            den += wc * p * p;
-            if (psi_out) psi_out[psi_off[sid] + e] = p;
-        }
     }
     num = block_sum(num, red);
     den = block_sum(den, red);
+    dip = block_sum(dip, red);
     if (threadIdx.x == 0) {
-        part[2 * sid] = num;
-        part[2 * sid + 1] = den;
+        part[3 * sid] = num;
+        part[3 * sid + 1] = den;
+        part[3 * sid + 2] = dip;
     }
 }
 
-__global__ void k_energy_reduce(SwrDeviceView v, const double* part, double* energy, double* norm2) {
+__global__ void k_energy_reduce(SwrDeviceView v, const double* part, double* energy, double* norm2, double* dipole) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= v.n_inst) return;
     const InstDev& in = v.inst[i];
-    double num = 0, den = 0;
+    double num = 0, den = 0, dip = 0;
     for (int j = 0; j < in.n_sub; ++j) {
-        num += part[2 * (in.sub_base + j)];
-        den += part[2 * (in.sub_base + j) + 1];
+        num += part[3 * (in.sub_base + j)];
+        den += part[3 * (in.sub_base + j) + 1];
+        dip += part[3 * (in.sub_base + j) + 2];
     }
     energy[i] = num / den;
     norm2[i] = den;
+    dipole[i] = dip / den;
 }
 
 // ------------------------------------------------------------- host driver
@@ -361,12 +401,12 @@ cudaError_t launch_residual(const SwrDeviceView& v, cudaStream_t st, const int* 
 }
 
 cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
-                          int cap, double* d_part, double* d_energy, double* d_norm2, double* psi_out,
-                          const long long* psi_off, int max_K, int max_kd, int max_q) {
+                          int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
+                          double* psi_out, const long long* psi_off, int max_K, int max_kd, int max_q) {
     size_t smem = ((size_t)max_K + 2 * (size_t)max_kd * max_q) * sizeof(double);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_energy<<<v.n_sub, 256, smem, st>>>(v, d_win, d_snorm, cap, d_part, psi_out, psi_off);
-    k_energy_reduce<<<div_up(v.n_inst, 128), 128, 0, st>>>(v, d_part, d_energy, d_norm2);
+    k_energy_reduce<<<div_up(v.n_inst, 128), 128, 0, st>>>(v, d_part, d_energy, d_norm2, d_dipole);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,219 @@
+// swr_tdse.cu -- real-time time window (Crank-Nicolson under the dipole field).
+//
+// Sec. 5.4 step 2 (real time) with the Robin data of Sec. 5.1 and the
+// length-gauge field of Sec. 1.2, in the orthonormal local basis (A' = I):
+//   (I + i dt/2 (H' + e_{n+1} Q')) c^{n+1}
+//       = (I - i dt/2 (H' + e_n Q')) c^n + i dt/2 kappa (b'^{n+1} + b'^n),
+// H' = kappa (Kf' + mu R') + V' (complex through mu = mu_re + i mu_im),
+// Q' = Xp' (+) Xp' (position in each coordinate, Kronecker sum).
+// With M0 = I + i dt/2 H' inverted once at assembly (G0 = M0^{-1}) and
+// theta_m = dt/2 e(t_m), a step is
+//   r = 2 c^n + i (theta_{n+1} - theta_n) Q' c^n + i dt/2 kappa (b'^{n+1} + b'^n),
+//   solve (M0 + i theta_{n+1} Q') x = r  by  x <- G0 (r - i theta_{n+1} Q' x),
+//   c^{n+1} = x - c^n.
+// The Hermitian part of M0 is I - (dt/2) kappa mu_im R' >= I for mu_im <= 0,
+// so ||G0|| <= 1 and the fixed point contracts with
+// rho <= (dt/2) max|e| max_{Omega_i}|x_1 + ... + x_N|; the host chooses the
+// iteration count from rho so that rho^(m+1) <= 1e-17.
+//
+// Complex vectors are planar: [re block K][im block K].  G0 is interleaved
+// (re, im) per element as the Gauss-Jordan inversion leaves it.
+#include <math.h>
+
+#include "swr_internal.cuh"
+
+namespace swr {
+
+#define CN_THREADS 256
+#define CN_ROWS 64   // rows per CTA of the element-wise kernels
+#define MV_ROWS 32   // rows per CTA of the complex matvec
+
+__device__ inline double field_e(const InstDev& in, double t) {
+    if (in.E0 == 0.0 || t < 0.0 || t > in.T) return 0.0;
+    double s = sin(M_PI * t / in.T);
+    return in.E0 * s * s * sin(in.omega * t + in.phase);
+}
+
+// (Q' x)[r] for rows r of one subdomain, x planar channel in shared memory.
+__device__ inline double qx_row(const SubDev& s, const double* Xp1, const double* Xp2, const double* x, int r) {
+    const int kd = s.kd;
+    if (s.N == 1) {
+        double acc = 0;
+        for (int c = 0; c < kd; ++c) acc += Xp1[r * kd + c] * x[c];
+        return acc;
+    }
+    const int a = r % kd, b = r / kd;
+    double acc = 0;
+    for (int c = 0; c < kd; ++c) acc += Xp1[a * kd + c] * x[c + kd * b];
+    for (int e = 0; e < kd; ++e) acc += Xp2[b * kd + e] * x[a + kd * e];
+    return acc;
+}
+
+struct CnBufs {
+    long long r, u, x;   // per-subdomain planar vectors (offsets in doubles, 2K each)
+};
+
+// r = 2c^n + i dth Q' c^n + i hk (b^{n+1} + b^n);  u = r
+__global__ void k_cn_rhs(SwrDeviceView v, const long long* boff, const int* win_prev, int n) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const InstDev& in = v.inst[s.inst];
+    const int K = s.K, kd = s.kd;
+    const int r0 = blockIdx.x * CN_ROWS;
+    if (r0 >= K) return;
+    extern __shared__ double sm[];
+    double* c = sm;               // 2K
+    double* X1 = sm + 2 * K;      // kd^2
+    double* X2 = X1 + kd * kd;    // kd^2
+    T1Layout lay(s.q, kd);
+    const double* cn = v.arena + s.hist + (long long)n * 2 * K;
+    for (int e = threadIdx.x; e < 2 * K; e += CN_THREADS) c[e] = cn[e];
+    const double* X1g = v.arena + s.t1[0] + lay.mat(M_XP);
+    const double* X2g = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_XP);
+    for (int e = threadIdx.x; e < kd * kd; e += CN_THREADS) {
+        X1[e] = X1g[e];
+        X2[e] = X2g[e];
+    }
+    __syncthreads();
+    const double th0 = 0.5 * in.dt * field_e(in, n * in.dt), th1 = 0.5 * in.dt * field_e(in, (n + 1) * in.dt);
+    const double dth = th1 - th0, hk = 0.5 * in.dt * in.kappa;
+    const int wp = win_prev[s.inst];
+    const double* b1 = (wp > 0) ? v.arena + s.bvec + (long long)min(n + 1, wp) * 2 * K : nullptr;
+    const double* b0 = (wp > 0) ? v.arena + s.bvec + (long long)min(n, wp) * 2 * K : nullptr;
+    double* R = v.arena + boff[3 * sid + 0];
+    double* U = v.arena + boff[3 * sid + 1];
+    for (int r = r0 + threadIdx.x; r < min(K, r0 + CN_ROWS); r += CN_THREADS) {
+        const double qre = qx_row(s, X1, X2, c, r), qim = qx_row(s, X1, X2, c + K, r);
+        double bre = 0, bim = 0;
+        if (b1) {
+            bre = b1[r] + b0[r];
+            bim = b1[K + r] + b0[K + r];
+        }
+        const double rre = 2.0 * c[r] - dth * qim - hk * bim;
+        const double rim = 2.0 * c[K + r] + dth * qre + hk * bre;
+        R[r] = rre;
+        R[K + r] = rim;
+        U[r] = rre;
+        U[K + r] = rim;
+    }
+}
+
+// x = G0 u  (complex, FP64); one warp per row, lanes over the columns.
+__global__ void __launch_bounds__(256) k_cmv(SwrDeviceView v, const long long* boff) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const int K = s.K;
+    const int r0 = blockIdx.x * MV_ROWS;
+    if (r0 >= K) return;
+    extern __shared__ double sm[];
+    const double* U = v.arena + boff[3 * sid + 1];
+    for (int e = threadIdx.x; e < 2 * K; e += blockDim.x) sm[e] = U[e];
+    __syncthreads();
+    const double2* G = (const double2*)(v.arena + s.Gm);
+    double* X = v.arena + boff[3 * sid + 2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = r0 + warp; r < min(K, r0 + MV_ROWS); r += nw) {
+        const double2* g = G + (long long)r * K;
+        double are = 0, aim = 0;
+        for (int c = lane; c < K; c += 32) {
+            const double2 gg = g[c];
+            const double ur = sm[c], ui = sm[K + c];
+            are = fma(gg.x, ur, fma(-gg.y, ui, are));
+            aim = fma(gg.x, ui, fma(gg.y, ur, aim));
+        }
+        are = warp_sum(are);
+        aim = warp_sum(aim);
+        if (lane == 0) {
+            X[r] = are;
+            X[K + r] = aim;
+        }
+    }
+}
+
+// u = r - i theta_{n+1} Q' x
+__global__ void k_cn_update(SwrDeviceView v, const long long* boff, int n) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const InstDev& in = v.inst[s.inst];
+    const int K = s.K, kd = s.kd;
+    const int r0 = blockIdx.x * CN_ROWS;
+    if (r0 >= K) return;
+    extern __shared__ double sm[];
+    double* x = sm;
+    double* X1 = sm + 2 * K;
+    double* X2 = X1 + kd * kd;
+    T1Layout lay(s.q, kd);
+    const double* Xg = v.arena + boff[3 * sid + 2];
+    for (int e = threadIdx.x; e < 2 * K; e += CN_THREADS) x[e] = Xg[e];
+    const double* X1g = v.arena + s.t1[0] + lay.mat(M_XP);
+    const double* X2g = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_XP);
+    for (int e = threadIdx.x; e < kd * kd; e += CN_THREADS) {
+        X1[e] = X1g[e];
+        X2[e] = X2g[e];
+    }
+    __syncthreads();
+    const double th1 = 0.5 * in.dt * field_e(in, (n + 1) * in.dt);
+    const double* R = v.arena + boff[3 * sid + 0];
+    double* U = v.arena + boff[3 * sid + 1];
+    for (int r = r0 + threadIdx.x; r < min(K, r0 + CN_ROWS); r += CN_THREADS) {
+        const double qre = qx_row(s, X1, X2, x, r), qim = qx_row(s, X1, X2, x + K, r);
+        U[r] = R[r] + th1 * qim;
+        U[K + r] = R[K + r] - th1 * qre;
+    }
+}
+
+// c^{n+1} = x - c^n
+__global__ void k_cn_finish(SwrDeviceView v, const long long* boff, int n) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const int K = s.K;
+    const double* X = v.arena + boff[3 * sid + 2];
+    const double* cn = v.arena + s.hist + (long long)n * 2 * K;
+    double* cn1 = v.arena + s.hist + (long long)(n + 1) * 2 * K;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * K; e += gridDim.x * blockDim.x) cn1[e] = X[e] - cn[e];
+}
+
+// c^0 into hist[0] (planar)
+__global__ void k_cn_init(SwrDeviceView v) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const int K = s.K;
+    const double* c0 = v.arena + s.c0;
+    double* h0 = v.arena + s.hist;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * K; e += gridDim.x * blockDim.x) h0[e] = c0[e];
+}
+
+static inline unsigned div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// Launches of one real-time window: n_steps steps with `iters` fixed-point
+// iterations each; returns the number of kernel launches.
+cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const long long* d_boff, const int* d_win_prev,
+                               int n_steps, int iters, int max_K, int max_kd, long long* launches) {
+    const size_t sm_el = (2 * (size_t)max_K + 2 * (size_t)max_kd * max_kd) * sizeof(double);
+    const size_t sm_mv = 2 * (size_t)max_K * sizeof(double);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_cn_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_cn_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_cmv, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        attr_done = true;
+    }
+    const dim3 ge(div_up(max_K, CN_ROWS), v.n_sub), gm(div_up(max_K, MV_ROWS), v.n_sub), gf(div_up(2 * max_K, 256), v.n_sub);
+    long long nl = 0;
+    k_cn_init<<<gf, 256, 0, st>>>(v);
+    ++nl;
+    for (int n = 0; n < n_steps; ++n) {
+        k_cn_rhs<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, d_win_prev, n);
+        k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff);
+        for (int m = 0; m < iters; ++m) {
+            k_cn_update<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, n);
+            k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff);
+        }
+        k_cn_finish<<<gf, 256, 0, st>>>(v, d_boff, n);
+        nl += 3 + 2 * iters;
+    }
+    *launches = nl;
+    return cudaGetLastError();
+}
+
+}  // namespace swr

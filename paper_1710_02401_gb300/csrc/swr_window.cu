@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
     __shared__ double red[33];
     __shared__ TaskCache tcs[WIN_TPC];
     __shared__ double own[WIN_TPC][6][WIN_RB];  // y slots 0..2, z slots 3..5 (ring of 3)
-    __shared__ double s_prev[WIN_TPC], is_prev[WIN_TPC];
+    __shared__ double is_prev[WIN_TPC];
     __shared__ int alive[WIN_TPC];
     __shared__ double s_sc[2];
     __shared__ int s_stop;
@@ -521,7 +521,6 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
             c.ngf_tol = in.ngf_tol;
             tcs[j] = c;
             alive[j] = 1;
-            s_prev[j] = 1.0;
             is_prev[j] = 1.0;
         }
         __syncthreads();
@@ -606,7 +605,6 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
                 } else {
                     s_sc[0] = is_n;
                     s_sc[1] = is_prev[j];
-                    s_prev[j] = s_n;
                     is_prev[j] = is_n;
                 }
                 s_stop = stop;

@@ -271,14 +271,27 @@ class SWR:
     def node_counts(self) -> np.ndarray:
         return self.get(FIELD_NODE_COUNTS, dtype=np.int32).reshape(-1, 3)
 
+    @property
+    def complex(self) -> bool:
+        return self.instances[0].mode == P.TDSE
+
+    def dipole(self) -> np.ndarray:
+        return self.get(FIELD_DIPOLE)
+
+    def norm2(self) -> np.ndarray:
+        return self.get(FIELD_NORM2)
+
     def psi_nodes(self) -> List[np.ndarray]:
-        """psi_i at the volume nodes of every subdomain (node p = q1 + q*q2)."""
+        """psi_i at the volume nodes of every subdomain (node p = q1 + q*q2);
+        complex in real time."""
         flat = self.get(FIELD_PSI_NODES)
+        nch = 2 if self.complex else 1
         out, o = [], 0
         for (q, ng, K), inst_sub in zip(self.node_counts(), self._sub_n()):
             n = q ** inst_sub
-            out.append(flat[o:o + n])
-            o += n
+            blk = flat[o:o + n * nch]
+            out.append(blk[0::2] + 1j * blk[1::2] if nch == 2 else blk)
+            o += n * nch
         return out
 
     def _sub_n(self):
@@ -295,13 +308,15 @@ class SWR:
     def _per_sub_steps(self, field):
         flat = self.get(field)
         win = self.window()
+        nch = 2 if self.complex else 1
         out, o, s = [], 0, 0
         counts = self.node_counts()
         for i, inst in enumerate(self.instances):
             for _ in range(inst.n_sub):
                 ng = int(counts[s][1])
-                n = (int(win[i]) + 1) * ng
-                out.append(flat[o:o + n].reshape(int(win[i]) + 1, ng))
+                n = (int(win[i]) + 1) * ng * nch
+                blk = flat[o:o + n].reshape(int(win[i]) + 1, nch, ng)
+                out.append(blk[:, 0, :] + 1j * blk[:, 1, :] if nch == 2 else blk[:, 0, :])
                 o += n
                 s += 1
         return out

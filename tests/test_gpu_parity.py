@@ -46,7 +46,10 @@ def _run_gpu(S, inst, kmax, tol=0.0, precision=0):
         rep = s.step()
         res.append(rep.res)
         wins.append(int(s.window()[0]))
-        energies.append(float(s.energy()[0]))
+        if inst.mode == P.TDSE:
+            energies.append((float(s.norm2()[0]), float(s.dipole()[0])))
+        else:
+            energies.append(float(s.energy()[0]))
         if rep.res <= tol:
             break
     return s, res, wins, energies
@@ -62,7 +65,11 @@ def _compare(S, inst, kmax, tol=0.0, rel=REL, precision=0):
     r0 = max(r.res for r in ref.records)
     for a, r in zip(res, ref.records):
         assert abs(a - r.res) <= rel * r0, (a, r.res)
-    if inst.normalize or inst.mode == P.TDSE:
+    if inst.mode == P.TDSE:
+        for (n2, dip), r in zip(energies, ref.records):
+            assert abs(n2 - r.norm2) <= rel * abs(r.norm2), (n2, r.norm2)
+            assert abs(dip - r.dipole) <= rel * max(1.0, abs(r.dipole)), (dip, r.dipole)
+    elif inst.normalize:
         for a, r in zip(energies, ref.records):
             if r.energy is not None:
                 assert abs(a - r.energy) <= rel * abs(r.energy), (a, r.energy)
@@ -120,6 +127,23 @@ def test_parity_heat_fixed_window(swr_mod):
                       mode=P.TISE, normalize=False, dt=0.1, n_steps=10, ngf_tol=0.0,
                       phi0_gamma=0.2)
     _compare(swr_mod, inst, kmax=5)
+
+
+def test_parity_real_time_one_electron(swr_mod):
+    # Crank-Nicolson under the dipole field, absorbing Robin mu = -10i, 2 subdomains
+    inst = P.tise_1d_two_subdomains().replace(mode=P.TDSE, mu=-10j, dt=0.01, n_steps=60,
+                                              field=(0.5, 0.6, 8.0, 0.3), K_d=30, delta=3.0)
+    _compare(swr_mod, inst, kmax=4)
+
+
+def test_parity_real_time_two_electrons_3x3(swr_mod):
+    _compare(swr_mod, P.small_tdse_2d(), kmax=3)
+
+
+def test_parity_real_time_uneven_no_field(swr_mod):
+    inst = P.small_tdse_2d(L=2, K_d=7, q_p=6, n_mid=2, n_steps=25).replace(
+        K_d=[7, 9, 8, 6], delta=[1.3, 2.1, 1.7, 1.1], field=(0.0, 1.0, 0.0, 0.0))
+    _compare(swr_mod, inst, kmax=3)
 
 
 def test_parity_batched_instances(swr_mod):
