@@ -35,6 +35,22 @@ METRIC = "SWR time-to-1e-8 interface residual; subdomain solves/s vs plain FP64 
 # independent FMA chains over all SMs (the ceilings of the window kernel)
 FP64_PEAK_TFLOPS = 1.01
 FP32_PEAK_TFLOPS = 67.7
+# DRAM bytes per launch of the window kernels from one ncu capture (profiles/), valid
+# only while the kernel source is the one that was profiled (sha256 prefix of swr_window.cu)
+PROFILED_TRAFFIC = {
+    "k_window_df32": ("9feb1703488c26c7", 327.6e6, "profiles/k_window_df32_tise_2e_16sd.md"),
+    "k_window_fp64": ("9feb1703488c26c7", 280.5e6, "profiles/k_window_fp64_tise_2e_16sd.md"),
+}
+
+
+def profiled_traffic(kernel):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1710_02401_gb300", "csrc", "swr_window.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    rec = PROFILED_TRAFFIC.get(kernel)
+    if rec is None or rec[0] != h:
+        return None, None
+    return rec[1], rec[2]
 
 
 def workload(name: str):
@@ -247,17 +263,19 @@ def main():
     if args.precision == "mixed":
         # double-single matvec: ~12 FP32 operations per matrix element on the FP32 pipes
         peak = FP32_PEAK_TFLOPS / 6.0
-        roof = {"kernel": "k_window<df32>", "bound": "alu", "achieved": achieved, "peak": peak,
+        roof = {"kernel": "k_window_df32", "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": "measured FP32 FMA rate of this pool's GB300 (67.7 TFLOP/s) / 6: the "
                                "double-single product-sum spends 12 FP32 operations per 2 FP64-equivalent flops",
                 "algorithmic": "2 K^2 FP64-equivalent flops per local step solve (matvec with the step-matrix inverse)"}
     else:
-        roof = {"kernel": "k_window<fp64>", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+        roof = {"kernel": "k_window_fp64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "FP64 FMA rate measured on this pool's GB300 (probe of independent FMA chains)",
                 "algorithmic": "2 K^2 flops per local step solve (FP64 matvec with the step-matrix inverse)"}
-    roof["traffic"] = None
+    traffic, src = profiled_traffic(roof["kernel"])
+    roof["traffic"] = traffic
+    roof["traffic_source"] = src
     roof["window_ms_per_launch"] = w_ms / max(w_launch, 1)
     roof["step_us"] = 1e3 * w_ms / max(1.0, cnt["solves"] / inst.n_sub)
     launches = int(cnt["kernel_launches"])
