@@ -188,6 +188,44 @@ swr_status swr_get(swr_ctx* ctx, int field, void* host, size_t bytes);
 /* Bytes that swr_get needs for `field` (for the sized fields). */
 swr_status swr_field_bytes(swr_ctx* ctx, int field, size_t* bytes);
 
+/* ---- learned initial traces (not part of the paper's method) ---------------
+ * The paper starts the Schwarz iteration from g^(0) = 0.  These entry points
+ * let a caller start it from predicted Robin data instead.  A trace code is
+ * the projection of each interior edge's Robin data onto discrete
+ * orthonormal polynomials of degree < S along the edge (S = 1 for the point
+ * edges of 1-electron problems) times degree < Tm in the step index; per
+ * subdomain the code has 4 x 2 x S x Tm floats ([edge slot 2d+side][re, im]
+ * [s][t], zero for absent edges and for the imaginary plane in imaginary
+ * time).  Needs one fixed time window for all instances. */
+
+/* Builds the bases for this context (after swr_assemble).  *floats_per_sub
+ * receives 8*S*Tm.  1 <= S <= 16, 1 <= Tm <= 32. */
+swr_status swr_trace_codec(swr_ctx* ctx, int S, int Tm, size_t* floats_per_sub);
+/* Code of the Robin data of the last iteration into code_dev, a DEVICE array
+ * of n_sub_total * floats_per_sub floats, subdomains in order. */
+swr_status swr_trace_encode(swr_ctx* ctx, float* code_dev);
+/* Decodes code_dev (device, same layout) into Robin data and the Robin
+ * source b' that the next swr_step starts from (instead of zero traces). */
+swr_status swr_trace_decode_set(swr_ctx* ctx, const float* code_dev);
+
+/* Small BF16 multilayer perceptron trained with its own kernels (tanh hidden
+ * layers, identity output, mean squared error, Adam); products on the tensor
+ * cores (mma.sync m16n8k16, BF16 inputs, FP32 accumulation), FP32 master
+ * weights.  Parameters: for each layer l, W_l [d_l x d_{l+1}] row-major then
+ * b_l [d_{l+1}], d = (n_in, width x n_hidden, n_out).  x, y, t are DEVICE
+ * arrays [batch x dim] row-major FP32.  Not part of the paper. */
+typedef struct swr_mlp swr_mlp;
+swr_status  swr_mlp_create(int n_in, int width, int n_hidden, int n_out, void* stream, swr_mlp** out);
+swr_status  swr_mlp_param_count(swr_mlp* mlp, size_t* n);
+swr_status  swr_mlp_set_params(swr_mlp* mlp, const float* host, size_t n);  /* also resets Adam */
+swr_status  swr_mlp_get_params(swr_mlp* mlp, float* host, size_t n);
+swr_status  swr_mlp_forward(swr_mlp* mlp, const float* x_dev, int batch, float* y_dev);
+/* One Adam step (lr > 0) or only gradients (lr == 0); loss_host / grad_host nullable. */
+swr_status  swr_mlp_train_step(swr_mlp* mlp, const float* x_dev, const float* t_dev, int batch, float lr,
+                               float* loss_host, float* grad_host);
+void        swr_mlp_destroy(swr_mlp* mlp);
+const char* swr_mlp_last_error(const swr_mlp* mlp);
+
 /* Allocation-free recomputation of Res(k) of the last completed Schwarz
  * iteration, one value per instance into res_host[0..n) (n = n_instances).
  * No counterpart in the paper: this is a service for callers that may not

@@ -925,10 +925,39 @@ bool residual_inputs(swr_ctx* c, ResidualInputs* r) {
 void set_error(swr_ctx* c, const char* msg) {
     if (c) c->err = msg;
 }
+struct CodecInputs {
+    SwrDeviceView v;
+    cudaStream_t stream;
+    int n_sub, n_inst, window, nch, max_q;
+    int* d_win_prev;
+    std::vector<int>* win_prev_h;
+    std::vector<int>* win_h;
+    bool* codec_ready;
+};
+bool codec_inputs(swr_ctx* c, CodecInputs* r) {
+    if (!c || !c->assembled) return false;
+    r->v = view(c);
+    r->stream = c->stream;
+    r->n_sub = (int)c->sub.size();
+    r->n_inst = (int)c->inst.size();
+    int w = c->inst[0].window_cap;
+    for (const InstDev& d : c->inst)
+        if (d.window_cap != w) w = 0;  // the code needs one fixed window for all instances
+    r->window = w;
+    r->nch = c->tdse ? 2 : 1;
+    r->max_q = c->max_q;
+    r->d_win_prev = c->d_win_prev;
+    r->win_prev_h = &c->win_prev_h;
+    r->win_h = &c->win_h;
+    r->codec_ready = nullptr;
+    return true;
+}
+void codec_release(const swr_ctx* c);
 }  // namespace swr
 
 extern "C" void swr_destroy(swr_ctx* c) {
     if (!c) return;
+    codec_release(c);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     if (c->ev0) cudaEventDestroy(c->ev0);

@@ -216,3 +216,24 @@ PRESETS = {
     "tise_2e_16sd": tise_2e_16_subdomains,
     "tdse_2e_64sd": tdse_2e_64_subdomains,
 }
+
+
+def learned_trace_family(n_instances: int, seed: int = 5) -> List[Instance]:
+    """Seeded real-time problems for the learned initial traces, on a reduced
+    grid: 2 electrons, [-6,6]^2 in 2x2 subdomains, 8x8 Gaussians, 40
+    Crank-Nicolson steps (dt = 0.01), mu = -10i, field
+    0.5 sin^2(pi t/0.4) sin(8 t + phase) with phase ~ U[0, 2 pi); 1 or 2
+    nuclei at U[-1.5, 1.5] with Z in {1, 2}; softening ~ U[0.3, 1]."""
+    rng = random.Random(seed)
+    box, L, ov, kd = (-6.0, 6.0), 2, 0.6, 8
+    out = []
+    for _ in range(n_instances):
+        P = rng.choice((1, 2))
+        nuc = tuple((rng.uniform(-1.5, 1.5), float(rng.choice((1, 2)))) for _ in range(P))
+        eps = rng.uniform(0.3, 1.0)
+        phase = rng.uniform(0.0, 2.0 * math.pi)
+        out.append(Instance(n_elec=2, box=box, L=L, overlap=ov, K_d=kd,
+                            delta=spacing_rule_delta(box, L, ov, kd), q_p=6, n_mid=mid_panels(box, L, ov),
+                            nuclei=nuc, eta_en=eps, eta_ee=eps, ee_coef=1.0, mu=-10j, mode=TDSE,
+                            dt=0.01, n_steps=40, field=(0.5, 0.4, 8.0, phase), phi0_gamma=1.0))
+    return out

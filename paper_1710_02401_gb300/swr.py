@@ -62,7 +62,10 @@ class swr_trace_view(C.Structure):
 
 
 EXPORTS = ["swr_workspace_size", "swr_setup", "swr_assemble", "swr_step", "swr_iterate", "swr_traces",
-           "swr_get", "swr_field_bytes", "swr_residual_noalloc", "swr_destroy", "swr_last_error"]
+           "swr_get", "swr_field_bytes", "swr_trace_codec", "swr_trace_encode", "swr_trace_decode_set",
+           "swr_mlp_create", "swr_mlp_param_count", "swr_mlp_set_params", "swr_mlp_get_params",
+           "swr_mlp_forward", "swr_mlp_train_step", "swr_mlp_destroy", "swr_mlp_last_error",
+           "swr_residual_noalloc", "swr_destroy", "swr_last_error"]
 
 _lib = None
 
@@ -85,12 +88,27 @@ def load_library(path: str = LIB_PATH):
     lib.swr_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]
     lib.swr_field_bytes.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]
     lib.swr_residual_noalloc.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]
+    lib.swr_trace_codec.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
+    lib.swr_trace_encode.argtypes = [C.c_void_p, C.c_void_p]
+    lib.swr_trace_decode_set.argtypes = [C.c_void_p, C.c_void_p]
+    lib.swr_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.swr_mlp_param_count.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
+    lib.swr_mlp_set_params.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+    lib.swr_mlp_get_params.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t]
+    lib.swr_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+    lib.swr_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float,
+                                       C.POINTER(C.c_float), C.c_void_p]
+    lib.swr_mlp_destroy.argtypes = [C.c_void_p]
+    lib.swr_mlp_destroy.restype = None
+    lib.swr_mlp_last_error.argtypes = [C.c_void_p]
+    lib.swr_mlp_last_error.restype = C.c_char_p
     lib.swr_destroy.argtypes = [C.c_void_p]
     lib.swr_destroy.restype = None
     lib.swr_last_error.argtypes = [C.c_void_p]
     lib.swr_last_error.restype = C.c_char_p
-    for name in EXPORTS[:-2]:
-        getattr(lib, name).restype = C.c_int
+    for name in EXPORTS:
+        if name not in ("swr_destroy", "swr_last_error", "swr_mlp_destroy", "swr_mlp_last_error"):
+            getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
 
@@ -238,6 +256,28 @@ class SWR:
                                                   out.size), self.ctx)
         return out
 
+    # ------------------------------------------------------ trace codes
+    def trace_codec(self, S: int, Tm: int) -> int:
+        n = C.c_size_t(0)
+        self._check(self.lib.swr_trace_codec(self.ctx, S, Tm, C.byref(n)), self.ctx)
+        self.code_floats = int(n.value)
+        return self.code_floats
+
+    def n_sub_total(self) -> int:
+        return sum(inst.n_sub for inst in self.instances)
+
+    def trace_encode(self):
+        """Codes of the last iteration's Robin data as a CUDA float32 tensor [n_sub, floats]."""
+        import torch
+        out = torch.empty(self.n_sub_total(), self.code_floats, dtype=torch.float32, device=self.device)
+        self._check(self.lib.swr_trace_encode(self.ctx, C.c_void_p(out.data_ptr())), self.ctx)
+        return out
+
+    def trace_decode_set(self, code) -> None:
+        """Start the next Schwarz iteration from the decoded codes (CUDA float32 tensor)."""
+        code = code.contiguous()
+        self._check(self.lib.swr_trace_decode_set(self.ctx, C.c_void_p(code.data_ptr())), self.ctx)
+
     def trace_bytes(self) -> int:
         return int(self.get(FIELD_TRACE_BYTES, dtype=np.uint64)[0])
 
@@ -320,3 +360,64 @@ class SWR:
                 o += n
                 s += 1
         return out
+
+
+class MLP:
+    """BF16 multilayer perceptron with its own CUDA forward/backward/Adam
+    kernels (tanh hidden layers).  Device arrays are torch CUDA tensors."""
+
+    def __init__(self, n_in: int, width: int, n_hidden: int, n_out: int, stream=None, device="cuda:0"):
+        import torch
+        self.lib = load_library()
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.dims = [n_in] + [width] * n_hidden + [n_out]
+        h = C.c_void_p(None)
+        st = self.lib.swr_mlp_create(n_in, width, n_hidden, n_out, C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != SWR_OK:
+            raise SWRError(st, "swr_mlp_create")
+        self.h = h
+        n = C.c_size_t(0)
+        self.lib.swr_mlp_param_count(self.h, C.byref(n))
+        self.n_params = int(n.value)
+
+    def _check(self, st):
+        if st != SWR_OK:
+            raise SWRError(st, self.lib.swr_mlp_last_error(self.h).decode())
+
+    def set_params(self, p: np.ndarray) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self.lib.swr_mlp_set_params(self.h, p.ctypes.data_as(C.c_void_p), p.size))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        self._check(self.lib.swr_mlp_get_params(self.h, out.ctypes.data_as(C.c_void_p), out.size))
+        return out
+
+    def forward(self, x):
+        import torch
+        x = x.contiguous()
+        y = torch.empty(x.shape[0], self.dims[-1], dtype=torch.float32, device=self.device)
+        self._check(self.lib.swr_mlp_forward(self.h, C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(y.data_ptr())))
+        return y
+
+    def train_step(self, x, t, lr: float, want_grad: bool = False):
+        x = x.contiguous()
+        t = t.contiguous()
+        loss = C.c_float(0.0)
+        g = np.empty(self.n_params, dtype=np.float32) if want_grad else None
+        self._check(self.lib.swr_mlp_train_step(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                                x.shape[0], float(lr), C.byref(loss),
+                                                g.ctypes.data_as(C.c_void_p) if g is not None else None))
+        return float(loss.value), g
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.swr_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
