@@ -56,9 +56,10 @@ typedef enum swr_mode {
 
 typedef enum swr_precision {
     SWR_PREC_FP64 = 0,   /* plain FP64 everywhere                                */
-    SWR_PREC_MIXED = 1   /* imaginary time: step matrices as FP32 hi/lo pairs with
-                            error-free FP32 accumulation (FP64-level accuracy on
-                            the FP32 pipes), FP64 reductions; real time: FP64     */
+    SWR_PREC_MIXED = 1   /* step matrices stored as FP32 hi/lo pairs (four planes for
+                            the complex real-time G0) with error-free FP32
+                            accumulation: FP64-level accuracy on the FP32 pipes;
+                            FP64 reductions, norms, orthogonalisation, inversion  */
 } swr_precision;
 
 /* One SWR problem: global box [box_lo, box_hi]^n_elec cut into L^n_elec
@@ -176,7 +177,9 @@ typedef enum swr_field {
                                    [1] launches of the time-window kernel,
                                    [2] kernel launches of the library (all kernels),
                                    [3] algorithmic flops of the window kernels
-                                       (2 K^2 real / 8 K^2 complex per local step solve),
+                                       (2 K^2 per local step solve in imaginary time;
+                                       8 K^2 per matrix sweep, 1 + m sweeps per step,
+                                       in real time),
                                    [4] algorithmic bytes of the window kernels
                                        (step-matrix bytes read per local step solve),
                                    [5] local step solves,

@@ -35,7 +35,8 @@ cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_
                           int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
                           double* psi_out, const long long* psi_off, int max_K, int max_kd, int max_q);
 cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const long long* d_boff, const int* d_win_prev,
-                               int n_steps, int iters, int max_K, int max_kd, long long* launches);
+                               int n_steps, int iters, int max_K, int max_kd, bool df32, long long* launches);
+cudaError_t launch_split_c_df32(const SwrDeviceView& v, cudaStream_t st, int max_K);
 }  // namespace swr
 
 using namespace swr;
@@ -359,7 +360,10 @@ static void plan(swr_ctx* c) {
                     off = align32(off + 2LL * K);
                 }
             }
-            if (c->df32) {
+            if (c->df32 && c->tdse) {
+                s.Gf = off; off = align32(off + 2LL * K * K);  // four FP32 planes of the complex G0
+                s.Wf = 0;
+            } else if (c->df32) {
                 s.Gf = off; off = align32(off + (long long)K * K);
                 s.Wf = off; off = align32(off + (long long)K * K);
             } else {
@@ -629,6 +633,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     CU(launch_assemble(view(c), c->stream, c->max_q, c->max_kd, c->max_K, c->any_ee, c->tdse, !c->tdse,
                        c->d_jobs1, c->d_jobs2, c->d_norm_part, CHOL_TAU));
     if (c->df32 && !c->tdse) CU(launch_split_df32(view(c), c->stream, c->max_K));
+    if (c->df32 && c->tdse) CU(launch_split_c_df32(view(c), c->stream, c->max_K));
     CU(cudaEventRecord(c->ev1, c->stream));
     swr_status st = check_err(c);
     if (st != SWR_OK) return st;
@@ -636,7 +641,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     CU(cudaEventElapsedTime(&ams, c->ev0, c->ev1));
     c->counters[6] += ams;
     c->counters[2] += kAssembleLaunchesFixed + (c->any_ee ? 3 : 0) + 2 * ((c->max_K + GJ_NB_HOST - 1) / GJ_NB_HOST) +
-                      (c->df32 && !c->tdse ? 2 : 0);
+                      (c->df32 ? (c->tdse ? 1 : 2) : 0);
     c->assembled = true;
     c->k = 0;
     c->parity = 0;
@@ -686,7 +691,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
         }
         CU(cudaEventRecord(c->evw0, c->stream));
         CU(launch_tdse_window(view(c), c->stream, c->d_boff, c->d_win_prev, nmax, c->cn_iters, c->max_K, c->max_kd,
-                              &win_launches));
+                              c->df32, &win_launches));
         CU(cudaEventRecord(c->evw1, c->stream));
         CU(cudaMemcpyAsync(c->d_win, wfix.data(), wfix.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     } else {
@@ -730,7 +735,9 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     {
         std::vector<int> nsolve(c->inst.size());
         for (size_t i = 0; i < ni; ++i) nsolve[i] = c->win_h[i];
-        const double per = c->tdse ? 8.0 : 2.0, bper = c->tdse ? 16.0 : 8.0;
+        // real time: (1 + fixed-point iterations) complex matvecs with G0 per step
+        const double sweeps = c->tdse ? 1.0 + c->cn_iters : 1.0;
+        const double per = (c->tdse ? 8.0 : 2.0) * sweeps, bper = (c->tdse ? 16.0 : 8.0) * sweeps;
         for (const SubDev& sd : c->sub) {
             double K2 = (double)sd.K * sd.K;
             flops += per * K2 * nsolve[sd.inst];

@@ -162,6 +162,99 @@ __global__ void k_cn_update(SwrDeviceView v, const long long* boff, int n) {
     }
 }
 
+__device__ inline void ds_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Double-single accumulation acc += g * x, g = (gh + gl), x = (xh + xl),
+// products and sums error-free on the FP32 pipes.
+__device__ inline void ds_mac(float& ah, float& al, float gh, float gl, float xh, float xl) {
+    float p = gh * xh, e = fmaf(gh, xh, -p), s, q;
+    ds_two_sum(ah, p, s, q);
+    ah = s;
+    al += (q + e) + fmaf(gh, xl, gl * xh);
+}
+
+// x = G0 u with G0 stored as four FP32 planes (re_hi, re_lo, im_hi, im_lo):
+// complex double-single matvec, FP64-level accuracy on the FP32 pipes.
+__global__ void __launch_bounds__(256) k_cmv_df32(SwrDeviceView v, const long long* boff) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const int K = s.K;
+    const int r0 = blockIdx.x * MV_ROWS;
+    if (r0 >= K) return;
+    extern __shared__ float smf[];
+    float* urh = smf;           // K
+    float* url = smf + K;
+    float* uih = smf + 2 * K;
+    float* uil = smf + 3 * K;
+    const double* U = v.arena + boff[3 * sid + 1];
+    for (int e = threadIdx.x; e < K; e += blockDim.x) {
+        double a = U[e], b = U[K + e];
+        float ah = (float)a, bh = (float)b;
+        urh[e] = ah;
+        url[e] = (float)(a - (double)ah);
+        uih[e] = bh;
+        uil[e] = (float)(b - (double)bh);
+    }
+    __syncthreads();
+    const long long KK = (long long)K * K;
+    const float* Grh = (const float*)(v.arena + s.Gf);
+    const float* Grl = Grh + KK;
+    const float* Gih = Grh + 2 * KK;
+    const float* Gil = Grh + 3 * KK;
+    double* X = v.arena + boff[3 * sid + 2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = r0 + warp; r < min(K, r0 + MV_ROWS); r += nw) {
+        const long long ro = (long long)r * K;
+        // re = Gr ur - Gi ui ; im = Gr ui + Gi ur
+        float reh = 0.f, rel = 0.f, imh = 0.f, iml = 0.f;
+        for (int c = lane; c < K; c += 32) {
+            const float grh = Grh[ro + c], grl = Grl[ro + c], gih = Gih[ro + c], gil = Gil[ro + c];
+            ds_mac(reh, rel, grh, grl, urh[c], url[c]);
+            ds_mac(reh, rel, -gih, -gil, uih[c], uil[c]);
+            ds_mac(imh, iml, grh, grl, uih[c], uil[c]);
+            ds_mac(imh, iml, gih, gil, urh[c], url[c]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float sh, eh;
+            float oh = __shfl_xor_sync(0xffffffffu, reh, o), ol = __shfl_xor_sync(0xffffffffu, rel, o);
+            ds_two_sum(reh, oh, sh, eh);
+            reh = sh;
+            rel = rel + ol + eh;
+            oh = __shfl_xor_sync(0xffffffffu, imh, o);
+            ol = __shfl_xor_sync(0xffffffffu, iml, o);
+            ds_two_sum(imh, oh, sh, eh);
+            imh = sh;
+            iml = iml + ol + eh;
+        }
+        if (lane == 0) {
+            X[r] = (double)reh + (double)rel;
+            X[K + r] = (double)imh + (double)iml;
+        }
+    }
+}
+
+// Complex G0 (interleaved doubles) -> four FP32 planes for the double-single matvec.
+__global__ void k_split_c_df32(SwrDeviceView v) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const long long KK = (long long)s.K * s.K;
+    const double* G = v.arena + s.Gm;
+    float* P = (float*)(v.arena + s.Gf);
+    for (long long e = threadIdx.x + (long long)blockIdx.x * blockDim.x; e < KK; e += (long long)blockDim.x * gridDim.x) {
+        double a = G[2 * e], b = G[2 * e + 1];
+        float ah = (float)a, bh = (float)b;
+        P[e] = ah;
+        P[KK + e] = (float)(a - (double)ah);
+        P[2 * KK + e] = bh;
+        P[3 * KK + e] = (float)(b - (double)bh);
+    }
+}
+
 // c^{n+1} = x - c^n
 __global__ void k_cn_finish(SwrDeviceView v, const long long* boff, int n) {
     const int sid = blockIdx.y;
@@ -187,8 +280,14 @@ static inline unsigned div_up(long long a, long long b) { return (unsigned)((a +
 
 // Launches of one real-time window: n_steps steps with `iters` fixed-point
 // iterations each; returns the number of kernel launches.
+cudaError_t launch_split_c_df32(const SwrDeviceView& v, cudaStream_t st, int max_K) {
+    long long kk = (long long)max_K * max_K;
+    k_split_c_df32<<<dim3((unsigned)((kk + 2047) / 2048), v.n_sub), 256, 0, st>>>(v);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const long long* d_boff, const int* d_win_prev,
-                               int n_steps, int iters, int max_K, int max_kd, long long* launches) {
+                               int n_steps, int iters, int max_K, int max_kd, bool df32, long long* launches) {
     const size_t sm_el = (2 * (size_t)max_K + 2 * (size_t)max_kd * max_kd) * sizeof(double);
     const size_t sm_mv = 2 * (size_t)max_K * sizeof(double);
     static bool attr_done = false;
@@ -196,6 +295,7 @@ cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const lo
         cudaFuncSetAttribute(k_cn_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         cudaFuncSetAttribute(k_cn_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         cudaFuncSetAttribute(k_cmv, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_cmv_df32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         attr_done = true;
     }
     const dim3 ge(div_up(max_K, CN_ROWS), v.n_sub), gm(div_up(max_K, MV_ROWS), v.n_sub), gf(div_up(2 * max_K, 256), v.n_sub);
@@ -204,10 +304,12 @@ cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const lo
     ++nl;
     for (int n = 0; n < n_steps; ++n) {
         k_cn_rhs<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, d_win_prev, n);
-        k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff);
+        if (df32) k_cmv_df32<<<gm, 256, sm_mv, st>>>(v, d_boff);
+        else k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff);
         for (int m = 0; m < iters; ++m) {
             k_cn_update<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, n);
-            k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff);
+            if (df32) k_cmv_df32<<<gm, 256, sm_mv, st>>>(v, d_boff);
+            else k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff);
         }
         k_cn_finish<<<gf, 256, 0, st>>>(v, d_boff, n);
         nl += 3 + 2 * iters;
