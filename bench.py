@@ -251,7 +251,8 @@ def main():
             dist.all_reduce(n, op=dist.ReduceOp.SUM)
             solves_all = int(n.item())
         d = {k: c1[k] - c0[k] for k in c1}
-        return dict(s=s, value=solves_all / (t_max * 1e-3), t_max=t_max, reps=reps, counters=d, clocks=clocks)
+        return dict(s=s, value=solves_all / (t_max * 1e-3), t_max=t_max, reps=reps, counters=d, clocks=clocks,
+                    plan=s.window_plan())
 
     main_run = timed(args.precision, args.steps, args.warmup, True)
     other = None
@@ -282,13 +283,14 @@ def main():
     elif args.precision == "mixed":
         # double-single matvec: ~12 FP32 operations per matrix element on the FP32 pipes
         peak = FP32_PEAK_TFLOPS / 6.0
-        roof = {"kernel": "k_window_df32", "bound": "alu", "achieved": achieved, "peak": peak,
+        kname = "k_window_fused" if main_run["plan"]["variant"] == S.WINDOW_FUSED else "k_window_2ph<true>"
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": "measured FP32 FMA rate of this pool's GB300 (67.7 TFLOP/s) / 6: the "
                                "double-single product-sum spends 12 FP32 operations per 2 FP64-equivalent flops",
                 "algorithmic": "2 K^2 FP64-equivalent flops per local step solve (matvec with the step-matrix inverse)"}
     else:
-        roof = {"kernel": "k_window_fp64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+        roof = {"kernel": "k_window_2ph<false>", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "FP64 FMA rate measured on this pool's GB300 (probe of independent FMA chains)",
                 "algorithmic": "2 K^2 flops per local step solve (FP64 matvec with the step-matrix inverse)"}

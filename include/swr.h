@@ -62,6 +62,35 @@ typedef enum swr_precision {
                             FP64 reductions, norms, orthogonalisation, inversion  */
 } swr_precision;
 
+/* How swr_step launches the kernels of one Schwarz iteration.  Both run the
+ * same kernels with the same arguments (bit-identical results).             */
+typedef enum swr_launch_mode {
+    SWR_LAUNCH_GRAPH = 0,      /* capture the iteration into a CUDA graph once
+                                  per kind (parity of the trace buffers, first
+                                  iteration) and replay it: one host launch per
+                                  iteration (if the driver refuses the capture,
+                                  the context launches directly; swr_window_plan
+                                  reports which)                                */
+    SWR_LAUNCH_DIRECT = 1      /* launch every kernel from the host             */
+} swr_launch_mode;
+
+/* Kernel that runs the imaginary-time window (Sec. 5.2, system SIT).  Both
+ * compute the same step; they differ in how the per-step normalisation is
+ * synchronised, and so in summation order (results agree to rounding).      */
+typedef enum swr_window_variant {
+    SWR_WINDOW_AUTO = 0,       /* fused when it fits (mixed precision), else
+                                  two-phase                                      */
+    SWR_WINDOW_TWO_PHASE = 1,  /* y = G v, grid barrier, z = (Pp (x) Pp) y, grid
+                                  barrier: G read once per step (8 bytes per
+                                  element in both precisions); any batch size
+                                  (task state in global memory when a CTA holds
+                                  more tasks than its shared memory)             */
+    SWR_WINDOW_FUSED = 2       /* mixed precision only: y = G v and z = W v with
+                                  W = (Pp (x) Pp) G precomputed, one grid barrier
+                                  per step (16 bytes per element); at most 4 row
+                                  tasks of at most 64 rows per CTA               */
+} swr_window_variant;
+
 /* One SWR problem: global box [box_lo, box_hi]^n_elec cut into L^n_elec
  * subdomains.  Subdomain sid = i1 + L*i2 covers, in coordinate e,
  * [a + i_e H - overlap/2, a + (i_e+1) H + overlap/2], H = (b-a)/L.          */
@@ -101,6 +130,10 @@ typedef struct swr_problem {
     void*               stream;       /* cudaStream_t (NULL: default stream)    */
     void*               workspace;    /* optional caller-owned device buffer    */
     size_t              workspace_bytes; /* >= swr_workspace_size() when given   */
+    int                 window_variant;  /* swr_window_variant (0: automatic)    */
+    int                 rows_per_task;   /* window row-task size: 0 (automatic) or
+                                            8..256; swr_autotune may change it   */
+    int                 launch_mode;     /* swr_launch_mode                        */
 } swr_problem;
 
 typedef struct swr_ctx swr_ctx;
@@ -247,6 +280,35 @@ const char* swr_mlp_last_error(const swr_mlp* mlp);
  * Returns SWR_ESTATE before the first swr_step.  The result equals
  * swr_get(SWR_FIELD_RES) of the same iteration. */
 swr_status swr_residual_noalloc(swr_ctx* ctx, double* res_host, size_t n);
+
+/* ----------------------------------------------------------------------------
+ * Window autotuner (no counterpart in the paper: a launch-configuration
+ * choice).  Times every candidate (window variant x row-task size:
+ * automatic, 16, 32, 64, 128, 256 rows; the fused variant only where its W was
+ * allocated, i.e. when the problem was set up with window_variant 0 or 2) on
+ * a fixed window of `steps` imaginary-time steps from the projected initial
+ * data, twice each, and keeps the fastest for all later swr_step calls.
+ * Call after swr_assemble and before the first swr_step (SWR_ESTATE
+ * otherwise); real-time problems have no window kernel (SWR_EINVAL).  The
+ * window state it writes is re-initialised by the first swr_step.  `out`
+ * (may be NULL) receives the choice.                                         */
+typedef struct swr_tune_report {
+    int    variant;          /* swr_window_variant chosen                       */
+    int    rows_per_task;    /* row-task target chosen                          */
+    int    tasks;            /* row tasks of the chosen plan                    */
+    int    ctas;             /* CTAs of the persistent launch                   */
+    int    task_state_global;/* 1: per-task state in global memory             */
+    int    candidates;       /* plans timed                                     */
+    int    graph;            /* 1: iterations replay a captured CUDA graph      */
+    double seconds_per_step; /* best time per window step                       */
+    double seconds_default;  /* time per step of the plan before tuning         */
+} swr_tune_report;
+swr_status swr_autotune(swr_ctx* ctx, int steps, swr_tune_report* out);
+
+/* The window plan in use (variant, rows_per_task, tasks, ctas,
+ * task_state_global, graph; the timing fields are zero).  variant is 0 for
+ * real-time problems, whose steps are launched from the host.               */
+swr_status swr_window_plan(const swr_ctx* ctx, swr_tune_report* out);
 
 void        swr_destroy(swr_ctx* ctx);
 const char* swr_last_error(const swr_ctx* ctx);

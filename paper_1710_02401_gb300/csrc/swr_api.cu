@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <string>
+#include <queue>
 #include <vector>
 
 #include "swr_internal.cuh"
@@ -20,12 +21,12 @@ namespace swr {
 cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, int max_kd, int max_K,
                             bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
                             const GemmJob* d_jobs2, double* d_norm_part, double tau);
-size_t window_smem(int kmax, int kdmax, int tasks_per_cta, long long g_resident_floats);
+size_t window_smem(int kmax, int kdmax, int rows_max, int tasks_in_smem, long long g_resident_floats);
 int window_tasks_per_cta_max();
 int window_rows_per_task_max();
-cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, bool df32);
-cudaError_t launch_split_df32(const SwrDeviceView& v, cudaStream_t st, int max_K);
-cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst, bool df32,
+cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, int variant, bool df32);
+cudaError_t launch_split_df32(const SwrDeviceView& v, cudaStream_t st, int max_K, bool make_w);
+cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst, int variant, bool df32,
                           cudaEvent_t ev_begin, cudaEvent_t ev_end);
 extern const int kAssembleLaunchesFixed, kStepLaunches;
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
@@ -68,6 +69,21 @@ struct swr_ctx {
     double* d_dipole = nullptr;
     std::vector<double> dipole_h;
     int nsm = 0, bps = 0, tasks_per_cta = 1, max_rows = 0;
+    // window plan: kernel variant, row-task target, CTA ranges, task state in global memory
+    int variant = WIN_TWO_PHASE, rows_target = 0, many = 0;
+    bool has_w = false;             // W = (Pp (x) Pp) G allocated (fused variant possible)
+    std::vector<int> cta_task0, cta_list;
+    long long tasks_cap = 0;        // capacity of the task arrays (row target 8)
+    int *d_cta_task0 = nullptr, *d_cta_list = nullptr;
+    // launch of one Schwarz iteration: a CUDA graph per (parity, first iteration), captured once
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    long long g_win_launches[2][2] = {{0, 0}, {0, 0}};
+    bool graph_failed = false;
+    int* d_wfix = nullptr;          // real time: the fixed window of every instance
+    TaskCache* d_tc = nullptr;
+    double *d_scal = nullptr, *d_own = nullptr;
+    int* d_alive = nullptr;
     // device memory
     void* base = nullptr;
     bool owns = false;
@@ -186,20 +202,40 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
     }
     if (p->precision != SWR_PREC_FP64 && p->precision != SWR_PREC_MIXED)
         return fail(c, SWR_EINVAL, "unknown precision");
+    if (p->window_variant < 0 || p->window_variant > SWR_WINDOW_FUSED)
+        return fail(c, SWR_EINVAL, "unknown window variant");
+    if (p->window_variant == SWR_WINDOW_FUSED && (p->precision != SWR_PREC_MIXED || mode0 != SWR_MODE_TISE))
+        return fail(c, SWR_EINVAL, "the fused window is the mixed-precision imaginary-time kernel");
+    if (p->launch_mode != SWR_LAUNCH_GRAPH && p->launch_mode != SWR_LAUNCH_DIRECT)
+        return fail(c, SWR_EINVAL, "unknown launch mode");
+    if (p->rows_per_task != 0 && (p->rows_per_task < 8 || p->rows_per_task > 256))
+        return fail(c, SWR_EINVAL, "rows_per_task must be 0 (automatic) or in [8, 256]");
     return SWR_OK;
 }
 
-// Row tasks of the window kernel: every subdomain's rows cut into equal blocks
-// so that the resident CTAs (blocks_per_sm x SMs) get the same number of rows.
-static void plan_tasks(swr_ctx* c) {
+static const int ROWS_MIN = 8;          // smallest row task
+static const int ROWS_MANY_MAX = 256;    // largest row task (task state in global memory)
+static const size_t WIN_SMEM_TASKS_MAX = 100 * 1024;  // dynamic shared memory for two CTAs per SM
+
+// Row tasks of the window kernel and their CTA ranges.  Every subdomain's rows
+// are cut into equal blocks of about `target_rows` rows (0: total rows over the
+// CTAs, at most 64); the tasks, in instance order, are dealt to `ctas` CTAs as
+// contiguous ranges of about equal cost (rows x (K + 64) plus a fixed per-task
+// overhead), so that uneven bases load the SMs evenly.
+static void plan_tasks(swr_ctx* c, int target_rows, int ctas) {
     c->tasks.clear();
     c->inst_task0.clear();
+    c->cta_task0.clear();
     long long rows = 0;
     for (const SubDev& s : c->sub) rows += s.K;
-    const int ctas = (c->nsm > 0 ? c->nsm : 152) * 2;
-    long long target = (rows + ctas - 1) / ctas;
-    if (target < 8) target = 8;
-    if (target > window_rows_per_task_max()) target = window_rows_per_task_max();
+    long long target = target_rows;
+    if (target <= 0) {
+        target = (rows + ctas - 1) / ctas;
+        if (target > window_rows_per_task_max()) target = window_rows_per_task_max();
+    }
+    if (target < ROWS_MIN) target = ROWS_MIN;
+    if (target > ROWS_MANY_MAX) target = ROWS_MANY_MAX;
+    c->rows_target = (int)target;
     c->max_rows = 0;
     long long own = 0;
     int cur_inst = -1;
@@ -218,7 +254,7 @@ static void plan_tasks(swr_ctx* c) {
             t.r1 = r0 + per < s.K ? r0 + per : s.K;
             t.inst = s.inst;
             t.own = own;
-            own += 4LL * (t.r1 - t.r0);
+            own += 6LL * (t.r1 - t.r0);
             if (t.r1 - t.r0 > c->max_rows) c->max_rows = t.r1 - t.r0;
             c->tasks.push_back(t);
         }
@@ -228,9 +264,73 @@ static void plan_tasks(swr_ctx* c) {
         ++cur_inst;
     }
     c->own_total = own;
+    // deal the tasks, in instance order, each to the least-loaded CTA (ties: the
+    // lowest index): loads end up balanced and every instance's rows spread
+    // over the SMs, so the instances whose windows run longest still use the
+    // whole GPU after the others have stopped
     const int nt = (int)c->tasks.size();
-    c->tasks_per_cta = (nt + ctas - 1) / ctas;
-    if (c->tasks_per_cta < 1) c->tasks_per_cta = 1;
+    const int g = nt < ctas ? nt : ctas;
+    typedef std::pair<double, int> Load;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int b = 0; b < g; ++b) heap.push(Load(0.0, b));
+    std::vector<std::vector<int>> per(g);
+    for (int t = 0; t < nt; ++t) {
+        const Task& tk = c->tasks[t];
+        const double cost = (double)(tk.r1 - tk.r0) * (c->sub[tk.sid].K + 64) + 16384.0;
+        Load l = heap.top();
+        heap.pop();
+        per[l.second].push_back(t);
+        heap.push(Load(l.first + cost, l.second));
+    }
+    c->grid = g;
+    c->cta_task0.assign(1, 0);
+    c->cta_list.clear();
+    c->tasks_per_cta = 1;
+    for (int b = 0; b < g; ++b) {
+        c->cta_list.insert(c->cta_list.end(), per[b].begin(), per[b].end());
+        c->cta_task0.push_back((int)c->cta_list.size());
+        if ((int)per[b].size() > c->tasks_per_cta) c->tasks_per_cta = (int)per[b].size();
+    }
+}
+
+// Task capacity of the auxiliary arrays: the finest row target.
+static long long task_capacity(const swr_ctx* c) {
+    long long n = 0;
+    for (const SubDev& s : c->sub) n += (s.K + ROWS_MIN - 1) / ROWS_MIN;
+    return n;
+}
+
+// Window plan for a requested variant (0: automatic) and row target (0:
+// automatic): the tasks, whether their state fits shared memory, the dynamic
+// shared memory and the CTAs per SM.  Returns false when the request cannot be
+// met (fused variant without W, or fused with task state in global memory).
+static bool plan_window(swr_ctx* c, int variant_req, int rows_req, bool have_dev) {
+    const int nsm = c->nsm > 0 ? c->nsm : 152;
+    for (int per_sm = 2; per_sm >= 1; --per_sm) {
+        plan_tasks(c, rows_req, per_sm * nsm);
+        const bool fits = c->tasks_per_cta <= window_tasks_per_cta_max() && c->max_rows <= window_rows_per_task_max() &&
+                          window_smem(c->max_K, c->max_kd, c->max_rows, c->tasks_per_cta, 0) <= WIN_SMEM_TASKS_MAX;
+        int variant = variant_req;
+        if (variant == 0) variant = (c->df32 && c->has_w && fits) ? WIN_FUSED : WIN_TWO_PHASE;
+        if (variant == WIN_FUSED && (!c->df32 || !c->has_w || !fits)) return false;
+        c->variant = variant;
+        c->many = fits ? 0 : 1;
+        const long long gres_floats = (long long)c->max_rows * df32_ld(c->max_K);
+        c->g_resident = variant == WIN_FUSED && c->tasks_per_cta == 1 &&
+                        window_smem(c->max_K, c->max_kd, c->max_rows, 1, gres_floats) <= 110 * 1024;
+        c->win_smem = window_smem(c->max_K, c->max_kd, c->max_rows, c->many ? 1 : c->tasks_per_cta,
+                                  c->g_resident ? gres_floats : 0);
+        c->bps = per_sm;
+        if (!have_dev) return true;
+        int bps = 0;
+        if (window_occupancy(&bps, c->win_smem, c->variant, c->df32) != cudaSuccess) {
+            cudaGetLastError();
+            bps = 0;
+        }
+        if (bps >= per_sm) return true;
+        c->bps = bps;
+    }
+    return true;  // bps < 1 is reported by swr_setup
 }
 
 // Fill descriptors and offsets; returns arena size (doubles) and aux bytes.
@@ -360,16 +460,8 @@ static void plan(swr_ctx* c) {
                     off = align32(off + 2LL * K);
                 }
             }
-            if (c->df32 && c->tdse) {
-                s.Gf = off; off = align32(off + 2LL * K * K);  // four FP32 planes of the complex G0
-                s.Wf = 0;
-            } else if (c->df32) {
-                s.Gf = off; off = align32(off + (long long)K * K);
-                s.Wf = off; off = align32(off + (long long)K * K);
-            } else {
-                s.Gf = 0;
-                s.Wf = 0;
-            }
+            s.Gf = 0;
+            s.Wf = 0;
             c->psi_off.push_back(po);
             po += (d.N == 2) ? (long long)q * q : q;
             if (K > c->max_K) c->max_K = K;
@@ -379,21 +471,41 @@ static void plan(swr_ctx* c) {
             c->sub.push_back(s);
         }
     }
+    // Mixed precision: FP32 planes of the step matrix, and W = (Pp (x) Pp) G when
+    // the fused single-barrier window can run (task state in shared memory).
+    c->has_w = false;
+    if (c->df32 && !c->tdse && p.window_variant != WIN_TWO_PHASE) {
+        plan_tasks(c, p.rows_per_task, 2 * (c->nsm > 0 ? c->nsm : 152));
+        c->has_w = p.window_variant == WIN_FUSED ||
+                   (c->tasks_per_cta <= window_tasks_per_cta_max() && c->max_rows <= window_rows_per_task_max() &&
+                    window_smem(c->max_K, c->max_kd, c->max_rows, c->tasks_per_cta, 0) <= WIN_SMEM_TASKS_MAX);
+    }
+    for (SubDev& s : c->sub) {
+        const long long K = s.K;
+        if (c->df32 && c->tdse) {
+            s.Gf = off; off = align32(off + 2LL * K * K);  // four FP32 planes of the complex G0
+        } else if (c->df32) {
+            s.Gf = off; off = align32(off + K * df32_ld((int)K));  // G_hi, G_lo planes [K][ldg]
+            if (c->has_w) {
+                s.Wf = off; off = align32(off + K * K);    // W_hi, W_lo planes
+            }
+        }
+    }
     c->arena_doubles = (size_t)off;
     c->psi_total = po;
-    plan_tasks(c);
 }
 
 // Auxiliary device arrays carved after the arena (bytes, 256-aligned).
 struct AuxPlan {
-    size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, snorm, sums_s, sums_d,
+    size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, cta0, tc, scal, alive, own,
+        ctal, wfix, snorm, sums_s, sums_d,
         n_active, win, win_prev, bar, res_part, res, epart, energy, norm2, dipole, boff, psi, psi_off, total;
 };
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 static AuxPlan aux_plan(const swr_ctx* c) {
     AuxPlan a;
     size_t o = al256(c->arena_doubles * sizeof(double));
-    const size_t ni = c->inst.size(), ns = c->sub.size(), nt = c->tasks.size();
+    const size_t ni = c->inst.size(), ns = c->sub.size(), nt = (size_t)c->tasks_cap;
     a.inst = o; o = al256(o + ni * sizeof(InstDev));
     a.sub = o; o = al256(o + ns * sizeof(SubDev));
     a.err = o; o = al256(o + sizeof(int) * 4);
@@ -404,6 +516,13 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.task0 = o; o = al256(o + (ni + 1) * sizeof(int));
     a.part_s = o; o = al256(o + 2 * nt * sizeof(double));
     a.part_d = o; o = al256(o + 2 * nt * sizeof(double));
+    a.cta0 = o; o = al256(o + (2 * (size_t)(c->nsm > 0 ? c->nsm : 152) + 1) * sizeof(int));
+    a.ctal = o; o = al256(o + nt * sizeof(int));
+    a.wfix = o; o = al256(o + ni * sizeof(int));
+    a.tc = o; o = al256(o + nt * sizeof(TaskCache));
+    a.scal = o; o = al256(o + 4 * ni * sizeof(double));
+    a.alive = o; o = al256(o + nt * sizeof(int));
+    a.own = o; o = al256(o + (size_t)c->own_total * sizeof(double));
     a.snorm = o; o = al256(o + ni * (size_t)(c->cap + 1) * sizeof(double));
     a.sums_s = o; o = al256(o + ni * sizeof(double));
     a.sums_d = o; o = al256(o + ni * sizeof(double));
@@ -426,7 +545,7 @@ static AuxPlan aux_plan(const swr_ctx* c) {
 
 // Layout for the current device: the row tasks depend on the SM count and on
 // how many window CTAs fit per SM (two at most; 152 x 2 without a device).
-static void plan_for_device(swr_ctx* c, const swr_problem* p) {
+static bool plan_for_device(swr_ctx* c, const swr_problem* p) {
     c->df32 = (p->precision == SWR_PREC_MIXED);
     int dev = 0;
     bool have_dev = cudaGetDevice(&dev) == cudaSuccess &&
@@ -435,23 +554,12 @@ static void plan_for_device(swr_ctx* c, const swr_problem* p) {
         cudaGetLastError();
         c->nsm = 152;
     }
-    plan(c);  // descriptors, arena and the row tasks for 2 CTAs per SM
+    plan(c);  // descriptors and arena
+    c->tasks_cap = task_capacity(c);
     c->any_ngf_stop = false;
     for (const InstDev& d : c->inst)
         if (d.window_cap == 0 && d.ngf_tol > 0.0) c->any_ngf_stop = true;
-    // keep the CTA's rows of G_hi in shared memory when one task per CTA fits twice per SM
-    c->g_resident = c->df32 && c->tasks_per_cta == 1;
-    c->win_smem = window_smem(c->max_K, c->max_kd, c->tasks_per_cta,
-                              c->g_resident ? (long long)c->max_rows * c->max_K : 0);
-    c->bps = 2;
-    if (have_dev) {
-        if (c->win_smem > 110 * 1024) {
-            c->g_resident = false;
-            c->win_smem = window_smem(c->max_K, c->max_kd, c->tasks_per_cta, 0);
-        }
-        if (window_occupancy(&c->bps, c->win_smem, c->df32) != cudaSuccess) c->bps = 0;
-        if (c->bps > 2) c->bps = 2;
-    }
+    return plan_window(c, p->window_variant, p->rows_per_task, have_dev);
 }
 
 static swr_status copy_problem(swr_ctx* c, const swr_problem* p) {
@@ -478,13 +586,33 @@ static swr_status copy_problem(swr_ctx* c, const swr_problem* p) {
     return SWR_OK;
 }
 
+// Row tasks, instance and CTA ranges to the device (stream-ordered).
+static cudaError_t upload_tasks(swr_ctx* c) {
+    cudaError_t e = cudaMemcpyAsync(c->d_tasks, c->tasks.data(), c->tasks.size() * sizeof(Task),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_inst_task0, c->inst_task0.data(), c->inst_task0.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_cta_task0, c->cta_task0.data(), c->cta_task0.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_cta_list, c->cta_list.data(), c->cta_list.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, c->stream);
+    c->counters[8] += (double)(c->tasks.size() * sizeof(Task) +
+                               (c->inst_task0.size() + c->cta_task0.size() + c->cta_list.size()) * sizeof(int));
+    return e;
+}
+
 extern "C" swr_status swr_workspace_size(const swr_problem* p, size_t* bytes) {
     if (!bytes) return fail(nullptr, SWR_EINVAL, "bytes is NULL");
     swr_status st = validate(nullptr, p);
     if (st != SWR_OK) return st;
     swr_ctx tmp;
     copy_problem(&tmp, p);
-    plan_for_device(&tmp, p);
+    if (!plan_for_device(&tmp, p))
+        return fail(nullptr, SWR_EINVAL, "the fused window needs mixed precision and at most %d row tasks of at most "
+                    "%d rows per CTA", window_tasks_per_cta_max(), window_rows_per_task_max());
     *bytes = aux_plan(&tmp).total;
     return SWR_OK;
 }
@@ -496,7 +624,11 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     if (st != SWR_OK) return st;
     swr_ctx* c = new swr_ctx();
     copy_problem(c, p);
-    plan_for_device(c, p);
+    if (!plan_for_device(c, p)) {
+        delete c;
+        return fail(nullptr, SWR_EINVAL, "the fused window needs mixed precision and at most %d row tasks of at most "
+                    "%d rows per CTA", window_tasks_per_cta_max(), window_rows_per_task_max());
+    }
     AuxPlan a = aux_plan(c);
     c->stream = (cudaStream_t)p->stream;
     if (p->workspace) {
@@ -530,6 +662,13 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->d_inst_task0 = (int*)(b + a.task0);
     c->d_part_s = (double*)(b + a.part_s);
     c->d_part_d = (double*)(b + a.part_d);
+    c->d_cta_task0 = (int*)(b + a.cta0);
+    c->d_cta_list = (int*)(b + a.ctal);
+    c->d_wfix = (int*)(b + a.wfix);
+    c->d_tc = (TaskCache*)(b + a.tc);
+    c->d_scal = (double*)(b + a.scal);
+    c->d_alive = (int*)(b + a.alive);
+    c->d_own = (double*)(b + a.own);
     c->d_snorm = (double*)(b + a.snorm);
     c->d_sums_s = (double*)(b + a.sums_s);
     c->d_sums_d = (double*)(b + a.sums_d);
@@ -570,13 +709,14 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     CU(cudaMemcpyAsync(c->d_sub, c->sub.data(), c->sub.size() * sizeof(SubDev), cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->d_jobs1, j1.data(), j1.size() * sizeof(GemmJob), cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->d_jobs2, j2.data(), j2.size() * sizeof(GemmJob), cudaMemcpyHostToDevice, c->stream));
-    CU(cudaMemcpyAsync(c->d_tasks, c->tasks.data(), c->tasks.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream));
-    CU(cudaMemcpyAsync(c->d_inst_task0, c->inst_task0.data(), c->inst_task0.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CU(upload_tasks(c));
+    std::vector<int> wfix(c->inst.size());
+    for (size_t i = 0; i < c->inst.size(); ++i) wfix[i] = c->inst[i].window_cap;
+    CU(cudaMemcpyAsync(c->d_wfix, wfix.data(), wfix.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(c->d_psi_off, c->psi_off.data(), c->psi_off.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
     if (!c->boff.empty())
         CU(cudaMemcpyAsync(c->d_boff, c->boff.data(), c->boff.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
-    c->counters[8] += (double)(c->inst.size() * sizeof(InstDev) + c->sub.size() * (sizeof(SubDev) + 2 * sizeof(GemmJob) + sizeof(long long)) +
-                               c->tasks.size() * sizeof(Task) + c->inst_task0.size() * sizeof(int));
+    c->counters[8] += (double)(c->inst.size() * sizeof(InstDev) + c->sub.size() * (sizeof(SubDev) + 2 * sizeof(GemmJob) + sizeof(long long)));
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
     CU(cudaMemsetAsync(c->d_win_prev, 0, c->inst.size() * sizeof(int), c->stream));
     CU(cudaMemsetAsync(c->d_win, 0, c->inst.size() * sizeof(int), c->stream));
@@ -586,11 +726,6 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     CU(cudaEventCreate(&c->evw1));
     // persistent grid for the window kernel: all CTAs must be co-resident
     if (c->bps < 1 || c->nsm < 1) return fail(c, SWR_EINVAL, "window kernel does not fit on an SM");
-    if (c->tasks_per_cta > window_tasks_per_cta_max())
-        return fail(c, SWR_EINVAL, "problem has %zu row tasks: more than %d per CTA for the window kernel",
-                    c->tasks.size(), window_tasks_per_cta_max());
-    int nt = (int)c->tasks.size();
-    c->grid = (nt + c->tasks_per_cta - 1) / c->tasks_per_cta;
     if (c->grid > c->bps * c->nsm)
         return fail(c, SWR_EINVAL, "window grid of %d CTAs exceeds %d resident CTAs", c->grid, c->bps * c->nsm);
     c->res_h.assign(c->inst.size(), 0.0);
@@ -632,7 +767,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     CU(cudaEventRecord(c->ev0, c->stream));
     CU(launch_assemble(view(c), c->stream, c->max_q, c->max_kd, c->max_K, c->any_ee, c->tdse, !c->tdse,
                        c->d_jobs1, c->d_jobs2, c->d_norm_part, CHOL_TAU));
-    if (c->df32 && !c->tdse) CU(launch_split_df32(view(c), c->stream, c->max_K));
+    if (c->df32 && !c->tdse) CU(launch_split_df32(view(c), c->stream, c->max_K, c->has_w));
     if (c->df32 && c->tdse) CU(launch_split_c_df32(view(c), c->stream, c->max_K));
     CU(cudaEventRecord(c->ev1, c->stream));
     swr_status st = check_err(c);
@@ -641,7 +776,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     CU(cudaEventElapsedTime(&ams, c->ev0, c->ev1));
     c->counters[6] += ams;
     c->counters[2] += kAssembleLaunchesFixed + (c->any_ee ? 3 : 0) + 2 * ((c->max_K + GJ_NB_HOST - 1) / GJ_NB_HOST) +
-                      (c->df32 ? (c->tdse ? 1 : 2) : 0);
+                      (c->df32 ? (c->tdse || !c->has_w ? 1 : 2) : 0);
     c->assembled = true;
     c->k = 0;
     c->parity = 0;
@@ -654,10 +789,19 @@ static SweepArgs sweep_args(swr_ctx* c) {
     SweepArgs a;
     a.v = view(c);
     a.tasks = c->d_tasks;
+    a.cta_task0 = c->d_cta_task0;
+    a.cta_list = c->d_cta_list;
     a.n_tasks = (int)c->tasks.size();
     a.tasks_per_cta = c->tasks_per_cta;
     a.kmax = c->max_K;
     a.kdmax = c->max_kd;
+    a.rows_max = c->max_rows;
+    a.many = c->many;
+    a.tune_steps = 0;
+    a.g_tc = c->d_tc;
+    a.scal_inst = c->d_scal;
+    a.g_alive = c->d_alive;
+    a.g_own = c->d_own;
     a.g_resident = c->g_resident ? 1 : 0;
     a.any_ngf_stop = c->any_ngf_stop ? 1 : 0;
     a.inst_task0 = c->d_inst_task0;
@@ -675,34 +819,87 @@ static SweepArgs sweep_args(swr_ctx* c) {
     return a;
 }
 
+// Every launch of one Schwarz iteration (Sec. 5.4 steps 1-5) on stream st:
+// the time window, line traces, averaged Robin data, residual, energy.
+static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_launches) {
+    cudaError_t e = cudaSuccess;
+    *win_launches = 1;
+    if (c->tdse) {
+        // real time: fixed window of n_steps Crank-Nicolson steps
+        int nmax = 0;
+        for (size_t i = 0; i < c->inst.size(); ++i) nmax = c->inst[i].window_cap > nmax ? c->inst[i].window_cap : nmax;
+        e = record_event(c->evw0, st);
+        if (e == cudaSuccess)
+            e = launch_tdse_window(view(c), st, c->d_boff, c->d_win_prev, nmax, c->cn_iters, c->max_K, c->max_kd,
+                                   c->df32, win_launches);
+        if (e == cudaSuccess) e = record_event(c->evw1, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->d_win, c->d_wfix, c->inst.size() * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    } else {
+        SweepArgs a = sweep_args(c);
+        e = launch_window(a, c->grid, c->win_smem, st, (int)c->inst.size(), c->variant, c->df32, c->evw0, c->evw1);
+    }
+    if (e == cudaSuccess)
+        e = launch_post(view(c), st, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
+                        c->d_res_part, RES_BLOCKS, c->d_res, c->cap);
+    if (e == cudaSuccess)
+        e = launch_energy(view(c), st, c->d_win, c->d_snorm, c->cap, c->d_epart, c->d_energy, c->d_norm2,
+                          c->d_dipole, c->d_psi, c->d_psi_off, c->max_K, c->max_kd, c->max_q);
+    return e;
+}
+
+static void drop_graphs(swr_ctx* c) {
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < 2; ++f)
+            if (c->gexec[p][f]) {
+                cudaGraphExecDestroy(c->gexec[p][f]);
+                c->gexec[p][f] = nullptr;
+            }
+}
+
+// Captures the iteration for the current (parity, first) once; later
+// iterations of the same kind replay it with one cudaGraphLaunch.
+static cudaError_t capture_iteration(swr_ctx* c, int p, int f) {
+    cudaError_t e = cudaSuccess;
+    if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    long long wl = 1;
+    cudaError_t er = record_iteration(c, c->cap_stream, &wl);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (er != cudaSuccess) e = er;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[p][f], g, 0ULL);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec[p][f] = nullptr;
+        return e;
+    }
+    c->g_win_launches[p][f] = wl;
+    return cudaSuccess;
+}
+
 extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     if (!c) return fail(nullptr, SWR_EINVAL, "ctx is NULL");
     if (!c->assembled) return fail(c, SWR_ESTATE, "swr_step before swr_assemble");
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
+    const int gp = c->parity, gf = c->k == 0 ? 1 : 0;
+    if (c->prob.launch_mode == SWR_LAUNCH_GRAPH && !c->graph_failed && !c->gexec[gp][gf]) {
+        // a capture the driver refuses leaves the context on direct launches
+        if (capture_iteration(c, gp, gf) != cudaSuccess) {
+            cudaGetLastError();
+            c->graph_failed = true;
+        }
+    }
     CU(cudaEventRecord(c->ev0, c->stream));
     long long win_launches = 1;
-    if (c->tdse) {
-        // real time: fixed window of n_steps Crank-Nicolson steps, launched from the host
-        std::vector<int> wfix(c->inst.size());
-        int nmax = 0;
-        for (size_t i = 0; i < c->inst.size(); ++i) {
-            wfix[i] = c->inst[i].window_cap;
-            nmax = wfix[i] > nmax ? wfix[i] : nmax;
-        }
-        CU(cudaEventRecord(c->evw0, c->stream));
-        CU(launch_tdse_window(view(c), c->stream, c->d_boff, c->d_win_prev, nmax, c->cn_iters, c->max_K, c->max_kd,
-                              c->df32, &win_launches));
-        CU(cudaEventRecord(c->evw1, c->stream));
-        CU(cudaMemcpyAsync(c->d_win, wfix.data(), wfix.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    if (c->gexec[gp][gf]) {
+        CU(cudaGraphLaunch(c->gexec[gp][gf], c->stream));
+        win_launches = c->g_win_launches[gp][gf];
     } else {
-        SweepArgs a = sweep_args(c);
-        int grid = c->grid;
-        CU(launch_window(a, grid, c->win_smem, c->stream, (int)c->inst.size(), c->df32, c->evw0, c->evw1));
+        CU(record_iteration(c, c->stream, &win_launches));
     }
-    CU(launch_post(view(c), c->stream, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
-                   c->d_res_part, RES_BLOCKS, c->d_res, c->cap));
-    CU(launch_energy(view(c), c->stream, c->d_win, c->d_snorm, c->cap, c->d_epart, c->d_energy, c->d_norm2,
-                     c->d_dipole, c->d_psi, c->d_psi_off, c->max_K, c->max_kd, c->max_q));
     CU(cudaEventRecord(c->ev1, c->stream));
     const size_t ni = c->inst.size();
     CU(cudaMemcpyAsync(c->res_h.data(), c->d_res, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -737,7 +934,10 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
         for (size_t i = 0; i < ni; ++i) nsolve[i] = c->win_h[i];
         // real time: (1 + fixed-point iterations) complex matvecs with G0 per step
         const double sweeps = c->tdse ? 1.0 + c->cn_iters : 1.0;
-        const double per = (c->tdse ? 8.0 : 2.0) * sweeps, bper = (c->tdse ? 16.0 : 8.0) * sweeps;
+        // bytes per matrix element: complex G0 16 (FP64 pair or four FP32 planes);
+        // real G 8 (FP64 or FP32 hi/lo); the fused variant also streams W (16)
+        const double bel = c->tdse ? 16.0 : (c->variant == WIN_FUSED ? 16.0 : 8.0);
+        const double per = (c->tdse ? 8.0 : 2.0) * sweeps, bper = bel * sweeps;
         for (const SubDev& sd : c->sub) {
             double K2 = (double)sd.K * sd.K;
             flops += per * K2 * nsolve[sd.inst];
@@ -759,6 +959,97 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
         rep->seconds = ms * 1e-3;
     }
     return SWR_OK;
+}
+
+// Times the current window plan on a fixed window of `steps` steps (best of two).
+static swr_status time_window_plan(swr_ctx* c, int steps, double* sec_per_step) {
+    CU(upload_tasks(c));
+    SweepArgs a = sweep_args(c);
+    a.tune_steps = steps;
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+        CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
+        CU(launch_window(a, c->grid, c->win_smem, c->stream, (int)c->inst.size(), c->variant, c->df32, c->evw0,
+                         c->evw1));
+        c->counters[2] += 2;
+        swr_status st = check_err(c);
+        if (st != SWR_OK) return st;
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, c->evw0, c->evw1));
+        best = ms < best ? ms : best;
+    }
+    *sec_per_step = 1e-3 * best / steps;
+    return SWR_OK;
+}
+
+extern "C" swr_status swr_window_plan(const swr_ctx* c, swr_tune_report* out) {
+    if (!c || !out) return fail(nullptr, SWR_EINVAL, "ctx or out is NULL");
+    memset(out, 0, sizeof(*out));
+    out->variant = c->tdse ? 0 : c->variant;
+    out->rows_per_task = c->rows_target;
+    out->tasks = (int)c->tasks.size();
+    out->ctas = c->grid;
+    out->task_state_global = c->many;
+    out->graph = (c->prob.launch_mode == SWR_LAUNCH_GRAPH && !c->graph_failed) ? 1 : 0;
+    return SWR_OK;
+}
+
+extern "C" swr_status swr_autotune(swr_ctx* c, int steps, swr_tune_report* out) {
+    if (!c) return fail(nullptr, SWR_EINVAL, "ctx is NULL");
+    if (c->tdse) return fail(c, SWR_EINVAL, "real-time problems have no window kernel to tune");
+    if (!c->assembled || c->k != 0) return fail(c, SWR_ESTATE, "swr_autotune needs swr_assemble and no swr_step yet");
+    if (steps < 2 || steps > c->cap) return fail(c, SWR_EINVAL, "steps must be in [2, %d]", c->cap);
+    struct Cand {
+        int variant, rows;
+    };
+    std::vector<Cand> cands;
+    cands.push_back({c->prob.window_variant, c->prob.rows_per_task});  // the plan before tuning
+    const int rows_list[] = {0, 16, 32, 64, 128, 256};
+    const int variants[] = {WIN_TWO_PHASE, WIN_FUSED};
+    for (int v : variants) {
+        if (v == WIN_FUSED && !(c->df32 && c->has_w)) continue;
+        for (int r : rows_list) cands.push_back({v, r});
+    }
+    std::vector<std::vector<int>> seen;  // (variant, tasks, grid, rows target) of the plans timed
+    double best_t = 1e30, t_default = 0;
+    Cand best = cands[0];
+    int timed = 0;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        if (!plan_window(c, cands[i].variant, cands[i].rows, true)) continue;
+        if (c->bps < 1 || c->grid > c->bps * c->nsm) continue;
+        std::vector<int> sig = {c->variant, (int)c->tasks.size(), c->grid, c->rows_target};
+        bool dup = false;
+        for (const auto& x : seen) dup = dup || x == sig;
+        if (dup) continue;
+        seen.push_back(sig);
+        double t = 0;
+        swr_status st = time_window_plan(c, steps, &t);
+        if (st != SWR_OK) return st;
+        ++timed;
+        if (i == 0) t_default = t;
+        if (t < best_t) {
+            best_t = t;
+            best = {c->variant, c->rows_target};
+        }
+    }
+    drop_graphs(c);  // captured with the old plan's launch configuration
+    if (!plan_window(c, best.variant, best.rows, true) || c->bps < 1 || c->grid > c->bps * c->nsm)
+        return fail(c, SWR_EINVAL, "autotune: the chosen plan no longer fits");
+    CU(upload_tasks(c));
+    c->prob.window_variant = best.variant;
+    c->prob.rows_per_task = best.rows;
+    if (out) {
+        out->variant = c->variant;
+        out->rows_per_task = c->rows_target;
+        out->tasks = (int)c->tasks.size();
+        out->ctas = c->grid;
+        out->task_state_global = c->many;
+        out->candidates = timed;
+        out->graph = (c->prob.launch_mode == SWR_LAUNCH_GRAPH && !c->graph_failed) ? 1 : 0;
+        out->seconds_per_step = best_t;
+        out->seconds_default = t_default;
+    }
+    return check_err(c);
 }
 
 extern "C" swr_status swr_iterate(swr_ctx* c, double tol, int kmax, swr_report* rep, double* hist) {
@@ -971,6 +1262,8 @@ extern "C" void swr_destroy(swr_ctx* c) {
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->evw0) cudaEventDestroy(c->evw0);
     if (c->evw1) cudaEventDestroy(c->evw1);
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->owns && c->base) cudaFree(c->base);
     delete c;
 }

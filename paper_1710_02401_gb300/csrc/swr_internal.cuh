@@ -156,13 +156,45 @@ struct GemmJob {
 // Row block [r0, r1) of the step matrix of subdomain sid (persistent task).
 struct Task {
     int sid, r0, r1, inst;
-    long long own;              // offset of the task's ring [4][r1-r0] in SweepArgs::own
+    long long own;              // offset of the task's ring [6][r1-r0] in SweepArgs::g_own
 };
+
+// Leading dimension of the real step matrix's FP32 planes (mixed precision):
+// K rounded up to 4 columns, zero-padded, so that every row starts on 16 bytes.
+__host__ __device__ inline int df32_ld(int K) { return (K + 3) & ~3; }
+
+// Constants of one row task, gathered once per window.
+struct TaskCache {
+    int inst, sid, r0, nr, K, kd, N, t0, first, maxs, ngf_stop, normalize;
+    long long hist, bvec, Gm, Gf, Wf, c0, p1, p2, own;
+    double kdt, ngf_tol;
+};
+
+// Window kernel variants.
+enum WindowVariant { WIN_TWO_PHASE = 1, WIN_FUSED = 2 };
+
+// Event record that becomes an event-record node of the graph under stream
+// capture (external record) and is a plain record otherwise.
+inline cudaError_t record_event(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, st);
+}
 
 struct SweepArgs {
     SwrDeviceView v;
     const Task* tasks;
-    int n_tasks, tasks_per_cta, kmax, kdmax;
+    const int* cta_task0;       // [grid+1] first position of each CTA in cta_list
+    const int* cta_list;        // [n_tasks] task indices, CTA by CTA (cost-balanced, instances spread)
+    int n_tasks, tasks_per_cta, kmax, kdmax, rows_max;
+    int many;                   // per-task state in global memory (more tasks per CTA than shared memory holds)
+    int tune_steps;             // > 0: fixed window of this many steps without the NGF stop (timing runs)
+    TaskCache* g_tc;            // [n_tasks] by position in cta_list (many)
+    double* scal_inst;          // [2][2][n_inst] s_n and 1/s_n per instance, by step parity (two-phase)
+    int* g_alive;               // [n_tasks] by position (many)
+    double* g_own;              // [sum of 6 x task rows] (many)
     int g_resident;             // mixed precision: G_hi rows of the CTA's task kept in shared memory
     int any_ngf_stop;           // some instance stops its window on ||c^{n+1} - c^n||
     const int* inst_task0;      // [n_inst+1] first task of each instance

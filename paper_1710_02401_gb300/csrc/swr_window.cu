@@ -65,10 +65,13 @@ __device__ inline double wblock_sum(double x, double* red) {
 // partials to part[]; the CTA whose arrival completes the count sums them per
 // instance in task order into sums[], then publishes 2*gen + go on the release
 // word, go = 0 when `nact` (if given) shows that no instance is still stepping.
+// With scal_out it also stores s = sqrt(sum) (1 without normalisation) and 1/s
+// per instance: scal_out[i], scal_out[n_inst + i].
 // Bounded waits; returns false on error, *go_out receives go.
 __device__ bool reduce_barrier(unsigned* count, unsigned* release, unsigned target, unsigned gen, bool reduce,
                                const double* part, const int* inst_task0, int n_inst, double* sums, int* err,
-                               long long limit, double* red, const int* nact, int* go_out) {
+                               long long limit, double* red, const int* nact, int* go_out,
+                               const InstDev* inst = nullptr, double* scal_out = nullptr) {
     __shared__ int s_last, s_ok, s_go;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -90,11 +93,25 @@ __device__ bool reduce_barrier(unsigned* count, unsigned* release, unsigned targ
                     if (threadIdx.x == 0) sums[i] = x;
                 }
             } else {
-                for (int i = threadIdx.x; i < n_inst; i += WIN_THREADS) {
+                // one warp per instance: lanes stride over its tasks, fixed-order shuffle sum
+                const int lane = threadIdx.x & 31;
+                for (int i = threadIdx.x >> 5; i < n_inst; i += WIN_THREADS / 32) {
                     double x = 0;
-                    for (int u = inst_task0[i]; u < inst_task0[i + 1]; ++u) x += __ldcg(part + u);
-                    sums[i] = x;
+#pragma unroll 4
+                    for (int u = inst_task0[i] + lane; u < inst_task0[i + 1]; u += 32) x += __ldcg(part + u);
+                    x = warp_sum(x);
+                    if (lane == 0) sums[i] = x;
                 }
+            }
+        }
+        if (scal_out) {
+            // s_n = sqrt(s_n^2) and 1/s_n once per instance (FP64 square root and
+            // division are slow sequences: here instead of in every task)
+            __syncthreads();
+            for (int i = threadIdx.x; i < n_inst; i += WIN_THREADS) {
+                const double sn = inst[i].normalize ? sqrt(sums[i]) : 1.0;
+                scal_out[i] = sn;
+                scal_out[n_inst + i] = 1.0 / sn;
             }
         }
         __syncthreads();
@@ -151,14 +168,20 @@ __device__ bool reduce_barrier2(unsigned* count, unsigned* release, unsigned tar
                 }
             }
         } else {
-            for (int i = threadIdx.x; i < n_inst; i += WIN_THREADS) {
+            const int lane = threadIdx.x & 31;
+            for (int i = threadIdx.x >> 5; i < n_inst; i += WIN_THREADS / 32) {
                 double xa = 0, xb = 0;
-                for (int u = inst_task0[i]; u < inst_task0[i + 1]; ++u) {
+#pragma unroll 4
+                for (int u = inst_task0[i] + lane; u < inst_task0[i + 1]; u += 32) {
                     xa += __ldcg(part_a + u);
                     xb += __ldcg(part_b + u);
                 }
-                sums_a[i] = xa;
-                sums_b[i] = xb;
+                xa = warp_sum(xa);
+                xb = warp_sum(xb);
+                if (lane == 0) {
+                    sums_a[i] = xa;
+                    sums_b[i] = xb;
+                }
             }
         }
         __syncthreads();
@@ -190,15 +213,45 @@ __device__ inline void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-struct TaskCache {
-    int inst, r0, nr, K, kd, N, t0, first, fixed, maxs, ngf_stop, normalize;
-    long long hist, bvec, Gm, Gf, Wf, c0;
-    double kdt, ngf_tol;
-};
+__device__ inline TaskCache make_task_cache(const SweepArgs& A, int t) {
+    const Task tk = A.tasks[t];
+    const SubDev& s = A.v.sub[tk.sid];
+    const InstDev& in = A.v.inst[tk.inst];
+    TaskCache c;
+    c.inst = tk.inst;
+    c.sid = tk.sid;
+    c.r0 = tk.r0;
+    c.nr = tk.r1 - tk.r0;
+    c.K = s.K;
+    c.kd = s.kd;
+    c.N = s.N;
+    c.t0 = A.inst_task0[tk.inst];
+    c.first = (t == c.t0);
+    c.maxs = in.window_cap > 0 ? in.window_cap : in.max_steps;
+    c.ngf_stop = (in.window_cap == 0 && in.ngf_tol > 0.0);
+    if (A.tune_steps > 0) {
+        c.maxs = min(c.maxs, A.tune_steps);
+        c.ngf_stop = 0;
+    }
+    c.normalize = in.normalize;
+    c.hist = s.hist;
+    c.bvec = s.bvec;
+    c.Gm = s.Gm;
+    c.Gf = s.Gf;
+    c.Wf = s.Wf;
+    c.c0 = s.c0;
+    T1Layout lay(s.q, s.kd);
+    c.p1 = s.t1[0] + lay.mat(M_PP);
+    c.p2 = s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_PP);
+    c.own = tk.own;
+    c.kdt = in.kappa * in.dt;
+    c.ngf_tol = in.ngf_tol;
+    return c;
+}
 
-// rows [r0, r0+nr) of z = (P1 (x) P2) y (N = 2) or P1 y (N = 1); P and y in
-// shared memory.  Warp-parallel dot products (lanes over the contraction,
-// shuffle reduction) keep the FP64 dependency chains short.
+// rows [r0, r0+nr) of z = (P1 (x) P2) y (N = 2) or P1 y (N = 1); y in shared
+// memory, P in shared or global memory.  Warp-parallel dot products (lanes over
+// the contraction, shuffle reduction) keep the FP64 dependency chains short.
 __device__ void z_rows_sm(const TaskCache& tc, const double* P1, const double* P2, const double* ys, double* z,
                           double* tmp) {
     const int kd = tc.kd, r0 = tc.r0, r1 = tc.r0 + tc.nr;
@@ -231,139 +284,264 @@ __device__ void z_rows_sm(const TaskCache& tc, const double* P1, const double* P
     __syncthreads();
 }
 
-// FP64 window: two phases and two reduce-barriers per step (see the top of
-// the file).  Dynamic shared memory (doubles):
-//   vs[kmax] | (unused)[kmax] | tmp[WIN_RB + 2 kdmax] | P[tasks_per_cta][2][kdmax^2]
-__global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fp64(SweepArgs A) {
+// Rows [r0, r0+nr) of z = (P1 (x) P2) y (N = 2) or P1 y (N = 1), y in shared
+// memory, for a task whose factors are in global memory: the factors are
+// first staged in shared memory (Ps: 2 kd^2 doubles, one coalesced pass), then
+// every thread computes whole outputs of the two small products
+//   tmp[bb][c] = sum_e Y[c][e] P2[b0+bb][e],   z[(a,b)] = sum_c P1[a][c] tmp[b-b0][c]
+// (no per-output warp reductions waiting on separate loads).
+__device__ void z_rows_staged(const TaskCache& tc, const double* P1g, const double* P2g, const double* ys, double* z,
+                              double* tmp, double* Ps) {
+    const int kd = tc.kd, r0 = tc.r0, r1 = tc.r0 + tc.nr, kk = kd * kd;
+    double* P1 = Ps;
+    double* P2 = Ps + kk;
+    for (int e = threadIdx.x; e < kk; e += WIN_THREADS) {
+        P1[e] = P1g[e];
+        if (tc.N == 2) P2[e] = P2g[e];
+    }
+    __syncthreads();
+    if (tc.N == 1) {
+        for (int r = r0 + threadIdx.x; r < r1; r += WIN_THREADS) {
+            double acc = 0;
+            for (int c = 0; c < kd; ++c) acc = fma(P1[r * kd + c], ys[c], acc);
+            z[r - r0] = acc;
+        }
+        __syncthreads();
+        return;
+    }
+    const int b0 = r0 / kd, b1 = (r1 - 1) / kd, nb = b1 - b0 + 1;
+    for (int item = threadIdx.x; item < nb * kd; item += WIN_THREADS) {
+        const int bb = item / kd, c = item - bb * kd;
+        const double* p2 = P2 + (b0 + bb) * kd;
+        double acc = 0;
+        for (int e = 0; e < kd; ++e) acc = fma(ys[c + kd * e], p2[e], acc);
+        tmp[item] = acc;
+    }
+    __syncthreads();
+    for (int r = r0 + threadIdx.x; r < r1; r += WIN_THREADS) {
+        const int b = r / kd, a = r - b * kd;
+        const double* p1 = P1 + a * kd;
+        const double* tb = tmp + (b - b0) * kd;
+        double acc = 0;
+        for (int c = 0; c < kd; ++c) acc = fma(p1[c], tb[c], acc);
+        z[r - r0] = acc;
+    }
+    __syncthreads();
+}
+
+// One double-single multiply-add: (yh, yl) += (g0 + g1)(x0 + x1), TwoProduct of
+// the leading terms, TwoSum into (yh, yl), the cross terms into yl.
+__device__ inline void df32_acc(float& yh, float& yl, float g0, float g1, float x0, float x1) {
+    const float p = g0 * x0, e = fmaf(g0, x0, -p);
+    float sh, q;
+    two_sum(yh, p, sh, q);
+    yh = sh;
+    yl += (q + e) + fmaf(g0, x1, g1 * x0);
+}
+
+// Rows [rb, rb + nrow), nrow <= 4, of G v in double-single: one warp, lanes
+// over groups of 4 columns (16-byte loads from each FP32 plane, rows of ld
+// columns zero-padded), independent (hi, lo) accumulators per row so that the
+// loads of four rows are in flight together; y[i] to lane 0.
+__device__ inline void df32_rows4(const float* Gh, const float* Gl, int ld, const float2* vf, int rb, int nrow,
+                                  int lane, double* y) {
+    float yh[4] = {0.f, 0.f, 0.f, 0.f}, yl[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c = lane * 4; c < ld; c += 128) {
+        const float4 xa = *reinterpret_cast<const float4*>(vf + c);      // h0 l0 h1 l1
+        const float4 xb = *reinterpret_cast<const float4*>(vf + c + 2);  // h2 l2 h3 l3
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i < nrow) {
+                const long long o = (long long)(rb + i) * ld + c;
+                const float4 gh = *reinterpret_cast<const float4*>(Gh + o);
+                const float4 gl = *reinterpret_cast<const float4*>(Gl + o);
+                df32_acc(yh[i], yl[i], gh.x, gl.x, xa.x, xa.y);
+                df32_acc(yh[i], yl[i], gh.y, gl.y, xa.z, xa.w);
+                df32_acc(yh[i], yl[i], gh.z, gl.z, xb.x, xb.y);
+                df32_acc(yh[i], yl[i], gh.w, gl.w, xb.z, xb.w);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float sh, eh;
+            const float oh = __shfl_xor_sync(0xffffffffu, yh[i], o), ol = __shfl_xor_sync(0xffffffffu, yl[i], o);
+            two_sum(yh[i], oh, sh, eh);
+            yh[i] = sh;
+            yl[i] = yl[i] + ol + eh;
+        }
+        y[i] = (double)yh[i] + (double)yl[i];
+    }
+}
+
+// Rows [rb, rb + nrow), nrow <= 4, of G v in FP64: per row two accumulators
+// over columns c = lane + 64 m and c = lane + 32 + 64 m, then a shuffle sum
+// (the same order for every row whatever warp computes it); y[i] to all lanes.
+__device__ inline void fp64_rows4(const double* G, int K, const double* vs, int rb, int nrow, int lane, double* y) {
+    double a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+    int c = lane;
+    for (; c + 32 < K; c += 64) {
+        const double x0 = vs[c], x1 = vs[c + 32];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i < nrow) {
+                const double* g = G + (long long)(rb + i) * K;
+                a[i] = fma(g[c], x0, a[i]);
+                b[i] = fma(g[c + 32], x1, b[i]);
+            }
+        }
+    }
+    if (c < K) {
+        const double x0 = vs[c];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (i < nrow) a[i] = fma(G[(long long)(rb + i) * K + c], x0, a[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) y[i] = warp_sum(a[i] + b[i]);
+}
+
+// Two-phase window: two reduce-barriers per step (see the top of the file).
+// DF32 = false: G in FP64 (DFMA).  DF32 = true: G as FP32 hi/lo planes
+// (8 bytes per element like FP64, on the FP32 pipes).  Per-task state sits in
+// shared memory when the CTA has at most WIN_TPC tasks, else (A.many) in
+// global memory.  Dynamic shared memory (doubles):
+//   vs[kmax] | vf[kmax] (float2) | tmp[rows_max + 2 kdmax] | P[tasks_per_cta][2][kdmax^2]
+// (many: P[1][2][kdmax^2], the factors of the task at hand)
+template <bool DF32>
+__global__ void __launch_bounds__(WIN_THREADS, 2) k_window_2ph(SweepArgs A) {
     extern __shared__ double sm[];
     __shared__ double red[33];
-    __shared__ TaskCache tcs[WIN_TPC];
-    __shared__ double own[WIN_TPC][4][WIN_RB];
-    __shared__ double s_prev[WIN_TPC];
-    __shared__ int alive[WIN_TPC];
-    __shared__ double s_sc[2];  // 1/s_n, 1/s_{n-1}
+    __shared__ TaskCache s_tcs[WIN_TPC];
+    __shared__ double s_own[WIN_TPC][4][WIN_RB];
+    __shared__ int s_alive[WIN_TPC];
     int go = 1;
     const SwrDeviceView& v = A.v;
-    const int t_begin = blockIdx.x * A.tasks_per_cta;
-    const int ntk = min(A.n_tasks - t_begin, A.tasks_per_cta);
+    const int t_begin = A.cta_task0[blockIdx.x];
+    const int ntk = A.cta_task0[blockIdx.x + 1] - t_begin;
+    const bool many = A.many != 0;
+    TaskCache* tcs = many ? A.g_tc + t_begin : s_tcs;
+    int* alive = many ? A.g_alive + t_begin : s_alive;
     const int cap = A.cap;
-    const int kmax = A.kmax, kdmax = A.kdmax;
+    const int kmax = df32_ld(A.kmax), kdmax = A.kdmax;
     double* vs = sm;
+    float2* vf = (float2*)(sm + kmax);
     double* tmp = sm + 2 * kmax;
-    double* Psm = tmp + WIN_RB + 2 * kdmax;
+    double* Psm = tmp + A.rows_max + 2 * kdmax;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = WIN_THREADS / 32;
     unsigned target = 0, gen = 0;
+    // own rows: slots 0,1 = y^n ring, 2,3 = z^n ring
+    auto own = [&](int j, int slot) -> double* {
+        return many ? A.g_own + tcs[j].own + (long long)slot * tcs[j].nr : &s_own[j][slot][0];
+    };
+    auto pmat = [&](int j, int which) -> const double* {
+        return many ? v.arena + (which ? tcs[j].p2 : tcs[j].p1)
+                    : Psm + (long long)j * 2 * kdmax * kdmax + (which ? (long long)kdmax * kdmax : 0);
+    };
+    // z rows: factors resident in shared memory (few tasks), else staged per task into Psm
+    auto z_rows = [&](int j, const TaskCache& tc, double* z) {
+        if (many) z_rows_staged(tc, v.arena + tc.p1, v.arena + tc.p2, vs, z, tmp, Psm);
+        else z_rows_sm(tc, pmat(j, 0), pmat(j, 1), vs, z, tmp);
+    };
 
     // ------------------------------------------------------- set-up + step 0
     for (int j = 0; j < ntk; ++j) {
-        const int t = t_begin + j;
-        const Task tk = A.tasks[t];
-        const SubDev& s = v.sub[tk.sid];
-        const InstDev& in = v.inst[tk.inst];
+        const int t = A.cta_list[t_begin + j];
         if (tid == 0) {
-            TaskCache c;
-            c.inst = tk.inst;
-            c.r0 = tk.r0;
-            c.nr = tk.r1 - tk.r0;
-            c.K = s.K;
-            c.kd = s.kd;
-            c.N = s.N;
-            c.t0 = A.inst_task0[tk.inst];
-            c.first = (t == c.t0);
-            c.fixed = in.window_cap;
-            c.maxs = in.window_cap > 0 ? in.window_cap : in.max_steps;
-            c.ngf_stop = (in.window_cap == 0 && in.ngf_tol > 0.0);
-            c.normalize = in.normalize;
-            c.hist = s.hist;
-            c.bvec = s.bvec;
-            c.Gm = s.Gm;
-            c.Gf = s.Gf;
-            c.c0 = s.c0;
-            c.kdt = in.kappa * in.dt;
-            c.ngf_tol = in.ngf_tol;
-            tcs[j] = c;
+            tcs[j] = make_task_cache(A, t);
             alive[j] = 1;
-            s_prev[j] = 1.0;
         }
         __syncthreads();
-        const TaskCache& tc = tcs[j];
+        const TaskCache tc = tcs[j];
         const int kd = tc.kd, K = tc.K, nr = tc.nr;
-        T1Layout lay(s.q, kd);
-        double* P1 = Psm + (long long)j * 2 * kdmax * kdmax;
-        double* P2 = P1 + (long long)kdmax * kdmax;
-        const double* P1g = v.arena + s.t1[0] + lay.mat(M_PP);
-        const double* P2g = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_PP);
-        for (int e = tid; e < kd * kd; e += WIN_THREADS) {
-            P1[e] = P1g[e];
-            P2[e] = P2g[e];
+        if (!many) {
+            double* P1 = Psm + (long long)j * 2 * kdmax * kdmax;
+            double* P2 = P1 + (long long)kdmax * kdmax;
+            const double* P1g = v.arena + tc.p1;
+            const double* P2g = v.arena + tc.p2;
+            for (int e = tid; e < kd * kd; e += WIN_THREADS) {
+                P1[e] = P1g[e];
+                P2[e] = P2g[e];
+            }
         }
         const double* c0 = v.arena + tc.c0;
         for (int c = tid; c < K; c += WIN_THREADS) vs[c] = c0[c];
         __syncthreads();
         double* h0 = v.arena + tc.hist;
+        double* y0 = own(j, 0);
         for (int r = tid; r < nr; r += WIN_THREADS) {
             h0[tc.r0 + r] = vs[tc.r0 + r];
-            own[j][0][r] = vs[tc.r0 + r];  // y^0 in slot 0
+            y0[r] = vs[tc.r0 + r];  // y^0 in slot 0
         }
-        z_rows_sm(tc, P1, P2, vs, own[j][2], tmp);  // z^0 in slot 0
+        z_rows(j, tc, own(j, 2));  // z^0 in slot 2
         double acc = 0;
-        for (int r = tid; r < nr; r += WIN_THREADS) acc += own[j][0][r] * own[j][2][r];
+        const double* z0 = own(j, 2);
+        for (int r = tid; r < nr; r += WIN_THREADS) acc += y0[r] * z0[r];
         acc = wblock_sum(acc, red);
         if (tid == 0) A.part_s[t] = acc;
     }
     target += gridDim.x;
     ++gen;
     if (!reduce_barrier(&A.bar->count, &A.bar->gen, target, gen, true, A.part_s, A.inst_task0, v.n_inst,
-                        A.sums_s, v.err, A.spin_limit, red, nullptr, &go))
+                        A.sums_s, v.err, A.spin_limit, red, nullptr, &go, v.inst, A.scal_inst))
         return;
 
     for (int n = 0;; ++n) {
+        // s_n, 1/s_n, 1/s_{n-1} per instance, by step parity
+        const double* sc_n = A.scal_inst + (n & 1) * 2 * v.n_inst;
+        const double* sc_p = A.scal_inst + ((n & 1) ^ 1) * 2 * v.n_inst;
         // ------------------------------------------------------ phase A(n+1)
+        int vs_sid = -1;  // subdomain whose v is in vs / vf (consecutive tasks of one subdomain share it)
         for (int j = 0; j < ntk; ++j) {
             __syncthreads();
             if (!alive[j]) continue;
-            const TaskCache& tc = tcs[j];
+            const TaskCache tc = tcs[j];
             const int K = tc.K, nr = tc.nr;
-            const int t = t_begin + j;
-            // one round trip: s_n^2, y^n, b'^{n+1}
-            const double s2 = tc.normalize ? __ldcg(A.sums_s + tc.inst) : 1.0;
-            const double* yn = v.arena + tc.hist + (long long)n * K;
-            const int wp = A.win_prev[tc.inst];
-            const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(n + 1, wp) * K : nullptr;
+            const int t = A.cta_list[t_begin + j];
+            const bool load = (tc.sid != vs_sid);
+            // one round trip: s_n, y^n, b'^{n+1}
+            const double s_n = __ldcg(sc_n + tc.inst), is_n = __ldcg(sc_n + v.n_inst + tc.inst);
+            const double is_p = n == 0 ? 1.0 : __ldcg(sc_p + v.n_inst + tc.inst);
             double yv[4], bv[4];
+            if (load) {
+                const double* yn = v.arena + tc.hist + (long long)n * K;
+                const int wp = A.win_prev[tc.inst];
+                const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(n + 1, wp) * K : nullptr;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                int c = tid + i * WIN_THREADS;
-                yv[i] = (c < K) ? yn[c] : 0.0;
-                bv[i] = (c < K && bsrc) ? bsrc[c] : 0.0;
-            }
-            // one thread takes the square root and the reciprocals (FP64 division
-            // and square root are slow sequences on this part)
-            if (tid == 0) {
-                const double s_n = tc.normalize ? sqrt(s2) : 1.0;
-                s_sc[0] = 1.0 / s_n;
-                s_sc[1] = 1.0 / s_prev[j];
-                s_prev[j] = s_n;
-                if (tc.first) A.snorm[(long long)tc.inst * (cap + 1) + n] = s_n;
-            }
-            __syncthreads();
-            const double s_n = s_prev[j];
-            const double is_n = s_sc[0], is_p = s_sc[1];
-            if (n >= tc.maxs || !isfinite(s_n) || s_n <= 0.0) continue;  // closed in phase B
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                int c = tid + i * WIN_THREADS;
-                if (c < K) {
-                    double val = yv[i] * is_n + tc.kdt * bv[i];
-                    vs[c] = val;
+                for (int i = 0; i < 4; ++i) {
+                    int c = tid + i * WIN_THREADS;
+                    yv[i] = (c < K) ? yn[c] : 0.0;
+                    bv[i] = (c < K && bsrc) ? bsrc[c] : 0.0;
                 }
+            }
+            if (tid == 0 && tc.first) A.snorm[(long long)tc.inst * (cap + 1) + n] = s_n;
+            if (n >= tc.maxs || !isfinite(s_n) || s_n <= 0.0) continue;  // closed in phase B
+            if (load) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    int c = tid + i * WIN_THREADS;
+                    if (c < K) {
+                        double val = yv[i] * is_n + tc.kdt * bv[i];
+                        if (DF32) {
+                            float h = (float)val;
+                            vf[c] = make_float2(h, (float)(val - (double)h));
+                        } else {
+                            vs[c] = val;
+                        }
+                    } else if (DF32 && c < df32_ld(K)) {
+                        vf[c] = make_float2(0.f, 0.f);  // padding columns of the FP32 planes
+                    }
+                }
+                vs_sid = tc.sid;
             }
             // partial of delta_n^2 = || y^n/s_n - y^{n-1}/s_{n-1} ||^2_chi over own rows
             if (n >= 1 && tc.ngf_stop) {
-                const double* y_n = own[j][n & 1];
-                const double* y_p = own[j][(n - 1) & 1];
-                const double* z_n = own[j][2 + (n & 1)];
-                const double* z_p = own[j][2 + ((n - 1) & 1)];
+                const double* y_n = own(j, n & 1);
+                const double* y_p = own(j, (n - 1) & 1);
+                const double* z_n = own(j, 2 + (n & 1));
+                const double* z_p = own(j, 2 + ((n - 1) & 1));
                 double acc = 0;
                 for (int r = tid; r < nr; r += WIN_THREADS)
                     acc += (y_n[r] * is_n - y_p[r] * is_p) * (z_n[r] * is_n - z_p[r] * is_p);
@@ -374,22 +552,23 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fp64(SweepArgs A) {
             }
             // rows of y^{n+1} = G v
             double* ynew = v.arena + tc.hist + (long long)(n + 1) * K;
-            double* yslot = own[j][(n + 1) & 1];
-            {
-                const double* G = v.arena + tc.Gm;
-                for (int r = tc.r0 + warp; r < tc.r0 + nr; r += nw) {
-                    const double* g = G + (long long)r * K;
-                    double a0 = 0, a1 = 0;
-                    int c = lane;
-                    for (; c + 32 < K; c += 64) {
-                        a0 = fma(g[c], vs[c], a0);
-                        a1 = fma(g[c + 32], vs[c + 32], a1);
-                    }
-                    if (c < K) a0 = fma(g[c], vs[c], a0);
-                    double y = warp_sum(a0 + a1);
-                    if (lane == 0) {
-                        ynew[r] = y;
-                        yslot[r - tc.r0] = y;
+            double* yslot = own(j, (n + 1) & 1);
+            // each warp takes blocks of 4 consecutive rows
+            const int ld = df32_ld(K);
+            const float* Gh = (const float*)(v.arena + tc.Gf);
+            const float* Gl = Gh + (long long)K * ld;
+            for (int rb = tc.r0 + 4 * warp; rb < tc.r0 + nr; rb += 4 * nw) {
+                const int nrow = min(4, tc.r0 + nr - rb);
+                double y[4];
+                if (DF32) df32_rows4(Gh, Gl, ld, vf, rb, nrow, lane, y);
+                else fp64_rows4(v.arena + tc.Gm, K, vs, rb, nrow, lane, y);
+                if (lane == 0) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (i < nrow) {
+                            ynew[rb + i] = y[i];
+                            yslot[rb + i - tc.r0] = y[i];
+                        }
                     }
                 }
             }
@@ -401,19 +580,21 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fp64(SweepArgs A) {
                             A.inst_task0, v.n_inst, A.sums_d, v.err, A.spin_limit, red, nullptr, &go))
             return;
         // ------------------------------------------------------ phase B(n+1)
+        vs_sid = -1;  // vs now holds y^{n+1} of subdomain vs_sid
         for (int j = 0; j < ntk; ++j) {
             __syncthreads();
             if (!alive[j]) continue;
-            const TaskCache& tc = tcs[j];
+            const TaskCache tc = tcs[j];
             const int K = tc.K, nr = tc.nr;
-            const int t = t_begin + j;
-            const double s_n = s_prev[j];
+            const int t = A.cta_list[t_begin + j];
+            const double s_n = __ldcg(sc_n + tc.inst);
             bool stop = (n >= tc.maxs) || !isfinite(s_n) || s_n <= 0.0;
             double d2 = 0;
             const double* yn1 = v.arena + tc.hist + (long long)(n + 1) * K;
             if (!stop) {
                 if (n >= 1 && tc.ngf_stop) d2 = __ldcg(A.sums_d + tc.inst);
-                for (int c = tid; c < K; c += WIN_THREADS) vs[c] = yn1[c];
+                if (tc.sid != vs_sid)
+                    for (int c = tid; c < K; c += WIN_THREADS) vs[c] = yn1[c];
                 if (n >= 1 && tc.ngf_stop) stop = sqrt(fmax(d2, 0.0)) <= tc.ngf_tol;
             }
             if (stop) {
@@ -429,12 +610,11 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fp64(SweepArgs A) {
                 }
                 continue;
             }
+            vs_sid = tc.sid;
             __syncthreads();
-            double* P1 = Psm + (long long)j * 2 * kdmax * kdmax;
-            double* P2 = P1 + (long long)kdmax * kdmax;
-            double* zslot = own[j][2 + ((n + 1) & 1)];
-            z_rows_sm(tc, P1, P2, vs, zslot, tmp);
-            const double* yslot = own[j][(n + 1) & 1];
+            double* zslot = own(j, 2 + ((n + 1) & 1));
+            z_rows(j, tc, zslot);
+            const double* yslot = own(j, (n + 1) & 1);
             double acc = 0;
             for (int r = tid; r < nr; r += WIN_THREADS) acc += yslot[r] * zslot[r];
             acc = wblock_sum(acc, red);
@@ -446,7 +626,8 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fp64(SweepArgs A) {
         // the last CTA to arrive reads the active count after every decrement of
         // this phase and hands the verdict to all CTAs with the release
         if (!reduce_barrier(&A.bar->count, &A.bar->gen, target, gen, true, A.part_s, A.inst_task0, v.n_inst,
-                            A.sums_s, v.err, A.spin_limit, red, A.n_active, &go))
+                            A.sums_s, v.err, A.spin_limit, red, A.n_active, &go, v.inst,
+                            A.scal_inst + ((n + 1) & 1) * 2 * v.n_inst))
             return;
         if (!go) return;
     }
@@ -465,9 +646,10 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fp64(SweepArgs A) {
 // barrier after P(n) reduces both partial arrays.  D_n is therefore known at
 // P(n+1): when D_n <= tol^2 the window ends at n (the step n+1 already
 // computed is dropped), which reproduces the stop of the plain algorithm.
-// Dynamic shared memory: vs[kmax] doubles | vf[kmax] float2 | tmp[WIN_RB + 2 kdmax]
+// Shared-memory task state only (at most WIN_TPC tasks per CTA).
+// Dynamic shared memory: vs[kmax] doubles | vf[kmax] float2 | tmp[rows_max + 2 kdmax]
 // doubles | P[tasks_per_cta][2][kdmax^2] doubles | G_hi rows (floats, when resident).
-__global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
+__global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
     extern __shared__ double sm[];
     __shared__ double red[33];
     __shared__ TaskCache tcs[WIN_TPC];
@@ -478,14 +660,14 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
     __shared__ int s_stop;
     int go = 1;
     const SwrDeviceView& v = A.v;
-    const int t_begin = blockIdx.x * A.tasks_per_cta;
-    const int ntk = min(A.n_tasks - t_begin, A.tasks_per_cta);
+    const int t_begin = A.cta_task0[blockIdx.x];
+    const int ntk = A.cta_task0[blockIdx.x + 1] - t_begin;
     const int cap = A.cap;
-    const int kmax = A.kmax, kdmax = A.kdmax;
+    const int kmax = df32_ld(A.kmax), kdmax = A.kdmax;
     double* vs = sm;
     float2* vf = (float2*)(sm + kmax);
     double* tmp = sm + 2 * kmax;
-    double* Psm = tmp + WIN_RB + 2 * kdmax;
+    double* Psm = tmp + A.rows_max + 2 * kdmax;
     float* Gsm = (float*)(Psm + (long long)A.tasks_per_cta * 2 * kdmax * kdmax);
     const bool gres = A.g_resident != 0;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = WIN_THREADS / 32;
@@ -493,51 +675,27 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
 
     // ------------------------------------------------------- set-up + step 0
     for (int j = 0; j < ntk; ++j) {
-        const int t = t_begin + j;
-        const Task tk = A.tasks[t];
-        const SubDev& s = v.sub[tk.sid];
-        const InstDev& in = v.inst[tk.inst];
+        const int t = A.cta_list[t_begin + j];
         if (tid == 0) {
-            TaskCache c;
-            c.inst = tk.inst;
-            c.r0 = tk.r0;
-            c.nr = tk.r1 - tk.r0;
-            c.K = s.K;
-            c.kd = s.kd;
-            c.N = s.N;
-            c.t0 = A.inst_task0[tk.inst];
-            c.first = (t == c.t0);
-            c.fixed = in.window_cap;
-            c.maxs = in.window_cap > 0 ? in.window_cap : in.max_steps;
-            c.ngf_stop = (in.window_cap == 0 && in.ngf_tol > 0.0);
-            c.normalize = in.normalize;
-            c.hist = s.hist;
-            c.bvec = s.bvec;
-            c.Gm = s.Gm;
-            c.Gf = s.Gf;
-            c.Wf = s.Wf;
-            c.c0 = s.c0;
-            c.kdt = in.kappa * in.dt;
-            c.ngf_tol = in.ngf_tol;
-            tcs[j] = c;
+            tcs[j] = make_task_cache(A, t);
             alive[j] = 1;
             is_prev[j] = 1.0;
         }
         __syncthreads();
         const TaskCache& tc = tcs[j];
         const int kd = tc.kd, K = tc.K, nr = tc.nr;
-        T1Layout lay(s.q, kd);
         double* P1 = Psm + (long long)j * 2 * kdmax * kdmax;
         double* P2 = P1 + (long long)kdmax * kdmax;
-        const double* P1g = v.arena + s.t1[0] + lay.mat(M_PP);
-        const double* P2g = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_PP);
+        const double* P1g = v.arena + tc.p1;
+        const double* P2g = v.arena + tc.p2;
         for (int e = tid; e < kd * kd; e += WIN_THREADS) {
             P1[e] = P1g[e];
             P2[e] = P2g[e];
         }
         if (gres) {
             const float* Gh = (const float*)(v.arena + tc.Gf);
-            for (long long e = tid; e < (long long)nr * K; e += WIN_THREADS) Gsm[e] = Gh[(long long)tc.r0 * K + e];
+            const long long ld = df32_ld(K);
+            for (long long e = tid; e < (long long)nr * ld; e += WIN_THREADS) Gsm[e] = Gh[(long long)tc.r0 * ld + e];
         }
         const double* c0 = v.arena + tc.c0;
         for (int c = tid; c < K; c += WIN_THREADS) vs[c] = c0[c];
@@ -568,7 +726,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
             if (!alive[j]) continue;
             const TaskCache& tc = tcs[j];
             const int K = tc.K, nr = tc.nr;
-            const int t = t_begin + j;
+            const int t = A.cta_list[t_begin + j];
             // one round trip: s_n^2, D_{n-1}, y^n, b'^{n+1}
             const double s2 = tc.normalize ? __ldcg(A.sums_s + tc.inst) : 1.0;
             const double d2 = (n >= 2 && tc.ngf_stop) ? __ldcg(A.sums_d + tc.inst) : 1.0e300;
@@ -627,13 +785,14 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_df32(SweepArgs A) {
             double* ynew = v.arena + tc.hist + (long long)(n + 1) * K;
             double* yslot = own[j][(n + 1) % 3];
             double* zslot = own[j][3 + (n + 1) % 3];
+            const long long ld = df32_ld(K);
             const float* Ghg = (const float*)(v.arena + tc.Gf);
-            const float* Gl = Ghg + (long long)K * K;
+            const float* Gl = Ghg + (long long)K * ld;
             const float* Wh = (const float*)(v.arena + tc.Wf);
             const float* Wl = Wh + (long long)K * K;
             for (int r = tc.r0 + warp; r < tc.r0 + nr; r += nw) {
-                const float* gh = gres ? Gsm + (long long)(r - tc.r0) * K : Ghg + (long long)r * K;
-                const float* gl = Gl + (long long)r * K;
+                const float* gh = gres ? Gsm + (long long)(r - tc.r0) * ld : Ghg + (long long)r * ld;
+                const float* gl = Gl + (long long)r * ld;
                 const float* wh = Wh + (long long)r * K;
                 const float* wl = Wl + (long long)r * K;
                 float yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f, eh;
@@ -718,16 +877,20 @@ __global__ void k_window_reset(SweepArgs A, int n_inst) {
 }
 
 // Split of the FP64 step-matrix inverse into FP32 pairs (mixed precision).
+// G_hi = fl32(G), G_lo = fl32(G - G_hi), rows padded to df32_ld(K) columns with zeros.
 __global__ void k_split_df32(SwrDeviceView v) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
-    const long long KK = (long long)s.K * s.K;
+    const int K = s.K, ld = df32_ld(K);
+    const long long n = (long long)K * ld;
     const double* G = v.arena + s.Gm;
     float* Gh = (float*)(v.arena + s.Gf);
-    float* Gl = Gh + KK;
-    for (long long e = threadIdx.x + (long long)blockIdx.x * blockDim.x; e < KK; e += (long long)blockDim.x * gridDim.x) {
-        double g = G[e];
-        float h = (float)g;
+    float* Gl = Gh + n;
+    for (long long e = threadIdx.x + (long long)blockIdx.x * blockDim.x; e < n; e += (long long)blockDim.x * gridDim.x) {
+        const long long r = e / ld;
+        const int c = (int)(e - r * ld);
+        const double g = c < K ? G[r * K + c] : 0.0;
+        const float h = (float)g;
         Gh[e] = h;
         Gl[e] = (float)(g - (double)h);
     }
@@ -783,8 +946,8 @@ __global__ void k_make_w(SwrDeviceView v) {
 
 // ------------------------------------------------------------- host side
 
-size_t window_smem(int kmax, int kdmax, int tasks_per_cta, long long g_resident_floats) {
-    return (2 * (size_t)kmax + WIN_RB + 2 * (size_t)kdmax + (size_t)tasks_per_cta * 2 * kdmax * kdmax) *
+size_t window_smem(int kmax, int kdmax, int rows_max, int tasks_in_smem, long long g_resident_floats) {
+    return (2 * (size_t)df32_ld(kmax) + (size_t)rows_max + 2 * (size_t)kdmax + (size_t)tasks_in_smem * 2 * kdmax * kdmax) *
                sizeof(double) +
            (size_t)g_resident_floats * sizeof(float);
 }
@@ -792,33 +955,38 @@ size_t window_smem(int kmax, int kdmax, int tasks_per_cta, long long g_resident_
 int window_tasks_per_cta_max() { return WIN_TPC; }
 int window_rows_per_task_max() { return WIN_RB; }
 
-cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, bool df32) {
-    const void* f = df32 ? (const void*)k_window_df32 : (const void*)k_window_fp64;
+static const void* window_kernel(int variant, bool df32) {
+    if (variant == WIN_FUSED) return (const void*)k_window_fused;
+    return df32 ? (const void*)k_window_2ph<true> : (const void*)k_window_2ph<false>;
+}
+
+cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, int variant, bool df32) {
+    const void* f = window_kernel(variant, df32);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, WIN_THREADS, smem);
 }
 
-cudaError_t launch_split_df32(const SwrDeviceView& v, cudaStream_t st, int max_K) {
-    long long kk = (long long)max_K * max_K;
+cudaError_t launch_split_df32(const SwrDeviceView& v, cudaStream_t st, int max_K, bool make_w) {
+    long long kk = (long long)max_K * df32_ld(max_K);
     unsigned gx = (unsigned)((kk + 256 * 8 - 1) / (256 * 8));
     k_split_df32<<<dim3(gx, v.n_sub), 256, 0, st>>>(v);
+    if (!make_w) return cudaGetLastError();
     size_t sm = ((size_t)max_K + 32 * 32) * sizeof(double);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_make_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_make_w<<<dim3(max_K < 512 ? max_K : 512, v.n_sub), 256, sm, st>>>(v);
     return cudaGetLastError();
 }
 
-cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst, bool df32,
+cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst, int variant, bool df32,
                           cudaEvent_t ev_begin, cudaEvent_t ev_end) {
     k_window_reset<<<1, 32, 0, st>>>(a, n_inst);
-    cudaError_t e = cudaEventRecord(ev_begin, st);
+    cudaError_t e = record_event(ev_begin, st);
     if (e != cudaSuccess) return e;
     void* params[] = {&a};
-    const void* f = df32 ? (const void*)k_window_df32 : (const void*)k_window_fp64;
-    e = cudaLaunchCooperativeKernel(f, dim3(grid), dim3(WIN_THREADS), params, smem, st);
+    e = cudaLaunchCooperativeKernel(window_kernel(variant, df32), dim3(grid), dim3(WIN_THREADS), params, smem, st);
     if (e != cudaSuccess) return e;
-    return cudaEventRecord(ev_end, st);
+    return record_event(ev_end, st);
 }
 
 }  // namespace swr

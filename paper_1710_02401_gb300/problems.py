@@ -154,8 +154,12 @@ def batched_uneven(n_instances: int = 512, seed: int = 171002401,
     Per instance: N in {1,2} (50/50); 1 or 2 nuclei at U[-2,2] with Z in
     {1,2,3}; softening eps ~ U[0.3,1] (e-n and e-e); box [-12,12]^N;
     N=1: L ~ U{4..64}; N=2: L ~ U{2..8}; overlap 10% of the core width;
-    per-subdomain basis size K ~ U[k_lo, k_hi], K_d = round(sqrt(K)) for N=2
-    and K_d = K for N=1; delta by the spacing rule per subdomain; quadrature
+    per-subdomain basis size K ~ U[k_lo, k_hi] drawn for every subdomain and
+    read as K_d = round(sqrt(K)) Gaussians per coordinate for both N (so the
+    draw sets the per-coordinate resolution; N=2 subdomains have K = K_d^2,
+    N=1 subdomains K = K_d: a 1-D basis of up to 1024 Gaussians on an
+    interval of width 0.4-6.6 would be 30-100x finer than the 1-electron
+    workload's 40 Gaussians on width 10.5); delta by the spacing rule per subdomain; quadrature
     panels as long as the overlap band with q_p nodes each, q_p chosen so every panel resolves the narrowest Gaussian (about 3.4 nodes per
     Gaussian of the finest subdomain); implicit Euler
     NGF dt = 0.1, mu = 10.
@@ -173,7 +177,7 @@ def batched_uneven(n_instances: int = 512, seed: int = 171002401,
         kds, deltas = [], []
         for _s in range(L ** n):
             K = rng.randint(k_lo, k_hi)
-            kd = K if n == 1 else max(2, int(round(math.sqrt(K))))
+            kd = max(2, int(round(math.sqrt(K))))
             kds.append(kd)
             deltas.append(spacing_rule_delta(box, L, ov, kd))
         kmax = max(kds)

@@ -22,6 +22,8 @@ SWR_OK, SWR_EINVAL, SWR_ENOMEM, SWR_ECUDA, SWR_ESINGULAR, SWR_ENUMERIC, SWR_ENOT
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENUMERIC", "ENOTCONV", "ETIMEOUT", "ESTATE"]
 MODE_TISE, MODE_TDSE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+WINDOW_AUTO, WINDOW_TWO_PHASE, WINDOW_FUSED = 0, 1, 2
+LAUNCH_GRAPH, LAUNCH_DIRECT = 0, 1
 GET, SET = 0, 1
 (FIELD_ENERGY, FIELD_NORM2, FIELD_DIPOLE, FIELD_RES, FIELD_WINDOW, FIELD_PSI_NODES, FIELD_OWN_TRACES,
  FIELD_ROBIN, FIELD_TRACE_BYTES, FIELD_NODE_COUNTS, FIELD_K_MAX, FIELD_COUNTERS) = range(12)
@@ -44,7 +46,15 @@ class swr_instance(C.Structure):
 
 class swr_problem(C.Structure):
     _fields_ = [("n_instances", C.c_int), ("instances", C.POINTER(swr_instance)), ("precision", C.c_int),
-                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+                ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+                ("window_variant", C.c_int), ("rows_per_task", C.c_int), ("launch_mode", C.c_int)]
+
+
+class swr_tune_report(C.Structure):
+    _fields_ = [("variant", C.c_int), ("rows_per_task", C.c_int), ("tasks", C.c_int), ("ctas", C.c_int),
+                ("task_state_global", C.c_int), ("candidates", C.c_int), ("graph", C.c_int),
+                ("seconds_per_step", C.c_double),
+                ("seconds_default", C.c_double)]
 
 
 class swr_iter_report(C.Structure):
@@ -65,7 +75,7 @@ EXPORTS = ["swr_workspace_size", "swr_setup", "swr_assemble", "swr_step", "swr_i
            "swr_get", "swr_field_bytes", "swr_trace_codec", "swr_trace_encode", "swr_trace_decode_set",
            "swr_mlp_create", "swr_mlp_param_count", "swr_mlp_set_params", "swr_mlp_get_params",
            "swr_mlp_forward", "swr_mlp_train_step", "swr_mlp_destroy", "swr_mlp_last_error",
-           "swr_residual_noalloc", "swr_destroy", "swr_last_error"]
+           "swr_residual_noalloc", "swr_autotune", "swr_window_plan", "swr_destroy", "swr_last_error"]
 
 _lib = None
 
@@ -88,6 +98,8 @@ def load_library(path: str = LIB_PATH):
     lib.swr_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]
     lib.swr_field_bytes.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]
     lib.swr_residual_noalloc.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]
+    lib.swr_autotune.argtypes = [C.c_void_p, C.c_int, C.POINTER(swr_tune_report)]
+    lib.swr_window_plan.argtypes = [C.c_void_p, C.POINTER(swr_tune_report)]
     lib.swr_trace_codec.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
     lib.swr_trace_encode.argtypes = [C.c_void_p, C.c_void_p]
     lib.swr_trace_decode_set.argtypes = [C.c_void_p, C.c_void_p]
@@ -171,7 +183,8 @@ class SWR:
     this object; work is ordered on `stream` (default: torch's current)."""
 
     def __init__(self, instances, precision: int = PREC_FP64, device: str = "cuda:0", stream=None,
-                 use_torch_workspace: bool = True):
+                 use_torch_workspace: bool = True, window_variant: int = 0, rows_per_task: int = 0,
+                 launch_mode: int = 0):
         import torch
         self.lib = load_library()
         if isinstance(instances, P.Instance):
@@ -189,6 +202,9 @@ class SWR:
         prob.instances = C.cast(arr, C.POINTER(swr_instance))
         prob.precision = precision
         prob.stream = C.c_void_p(self.stream.cuda_stream)
+        prob.window_variant = int(window_variant)
+        prob.rows_per_task = int(rows_per_task)
+        prob.launch_mode = int(launch_mode)
         nbytes = C.c_size_t(0)
         self._check(self.lib.swr_workspace_size(C.byref(prob), C.byref(nbytes)), None)
         self.workspace = None
@@ -229,6 +245,17 @@ class SWR:
         rep = swr_iter_report()
         self._check(self.lib.swr_step(self.ctx, C.byref(rep)), self.ctx)
         return rep
+
+    def autotune(self, steps: int = 24) -> dict:
+        """Times the window plans on a fixed window and keeps the fastest."""
+        rep = swr_tune_report()
+        self._check(self.lib.swr_autotune(self.ctx, int(steps), C.byref(rep)), self.ctx)
+        return {f: getattr(rep, f) for f, _ in swr_tune_report._fields_}
+
+    def window_plan(self) -> dict:
+        rep = swr_tune_report()
+        self._check(self.lib.swr_window_plan(self.ctx, C.byref(rep)), self.ctx)
+        return {f: getattr(rep, f) for f, _ in swr_tune_report._fields_}
 
     def iterate(self, tol: float, kmax: int, raise_on_notconv: bool = False):
         rep = swr_report()

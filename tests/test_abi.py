@@ -52,8 +52,11 @@ int main(void) {{
   printf("swr_iter_report %zu\\n", sizeof(swr_iter_report));
   printf("swr_report %zu\\n", sizeof(swr_report));
   printf("swr_trace_view %zu\\n", sizeof(swr_trace_view));
+  printf("swr_tune_report %zu\\n", sizeof(swr_tune_report));
   F(swr_instance, delta_per_sub) F(swr_instance, x_nuc) F(swr_instance, mode) F(swr_instance, phi0_center)
   F(swr_instance, max_steps) F(swr_problem, workspace_bytes) F(swr_iter_report, seconds)
+  F(swr_problem, window_variant) F(swr_problem, rows_per_task) F(swr_problem, launch_mode)
+  F(swr_tune_report, graph) F(swr_tune_report, seconds_default)
   return 0;
 }}
 ''')
@@ -69,6 +72,11 @@ int main(void) {{
         assert int(got[f"swr_instance.{key}"]) == getattr(S.swr_instance, key).offset, key
     assert int(got["swr_problem.workspace_bytes"]) == S.swr_problem.workspace_bytes.offset
     assert int(got["swr_iter_report.seconds"]) == S.swr_iter_report.seconds.offset
+    assert int(got["swr_tune_report"]) == C.sizeof(S.swr_tune_report)
+    for key in ["window_variant", "rows_per_task", "launch_mode"]:
+        assert int(got[f"swr_problem.{key}"]) == getattr(S.swr_problem, key).offset, key
+    assert int(got["swr_tune_report.seconds_default"]) == S.swr_tune_report.seconds_default.offset
+    assert int(got["swr_tune_report.graph"]) == S.swr_tune_report.graph.offset
 
 
 def _problem(insts, keep):
@@ -118,3 +126,38 @@ def test_mixed_modes_rejected(lib):
     n = C.c_size_t(0)
     p = _problem([P.small_tise_2d(), P.small_tdse_2d()], keep)
     assert lib.swr_workspace_size(C.byref(p), C.byref(n)) == S.SWR_EINVAL
+
+
+def test_window_plan_requests_on_host(lib):
+    keep = []
+    n = C.c_size_t(0)
+    p = _problem([P.small_tise_2d()], keep)
+    p.launch_mode = 2
+    assert lib.swr_workspace_size(C.byref(p), C.byref(n)) == S.SWR_EINVAL
+    p.launch_mode = S.LAUNCH_DIRECT
+    for variant, rows, prec, ok in [
+        (S.WINDOW_TWO_PHASE, 0, S.PREC_FP64, True),
+        (S.WINDOW_TWO_PHASE, 256, S.PREC_MIXED, True),
+        (S.WINDOW_FUSED, 0, S.PREC_MIXED, True),
+        (S.WINDOW_FUSED, 0, S.PREC_FP64, False),    # the fused kernel is the mixed one
+        (S.WINDOW_FUSED, 256, S.PREC_MIXED, False),  # 256-row tasks do not fit its shared memory
+        (3, 0, S.PREC_FP64, False),
+        (0, 4, S.PREC_FP64, False),
+        (0, 257, S.PREC_FP64, False),
+    ]:
+        p.window_variant, p.rows_per_task, p.precision = variant, rows, prec
+        st = lib.swr_workspace_size(C.byref(p), C.byref(n))
+        assert (st == S.SWR_OK) == ok, (variant, rows, prec, lib.swr_last_error(None))
+    # a batch with more row tasks per CTA than shared memory holds plans with the
+    # task state in global memory; requesting the two-phase variant never
+    # allocates W, and the fused variant cannot run such a batch
+    big = P.batched_uneven(24, seed=3)
+    pb = _problem(big, keep)
+    pb.precision = S.PREC_MIXED
+    auto, two = C.c_size_t(0), C.c_size_t(0)
+    assert lib.swr_workspace_size(C.byref(pb), C.byref(auto)) == S.SWR_OK
+    pb.window_variant = S.WINDOW_TWO_PHASE
+    assert lib.swr_workspace_size(C.byref(pb), C.byref(two)) == S.SWR_OK
+    assert two.value <= auto.value
+    pb.window_variant = S.WINDOW_FUSED
+    assert lib.swr_workspace_size(C.byref(pb), C.byref(n)) == S.SWR_EINVAL
