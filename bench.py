@@ -53,8 +53,13 @@ def profiled_traffic(kernel):
     return rec[1], rec[2]
 
 
+BATCHED = "batched_uneven_512"
+
+
 def workload(name: str):
     from paper_1710_02401_gb300 import problems as P
+    if name == BATCHED:
+        return P.batched_uneven(512)
     if name == "tise_2e_16sd":
         return P.tise_2e_16_subdomains()
     if name == "tise_1d_2sd":
@@ -62,6 +67,18 @@ def workload(name: str):
     if name == "tdse_2e_64sd":
         return P.tdse_2e_64_subdomains()
     raise SystemExit(f"unknown workload {name}")
+
+
+def batched_config(insts) -> dict:
+    n1 = sum(1 for i in insts if i.n_elec == 1)
+    kk = [kd ** i.n_elec for i in insts for kd in i.K_d]
+    return {"workload": BATCHED, "instances": len(insts), "one_electron": n1, "two_electron": len(insts) - n1,
+            "subdomains": sum(i.n_sub for i in insts), "K_min": min(kk), "K_max": max(kk),
+            "K_mean": sum(kk) / len(kk), "seed": 171002401, "dt": 0.1, "mu": "10.0", "ngf_tol": 1e-12,
+            "max_steps": 5000, "l2": "flushed (256 MB write) before every step; step matrices (>=100 GB per chunk) "
+            "exceed L2", "parallelism": "instances sharded over ranks (no data-path collective)",
+            "step": "one Schwarz iteration of every instance (chunks sized to the free HBM, each one "
+                    "persistent window launch per iteration, replayed from a captured CUDA graph)"}
 
 
 def workload_config(name: str, inst) -> dict:
@@ -137,9 +154,47 @@ def oracle_sample(inst, gpu_solves_per_iter=None):
     return solves / t_it, desc, t_asm
 
 
+def batched_oracle_sample(insts):
+    """Bounded oracle sample of the batched workload: the first Schwarz
+    iteration of its smallest 1-electron and smallest 2-electron instances
+    (fewest subdomains), local assembly excluded from the rate."""
+    from oracle import swr_oracle as O
+    pick = [min((i for i in insts if i.n_elec == n), key=lambda i: (i.n_sub, sum(i.K_d))) for n in (1, 2)]
+    solves, t_it = 0, 0.0
+    for inst in pick:
+        locs = O.assemble(inst)
+        t0 = time.perf_counter()
+        r = O.run_swr(inst, kmax=1, tol=0.0, locs=locs)
+        t_it += time.perf_counter() - t0
+        solves += r.records[0].n_win * inst.n_sub
+    desc = (f"oracle (numpy FP64) on the batch's smallest 1-electron and 2-electron instances "
+            f"({pick[0].n_sub} and {pick[1].n_sub} subdomains): first Schwarz iteration, {solves} local "
+            f"step solves in {t_it:.2f} s, local assembly excluded")
+    return solves, t_it, desc
+
+
 def run_reference(args, inst, name):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if name == BATCHED:
+        for _ in range(args.warmup):
+            batched_oracle_sample(inst)
+        solves, t_tot = 0, 0.0
+        for _ in range(args.steps):
+            n, t, desc = batched_oracle_sample(inst)
+            solves += n
+            t_tot += t
+        value = solves / t_tot
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "subdomain solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": batched_config(inst),
+            "cpu_baseline": {"value": value, "unit": "subdomain solves/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": "each step: " + desc},
+            "e2e": {"value": value, "unit": "subdomain solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
         return
     from oracle import swr_oracle as O
     locs = O.assemble(inst)
@@ -167,6 +222,148 @@ def run_reference(args, inst, name):
     }))
 
 
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path))["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
+    return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def run_batched(args, insts, env):
+    """The uneven batch: instances sharded over ranks, cut into chunks that fit
+    the free HBM; per chunk setup + assembly + window autotune (untimed), W
+    warm-up and K timed Schwarz iterations (CUDA events around each swr_step,
+    L2 flushed before each)."""
+    S, torch, dist, dev, stream, flush, world, rank, local = env
+    from paper_1710_02401_gb300 import dist as D
+    mine = [insts[i] for i in D.shard(insts, rank, world)]
+    prec_of = {"mixed": S.PREC_MIXED, "fp64": S.PREC_FP64}
+
+    def chunks_for(prec):
+        free, _ = torch.cuda.mem_get_info(dev)
+        budget = 0.85 * free
+        out, cur, cur_b = [], [], 0
+        for inst in mine:
+            b = S.workspace_bytes(inst, prec) + (1 << 20)
+            if cur and cur_b + b > budget:
+                out.append(cur)
+                cur, cur_b = [], 0
+            cur.append(inst)
+            cur_b += b
+        if cur:
+            out.append(cur)
+        return out
+
+    def run(prec_name, steps, warmup, sample_clocks):
+        prec = prec_of[prec_name]
+        t_ms, solves, wbytes, wms, wlaunch, launches = 0.0, 0, 0.0, 0.0, 0, 0
+        e2e_wall, e2e_solves, h2d, d2h, tunes, energies, first_e = 0.0, 0, 0, 0, [], [], []
+        chunks = chunks_for(prec)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+        for chunk in chunks:
+            torch.cuda.synchronize(dev)
+            w0 = time.perf_counter()
+            s = S.SWR(chunk, precision=prec, device=str(dev), stream=stream)
+            s.assemble()
+            tunes.append(s.autotune(steps=24))
+            for w in range(warmup):
+                e2e_solves += s.step().subdomain_solves
+                if w == 0:
+                    first_e += [float(x) for x in s.energy()]
+            c0 = s.counters()
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = s.step()
+                e1.record(stream)
+                e1.synchronize()
+                t_ms += e0.elapsed_time(e1)
+                solves += r.subdomain_solves
+                e2e_solves += r.subdomain_solves
+            c1 = s.counters()
+            energies += [float(x) for x in s.energy()]
+            s.close()
+            del s
+            torch.cuda.synchronize(dev)
+            e2e_wall += time.perf_counter() - w0
+            wbytes += c1["window_bytes"] - c0["window_bytes"]
+            wms += c1["window_ms"] - c0["window_ms"]
+            wlaunch += int(c1["window_launches"] - c0["window_launches"])
+            launches += int(c1["kernel_launches"] - c0["kernel_launches"])
+            h2d += int(c1["h2d_bytes"])
+            d2h += int(c1["d2h_bytes"])
+        clocks = sampler.stop() if sampler else None
+        t_max, solves_all = D.combine(t_ms * 1e-3, solves)
+        e_max, e_solves_all = D.combine(e2e_wall, e2e_solves)
+        return dict(value=solves_all / t_max, t_max=t_max, wbytes=wbytes, wms=wms, wlaunch=wlaunch,
+                    launches=launches, e2e=e_solves_all / e_max, h2d=h2d, d2h=d2h, tunes=tunes,
+                    chunks=len(chunks), clocks=clocks, energies=energies, first_e=first_e)
+
+    main_run = run(args.precision, args.steps, args.warmup, True)
+    other = None
+    if not args.no_compare:
+        other_name = "fp64" if args.precision == "mixed" else "mixed"
+        other = run(other_name, args.steps, args.warmup, False)
+        other["name"] = other_name
+    if rank != 0:
+        return
+    peak, peak_src = hbm_peak()
+    gbs = main_run["wbytes"] / (main_run["wms"] * 1e-3) / 1e9 if main_run["wms"] > 0 else 0.0
+    kname = "k_window_2ph<true>" if args.precision == "mixed" else "k_window_2ph<false>"
+    roof = {"kernel": kname, "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak, "peak_source": peak_src,
+            "algorithmic": "8 bytes of the step-matrix inverse per element (FP32 hi/lo planes or FP64) per local "
+                           "step solve, K^2 elements per solve; each chunk's matrices (>= 100 GB) stream from HBM "
+                           "every step",
+            "window_ms_per_launch": main_run["wms"] / max(1, main_run["wlaunch"])}
+    ratio, src = profiled_traffic(kname + "@batched")
+    roof["traffic"] = ratio * main_run["wbytes"] / max(1, main_run["wlaunch"]) if ratio else None
+    roof["traffic_source"] = src
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        n, t, desc = batched_oracle_sample(insts)
+        cpu = {"value": n / t, "unit": "subdomain solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": desc}
+    it = args.warmup + args.steps
+    out = {
+        "metric": METRIC, "value": main_run["value"], "unit": "subdomain solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * main_run["t_max"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32x2 (double-single) step matrices, f64 reductions" if args.precision == "mixed" else "f64",
+        "data": "synthetic", "config": dict(batched_config(insts), chunks=main_run["chunks"]),
+        "precision": args.precision, "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": main_run["e2e"], "unit": "subdomain solves/s",
+                "h2d_bytes_per_step": main_run["h2d"] // it, "d2h_bytes_per_step": main_run["d2h"] // it,
+                "note": "whole public-API path per chunk: setup from host descriptors, assembly, autotune, "
+                        "all warm-up and timed iterations, energy read-back, teardown"},
+        "gpu_launches": main_run["launches"],
+        "clocks": main_run["clocks"],
+        "autotune": [{k: t[k] for k in ("variant", "rows_per_task", "tasks", "ctas", "task_state_global")}
+                     for t in main_run["tunes"]],
+        "energy_first": main_run["energies"][:4],
+    }
+    if other is not None:
+        out["other_precision"] = {"precision": other["name"], "value": other["value"],
+                                  "ms_per_step": 1e3 * other["t_max"] / args.steps,
+                                  "speedup_of_headline": main_run["value"] / other["value"],
+                                  # same inputs: the first Schwarz iteration of every instance
+                                  "max_rel_energy_difference_first_iteration": max(
+                                      abs(a - b) / max(abs(b), 1e-300)
+                                      for a, b in zip(main_run["first_e"], other["first_e"])),
+                                  "note": "later iterations of the 1-electron instances with 30-64 subdomains "
+                                          "separate between precisions: their Schwarz trajectories amplify "
+                                          "1e-14 perturbations to O(0.1) within three iterations (also in the "
+                                          "oracle)"}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,9 +379,13 @@ def main():
     ap.add_argument("--iterations", type=int, default=0,
                     help="fixed Schwarz iterations per step instead of iterating to Res <= 1e-8 "
                          "(for the long real-time workload)")
+    ap.add_argument("--batch-instances", type=int, default=512,
+                    help="batched workload: first N instances of the 512 (a bounded run)")
     args = ap.parse_args()
     name = args.workload
     inst = workload(name)
+    if name == BATCHED:
+        inst = inst[:args.batch_instances]
     if args.impl == "reference":
         run_reference(args, inst, name)
         return
@@ -208,6 +409,11 @@ def main():
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     prec_of = {"mixed": S.PREC_MIXED, "fp64": S.PREC_FP64}
+    if name == BATCHED:
+        run_batched(args, inst, (S, torch, dist, dev, stream, flush, world, rank, local))
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     def timed(prec_name, steps, warmup, sample_clocks):
         """W untimed + K timed steps (assemble + iterate to Res <= TOL), CUDA

@@ -177,6 +177,30 @@ def _to_c_instance(inst: P.Instance, keep: list) -> swr_instance:
     return ci
 
 
+def workspace_bytes(instances, precision: int = PREC_FP64, window_variant: int = 0,
+                    rows_per_task: int = 0) -> int:
+    """Device bytes a context over `instances` needs (swr_workspace_size)."""
+    lib = load_library()
+    if isinstance(instances, P.Instance):
+        instances = [instances]
+    keep: list = []
+    arr = (swr_instance * len(instances))()
+    for i, inst in enumerate(instances):
+        arr[i] = _to_c_instance(inst, keep)
+    prob = swr_problem()
+    prob.n_instances = len(instances)
+    prob.instances = C.cast(arr, C.POINTER(swr_instance))
+    prob.precision = precision
+    prob.window_variant = int(window_variant)
+    prob.rows_per_task = int(rows_per_task)
+    n = C.c_size_t(0)
+    st = lib.swr_workspace_size(C.byref(prob), C.byref(n))
+    if st != SWR_OK:
+        msg = lib.swr_last_error(None)
+        raise SWRError(st, msg.decode() if msg else "")
+    return int(n.value)
+
+
 class SWR:
     """One SWR context over a batch of instances (all subdomains of all
     instances in one sweep).  Device memory is a torch uint8 tensor owned by
