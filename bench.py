@@ -35,20 +35,42 @@ METRIC = "SWR time-to-1e-8 interface residual; subdomain solves/s vs plain FP64 
 # independent FMA chains over all SMs (the ceilings of the window kernel)
 FP64_PEAK_TFLOPS = 1.01
 FP32_PEAK_TFLOPS = 67.7
-# DRAM bytes per launch of the window kernels from one ncu capture (profiles/), valid
-# only while the kernel source is the one that was profiled (sha256 prefix of swr_window.cu)
+# DRAM traffic of the window kernels from one ncu capture each (profiles/): bytes per
+# launch, or for the batched case bytes per algorithmic byte, valid only while the
+# source of the kernel and of the device functions it calls is the one that was
+# profiled (sha256 prefix over those functions' text in swr_window.cu)
+KERNEL_FUNCS = {
+    "k_window_fused": ["reduce_barrier", "reduce_barrier2", "two_sum", "make_task_cache", "z_rows_sm",
+                       "k_window_fused"],
+    "k_window_2ph<false>": ["reduce_barrier", "make_task_cache", "z_rows_sm", "z_rows_staged", "fp64_rows4",
+                            "k_window_2ph"],
+    "k_window_2ph<true>": ["reduce_barrier", "two_sum", "make_task_cache", "z_rows_sm", "z_rows_staged",
+                           "df32_acc", "df32_rows4", "k_window_2ph"],
+}
+KERNEL_FUNCS["k_window_2ph<true>@batched"] = KERNEL_FUNCS["k_window_2ph<true>"]
 PROFILED_TRAFFIC = {
-    "k_window_df32": ("9feb1703488c26c7", 327.6e6, "profiles/k_window_df32_tise_2e_16sd.md"),
-    "k_window_fp64": ("9feb1703488c26c7", 280.5e6, "profiles/k_window_fp64_tise_2e_16sd.md"),
+    "k_window_fused": ("9f44120ea1da08af", 331.2e6, "profiles/k_window_fused_tise_2e_16sd.md"),
+    "k_window_2ph<false>": ("adf87af87bbeba68", 279.3e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
 }
 
 
-def profiled_traffic(kernel):
+def kernel_source_hash(kernel):
+    """sha256 prefix of the text of the functions `kernel` is built from."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1710_02401_gb300", "csrc", "swr_window.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    import re
+    src = open(os.path.join(ROOT, "paper_1710_02401_gb300", "csrc", "swr_window.cu")).read()
+    h = hashlib.sha256()
+    for fn in KERNEL_FUNCS[kernel]:
+        m = re.search(r"^[^\n]*\b" + re.escape(fn) + r"\(.*?^}\n", src, re.M | re.S)
+        if m is None:
+            return None
+        h.update(m.group(0).encode())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
     rec = PROFILED_TRAFFIC.get(kernel)
-    if rec is None or rec[0] != h:
+    if rec is None or kernel not in KERNEL_FUNCS or rec[0] != kernel_source_hash(kernel):
         return None, None
     return rec[1], rec[2]
 
@@ -75,7 +97,7 @@ def batched_config(insts) -> dict:
     return {"workload": BATCHED, "instances": len(insts), "one_electron": n1, "two_electron": len(insts) - n1,
             "subdomains": sum(i.n_sub for i in insts), "K_min": min(kk), "K_max": max(kk),
             "K_mean": sum(kk) / len(kk), "seed": 171002401, "dt": 0.1, "mu": "10.0", "ngf_tol": 1e-12,
-            "max_steps": 5000, "l2": "flushed (256 MB write) before every step; step matrices (>=100 GB per chunk) "
+            "max_steps": max(i.max_steps for i in insts), "l2": "flushed (256 MB write) before every step; step matrices (>=100 GB per chunk) "
             "exceed L2", "parallelism": "instances sharded over ranks (no data-path collective)",
             "step": "one Schwarz iteration of every instance (chunks sized to the free HBM, each one "
                     "persistent window launch per iteration, replayed from a captured CUDA graph)"}
@@ -268,9 +290,9 @@ def run_batched(args, insts, env):
         for chunk in chunks:
             torch.cuda.synchronize(dev)
             w0 = time.perf_counter()
-            s = S.SWR(chunk, precision=prec, device=str(dev), stream=stream)
+            s = S.SWR(chunk, precision=prec, device=str(dev), stream=stream, rows_per_task=args.rows_per_task)
             s.assemble()
-            tunes.append(s.autotune(steps=24))
+            tunes.append(s.window_plan() if args.no_autotune else s.autotune(steps=24))
             for w in range(warmup):
                 e2e_solves += s.step().subdomain_solves
                 if w == 0:
@@ -381,11 +403,17 @@ def main():
                          "(for the long real-time workload)")
     ap.add_argument("--batch-instances", type=int, default=512,
                     help="batched workload: first N instances of the 512 (a bounded run)")
+    ap.add_argument("--max-steps", type=int, default=0,
+                    help="batched workload: imaginary-time window cap (default: the instances' 5000)")
+    ap.add_argument("--rows-per-task", type=int, default=0, help="batched workload: window row-task size")
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the automatic plan")
     args = ap.parse_args()
     name = args.workload
     inst = workload(name)
     if name == BATCHED:
         inst = inst[:args.batch_instances]
+        if args.max_steps > 0:
+            inst = [i.replace(max_steps=args.max_steps) for i in inst]
     if args.impl == "reference":
         run_reference(args, inst, name)
         return

@@ -329,6 +329,36 @@ __device__ void z_rows_staged(const TaskCache& tc, const double* P1g, const doub
     __syncthreads();
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 by the copy engine (no registers, no
+// shared memory): the range is widened to 16-byte boundaries (it stays inside
+// the workspace, whose matrices are followed by other arena data) and issued
+// in pieces of at most 64 KB.
+__device__ inline void prefetch_l2(const void* p, size_t bytes) {
+    const unsigned long long g = (unsigned long long)__cvta_generic_to_global(p);
+    unsigned long long a = g & ~15ULL;
+    const unsigned long long e = (g + bytes + 15ULL) & ~15ULL;
+    while (a < e) {
+        const unsigned n = (unsigned)((e - a) < 65536ULL ? (e - a) : 65536ULL);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+        a += n;
+    }
+}
+
+// Lane 0 prefetches rows [rb, rb + nrow) of the task's step matrix (both FP32
+// planes, or the FP64 rows).
+template <bool DF32>
+__device__ inline void prefetch_rows(const SwrDeviceView& v, const TaskCache& tc, int rb, int nrow) {
+    if (nrow <= 0) return;
+    if (DF32) {
+        const long long ld = df32_ld(tc.K);
+        const float* Gh = (const float*)(v.arena + tc.Gf);
+        prefetch_l2(Gh + rb * ld, (size_t)nrow * ld * sizeof(float));
+        prefetch_l2(Gh + (long long)tc.K * ld + rb * ld, (size_t)nrow * ld * sizeof(float));
+    } else {
+        prefetch_l2(v.arena + tc.Gm + (long long)rb * tc.K, (size_t)nrow * tc.K * sizeof(double));
+    }
+}
+
 // One double-single multiply-add: (yh, yl) += (g0 + g1)(x0 + x1), TwoProduct of
 // the leading terms, TwoSum into (yh, yl), the cross terms into yl.
 __device__ inline void df32_acc(float& yh, float& yl, float g0, float g1, float x0, float x1) {
@@ -501,6 +531,9 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_2ph(SweepArgs A) {
             const int K = tc.K, nr = tc.nr;
             const int t = A.cta_list[t_begin + j];
             const bool load = (tc.sid != vs_sid);
+            // the warp's first block of rows travels to L2 while v and the partials are formed
+            if (many && lane == 0 && n < tc.maxs)
+                prefetch_rows<DF32>(v, tc, tc.r0 + 4 * warp, min(4, tc.r0 + nr - (tc.r0 + 4 * warp)));
             // one round trip: s_n, y^n, b'^{n+1}
             const double s_n = __ldcg(sc_n + tc.inst), is_n = __ldcg(sc_n + v.n_inst + tc.inst);
             const double is_p = n == 0 ? 1.0 : __ldcg(sc_p + v.n_inst + tc.inst);
@@ -559,6 +592,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_2ph(SweepArgs A) {
             const float* Gl = Gh + (long long)K * ld;
             for (int rb = tc.r0 + 4 * warp; rb < tc.r0 + nr; rb += 4 * nw) {
                 const int nrow = min(4, tc.r0 + nr - rb);
+                if (many && lane == 0) prefetch_rows<DF32>(v, tc, rb + 4 * nw, min(4, tc.r0 + nr - (rb + 4 * nw)));
                 double y[4];
                 if (DF32) df32_rows4(Gh, Gl, ld, vf, rb, nrow, lane, y);
                 else fp64_rows4(v.arena + tc.Gm, K, vs, rb, nrow, lane, y);
