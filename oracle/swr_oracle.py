@@ -17,6 +17,11 @@ Schroedinger Equation"), in plain, slow numpy:
                          solutions": A_i, H~_i (incl. Robin R_i), Q_i
   Robin TC ............ Sec. 5.1, Eq. RTC; averaging over several overlapping
                          subdomains (Sec. 5.1, multi-subdomain zones)
+  basis reduction ..... Sec. 2's Gaussian overlaps are ill-conditioned: per
+                         coordinate Cholesky when every pivot >= tau * max
+                         diagonal, else canonical orthogonalisation (eigen-
+                         vectors with lambda > tau lambda_max); solves run in
+                         the retained subspace
   initial data ........ Sec. 6.1 (Test 1.a): c~ = <phi0, v>, A c = c~
   time stepping ....... Sec. 5.4 step 2: Crank-Nicolson (real time), implicit
                          Euler (imaginary time), step 4 normalisation
@@ -220,6 +225,49 @@ class Local:
     own_vals: np.ndarray = None   # (G, K) basis values on Gamma nodes
     contrib: list = None     # per Gamma node: list of contributing subdomains
     c0: np.ndarray = None
+    Xr: np.ndarray = None    # (K, r) basis of the retained subspace (canonical orthogonalisation), None: all of it
+
+
+def overlap_1d(inst, basis: "Basis", d: int) -> np.ndarray:
+    """S_d[a][c] = int phi_a phi_c over the subdomain's interval of coordinate d
+    (the composite Gauss-Legendre rule of the volume quadrature)."""
+    x, w = nodes_1d(inst, basis.midx[d])
+    F = phi(x[:, None], basis.centres[d][None, :], basis.delta)
+    return F.T @ (w[:, None] * F)
+
+
+def orth_coordinate(S: np.ndarray, tau: float):
+    """Per-coordinate orthogonalisation of Sec. 2's Gaussian basis (reading:
+    the Gaussian overlaps are ill-conditioned, so the basis is reduced when
+    they are numerically singular).  Cholesky S = L L^T succeeds when every
+    pivot is at least tau times the largest diagonal entry: the whole basis is
+    kept (None).  Otherwise canonical orthogonalisation: S = U diag(lam) U^T,
+    keep the eigenvectors with lam > tau * lam_max, X = U_r lam_r^(-1/2)."""
+    n = S.shape[0]
+    dmax = float(np.max(np.diag(S)))
+    Lc = np.array(S, dtype=float)
+    ok = True
+    for j in range(n):  # plain right-looking Cholesky, pivot by pivot
+        pj = Lc[j, j] - float(np.dot(Lc[j, :j], Lc[j, :j]))
+        if not pj > tau * dmax:
+            ok = False
+            break
+        Lc[j, j] = math.sqrt(pj)
+        for i in range(j + 1, n):
+            Lc[i, j] = (Lc[i, j] - float(np.dot(Lc[i, :j], Lc[j, :j]))) / Lc[j, j]
+    if ok:
+        return None
+    lam, U = np.linalg.eigh(S)
+    keep = lam > tau * float(np.max(lam))
+    return U[:, keep] / np.sqrt(lam[keep])[None, :]
+
+
+def reduced_solve(loc: "Local", M: np.ndarray, rhs: np.ndarray) -> np.ndarray:
+    """Solution of M c = rhs restricted to the retained subspace: c = Xr y with
+    (Xr^T M Xr) y = Xr^T rhs (the plain solve when the whole basis is kept)."""
+    if loc.Xr is None:
+        return np.linalg.solve(M, rhs)
+    return loc.Xr @ np.linalg.solve(loc.Xr.T @ M @ loc.Xr, loc.Xr.T @ rhs)
 
 
 def gamma_nodes(inst, sid: int) -> GammaSet:
@@ -302,9 +350,15 @@ def build_local(inst, sid: int) -> Local:
     # contributors of every interface node: the other subdomains whose closure holds it
     loc.contrib = [[j for j in range(inst.n_sub) if j != sid and contains_closed(inst, j, x)]
                    for x in gam.X]
+    # retained subspace: per coordinate Cholesky or canonical orthogonalisation,
+    # the tensor product over coordinates (index m = a + K_d b: kron(X_2, X_1))
+    xs = [orth_coordinate(overlap_1d(inst, basis, d), inst.orth_tau) for d in range(N)]
+    if any(x is not None for x in xs):
+        full = [np.eye(basis.kd) if x is None else x for x in xs]
+        loc.Xr = full[0] if N == 1 else np.kron(full[1], full[0])
     # initial data: c~_l = <phi0, v_l>_{Omega_i}, A c = c~  (Sec. 6.1)
     ct = B.T @ (w * phi0_values(inst, X))
-    loc.c0 = np.linalg.solve(loc.A, ct)
+    loc.c0 = reduced_solve(loc, loc.A, ct)
     return loc
 
 
@@ -452,8 +506,9 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
 
     # imaginary time: (A + dt H~) c~^{n+1} = A c^n + kappa dt b^{n+1}
     lu_ie = None
-    if not tdse:
-        lu_ie = [sla.lu_factor(l.A + dt * l.Ht) for l in locs]
+    if not tdse:  # factorised once, in the retained subspace when the basis is reduced
+        lu_ie = [sla.lu_factor(l.A + dt * l.Ht if l.Xr is None else l.Xr.T @ (l.A + dt * l.Ht) @ l.Xr)
+                 for l in locs]
 
     result = SWRResult(locs=locs)
     for k in range(1, kmax + 1):
@@ -476,11 +531,11 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
                     M1 = l.A + 0.5j * dt * (l.Ht + e1 * l.Qx)
                     M0 = l.A - 0.5j * dt * (l.Ht + e0 * l.Qx)
                     rhs = M0 @ coeffs[i] + 0.5j * dt * kappa * (b_vec(i, g_at(i, n + 1)) + b_vec(i, g_at(i, n)))
-                    new.append(np.linalg.solve(M1, rhs))
+                    new.append(reduced_solve(l, M1, rhs))
             else:
                 for i, l in enumerate(locs):
                     rhs = l.A @ coeffs[i] + kappa * dt * b_vec(i, g_at(i, n + 1))
-                    new.append(sla.lu_solve(lu_ie[i], rhs))
+                    new.append(sla.lu_solve(lu_ie[i], rhs) if l.Xr is None else l.Xr @ sla.lu_solve(lu_ie[i], l.Xr.T @ rhs))
                 raw = new
                 if inst.normalize:
                     s = math.sqrt(pou_norm2(locs, new))
@@ -536,5 +591,9 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
 # ---------------------------------------------------- single-domain helpers
 
 def generalized_eigs(loc: Local, kinetic_only_h=False):
-    """Eigenvalues of H~ c = lambda A c for one subdomain (brute force check)."""
-    return sla.eigh(np.real(loc.Ht), loc.A, eigvals_only=True)
+    """Eigenvalues of H~ c = lambda A c for one subdomain (brute force check),
+    in the retained subspace when the basis is reduced."""
+    if loc.Xr is None:
+        return sla.eigh(np.real(loc.Ht), loc.A, eigvals_only=True)
+    X = loc.Xr
+    return sla.eigh(X.T @ np.real(loc.Ht) @ X, X.T @ loc.A @ X, eigvals_only=True)

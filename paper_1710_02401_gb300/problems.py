@@ -60,6 +60,8 @@ class Instance:
     field: Tuple[float, float, float, float] = (0.0, 1.0, 0.0, 0.0)  # (E0, T, omega, phase)
     phi0_gamma: float = 1.0              # phi0 = exp(-gamma |x - x0|^2)
     phi0_center: Tuple[float, float] = (0.0, 0.0)
+    orth_tau: float = 1e-12              # per-coordinate overlap: Cholesky if every pivot >= tau * max diagonal,
+                                         # else canonical (eigenvectors with lambda > tau * lambda_max)
 
     @property
     def n_sub(self) -> int:

@@ -187,6 +187,34 @@ def test_harmonic_oscillator_generalized_eigenvalues():
     assert np.allclose(ev[:3], [0.5, 1.5, 2.5], atol=1e-9)
 
 
+def test_canonical_orthogonalisation_of_an_overcomplete_basis():
+    # 60 Gaussians of width ~1.3 at spacing 0.36: the overlap Cholesky meets a
+    # pivot below 1e-12 of the diagonal, so the basis is reduced to the
+    # eigenvectors of S above 1e-12 lambda_max (X^T S X = I on them); the
+    # oscillator spectrum n + 1/2 is still reproduced to the accuracy the
+    # retained subspace can carry
+    inst = _ho(1, 60, 0.3)
+    loc = O.build_local(inst, 0)
+    S = O.overlap_1d(inst, loc.basis, 0)
+    X = O.orth_coordinate(S, inst.orth_tau)
+    assert X is not None and 0 < X.shape[1] < 60
+    # orthonormal to the rounding of the smallest kept eigenpairs (eps lambda_max / lambda ~ 1e-4)
+    np.testing.assert_allclose(X.T @ S @ X, np.eye(X.shape[1]), atol=1e-4)
+    lam = np.linalg.eigvalsh(S)
+    assert X.shape[1] == int(np.sum(lam > inst.orth_tau * lam.max()))
+    ev = O.generalized_eigs(loc)
+    assert abs(ev[0] - 0.5) < 1e-6 and abs(ev[1] - 1.5) < 1e-5
+    assert np.allclose(ev[:4], [0.5, 1.5, 2.5, 3.5], atol=1e-3)
+    # a well-conditioned basis keeps every function (Cholesky path)
+    assert O.orth_coordinate(O.overlap_1d(_ho(1, 20, 2.0), O.Basis(_ho(1, 20, 2.0), 0), 0), 1e-12) is None
+
+
+def test_swr_on_reduced_bases_converges_to_ground_state():
+    r = O.run_swr(_ho(2, 60, 0.3, ngf_tol=1e-10), kmax=40, tol=1e-8)
+    assert all(l.Xr is not None for l in r.locs)
+    assert r.converged and abs(r.records[-1].energy - 0.5) < 1e-4
+
+
 def test_two_electron_harmonic_ground_state():
     # K_d odd and delta = 1/2: the exact ground state exp(-(x1^2+x2^2)/2) is the
     # centre basis function, so E0 = 1 up to rounding; E1 = 2 (twice degenerate)
