@@ -121,6 +121,13 @@ typedef struct swr_instance {
     double field_E0, field_T, field_omega, field_phase; /* e(t) = E0 sin^2(pi t/T) sin(omega t + phase), 0 <= t <= T */
     double phi0_gamma;      /* phi0 = exp(-gamma |x - x0|^2)                       */
     double phi0_center[2];
+    double orth_tau;        /* basis reduction (Sec. 2's Gaussian overlaps are ill-
+                               conditioned): per coordinate, Cholesky of the 1-D
+                               overlap S when every pivot >= orth_tau * max diag,
+                               else canonical orthogonalisation, keeping the
+                               eigenvectors with lambda > orth_tau * lambda_max
+                               (X = U_r lambda_r^-1/2, the other columns zero).
+                               0 selects 1e-12; must be < 1                      */
 } swr_instance;
 
 typedef struct swr_problem {

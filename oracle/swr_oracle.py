@@ -20,8 +20,9 @@ Schroedinger Equation"), in plain, slow numpy:
   basis reduction ..... Sec. 2's Gaussian overlaps are ill-conditioned: per
                          coordinate Cholesky when every pivot >= tau * max
                          diagonal, else canonical orthogonalisation (eigen-
-                         vectors with lambda > tau lambda_max); solves run in
-                         the retained subspace
+                         vectors with lambda > tau lambda_max), the local
+                         basis being the tensor product of the kept
+                         per-coordinate functions
   initial data ........ Sec. 6.1 (Test 1.a): c~ = <phi0, v>, A c = c~
   time stepping ....... Sec. 5.4 step 2: Crank-Nicolson (real time), implicit
                          Euler (imaginary time), step 4 normalisation
@@ -134,9 +135,14 @@ def dphi(x, alpha, delta):
 
 class Basis:
     """Tensor-product Gaussian basis of one subdomain: v_m = prod_d phi_{a_d}(x_d),
-    m = a_1 + K_d a_2 (Sec. 2, v_{l,p}(x1,x2) = phi_l(x1) phi_p(x2))."""
+    m = a_1 + K_d a_2 (Sec. 2, v_{l,p}(x1,x2) = phi_l(x1) phi_p(x2)).
 
-    def __init__(self, inst, sid: int):
+    With per-coordinate transforms T_d (K_d x r_d, canonical orthogonalisation)
+    the functions of coordinate d are phi'_i = sum_a T_d[a, i] phi_a and the
+    basis is their tensor product (index i_1 + r_1 i_2): each factor is
+    evaluated per coordinate, so the products stay O(1) functions."""
+
+    def __init__(self, inst, sid: int, transforms=None):
         self.inst = inst
         self.sid = sid
         self.N = inst.n_elec
@@ -144,27 +150,30 @@ class Basis:
         self.delta = inst.delta_of(sid)
         self.midx = sub_multi_index(inst, sid)
         self.centres = [centres_1d(inst, sid, k) for k in self.midx]
-        self.K = self.kd ** self.N
+        self.T = list(transforms) if transforms is not None else [None] * self.N
+        self.r = [self.kd if t is None else t.shape[1] for t in self.T]
+        self.K = int(np.prod(self.r))
+
+    def _factor(self, x, d, fn):
+        f = fn(x[:, None], self.centres[d][None, :], self.delta)
+        return f if self.T[d] is None else f @ self.T[d]
+
+    def _tensor(self, f, npts):
+        if self.N == 1:
+            return f[0]
+        # m = a + r_1 * b  ->  column index b*r_1 + a
+        return (f[1][:, :, None] * f[0][:, None, :]).reshape(npts, -1)
 
     def values(self, X):
         """X: (P, N) points -> (P, K) basis values."""
         X = np.atleast_2d(X)
-        f = [phi(X[:, d][:, None], self.centres[d][None, :], self.delta) for d in range(self.N)]
-        if self.N == 1:
-            return f[0]
-        # m = a + K_d * b  ->  column index b*K_d + a
-        return (f[1][:, :, None] * f[0][:, None, :]).reshape(X.shape[0], -1)
+        return self._tensor([self._factor(X[:, d], d, phi) for d in range(self.N)], X.shape[0])
 
     def grad(self, X, dim: int):
         """d/dx_dim of every basis function at the points X."""
         X = np.atleast_2d(X)
-        f = []
-        for d in range(self.N):
-            fn = dphi if d == dim else phi
-            f.append(fn(X[:, d][:, None], self.centres[d][None, :], self.delta))
-        if self.N == 1:
-            return f[0]
-        return (f[1][:, :, None] * f[0][:, None, :]).reshape(X.shape[0], -1)
+        return self._tensor([self._factor(X[:, d], d, dphi if d == dim else phi) for d in range(self.N)],
+                            X.shape[0])
 
 
 # --------------------------------------------------------------- potential
@@ -225,7 +234,6 @@ class Local:
     own_vals: np.ndarray = None   # (G, K) basis values on Gamma nodes
     contrib: list = None     # per Gamma node: list of contributing subdomains
     c0: np.ndarray = None
-    Xr: np.ndarray = None    # (K, r) basis of the retained subspace (canonical orthogonalisation), None: all of it
 
 
 def overlap_1d(inst, basis: "Basis", d: int) -> np.ndarray:
@@ -260,14 +268,6 @@ def orth_coordinate(S: np.ndarray, tau: float):
     lam, U = np.linalg.eigh(S)
     keep = lam > tau * float(np.max(lam))
     return U[:, keep] / np.sqrt(lam[keep])[None, :]
-
-
-def reduced_solve(loc: "Local", M: np.ndarray, rhs: np.ndarray) -> np.ndarray:
-    """Solution of M c = rhs restricted to the retained subspace: c = Xr y with
-    (Xr^T M Xr) y = Xr^T rhs (the plain solve when the whole basis is kept)."""
-    if loc.Xr is None:
-        return np.linalg.solve(M, rhs)
-    return loc.Xr @ np.linalg.solve(loc.Xr.T @ M @ loc.Xr, loc.Xr.T @ rhs)
 
 
 def gamma_nodes(inst, sid: int) -> GammaSet:
@@ -310,8 +310,10 @@ def phi0_values(inst, X):
 
 def build_local(inst, sid: int) -> Local:
     """Galerkin matrices of Omega_sid by straightforward quadrature on the
-    tensor grid of composite Gauss-Legendre nodes (Sec. 5.1)."""
-    basis = Basis(inst, sid)
+    tensor grid of composite Gauss-Legendre nodes (Sec. 5.1), in the basis
+    kept by the per-coordinate orthogonalisation test (orth_coordinate)."""
+    raw = Basis(inst, sid)
+    basis = Basis(inst, sid, [orth_coordinate(overlap_1d(inst, raw, d), inst.orth_tau) for d in range(raw.N)])
     midx = basis.midx
     N = inst.n_elec
     x1, w1 = nodes_1d(inst, midx[0])
@@ -350,15 +352,9 @@ def build_local(inst, sid: int) -> Local:
     # contributors of every interface node: the other subdomains whose closure holds it
     loc.contrib = [[j for j in range(inst.n_sub) if j != sid and contains_closed(inst, j, x)]
                    for x in gam.X]
-    # retained subspace: per coordinate Cholesky or canonical orthogonalisation,
-    # the tensor product over coordinates (index m = a + K_d b: kron(X_2, X_1))
-    xs = [orth_coordinate(overlap_1d(inst, basis, d), inst.orth_tau) for d in range(N)]
-    if any(x is not None for x in xs):
-        full = [np.eye(basis.kd) if x is None else x for x in xs]
-        loc.Xr = full[0] if N == 1 else np.kron(full[1], full[0])
     # initial data: c~_l = <phi0, v_l>_{Omega_i}, A c = c~  (Sec. 6.1)
     ct = B.T @ (w * phi0_values(inst, X))
-    loc.c0 = reduced_solve(loc, loc.A, ct)
+    loc.c0 = np.linalg.solve(loc.A, ct)
     return loc
 
 
@@ -506,9 +502,8 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
 
     # imaginary time: (A + dt H~) c~^{n+1} = A c^n + kappa dt b^{n+1}
     lu_ie = None
-    if not tdse:  # factorised once, in the retained subspace when the basis is reduced
-        lu_ie = [sla.lu_factor(l.A + dt * l.Ht if l.Xr is None else l.Xr.T @ (l.A + dt * l.Ht) @ l.Xr)
-                 for l in locs]
+    if not tdse:
+        lu_ie = [sla.lu_factor(l.A + dt * l.Ht) for l in locs]
 
     result = SWRResult(locs=locs)
     for k in range(1, kmax + 1):
@@ -531,11 +526,11 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
                     M1 = l.A + 0.5j * dt * (l.Ht + e1 * l.Qx)
                     M0 = l.A - 0.5j * dt * (l.Ht + e0 * l.Qx)
                     rhs = M0 @ coeffs[i] + 0.5j * dt * kappa * (b_vec(i, g_at(i, n + 1)) + b_vec(i, g_at(i, n)))
-                    new.append(reduced_solve(l, M1, rhs))
+                    new.append(np.linalg.solve(M1, rhs))
             else:
                 for i, l in enumerate(locs):
                     rhs = l.A @ coeffs[i] + kappa * dt * b_vec(i, g_at(i, n + 1))
-                    new.append(sla.lu_solve(lu_ie[i], rhs) if l.Xr is None else l.Xr @ sla.lu_solve(lu_ie[i], l.Xr.T @ rhs))
+                    new.append(sla.lu_solve(lu_ie[i], rhs))
                 raw = new
                 if inst.normalize:
                     s = math.sqrt(pou_norm2(locs, new))
@@ -591,9 +586,5 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
 # ---------------------------------------------------- single-domain helpers
 
 def generalized_eigs(loc: Local, kinetic_only_h=False):
-    """Eigenvalues of H~ c = lambda A c for one subdomain (brute force check),
-    in the retained subspace when the basis is reduced."""
-    if loc.Xr is None:
-        return sla.eigh(np.real(loc.Ht), loc.A, eigvals_only=True)
-    X = loc.Xr
-    return sla.eigh(X.T @ np.real(loc.Ht) @ X, X.T @ loc.A @ X, eigvals_only=True)
+    """Eigenvalues of H~ c = lambda A c for one subdomain (brute force check)."""
+    return sla.eigh(np.real(loc.Ht), loc.A, eigvals_only=True)

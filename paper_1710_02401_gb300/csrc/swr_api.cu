@@ -20,7 +20,7 @@
 namespace swr {
 cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, int max_kd, int max_K,
                             bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
-                            const GemmJob* d_jobs2, double* d_norm_part, double tau);
+                            const GemmJob* d_jobs2, double* d_norm_part);
 size_t window_smem(int kmax, int kdmax, int rows_max, int tasks_in_smem, long long g_resident_floats);
 int window_tasks_per_cta_max();
 int window_rows_per_task_max();
@@ -44,7 +44,7 @@ using namespace swr;
 
 static const int GJ_NB_HOST = 32;     // Gauss-Jordan block (matches swr_assemble.cu)
 static const int RES_BLOCKS = 8;      // residual partial blocks per subdomain
-static const double CHOL_TAU = 1e-15; // relative pivot floor of the overlap Cholesky
+static const double ORTH_TAU_DEFAULT = 1e-12;  // basis reduction threshold when an instance gives 0
 static const long long SPIN_LIMIT = 1LL << 24;  // polls (x ~64 ns) before a barrier gives up
 
 struct swr_ctx {
@@ -173,6 +173,8 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
         if (in.n_mid < 1) return fail(c, SWR_EINVAL, "instance %d: n_mid must be >= 1", i);
         int q = (in.n_mid + 2) * in.q_p;
         if (q > 384) return fail(c, SWR_EINVAL, "instance %d: (n_mid+2)*q_p = %d exceeds 384", i, q);
+        if (!(in.orth_tau >= 0.0 && in.orth_tau < 1.0))
+            return fail(c, SWR_EINVAL, "instance %d: orth_tau must be in [0, 1)", i);
         if (in.n_nuclei < 0 || in.n_nuclei > SWR_MAX_NUC) return fail(c, SWR_EINVAL, "instance %d: at most 3 nuclei", i);
         if (!(in.dt > 0)) return fail(c, SWR_EINVAL, "instance %d: dt must be > 0", i);
         if (in.mode == SWR_MODE_TDSE && in.n_steps < 1) return fail(c, SWR_EINVAL, "instance %d: TDSE needs n_steps >= 1", i);
@@ -399,6 +401,7 @@ static void plan(swr_ctx* c) {
         d.gamma0 = in.phi0_gamma;
         d.x0[0] = in.phi0_center[0];
         d.x0[1] = in.phi0_center[1];
+        d.orth_tau = in.orth_tau > 0.0 ? in.orth_tau : ORTH_TAU_DEFAULT;
         if (d.N == 2 && d.ee_coef != 0.0) c->any_ee = true;
         c->inst.push_back(d);
         c->inst_task0.push_back((int)c->tasks.size());
@@ -766,7 +769,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
     CU(cudaEventRecord(c->ev0, c->stream));
     CU(launch_assemble(view(c), c->stream, c->max_q, c->max_kd, c->max_K, c->any_ee, c->tdse, !c->tdse,
-                       c->d_jobs1, c->d_jobs2, c->d_norm_part, CHOL_TAU));
+                       c->d_jobs1, c->d_jobs2, c->d_norm_part));
     if (c->df32 && !c->tdse) CU(launch_split_df32(view(c), c->stream, c->max_K, c->has_w));
     if (c->df32 && c->tdse) CU(launch_split_c_df32(view(c), c->stream, c->max_K));
     CU(cudaEventRecord(c->ev1, c->stream));

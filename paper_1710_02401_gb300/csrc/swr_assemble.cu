@@ -153,10 +153,154 @@ __global__ void k_mat1d(SwrDeviceView v) {
 // the transformed tables B' = B X, D' = D X, L' = L X and the Robin mass
 // Rp = sum over interior sides of l' l'^T.
 #define ORTH_MAX_KD 96
-__global__ void k_orth(SwrDeviceView v, double tau) {
+// Symmetric eigen-decomposition A = V diag(A_jj) V^T of an n x n matrix in
+// shared memory by the cyclic Jacobi method with round-robin ordering: a
+// sweep is n'-1 rounds (n' = n rounded up to even) of n'/2 disjoint index
+// pairs, whose rotations commute and are applied together (two-sided on A,
+// from the right on V).  Rotation of pair (p, q): t = sgn(r)/(|r| + sqrt(1+r^2)),
+// r = (a_qq - a_pp)/(2 a_pq), c = 1/sqrt(1+t^2), s = t c zeroes a_pq.  Sweeps
+// run until the off-diagonal mass is below 1e-28 of the diagonal one (at most
+// 40).  On return A holds the eigenvalues on its diagonal, V the eigenvectors
+// in its columns.
+__device__ void jacobi_eig(double* A, double* V, int n) {
+    __shared__ double s_c[ORTH_MAX_KD / 2], s_s[ORTH_MAX_KD / 2];
+    __shared__ int s_p[ORTH_MAX_KD / 2], s_q[ORTH_MAX_KD / 2];
+    __shared__ double s_red[2][32];
+    __shared__ int s_done;
+    const int m = n + (n & 1), np = m / 2;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e / n == e % n) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        double off = 0, dia = 0;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const double a = A[e];
+            if (e / n == e % n) dia += a * a;
+            else off += a * a;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            dia += __shfl_xor_sync(0xffffffffu, dia, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            s_red[0][threadIdx.x >> 5] = off;
+            s_red[1][threadIdx.x >> 5] = dia;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double o2 = 0, d2 = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                o2 += s_red[0][w];
+                d2 += s_red[1][w];
+            }
+            s_done = !(o2 > 1e-28 * d2);
+        }
+        __syncthreads();
+        if (s_done) break;
+        for (int r = 0; r < m - 1; ++r) {
+            for (int k = threadIdx.x; k < np; k += blockDim.x) {
+                int p = (k == 0) ? r : (r + k) % (m - 1);
+                int q = (k == 0) ? m - 1 : (r - k + (m - 1)) % (m - 1);
+                double c = 1.0, sn = 0.0;
+                if (p < n && q < n) {
+                    const double apq = A[p * n + q];
+                    if (apq != 0.0) {
+                        const double rr = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                        const double t = (rr >= 0.0 ? 1.0 : -1.0) / (fabs(rr) + sqrt(1.0 + rr * rr));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        sn = t * c;
+                    }
+                } else {
+                    p = q = -1;
+                }
+                s_p[k] = p;
+                s_q[k] = q;
+                s_c[k] = c;
+                s_s[k] = sn;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J
+            for (int e = threadIdx.x; e < np * n; e += blockDim.x) {
+                const int k = e / n, i = e - k * n, p = s_p[k], q = s_q[k];
+                if (p < 0) continue;
+                const double c = s_c[k], sn = s_s[k];
+                const double aip = A[i * n + p], aiq = A[i * n + q];
+                A[i * n + p] = c * aip - sn * aiq;
+                A[i * n + q] = sn * aip + c * aiq;
+                const double vip = V[i * n + p], viq = V[i * n + q];
+                V[i * n + p] = c * vip - sn * viq;
+                V[i * n + q] = sn * vip + c * viq;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int e = threadIdx.x; e < np * n; e += blockDim.x) {
+                const int k = e / n, j = e - k * n, p = s_p[k], q = s_q[k];
+                if (p < 0) continue;
+                const double c = s_c[k], sn = s_s[k];
+                const double apj = A[p * n + j], aqj = A[q * n + j];
+                A[p * n + j] = c * apj - sn * aqj;
+                A[q * n + j] = sn * apj + c * aqj;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Right-looking Cholesky of the n x n matrix in L (lower triangle; block-wide).
+// Returns 1 when a pivot is not above tau * (largest diagonal entry).
+__device__ int chol_block(double* L, int n, double tau) {
+    __shared__ int s_bad;
+    __shared__ double s_dmax;
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        double m = 0;
+        for (int j = 0; j < n; ++j) m = fmax(m, L[j * n + j]);
+        s_dmax = m;
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            double pj = L[j * n + j];
+            if (!(pj > tau * s_dmax)) { s_bad = 1; pj = 1.0; }
+            L[j * n + j] = sqrt(pj);
+        }
+        __syncthreads();
+        const double ljj = L[j * n + j];
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) L[i * n + j] /= ljj;
+        __syncthreads();
+        for (int e = threadIdx.x; e < (n - j - 1) * (n - j - 1); e += blockDim.x) {
+            int i = j + 1 + e / (n - j - 1), c = j + 1 + e % (n - j - 1);
+            if (c <= i) L[i * n + c] -= L[i * n + j] * L[c * n + j];
+        }
+        __syncthreads();
+    }
+    const int bad = s_bad;
+    __syncthreads();
+    return bad;
+}
+
+// L (Cholesky factor, lower) -> X = L^{-T} in L (upper triangular, explicit
+// zeros below the diagonal); W is n x n scratch.
+__device__ void chol_inv_t(double* L, double* W, int n) {
+    for (int col = threadIdx.x; col < n; col += blockDim.x) {  // W <- L^{-1}
+        for (int i = 0; i < n; ++i) {
+            double acc = (i == col) ? 1.0 : 0.0;
+            for (int k = col; k < i; ++k) acc -= L[i * n + k] * W[k * n + col];
+            W[i * n + col] = (i < col) ? 0.0 : acc / L[i * n + i];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e / n, j = e % n;
+        L[i * n + j] = W[j * n + i];  // X[i][j] = Linv[j][i]
+    }
+    __syncthreads();
+}
+
+__global__ void k_orth(SwrDeviceView v) {
     const int sid = blockIdx.x, d = blockIdx.y;
     const SubDev& s = v.sub[sid];
     if (d >= s.N) return;
+    const double tau = v.inst[s.inst].orth_tau;
     extern __shared__ double sm[];
     const int kd = s.kd, q = s.q;
     double* Ls = sm;                 // kd*kd: L then X
@@ -164,53 +308,73 @@ __global__ void k_orth(SwrDeviceView v, double tau) {
     double* rowbuf = sm + 2 * kd * kd;  // 8 warps * kd
     double* T = v.arena + s.t1[d];
     T1Layout lay(q, kd);
-    for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) Ls[e] = T[lay.mat(M_S) + e];
+    const double* Sg = T + lay.mat(M_S);
+    double* Xc = T + lay.mat(M_XO);  // canonical X (global scratch; X is stored there at the end)
+    for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) Ls[e] = Sg[e];
     __syncthreads();
-    // right-looking Cholesky, lower triangle of Ls
-    __shared__ int s_bad;
-    __shared__ double s_dmax;
-    if (threadIdx.x == 0) {
-        s_bad = 0;
-        double m = 0;
-        for (int j = 0; j < kd; ++j) m = fmax(m, Ls[j * kd + j]);
-        s_dmax = m;
-    }
-    __syncthreads();
-    for (int j = 0; j < kd; ++j) {
+    const int canonical = chol_block(Ls, kd, tau);
+    if (canonical) {
+        // canonical orthogonalisation: S = U diag(lam) U^T, keep lam > tau lam_max,
+        // Xc = U_r lam_r^{-1/2}; the other columns are zero, so the dropped
+        // directions stay zero in H', G, c0, b' and the norm
+        for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) Ls[e] = Sg[e];
+        __syncthreads();
+        jacobi_eig(Ls, Ts, kd);
+        __shared__ double s_lmax;
         if (threadIdx.x == 0) {
-            double pj = Ls[j * kd + j];
-            if (!(pj > tau * s_dmax)) { s_bad = 1; pj = 1.0; }
-            Ls[j * kd + j] = sqrt(pj);
+            double m = 0;
+            for (int j = 0; j < kd; ++j) m = fmax(m, Ls[j * kd + j]);
+            s_lmax = m;
         }
         __syncthreads();
-        double ljj = Ls[j * kd + j];
-        for (int i = j + 1 + threadIdx.x; i < kd; i += blockDim.x) Ls[i * kd + j] /= ljj;
+        int* keep = (int*)rowbuf;  // kd flags
+        for (int j = threadIdx.x; j < kd; j += blockDim.x) keep[j] = Ls[j * kd + j] > tau * s_lmax;
         __syncthreads();
-        for (int e = threadIdx.x; e < (kd - j - 1) * (kd - j - 1); e += blockDim.x) {
-            int i = j + 1 + e / (kd - j - 1), c = j + 1 + e % (kd - j - 1);
-            if (c <= i) Ls[i * kd + c] -= Ls[i * kd + j] * Ls[c * kd + j];
+        for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {
+            const int j = e % kd;
+            Xc[e] = keep[j] ? Ts[e] / sqrt(Ls[j * kd + j]) : 0.0;
         }
         __syncthreads();
-    }
-    if (s_bad) {
-        if (threadIdx.x == 0) atomicOr(v.err, SWR_ERR_SINGULAR);
-        return;
-    }
-    // X = L^{-T}: solve L^T X = I column by column (X upper triangular).
-    // Ts <- L^{-1} (lower), then X = (L^{-1})^T.
-    for (int col = threadIdx.x; col < kd; col += blockDim.x) {
-        for (int i = 0; i < kd; ++i) {
-            double acc = (i == col) ? 1.0 : 0.0;
-            for (int k = col; k < i; ++k) acc -= Ls[i * kd + k] * Ts[k * kd + col];
-            Ts[i * kd + col] = (i < col) ? 0.0 : acc / Ls[i * kd + i];
+        // Xc^T S Xc equals I only to eps lam_max / lam (small kept eigenvalues):
+        // Gram of the kept columns, G = Xc^T S Xc (e_j for dropped j), is
+        // factorised and Xc re-orthonormalised, X = Xc G_L^{-T}, so X^T S X = I
+        // to rounding
+        for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {  // Ts = S Xc
+            const int i = e / kd, j = e % kd;
+            double acc = 0;
+            for (int k = 0; k < kd; ++k) acc += Sg[i * kd + k] * Xc[k * kd + j];
+            Ts[e] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {  // Ls = Xc^T Ts
+            const int i = e / kd, j = e % kd;
+            double acc = 0;
+            if (keep[i] && keep[j])
+                for (int k = 0; k < kd; ++k) acc += Xc[k * kd + i] * Ts[k * kd + j];
+            else
+                acc = (i == j) ? 1.0 : 0.0;
+            Ls[e] = acc;
+        }
+        __syncthreads();
+        if (chol_block(Ls, kd, 1e-3)) {  // G is near the identity: a failure is a fault
+            if (threadIdx.x == 0) atomicOr(v.err, SWR_ERR_SINGULAR);
+            return;
         }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {
-        int i = e / kd, j = e % kd;
-        Ls[i * kd + j] = Ts[j * kd + i];  // X[i][j] = Linv[j][i]
+    chol_inv_t(Ls, Ts, kd);  // Ls = L^{-T}
+    if (canonical) {
+        for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {  // X = Xc L^{-T}
+            const int i = e / kd, j = e % kd;
+            double acc = 0;
+            for (int k = 0; k < kd; ++k) acc += Xc[i * kd + k] * Ls[k * kd + j];
+            Ts[e] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) Ls[e] = Ts[e];
+        __syncthreads();
     }
-    __syncthreads();
+    // from here on X (in Ls) is dense in general: the sums run over all k (with
+    // the upper-triangular Cholesky X the extra terms are exact zeros)
     for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) T[lay.mat(M_XO) + e] = Ls[e];
     // congruence transforms X^T M X for M in {Kf, U, Schi, Xpos}
     const int srcm[4] = {M_KF, M_U, M_SCHI, M_XPOS};
@@ -221,14 +385,14 @@ __global__ void k_orth(SwrDeviceView v, double tau) {
         for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {  // Ts = M X
             int i = e / kd, j = e % kd;
             double acc = 0;
-            for (int k = 0; k <= j; ++k) acc += Mg[i * kd + k] * Ls[k * kd + j];
+            for (int k = 0; k < kd; ++k) acc += Mg[i * kd + k] * Ls[k * kd + j];
             Ts[e] = acc;
         }
         __syncthreads();
         for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {  // X^T Ts
             int i = e / kd, j = e % kd;
             double acc = 0;
-            for (int k = 0; k <= i; ++k) acc += Ls[k * kd + i] * Ts[k * kd + j];
+            for (int k = 0; k < kd; ++k) acc += Ls[k * kd + i] * Ts[k * kd + j];
             T[lay.mat(dstm[m]) + e] = acc;
         }
     }
@@ -245,7 +409,7 @@ __global__ void k_orth(SwrDeviceView v, double tau) {
             __syncwarp();
             for (int j = lane; j < kd; j += 32) {
                 double acc = 0;
-                for (int k = 0; k <= j; ++k) acc += rb[k] * Ls[k * kd + j];
+                for (int k = 0; k < kd; ++k) acc += rb[k] * Ls[k * kd + j];
                 row[j] = acc;
             }
             __syncwarp();
@@ -663,13 +827,13 @@ extern const int kAssembleLaunchesFixed = 8;
 
 cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, int max_kd, int max_K,
                             bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
-                            const GemmJob* d_jobs2, double* d_norm_part, double tau) {
+                            const GemmJob* d_jobs2, double* d_norm_part) {
     dim3 g2(v.n_sub, 2);
     k_tabulate<<<g2, 256, 0, st>>>(v);
     k_mat1d<<<g2, 256, 0, st>>>(v);
     size_t sm = (2 * (size_t)max_kd * max_kd + 8 * (size_t)max_kd) * sizeof(double);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_orth<<<g2, 256, sm, st>>>(v, tau);
+    k_orth<<<g2, 256, sm, st>>>(v);
     if (any_ee) {
         k_ee_operands<<<dim3(v.n_sub, 16), 256, 0, st>>>(v);
         int kd2 = max_kd * max_kd;

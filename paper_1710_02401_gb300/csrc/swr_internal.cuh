@@ -36,6 +36,7 @@ struct InstDev {
     double mu_re, mu_im, dt, ngf_tol;
     double E0, T, omega, phase;
     double gamma0, x0[2];
+    double orth_tau;              // Cholesky acceptance / canonical cut-off of the 1-D overlaps
 };
 
 // Per-subdomain descriptor.  Offsets are in doubles from the arena base.

@@ -40,7 +40,7 @@ class swr_instance(C.Structure):
         ("normalize", C.c_int), ("dt", C.c_double), ("n_steps", C.c_int), ("ngf_tol", C.c_double),
         ("max_steps", C.c_int), ("field_E0", C.c_double), ("field_T", C.c_double),
         ("field_omega", C.c_double), ("field_phase", C.c_double), ("phi0_gamma", C.c_double),
-        ("phi0_center", C.c_double * 2),
+        ("phi0_center", C.c_double * 2), ("orth_tau", C.c_double),
     ]
 
 
@@ -174,6 +174,7 @@ def _to_c_instance(inst: P.Instance, keep: list) -> swr_instance:
     ci.field_E0, ci.field_T, ci.field_omega, ci.field_phase = (float(f) for f in inst.field)
     ci.phi0_gamma = float(inst.phi0_gamma)
     ci.phi0_center[0], ci.phi0_center[1] = float(inst.phi0_center[0]), float(inst.phi0_center[1])
+    ci.orth_tau = float(inst.orth_tau)
     return ci
 
 
