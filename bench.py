@@ -406,7 +406,7 @@ def main():
     ap.add_argument("--max-steps", type=int, default=0,
                     help="batched workload: imaginary-time window cap (default: the instances' 5000)")
     ap.add_argument("--rows-per-task", type=int, default=0, help="batched workload: window row-task size")
-    ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the automatic plan")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the automatic window plan (no swr_autotune)")
     args = ap.parse_args()
     name = args.workload
     inst = workload(name)
@@ -447,6 +447,10 @@ def main():
         """W untimed + K timed steps (assemble + iterate to Res <= TOL), CUDA
         events on the library's stream, L2 flushed before every step."""
         s = S.SWR(inst, precision=prec_of[prec_name], device=str(dev), stream=stream)
+        tune = None
+        if inst.mode == "tise" and not args.no_autotune:
+            s.assemble()
+            tune = s.autotune(steps=24)  # the window plan, chosen once (untimed)
         for _ in range(warmup):
             s.assemble()
             s.iterate(TOL if not args.iterations else 0.0, args.iterations or KMAX)
@@ -486,7 +490,7 @@ def main():
             solves_all = int(n.item())
         d = {k: c1[k] - c0[k] for k in c1}
         return dict(s=s, value=solves_all / (t_max * 1e-3), t_max=t_max, reps=reps, counters=d, clocks=clocks,
-                    plan=s.window_plan())
+                    plan=s.window_plan(), tune=tune)
 
     main_run = timed(args.precision, args.steps, args.warmup, True)
     other = None
@@ -545,6 +549,8 @@ def main():
             t0 = time.perf_counter()
             se = S.SWR(inst, precision=prec_of[args.precision], device=str(dev), stream=stream)
             se.assemble()
+            if inst.mode == "tise" and not args.no_autotune:
+                se.autotune(steps=24)
             rep_e, _ = se.iterate(TOL if not args.iterations else 0.0, args.iterations or KMAX)
             energy = se.energy()
             psi = se.psi_nodes()
@@ -583,7 +589,11 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": main_run["clocks"],
+        "window_plan": {k: main_run["plan"][k] for k in ("variant", "rows_per_task", "tasks", "ctas", "graph")},
     }
+    if main_run["tune"] is not None:
+        out["window_plan"]["autotune_us_per_step"] = {"chosen": 1e6 * main_run["tune"]["seconds_per_step"],
+                                                      "automatic": 1e6 * main_run["tune"]["seconds_default"]}
     if other is not None:
         o_reps = other["reps"]
         out["other_precision"] = {

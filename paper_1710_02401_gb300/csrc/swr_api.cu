@@ -486,11 +486,11 @@ static void plan(swr_ctx* c) {
     for (SubDev& s : c->sub) {
         const long long K = s.K;
         if (c->df32 && c->tdse) {
-            s.Gf = off; off = align32(off + 2LL * K * K);  // four FP32 planes of the complex G0
+            s.Gf = off; off = align32(off + 2LL * K * df32_ld((int)K));  // four FP32 planes of the complex G0 [K][ld]
         } else if (c->df32) {
             s.Gf = off; off = align32(off + K * df32_ld((int)K));  // G_hi, G_lo planes [K][ldg]
             if (c->has_w) {
-                s.Wf = off; off = align32(off + K * K);    // W_hi, W_lo planes
+                s.Wf = off; off = align32(off + K * df32_ld((int)K));  // W_hi, W_lo planes [K][ld]
             }
         }
     }

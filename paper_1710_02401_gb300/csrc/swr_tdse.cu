@@ -177,63 +177,87 @@ __device__ inline void ds_mac(float& ah, float& al, float gh, float gl, float xh
     al += (q + e) + fmaf(gh, xl, gl * xh);
 }
 
-// x = G0 u with G0 stored as four FP32 planes (re_hi, re_lo, im_hi, im_lo):
-// complex double-single matvec, FP64-level accuracy on the FP32 pipes.
+// x = G0 u with G0 stored as four FP32 planes (re_hi, re_lo, im_hi, im_lo),
+// rows of ld = df32_ld(K) columns (zero-padded, 16-byte aligned): complex
+// double-single matvec, FP64-level accuracy on the FP32 pipes.  Each warp
+// takes two rows at a time with 16-byte loads of every plane, so that eight
+// independent 512-byte requests per warp are in flight.
 __global__ void __launch_bounds__(256) k_cmv_df32(SwrDeviceView v, const long long* boff) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
-    const int K = s.K;
+    const int K = s.K, ld = df32_ld(K);
     const int r0 = blockIdx.x * MV_ROWS;
     if (r0 >= K) return;
     extern __shared__ float smf[];
-    float* urh = smf;           // K
-    float* url = smf + K;
-    float* uih = smf + 2 * K;
-    float* uil = smf + 3 * K;
+    float* urh = smf;           // ld each
+    float* url = smf + ld;
+    float* uih = smf + 2 * ld;
+    float* uil = smf + 3 * ld;
     const double* U = v.arena + boff[3 * sid + 1];
-    for (int e = threadIdx.x; e < K; e += blockDim.x) {
-        double a = U[e], b = U[K + e];
-        float ah = (float)a, bh = (float)b;
+    for (int e = threadIdx.x; e < ld; e += blockDim.x) {
+        const double a = e < K ? U[e] : 0.0, b = e < K ? U[K + e] : 0.0;
+        const float ah = (float)a, bh = (float)b;
         urh[e] = ah;
         url[e] = (float)(a - (double)ah);
         uih[e] = bh;
         uil[e] = (float)(b - (double)bh);
     }
     __syncthreads();
-    const long long KK = (long long)K * K;
+    const long long KL = (long long)K * ld;
     const float* Grh = (const float*)(v.arena + s.Gf);
-    const float* Grl = Grh + KK;
-    const float* Gih = Grh + 2 * KK;
-    const float* Gil = Grh + 3 * KK;
+    const float* Grl = Grh + KL;
+    const float* Gih = Grh + 2 * KL;
+    const float* Gil = Grh + 3 * KL;
     double* X = v.arena + boff[3 * sid + 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int r = r0 + warp; r < min(K, r0 + MV_ROWS); r += nw) {
-        const long long ro = (long long)r * K;
+    const int r1 = min(K, r0 + MV_ROWS);
+    for (int rb = r0 + 2 * warp; rb < r1; rb += 2 * nw) {
+        const int nrow = min(2, r1 - rb);
         // re = Gr ur - Gi ui ; im = Gr ui + Gi ur
-        float reh = 0.f, rel = 0.f, imh = 0.f, iml = 0.f;
-        for (int c = lane; c < K; c += 32) {
-            const float grh = Grh[ro + c], grl = Grl[ro + c], gih = Gih[ro + c], gil = Gil[ro + c];
-            ds_mac(reh, rel, grh, grl, urh[c], url[c]);
-            ds_mac(reh, rel, -gih, -gil, uih[c], uil[c]);
-            ds_mac(imh, iml, grh, grl, uih[c], uil[c]);
-            ds_mac(imh, iml, gih, gil, urh[c], url[c]);
+        float reh[2] = {0.f, 0.f}, rel[2] = {0.f, 0.f}, imh[2] = {0.f, 0.f}, iml[2] = {0.f, 0.f};
+        for (int c = lane * 4; c < ld; c += 128) {
+            const float4 xrh = *reinterpret_cast<const float4*>(urh + c), xrl = *reinterpret_cast<const float4*>(url + c);
+            const float4 xih = *reinterpret_cast<const float4*>(uih + c), xil = *reinterpret_cast<const float4*>(uil + c);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                if (i < nrow) {
+                    const long long o = (long long)(rb + i) * ld + c;
+                    const float4 grh = *reinterpret_cast<const float4*>(Grh + o);
+                    const float4 grl = *reinterpret_cast<const float4*>(Grl + o);
+                    const float4 gih = *reinterpret_cast<const float4*>(Gih + o);
+                    const float4 gil = *reinterpret_cast<const float4*>(Gil + o);
+#define CMV_TERM(f)                                                   \
+    ds_mac(reh[i], rel[i], grh.f, grl.f, xrh.f, xrl.f);               \
+    ds_mac(reh[i], rel[i], -gih.f, -gil.f, xih.f, xil.f);             \
+    ds_mac(imh[i], iml[i], grh.f, grl.f, xih.f, xil.f);               \
+    ds_mac(imh[i], iml[i], gih.f, gil.f, xrh.f, xrl.f);
+                    CMV_TERM(x)
+                    CMV_TERM(y)
+                    CMV_TERM(z)
+                    CMV_TERM(w)
+#undef CMV_TERM
+                }
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float sh, eh;
-            float oh = __shfl_xor_sync(0xffffffffu, reh, o), ol = __shfl_xor_sync(0xffffffffu, rel, o);
-            ds_two_sum(reh, oh, sh, eh);
-            reh = sh;
-            rel = rel + ol + eh;
-            oh = __shfl_xor_sync(0xffffffffu, imh, o);
-            ol = __shfl_xor_sync(0xffffffffu, iml, o);
-            ds_two_sum(imh, oh, sh, eh);
-            imh = sh;
-            iml = iml + ol + eh;
-        }
-        if (lane == 0) {
-            X[r] = (double)reh + (double)rel;
-            X[K + r] = (double)imh + (double)iml;
+        for (int i = 0; i < 2; ++i) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                float sh, eh;
+                float oh = __shfl_xor_sync(0xffffffffu, reh[i], o), ol = __shfl_xor_sync(0xffffffffu, rel[i], o);
+                ds_two_sum(reh[i], oh, sh, eh);
+                reh[i] = sh;
+                rel[i] = rel[i] + ol + eh;
+                oh = __shfl_xor_sync(0xffffffffu, imh[i], o);
+                ol = __shfl_xor_sync(0xffffffffu, iml[i], o);
+                ds_two_sum(imh[i], oh, sh, eh);
+                imh[i] = sh;
+                iml[i] = iml[i] + ol + eh;
+            }
+            if (lane == 0 && i < nrow) {
+                X[rb + i] = (double)reh[i] + (double)rel[i];
+                X[K + rb + i] = (double)imh[i] + (double)iml[i];
+            }
         }
     }
 }
@@ -242,16 +266,19 @@ __global__ void __launch_bounds__(256) k_cmv_df32(SwrDeviceView v, const long lo
 __global__ void k_split_c_df32(SwrDeviceView v) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
-    const long long KK = (long long)s.K * s.K;
+    const int K = s.K, ld = df32_ld(K);
+    const long long KL = (long long)K * ld;
     const double* G = v.arena + s.Gm;
     float* P = (float*)(v.arena + s.Gf);
-    for (long long e = threadIdx.x + (long long)blockIdx.x * blockDim.x; e < KK; e += (long long)blockDim.x * gridDim.x) {
-        double a = G[2 * e], b = G[2 * e + 1];
-        float ah = (float)a, bh = (float)b;
+    for (long long e = threadIdx.x + (long long)blockIdx.x * blockDim.x; e < KL; e += (long long)blockDim.x * gridDim.x) {
+        const long long r = e / ld;
+        const int c = (int)(e - r * ld);
+        const double a = c < K ? G[2 * (r * K + c)] : 0.0, b = c < K ? G[2 * (r * K + c) + 1] : 0.0;
+        const float ah = (float)a, bh = (float)b;
         P[e] = ah;
-        P[KK + e] = (float)(a - (double)ah);
-        P[2 * KK + e] = bh;
-        P[3 * KK + e] = (float)(b - (double)bh);
+        P[KL + e] = (float)(a - (double)ah);
+        P[2 * KL + e] = bh;
+        P[3 * KL + e] = (float)(b - (double)bh);
     }
 }
 
@@ -281,7 +308,7 @@ static inline unsigned div_up(long long a, long long b) { return (unsigned)((a +
 // Launches of one real-time window: n_steps steps with `iters` fixed-point
 // iterations each; returns the number of kernel launches.
 cudaError_t launch_split_c_df32(const SwrDeviceView& v, cudaStream_t st, int max_K) {
-    long long kk = (long long)max_K * max_K;
+    long long kk = (long long)max_K * df32_ld(max_K);
     k_split_c_df32<<<dim3((unsigned)((kk + 2047) / 2048), v.n_sub), 256, 0, st>>>(v);
     return cudaGetLastError();
 }
@@ -289,7 +316,7 @@ cudaError_t launch_split_c_df32(const SwrDeviceView& v, cudaStream_t st, int max
 cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const long long* d_boff, const int* d_win_prev,
                                int n_steps, int iters, int max_K, int max_kd, bool df32, long long* launches) {
     const size_t sm_el = (2 * (size_t)max_K + 2 * (size_t)max_kd * max_kd) * sizeof(double);
-    const size_t sm_mv = 2 * (size_t)max_K * sizeof(double);
+    const size_t sm_mv = 2 * (size_t)df32_ld(max_K) * sizeof(double);
     static bool attr_done = false;
     if (!attr_done) {
         cudaFuncSetAttribute(k_cn_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);

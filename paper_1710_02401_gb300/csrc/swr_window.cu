@@ -702,7 +702,9 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
     float2* vf = (float2*)(sm + kmax);
     double* tmp = sm + 2 * kmax;
     double* Psm = tmp + A.rows_max + 2 * kdmax;
-    float* Gsm = (float*)(Psm + (long long)A.tasks_per_cta * 2 * kdmax * kdmax);
+    // resident G_hi rows start on 16 bytes (16-byte vector loads)
+    // (everything before it is an even number of doubles except tmp's rows_max)
+    float* Gsm = (float*)(Psm + (long long)A.tasks_per_cta * 2 * kdmax * kdmax + (A.rows_max & 1));
     const bool gres = A.g_resident != 0;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = WIN_THREADS / 32;
     unsigned target = 0, gen = 0;
@@ -812,10 +814,13 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
                     vs[c] = val;
                     float h = (float)val;
                     vf[c] = make_float2(h, (float)(val - (double)h));
+                } else if (c < df32_ld(K)) {
+                    vf[c] = make_float2(0.f, 0.f);  // padding columns of the FP32 planes
                 }
             }
             __syncthreads();
-            // fused double-single rows of y^{n+1} = G v and z^{n+1} = W v
+            // fused double-single rows of y^{n+1} = G v and z^{n+1} = W v, two rows
+            // per warp at a time, 16-byte loads of the four FP32 planes
             double* ynew = v.arena + tc.hist + (long long)(n + 1) * K;
             double* yslot = own[j][(n + 1) % 3];
             double* zslot = own[j][3 + (n + 1) % 3];
@@ -823,44 +828,54 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
             const float* Ghg = (const float*)(v.arena + tc.Gf);
             const float* Gl = Ghg + (long long)K * ld;
             const float* Wh = (const float*)(v.arena + tc.Wf);
-            const float* Wl = Wh + (long long)K * K;
-            for (int r = tc.r0 + warp; r < tc.r0 + nr; r += nw) {
-                const float* gh = gres ? Gsm + (long long)(r - tc.r0) * ld : Ghg + (long long)r * ld;
-                const float* gl = Gl + (long long)r * ld;
-                const float* wh = Wh + (long long)r * K;
-                const float* wl = Wl + (long long)r * K;
-                float yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f, eh;
-                for (int c = lane; c < K; c += 32) {
-                    const float2 x = vf[c];
-                    const float g0 = gh[c], g1 = gl[c], w0 = wh[c], w1 = wl[c];
-                    float p = g0 * x.x, e = fmaf(g0, x.x, -p), sh, q;
-                    two_sum(yh, p, sh, q);
-                    yh = sh;
-                    yl += (q + e) + fmaf(g0, x.y, g1 * x.x);
-                    p = w0 * x.x;
-                    e = fmaf(w0, x.x, -p);
-                    two_sum(zh, p, sh, q);
-                    zh = sh;
-                    zl += (q + e) + fmaf(w0, x.y, w1 * x.x);
+            const float* Wl = Wh + (long long)K * ld;
+            for (int rb = tc.r0 + 2 * warp; rb < tc.r0 + nr; rb += 2 * nw) {
+                const int nrow = min(2, tc.r0 + nr - rb);
+                float yh[2] = {0.f, 0.f}, yl[2] = {0.f, 0.f}, zh[2] = {0.f, 0.f}, zl[2] = {0.f, 0.f};
+                for (int c = lane * 4; c < ld; c += 128) {
+                    const float4 xa = *reinterpret_cast<const float4*>(vf + c);
+                    const float4 xb = *reinterpret_cast<const float4*>(vf + c + 2);
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        if (i < nrow) {
+                            const long long o = (long long)(rb + i) * ld + c;
+                            const float* ghp = gres ? Gsm + (long long)(rb + i - tc.r0) * ld + c : Ghg + o;
+                            const float4 g0 = *reinterpret_cast<const float4*>(ghp);
+                            const float4 g1 = *reinterpret_cast<const float4*>(Gl + o);
+                            const float4 w0 = *reinterpret_cast<const float4*>(Wh + o);
+                            const float4 w1 = *reinterpret_cast<const float4*>(Wl + o);
+                            df32_acc(yh[i], yl[i], g0.x, g1.x, xa.x, xa.y);
+                            df32_acc(zh[i], zl[i], w0.x, w1.x, xa.x, xa.y);
+                            df32_acc(yh[i], yl[i], g0.y, g1.y, xa.z, xa.w);
+                            df32_acc(zh[i], zl[i], w0.y, w1.y, xa.z, xa.w);
+                            df32_acc(yh[i], yl[i], g0.z, g1.z, xb.x, xb.y);
+                            df32_acc(zh[i], zl[i], w0.z, w1.z, xb.x, xb.y);
+                            df32_acc(yh[i], yl[i], g0.w, g1.w, xb.z, xb.w);
+                            df32_acc(zh[i], zl[i], w0.w, w1.w, xb.z, xb.w);
+                        }
+                    }
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    float sh;
-                    float oh = __shfl_xor_sync(0xffffffffu, yh, o), ol = __shfl_xor_sync(0xffffffffu, yl, o);
-                    two_sum(yh, oh, sh, eh);
-                    yh = sh;
-                    yl = yl + ol + eh;
-                    oh = __shfl_xor_sync(0xffffffffu, zh, o);
-                    ol = __shfl_xor_sync(0xffffffffu, zl, o);
-                    two_sum(zh, oh, sh, eh);
-                    zh = sh;
-                    zl = zl + ol + eh;
-                }
-                if (lane == 0) {
-                    const double y = (double)yh + (double)yl;
-                    ynew[r] = y;
-                    yslot[r - tc.r0] = y;
-                    zslot[r - tc.r0] = (double)zh + (double)zl;
+                for (int i = 0; i < 2; ++i) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        float sh, eh;
+                        float oh = __shfl_xor_sync(0xffffffffu, yh[i], o), ol = __shfl_xor_sync(0xffffffffu, yl[i], o);
+                        two_sum(yh[i], oh, sh, eh);
+                        yh[i] = sh;
+                        yl[i] = yl[i] + ol + eh;
+                        oh = __shfl_xor_sync(0xffffffffu, zh[i], o);
+                        ol = __shfl_xor_sync(0xffffffffu, zl[i], o);
+                        two_sum(zh[i], oh, sh, eh);
+                        zh[i] = sh;
+                        zl[i] = zl[i] + ol + eh;
+                    }
+                    if (lane == 0 && i < nrow) {
+                        const double y = (double)yh[i] + (double)yl[i];
+                        ynew[rb + i] = y;
+                        yslot[rb + i - tc.r0] = y;
+                        zslot[rb + i - tc.r0] = (double)zh[i] + (double)zl[i];
+                    }
                 }
             }
             __syncthreads();
@@ -927,6 +942,11 @@ __global__ void k_split_df32(SwrDeviceView v) {
         const float h = (float)g;
         Gh[e] = h;
         Gl[e] = (float)(g - (double)h);
+        if (c >= K && s.Wf) {  // padding columns of W (its other columns come from k_make_w)
+            float* Wh = (float*)(v.arena + s.Wf);
+            Wh[e] = 0.f;
+            Wh[n + e] = 0.f;
+        }
     }
 }
 
@@ -941,8 +961,9 @@ __global__ void k_make_w(SwrDeviceView v) {
     const double* P1 = v.arena + s.t1[0] + lay.mat(M_PP);
     const double* P2 = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_PP);
     const double* G = v.arena + s.Gm;
+    const long long ld = df32_ld(K);
     float* Wh = (float*)(v.arena + s.Wf);
-    float* Wl = Wh + (long long)K * K;
+    float* Wl = Wh + (long long)K * ld;
     extern __shared__ double sw[];
     double* Y = sw;            // K
     double* T = sw + K;        // kd * kd (N = 2)
@@ -954,8 +975,8 @@ __global__ void k_make_w(SwrDeviceView v) {
                 double acc = 0;
                 for (int c = 0; c < K; ++c) acc += P1[a * kd + c] * Y[c];
                 float h = (float)acc;
-                Wh[(long long)a * K + j] = h;
-                Wl[(long long)a * K + j] = (float)(acc - (double)h);
+                Wh[(long long)a * ld + j] = h;
+                Wl[(long long)a * ld + j] = (float)(acc - (double)h);
             }
         } else {
             for (int e2 = threadIdx.x; e2 < kd * kd; e2 += blockDim.x) {  // T[a][e] = sum_c P1[a][c] Y[c][e]
@@ -970,8 +991,8 @@ __global__ void k_make_w(SwrDeviceView v) {
                 double acc = 0;
                 for (int e = 0; e < kd; ++e) acc += T[a * kd + e] * P2[b * kd + e];
                 float h = (float)acc;
-                Wh[(long long)m * K + j] = h;
-                Wl[(long long)m * K + j] = (float)(acc - (double)h);
+                Wh[(long long)m * ld + j] = h;
+                Wl[(long long)m * ld + j] = (float)(acc - (double)h);
             }
         }
         __syncthreads();
@@ -981,8 +1002,8 @@ __global__ void k_make_w(SwrDeviceView v) {
 // ------------------------------------------------------------- host side
 
 size_t window_smem(int kmax, int kdmax, int rows_max, int tasks_in_smem, long long g_resident_floats) {
-    return (2 * (size_t)df32_ld(kmax) + (size_t)rows_max + 2 * (size_t)kdmax + (size_t)tasks_in_smem * 2 * kdmax * kdmax) *
-               sizeof(double) +
+    return (2 * (size_t)df32_ld(kmax) + (size_t)rows_max + 2 * (size_t)kdmax + (size_t)tasks_in_smem * 2 * kdmax * kdmax +
+            1) * sizeof(double) +
            (size_t)g_resident_floats * sizeof(float);
 }
 
