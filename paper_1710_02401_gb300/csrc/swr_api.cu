@@ -31,7 +31,7 @@ cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, 
 extern const int kAssembleLaunchesFixed, kStepLaunches;
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
-                        int res_blocks, double* d_res, int max_cap_hint);
+                        int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax);
 cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
                           int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
                           double* psi_out, const long long* psi_off, int max_K, int max_kd, int max_q);
@@ -844,7 +844,7 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
     }
     if (e == cudaSuccess)
         e = launch_post(view(c), st, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
-                        c->d_res_part, RES_BLOCKS, c->d_res, c->cap);
+                        c->d_res_part, RES_BLOCKS, c->d_res, c->cap, c->max_K, c->max_kd, c->max_q);
     if (e == cudaSuccess)
         e = launch_energy(view(c), st, c->d_win, c->d_snorm, c->cap, c->d_epart, c->d_energy, c->d_norm2,
                           c->d_dipole, c->d_psi, c->d_psi_off, c->max_K, c->max_kd, c->max_q);

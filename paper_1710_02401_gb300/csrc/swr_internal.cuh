@@ -128,6 +128,20 @@ __device__ inline bool grid_sync_bounded(GridBarrier* bar, unsigned int nblocks,
 }
 
 // Warp reduction.
+// Double-single arithmetic (FP32 pairs carrying FP64-level accuracy on the
+// FP32 pipes): split of a double, and (h, l) += a b with TwoProduct of the
+// leading terms, TwoSum into (h, l) and the cross terms into l.
+__device__ inline float2 ds_split(double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+__device__ inline void ds_fma(float& h, float& l, float2 a, float2 b) {
+    const float p = a.x * b.x, e = fmaf(a.x, b.x, -p);
+    const float sm = h + p, bb = sm - h, err = (h - (sm - bb)) + (p - bb);
+    h = sm;
+    l += (err + e) + fmaf(a.x, b.y, a.y * b.x);
+}
+
 __device__ inline double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

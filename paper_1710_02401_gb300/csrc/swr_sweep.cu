@@ -46,20 +46,41 @@ __device__ inline int n_channels(const InstDev& in) { return in.mode == SWR_MODE
 // Line traces of subdomain j at step n from the un-normalised iterate y^n:
 // N = 2: [d][l][kind][q] with psi (kind 0) and d_{x_d} psi (kind 1) on the line
 // x_d = pos_l, sampled at the nodes of the other coordinate.  N = 1: [l][kind].
-__global__ void k_line_traces(SwrDeviceView v, const int* win, int cap) {
+// The two contractions (line values of one coordinate against Y, then the
+// other coordinate's node values) run in double-single on the FP32 pipes; the
+// subdomain's line and node tables are staged once per CTA as FP32 pairs
+// (from global memory when they do not fit, `staged` = 0).  Shared-memory
+// layouts avoid bank conflicts: Y with an odd column stride (kd + 1), the node
+// tables transposed (node index fastest).
+// Dynamic shared memory (float2): ys[kmax + kdmax] | r[16 kdmax] | Lt[2][8][kdmax] | Bt[2][kdmax][qmax] (staged)
+__global__ void k_line_traces(SwrDeviceView v, const int* win, int cap, int kmax, int kdmax, int qmax, int staged) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
     const InstDev& in = v.inst[s.inst];
     const int W = win[s.inst], nch = n_channels(in);
     const int kd = s.kd, q = s.q, K = s.K;
     T1Layout lay(q, kd);
-    __shared__ double ys[1024];
-    __shared__ double r[16][64];
+    extern __shared__ float2 ls[];
+    float2* ys = ls;
+    float2* r = ys + kmax + kdmax;
+    float2* Lt = r + 16 * kdmax;
+    float2* Bt = Lt + 2 * 8 * kdmax;
+    if (s.N == 2) {
+        for (int e = threadIdx.x; e < 2 * 8 * kd; e += blockDim.x) {  // Lt[d][2 l + kind][a]
+            const int d = e / (8 * kd), rest = e % (8 * kd), lk = rest / kd, a = rest % kd;
+            const double* T = v.arena + s.t1[d];
+            Lt[e] = ds_split(T[((lk & 1) ? lay.Ld() : lay.Lv()) + (lk >> 1) * kd + a]);
+        }
+        if (staged)
+            for (int e = threadIdx.x; e < 2 * q * kd; e += blockDim.x) {  // Bt[d][m][node] = B_d[node][m]
+                const int d = e / (q * kd), rest = e % (q * kd), node = rest / kd, m = rest % kd;
+                Bt[(d * kd + m) * q + node] = ds_split(v.arena[s.t1[d] + lay.B() + rest]);
+            }
+    }
+    __syncthreads();
     for (int item = blockIdx.x; item <= W * nch + nch - 1; item += gridDim.x) {
         const int n = item / nch, ch = item % nch;
         const double* y = v.arena + s.hist + ((long long)n * nch + ch) * K;
-        for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c] = y[c];
-        __syncthreads();
         double* out = v.arena + s.line + ((long long)n * nch + ch) * s.nline;
         if (s.N == 1) {
             const double* T = v.arena + s.t1[0];
@@ -67,33 +88,40 @@ __global__ void k_line_traces(SwrDeviceView v, const int* win, int cap) {
                 int l = e / 2, kind = e % 2;
                 const double* Lr = T + (kind ? lay.Ld() : lay.Lv()) + l * kd;
                 double acc = 0;
-                for (int a = 0; a < kd; ++a) acc += Lr[a] * ys[a];
+                for (int a = 0; a < kd; ++a) acc += Lr[a] * y[a];
                 out[l * 2 + kind] = acc;
             }
-            __syncthreads();
             continue;
         }
+        for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c + c / kd] = ds_split(y[c]);  // (a, b) at a + (kd+1) b
+        __syncthreads();
         for (int e = threadIdx.x; e < 16 * kd; e += blockDim.x) {
-            int combo = e / kd, m = e % kd;
-            int d = combo / 8, l = (combo / 2) % 4, kind = combo % 2;
-            const double* T = v.arena + s.t1[d];
-            const double* Lr = T + (kind ? lay.Ld() : lay.Lv()) + l * kd;
-            double acc = 0;
+            const int combo = e / kd, m = e % kd;
+            const int d = combo / 8, lk = combo % 8;  // lk = 2 l + kind
+            const float2* Lr = Lt + (d * 8 + lk) * kd;
+            float h = 0.f, lo = 0.f;
             if (d == 0) {  // r[b] = sum_a L1[a] Y[a][b]
-                for (int a = 0; a < kd; ++a) acc += Lr[a] * ys[a + kd * m];
+                for (int a = 0; a < kd; ++a) ds_fma(h, lo, Lr[a], ys[a + (kd + 1) * m]);
             } else {       // r[a] = sum_b Y[a][b] L2[b]
-                for (int b = 0; b < kd; ++b) acc += ys[m + kd * b] * Lr[b];
+                for (int b = 0; b < kd; ++b) ds_fma(h, lo, Lr[b], ys[m + (kd + 1) * b]);
             }
-            r[combo][m] = acc;
+            const float hs = h + lo;  // renormalised pair
+            r[e] = make_float2(hs, lo - (hs - h));
         }
         __syncthreads();
         for (int e = threadIdx.x; e < 16 * q; e += blockDim.x) {
-            int combo = e / q, node = e % q;
-            int d = combo / 8;
-            const double* Bo = v.arena + s.t1[1 - d] + lay.B() + (long long)node * kd;
-            double acc = 0;
-            for (int m = 0; m < kd; ++m) acc += Bo[m] * r[combo][m];
-            out[combo * q + node] = acc;
+            const int combo = e / q, node = e % q;
+            const int d = combo / 8;
+            const float2* rc = r + combo * kd;
+            float h = 0.f, lo = 0.f;
+            if (staged) {
+                const float2* Bo = Bt + (1 - d) * kd * q + node;
+                for (int m = 0; m < kd; ++m) ds_fma(h, lo, Bo[m * q], rc[m]);
+            } else {
+                const double* Bo = v.arena + s.t1[1 - d] + lay.B() + (long long)node * kd;
+                for (int m = 0; m < kd; ++m) ds_fma(h, lo, ds_split(Bo[m]), rc[m]);
+            }
+            out[combo * q + node] = (double)h + (double)lo;
         }
         __syncthreads();
     }
@@ -113,7 +141,11 @@ __device__ inline void gamma_slot(const SubDev& s, int node, int& slot, int& nt)
 
 // Averaged Robin data g_i and own traces u_i at the interface nodes of every
 // subdomain for steps 0..W, and the Robin source b'_i of the next iteration.
-__global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, int cap, int parity) {
+// The tangential sums of b' run over the weighted node tables
+// WB_d[t][m] = w_t B_d[t][m], staged once per CTA in shared memory when they
+// fit (`staged`), each sum split into GATHER_SPLIT chunks added in a fixed order.
+#define GATHER_SPLIT 4
+__global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, int cap, int parity, int staged) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
     const InstDev& in = v.inst[s.inst];
@@ -122,6 +154,16 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
     T1Layout lay(q, kd);
     __shared__ double gs[2][4 * 384];
     __shared__ double hsum[4][64];
+    __shared__ double hpart[GATHER_SPLIT][4][64];
+    extern __shared__ double wbs[];  // [2][q][kd] (staged)
+    if (staged && s.N == 2) {
+        for (int e = threadIdx.x; e < 2 * q * kd; e += blockDim.x) {
+            const int d = e / (q * kd), rest = e % (q * kd), t = rest / kd;
+            const double* To = v.arena + s.t1[d];
+            wbs[e] = To[lay.w() + t] * To[lay.B() + rest];
+        }
+        __syncthreads();
+    }
     for (int n = blockIdx.x; n <= W; n += gridDim.x) {
         const double sn = in.normalize ? snorm[(long long)s.inst * (cap + 1) + n] : 1.0;
         for (int node = threadIdx.x; node < s.ngam; node += blockDim.x) {
@@ -202,15 +244,28 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
                     bdst[a] = acc;
                 }
             } else {
-                for (int e = threadIdx.x; e < 4 * kd; e += blockDim.x) {
-                    int sl = e / kd, m = e % kd;
+                const int chunk = (q + GATHER_SPLIT - 1) / GATHER_SPLIT;
+                for (int e = threadIdx.x; e < GATHER_SPLIT * 4 * kd; e += blockDim.x) {
+                    const int part = e / (4 * kd), rest = e % (4 * kd), sl = rest / kd, m = rest % kd;
                     double acc = 0;
                     if (s.gam_off[sl] >= 0) {
-                        int d = sl / 2;
-                        const double* To = v.arena + s.t1[1 - d];
-                        for (int t = 0; t < q; ++t)
-                            acc += To[lay.w() + t] * gs[ch][s.gam_off[sl] + t] * To[lay.B() + t * kd + m];
+                        const int d = sl / 2, t0 = part * chunk, t1 = min(q, t0 + chunk);
+                        const double* gv = gs[ch] + s.gam_off[sl];
+                        if (staged) {
+                            const double* wb = wbs + (long long)(1 - d) * q * kd;
+                            for (int t = t0; t < t1; ++t) acc += gv[t] * wb[t * kd + m];
+                        } else {
+                            const double* To = v.arena + s.t1[1 - d];
+                            for (int t = t0; t < t1; ++t) acc += gv[t] * (To[lay.w() + t] * To[lay.B() + t * kd + m]);
+                        }
                     }
+                    hpart[part][sl][m] = acc;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < 4 * kd; e += blockDim.x) {
+                    const int sl = e / kd, m = e % kd;
+                    double acc = 0;
+                    for (int part = 0; part < GATHER_SPLIT; ++part) acc += hpart[part][sl][m];
                     hsum[sl][m] = acc;
                 }
                 __syncthreads();
@@ -383,10 +438,22 @@ extern const int kStepLaunches = 8;
 
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
-                        int res_blocks, double* d_res, int max_cap_hint) {
+                        int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax) {
     int nb = 64;
-    k_line_traces<<<dim3(nb, v.n_sub), 256, 0, st>>>(v, d_win, cap);
-    k_gather<<<dim3(nb, v.n_sub), 256, 0, st>>>(v, d_win, d_snorm, cap, parity);
+    {
+        const size_t base = ((size_t)lt_kmax + (size_t)lt_kdmax + 32 * (size_t)lt_kdmax) * sizeof(float2);
+        const size_t tab = 2 * (size_t)lt_qmax * lt_kdmax * sizeof(float2);
+        const int staged = base + tab <= 96 * 1024;
+        const size_t sm = base + (staged ? tab : 0);
+        if (sm > 48 * 1024) cudaFuncSetAttribute(k_line_traces, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_line_traces<<<dim3(nb, v.n_sub), 256, sm, st>>>(v, d_win, cap, lt_kmax, lt_kdmax, lt_qmax, staged);
+    }
+    {
+        const size_t tab = 2 * (size_t)lt_qmax * lt_kdmax * sizeof(double);
+        const int staged = tab <= 96 * 1024;
+        if (staged) cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab);
+        k_gather<<<dim3(nb, v.n_sub), 256, staged ? tab : 0, st>>>(v, d_win, d_snorm, cap, parity, staged);
+    }
     k_residual<<<dim3(res_blocks, v.n_sub), 256, 0, st>>>(v, d_win, d_win_prev, parity, first_iter, d_res_part);
     k_residual_reduce<<<v.n_inst, 256, 0, st>>>(v, d_res_part, res_blocks, d_res);
     return cudaGetLastError();
