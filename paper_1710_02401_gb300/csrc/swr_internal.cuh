@@ -92,9 +92,13 @@ __host__ __device__ inline double line_pos(double lo, double hi, double eps, int
 
 // Bounded sense-reversal grid barrier for a cooperative launch.  Spins at most
 // `limit` polls; on timeout it raises SWR_ERR_TIMEOUT in *err and returns false.
+// Arrival counter and release word on separate 128-byte lines: the CTAs that
+// poll the release word do not contend with the arrivals' atomics.
 struct GridBarrier {
     unsigned int count;
+    unsigned int pad0[31];
     unsigned int gen;
+    unsigned int pad1[31];
 };
 
 __device__ inline bool grid_sync_bounded(GridBarrier* bar, unsigned int nblocks, int* err,
