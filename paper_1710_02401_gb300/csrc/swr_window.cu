@@ -137,74 +137,69 @@ __device__ bool reduce_barrier(unsigned* count, unsigned* release, unsigned targ
     return s_ok != 0 && *(volatile int*)err == 0;
 }
 
-// The same, reducing two partial arrays (part_a -> sums_a, part_b -> sums_b).
-__device__ bool reduce_barrier2(unsigned* count, unsigned* release, unsigned target, unsigned gen,
-                                const double* part_a, const double* part_b, const int* inst_task0, int n_inst,
-                                double* sums_a, double* sums_b, int* err, long long limit, double* red,
-                                const int* nact, int* go_out) {
-    __shared__ int s_last, s_ok, s_go;
+// Grid barrier without reduction: the CTA whose arrival completes the count
+// publishes 2*gen + go at once (go = 0 when `nact` shows no instance still
+// stepping); every CTA then sums the partials it needs itself (block_sums2).
+// Bounded waits; returns false on error.
+__device__ bool release_barrier(unsigned* count, unsigned* release, unsigned target, unsigned gen, int* err,
+                                long long limit, const int* nact, int* go_out) {
+    __shared__ int s_ok, s_go;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned old = atomicAdd(count, 1u);
-        s_last = (old == target - 1);
         s_ok = 1;
-    }
-    __syncthreads();
-    if (s_last) {
         __threadfence();
-        if (n_inst < 8) {
-            for (int i = 0; i < n_inst; ++i) {
-                double xa = 0, xb = 0;
-                for (int u = inst_task0[i] + threadIdx.x; u < inst_task0[i + 1]; u += WIN_THREADS) {
-                    xa += __ldcg(part_a + u);
-                    xb += __ldcg(part_b + u);
-                }
-                xa = wblock_sum(xa, red);
-                xb = wblock_sum(xb, red);
-                if (threadIdx.x == 0) {
-                    sums_a[i] = xa;
-                    sums_b[i] = xb;
-                }
-            }
-        } else {
-            const int lane = threadIdx.x & 31;
-            for (int i = threadIdx.x >> 5; i < n_inst; i += WIN_THREADS / 32) {
-                double xa = 0, xb = 0;
-#pragma unroll 4
-                for (int u = inst_task0[i] + lane; u < inst_task0[i + 1]; u += 32) {
-                    xa += __ldcg(part_a + u);
-                    xb += __ldcg(part_b + u);
-                }
-                xa = warp_sum(xa);
-                xb = warp_sum(xb);
-                if (lane == 0) {
-                    sums_a[i] = xa;
-                    sums_b[i] = xb;
-                }
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int go = nact ? (__ldcg(nact) > 0) : 1;
+        const unsigned old = atomicAdd(count, 1u);
+        if (old == target - 1) {
+            const int go = nact ? (__ldcg(nact) > 0) : 1;
             s_go = go;
             __threadfence();
             st_release_u32(release, 2u * gen + (unsigned)go);
+        } else {
+            long long it = 0;
+            unsigned w = 0;
+            while ((w = ld_acquire_u32(release)) < 2u * gen) {
+                if (++it > limit) { atomicOr(err, SWR_ERR_TIMEOUT); s_ok = 0; break; }
+                if ((it & 255) == 0 && *(volatile int*)err) { s_ok = 0; break; }
+                __nanosleep(20);
+            }
+            s_go = (int)(w & 1u);
         }
-    } else if (threadIdx.x == 0) {
-        long long it = 0;
-        unsigned w = 0;
-        while ((w = ld_acquire_u32(release)) < 2u * gen) {
-            if (++it > limit) { atomicOr(err, SWR_ERR_TIMEOUT); s_ok = 0; break; }
-            if ((it & 255) == 0 && *(volatile int*)err) { s_ok = 0; break; }
-            __nanosleep(20);
-        }
-        s_go = (int)(w & 1u);
         __threadfence();
     }
     __syncthreads();
     *go_out = s_go;
     return s_ok != 0 && *(volatile int*)err == 0;
+}
+
+// sa = sum of part_a[t0, t1), sb = sum of part_b[t0, t1): strided per thread,
+// warp tree, warps in order -- the same order in every CTA, so every CTA gets
+// the same bits.
+__device__ void block_sums2(const double* part_a, const double* part_b, int t0, int t1, double* red, double* sa,
+                            double* sb) {
+    double xa = 0, xb = 0;
+    for (int u = t0 + threadIdx.x; u < t1; u += WIN_THREADS) {
+        xa += __ldcg(part_a + u);
+        xb += __ldcg(part_b + u);
+    }
+    xa = warp_sum(xa);
+    xb = warp_sum(xb);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        red[w] = xa;
+        red[16 + w] = xb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0, tb = 0;
+        for (int i = 0; i < WIN_THREADS / 32; ++i) {
+            ta += red[i];
+            tb += red[16 + i];
+        }
+        *sa = ta;
+        *sb = tb;
+    }
+    __syncthreads();
 }
 
 __device__ inline void two_sum(float a, float b, float& s, float& e) {
@@ -692,6 +687,10 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
     __shared__ int alive[WIN_TPC];
     __shared__ double s_sc[2];
     __shared__ int s_stop;
+    __shared__ double s2_sm[WIN_TPC], d2_sm[WIN_TPC];  // s^2 and D sums of each task's instance
+    // partials double-buffered by barrier parity: a CTA that has passed a
+    // barrier writes the next buffer while others still sum this one
+    long long pofs = 0;
     int go = 1;
     const SwrDeviceView& v = A.v;
     const int t_begin = A.cta_task0[blockIdx.x];
@@ -746,15 +745,31 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
         for (int r = tid; r < nr; r += WIN_THREADS) acc += own[j][0][r] * own[j][3][r];
         acc = wblock_sum(acc, red);
         if (tid == 0) {
-            A.part_s[t] = acc;
-            A.part_d[t] = 0.0;
+            A.part_s[pofs + t] = acc;
+            A.part_d[pofs + t] = 0.0;
         }
     }
+    // after each barrier: the sums of the CTA's instances, reduced locally
+    auto task_sums = [&]() {
+        for (int j = 0; j < ntk; ++j) {
+            const int i = tcs[j].inst;
+            if (j > 0 && tcs[j - 1].inst == i) {
+                if (tid == 0) {
+                    s2_sm[j] = s2_sm[j - 1];
+                    d2_sm[j] = d2_sm[j - 1];
+                }
+                continue;
+            }
+            block_sums2(A.part_s + pofs, A.part_d + pofs, A.inst_task0[i], A.inst_task0[i + 1], red, &s2_sm[j],
+                        &d2_sm[j]);
+        }
+        __syncthreads();
+        pofs = pofs ? 0 : A.n_tasks;
+    };
     target += gridDim.x;
     ++gen;
-    if (!reduce_barrier2(&A.bar->count, &A.bar->gen, target, gen, A.part_s, A.part_d, A.inst_task0, v.n_inst,
-                         A.sums_s, A.sums_d, v.err, A.spin_limit, red, nullptr, &go))
-        return;
+    if (!release_barrier(&A.bar->count, &A.bar->gen, target, gen, v.err, A.spin_limit, nullptr, &go)) return;
+    task_sums();
 
     for (int n = 0;; ++n) {
         for (int j = 0; j < ntk; ++j) {
@@ -764,8 +779,8 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
             const int K = tc.K, nr = tc.nr;
             const int t = A.cta_list[t_begin + j];
             // one round trip: s_n^2, D_{n-1}, y^n, b'^{n+1}
-            const double s2 = tc.normalize ? __ldcg(A.sums_s + tc.inst) : 1.0;
-            const double d2 = (n >= 2 && tc.ngf_stop) ? __ldcg(A.sums_d + tc.inst) : 1.0e300;
+            const double s2 = tc.normalize ? s2_sm[j] : 1.0;
+            const double d2 = (n >= 2 && tc.ngf_stop) ? d2_sm[j] : 1.0e300;
             const double* yn = v.arena + tc.hist + (long long)n * K;
             const int wp = A.win_prev[tc.inst];
             const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(n + 1, wp) * K : nullptr;
@@ -903,17 +918,16 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
                     a += red[i];
                     b += red[16 + i];
                 }
-                A.part_s[t] = a;
-                if (dn) A.part_d[t] = b;
+                A.part_s[pofs + t] = a;
+                if (dn) A.part_d[pofs + t] = b;
             }
         }
         __syncthreads();
         target += gridDim.x;
         ++gen;
-        if (!reduce_barrier2(&A.bar->count, &A.bar->gen, target, gen, A.part_s, A.part_d, A.inst_task0, v.n_inst,
-                             A.sums_s, A.sums_d, v.err, A.spin_limit, red, A.n_active, &go))
-            return;
+        if (!release_barrier(&A.bar->count, &A.bar->gen, target, gen, v.err, A.spin_limit, A.n_active, &go)) return;
         if (!go) return;
+        task_sums();
     }
 }
 
