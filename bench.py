@@ -40,7 +40,7 @@ FP32_PEAK_TFLOPS = 67.7
 # source of the kernel and of the device functions it calls is the one that was
 # profiled (sha256 prefix over those functions' text in swr_window.cu)
 KERNEL_FUNCS = {
-    "k_window_fused": ["reduce_barrier", "reduce_barrier2", "two_sum", "make_task_cache", "z_rows_sm", "df32_acc",
+    "k_window_fused": ["release_barrier", "block_sums2", "two_sum", "make_task_cache", "z_rows_sm", "df32_acc",
                        "k_window_fused"],
     "k_window_2ph<false>": ["reduce_barrier", "make_task_cache", "z_rows_sm", "z_rows_staged", "prefetch_l2",
                             "prefetch_rows", "fp64_rows4", "k_window_2ph"],
@@ -49,7 +49,7 @@ KERNEL_FUNCS = {
 }
 KERNEL_FUNCS["k_window_2ph<true>@batched"] = KERNEL_FUNCS["k_window_2ph<true>"]
 PROFILED_TRAFFIC = {
-    "k_window_fused": ("c09e0cca30613924", 329.1e6, "profiles/k_window_fused_tise_2e_16sd.md"),
+    "k_window_fused": ("123b4a784de2ee96", 329.5e6, "profiles/k_window_fused_tise_2e_16sd.md"),
     "k_window_2ph<false>": ("654a871bbf4d80e1", 278.7e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
     "k_window_2ph<true>@batched": ("132abcba8871d5ad", 1.196, "profiles/k_window_2ph_df32_batched_uneven.md"),
 }
