@@ -47,7 +47,10 @@ KERNEL_FUNCS = {
     "k_window_2ph<true>": ["reduce_barrier", "two_sum", "make_task_cache", "z_rows_sm", "z_rows_staged",
                            "prefetch_l2", "prefetch_rows", "df32_acc", "df32_rows4", "k_window_2ph"],
 }
+KERNEL_FUNCS["k_window_split"] = ["reduce_barrier_sd", "two_sum", "make_task_cache", "z_rows_staged", "prefetch_l2",
+                                  "prefetch_rows", "df32_acc", "df32_rows2x2", "k_window_split"]
 KERNEL_FUNCS["k_window_2ph<true>@batched"] = KERNEL_FUNCS["k_window_2ph<true>"]
+KERNEL_FUNCS["k_window_split@batched"] = KERNEL_FUNCS["k_window_split"]
 PROFILED_TRAFFIC = {
     "k_window_fused": ("123b4a784de2ee96", 329.5e6, "profiles/k_window_fused_tise_2e_16sd.md"),
     "k_window_2ph<false>": ("654a871bbf4d80e1", 278.7e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
@@ -291,7 +294,8 @@ def run_batched(args, insts, env):
         for chunk in chunks:
             torch.cuda.synchronize(dev)
             w0 = time.perf_counter()
-            s = S.SWR(chunk, precision=prec, device=str(dev), stream=stream, rows_per_task=args.rows_per_task)
+            s = S.SWR(chunk, precision=prec, device=str(dev), stream=stream, rows_per_task=args.rows_per_task,
+                      window_variant=args.window_variant if prec == S.PREC_MIXED else 0)
             s.assemble()
             tunes.append(s.window_plan() if args.no_autotune else s.autotune(steps=24))
             for w in range(warmup):
@@ -340,6 +344,9 @@ def run_batched(args, insts, env):
     peak, peak_src = hbm_peak()
     gbs = main_run["wbytes"] / (main_run["wms"] * 1e-3) / 1e9 if main_run["wms"] > 0 else 0.0
     kname = "k_window_2ph<true>" if args.precision == "mixed" else "k_window_2ph<false>"
+    n_split = sum(t["variant"] == S.WINDOW_SPLIT for t in main_run["tunes"])
+    if args.precision == "mixed" and 2 * n_split > len(main_run["tunes"]):
+        kname = "k_window_split"
     roof = {"kernel": kname, "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
             "frac": gbs / peak, "peak_source": peak_src,
             "algorithmic": "8 bytes of the step-matrix inverse per element (FP32 hi/lo planes or FP64) per local "
@@ -407,6 +414,9 @@ def main():
     ap.add_argument("--max-steps", type=int, default=0,
                     help="batched workload: imaginary-time window cap (default: the instances' 5000)")
     ap.add_argument("--rows-per-task", type=int, default=0, help="batched workload: window row-task size")
+    ap.add_argument("--window-variant", type=int, default=0,
+                    help="batched workload, mixed precision: window kernel before autotuning (0 automatic, 1 two-phase, "
+                         "3 split)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic window plan (no swr_autotune)")
     args = ap.parse_args()
     name = args.workload

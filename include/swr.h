@@ -85,10 +85,18 @@ typedef enum swr_window_variant {
                                   element in both precisions); any batch size
                                   (task state in global memory when a CTA holds
                                   more tasks than its shared memory)             */
-    SWR_WINDOW_FUSED = 2       /* mixed precision only: y = G v and z = W v with
+    SWR_WINDOW_FUSED = 2,      /* mixed precision only: y = G v and z = W v with
                                   W = (Pp (x) Pp) G precomputed, one grid barrier
                                   per step (16 bytes per element); at most 4 row
                                   tasks of at most 64 rows per CTA               */
+    SWR_WINDOW_SPLIT = 3       /* mixed precision only: u = G y^n and
+                                  w = G (kappa dt b') in one pass over G before
+                                  s_n is known, y^{n+1} = u / s_n + w formed after
+                                  the next barrier: one grid barrier per step,
+                                  8 bytes per element, any batch size (task state
+                                  in global memory); the stop on the NGF
+                                  tolerance is decided one step later and the
+                                  extra step dropped                             */
 } swr_window_variant;
 
 /* One SWR problem: global box [box_lo, box_hi]^n_elec cut into L^n_elec

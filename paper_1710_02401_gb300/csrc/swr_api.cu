@@ -22,6 +22,7 @@ cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, 
                             bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
                             const GemmJob* d_jobs2, double* d_norm_part);
 size_t window_smem(int kmax, int kdmax, int rows_max, int tasks_in_smem, long long g_resident_floats);
+size_t window_smem_split(int kmax, int kdmax, int rows_max);
 int window_tasks_per_cta_max();
 int window_rows_per_task_max();
 cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, int variant, bool df32);
@@ -204,10 +205,12 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
     }
     if (p->precision != SWR_PREC_FP64 && p->precision != SWR_PREC_MIXED)
         return fail(c, SWR_EINVAL, "unknown precision");
-    if (p->window_variant < 0 || p->window_variant > SWR_WINDOW_FUSED)
+    if (p->window_variant < 0 || p->window_variant > SWR_WINDOW_SPLIT)
         return fail(c, SWR_EINVAL, "unknown window variant");
     if (p->window_variant == SWR_WINDOW_FUSED && (p->precision != SWR_PREC_MIXED || mode0 != SWR_MODE_TISE))
         return fail(c, SWR_EINVAL, "the fused window is the mixed-precision imaginary-time kernel");
+    if (p->window_variant == SWR_WINDOW_SPLIT && (p->precision != SWR_PREC_MIXED || mode0 != SWR_MODE_TISE))
+        return fail(c, SWR_EINVAL, "the split window is the mixed-precision imaginary-time kernel");
     if (p->launch_mode != SWR_LAUNCH_GRAPH && p->launch_mode != SWR_LAUNCH_DIRECT)
         return fail(c, SWR_EINVAL, "unknown launch mode");
     if (p->rows_per_task != 0 && (p->rows_per_task < 8 || p->rows_per_task > 256))
@@ -315,13 +318,15 @@ static bool plan_window(swr_ctx* c, int variant_req, int rows_req, bool have_dev
         int variant = variant_req;
         if (variant == 0) variant = (c->df32 && c->has_w && fits) ? WIN_FUSED : WIN_TWO_PHASE;
         if (variant == WIN_FUSED && (!c->df32 || !c->has_w || !fits)) return false;
+        if (variant == WIN_SPLIT && !c->df32) return false;
         c->variant = variant;
-        c->many = fits ? 0 : 1;
+        c->many = (fits && variant != WIN_SPLIT) ? 0 : 1;  // the split kernel keeps task state in global memory
         const long long gres_floats = (long long)c->max_rows * df32_ld(c->max_K);
         c->g_resident = variant == WIN_FUSED && c->tasks_per_cta == 1 &&
                         window_smem(c->max_K, c->max_kd, c->max_rows, 1, gres_floats) <= 110 * 1024;
-        c->win_smem = window_smem(c->max_K, c->max_kd, c->max_rows, c->many ? 1 : c->tasks_per_cta,
-                                  c->g_resident ? gres_floats : 0);
+        c->win_smem = variant == WIN_SPLIT ? window_smem_split(c->max_K, c->max_kd, c->max_rows)
+                                           : window_smem(c->max_K, c->max_kd, c->max_rows, c->many ? 1 : c->tasks_per_cta,
+                                                         c->g_resident ? gres_floats : 0);
         c->bps = per_sm;
         if (!have_dev) return true;
         int bps = 0;
@@ -477,7 +482,7 @@ static void plan(swr_ctx* c) {
     // Mixed precision: FP32 planes of the step matrix, and W = (Pp (x) Pp) G when
     // the fused single-barrier window can run (task state in shared memory).
     c->has_w = false;
-    if (c->df32 && !c->tdse && p.window_variant != WIN_TWO_PHASE) {
+    if (c->df32 && !c->tdse && (p.window_variant == 0 || p.window_variant == WIN_FUSED)) {
         plan_tasks(c, p.rows_per_task, 2 * (c->nsm > 0 ? c->nsm : 152));
         c->has_w = p.window_variant == WIN_FUSED ||
                    (c->tasks_per_cta <= window_tasks_per_cta_max() && c->max_rows <= window_rows_per_task_max() &&
@@ -1008,9 +1013,10 @@ extern "C" swr_status swr_autotune(swr_ctx* c, int steps, swr_tune_report* out) 
     std::vector<Cand> cands;
     cands.push_back({c->prob.window_variant, c->prob.rows_per_task});  // the plan before tuning
     const int rows_list[] = {0, 16, 32, 64, 128, 256};
-    const int variants[] = {WIN_TWO_PHASE, WIN_FUSED};
+    const int variants[] = {WIN_TWO_PHASE, WIN_FUSED, WIN_SPLIT};
     for (int v : variants) {
         if (v == WIN_FUSED && !(c->df32 && c->has_w)) continue;
+        if (v == WIN_SPLIT && !c->df32) continue;
         for (int r : rows_list) cands.push_back({v, r});
     }
     std::vector<std::vector<int>> seen;  // (variant, tasks, grid, rows target) of the plans timed

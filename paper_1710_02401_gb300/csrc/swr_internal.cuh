@@ -190,7 +190,7 @@ struct TaskCache {
 };
 
 // Window kernel variants.
-enum WindowVariant { WIN_TWO_PHASE = 1, WIN_FUSED = 2 };
+enum WindowVariant { WIN_TWO_PHASE = 1, WIN_FUSED = 2, WIN_SPLIT = 3 };
 
 // Event record that becomes an event-record node of the graph under stream
 // capture (external record) and is a plain record otherwise.

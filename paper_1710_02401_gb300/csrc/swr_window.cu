@@ -931,6 +931,304 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
     }
 }
 
+// ------------------------------------------------------- single-barrier window
+//
+// Mixed precision, batches of any size, ONE reduce-barrier per step, G read
+// once per step (8 bytes per element).  With y^{n+1} = G (y^n / s_n + kappa dt
+// b'^{n+1}) = u^{n+1} / s_n + w^{n+1}, u^{n+1} = G y^n, w^{n+1} = G (kappa dt
+// b'^{n+1}), both products need no s_n: phase X(m) forms the full y^m =
+// u^m / s_{m-1} + w^m of each of its tasks' subdomains (s_{m-1} reduced at the
+// last barrier), writes its rows, computes z^m = (Pp (x) Pp) y^m and the
+// partials of s_m^2 and D_{m-1} = ||c^{m-1} - c^{m-2}||_chi^2, and the rows of
+// u^{m+1} and w^{m+1} in one double-single pass over G (two dot products per
+// row).  The stop of the plain algorithm at step n is decided at X(n+2) (D_n
+// is reduced at the barrier after X(n+1)), the steps computed beyond it are
+// dropped.  u and w live, double-buffered by step parity, in the subdomain's
+// assembly scratch.  Per-task state in global memory.
+// Dynamic shared memory (doubles): vs[kmax4] | vf[kmax4] (float2) | bf[kmax4]
+// (float2) | tmp[rows_max + 2 kdmax] | Ps[2 kdmax^2]
+
+// Two double-single dot products per row over one pass of G (TWO) or one.
+template <bool TWO>
+__device__ inline void df32_rows2x2(const float* Gh, const float* Gl, int ld, const float2* vf, const float2* bf, int rb,
+                                    int nrow, int lane, double* y, double* w) {
+    float yh[2] = {0.f, 0.f}, yl[2] = {0.f, 0.f}, wh[2] = {0.f, 0.f}, wl[2] = {0.f, 0.f};
+    for (int c = lane * 4; c < ld; c += 128) {
+        const float4 xa = *reinterpret_cast<const float4*>(vf + c), xb = *reinterpret_cast<const float4*>(vf + c + 2);
+        float4 ba = make_float4(0.f, 0.f, 0.f, 0.f), bb = ba;
+        if (TWO) {
+            ba = *reinterpret_cast<const float4*>(bf + c);
+            bb = *reinterpret_cast<const float4*>(bf + c + 2);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            if (i < nrow) {
+                const long long o = (long long)(rb + i) * ld + c;
+                const float4 g0 = *reinterpret_cast<const float4*>(Gh + o);
+                const float4 g1 = *reinterpret_cast<const float4*>(Gl + o);
+                df32_acc(yh[i], yl[i], g0.x, g1.x, xa.x, xa.y);
+                df32_acc(yh[i], yl[i], g0.y, g1.y, xa.z, xa.w);
+                df32_acc(yh[i], yl[i], g0.z, g1.z, xb.x, xb.y);
+                df32_acc(yh[i], yl[i], g0.w, g1.w, xb.z, xb.w);
+                if (TWO) {
+                    df32_acc(wh[i], wl[i], g0.x, g1.x, ba.x, ba.y);
+                    df32_acc(wh[i], wl[i], g0.y, g1.y, ba.z, ba.w);
+                    df32_acc(wh[i], wl[i], g0.z, g1.z, bb.x, bb.y);
+                    df32_acc(wh[i], wl[i], g0.w, g1.w, bb.z, bb.w);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float sh, eh;
+            float oh = __shfl_xor_sync(0xffffffffu, yh[i], o), ol = __shfl_xor_sync(0xffffffffu, yl[i], o);
+            two_sum(yh[i], oh, sh, eh);
+            yh[i] = sh;
+            yl[i] = yl[i] + ol + eh;
+            if (TWO) {
+                oh = __shfl_xor_sync(0xffffffffu, wh[i], o);
+                ol = __shfl_xor_sync(0xffffffffu, wl[i], o);
+                two_sum(wh[i], oh, sh, eh);
+                wh[i] = sh;
+                wl[i] = wl[i] + ol + eh;
+            }
+        }
+        y[i] = (double)yh[i] + (double)yl[i];
+        w[i] = TWO ? (double)wh[i] + (double)wl[i] : 0.0;
+    }
+}
+
+// Last-arriver reduction of two partial arrays per instance (warp per instance
+// from 8 instances on), s = sqrt(sum_a) and 1/s per instance into scal_out,
+// then the release (go = 0 when `nact` shows no instance still stepping).
+__device__ bool reduce_barrier_sd(unsigned* count, unsigned* release, unsigned target, unsigned gen,
+                                  const double* part_a, const double* part_b, const int* inst_task0, int n_inst,
+                                  double* sums_a, double* sums_b, const InstDev* inst, double* scal_out, int* err,
+                                  long long limit, double* red, const int* nact, int* go_out) {
+    __shared__ int s_last, s_ok, s_go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned old = atomicAdd(count, 1u);
+        s_last = (old == target - 1);
+        s_ok = 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        const int lane = threadIdx.x & 31;
+        if (n_inst < 8) {
+            for (int i = 0; i < n_inst; ++i) {
+                double xa = 0, xb = 0;
+                for (int u = inst_task0[i] + threadIdx.x; u < inst_task0[i + 1]; u += WIN_THREADS) {
+                    xa += __ldcg(part_a + u);
+                    xb += __ldcg(part_b + u);
+                }
+                xa = wblock_sum(xa, red);
+                xb = wblock_sum(xb, red);
+                if (threadIdx.x == 0) {
+                    sums_a[i] = xa;
+                    sums_b[i] = xb;
+                }
+            }
+        } else {
+            for (int i = threadIdx.x >> 5; i < n_inst; i += WIN_THREADS / 32) {
+                double xa = 0, xb = 0;
+#pragma unroll 4
+                for (int u = inst_task0[i] + lane; u < inst_task0[i + 1]; u += 32) {
+                    xa += __ldcg(part_a + u);
+                    xb += __ldcg(part_b + u);
+                }
+                xa = warp_sum(xa);
+                xb = warp_sum(xb);
+                if (lane == 0) {
+                    sums_a[i] = xa;
+                    sums_b[i] = xb;
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n_inst; i += WIN_THREADS) {
+            const double sn = inst[i].normalize ? sqrt(sums_a[i]) : 1.0;
+            scal_out[i] = sn;
+            scal_out[n_inst + i] = 1.0 / sn;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int go = nact ? (__ldcg(nact) > 0) : 1;
+            s_go = go;
+            __threadfence();
+            st_release_u32(release, 2u * gen + (unsigned)go);
+        }
+    } else if (threadIdx.x == 0) {
+        long long it = 0;
+        unsigned w = 0;
+        while ((w = ld_acquire_u32(release)) < 2u * gen) {
+            if (++it > limit) { atomicOr(err, SWR_ERR_TIMEOUT); s_ok = 0; break; }
+            if ((it & 255) == 0 && *(volatile int*)err) { s_ok = 0; break; }
+            __nanosleep(20);
+        }
+        s_go = (int)(w & 1u);
+        __threadfence();
+    }
+    __syncthreads();
+    *go_out = s_go;
+    return s_ok != 0 && *(volatile int*)err == 0;
+}
+
+__global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    int go = 1;
+    const SwrDeviceView& v = A.v;
+    const int t_begin = A.cta_task0[blockIdx.x];
+    const int ntk = A.cta_task0[blockIdx.x + 1] - t_begin;
+    TaskCache* tcs = A.g_tc + t_begin;
+    int* alive = A.g_alive + t_begin;
+    const int cap = A.cap, ni = v.n_inst;
+    const int kmax = df32_ld(A.kmax), kdmax = A.kdmax;
+    double* vs = sm;
+    float2* vf = (float2*)(sm + kmax);
+    float2* bf = (float2*)(sm + 2 * kmax);
+    double* tmp = sm + 3 * kmax;
+    double* Ps = tmp + A.rows_max + 2 * kdmax;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = WIN_THREADS / 32;
+    unsigned target = 0, gen = 0;
+    auto own = [&](const TaskCache& tc, int slot) -> double* { return A.g_own + tc.own + (long long)slot * tc.nr; };
+
+    for (int j = 0; j < ntk; ++j) {
+        if (tid == 0) {
+            tcs[j] = make_task_cache(A, A.cta_list[t_begin + j]);
+            alive[j] = 1;
+        }
+    }
+    __syncthreads();
+
+    for (int m = 0;; ++m) {
+        const double* sc1 = A.scal_inst + ((m - 1) & 1) * 2 * ni;  // s_{m-1}, 1/s_{m-1}
+        const double* sc2 = A.scal_inst + ((m - 2) & 1) * 2 * ni;  // s_{m-2}, 1/s_{m-2}
+        for (int j = 0; j < ntk; ++j) {
+            __syncthreads();
+            if (!alive[j]) continue;
+            const TaskCache tc = tcs[j];
+            const int K = tc.K, nr = tc.nr, ld = df32_ld(K);
+            const int t = A.cta_list[t_begin + j];
+            const double s1 = m >= 1 ? __ldcg(sc1 + tc.inst) : 1.0;
+            const double is1 = m >= 1 ? __ldcg(sc1 + ni + tc.inst) : 1.0;
+            const double is2 = m >= 2 ? __ldcg(sc2 + ni + tc.inst) : 1.0;
+            // the plain algorithm's stop at n = m-2 (D_{m-2}), then at n = m-1
+            int stop = 0, win = 0, bad = 0;
+            if (m >= 3 && tc.ngf_stop && sqrt(fmax(__ldcg(A.sums_d + tc.inst), 0.0)) <= tc.ngf_tol) {
+                stop = 1;
+                win = m - 2;
+            } else if (m >= 1 && (m - 1 >= tc.maxs || !isfinite(s1) || s1 <= 0.0)) {
+                stop = 1;
+                win = m - 1;
+                bad = !isfinite(s1) || s1 <= 0.0;
+            }
+            if (tid == 0 && tc.first && m >= 1) A.snorm[(long long)tc.inst * (cap + 1) + m - 1] = s1;
+            if (stop) {
+                if (tid == 0) {
+                    alive[j] = 0;
+                    if (tc.first) {
+                        A.win[tc.inst] = win;
+                        if (bad) atomicOr(v.err, SWR_ERR_NUMERIC);
+                        __threadfence();
+                        atomicSub(A.n_active, 1);
+                    }
+                }
+                continue;
+            }
+            // full y^m = u^m / s_{m-1} + w^m (y^0 = c0), and kappa dt b'^{m+1}; the
+            // warp's first rows of G travel to L2 meanwhile
+            const bool mv = m < tc.maxs;  // y^{m+1} is needed only below the cap
+            if (mv && lane == 0) prefetch_rows<true>(v, tc, tc.r0 + 2 * warp, min(2, tc.r0 + nr - (tc.r0 + 2 * warp)));
+            const SubDev& sd = v.sub[tc.sid];
+            const double* U = v.arena + sd.work + (long long)(m & 1) * 2 * K;
+            const double* Wv = U + K;
+            const double* c0 = v.arena + tc.c0;
+            const int wp = A.win_prev[tc.inst];
+            const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(m + 1, wp) * K : nullptr;
+            for (int c = tid; c < ld; c += WIN_THREADS) {
+                if (c < K) {
+                    const double y = m == 0 ? c0[c] : __ldcg(U + c) * is1 + __ldcg(Wv + c);
+                    vs[c] = y;
+                    vf[c] = ds_split(y);
+                    bf[c] = bsrc ? ds_split(tc.kdt * bsrc[c]) : make_float2(0.f, 0.f);
+                } else {
+                    vf[c] = make_float2(0.f, 0.f);
+                    bf[c] = make_float2(0.f, 0.f);
+                }
+            }
+            __syncthreads();
+            double* ym = own(tc, m % 3);
+            double* hrow = v.arena + tc.hist + (long long)m * K;
+            for (int r = tid; r < nr; r += WIN_THREADS) {
+                ym[r] = vs[tc.r0 + r];
+                hrow[tc.r0 + r] = vs[tc.r0 + r];
+            }
+            double* zm = own(tc, 3 + m % 3);
+            z_rows_staged(tc, v.arena + tc.p1, v.arena + tc.p2, vs, zm, tmp, Ps);
+            // partials: s_m^2 (own rows of y^m . z^m) and D_{m-1}
+            const bool dn = m >= 2 && tc.ngf_stop;
+            const double* y1 = own(tc, (m + 2) % 3);
+            const double* y2 = own(tc, (m + 1) % 3);
+            const double* z1 = own(tc, 3 + (m + 2) % 3);
+            const double* z2 = own(tc, 3 + (m + 1) % 3);
+            double acc = 0, accd = 0;
+            for (int r = tid; r < nr; r += WIN_THREADS) {
+                acc += ym[r] * zm[r];
+                if (dn) accd += (y1[r] * is1 - y2[r] * is2) * (z1[r] * is1 - z2[r] * is2);
+            }
+            acc = warp_sum(acc);
+            accd = warp_sum(accd);
+            if (lane == 0) {
+                red[warp] = acc;
+                red[16 + warp] = accd;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double a = 0, b = 0;
+                for (int i = 0; i < nw; ++i) {
+                    a += red[i];
+                    b += red[16 + i];
+                }
+                A.part_s[t] = a;
+                if (dn) A.part_d[t] = b;
+            }
+            // rows of u^{m+1} = G y^m and w^{m+1} = G (kappa dt b'^{m+1}), one pass over G
+            double* Un = v.arena + sd.work + (long long)((m + 1) & 1) * 2 * K;
+            double* Wn = Un + K;
+            const float* Gh = (const float*)(v.arena + tc.Gf);
+            const float* Gl = Gh + (long long)K * ld;
+            for (int rb = tc.r0 + 2 * warp; mv && rb < tc.r0 + nr; rb += 2 * nw) {
+                const int nrow = min(2, tc.r0 + nr - rb);
+                if (lane == 0) prefetch_rows<true>(v, tc, rb + 2 * nw, min(2, tc.r0 + nr - (rb + 2 * nw)));
+                double y[2], w[2];
+                if (bsrc) df32_rows2x2<true>(Gh, Gl, ld, vf, bf, rb, nrow, lane, y, w);
+                else df32_rows2x2<false>(Gh, Gl, ld, vf, bf, rb, nrow, lane, y, w);
+                if (lane == 0) {
+                    for (int i = 0; i < nrow; ++i) {
+                        Un[rb + i] = y[i];
+                        Wn[rb + i] = w[i];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        target += gridDim.x;
+        ++gen;
+        if (!reduce_barrier_sd(&A.bar->count, &A.bar->gen, target, gen, A.part_s, A.part_d, A.inst_task0, ni,
+                               A.sums_s, A.sums_d, v.inst, A.scal_inst + (m & 1) * 2 * ni, v.err, A.spin_limit, red,
+                               A.n_active, &go))
+            return;
+        if (!go) return;
+    }
+}
+
 __global__ void k_window_reset(SweepArgs A, int n_inst) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.bar->count = 0;
@@ -1021,11 +1319,17 @@ size_t window_smem(int kmax, int kdmax, int rows_max, int tasks_in_smem, long lo
            (size_t)g_resident_floats * sizeof(float);
 }
 
+size_t window_smem_split(int kmax, int kdmax, int rows_max) {
+    return (3 * (size_t)df32_ld(kmax) + (size_t)rows_max + 2 * (size_t)kdmax + 2 * (size_t)kdmax * kdmax) *
+           sizeof(double);
+}
+
 int window_tasks_per_cta_max() { return WIN_TPC; }
 int window_rows_per_task_max() { return WIN_RB; }
 
 static const void* window_kernel(int variant, bool df32) {
     if (variant == WIN_FUSED) return (const void*)k_window_fused;
+    if (variant == WIN_SPLIT) return (const void*)k_window_split;
     return df32 ? (const void*)k_window_2ph<true> : (const void*)k_window_2ph<false>;
 }
 

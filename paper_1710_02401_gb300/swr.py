@@ -22,7 +22,7 @@ SWR_OK, SWR_EINVAL, SWR_ENOMEM, SWR_ECUDA, SWR_ESINGULAR, SWR_ENUMERIC, SWR_ENOT
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENUMERIC", "ENOTCONV", "ETIMEOUT", "ESTATE"]
 MODE_TISE, MODE_TDSE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
-WINDOW_AUTO, WINDOW_TWO_PHASE, WINDOW_FUSED = 0, 1, 2
+WINDOW_AUTO, WINDOW_TWO_PHASE, WINDOW_FUSED, WINDOW_SPLIT = 0, 1, 2, 3
 LAUNCH_GRAPH, LAUNCH_DIRECT = 0, 1
 GET, SET = 0, 1
 (FIELD_ENERGY, FIELD_NORM2, FIELD_DIPOLE, FIELD_RES, FIELD_WINDOW, FIELD_PSI_NODES, FIELD_OWN_TRACES,

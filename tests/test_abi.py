@@ -141,7 +141,10 @@ def test_window_plan_requests_on_host(lib):
         (S.WINDOW_FUSED, 0, S.PREC_MIXED, True),
         (S.WINDOW_FUSED, 0, S.PREC_FP64, False),    # the fused kernel is the mixed one
         (S.WINDOW_FUSED, 256, S.PREC_MIXED, False),  # 256-row tasks do not fit its shared memory
-        (3, 0, S.PREC_FP64, False),
+        (S.WINDOW_SPLIT, 0, S.PREC_MIXED, True),
+        (S.WINDOW_SPLIT, 256, S.PREC_MIXED, True),   # task state in global memory: any task size
+        (S.WINDOW_SPLIT, 0, S.PREC_FP64, False),     # the split kernel is the mixed one
+        (4, 0, S.PREC_MIXED, False),
         (0, 4, S.PREC_FP64, False),
         (0, 257, S.PREC_FP64, False),
     ]:
@@ -161,3 +164,9 @@ def test_window_plan_requests_on_host(lib):
     assert two.value <= auto.value
     pb.window_variant = S.WINDOW_FUSED
     assert lib.swr_workspace_size(C.byref(pb), C.byref(n)) == S.SWR_EINVAL
+    pb.window_variant = S.WINDOW_SPLIT  # runs it, without W
+    assert lib.swr_workspace_size(C.byref(pb), C.byref(n)) == S.SWR_OK
+    assert n.value == two.value
+    ps = _problem([P.small_tdse_2d()], keep)
+    ps.precision, ps.window_variant = S.PREC_MIXED, S.WINDOW_SPLIT
+    assert lib.swr_workspace_size(C.byref(ps), C.byref(n)) == S.SWR_EINVAL  # imaginary time only

@@ -66,6 +66,8 @@ def plan_ref():
     (1, 1, 32, 0),    # double-single two-phase
     (1, 1, 256, 1),   # double-single two-phase, task state in global memory
     (1, 2, 16, 0),    # fused (W) single-barrier
+    (1, 3, 16, 1),    # split single-barrier (u = G y, w = G b' in one pass)
+    (1, 3, 256, 1),
 ])
 def test_window_plans_match_oracle(S, plan_ref, precision, variant, rows, many):
     s = S.SWR(PLAN_INST, precision=precision, window_variant=variant, rows_per_task=rows)
@@ -83,15 +85,15 @@ def batch():
     return insts, refs
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_batched_uneven_many_tasks_per_cta(S, batch, precision):
-    # the two-phase kernel with its task state in global memory
+@pytest.mark.parametrize("precision,variant", [(0, 0), (1, 0), (1, 3)])
+def test_batched_uneven_many_tasks_per_cta(S, batch, precision, variant):
+    # the two-phase and split kernels with their task state in global memory
     insts, refs = batch
-    s = S.SWR(insts, precision=precision, rows_per_task=8)
+    s = S.SWR(insts, precision=precision, rows_per_task=8, window_variant=variant)
     plan = s.window_plan()
     n_tasks = sum(math.ceil(kd ** i.n_elec / 8) for i in insts for kd in i.K_d)
     assert plan["tasks"] == n_tasks and plan["tasks"] > 4 * plan["ctas"]
-    assert plan["task_state_global"] == 1 and plan["variant"] == 1
+    assert plan["task_state_global"] == 1 and plan["variant"] == (variant or 1)
     s.assemble()
     _check(*_steps(s, 2), refs)
 
