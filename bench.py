@@ -47,8 +47,8 @@ KERNEL_FUNCS = {
     "k_window_2ph<true>": ["reduce_barrier", "two_sum", "make_task_cache", "z_rows_sm", "z_rows_staged",
                            "prefetch_l2", "prefetch_rows", "df32_acc", "df32_rows4", "k_window_2ph"],
 }
-KERNEL_FUNCS["k_window_split"] = ["reduce_barrier_sd", "two_sum", "make_task_cache", "z_rows_staged", "prefetch_l2",
-                                  "prefetch_rows", "df32_acc", "df32_rows2x2", "k_window_split"]
+KERNEL_FUNCS["k_window_split"] = ["mbar_wait", "split_stage_rows", "reduce_barrier_sd", "two_sum", "make_task_cache",
+                                  "z_rows_staged", "df32_acc", "k_window_split"]
 KERNEL_FUNCS["k_window_2ph<true>@batched"] = KERNEL_FUNCS["k_window_2ph<true>"]
 KERNEL_FUNCS["k_window_split@batched"] = KERNEL_FUNCS["k_window_split"]
 PROFILED_TRAFFIC = {

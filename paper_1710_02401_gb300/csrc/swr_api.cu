@@ -22,7 +22,7 @@ cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, 
                             bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
                             const GemmJob* d_jobs2, double* d_norm_part);
 size_t window_smem(int kmax, int kdmax, int rows_max, int tasks_in_smem, long long g_resident_floats);
-size_t window_smem_split(int kmax, int kdmax, int rows_max);
+size_t window_smem_split(int kmax, int kdmax, int rows_max, int stage_floats, int n_stages);
 int window_tasks_per_cta_max();
 int window_rows_per_task_max();
 cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, int variant, bool df32);
@@ -64,6 +64,8 @@ struct swr_ctx {
     bool any_ee = false, tdse = false;
     long long psi_total = 0, own_total = 0;
     bool df32 = false, g_resident = false, any_ngf_stop = false;
+    int stage_floats = 0;           // split window: floats per stage of staged rows
+    int n_stages = 0;               // split window: stages in the ring
     int cn_iters = 0;
     std::vector<long long> boff;  // real time: per subdomain r, u, x work vectors
     long long* d_boff = nullptr;
@@ -99,6 +101,8 @@ struct swr_ctx {
     double *d_part_s = nullptr, *d_part_d = nullptr, *d_snorm = nullptr, *d_sums_s = nullptr, *d_sums_d = nullptr;
     int *d_n_active = nullptr, *d_win = nullptr, *d_win_prev = nullptr;
     GridBarrier* d_bar = nullptr;
+    SplitQueue* d_queue = nullptr;
+    int* d_qlist = nullptr;
     double *d_res_part = nullptr, *d_res = nullptr, *d_epart = nullptr, *d_energy = nullptr, *d_norm2 = nullptr;
     double* d_psi = nullptr;
     long long* d_psi_off = nullptr;
@@ -221,13 +225,19 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
 static const int ROWS_MIN = 8;          // smallest row task
 static const int ROWS_MANY_MAX = 256;    // largest row task (task state in global memory)
 static const size_t WIN_SMEM_TASKS_MAX = 100 * 1024;  // dynamic shared memory for two CTAs per SM
+static const int SPLIT_STAGES = 2;       // split window: stages of staged step-matrix rows in flight per CTA
+static const int SPLIT_STAGE_ROWS = 4;   // split window: rows of the widest subdomain per stage (at most)
 
 // Row tasks of the window kernel and their CTA ranges.  Every subdomain's rows
 // are cut into equal blocks of about `target_rows` rows (0: total rows over the
-// CTAs, at most 64); the tasks, in instance order, are dealt to `ctas` CTAs as
-// contiguous ranges of about equal cost (rows x (K + 64) plus a fixed per-task
-// overhead), so that uneven bases load the SMs evenly.
-static void plan_tasks(swr_ctx* c, int target_rows, int ctas) {
+// CTAs, at most 64); with `by_bytes`, that is the block of the widest
+// subdomain and a narrower subdomain of K rows gets blocks of about
+// target_rows x max_K / K rows, so that every task streams about the same bytes
+// (the split window hands tasks out dynamically).  The tasks, in instance
+// order, are dealt to `ctas` CTAs as contiguous ranges of about equal cost
+// (rows x (K + 64) plus a fixed per-task overhead), so that uneven bases load
+// the SMs evenly.
+static void plan_tasks(swr_ctx* c, int target_rows, int ctas, bool by_bytes = false) {
     c->tasks.clear();
     c->inst_task0.clear();
     c->cta_task0.clear();
@@ -250,7 +260,12 @@ static void plan_tasks(swr_ctx* c, int target_rows, int ctas) {
             c->inst_task0.push_back((int)c->tasks.size());
             ++cur_inst;
         }
-        int nt = (int)((s.K + target - 1) / target);
+        long long tgt = target;
+        if (by_bytes) {
+            tgt = (target * (long long)c->max_K + s.K / 2) / s.K;
+            if (tgt > ROWS_MANY_MAX) tgt = ROWS_MANY_MAX;
+        }
+        int nt = (int)((s.K + tgt - 1) / tgt);
         int per = (s.K + nt - 1) / nt;
         for (int r0 = 0; r0 < s.K; r0 += per) {
             Task t;
@@ -312,7 +327,7 @@ static long long task_capacity(const swr_ctx* c) {
 static bool plan_window(swr_ctx* c, int variant_req, int rows_req, bool have_dev) {
     const int nsm = c->nsm > 0 ? c->nsm : 152;
     for (int per_sm = 2; per_sm >= 1; --per_sm) {
-        plan_tasks(c, rows_req, per_sm * nsm);
+        plan_tasks(c, rows_req, per_sm * nsm, variant_req == WIN_SPLIT);
         const bool fits = c->tasks_per_cta <= window_tasks_per_cta_max() && c->max_rows <= window_rows_per_task_max() &&
                           window_smem(c->max_K, c->max_kd, c->max_rows, c->tasks_per_cta, 0) <= WIN_SMEM_TASKS_MAX;
         int variant = variant_req;
@@ -324,9 +339,20 @@ static bool plan_window(swr_ctx* c, int variant_req, int rows_req, bool have_dev
         const long long gres_floats = (long long)c->max_rows * df32_ld(c->max_K);
         c->g_resident = variant == WIN_FUSED && c->tasks_per_cta == 1 &&
                         window_smem(c->max_K, c->max_kd, c->max_rows, 1, gres_floats) <= 110 * 1024;
-        c->win_smem = variant == WIN_SPLIT ? window_smem_split(c->max_K, c->max_kd, c->max_rows)
-                                           : window_smem(c->max_K, c->max_kd, c->max_rows, c->many ? 1 : c->tasks_per_cta,
-                                                         c->g_resident ? gres_floats : 0);
+        if (variant == WIN_SPLIT) {
+            // stages of 4 rows of the widest subdomain (both planes), fewer rows when
+            // the shared memory of per_sm CTAs per SM would not hold two of them
+            const size_t budget = per_sm == 2 ? 112 * 1024 : 225 * 1024;
+            c->n_stages = SPLIT_STAGES;
+            for (int rs = SPLIT_STAGE_ROWS; rs >= 1; rs >>= 1) {
+                c->stage_floats = 2 * rs * df32_ld(c->max_K);
+                if (window_smem_split(c->max_K, c->max_kd, c->max_rows, c->stage_floats, c->n_stages) <= budget) break;
+            }
+            c->win_smem = window_smem_split(c->max_K, c->max_kd, c->max_rows, c->stage_floats, c->n_stages);
+        } else {
+            c->win_smem = window_smem(c->max_K, c->max_kd, c->max_rows, c->many ? 1 : c->tasks_per_cta,
+                                      c->g_resident ? gres_floats : 0);
+        }
         c->bps = per_sm;
         if (!have_dev) return true;
         int bps = 0;
@@ -507,7 +533,7 @@ static void plan(swr_ctx* c) {
 struct AuxPlan {
     size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, cta0, tc, scal, alive, own,
         ctal, wfix, snorm, sums_s, sums_d,
-        n_active, win, win_prev, bar, res_part, res, epart, energy, norm2, dipole, boff, psi, psi_off, total;
+        n_active, win, win_prev, bar, queue, qlist, res_part, res, epart, energy, norm2, dipole, boff, psi, psi_off, total;
 };
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 static AuxPlan aux_plan(const swr_ctx* c) {
@@ -538,6 +564,8 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.win = o; o = al256(o + ni * sizeof(int));
     a.win_prev = o; o = al256(o + ni * sizeof(int));
     a.bar = o; o = al256(o + sizeof(GridBarrier));
+    a.queue = o; o = al256(o + sizeof(SplitQueue));
+    a.qlist = o; o = al256(o + 2 * nt * sizeof(int));
     a.res_part = o; o = al256(o + ns * RES_BLOCKS * sizeof(double));
     a.res = o; o = al256(o + ni * sizeof(double));
     a.epart = o; o = al256(o + 3 * ns * sizeof(double));
@@ -684,6 +712,8 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->d_win = (int*)(b + a.win);
     c->d_win_prev = (int*)(b + a.win_prev);
     c->d_bar = (GridBarrier*)(b + a.bar);
+    c->d_queue = (SplitQueue*)(b + a.queue);
+    c->d_qlist = (int*)(b + a.qlist);
     c->d_res_part = (double*)(b + a.res_part);
     c->d_res = (double*)(b + a.res);
     c->d_epart = (double*)(b + a.epart);
@@ -823,7 +853,11 @@ static SweepArgs sweep_args(swr_ctx* c) {
     a.win_prev = c->d_win_prev;
     a.cap = c->cap;
     a.bar = c->d_bar;
+    a.q = c->d_queue;
+    a.q_list = c->d_qlist;
     a.spin_limit = SPIN_LIMIT;
+    a.stage_floats = c->stage_floats;
+    a.n_stages = c->n_stages;
     return a;
 }
 

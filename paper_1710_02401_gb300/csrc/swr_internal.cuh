@@ -101,6 +101,16 @@ struct GridBarrier {
     unsigned int pad1[31];
 };
 
+// Work queue of the split window, by step parity p: list[p] holds the tasks
+// still stepping at a step of parity p (appended during the step before),
+// count[p] its length, claim[p] the next list position to hand out.
+struct SplitQueue {
+    unsigned int claim[2];
+    unsigned int pad0[30];
+    unsigned int count[2];
+    unsigned int pad1[30];
+};
+
 __device__ inline bool grid_sync_bounded(GridBarrier* bar, unsigned int nblocks, int* err,
                                          long long limit) {
     __shared__ int s_ok;
@@ -228,6 +238,10 @@ struct SweepArgs {
     int cap;                    // max window stored
     GridBarrier* bar;
     long long spin_limit;
+    int stage_floats;           // split window: floats per stage of staged step-matrix rows (both planes)
+    int n_stages;               // split window: stages in the ring (2..8)
+    SplitQueue* q;              // split window: work queue counters
+    int* q_list;                // split window: [2][n_tasks] task lists by step parity
 };
 
 // What the allocation-free residual entry point needs from a context.

@@ -27,6 +27,7 @@
 // in FP32 pairs, v = v_hi + v_lo; products run on the FP32 pipes with
 // error-free TwoProduct/TwoSum accumulation into a (hi, lo) pair, which keeps
 // the FP64 accuracy of the step (~1e-14) on units with 64x the FP64 rate.
+#include <limits.h>
 #include <math.h>
 
 #include "swr_internal.cuh"
@@ -933,81 +934,67 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
 
 // ------------------------------------------------------- single-barrier window
 //
-// Mixed precision, batches of any size, ONE reduce-barrier per step, G read
-// once per step (8 bytes per element).  With y^{n+1} = G (y^n / s_n + kappa dt
-// b'^{n+1}) = u^{n+1} / s_n + w^{n+1}, u^{n+1} = G y^n, w^{n+1} = G (kappa dt
-// b'^{n+1}), both products need no s_n: phase X(m) forms the full y^m =
-// u^m / s_{m-1} + w^m of each of its tasks' subdomains (s_{m-1} reduced at the
-// last barrier), writes its rows, computes z^m = (Pp (x) Pp) y^m and the
-// partials of s_m^2 and D_{m-1} = ||c^{m-1} - c^{m-2}||_chi^2, and the rows of
-// u^{m+1} and w^{m+1} in one double-single pass over G (two dot products per
-// row).  The stop of the plain algorithm at step n is decided at X(n+2) (D_n
-// is reduced at the barrier after X(n+1)), the steps computed beyond it are
-// dropped.  u and w live, double-buffered by step parity, in the subdomain's
-// assembly scratch.  Per-task state in global memory.
-// Dynamic shared memory (doubles): vs[kmax4] | vf[kmax4] (float2) | bf[kmax4]
-// (float2) | tmp[rows_max + 2 kdmax] | Ps[2 kdmax^2]
+// Mixed precision, batches of any size, ONE reduce-barrier per step, G streamed
+// from HBM once per step (8 bytes per element) through shared memory.  With
+// y^{n+1} = G (y^n / s_n + kappa dt b'^{n+1}) = u^{n+1} / s_n + w^{n+1},
+// u^{n+1} = G y^n, w^{n+1} = G (kappa dt b'^{n+1}), neither product needs
+// s_n: phase X(m) forms the full y^m = u^m / s_{m-1} + w^m of each of its
+// tasks' subdomains (s_{m-1} reduced at the last barrier), writes its rows,
+// computes z^m = (Pp (x) Pp) y^m and the partials of s_m^2 and
+// D_{m-1} = ||c^{m-1} - c^{m-2}||_chi^2, and the rows of u^{m+1} and w^{m+1}
+// in one double-single pass over G.  The stop of the plain algorithm at step
+// n is decided at X(n+2) (D_n is reduced at the barrier after X(n+1)); the
+// steps computed beyond it are dropped.  u and w live, double-buffered by step
+// parity, in the subdomain's assembly scratch.  Task state in global memory.
+//
+// The rows of G reach shared memory by bulk copies (cp.async.bulk, both FP32
+// planes of a stage of rows per copy pair) into a ring of n_stages stages
+// (2..SPLIT_NS_MAX, a plan parameter), each completing on its own mbarrier;
+// thread 0 issues the next stage as soon as a slot is consumed, along the
+// CTA's fixed order of (step, task, rows), so the copies stay in flight
+// through the prologues of the tasks (y, z, partials) and through the grid
+// barrier (G is constant: the first stages of step m+1 load while the barrier
+// after step m completes).  Step m+1 streams the tasks still stepping after
+// the decisions of step m; a task found stopped at m+1 has its stages waited
+// for and skipped.
+// Dynamic shared memory: vs[kmax4] doubles | vf[kmax4] float2 | bf[kmax4] float2
+// | tmp[rows_max + 2 kdmax] | Ps[2 kdmax^2] | (128-byte aligned) ring of
+// n_stages stages of stage_floats floats.
+#define SPLIT_NS_MAX 8
+#define SPLIT_FIFO 8        // claimed tasks queued between the producer thread and the consumers
+#define SPLIT_CLAIM_MAX 8   // list positions per claim (at most)
 
-// Two double-single dot products per row over one pass of G (TWO) or one.
-template <bool TWO>
-__device__ inline void df32_rows2x2(const float* Gh, const float* Gl, int ld, const float2* vf, const float2* bf, int rb,
-                                    int nrow, int lane, double* y, double* w) {
-    float yh[2] = {0.f, 0.f}, yl[2] = {0.f, 0.f}, wh[2] = {0.f, 0.f}, wl[2] = {0.f, 0.f};
-    for (int c = lane * 4; c < ld; c += 128) {
-        const float4 xa = *reinterpret_cast<const float4*>(vf + c), xb = *reinterpret_cast<const float4*>(vf + c + 2);
-        float4 ba = make_float4(0.f, 0.f, 0.f, 0.f), bb = ba;
-        if (TWO) {
-            ba = *reinterpret_cast<const float4*>(bf + c);
-            bb = *reinterpret_cast<const float4*>(bf + c + 2);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            if (i < nrow) {
-                const long long o = (long long)(rb + i) * ld + c;
-                const float4 g0 = *reinterpret_cast<const float4*>(Gh + o);
-                const float4 g1 = *reinterpret_cast<const float4*>(Gl + o);
-                df32_acc(yh[i], yl[i], g0.x, g1.x, xa.x, xa.y);
-                df32_acc(yh[i], yl[i], g0.y, g1.y, xa.z, xa.w);
-                df32_acc(yh[i], yl[i], g0.z, g1.z, xb.x, xb.y);
-                df32_acc(yh[i], yl[i], g0.w, g1.w, xb.z, xb.w);
-                if (TWO) {
-                    df32_acc(wh[i], wl[i], g0.x, g1.x, ba.x, ba.y);
-                    df32_acc(wh[i], wl[i], g0.y, g1.y, ba.z, ba.w);
-                    df32_acc(wh[i], wl[i], g0.z, g1.z, bb.x, bb.y);
-                    df32_acc(wh[i], wl[i], g0.w, g1.w, bb.z, bb.w);
-                }
-            }
-        }
+__device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Bounded wait for the phase of parity `par` of an mbarrier.
+__device__ inline bool mbar_wait(const unsigned long long* bar, unsigned par, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(par)
+            : "memory");
+        if (done) return true;
     }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float sh, eh;
-            float oh = __shfl_xor_sync(0xffffffffu, yh[i], o), ol = __shfl_xor_sync(0xffffffffu, yl[i], o);
-            two_sum(yh[i], oh, sh, eh);
-            yh[i] = sh;
-            yl[i] = yl[i] + ol + eh;
-            if (TWO) {
-                oh = __shfl_xor_sync(0xffffffffu, wh[i], o);
-                ol = __shfl_xor_sync(0xffffffffu, wl[i], o);
-                two_sum(wh[i], oh, sh, eh);
-                wh[i] = sh;
-                wl[i] = wl[i] + ol + eh;
-            }
-        }
-        y[i] = (double)yh[i] + (double)yl[i];
-        w[i] = TWO ? (double)wh[i] + (double)wl[i] : 0.0;
-    }
+    return false;
+}
+
+// Rows per stage for rows of ld floats: a power of two <= 32 with both planes in
+// stage_floats.
+__device__ inline int split_stage_rows(int ld, int stage_floats) {
+    const int r = stage_floats / (2 * ld);
+    return r >= 32 ? 32 : r >= 16 ? 16 : r >= 8 ? 8 : r >= 4 ? 4 : r >= 2 ? 2 : 1;
 }
 
 // Last-arriver reduction of two partial arrays per instance (warp per instance
 // from 8 instances on), s = sqrt(sum_a) and 1/s per instance into scal_out,
-// then the release (go = 0 when `nact` shows no instance still stepping).
+// the reset of the work queue of parity `qpar` (its list is used up), then the
+// release (go = 0 when `nact` shows no instance still stepping).
 __device__ bool reduce_barrier_sd(unsigned* count, unsigned* release, unsigned target, unsigned gen,
                                   const double* part_a, const double* part_b, const int* inst_task0, int n_inst,
                                   double* sums_a, double* sums_b, const InstDev* inst, double* scal_out, int* err,
-                                  long long limit, double* red, const int* nact, int* go_out) {
+                                  long long limit, double* red, const int* nact, int* go_out, SplitQueue* q, int qpar) {
     __shared__ int s_last, s_ok, s_go;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1058,6 +1045,8 @@ __device__ bool reduce_barrier_sd(unsigned* count, unsigned* release, unsigned t
         }
         __syncthreads();
         if (threadIdx.x == 0) {
+            q->claim[qpar] = 0;
+            q->count[qpar] = 0;
             const int go = nact ? (__ldcg(nact) > 0) : 1;
             s_go = go;
             __threadfence();
@@ -1082,85 +1071,203 @@ __device__ bool reduce_barrier_sd(unsigned* count, unsigned* release, unsigned t
 __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
     extern __shared__ double sm[];
     __shared__ double red[33];
+    __shared__ __align__(8) unsigned long long full[SPLIT_NS_MAX];
+    __shared__ float4 sred[2][32];
+    __shared__ int fifo[SPLIT_FIFO];
+    __shared__ int cbuf[SPLIT_CLAIM_MAX];
+    __shared__ int s_fail;
     int go = 1;
     const SwrDeviceView& v = A.v;
-    const int t_begin = A.cta_task0[blockIdx.x];
-    const int ntk = A.cta_task0[blockIdx.x + 1] - t_begin;
-    TaskCache* tcs = A.g_tc + t_begin;
-    int* alive = A.g_alive + t_begin;
-    const int cap = A.cap, ni = v.n_inst;
+    const int cap = A.cap, ni = v.n_inst, SC = A.stage_floats, nt = A.n_tasks;
+    const unsigned NS = (unsigned)A.n_stages;
     const int kmax = df32_ld(A.kmax), kdmax = A.kdmax;
     double* vs = sm;
     float2* vf = (float2*)(sm + kmax);
     float2* bf = (float2*)(sm + 2 * kmax);
     double* tmp = sm + 3 * kmax;
     double* Ps = tmp + A.rows_max + 2 * kdmax;
+    float* ring = (float*)(sm + ((3 * kmax + A.rows_max + 2 * kdmax + 2 * kdmax * kdmax + 15) & ~15));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = WIN_THREADS / 32;
+    const long long wait_limit = A.spin_limit >> 4;
+    SplitQueue* q = A.q;
     unsigned target = 0, gen = 0;
+    unsigned consumed = 0;  // stages consumed (every thread)
+    int fhead = 0;          // task entries taken from the FIFO (every thread)
+    // thread 0: producer state
+    unsigned issued = 0;                               // stages issued
+    int ftail = 0;                                     // task entries pushed
+    bool p_has = false, p_done = false;                // a task with stages left to issue; step's list exhausted
+    int prb = 0, p_end = 0, p_ld = 0, p_rs = 0;        // its next row, end row, row stride, rows per stage
+    const float* p_gh = nullptr;                       // its G_hi plane (G_lo follows after p_plane floats)
+    long long p_plane = 0;
+    int c_next = 0, c_end = 0;                         // claimed list positions not yet taken (task ids in cbuf)
+    unsigned c_hint = 0;                               // end of the last claim (estimate of the list handed out)
+    unsigned a_pos = 0;                                // pending append: list position (from the atomic)
+    int a_t = -1, a_par = 0;                           // pending append: task, list parity
     auto own = [&](const TaskCache& tc, int slot) -> double* { return A.g_own + tc.own + (long long)slot * tc.nr; };
 
-    for (int j = 0; j < ntk; ++j) {
-        if (tid == 0) {
-            tcs[j] = make_task_cache(A, A.cta_list[t_begin + j]);
-            alive[j] = 1;
+    // Thread 0: the next task id of step m from the list (guided chunks of at most
+    // SPLIT_CLAIM_MAX positions, smaller as the list runs out), -1 at its end.
+    auto next_task = [&](int m) -> int {
+        if (c_next == c_end) {
+            const unsigned n = m == 0 ? (unsigned)nt : __ldcg(&q->count[m & 1]);
+            unsigned b = c_hint < n ? (n - c_hint) / (2u * gridDim.x) : 1u;
+            b = b < 1u ? 1u : (b > SPLIT_CLAIM_MAX ? SPLIT_CLAIM_MAX : b);
+            const unsigned i = atomicAdd(&q->claim[m & 1], b);
+            c_hint = i + b;
+            if (i >= n) return -1;
+            const unsigned e = i + b < n ? i + b : n;
+            for (unsigned k = i; k < e; ++k)
+                cbuf[k - i] = m == 0 ? (int)k : __ldcg(A.q_list + (size_t)(m & 1) * nt + k);
+            c_next = 0;
+            c_end = (int)(e - i);
         }
-    }
-    __syncthreads();
-
-    for (int m = 0;; ++m) {
-        const double* sc1 = A.scal_inst + ((m - 1) & 1) * 2 * ni;  // s_{m-1}, 1/s_{m-1}
-        const double* sc2 = A.scal_inst + ((m - 2) & 1) * 2 * ni;  // s_{m-2}, 1/s_{m-2}
-        for (int j = 0; j < ntk; ++j) {
-            __syncthreads();
-            if (!alive[j]) continue;
-            const TaskCache tc = tcs[j];
-            const int K = tc.K, nr = tc.nr, ld = df32_ld(K);
-            const int t = A.cta_list[t_begin + j];
-            const double s1 = m >= 1 ? __ldcg(sc1 + tc.inst) : 1.0;
-            const double is1 = m >= 1 ? __ldcg(sc1 + ni + tc.inst) : 1.0;
-            const double is2 = m >= 2 ? __ldcg(sc2 + ni + tc.inst) : 1.0;
-            // the plain algorithm's stop at n = m-2 (D_{m-2}), then at n = m-1
-            int stop = 0, win = 0, bad = 0;
-            if (m >= 3 && tc.ngf_stop && sqrt(fmax(__ldcg(A.sums_d + tc.inst), 0.0)) <= tc.ngf_tol) {
-                stop = 1;
-                win = m - 2;
-            } else if (m >= 1 && (m - 1 >= tc.maxs || !isfinite(s1) || s1 <= 0.0)) {
-                stop = 1;
-                win = m - 1;
-                bad = !isfinite(s1) || s1 <= 0.0;
+        return cbuf[c_next++];
+    };
+    auto flush_append = [&]() {
+        if (a_t >= 0) A.q_list[(size_t)a_par * nt + a_pos] = a_t;
+        a_t = -1;
+    };
+    // Thread 0: issue stages while ring slots are free; claim, decide and queue
+    // tasks while the FIFO has room (and the ring is not full with queued work).
+    auto produce = [&](int m) {
+        const double* sc1 = A.scal_inst + ((m - 1) & 1) * 2 * ni;
+        for (;;) {
+            if (p_has) {
+                if (issued - consumed >= NS) return;
+                const int nrow = min(p_rs, p_end - prb);
+                const unsigned slot = issued % NS, bytes = (unsigned)nrow * p_ld * 4u;
+                const float* Gh = p_gh + (long long)prb * p_ld;
+                float* dst = ring + (size_t)slot * SC;
+                const unsigned mb = smem_u32(&full[slot]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2u * bytes)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(dst)),
+                    "l"(Gh), "r"(bytes), "r"(mb)
+                    : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(dst + p_rs * p_ld)),
+                    "l"(Gh + p_plane), "r"(bytes), "r"(mb)
+                    : "memory");
+                ++issued;
+                prb += p_rs;
+                if (prb >= p_end) p_has = false;
+                continue;
             }
-            if (tid == 0 && tc.first && m >= 1) A.snorm[(long long)tc.inst * (cap + 1) + m - 1] = s1;
-            if (stop) {
-                if (tid == 0) {
-                    alive[j] = 0;
+            if (p_done || ftail - fhead >= SPLIT_FIFO) return;
+            if (ftail > fhead && issued - consumed >= NS) return;
+            const int t = next_task(m);
+            if (t < 0) {
+                fifo[ftail % SPLIT_FIFO] = -1;
+                ++ftail;
+                p_done = true;
+                return;
+            }
+            const TaskCache tc = make_task_cache(A, t);
+            if (m >= 1) {
+                // the plain algorithm's stop at n = m-2 (D_{m-2}), else at n = m-1
+                // (cap, or s_{m-1} not positive and finite)
+                const double s1 = __ldcg(sc1 + tc.inst);
+                int stop = 0, win = 0, bad = 0;
+                if (m >= 3 && tc.ngf_stop && sqrt(fmax(__ldcg(A.sums_d + tc.inst), 0.0)) <= tc.ngf_tol) {
+                    stop = 1;
+                    win = m - 2;
+                } else if (m - 1 >= tc.maxs || !isfinite(s1) || s1 <= 0.0) {
+                    stop = 1;
+                    win = m - 1;
+                    bad = !isfinite(s1) || s1 <= 0.0;
+                }
+                if (tc.first) A.snorm[(long long)tc.inst * (cap + 1) + m - 1] = s1;
+                if (stop) {
                     if (tc.first) {
                         A.win[tc.inst] = win;
                         if (bad) atomicOr(v.err, SWR_ERR_NUMERIC);
                         __threadfence();
                         atomicSub(A.n_active, 1);
                     }
+                    continue;
                 }
-                continue;
             }
-            // full y^m = u^m / s_{m-1} + w^m (y^0 = c0), and kappa dt b'^{m+1}; the
-            // warp's first rows of G travel to L2 meanwhile
-            const bool mv = m < tc.maxs;  // y^{m+1} is needed only below the cap
-            if (mv && lane == 0) prefetch_rows<true>(v, tc, tc.r0 + 2 * warp, min(2, tc.r0 + nr - (tc.r0 + 2 * warp)));
+            // still stepping after the decisions of step m: a member of step m+1's list
+            // (the list entry is stored at the next append or at the end of the step,
+            // so that the atomic's round trip overlaps other work)
+            flush_append();
+            a_par = (m + 1) & 1;
+            a_pos = atomicAdd(&q->count[a_par], 1u);
+            a_t = t;
+            const bool str = m < tc.maxs;
+            fifo[ftail % SPLIT_FIFO] = 2 * t + (str ? 1 : 0);
+            ++ftail;
+            if (str) {
+                p_has = true;
+                prb = tc.r0;
+                p_end = tc.r0 + tc.nr;
+                p_ld = df32_ld(tc.K);
+                p_rs = split_stage_rows(p_ld, SC);
+                p_gh = (const float*)(v.arena + tc.Gf);
+                p_plane = (long long)tc.K * p_ld;
+            }
+        }
+    };
+    // Thread 0: wait (bounded) for every stage still in flight before the CTA ends.
+    auto drain = [&]() {
+        if (tid == 0) {
+            for (; consumed < issued; ++consumed)
+                if (!mbar_wait(&full[consumed % NS], (consumed / NS) & 1u, wait_limit)) {
+                    atomicOr(v.err, SWR_ERR_TIMEOUT);
+                    break;
+                }
+        }
+        __syncthreads();
+    };
+
+    if (tid == 0) {
+        for (unsigned i = 0; i < NS; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+
+    for (int m = 0;; ++m) {
+        const double* sc1 = A.scal_inst + ((m - 1) & 1) * 2 * ni;  // s_{m-1}, 1/s_{m-1}
+        const double* sc2 = A.scal_inst + ((m - 2) & 1) * 2 * ni;  // s_{m-2}, 1/s_{m-2}
+        c_next = c_end = 0;
+        c_hint = 0;
+        p_done = false;
+        for (;;) {
+            __syncthreads();
+            if (tid == 0) produce(m);
+            __syncthreads();
+            const int e = fifo[fhead % SPLIT_FIFO];
+            ++fhead;
+            if (e < 0) break;
+            const int t = e >> 1;
+            const bool str = (e & 1) != 0;
+            const TaskCache tc = make_task_cache(A, t);
+            const int K = tc.K, nr = tc.nr, ld = df32_ld(K);
             const SubDev& sd = v.sub[tc.sid];
-            const double* U = v.arena + sd.work + (long long)(m & 1) * 2 * K;
-            const double* Wv = U + K;
-            const double* c0 = v.arena + tc.c0;
             const int wp = A.win_prev[tc.inst];
             const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(m + 1, wp) * K : nullptr;
-            for (int c = tid; c < ld; c += WIN_THREADS) {
-                if (c < K) {
-                    const double y = m == 0 ? c0[c] : __ldcg(U + c) * is1 + __ldcg(Wv + c);
-                    vs[c] = y;
-                    vf[c] = ds_split(y);
-                    bf[c] = bsrc ? ds_split(tc.kdt * bsrc[c]) : make_float2(0.f, 0.f);
-                } else {
-                    vf[c] = make_float2(0.f, 0.f);
-                    bf[c] = make_float2(0.f, 0.f);
+            // full y^m = u^m / s_{m-1} + w^m (y^0 = c0), and kappa dt b'^{m+1}
+            const double is1 = m >= 1 ? __ldcg(sc1 + ni + tc.inst) : 1.0;
+            const double is2 = m >= 2 ? __ldcg(sc2 + ni + tc.inst) : 1.0;
+            {
+                const double* U = v.arena + sd.work + (long long)(m & 1) * 2 * K;
+                const double* Wv = U + K;
+                const double* c0 = v.arena + tc.c0;
+                for (int c = tid; c < ld; c += WIN_THREADS) {
+                    if (c < K) {
+                        const double y = m == 0 ? c0[c] : __ldcg(U + c) * is1 + __ldcg(Wv + c);
+                        vs[c] = y;
+                        vf[c] = ds_split(y);
+                        bf[c] = bsrc ? ds_split(tc.kdt * bsrc[c]) : make_float2(0.f, 0.f);
+                    } else {
+                        vf[c] = make_float2(0.f, 0.f);
+                        bf[c] = make_float2(0.f, 0.f);
+                    }
                 }
             }
             __syncthreads();
@@ -1173,59 +1280,119 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
             double* zm = own(tc, 3 + m % 3);
             z_rows_staged(tc, v.arena + tc.p1, v.arena + tc.p2, vs, zm, tmp, Ps);
             // partials: s_m^2 (own rows of y^m . z^m) and D_{m-1}
-            const bool dn = m >= 2 && tc.ngf_stop;
-            const double* y1 = own(tc, (m + 2) % 3);
-            const double* y2 = own(tc, (m + 1) % 3);
-            const double* z1 = own(tc, 3 + (m + 2) % 3);
-            const double* z2 = own(tc, 3 + (m + 1) % 3);
-            double acc = 0, accd = 0;
-            for (int r = tid; r < nr; r += WIN_THREADS) {
-                acc += ym[r] * zm[r];
-                if (dn) accd += (y1[r] * is1 - y2[r] * is2) * (z1[r] * is1 - z2[r] * is2);
-            }
-            acc = warp_sum(acc);
-            accd = warp_sum(accd);
-            if (lane == 0) {
-                red[warp] = acc;
-                red[16 + warp] = accd;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double a = 0, b = 0;
-                for (int i = 0; i < nw; ++i) {
-                    a += red[i];
-                    b += red[16 + i];
+            {
+                const bool dn = m >= 2 && tc.ngf_stop;
+                const double* y1 = own(tc, (m + 2) % 3);
+                const double* y2 = own(tc, (m + 1) % 3);
+                const double* z1 = own(tc, 3 + (m + 2) % 3);
+                const double* z2 = own(tc, 3 + (m + 1) % 3);
+                double acc = 0, accd = 0;
+                for (int r = tid; r < nr; r += WIN_THREADS) {
+                    acc += ym[r] * zm[r];
+                    if (dn) accd += (y1[r] * is1 - y2[r] * is2) * (z1[r] * is1 - z2[r] * is2);
                 }
-                A.part_s[t] = a;
-                if (dn) A.part_d[t] = b;
+                acc = warp_sum(acc);
+                accd = warp_sum(accd);
+                if (lane == 0) {
+                    red[warp] = acc;
+                    red[16 + warp] = accd;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    double a = 0, b = 0;
+                    for (int i = 0; i < nw; ++i) {
+                        a += red[i];
+                        b += red[16 + i];
+                    }
+                    A.part_s[t] = a;
+                    if (dn) A.part_d[t] = b;
+                }
             }
-            // rows of u^{m+1} = G y^m and w^{m+1} = G (kappa dt b'^{m+1}), one pass over G
+            if (!str) continue;
+            // rows of u^{m+1} = G y^m and w^{m+1} = G (kappa dt b'^{m+1}) from the staged
+            // rows: rs rows per stage; up to 8 rows, 8 / rs warps per row (lanes over
+            // groups of 4 columns), beyond, one warp per row
+            const int rs = split_stage_rows(ld, SC), wpr = rs >= nw ? 1 : nw / rs;
+            const int part = warp % wpr, rstep = nw / wpr;
             double* Un = v.arena + sd.work + (long long)((m + 1) & 1) * 2 * K;
             double* Wn = Un + K;
-            const float* Gh = (const float*)(v.arena + tc.Gf);
-            const float* Gl = Gh + (long long)K * ld;
-            for (int rb = tc.r0 + 2 * warp; mv && rb < tc.r0 + nr; rb += 2 * nw) {
-                const int nrow = min(2, tc.r0 + nr - rb);
-                if (lane == 0) prefetch_rows<true>(v, tc, rb + 2 * nw, min(2, tc.r0 + nr - (rb + 2 * nw)));
-                double y[2], w[2];
-                if (bsrc) df32_rows2x2<true>(Gh, Gl, ld, vf, bf, rb, nrow, lane, y, w);
-                else df32_rows2x2<false>(Gh, Gl, ld, vf, bf, rb, nrow, lane, y, w);
-                if (lane == 0) {
-                    for (int i = 0; i < nrow; ++i) {
-                        Un[rb + i] = y[i];
-                        Wn[rb + i] = w[i];
+            const bool hasb = bsrc != nullptr;
+            for (int rb = tc.r0; rb < tc.r0 + nr; rb += rs) {
+                const int nrow = min(rs, tc.r0 + nr - rb);
+                const unsigned slot = consumed % NS;
+                if (!mbar_wait(&full[slot], (consumed / NS) & 1u, wait_limit)) {
+                    atomicOr(v.err, SWR_ERR_TIMEOUT);
+                    s_fail = 1;
+                }
+                for (int row = warp / wpr; row < rs; row += rstep) {
+                    const float* sh = ring + (size_t)slot * SC + (size_t)row * ld;
+                    const float* sl = sh + (size_t)rs * ld;
+                    float yh = 0.f, yl = 0.f, wh = 0.f, wl = 0.f;
+                    if (row < nrow) {
+                        for (int c = (part * 32 + lane) * 4; c < ld; c += 128 * wpr) {
+                            const float4 g0 = *reinterpret_cast<const float4*>(sh + c);
+                            const float4 g1 = *reinterpret_cast<const float4*>(sl + c);
+                            const float4 xa = *reinterpret_cast<const float4*>(vf + c);
+                            const float4 xb = *reinterpret_cast<const float4*>(vf + c + 2);
+                            df32_acc(yh, yl, g0.x, g1.x, xa.x, xa.y);
+                            df32_acc(yh, yl, g0.y, g1.y, xa.z, xa.w);
+                            df32_acc(yh, yl, g0.z, g1.z, xb.x, xb.y);
+                            df32_acc(yh, yl, g0.w, g1.w, xb.z, xb.w);
+                            if (hasb) {
+                                const float4 ba = *reinterpret_cast<const float4*>(bf + c);
+                                const float4 bb = *reinterpret_cast<const float4*>(bf + c + 2);
+                                df32_acc(wh, wl, g0.x, g1.x, ba.x, ba.y);
+                                df32_acc(wh, wl, g0.y, g1.y, ba.z, ba.w);
+                                df32_acc(wh, wl, g0.z, g1.z, bb.x, bb.y);
+                                df32_acc(wh, wl, g0.w, g1.w, bb.z, bb.w);
+                            }
+                        }
                     }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        float s2, e2;
+                        float oh = __shfl_xor_sync(0xffffffffu, yh, o), ol = __shfl_xor_sync(0xffffffffu, yl, o);
+                        two_sum(yh, oh, s2, e2);
+                        yh = s2;
+                        yl = yl + ol + e2;
+                        oh = __shfl_xor_sync(0xffffffffu, wh, o);
+                        ol = __shfl_xor_sync(0xffffffffu, wl, o);
+                        two_sum(wh, oh, s2, e2);
+                        wh = s2;
+                        wl = wl + ol + e2;
+                    }
+                    if (lane == 0) sred[consumed & 1][row * wpr + part] = make_float4(yh, yl, wh, wl);
+                }
+                ++consumed;
+                __syncthreads();  // the slot is free, the row partials are complete
+                if (s_fail) {
+                    drain();
+                    return;
+                }
+                if (tid == 0) produce(m);
+                if (warp == 1 && lane < nrow) {  // warp 0 issues the copies meanwhile
+                    double y = 0, w = 0;
+                    for (int p = 0; p < wpr; ++p) {
+                        const float4 qv = sred[(consumed - 1) & 1][lane * wpr + p];
+                        y += (double)qv.x + (double)qv.y;
+                        w += (double)qv.z + (double)qv.w;
+                    }
+                    Un[rb + lane] = y;
+                    Wn[rb + lane] = w;
                 }
             }
         }
+        if (tid == 0) flush_append();
         __syncthreads();
         target += gridDim.x;
         ++gen;
-        if (!reduce_barrier_sd(&A.bar->count, &A.bar->gen, target, gen, A.part_s, A.part_d, A.inst_task0, ni,
-                               A.sums_s, A.sums_d, v.inst, A.scal_inst + (m & 1) * 2 * ni, v.err, A.spin_limit, red,
-                               A.n_active, &go))
+        const bool ok = reduce_barrier_sd(&A.bar->count, &A.bar->gen, target, gen, A.part_s, A.part_d, A.inst_task0,
+                                          ni, A.sums_s, A.sums_d, v.inst, A.scal_inst + (m & 1) * 2 * ni, v.err,
+                                          A.spin_limit, red, A.n_active, &go, q, m & 1);
+        if (!ok || !go) {
+            drain();
             return;
-        if (!go) return;
+        }
     }
 }
 
@@ -1234,6 +1401,8 @@ __global__ void k_window_reset(SweepArgs A, int n_inst) {
         A.bar->count = 0;
         A.bar->gen = 0;
         *A.n_active = n_inst;
+        A.q->claim[0] = A.q->claim[1] = 0;
+        A.q->count[0] = A.q->count[1] = 0;
     }
 }
 
@@ -1319,9 +1488,11 @@ size_t window_smem(int kmax, int kdmax, int rows_max, int tasks_in_smem, long lo
            (size_t)g_resident_floats * sizeof(float);
 }
 
-size_t window_smem_split(int kmax, int kdmax, int rows_max) {
-    return (3 * (size_t)df32_ld(kmax) + (size_t)rows_max + 2 * (size_t)kdmax + 2 * (size_t)kdmax * kdmax) *
-           sizeof(double);
+size_t window_smem_split(int kmax, int kdmax, int rows_max, int stage_floats, int n_stages) {
+    return (((3 * (size_t)df32_ld(kmax) + (size_t)rows_max + 2 * (size_t)kdmax + 2 * (size_t)kdmax * kdmax + 15) &
+             ~(size_t)15) *
+            sizeof(double)) +
+           (size_t)n_stages * stage_floats * sizeof(float);
 }
 
 int window_tasks_per_cta_max() { return WIN_TPC; }
