@@ -1063,19 +1063,136 @@ __device__ bool reduce_barrier_sd(unsigned* count, unsigned* release, unsigned t
         s_go = (int)(w & 1u);
         __threadfence();
     }
+    if (threadIdx.x == 0 && *(volatile int*)err) s_ok = 0;  // one verdict for the whole CTA
     __syncthreads();
     *go_out = s_go;
-    return s_ok != 0 && *(volatile int*)err == 0;
+    return s_ok != 0;
+}
+
+// Consumer-group barrier of the split window: warps 1..7 (named barrier 1).
+__device__ inline void split_cbar() { asm volatile("bar.sync 1, %0;" ::"n"(WIN_THREADS - 32) : "memory"); }
+
+// Consumer-group barrier that also ORs x over the group (the same result in
+// every consumer thread).
+__device__ inline int split_cbar_or(int x) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(x), "n"(WIN_THREADS - 32)
+        : "memory");
+    return r;
+}
+
+__device__ inline void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Rows [r0, r0+nr) of z = (P1 (x) P2) y (N = 2) or P1 y (N = 1) by the consumer
+// group (threads ct = 0..CT-1): the factors are staged in shared memory (Ps),
+// then every thread computes whole outputs of the two small products
+//   tmp[bb][c] = sum_e Y[c][e] P2[b0+bb][e],   z[(a,b)] = sum_c P1[a][c] tmp[b-b0][c].
+__device__ void z_rows_group(const TaskCache& tc, const double* P1g, const double* P2g, const double* ys, double* z,
+                             double* tmp, double* Ps, int ct, int CT) {
+    const int kd = tc.kd, r0 = tc.r0, r1 = tc.r0 + tc.nr, kk = kd * kd;
+    double* P1 = Ps;
+    double* P2 = Ps + kk;
+    for (int e = ct; e < kk; e += CT) {
+        P1[e] = P1g[e];
+        if (tc.N == 2) P2[e] = P2g[e];
+    }
+    split_cbar();
+    if (tc.N == 1) {
+        for (int r = r0 + ct; r < r1; r += CT) {
+            double acc = 0;
+            for (int c = 0; c < kd; ++c) acc = fma(P1[r * kd + c], ys[c], acc);
+            z[r - r0] = acc;
+        }
+        split_cbar();
+        return;
+    }
+    const int b0 = r0 / kd, b1 = (r1 - 1) / kd, nb = b1 - b0 + 1;
+    for (int item = ct; item < nb * kd; item += CT) {
+        const int bb = item / kd, c = item - bb * kd;
+        const double* p2 = P2 + (b0 + bb) * kd;
+        double acc = 0;
+        for (int e = 0; e < kd; ++e) acc = fma(ys[c + kd * e], p2[e], acc);
+        tmp[item] = acc;
+    }
+    split_cbar();
+    for (int r = r0 + ct; r < r1; r += CT) {
+        const int b = r / kd, a = r - b * kd;
+        const double* p1 = P1 + a * kd;
+        const double* tb = tmp + (b - b0) * kd;
+        double acc = 0;
+        for (int c = 0; c < kd; ++c) acc = fma(p1[c], tb[c], acc);
+        z[r - r0] = acc;
+    }
+    split_cbar();
+}
+
+// One double-single chunk of 4 columns of a staged row into (yh, yl) and,
+// with HASB, (wh, wl).
+template <bool HASB>
+__device__ inline void split_chunk(const float* sh, const float* sl, const float2* vf, const float2* bf, int c,
+                                   float& yh, float& yl, float& wh, float& wl) {
+    const float4 g0 = *reinterpret_cast<const float4*>(sh + c);
+    const float4 g1 = *reinterpret_cast<const float4*>(sl + c);
+    const float4 xa = *reinterpret_cast<const float4*>(vf + c);
+    const float4 xb = *reinterpret_cast<const float4*>(vf + c + 2);
+    df32_acc(yh, yl, g0.x, g1.x, xa.x, xa.y);
+    df32_acc(yh, yl, g0.y, g1.y, xa.z, xa.w);
+    df32_acc(yh, yl, g0.z, g1.z, xb.x, xb.y);
+    df32_acc(yh, yl, g0.w, g1.w, xb.z, xb.w);
+    if (HASB) {
+        const float4 ba = *reinterpret_cast<const float4*>(bf + c);
+        const float4 bb = *reinterpret_cast<const float4*>(bf + c + 2);
+        df32_acc(wh, wl, g0.x, g1.x, ba.x, ba.y);
+        df32_acc(wh, wl, g0.y, g1.y, ba.z, ba.w);
+        df32_acc(wh, wl, g0.z, g1.z, bb.x, bb.y);
+        df32_acc(wh, wl, g0.w, g1.w, bb.z, bb.w);
+    }
+}
+
+// (h, l) += (oh, ol) in double-single.
+__device__ inline void ds_add(float& h, float& l, float oh, float ol) {
+    float s, e;
+    two_sum(h, oh, s, e);
+    h = s;
+    l = l + ol + e;
+}
+
+// One staged row by one warp: lanes over groups of 4 columns, two accumulator
+// pairs per product (alternate column groups), shuffle sum; the row's values of
+// G y and G b to all lanes.
+template <bool HASB>
+__device__ inline void split_row(const float* sh, const float* sl, const float2* vf, const float2* bf, int ld,
+                                 int lane, double& y, double& w) {
+    float yh0 = 0.f, yl0 = 0.f, wh0 = 0.f, wl0 = 0.f, yh1 = 0.f, yl1 = 0.f, wh1 = 0.f, wl1 = 0.f;
+    int c = lane * 4;
+    for (; c + 128 < ld; c += 256) {
+        split_chunk<HASB>(sh, sl, vf, bf, c, yh0, yl0, wh0, wl0);
+        split_chunk<HASB>(sh, sl, vf, bf, c + 128, yh1, yl1, wh1, wl1);
+    }
+    if (c < ld) split_chunk<HASB>(sh, sl, vf, bf, c, yh0, yl0, wh0, wl0);
+    ds_add(yh0, yl0, yh1, yl1);
+    if (HASB) ds_add(wh0, wl0, wh1, wl1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ds_add(yh0, yl0, __shfl_xor_sync(0xffffffffu, yh0, o), __shfl_xor_sync(0xffffffffu, yl0, o));
+        if (HASB) ds_add(wh0, wl0, __shfl_xor_sync(0xffffffffu, wh0, o), __shfl_xor_sync(0xffffffffu, wl0, o));
+    }
+    y = (double)yh0 + (double)yl0;
+    w = HASB ? (double)wh0 + (double)wl0 : 0.0;
 }
 
 __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
     extern __shared__ double sm[];
     __shared__ double red[33];
-    __shared__ __align__(8) unsigned long long full[SPLIT_NS_MAX];
-    __shared__ float4 sred[2][32];
+    __shared__ __align__(8) unsigned long long full[SPLIT_NS_MAX], empty[SPLIT_NS_MAX];
+    __shared__ __align__(8) unsigned long long ff[SPLIT_FIFO], fe[SPLIT_FIFO];
     __shared__ int fifo[SPLIT_FIFO];
     __shared__ int cbuf[SPLIT_CLAIM_MAX];
-    __shared__ int s_fail;
     int go = 1;
     const SwrDeviceView& v = A.v;
     const int cap = A.cap, ni = v.n_inst, SC = A.stage_floats, nt = A.n_tasks;
@@ -1087,302 +1204,244 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
     double* tmp = sm + 3 * kmax;
     double* Ps = tmp + A.rows_max + 2 * kdmax;
     float* ring = (float*)(sm + ((3 * kmax + A.rows_max + 2 * kdmax + 2 * kdmax * kdmax + 15) & ~15));
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = WIN_THREADS / 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NCW = WIN_THREADS / 32 - 1, CT = WIN_THREADS - 32;  // consumer warps, threads
     const long long wait_limit = A.spin_limit >> 4;
     SplitQueue* q = A.q;
     unsigned target = 0, gen = 0;
-    unsigned consumed = 0;  // stages consumed (every thread)
-    int fhead = 0;          // task entries taken from the FIFO (every thread)
-    // thread 0: producer state
-    unsigned issued = 0;                               // stages issued
-    int ftail = 0;                                     // task entries pushed
-    bool p_has = false, p_done = false;                // a task with stages left to issue; step's list exhausted
-    int prb = 0, p_end = 0, p_ld = 0, p_rs = 0;        // its next row, end row, row stride, rows per stage
-    const float* p_gh = nullptr;                       // its G_hi plane (G_lo follows after p_plane floats)
-    long long p_plane = 0;
-    int c_next = 0, c_end = 0;                         // claimed list positions not yet taken (task ids in cbuf)
-    unsigned c_hint = 0;                               // end of the last claim (estimate of the list handed out)
-    unsigned a_pos = 0;                                // pending append: list position (from the atomic)
-    int a_t = -1, a_par = 0;                           // pending append: task, list parity
+    bool failed = false;  // a bounded wait gave up: the rest of the window skips its waits
+    // producer (warp 0, lane 0)
+    unsigned issued = 0, pushed = 0;
+    int c_next = 0, c_end = 0;
+    unsigned c_hint = 0;
+    // consumers (warps 1..7)
+    unsigned taken = 0, used = 0;  // FIFO entries taken, stages used
     auto own = [&](const TaskCache& tc, int slot) -> double* { return A.g_own + tc.own + (long long)slot * tc.nr; };
-
-    // Thread 0: the next task id of step m from the list (guided chunks of at most
-    // SPLIT_CLAIM_MAX positions, smaller as the list runs out), -1 at its end.
-    auto next_task = [&](int m) -> int {
-        if (c_next == c_end) {
-            const unsigned n = m == 0 ? (unsigned)nt : __ldcg(&q->count[m & 1]);
-            unsigned b = c_hint < n ? (n - c_hint) / (2u * gridDim.x) : 1u;
-            b = b < 1u ? 1u : (b > SPLIT_CLAIM_MAX ? SPLIT_CLAIM_MAX : b);
-            const unsigned i = atomicAdd(&q->claim[m & 1], b);
-            c_hint = i + b;
-            if (i >= n) return -1;
-            const unsigned e = i + b < n ? i + b : n;
-            for (unsigned k = i; k < e; ++k)
-                cbuf[k - i] = m == 0 ? (int)k : __ldcg(A.q_list + (size_t)(m & 1) * nt + k);
-            c_next = 0;
-            c_end = (int)(e - i);
+    auto wait = [&](unsigned long long* bar, unsigned par) {
+        if (failed) return;
+        if (!mbar_wait(bar, par, wait_limit)) {
+            atomicOr(v.err, SWR_ERR_TIMEOUT);
+            failed = true;
         }
-        return cbuf[c_next++];
-    };
-    auto flush_append = [&]() {
-        if (a_t >= 0) A.q_list[(size_t)a_par * nt + a_pos] = a_t;
-        a_t = -1;
-    };
-    // Thread 0: issue stages while ring slots are free; claim, decide and queue
-    // tasks while the FIFO has room (and the ring is not full with queued work).
-    auto produce = [&](int m) {
-        const double* sc1 = A.scal_inst + ((m - 1) & 1) * 2 * ni;
-        for (;;) {
-            if (p_has) {
-                if (issued - consumed >= NS) return;
-                const int nrow = min(p_rs, p_end - prb);
-                const unsigned slot = issued % NS, bytes = (unsigned)nrow * p_ld * 4u;
-                const float* Gh = p_gh + (long long)prb * p_ld;
-                float* dst = ring + (size_t)slot * SC;
-                const unsigned mb = smem_u32(&full[slot]);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(2u * bytes)
-                             : "memory");
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(dst)),
-                    "l"(Gh), "r"(bytes), "r"(mb)
-                    : "memory");
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(dst + p_rs * p_ld)),
-                    "l"(Gh + p_plane), "r"(bytes), "r"(mb)
-                    : "memory");
-                ++issued;
-                prb += p_rs;
-                if (prb >= p_end) p_has = false;
-                continue;
-            }
-            if (p_done || ftail - fhead >= SPLIT_FIFO) return;
-            if (ftail > fhead && issued - consumed >= NS) return;
-            const int t = next_task(m);
-            if (t < 0) {
-                fifo[ftail % SPLIT_FIFO] = -1;
-                ++ftail;
-                p_done = true;
-                return;
-            }
-            const TaskCache tc = make_task_cache(A, t);
-            if (m >= 1) {
-                // the plain algorithm's stop at n = m-2 (D_{m-2}), else at n = m-1
-                // (cap, or s_{m-1} not positive and finite)
-                const double s1 = __ldcg(sc1 + tc.inst);
-                int stop = 0, win = 0, bad = 0;
-                if (m >= 3 && tc.ngf_stop && sqrt(fmax(__ldcg(A.sums_d + tc.inst), 0.0)) <= tc.ngf_tol) {
-                    stop = 1;
-                    win = m - 2;
-                } else if (m - 1 >= tc.maxs || !isfinite(s1) || s1 <= 0.0) {
-                    stop = 1;
-                    win = m - 1;
-                    bad = !isfinite(s1) || s1 <= 0.0;
-                }
-                if (tc.first) A.snorm[(long long)tc.inst * (cap + 1) + m - 1] = s1;
-                if (stop) {
-                    if (tc.first) {
-                        A.win[tc.inst] = win;
-                        if (bad) atomicOr(v.err, SWR_ERR_NUMERIC);
-                        __threadfence();
-                        atomicSub(A.n_active, 1);
-                    }
-                    continue;
-                }
-            }
-            // still stepping after the decisions of step m: a member of step m+1's list
-            // (the list entry is stored at the next append or at the end of the step,
-            // so that the atomic's round trip overlaps other work)
-            flush_append();
-            a_par = (m + 1) & 1;
-            a_pos = atomicAdd(&q->count[a_par], 1u);
-            a_t = t;
-            const bool str = m < tc.maxs;
-            fifo[ftail % SPLIT_FIFO] = 2 * t + (str ? 1 : 0);
-            ++ftail;
-            if (str) {
-                p_has = true;
-                prb = tc.r0;
-                p_end = tc.r0 + tc.nr;
-                p_ld = df32_ld(tc.K);
-                p_rs = split_stage_rows(p_ld, SC);
-                p_gh = (const float*)(v.arena + tc.Gf);
-                p_plane = (long long)tc.K * p_ld;
-            }
-        }
-    };
-    // Thread 0: wait (bounded) for every stage still in flight before the CTA ends.
-    auto drain = [&]() {
-        if (tid == 0) {
-            for (; consumed < issued; ++consumed)
-                if (!mbar_wait(&full[consumed % NS], (consumed / NS) & 1u, wait_limit)) {
-                    atomicOr(v.err, SWR_ERR_TIMEOUT);
-                    break;
-                }
-        }
-        __syncthreads();
     };
 
     if (tid == 0) {
-        for (unsigned i = 0; i < NS; ++i)
+        for (unsigned i = 0; i < NS; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(NCW) : "memory");
+        }
+        for (int i = 0; i < SPLIT_FIFO; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ff[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fe[i])) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_fail = 0;
     }
+    __syncthreads();
 
     for (int m = 0;; ++m) {
         const double* sc1 = A.scal_inst + ((m - 1) & 1) * 2 * ni;  // s_{m-1}, 1/s_{m-1}
         const double* sc2 = A.scal_inst + ((m - 2) & 1) * 2 * ni;  // s_{m-2}, 1/s_{m-2}
-        c_next = c_end = 0;
-        c_hint = 0;
-        p_done = false;
-        for (;;) {
-            __syncthreads();
-            if (tid == 0) produce(m);
-            __syncthreads();
-            const int e = fifo[fhead % SPLIT_FIFO];
-            ++fhead;
-            if (e < 0) break;
-            const int t = e >> 1;
-            const bool str = (e & 1) != 0;
-            const TaskCache tc = make_task_cache(A, t);
-            const int K = tc.K, nr = tc.nr, ld = df32_ld(K);
-            const SubDev& sd = v.sub[tc.sid];
-            const int wp = A.win_prev[tc.inst];
-            const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(m + 1, wp) * K : nullptr;
-            // full y^m = u^m / s_{m-1} + w^m (y^0 = c0), and kappa dt b'^{m+1}
-            const double is1 = m >= 1 ? __ldcg(sc1 + ni + tc.inst) : 1.0;
-            const double is2 = m >= 2 ? __ldcg(sc2 + ni + tc.inst) : 1.0;
-            {
-                const double* U = v.arena + sd.work + (long long)(m & 1) * 2 * K;
-                const double* Wv = U + K;
-                const double* c0 = v.arena + tc.c0;
-                for (int c = tid; c < ld; c += WIN_THREADS) {
-                    if (c < K) {
-                        const double y = m == 0 ? c0[c] : __ldcg(U + c) * is1 + __ldcg(Wv + c);
-                        vs[c] = y;
-                        vf[c] = ds_split(y);
-                        bf[c] = bsrc ? ds_split(tc.kdt * bsrc[c]) : make_float2(0.f, 0.f);
-                    } else {
-                        vf[c] = make_float2(0.f, 0.f);
-                        bf[c] = make_float2(0.f, 0.f);
+        if (warp == 0) {
+            if (lane == 0) {
+                // ------------------------------------------------ producer
+                auto push = [&](int val) {
+                    const unsigned s = pushed % SPLIT_FIFO;
+                    if (pushed >= SPLIT_FIFO) wait(&fe[s], (pushed / SPLIT_FIFO - 1) & 1u);
+                    fifo[s] = val;
+                    mbar_arrive(&ff[s]);
+                    ++pushed;
+                };
+                c_next = c_end = 0;
+                c_hint = 0;
+                unsigned a_pos = 0;
+                int a_t = -1, a_par = 0;
+                for (;;) {
+                    // next task of step m: guided chunks of the step's list
+                    if (c_next == c_end) {
+                        const unsigned n = m == 0 ? (unsigned)nt : __ldcg(&q->count[m & 1]);
+                        unsigned b = c_hint < n ? (n - c_hint) / (2u * gridDim.x) : 1u;
+                        b = b < 1u ? 1u : (b > SPLIT_CLAIM_MAX ? SPLIT_CLAIM_MAX : b);
+                        const unsigned i = atomicAdd(&q->claim[m & 1], b);
+                        c_hint = i + b;
+                        if (i >= n) break;
+                        const unsigned e = i + b < n ? i + b : n;
+                        for (unsigned k = i; k < e; ++k)
+                            cbuf[k - i] = m == 0 ? (int)k : __ldcg(A.q_list + (size_t)(m & 1) * nt + k);
+                        c_next = 0;
+                        c_end = (int)(e - i);
                     }
-                }
-            }
-            __syncthreads();
-            double* ym = own(tc, m % 3);
-            double* hrow = v.arena + tc.hist + (long long)m * K;
-            for (int r = tid; r < nr; r += WIN_THREADS) {
-                ym[r] = vs[tc.r0 + r];
-                hrow[tc.r0 + r] = vs[tc.r0 + r];
-            }
-            double* zm = own(tc, 3 + m % 3);
-            z_rows_staged(tc, v.arena + tc.p1, v.arena + tc.p2, vs, zm, tmp, Ps);
-            // partials: s_m^2 (own rows of y^m . z^m) and D_{m-1}
-            {
-                const bool dn = m >= 2 && tc.ngf_stop;
-                const double* y1 = own(tc, (m + 2) % 3);
-                const double* y2 = own(tc, (m + 1) % 3);
-                const double* z1 = own(tc, 3 + (m + 2) % 3);
-                const double* z2 = own(tc, 3 + (m + 1) % 3);
-                double acc = 0, accd = 0;
-                for (int r = tid; r < nr; r += WIN_THREADS) {
-                    acc += ym[r] * zm[r];
-                    if (dn) accd += (y1[r] * is1 - y2[r] * is2) * (z1[r] * is1 - z2[r] * is2);
-                }
-                acc = warp_sum(acc);
-                accd = warp_sum(accd);
-                if (lane == 0) {
-                    red[warp] = acc;
-                    red[16 + warp] = accd;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    double a = 0, b = 0;
-                    for (int i = 0; i < nw; ++i) {
-                        a += red[i];
-                        b += red[16 + i];
-                    }
-                    A.part_s[t] = a;
-                    if (dn) A.part_d[t] = b;
-                }
-            }
-            if (!str) continue;
-            // rows of u^{m+1} = G y^m and w^{m+1} = G (kappa dt b'^{m+1}) from the staged
-            // rows: rs rows per stage; up to 8 rows, 8 / rs warps per row (lanes over
-            // groups of 4 columns), beyond, one warp per row
-            const int rs = split_stage_rows(ld, SC), wpr = rs >= nw ? 1 : nw / rs;
-            const int part = warp % wpr, rstep = nw / wpr;
-            double* Un = v.arena + sd.work + (long long)((m + 1) & 1) * 2 * K;
-            double* Wn = Un + K;
-            const bool hasb = bsrc != nullptr;
-            for (int rb = tc.r0; rb < tc.r0 + nr; rb += rs) {
-                const int nrow = min(rs, tc.r0 + nr - rb);
-                const unsigned slot = consumed % NS;
-                if (!mbar_wait(&full[slot], (consumed / NS) & 1u, wait_limit)) {
-                    atomicOr(v.err, SWR_ERR_TIMEOUT);
-                    s_fail = 1;
-                }
-                for (int row = warp / wpr; row < rs; row += rstep) {
-                    const float* sh = ring + (size_t)slot * SC + (size_t)row * ld;
-                    const float* sl = sh + (size_t)rs * ld;
-                    float yh = 0.f, yl = 0.f, wh = 0.f, wl = 0.f;
-                    if (row < nrow) {
-                        for (int c = (part * 32 + lane) * 4; c < ld; c += 128 * wpr) {
-                            const float4 g0 = *reinterpret_cast<const float4*>(sh + c);
-                            const float4 g1 = *reinterpret_cast<const float4*>(sl + c);
-                            const float4 xa = *reinterpret_cast<const float4*>(vf + c);
-                            const float4 xb = *reinterpret_cast<const float4*>(vf + c + 2);
-                            df32_acc(yh, yl, g0.x, g1.x, xa.x, xa.y);
-                            df32_acc(yh, yl, g0.y, g1.y, xa.z, xa.w);
-                            df32_acc(yh, yl, g0.z, g1.z, xb.x, xb.y);
-                            df32_acc(yh, yl, g0.w, g1.w, xb.z, xb.w);
-                            if (hasb) {
-                                const float4 ba = *reinterpret_cast<const float4*>(bf + c);
-                                const float4 bb = *reinterpret_cast<const float4*>(bf + c + 2);
-                                df32_acc(wh, wl, g0.x, g1.x, ba.x, ba.y);
-                                df32_acc(wh, wl, g0.y, g1.y, ba.z, ba.w);
-                                df32_acc(wh, wl, g0.z, g1.z, bb.x, bb.y);
-                                df32_acc(wh, wl, g0.w, g1.w, bb.z, bb.w);
+                    const int t = cbuf[c_next++];
+                    const TaskCache tc = make_task_cache(A, t);
+                    if (m >= 1) {
+                        // the plain algorithm's stop at n = m-2 (D_{m-2}), else at n = m-1
+                        // (cap, or s_{m-1} not positive and finite)
+                        const double s1 = __ldcg(sc1 + tc.inst);
+                        int stop = 0, win = 0, bad = 0;
+                        if (m >= 3 && tc.ngf_stop && sqrt(fmax(__ldcg(A.sums_d + tc.inst), 0.0)) <= tc.ngf_tol) {
+                            stop = 1;
+                            win = m - 2;
+                        } else if (m - 1 >= tc.maxs || !isfinite(s1) || s1 <= 0.0) {
+                            stop = 1;
+                            win = m - 1;
+                            bad = !isfinite(s1) || s1 <= 0.0;
+                        }
+                        if (tc.first) A.snorm[(long long)tc.inst * (cap + 1) + m - 1] = s1;
+                        if (stop) {
+                            if (tc.first) {
+                                A.win[tc.inst] = win;
+                                if (bad) atomicOr(v.err, SWR_ERR_NUMERIC);
+                                __threadfence();
+                                atomicSub(A.n_active, 1);
                             }
+                            continue;
                         }
                     }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        float s2, e2;
-                        float oh = __shfl_xor_sync(0xffffffffu, yh, o), ol = __shfl_xor_sync(0xffffffffu, yl, o);
-                        two_sum(yh, oh, s2, e2);
-                        yh = s2;
-                        yl = yl + ol + e2;
-                        oh = __shfl_xor_sync(0xffffffffu, wh, o);
-                        ol = __shfl_xor_sync(0xffffffffu, wl, o);
-                        two_sum(wh, oh, s2, e2);
-                        wh = s2;
-                        wl = wl + ol + e2;
+                    // still stepping after the decisions of step m: a member of step
+                    // m+1's list (the entry is stored one append later, or at the end
+                    // of the step, so that the atomic's round trip overlaps other work)
+                    if (a_t >= 0) A.q_list[(size_t)a_par * nt + a_pos] = a_t;
+                    a_par = (m + 1) & 1;
+                    a_pos = atomicAdd(&q->count[a_par], 1u);
+                    a_t = t;
+                    const bool str = m < tc.maxs;
+                    push(2 * t + (str ? 1 : 0));
+                    if (!str) continue;
+                    // the task's stages: rows [rb, rb + rs) of both planes per stage
+                    const int ld = df32_ld(tc.K), rs = split_stage_rows(ld, SC);
+                    const float* Gh = (const float*)(v.arena + tc.Gf);
+                    const long long plane = (long long)tc.K * ld;
+                    for (int rb = tc.r0; rb < tc.r0 + tc.nr; rb += rs) {
+                        const unsigned s = issued % NS;
+                        if (issued >= NS) wait(&empty[s], (issued / NS - 1) & 1u);
+                        const int nrow = min(rs, tc.r0 + tc.nr - rb);
+                        const unsigned bytes = (unsigned)nrow * ld * 4u, mb = smem_u32(&full[s]);
+                        float* dst = ring + (size_t)s * SC;
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+                                     "r"(2u * bytes)
+                                     : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                            "[%3];" ::"r"(smem_u32(dst)),
+                            "l"(Gh + (long long)rb * ld), "r"(bytes), "r"(mb)
+                            : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                            "[%3];" ::"r"(smem_u32(dst + rs * ld)),
+                            "l"(Gh + plane + (long long)rb * ld), "r"(bytes), "r"(mb)
+                            : "memory");
+                        ++issued;
                     }
-                    if (lane == 0) sred[consumed & 1][row * wpr + part] = make_float4(yh, yl, wh, wl);
                 }
-                ++consumed;
-                __syncthreads();  // the slot is free, the row partials are complete
-                if (s_fail) {
-                    drain();
-                    return;
-                }
-                if (tid == 0) produce(m);
-                if (warp == 1 && lane < nrow) {  // warp 0 issues the copies meanwhile
-                    double y = 0, w = 0;
-                    for (int p = 0; p < wpr; ++p) {
-                        const float4 qv = sred[(consumed - 1) & 1][lane * wpr + p];
-                        y += (double)qv.x + (double)qv.y;
-                        w += (double)qv.z + (double)qv.w;
+                if (a_t >= 0) A.q_list[(size_t)a_par * nt + a_pos] = a_t;
+                push(-1);  // end of the step's tasks
+            }
+            __syncwarp();
+        } else {
+            // ------------------------------------------------ consumers
+            const int ct = tid - 32, cw = warp - 1;
+            for (;;) {
+                const unsigned fs = taken % SPLIT_FIFO;
+                wait(&ff[fs], (taken / SPLIT_FIFO) & 1u);
+                // every consumer has the entry and the previous task's rows are done; a
+                // wait that gave up anywhere in the group ends the step for all of it
+                const int e = split_cbar_or(failed ? 1 : 0) ? -1 : fifo[fs];
+                ++taken;
+                split_cbar();
+                if (ct == 0) mbar_arrive(&fe[fs]);
+                if (e < 0) break;
+                const int t = e >> 1;
+                const bool str = (e & 1) != 0;
+                const TaskCache tc = make_task_cache(A, t);
+                const int K = tc.K, nr = tc.nr, ld = df32_ld(K);
+                const SubDev& sd = v.sub[tc.sid];
+                const int wp = A.win_prev[tc.inst];
+                const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(m + 1, wp) * K : nullptr;
+                // full y^m = u^m / s_{m-1} + w^m (y^0 = c0), and kappa dt b'^{m+1}
+                const double is1 = m >= 1 ? __ldcg(sc1 + ni + tc.inst) : 1.0;
+                const double is2 = m >= 2 ? __ldcg(sc2 + ni + tc.inst) : 1.0;
+                {
+                    const double* U = v.arena + sd.work + (long long)(m & 1) * 2 * K;
+                    const double* Wv = U + K;
+                    const double* c0 = v.arena + tc.c0;
+                    for (int c = ct; c < ld; c += CT) {
+                        if (c < K) {
+                            const double y = m == 0 ? c0[c] : __ldcg(U + c) * is1 + __ldcg(Wv + c);
+                            vs[c] = y;
+                            vf[c] = ds_split(y);
+                            bf[c] = bsrc ? ds_split(tc.kdt * bsrc[c]) : make_float2(0.f, 0.f);
+                        } else {
+                            vf[c] = make_float2(0.f, 0.f);
+                            bf[c] = make_float2(0.f, 0.f);
+                        }
                     }
-                    Un[rb + lane] = y;
-                    Wn[rb + lane] = w;
+                }
+                split_cbar();
+                double* ym = own(tc, m % 3);
+                double* hrow = v.arena + tc.hist + (long long)m * K;
+                for (int r = ct; r < nr; r += CT) {
+                    ym[r] = vs[tc.r0 + r];
+                    hrow[tc.r0 + r] = vs[tc.r0 + r];
+                }
+                double* zm = own(tc, 3 + m % 3);
+                z_rows_group(tc, v.arena + tc.p1, v.arena + tc.p2, vs, zm, tmp, Ps, ct, CT);
+                // partials: s_m^2 (own rows of y^m . z^m) and D_{m-1}
+                {
+                    const bool dn = m >= 2 && tc.ngf_stop;
+                    const double* y1 = own(tc, (m + 2) % 3);
+                    const double* y2 = own(tc, (m + 1) % 3);
+                    const double* z1 = own(tc, 3 + (m + 2) % 3);
+                    const double* z2 = own(tc, 3 + (m + 1) % 3);
+                    double acc = 0, accd = 0;
+                    for (int r = ct; r < nr; r += CT) {
+                        acc += ym[r] * zm[r];
+                        if (dn) accd += (y1[r] * is1 - y2[r] * is2) * (z1[r] * is1 - z2[r] * is2);
+                    }
+                    acc = warp_sum(acc);
+                    accd = warp_sum(accd);
+                    if (lane == 0) {
+                        red[warp] = acc;
+                        red[16 + warp] = accd;
+                    }
+                    split_cbar();
+                    if (ct == 0) {
+                        double a = 0, b = 0;
+                        for (int i = 1; i <= NCW; ++i) {
+                            a += red[i];
+                            b += red[16 + i];
+                        }
+                        A.part_s[t] = a;
+                        if (dn) A.part_d[t] = b;
+                    }
+                }
+                if (!str) continue;
+                // rows of u^{m+1} = G y^m and w^{m+1} = G (kappa dt b'^{m+1}) from the
+                // staged rows: row r0 + o of the task to consumer warp o mod 7, whole
+                // rows per warp, no block barrier between stages
+                const int rs = split_stage_rows(ld, SC);
+                double* Un = v.arena + sd.work + (long long)((m + 1) & 1) * 2 * K;
+                double* Wn = Un + K;
+                const bool hasb = bsrc != nullptr;
+                for (int rb = tc.r0; rb < tc.r0 + nr; rb += rs) {
+                    const int nrow = min(rs, tc.r0 + nr - rb);
+                    const unsigned s = used % NS;
+                    wait(&full[s], (used / NS) & 1u);
+                    const float* stage = ring + (size_t)s * SC;
+                    int r = ((cw - (rb - tc.r0)) % NCW + NCW) % NCW;
+                    for (; r < nrow; r += NCW) {
+                        double y, w;
+                        if (hasb) split_row<true>(stage + (size_t)r * ld, stage + (size_t)(rs + r) * ld, vf, bf, ld, lane, y, w);
+                        else split_row<false>(stage + (size_t)r * ld, stage + (size_t)(rs + r) * ld, vf, bf, ld, lane, y, w);
+                        if (lane == 0) {
+                            Un[rb + r] = y;
+                            Wn[rb + r] = w;
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                    ++used;
                 }
             }
         }
-        if (tid == 0) flush_append();
         __syncthreads();
         target += gridDim.x;
         ++gen;
@@ -1390,7 +1449,13 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                                           ni, A.sums_s, A.sums_d, v.inst, A.scal_inst + (m & 1) * 2 * ni, v.err,
                                           A.spin_limit, red, A.n_active, &go, q, m & 1);
         if (!ok || !go) {
-            drain();
+            // every stage issued has been consumed (each step's list ends with its
+            // stages), except after a wait that gave up: the producer waits
+            // (bounded) for the last copy into each slot before the CTA ends
+            if (tid == 0)
+                for (unsigned i = issued > NS ? issued - NS : 0; i < issued; ++i)
+                    mbar_wait(&full[i % NS], (i / NS) & 1u, wait_limit);
+            __syncthreads();
             return;
         }
     }
