@@ -47,14 +47,16 @@ KERNEL_FUNCS = {
     "k_window_2ph<true>": ["reduce_barrier", "two_sum", "make_task_cache", "z_rows_sm", "z_rows_staged",
                            "prefetch_l2", "prefetch_rows", "df32_acc", "df32_rows4", "k_window_2ph"],
 }
-KERNEL_FUNCS["k_window_split"] = ["mbar_wait", "split_stage_rows", "reduce_barrier_sd", "two_sum", "make_task_cache",
-                                  "z_rows_staged", "df32_acc", "k_window_split"]
+KERNEL_FUNCS["k_window_split"] = ["mbar_wait", "split_stage_rows", "reduce_barrier_sd", "split_cbar", "split_cbar_or",
+                                  "mbar_arrive", "z_rows_group", "split_chunk", "ds_add", "split_row", "two_sum",
+                                  "make_task_cache", "df32_acc", "k_window_split"]
 KERNEL_FUNCS["k_window_2ph<true>@batched"] = KERNEL_FUNCS["k_window_2ph<true>"]
 KERNEL_FUNCS["k_window_split@batched"] = KERNEL_FUNCS["k_window_split"]
 PROFILED_TRAFFIC = {
     "k_window_fused": ("123b4a784de2ee96", 329.5e6, "profiles/k_window_fused_tise_2e_16sd.md"),
     "k_window_2ph<false>": ("654a871bbf4d80e1", 278.7e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
     "k_window_2ph<true>@batched": ("132abcba8871d5ad", 1.196, "profiles/k_window_2ph_df32_batched_uneven.md"),
+    "k_window_split@batched": ("27a126d6e8f6a859", 1.033, "profiles/k_window_split_batched_uneven.md"),
 }
 
 

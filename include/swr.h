@@ -78,8 +78,8 @@ typedef enum swr_launch_mode {
  * compute the same step; they differ in how the per-step normalisation is
  * synchronised, and so in summation order (results agree to rounding).      */
 typedef enum swr_window_variant {
-    SWR_WINDOW_AUTO = 0,       /* fused when it fits (mixed precision), else
-                                  two-phase                                      */
+    SWR_WINDOW_AUTO = 0,       /* mixed precision: fused when it fits, else
+                                  split; FP64: two-phase                         */
     SWR_WINDOW_TWO_PHASE = 1,  /* y = G v, grid barrier, z = (Pp (x) Pp) y, grid
                                   barrier: G read once per step (8 bytes per
                                   element in both precisions); any batch size

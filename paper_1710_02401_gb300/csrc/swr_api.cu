@@ -328,10 +328,12 @@ static bool plan_window(swr_ctx* c, int variant_req, int rows_req, bool have_dev
     const int nsm = c->nsm > 0 ? c->nsm : 152;
     for (int per_sm = 2; per_sm >= 1; --per_sm) {
         plan_tasks(c, rows_req, per_sm * nsm, variant_req == WIN_SPLIT);
+        if (variant_req == 0 && c->df32 && !c->tdse && !c->has_w) plan_tasks(c, rows_req, per_sm * nsm, true);
         const bool fits = c->tasks_per_cta <= window_tasks_per_cta_max() && c->max_rows <= window_rows_per_task_max() &&
                           window_smem(c->max_K, c->max_kd, c->max_rows, c->tasks_per_cta, 0) <= WIN_SMEM_TASKS_MAX;
         int variant = variant_req;
-        if (variant == 0) variant = (c->df32 && c->has_w && fits) ? WIN_FUSED : WIN_TWO_PHASE;
+        if (variant == 0)
+            variant = (c->df32 && c->has_w && fits) ? WIN_FUSED : c->df32 && !c->tdse ? WIN_SPLIT : WIN_TWO_PHASE;
         if (variant == WIN_FUSED && (!c->df32 || !c->has_w || !fits)) return false;
         if (variant == WIN_SPLIT && !c->df32) return false;
         c->variant = variant;
