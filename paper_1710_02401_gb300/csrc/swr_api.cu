@@ -37,7 +37,8 @@ cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_
                           int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
                           double* psi_out, const long long* psi_off, int max_K, int max_kd, int max_q);
 cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const long long* d_boff, const int* d_win_prev,
-                               int n_steps, int iters, int max_K, int max_kd, bool df32, long long* launches);
+                               int n_steps, const unsigned char* h_need, const unsigned char* d_need, int max_K,
+                               int max_kd, bool df32, long long* launches);
 cudaError_t launch_split_c_df32(const SwrDeviceView& v, cudaStream_t st, int max_K);
 }  // namespace swr
 
@@ -69,6 +70,9 @@ struct swr_ctx {
     int cn_iters = 0;
     std::vector<long long> boff;  // real time: per subdomain r, u, x work vectors
     long long* d_boff = nullptr;
+    std::vector<unsigned char> cn_need;  // real time: fixed-point iterations [step][subdomain]
+    std::vector<double> cn_sweeps;       // real time: matvecs with G0 per subdomain over the whole window
+    unsigned char* d_cn_need = nullptr;
     double* d_dipole = nullptr;
     std::vector<double> dipole_h;
     int nsm = 0, bps = 0, tasks_per_cta = 1, max_rows = 0;
@@ -152,11 +156,50 @@ static double cn_contraction(const swr_instance& in) {
 }
 
 // Fixed-point iterations after x0 = G0 r so that rho^(m+1) <= 1e-17.
-static int cn_iterations(const swr_instance& in) {
-    double rho = cn_contraction(in);
+static int cn_iterations_rho(double rho) {
     if (!(rho > 0.0)) return 0;
     int m = (int)ceil(log(1e-17) / log(rho)) - 1;
     return m < 0 ? 0 : m;
+}
+static int cn_iterations(const swr_instance& in) { return cn_iterations_rho(cn_contraction(in)); }
+
+// Length-gauge field e(t) (Sec. 1.2), as the device evaluates it.
+static double cn_field(const swr_instance& in, double t) {
+    if (in.field_E0 == 0.0 || t < 0.0 || t > in.field_T) return 0.0;
+    const double sn = sin(M_PI * t / in.field_T);
+    return in.field_E0 * sn * sn * sin(in.field_omega * t + in.field_phase);
+}
+
+// Fixed-point iterations of step n in subdomain s: the contraction there is
+// at most |theta_{n+1}| ||Q'_s|| (||G0|| <= 1) with theta = dt/2 e(t_{n+1}) and
+// ||Q'_s|| <= max over the subdomain box of |x_1 + ... + x_N| (Q' is the
+// Galerkin matrix of x_1 + ... + x_N in a basis orthonormal on the box), so
+// the same rho^(m+1) <= 1e-17 holds with far fewer iterations where the pulse
+// is weak or the subdomain lies near x_1 + ... + x_N = 0; capped by the
+// a-priori count of the instance.
+static void plan_cn_iterations(swr_ctx* c, int nmax) {
+    const size_t ns = c->sub.size();
+    c->cn_need.assign((size_t)nmax * ns, 0);
+    c->cn_sweeps.assign(ns, 0.0);
+    for (size_t sid = 0; sid < ns; ++sid) {
+        const SubDev& sd = c->sub[sid];
+        const swr_instance& in = c->inst_h[sd.inst];
+        if (in.mode != SWR_MODE_TDSE) continue;
+        double lo = 0, hi = 0;
+        for (int e = 0; e < sd.N; ++e) {
+            lo += sd.lo[e];
+            hi += sd.hi[e];
+        }
+        const double qn = fmax(fabs(lo), fabs(hi));
+        const int cap_m = cn_iterations(in);
+        for (int n = 0; n < in.n_steps && n < nmax; ++n) {
+            const double th = 0.5 * in.dt * fabs(cn_field(in, (n + 1) * in.dt));
+            int m = cn_iterations_rho(th * qn);
+            m = m > cap_m ? cap_m : m;
+            c->cn_need[(size_t)n * ns + sid] = (unsigned char)m;
+            c->cn_sweeps[sid] += 1.0 + m;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ layout
@@ -529,13 +572,16 @@ static void plan(swr_ctx* c) {
     }
     c->arena_doubles = (size_t)off;
     c->psi_total = po;
+    int nmax = 0;
+    for (const InstDev& d : c->inst) nmax = (d.mode == SWR_MODE_TDSE && d.window_cap > nmax) ? d.window_cap : nmax;
+    plan_cn_iterations(c, nmax);
 }
 
 // Auxiliary device arrays carved after the arena (bytes, 256-aligned).
 struct AuxPlan {
     size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, cta0, tc, scal, alive, own,
         ctal, wfix, snorm, sums_s, sums_d,
-        n_active, win, win_prev, bar, queue, qlist, res_part, res, epart, energy, norm2, dipole, boff, psi, psi_off, total;
+        n_active, win, win_prev, bar, queue, qlist, cnneed, res_part, res, epart, energy, norm2, dipole, boff, psi, psi_off, total;
 };
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 static AuxPlan aux_plan(const swr_ctx* c) {
@@ -575,6 +621,7 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.norm2 = o; o = al256(o + ni * sizeof(double));
     a.dipole = o; o = al256(o + ni * sizeof(double));
     a.boff = o; o = al256(o + (c->boff.size() + 1) * sizeof(long long));
+    a.cnneed = o; o = al256(o + c->cn_need.size() + 1);
     a.psi = o; o = al256(o + (size_t)c->psi_total * sizeof(double) * (c->tdse ? 2 : 1));
     a.psi_off = o; o = al256(o + ns * sizeof(long long));
     a.total = o;
@@ -723,6 +770,7 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->d_norm2 = (double*)(b + a.norm2);
     c->d_dipole = (double*)(b + a.dipole);
     c->d_boff = (long long*)(b + a.boff);
+    c->d_cn_need = (unsigned char*)(b + a.cnneed);
     c->d_psi = (double*)(b + a.psi);
     c->d_psi_off = (long long*)(b + a.psi_off);
     // GEMM jobs of the sum-factorised e-e block
@@ -756,6 +804,8 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     CU(cudaMemcpyAsync(c->d_psi_off, c->psi_off.data(), c->psi_off.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
     if (!c->boff.empty())
         CU(cudaMemcpyAsync(c->d_boff, c->boff.data(), c->boff.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream));
+        if (!c->cn_need.empty())
+            CU(cudaMemcpyAsync(c->d_cn_need, c->cn_need.data(), c->cn_need.size(), cudaMemcpyHostToDevice, c->stream));
     c->counters[8] += (double)(c->inst.size() * sizeof(InstDev) + c->sub.size() * (sizeof(SubDev) + 2 * sizeof(GemmJob) + sizeof(long long)));
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
     CU(cudaMemsetAsync(c->d_win_prev, 0, c->inst.size() * sizeof(int), c->stream));
@@ -874,7 +924,8 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
         for (size_t i = 0; i < c->inst.size(); ++i) nmax = c->inst[i].window_cap > nmax ? c->inst[i].window_cap : nmax;
         e = record_event(c->evw0, st);
         if (e == cudaSuccess)
-            e = launch_tdse_window(view(c), st, c->d_boff, c->d_win_prev, nmax, c->cn_iters, c->max_K, c->max_kd,
+            e = launch_tdse_window(view(c), st, c->d_boff, c->d_win_prev, nmax, c->cn_need.data(), c->d_cn_need,
+                                   c->max_K, c->max_kd,
                                    c->df32, win_launches);
         if (e == cudaSuccess) e = record_event(c->evw1, st);
         if (e == cudaSuccess)
@@ -976,16 +1027,16 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     {
         std::vector<int> nsolve(c->inst.size());
         for (size_t i = 0; i < ni; ++i) nsolve[i] = c->win_h[i];
-        // real time: (1 + fixed-point iterations) complex matvecs with G0 per step
-        const double sweeps = c->tdse ? 1.0 + c->cn_iters : 1.0;
         // bytes per matrix element: complex G0 16 (FP64 pair or four FP32 planes);
         // real G 8 (FP64 or FP32 hi/lo); the fused variant also streams W (16)
         const double bel = c->tdse ? 16.0 : (c->variant == WIN_FUSED ? 16.0 : 8.0);
-        const double per = (c->tdse ? 8.0 : 2.0) * sweeps, bper = bel * sweeps;
-        for (const SubDev& sd : c->sub) {
-            double K2 = (double)sd.K * sd.K;
-            flops += per * K2 * nsolve[sd.inst];
-            bytes += bper * K2 * nsolve[sd.inst];
+        for (size_t sid = 0; sid < c->sub.size(); ++sid) {
+            const SubDev& sd = c->sub[sid];
+            const double K2 = (double)sd.K * sd.K;
+            // real time: (1 + fixed-point iterations) complex matvecs with G0 per step
+            const double mv = c->tdse ? c->cn_sweeps[sid] : (double)nsolve[sd.inst];
+            flops += (c->tdse ? 8.0 : 2.0) * K2 * mv;
+            bytes += bel * K2 * mv;
         }
     }
     c->counters[0] += wms;

@@ -99,12 +99,15 @@ __global__ void k_cn_rhs(SwrDeviceView v, const long long* boff, const int* win_
 }
 
 // x = G0 u  (complex, FP64); one warp per row, lanes over the columns.
-__global__ void __launch_bounds__(256) k_cmv(SwrDeviceView v, const long long* boff) {
+// need (nullable): fixed-point iterations of this step per subdomain; the
+// launch of iteration m skips the subdomains that need no more than m.
+__global__ void __launch_bounds__(256) k_cmv(SwrDeviceView v, const long long* boff, const unsigned char* need,
+                                             int m) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
     const int K = s.K;
     const int r0 = blockIdx.x * MV_ROWS;
-    if (r0 >= K) return;
+    if (r0 >= K || (need && m >= need[sid])) return;
     extern __shared__ double sm[];
     const double* U = v.arena + boff[3 * sid + 1];
     for (int e = threadIdx.x; e < 2 * K; e += blockDim.x) sm[e] = U[e];
@@ -130,14 +133,15 @@ __global__ void __launch_bounds__(256) k_cmv(SwrDeviceView v, const long long* b
     }
 }
 
-// u = r - i theta_{n+1} Q' x
-__global__ void k_cn_update(SwrDeviceView v, const long long* boff, int n) {
+// u = r - i theta_{n+1} Q' x  (fixed-point iteration m; the subdomains that
+// need no more than m iterations at this step are skipped)
+__global__ void k_cn_update(SwrDeviceView v, const long long* boff, int n, const unsigned char* need, int m) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
     const InstDev& in = v.inst[s.inst];
     const int K = s.K, kd = s.kd;
     const int r0 = blockIdx.x * CN_ROWS;
-    if (r0 >= K) return;
+    if (r0 >= K || m >= need[sid]) return;
     extern __shared__ double sm[];
     double* x = sm;
     double* X1 = sm + 2 * K;
@@ -182,12 +186,13 @@ __device__ inline void ds_mac(float& ah, float& al, float gh, float gl, float xh
 // double-single matvec, FP64-level accuracy on the FP32 pipes.  Each warp
 // takes two rows at a time with 16-byte loads of every plane, so that eight
 // independent 512-byte requests per warp are in flight.
-__global__ void __launch_bounds__(256) k_cmv_df32(SwrDeviceView v, const long long* boff) {
+__global__ void __launch_bounds__(256) k_cmv_df32(SwrDeviceView v, const long long* boff, const unsigned char* need,
+                                                  int m) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
     const int K = s.K, ld = df32_ld(K);
     const int r0 = blockIdx.x * MV_ROWS;
-    if (r0 >= K) return;
+    if (r0 >= K || (need && m >= need[sid])) return;
     extern __shared__ float smf[];
     float* urh = smf;           // ld each
     float* url = smf + ld;
@@ -305,8 +310,10 @@ __global__ void k_cn_init(SwrDeviceView v) {
 
 static inline unsigned div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
-// Launches of one real-time window: n_steps steps with `iters` fixed-point
-// iterations each; returns the number of kernel launches.
+// Launches of one real-time window: n_steps steps, step n with as many
+// fixed-point iterations as its neediest subdomain (h_need / d_need:
+// [n_steps][n_sub] iteration counts, host and device copies); returns the
+// number of kernel launches.
 cudaError_t launch_split_c_df32(const SwrDeviceView& v, cudaStream_t st, int max_K) {
     long long kk = (long long)max_K * df32_ld(max_K);
     k_split_c_df32<<<dim3((unsigned)((kk + 2047) / 2048), v.n_sub), 256, 0, st>>>(v);
@@ -314,7 +321,8 @@ cudaError_t launch_split_c_df32(const SwrDeviceView& v, cudaStream_t st, int max
 }
 
 cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const long long* d_boff, const int* d_win_prev,
-                               int n_steps, int iters, int max_K, int max_kd, bool df32, long long* launches) {
+                               int n_steps, const unsigned char* h_need, const unsigned char* d_need, int max_K,
+                               int max_kd, bool df32, long long* launches) {
     const size_t sm_el = (2 * (size_t)max_K + 2 * (size_t)max_kd * max_kd) * sizeof(double);
     const size_t sm_mv = 2 * (size_t)df32_ld(max_K) * sizeof(double);
     static bool attr_done = false;
@@ -330,13 +338,16 @@ cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const lo
     k_cn_init<<<gf, 256, 0, st>>>(v);
     ++nl;
     for (int n = 0; n < n_steps; ++n) {
+        const unsigned char* nd = d_need + (size_t)n * v.n_sub;
+        int iters = 0;
+        for (int s = 0; s < v.n_sub; ++s) iters = h_need[(size_t)n * v.n_sub + s] > iters ? h_need[(size_t)n * v.n_sub + s] : iters;
         k_cn_rhs<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, d_win_prev, n);
-        if (df32) k_cmv_df32<<<gm, 256, sm_mv, st>>>(v, d_boff);
-        else k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff);
+        if (df32) k_cmv_df32<<<gm, 256, sm_mv, st>>>(v, d_boff, nullptr, 0);
+        else k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff, nullptr, 0);
         for (int m = 0; m < iters; ++m) {
-            k_cn_update<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, n);
-            if (df32) k_cmv_df32<<<gm, 256, sm_mv, st>>>(v, d_boff);
-            else k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff);
+            k_cn_update<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, n, nd, m);
+            if (df32) k_cmv_df32<<<gm, 256, sm_mv, st>>>(v, d_boff, nd, m);
+            else k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff, nd, m);
         }
         k_cn_finish<<<gf, 256, 0, st>>>(v, d_boff, n);
         nl += 3 + 2 * iters;
