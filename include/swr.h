@@ -99,6 +99,18 @@ typedef enum swr_window_variant {
                                   extra step dropped                             */
 } swr_window_variant;
 
+/* Transmission condition (Sec. 4, "Selection of the transmission
+ * conditions"): the data g_i each subdomain takes from its covering
+ * neighbours j at its interface nodes, averaged over them.  Both enter the
+ * local problem through the same boundary term (mu/2 R, kappa = 1/2) and the
+ * source of g_i.                                                            */
+typedef enum swr_tc {
+    SWR_TC_ROBIN = 0,      /* g_i = (n_i . grad + mu) psi_j  (Eq. RTC)            */
+    SWR_TC_DIRICHLET = 1   /* g_i = mu psi_j: the classical SWR (Dirichlet
+                              condition psi_i = psi_j) imposed by penalty with
+                              constant mu; consistent up to O(1/mu)               */
+} swr_tc;
+
 /* One SWR problem: global box [box_lo, box_hi]^n_elec cut into L^n_elec
  * subdomains.  Subdomain sid = i1 + L*i2 covers, in coordinate e,
  * [a + i_e H - overlap/2, a + (i_e+1) H + overlap/2], H = (b-a)/L.          */
@@ -136,6 +148,7 @@ typedef struct swr_instance {
                                eigenvectors with lambda > orth_tau * lambda_max
                                (X = U_r lambda_r^-1/2, the other columns zero).
                                0 selects 1e-12; must be < 1                      */
+    int    tc;              /* swr_tc: transmission condition of the Schwarz data  */
 } swr_instance;
 
 typedef struct swr_problem {

@@ -388,15 +388,19 @@ class TraceOps:
             self.ops.append((per_j, cnt))
 
     def robin_data(self, coeffs: List[np.ndarray]) -> List[np.ndarray]:
-        """g_i = (1/|J|) sum_{j in J} (n_i . grad + mu) psi_j at i's nodes."""
+        """g_i = (1/|J|) sum_{j in J} (n_i . grad + mu) psi_j at i's nodes
+        (Eq. RTC); for the classical SWR (Dirichlet condition psi_i = psi_j,
+        Sec. 4) imposed by penalty with the same boundary term, the data is
+        (1/|J|) sum_{j in J} mu psi_j."""
         mu = self.inst.mu
+        robin = getattr(self.inst, "tc", "robin") != "dirichlet"
         out = []
         for i, (per_j, cnt) in enumerate(self.ops):
             G = cnt.size
             dt = complex if (np.iscomplexobj(coeffs[0]) or np.iscomplexobj(mu)) else float
             g = np.zeros(G, dtype=dt)
             for j, (rows, vals, ders) in per_j.items():
-                g[rows] += ders @ coeffs[j] + mu * (vals @ coeffs[j])
+                g[rows] += (ders @ coeffs[j] if robin else 0.0) + mu * (vals @ coeffs[j])
             with np.errstate(invalid="ignore", divide="ignore"):
                 g = np.where(cnt > 0, g / np.maximum(cnt, 1), 0.0)
             out.append(g)

@@ -223,6 +223,8 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
         if (q > 384) return fail(c, SWR_EINVAL, "instance %d: (n_mid+2)*q_p = %d exceeds 384", i, q);
         if (!(in.orth_tau >= 0.0 && in.orth_tau < 1.0))
             return fail(c, SWR_EINVAL, "instance %d: orth_tau must be in [0, 1)", i);
+        if (in.tc != SWR_TC_ROBIN && in.tc != SWR_TC_DIRICHLET)
+            return fail(c, SWR_EINVAL, "instance %d: unknown transmission condition", i);
         if (in.n_nuclei < 0 || in.n_nuclei > SWR_MAX_NUC) return fail(c, SWR_EINVAL, "instance %d: at most 3 nuclei", i);
         if (!(in.dt > 0)) return fail(c, SWR_EINVAL, "instance %d: dt must be > 0", i);
         if (in.mode == SWR_MODE_TDSE && in.n_steps < 1) return fail(c, SWR_EINVAL, "instance %d: TDSE needs n_steps >= 1", i);
@@ -467,6 +469,7 @@ static void plan(swr_ctx* c) {
         d.harmonic = in.harmonic;
         d.kappa = in.kinetic;
         d.mu_re = in.mu_re;
+        d.tc = in.tc;
         d.mu_im = in.mu_im;
         d.dt = in.dt;
         d.ngf_tol = in.ngf_tol;

@@ -37,6 +37,7 @@ struct InstDev {
     double E0, T, omega, phase;
     double gamma0, x0[2];
     double orth_tau;              // Cholesky acceptance / canonical cut-off of the 1-D overlaps
+    int tc;                       // transmission condition (swr_tc)
 };
 
 // Per-subdomain descriptor.  Offsets are in doubles from the arena base.

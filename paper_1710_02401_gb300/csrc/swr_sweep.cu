@@ -218,9 +218,11 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
                 }
             }
             const double inv = 1.0 / (double)cnt;
-            // g = (n.grad + mu) psi_j averaged; complex mu mixes the planes
-            double gre = (sig * der[0] + in.mu_re * val[0] - in.mu_im * val[1]) * inv;
-            double gim = (sig * der[1] + in.mu_re * val[1] + in.mu_im * val[0]) * inv;
+            // g = (n.grad + mu) psi_j averaged (Robin), or mu psi_j (classical SWR by
+            // penalty); complex mu mixes the planes
+            const double sd = in.tc == SWR_TC_DIRICHLET ? 0.0 : sig;
+            double gre = (sd * der[0] + in.mu_re * val[0] - in.mu_im * val[1]) * inv;
+            double gim = (sd * der[1] + in.mu_re * val[1] + in.mu_im * val[0]) * inv;
             for (int ch = 0; ch < nch; ++ch) {
                 const double gv = ch ? gim : gre;
                 v.arena[s.u[parity] + ((long long)n * nch + ch) * s.ngam + node] = own[ch] / sn;

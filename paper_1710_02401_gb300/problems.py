@@ -62,6 +62,8 @@ class Instance:
     phi0_center: Tuple[float, float] = (0.0, 0.0)
     orth_tau: float = 1e-12              # per-coordinate overlap: Cholesky if every pivot >= tau * max diagonal,
                                          # else canonical (eigenvectors with lambda > tau * lambda_max)
+    tc: str = "robin"                    # transmission condition: "robin" (Eq. RTC) or "dirichlet"
+                                         # (classical SWR, imposed by penalty with constant mu)
 
     @property
     def n_sub(self) -> int:

@@ -54,7 +54,7 @@ int main(void) {{
   printf("swr_trace_view %zu\\n", sizeof(swr_trace_view));
   printf("swr_tune_report %zu\\n", sizeof(swr_tune_report));
   F(swr_instance, delta_per_sub) F(swr_instance, x_nuc) F(swr_instance, mode) F(swr_instance, phi0_center)
-  F(swr_instance, max_steps) F(swr_problem, workspace_bytes) F(swr_iter_report, seconds)
+  F(swr_instance, max_steps) F(swr_instance, orth_tau) F(swr_instance, tc) F(swr_problem, workspace_bytes) F(swr_iter_report, seconds)
   F(swr_problem, window_variant) F(swr_problem, rows_per_task) F(swr_problem, launch_mode)
   F(swr_tune_report, graph) F(swr_tune_report, seconds_default)
   return 0;
@@ -68,7 +68,7 @@ int main(void) {{
     assert int(got["swr_iter_report"]) == C.sizeof(S.swr_iter_report)
     assert int(got["swr_report"]) == C.sizeof(S.swr_report)
     assert int(got["swr_trace_view"]) == C.sizeof(S.swr_trace_view)
-    for key in ["delta_per_sub", "x_nuc", "mode", "phi0_center", "max_steps"]:
+    for key in ["delta_per_sub", "x_nuc", "mode", "phi0_center", "max_steps", "orth_tau", "tc"]:
         assert int(got[f"swr_instance.{key}"]) == getattr(S.swr_instance, key).offset, key
     assert int(got["swr_problem.workspace_bytes"]) == S.swr_problem.workspace_bytes.offset
     assert int(got["swr_iter_report.seconds"]) == S.swr_iter_report.seconds.offset

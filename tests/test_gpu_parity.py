@@ -165,6 +165,17 @@ def test_parity_real_time_mixed_precision(swr_mod):
     _compare(swr_mod, P.small_tdse_2d(), kmax=3, precision=swr_mod.PREC_MIXED)
 
 
+def test_parity_classical_swr_imaginary_time(swr_mod):
+    # classical SWR (Dirichlet data mu psi_j, imposed by penalty): FP64 and mixed
+    inst = P.small_tise_2d().replace(tc="dirichlet", mu=50.0)
+    _compare(swr_mod, inst, kmax=4)
+    _compare(swr_mod, inst, kmax=4, precision=swr_mod.PREC_MIXED)
+
+
+def test_parity_classical_swr_real_time(swr_mod):
+    _compare(swr_mod, P.small_tdse_2d().replace(tc="dirichlet"), kmax=3)
+
+
 def test_parity_real_time_uneven_no_field(swr_mod):
     inst = P.small_tdse_2d(L=2, K_d=7, q_p=6, n_mid=2, n_steps=25).replace(
         K_d=[7, 9, 8, 6], delta=[1.3, 2.1, 1.7, 1.1], field=(0.0, 1.0, 0.0, 0.0))

@@ -356,3 +356,23 @@ def test_singlet_ground_state_is_exchange_symmetric():
         a = O.psi_at_nodes(r.locs[sid], r.coeffs[sid]).reshape(q, q)      # [q2, q1]
         b = O.psi_at_nodes(r.locs[mir], r.coeffs[mir]).reshape(q, q)
         assert np.abs(a - b.T).max() <= 1e-11 * np.abs(a).max()
+
+
+def test_classical_swr_by_penalty_is_consistent_to_order_one_over_mu():
+    # Classical SWR (Dirichlet condition psi_i = psi_j on the interfaces, Sec. 4)
+    # imposed through the same boundary term with data g = mu psi_j: the fixed
+    # point satisfies d_n psi_i + mu psi_i = mu psi_j, so psi_i - psi_j = O(1/mu)
+    # and the converged energy of the harmonic oscillator (exact 1/2) is off by
+    # C/mu; the Robin data (d_n + mu) psi_j is consistent for any mu.  Keeping
+    # the normal derivative in the classical data, or dropping the 1/|J|
+    # average, breaks one of the two.
+    err = {}
+    for mu in (10.0, 100.0, 1000.0):
+        r = O.run_swr(_ho(2, 24, 1.0, q_p=12, ngf_tol=1e-10, mu=mu, tc="dirichlet"), kmax=100, tol=1e-8)
+        assert r.converged
+        err[mu] = r.records[-1].energy - 0.5
+    c = [err[mu] * mu for mu in err]
+    assert all(abs(x) > 0.05 for x in c)
+    assert max(c) - min(c) < 0.2 * max(abs(x) for x in c)  # error * mu constant: first order in 1/mu
+    rr = O.run_swr(_ho(2, 24, 1.0, q_p=12, ngf_tol=1e-10, mu=10.0), kmax=100, tol=1e-8)
+    assert rr.converged and abs(rr.records[-1].energy - 0.5) < 1e-4
