@@ -35,7 +35,8 @@ cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_wi
                         int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax);
 cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
                           int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
-                          double* psi_out, const long long* psi_off, int max_K, int max_kd, int max_q);
+                          double* psi_out, const long long* psi_off, size_t smem);
+size_t energy_smem(const SubDev& s);
 cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const long long* d_boff, const int* d_win_prev,
                                int n_steps, const unsigned char* h_need, const unsigned char* d_need, int max_K,
                                int max_kd, bool df32, long long* launches);
@@ -66,6 +67,7 @@ struct swr_ctx {
     long long psi_total = 0, own_total = 0;
     bool df32 = false, g_resident = false, any_ngf_stop = false;
     int stage_floats = 0;           // split window: floats per stage of staged rows
+    size_t energy_smem = 0;         // dynamic shared memory of the energy / node-value kernel
     int n_stages = 0;               // split window: stages in the ring
     int cn_iters = 0;
     std::vector<long long> boff;  // real time: per subdomain r, u, x work vectors
@@ -578,6 +580,8 @@ static void plan(swr_ctx* c) {
     int nmax = 0;
     for (const InstDev& d : c->inst) nmax = (d.mode == SWR_MODE_TDSE && d.window_cap > nmax) ? d.window_cap : nmax;
     plan_cn_iterations(c, nmax);
+    c->energy_smem = 0;
+    for (const SubDev& s : c->sub) c->energy_smem = energy_smem(s) > c->energy_smem ? energy_smem(s) : c->energy_smem;
 }
 
 // Auxiliary device arrays carved after the arena (bytes, 256-aligned).
@@ -819,6 +823,9 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     CU(cudaEventCreate(&c->evw1));
     // persistent grid for the window kernel: all CTAs must be co-resident
     if (c->bps < 1 || c->nsm < 1) return fail(c, SWR_EINVAL, "window kernel does not fit on an SM");
+    if (c->energy_smem > 227 * 1024)
+        return fail(c, SWR_EINVAL, "2-electron subdomain with K_d x q = %zu node values: the energy kernel's tables "
+                    "exceed shared memory", c->energy_smem / (2 * sizeof(double)));
     if (c->grid > c->bps * c->nsm)
         return fail(c, SWR_EINVAL, "window grid of %d CTAs exceeds %d resident CTAs", c->grid, c->bps * c->nsm);
     c->res_h.assign(c->inst.size(), 0.0);
@@ -942,7 +949,7 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
                         c->d_res_part, RES_BLOCKS, c->d_res, c->cap, c->max_K, c->max_kd, c->max_q);
     if (e == cudaSuccess)
         e = launch_energy(view(c), st, c->d_win, c->d_snorm, c->cap, c->d_epart, c->d_energy, c->d_norm2,
-                          c->d_dipole, c->d_psi, c->d_psi_off, c->max_K, c->max_kd, c->max_q);
+                          c->d_dipole, c->d_psi, c->d_psi_off, c->energy_smem);
     return e;
 }
 

@@ -469,10 +469,15 @@ cudaError_t launch_residual(const SwrDeviceView& v, cudaStream_t st, const int* 
     return cudaGetLastError();
 }
 
+// Dynamic shared memory of k_energy for one subdomain: the scaled iterate (K)
+// and, with two electrons, the two half-contracted node tables (2 K_d q).
+size_t energy_smem(const SubDev& s) {
+    return ((size_t)s.K + (s.N == 2 ? 2 * (size_t)s.kd * s.q : 0)) * sizeof(double);
+}
+
 cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
                           int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
-                          double* psi_out, const long long* psi_off, int max_K, int max_kd, int max_q) {
-    size_t smem = ((size_t)max_K + 2 * (size_t)max_kd * max_q) * sizeof(double);
+                          double* psi_out, const long long* psi_off, size_t smem) {
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_energy<<<v.n_sub, 256, smem, st>>>(v, d_win, d_snorm, cap, d_part, psi_out, psi_off);
     k_energy_reduce<<<div_up(v.n_inst, 128), 128, 0, st>>>(v, d_part, d_energy, d_norm2, d_dipole);

@@ -137,3 +137,27 @@ def test_graph_replay_is_bit_identical_to_direct_launches(S, which):
     assert ra == rb
     for x, y in zip(ua + ga + pa, ub + gb + pb):
         np.testing.assert_array_equal(x, y)
+
+
+EDGE_INSTS = [
+    P.small_tise_2d(L=2, K_d=8, q_p=6, n_mid=2).replace(max_steps=40),             # stops at its cap
+    P.small_tise_2d(L=2, K_d=9, q_p=6, n_mid=2).replace(nuclei=((0.3, 2.0),)),    # NGF stop, ~1080 steps
+    P.tise_1d_two_subdomains().replace(L=1, K_d=30, delta=2.0, q_p=12, n_mid=6),  # one subdomain, no interface
+    P.tise_1d_two_subdomains().replace(K_d=96, delta=16.0, q_p=24, n_mid=8, max_steps=400),  # K_d = 96
+]
+
+
+@pytest.fixture(scope="module")
+def edge_refs():
+    return [O.run_swr(i, kmax=2, tol=0.0) for i in EDGE_INSTS]
+
+
+@pytest.mark.parametrize("precision,variant", [(1, 3), (0, 0)])
+def test_window_edge_cases_in_one_launch(S, edge_refs, precision, variant):
+    # instances that stop at the cap beside ones that stop on the NGF tolerance,
+    # a single-subdomain instance and a 1-electron basis of 96 Gaussians (its
+    # Kronecker factors leave one CTA per SM), in one persistent launch
+    s = S.SWR(EDGE_INSTS, precision=precision, window_variant=variant)
+    assert s.window_plan()["variant"] == (3 if precision == 1 else 1)
+    s.assemble()
+    _check(*_steps(s, 2), edge_refs)
