@@ -205,6 +205,35 @@ def test_parity_batched_instances(swr_mod):
             assert abs(gres[k][i] - ref.records[k].res) <= REL * rmax
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_parity_batched_real_time_uneven_windows(swr_mod, precision):
+    # real-time instances with different windows, fields, mu and bases in one
+    # launch sequence: the fixed-point iteration count is chosen per step and
+    # subdomain, and the shorter windows end before the longest
+    S = swr_mod
+    insts = [P.small_tdse_2d(L=2, K_d=7, q_p=6, n_mid=2, n_steps=30),
+             P.small_tdse_2d(L=3, K_d=6, q_p=6, n_mid=2, n_steps=45).replace(field=(1.5, 0.45, 5.0, 1.0), mu=-4j),
+             P.tise_1d_two_subdomains().replace(mode=P.TDSE, mu=-10j, dt=0.01, n_steps=20, K_d=24, delta=2.0,
+                                                field=(0.8, 0.2, 9.0, 0.0))]
+    s = S.SWR(insts, precision=precision)
+    s.assemble()
+    kmax = 3
+    gres, gn2, gdip = [], [], []
+    for _ in range(kmax):
+        s.step()
+        gres.append(s.residual().copy())
+        gn2.append(s.norm2().copy())
+        gdip.append(s.dipole().copy())
+    for i, inst in enumerate(insts):
+        ref = O.run_swr(inst, kmax=kmax, tol=0.0)
+        rmax = max(r.res for r in ref.records)
+        for k in range(kmax):
+            r = ref.records[k]
+            assert abs(gres[k][i] - r.res) <= REL * rmax, (i, k)
+            assert abs(gn2[k][i] - r.norm2) <= REL * abs(r.norm2), (i, k)
+            assert abs(gdip[k][i] - r.dipole) <= REL * max(1.0, abs(r.dipole)), (i, k)
+
+
 def test_checkpoint_resume_is_bit_exact(swr_mod):
     S = swr_mod
     inst = P.small_tise_2d(L=2, K_d=6, q_p=6, n_mid=2)
