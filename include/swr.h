@@ -111,6 +111,21 @@ typedef enum swr_tc {
                               constant mu; consistent up to O(1/mu)               */
 } swr_tc;
 
+/* Exchange symmetry of the sought state (Appendix A).  With
+ * SWR_SYM_ANTISYMMETRIC (N = 2, imaginary time) every step acts on the
+ * antisymmetric part of its input over mirror subdomains: with sigma(i) the
+ * subdomain (i2, i1) of subdomain (i1, i2),
+ *   v_i <- (v_i - swap(v_sigma(i))) / 2,   swap: coefficient (a, b) -> (b, a),
+ * so that psi_sigma(i)(x2, x1) = -psi_i(x1, x2) holds at every step and the
+ * iteration reaches the lowest antisymmetric (triplet) state.  Needs mirror
+ * subdomains with the same K_d and delta, and an initial Gaussian whose
+ * antisymmetric part is not zero (phi0_center off the diagonal); the fused
+ * window variant is not available for such instances.                      */
+typedef enum swr_symmetry {
+    SWR_SYM_NONE = 0,
+    SWR_SYM_ANTISYMMETRIC = 1
+} swr_symmetry;
+
 /* One SWR problem: global box [box_lo, box_hi]^n_elec cut into L^n_elec
  * subdomains.  Subdomain sid = i1 + L*i2 covers, in coordinate e,
  * [a + i_e H - overlap/2, a + (i_e+1) H + overlap/2], H = (b-a)/L.          */
@@ -149,6 +164,7 @@ typedef struct swr_instance {
                                (X = U_r lambda_r^-1/2, the other columns zero).
                                0 selects 1e-12; must be < 1                      */
     int    tc;              /* swr_tc: transmission condition of the Schwarz data  */
+    int    symmetry;        /* swr_symmetry                                        */
 } swr_instance;
 
 typedef struct swr_problem {

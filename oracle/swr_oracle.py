@@ -504,6 +504,23 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
         n_prev = 0
     u_prev = None
 
+    # antisymmetric states (Appendix A: psi_sigma(i)(x1, x2) = -psi_i(x2, x1) with
+    # sigma the mirror subdomain across x1 = x2): every step acts on the
+    # antisymmetric part of its input, P(c)_i = (c_i - swap(c_sigma(i))) / 2,
+    # swap transposing the (coordinate-2, coordinate-1) coefficient matrix
+    anti = getattr(inst, "symmetry", "none") == "antisymmetric"
+
+    def mirror(i):
+        return (i // inst.L) + inst.L * (i % inst.L)
+
+    def proj(vecs):
+        out = []
+        for i in range(S):
+            j = mirror(i)
+            r1, r2 = locs[j].basis.r
+            out.append(0.5 * (vecs[i] - vecs[j].reshape(r2, r1).T.reshape(-1)))
+        return out
+
     # imaginary time: (A + dt H~) c~^{n+1} = A c^n + kappa dt b^{n+1}
     lu_ie = None
     if not tdse:
@@ -532,8 +549,12 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
                     rhs = M0 @ coeffs[i] + 0.5j * dt * kappa * (b_vec(i, g_at(i, n + 1)) + b_vec(i, g_at(i, n)))
                     new.append(np.linalg.solve(M1, rhs))
             else:
+                cin = proj(coeffs) if anti else coeffs
+                bin_ = [b_vec(i, g_at(i, n + 1)) for i in range(S)]
+                if anti:
+                    bin_ = proj(bin_)
                 for i, l in enumerate(locs):
-                    rhs = l.A @ coeffs[i] + kappa * dt * b_vec(i, g_at(i, n + 1))
+                    rhs = l.A @ cin[i] + kappa * dt * bin_[i]
                     new.append(sla.lu_solve(lu_ie[i], rhs))
                 raw = new
                 if inst.normalize:

@@ -227,6 +227,22 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
             return fail(c, SWR_EINVAL, "instance %d: orth_tau must be in [0, 1)", i);
         if (in.tc != SWR_TC_ROBIN && in.tc != SWR_TC_DIRICHLET)
             return fail(c, SWR_EINVAL, "instance %d: unknown transmission condition", i);
+        if (in.symmetry != SWR_SYM_NONE && in.symmetry != SWR_SYM_ANTISYMMETRIC)
+            return fail(c, SWR_EINVAL, "instance %d: unknown symmetry", i);
+        if (in.symmetry == SWR_SYM_ANTISYMMETRIC) {
+            if (in.n_elec != 2 || in.mode != SWR_MODE_TISE)
+                return fail(c, SWR_EINVAL, "instance %d: antisymmetric states need N = 2 in imaginary time", i);
+            for (int s = 0; s < in.L * in.L; ++s) {
+                const int m = s / in.L + in.L * (s % in.L);
+                const int ks = in.K_d_per_sub ? in.K_d_per_sub[s] : in.K_d, km = in.K_d_per_sub ? in.K_d_per_sub[m] : in.K_d;
+                const double ds = in.delta_per_sub ? in.delta_per_sub[s] : in.delta;
+                const double dm = in.delta_per_sub ? in.delta_per_sub[m] : in.delta;
+                if (ks != km || ds != dm)
+                    return fail(c, SWR_EINVAL, "instance %d: subdomains %d and %d (mirror images) differ in basis", i, s, m);
+            }
+            if (p->window_variant == SWR_WINDOW_FUSED)
+                return fail(c, SWR_EINVAL, "instance %d: the fused window does not take antisymmetric states", i);
+        }
         if (in.n_nuclei < 0 || in.n_nuclei > SWR_MAX_NUC) return fail(c, SWR_EINVAL, "instance %d: at most 3 nuclei", i);
         if (!(in.dt > 0)) return fail(c, SWR_EINVAL, "instance %d: dt must be > 0", i);
         if (in.mode == SWR_MODE_TDSE && in.n_steps < 1) return fail(c, SWR_EINVAL, "instance %d: TDSE needs n_steps >= 1", i);
@@ -472,6 +488,7 @@ static void plan(swr_ctx* c) {
         d.kappa = in.kinetic;
         d.mu_re = in.mu_re;
         d.tc = in.tc;
+        d.anti = in.symmetry == SWR_SYM_ANTISYMMETRIC;
         d.mu_im = in.mu_im;
         d.dt = in.dt;
         d.ngf_tol = in.ngf_tol;
@@ -558,7 +575,9 @@ static void plan(swr_ctx* c) {
     // Mixed precision: FP32 planes of the step matrix, and W = (Pp (x) Pp) G when
     // the fused single-barrier window can run (task state in shared memory).
     c->has_w = false;
-    if (c->df32 && !c->tdse && (p.window_variant == 0 || p.window_variant == WIN_FUSED)) {
+    bool any_anti = false;  // antisymmetric states: no fused window
+    for (const swr_instance& in : c->inst_h) any_anti = any_anti || in.symmetry == SWR_SYM_ANTISYMMETRIC;
+    if (c->df32 && !c->tdse && !any_anti && (p.window_variant == 0 || p.window_variant == WIN_FUSED)) {
         plan_tasks(c, p.rows_per_task, 2 * (c->nsm > 0 ? c->nsm : 152));
         c->has_w = p.window_variant == WIN_FUSED ||
                    (c->tasks_per_cta <= window_tasks_per_cta_max() && c->max_rows <= window_rows_per_task_max() &&

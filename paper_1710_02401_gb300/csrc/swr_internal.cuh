@@ -38,6 +38,7 @@ struct InstDev {
     double gamma0, x0[2];
     double orth_tau;              // Cholesky acceptance / canonical cut-off of the 1-D overlaps
     int tc;                       // transmission condition (swr_tc)
+    int anti;                     // antisymmetric states: steps act on the antisymmetric part (swr_symmetry)
 };
 
 // Per-subdomain descriptor.  Offsets are in doubles from the arena base.

@@ -245,6 +245,17 @@ __device__ inline TaskCache make_task_cache(const SweepArgs& A, int t) {
     return c;
 }
 
+// Antisymmetric states (Appendix A): the mirror subdomain (i2, i1) of the
+// task's subdomain (i1, i2), and the index of coefficient (a, b) -> (b, a)
+// (index a + kd b: the orthonormal per-coordinate functions of an interval
+// are the same in both coordinates, dropped directions kept as zero columns).
+__device__ inline int mirror_sid(const SwrDeviceView& v, const TaskCache& tc) {
+    const InstDev& in = v.inst[tc.inst];
+    const int s = tc.sid - in.sub_base;
+    return in.sub_base + s / in.L + in.L * (s % in.L);
+}
+__device__ inline int swap_index(int c, int kd) { return c / kd + kd * (c % kd); }
+
 // rows [r0, r0+nr) of z = (P1 (x) P2) y (N = 2) or P1 y (N = 1); y in shared
 // memory, P in shared or global memory.  Warp-parallel dot products (lanes over
 // the contraction, shuffle reduction) keep the FP64 dependency chains short.
@@ -548,11 +559,24 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_2ph(SweepArgs A) {
             if (tid == 0 && tc.first) A.snorm[(long long)tc.inst * (cap + 1) + n] = s_n;
             if (n >= tc.maxs || !isfinite(s_n) || s_n <= 0.0) continue;  // closed in phase B
             if (load) {
+                // antisymmetric states: v <- (v - swap(v of the mirror subdomain)) / 2
+                const bool anti = v.inst[tc.inst].anti != 0;
+                const double *ynm = nullptr, *bnm = nullptr;
+                if (anti) {
+                    const SubDev& ms = v.sub[mirror_sid(v, tc)];
+                    const int wp = A.win_prev[tc.inst];
+                    ynm = v.arena + ms.hist + (long long)n * K;
+                    if (wp > 0) bnm = v.arena + ms.bvec + (long long)min(n + 1, wp) * K;
+                }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     int c = tid + i * WIN_THREADS;
                     if (c < K) {
                         double val = yv[i] * is_n + tc.kdt * bv[i];
+                        if (anti) {
+                            const int sc = swap_index(c, tc.kd);
+                            val = 0.5 * (val - (__ldcg(ynm + sc) * is_n + (bnm ? tc.kdt * __ldcg(bnm + sc) : 0.0)));
+                        }
                         if (DF32) {
                             float h = (float)val;
                             vf[c] = make_float2(h, (float)(val - (double)h));
@@ -1363,12 +1387,29 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                     const double* U = v.arena + sd.work + (long long)(m & 1) * 2 * K;
                     const double* Wv = U + K;
                     const double* c0 = v.arena + tc.c0;
+                    // antisymmetric states: the products act on (y - swap(y of the mirror
+                    // subdomain)) / 2 and likewise b'; y itself is kept for the history and z
+                    const bool anti = v.inst[tc.inst].anti != 0;
+                    const double *Um = nullptr, *Wm = nullptr, *c0m = nullptr, *bm = nullptr;
+                    if (anti) {
+                        const SubDev& ms = v.sub[mirror_sid(v, tc)];
+                        Um = v.arena + ms.work + (long long)(m & 1) * 2 * K;
+                        Wm = Um + K;
+                        c0m = v.arena + ms.c0;
+                        if (bsrc) bm = v.arena + ms.bvec + (long long)min(m + 1, wp) * K;
+                    }
                     for (int c = ct; c < ld; c += CT) {
                         if (c < K) {
                             const double y = m == 0 ? c0[c] : __ldcg(U + c) * is1 + __ldcg(Wv + c);
+                            double yp = y, bp = bsrc ? bsrc[c] : 0.0;
+                            if (anti) {
+                                const int sc = swap_index(c, tc.kd);
+                                yp = 0.5 * (y - (m == 0 ? c0m[sc] : __ldcg(Um + sc) * is1 + __ldcg(Wm + sc)));
+                                if (bsrc) bp = 0.5 * (bp - __ldcg(bm + sc));
+                            }
                             vs[c] = y;
-                            vf[c] = ds_split(y);
-                            bf[c] = bsrc ? ds_split(tc.kdt * bsrc[c]) : make_float2(0.f, 0.f);
+                            vf[c] = ds_split(yp);
+                            bf[c] = bsrc ? ds_split(tc.kdt * bp) : make_float2(0.f, 0.f);
                         } else {
                             vf[c] = make_float2(0.f, 0.f);
                             bf[c] = make_float2(0.f, 0.f);

@@ -64,6 +64,8 @@ class Instance:
                                          # else canonical (eigenvectors with lambda > tau * lambda_max)
     tc: str = "robin"                    # transmission condition: "robin" (Eq. RTC) or "dirichlet"
                                          # (classical SWR, imposed by penalty with constant mu)
+    symmetry: str = "none"               # "antisymmetric": N = 2 imaginary time restricted to states with
+                                         # psi(x2, x1) = -psi(x1, x2) (Appendix A, mirror subdomains)
 
     @property
     def n_sub(self) -> int:

@@ -24,6 +24,7 @@ MODE_TISE, MODE_TDSE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 WINDOW_AUTO, WINDOW_TWO_PHASE, WINDOW_FUSED, WINDOW_SPLIT = 0, 1, 2, 3
 TC_ROBIN, TC_DIRICHLET = 0, 1
+SYM_NONE, SYM_ANTISYMMETRIC = 0, 1
 LAUNCH_GRAPH, LAUNCH_DIRECT = 0, 1
 GET, SET = 0, 1
 (FIELD_ENERGY, FIELD_NORM2, FIELD_DIPOLE, FIELD_RES, FIELD_WINDOW, FIELD_PSI_NODES, FIELD_OWN_TRACES,
@@ -41,7 +42,7 @@ class swr_instance(C.Structure):
         ("normalize", C.c_int), ("dt", C.c_double), ("n_steps", C.c_int), ("ngf_tol", C.c_double),
         ("max_steps", C.c_int), ("field_E0", C.c_double), ("field_T", C.c_double),
         ("field_omega", C.c_double), ("field_phase", C.c_double), ("phi0_gamma", C.c_double),
-        ("phi0_center", C.c_double * 2), ("orth_tau", C.c_double), ("tc", C.c_int),
+        ("phi0_center", C.c_double * 2), ("orth_tau", C.c_double), ("tc", C.c_int), ("symmetry", C.c_int),
     ]
 
 
@@ -177,6 +178,7 @@ def _to_c_instance(inst: P.Instance, keep: list) -> swr_instance:
     ci.phi0_center[0], ci.phi0_center[1] = float(inst.phi0_center[0]), float(inst.phi0_center[1])
     ci.orth_tau = float(inst.orth_tau)
     ci.tc = TC_DIRICHLET if inst.tc == "dirichlet" else TC_ROBIN
+    ci.symmetry = SYM_ANTISYMMETRIC if inst.symmetry == "antisymmetric" else SYM_NONE
     return ci
 
 

@@ -176,6 +176,30 @@ def test_parity_classical_swr_real_time(swr_mod):
     _compare(swr_mod, P.small_tdse_2d().replace(tc="dirichlet"), kmax=3)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_parity_antisymmetric_states(swr_mod, precision):
+    # the 3 x 3 decomposition has three diagonal subdomains and three mirror
+    # pairs; every step acts on the antisymmetric part over mirror subdomains
+    S = swr_mod
+    inst = P.small_tise_2d().replace(symmetry="antisymmetric", phi0_center=(0.8, -0.8))
+    s, _ = _compare(S, inst, kmax=3, precision=precision)
+    assert s.window_plan()["variant"] == (3 if precision == 1 else 1)  # no fused window for these
+
+
+def test_antisymmetric_harmonic_pair_reaches_the_triplet_level(swr_mod):
+    # two non-interacting electrons in a harmonic well: lowest antisymmetric
+    # level 1/2 + 3/2 = 2 (the symmetric ground state is 1)
+    S = swr_mod
+    b = P.small_tise_2d(L=2, K_d=12, q_p=10, n_mid=3)
+    inst = b.replace(nuclei=(), ee_coef=0.0, harmonic=1.0, overlap=1.0, phi0_center=(0.8, -0.8), ngf_tol=1e-10,
+                     delta=P.spacing_rule_delta(b.box, 2, 1.0, 12), symmetry="antisymmetric")
+    for prec in (S.PREC_FP64, S.PREC_MIXED):
+        s = S.SWR(inst, precision=prec)
+        s.assemble()
+        rep, _ = s.iterate(1e-8, 60)
+        assert rep.converged and abs(float(s.energy()[0]) - 2.0) < 5e-3
+
+
 def test_parity_real_time_uneven_no_field(swr_mod):
     inst = P.small_tdse_2d(L=2, K_d=7, q_p=6, n_mid=2, n_steps=25).replace(
         K_d=[7, 9, 8, 6], delta=[1.3, 2.1, 1.7, 1.1], field=(0.0, 1.0, 0.0, 0.0))
