@@ -54,9 +54,9 @@ KERNEL_FUNCS["k_window_2ph<true>@batched"] = KERNEL_FUNCS["k_window_2ph<true>"]
 KERNEL_FUNCS["k_window_split@batched"] = KERNEL_FUNCS["k_window_split"]
 PROFILED_TRAFFIC = {
     "k_window_fused": ("123b4a784de2ee96", 329.5e6, "profiles/k_window_fused_tise_2e_16sd.md"),
-    "k_window_2ph<false>": ("654a871bbf4d80e1", 278.7e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
-    "k_window_2ph<true>@batched": ("132abcba8871d5ad", 1.196, "profiles/k_window_2ph_df32_batched_uneven.md"),
-    "k_window_split@batched": ("27a126d6e8f6a859", 1.033, "profiles/k_window_split_batched_uneven.md"),
+    "k_window_2ph<false>": ("36eacbc20ac4f33a", 278.4e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
+    "k_window_2ph<true>@batched": ("295b45653b3c50bc", 1.195, "profiles/k_window_2ph_df32_batched_uneven.md"),
+    "k_window_split@batched": ("c9b76ea5b5df2f56", 1.033, "profiles/k_window_split_batched_uneven.md"),
 }
 
 
