@@ -170,3 +170,29 @@ def test_window_plan_requests_on_host(lib):
     ps = _problem([P.small_tdse_2d()], keep)
     ps.precision, ps.window_variant = S.PREC_MIXED, S.WINDOW_SPLIT
     assert lib.swr_workspace_size(C.byref(ps), C.byref(n)) == S.SWR_EINVAL  # imaginary time only
+
+
+def test_transmission_and_symmetry_requests_on_host(lib):
+    keep = []
+    n = C.c_size_t(0)
+
+    def status(inst, precision=S.PREC_FP64, variant=0, raw=None):
+        p = _problem([inst], keep)
+        p.precision, p.window_variant = precision, variant
+        if raw:  # set a raw field of the C instance (values the Python side does not produce)
+            arr = C.cast(p.instances, C.POINTER(S.swr_instance))
+            setattr(arr[0], *raw)
+        return lib.swr_workspace_size(C.byref(p), C.byref(n))
+
+    anti = P.small_tise_2d().replace(symmetry="antisymmetric", phi0_center=(0.8, -0.8))
+    assert status(P.small_tise_2d().replace(tc="dirichlet")) == S.SWR_OK
+    assert status(P.small_tise_2d(), raw=("tc", 2)) == S.SWR_EINVAL
+    assert status(P.small_tise_2d(), raw=("symmetry", 2)) == S.SWR_EINVAL
+    assert status(anti) == S.SWR_OK
+    assert status(anti, S.PREC_MIXED) == S.SWR_OK                              # split window
+    assert status(anti, S.PREC_MIXED, S.WINDOW_FUSED) == S.SWR_EINVAL          # not the fused one
+    assert status(P.tise_1d_two_subdomains().replace(symmetry="antisymmetric")) == S.SWR_EINVAL  # N = 1
+    assert status(P.small_tdse_2d().replace(symmetry="antisymmetric")) == S.SWR_EINVAL         # real time
+    kd = [8, 9, 8, 9]  # subdomain (1, 0) and its mirror (0, 1) differ
+    assert status(P.small_tise_2d(L=2, K_d=8).replace(K_d=kd, symmetry="antisymmetric")) == S.SWR_EINVAL
+    assert status(P.small_tise_2d(L=2, K_d=8).replace(K_d=[8, 9, 9, 8], symmetry="antisymmetric")) == S.SWR_OK
