@@ -42,14 +42,17 @@ FP32_PEAK_TFLOPS = 67.7
 KERNEL_FUNCS = {
     "k_window_fused": ["release_barrier", "block_sums2", "two_sum", "make_task_cache", "z_rows_sm", "df32_acc",
                        "k_window_fused"],
-    "k_window_2ph<false>": ["reduce_barrier", "make_task_cache", "z_rows_sm", "z_rows_staged", "prefetch_l2",
-                            "prefetch_rows", "fp64_rows4", "k_window_2ph"],
-    "k_window_2ph<true>": ["reduce_barrier", "two_sum", "make_task_cache", "z_rows_sm", "z_rows_staged",
-                           "prefetch_l2", "prefetch_rows", "df32_acc", "df32_rows4", "k_window_2ph"],
+    "k_window_2ph<false>": ["reduce_barrier", "make_task_cache", "mirror_sid", "swap_index", "mirror_weight",
+                            "diagonal_anti", "z_rows_sm", "z_rows_staged", "prefetch_l2", "prefetch_rows",
+                            "fp64_rows4", "k_window_2ph"],
+    "k_window_2ph<true>": ["reduce_barrier", "two_sum", "make_task_cache", "mirror_sid", "swap_index",
+                           "mirror_weight", "diagonal_anti", "z_rows_sm", "z_rows_staged", "prefetch_l2",
+                           "prefetch_rows", "df32_acc", "df32_rows4", "k_window_2ph"],
 }
 KERNEL_FUNCS["k_window_split"] = ["mbar_wait", "split_stage_rows", "reduce_barrier_sd", "split_cbar", "split_cbar_or",
                                   "mbar_arrive", "z_rows_group", "split_chunk", "ds_add", "split_row", "two_sum",
-                                  "make_task_cache", "df32_acc", "k_window_split"]
+                                  "make_task_cache", "mirror_sid", "swap_index", "mirror_weight", "diagonal_anti",
+                                  "df32_acc", "k_window_split"]
 KERNEL_FUNCS["k_window_2ph<true>@batched"] = KERNEL_FUNCS["k_window_2ph<true>"]
 KERNEL_FUNCS["k_window_split@batched"] = KERNEL_FUNCS["k_window_split"]
 PROFILED_TRAFFIC = {

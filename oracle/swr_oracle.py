@@ -490,20 +490,6 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
     def b_vec(i, g):  # b_l = sum_Gamma w g v_l
         return locs[i].own_vals.T @ (locs[i].gamma.w * g)
 
-    # initial data (step 1), normalised for the NGF
-    c0 = [l.c0.astype(complex if cplx else float) for l in locs]
-    if inst.mode == TISE and inst.normalize:
-        s0 = math.sqrt(pou_norm2(locs, c0))
-        c0 = [c / s0 for c in c0]
-
-    if g_init is not None:
-        g_prev = [np.asarray(g) for g in g_init]
-        n_prev = g_prev[0].shape[0] - 1
-    else:
-        g_prev = None
-        n_prev = 0
-    u_prev = None
-
     # antisymmetric states (Appendix A: psi_sigma(i)(x1, x2) = -psi_i(x2, x1) with
     # sigma the mirror subdomain across x1 = x2): every step acts on the
     # antisymmetric part of its input, P(c)_i = (c_i - swap(c_sigma(i))) / 2,
@@ -520,6 +506,23 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
             r1, r2 = locs[j].basis.r
             out.append(0.5 * (vecs[i] - vecs[j].reshape(r2, r1).T.reshape(-1)))
         return out
+
+    # initial data (step 1), normalised for the NGF; antisymmetric states start
+    # from the antisymmetric part of the projected initial Gaussian
+    c0 = [l.c0.astype(complex if cplx else float) for l in locs]
+    if anti:
+        c0 = proj(c0)
+    if inst.mode == TISE and inst.normalize:
+        s0 = math.sqrt(pou_norm2(locs, c0))
+        c0 = [c / s0 for c in c0]
+
+    if g_init is not None:
+        g_prev = [np.asarray(g) for g in g_init]
+        n_prev = g_prev[0].shape[0] - 1
+    else:
+        g_prev = None
+        n_prev = 0
+    u_prev = None
 
     # imaginary time: (A + dt H~) c~^{n+1} = A c^n + kappa dt b^{n+1}
     lu_ie = None

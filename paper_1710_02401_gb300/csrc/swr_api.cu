@@ -32,7 +32,8 @@ cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, 
 extern const int kAssembleLaunchesFixed, kStepLaunches;
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
-                        int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax);
+                        int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax,
+                        bool any_anti);
 cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
                           int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
                           double* psi_out, const long long* psi_off, size_t smem);
@@ -65,7 +66,7 @@ struct swr_ctx {
     int cap = 0, max_K = 0, max_kd = 0, max_q = 0, max_ngam = 0;
     bool any_ee = false, tdse = false;
     long long psi_total = 0, own_total = 0;
-    bool df32 = false, g_resident = false, any_ngf_stop = false;
+    bool df32 = false, g_resident = false, any_ngf_stop = false, any_anti = false;
     int stage_floats = 0;           // split window: floats per stage of staged rows
     size_t energy_smem = 0;         // dynamic shared memory of the energy / node-value kernel
     int n_stages = 0;               // split window: stages in the ring
@@ -323,6 +324,9 @@ static void plan_tasks(swr_ctx* c, int target_rows, int ctas, bool by_bytes = fa
             c->inst_task0.push_back((int)c->tasks.size());
             ++cur_inst;
         }
+        // antisymmetric states: the lower subdomain (i1 > i2) of a mirror pair is
+        // not solved, its iterates are the mirror images of the upper one's
+        if (c->inst[s.inst].anti && s.N == 2 && s.idx[0] > s.idx[1]) continue;
         long long tgt = target;
         if (by_bytes) {
             tgt = (target * (long long)c->max_K + s.K / 2) / s.K;
@@ -575,9 +579,9 @@ static void plan(swr_ctx* c) {
     // Mixed precision: FP32 planes of the step matrix, and W = (Pp (x) Pp) G when
     // the fused single-barrier window can run (task state in shared memory).
     c->has_w = false;
-    bool any_anti = false;  // antisymmetric states: no fused window
-    for (const swr_instance& in : c->inst_h) any_anti = any_anti || in.symmetry == SWR_SYM_ANTISYMMETRIC;
-    if (c->df32 && !c->tdse && !any_anti && (p.window_variant == 0 || p.window_variant == WIN_FUSED)) {
+    c->any_anti = false;  // antisymmetric states: no fused window
+    for (const swr_instance& in : c->inst_h) c->any_anti = c->any_anti || in.symmetry == SWR_SYM_ANTISYMMETRIC;
+    if (c->df32 && !c->tdse && !c->any_anti && (p.window_variant == 0 || p.window_variant == WIN_FUSED)) {
         plan_tasks(c, p.rows_per_task, 2 * (c->nsm > 0 ? c->nsm : 152));
         c->has_w = p.window_variant == WIN_FUSED ||
                    (c->tasks_per_cta <= window_tasks_per_cta_max() && c->max_rows <= window_rows_per_task_max() &&
@@ -965,7 +969,7 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
     }
     if (e == cudaSuccess)
         e = launch_post(view(c), st, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
-                        c->d_res_part, RES_BLOCKS, c->d_res, c->cap, c->max_K, c->max_kd, c->max_q);
+                        c->d_res_part, RES_BLOCKS, c->d_res, c->cap, c->max_K, c->max_kd, c->max_q, c->any_anti);
     if (e == cudaSuccess)
         e = launch_energy(view(c), st, c->d_win, c->d_snorm, c->cap, c->d_epart, c->d_energy, c->d_norm2,
                           c->d_dipole, c->d_psi, c->d_psi_off, c->energy_smem);
@@ -1070,7 +1074,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     }
     c->counters[0] += wms;
     c->counters[1] += 1;
-    c->counters[2] += kStepLaunches - 1 + win_launches;
+    c->counters[2] += kStepLaunches - 1 + win_launches + (c->any_anti ? 1 : 0);
     c->counters[3] += flops;
     c->counters[4] += bytes;
     c->counters[5] += (double)solves;

@@ -799,6 +799,60 @@ __global__ void k_project(SwrDeviceView v, double* norm_part) {
     if (threadIdx.x == 0) norm_part[sid] = (s.N == 1) ? nrm[0] : nrm[0] * nrm[1];
 }
 
+// Antisymmetric states (Appendix A): the initial data of each mirror pair
+// (sigma(i) = (i2, i1) of subdomain (i1, i2)) replaced by its antisymmetric
+// part, c0_i <- (c0_i - swap(c0_sigma(i))) / 2 and c0_sigma(i) = -swap(c0_i)
+// (swap: coefficient (a, b) -> (b, a)), with the partition-of-unity norm
+// c0^T (Pp (x) Pp) c0 of both for the normalisation that follows.  One block
+// per subdomain; the block of the upper (or diagonal) subdomain of a pair
+// writes both.
+__global__ void k_anti_c0(SwrDeviceView v, double* norm_part) {
+    const int sid = blockIdx.x;
+    const SubDev& s = v.sub[sid];
+    const InstDev& in = v.inst[s.inst];
+    if (!in.anti || s.N != 2) return;
+    const int loc = sid - in.sub_base, i1 = loc % in.L, i2 = loc / in.L;
+    if (i1 > i2) return;
+    const int msid = in.sub_base + i2 + in.L * i1;
+    const int kd = s.kd, K = s.K;
+    __shared__ double y[32 * 32], tmp[32 * 32];
+    __shared__ double red[8];
+    double* c0 = v.arena + s.c0;
+    double* cm = v.arena + v.sub[msid].c0;
+    for (int c = threadIdx.x; c < K; c += blockDim.x) y[c] = 0.5 * (c0[c] - cm[c / kd + kd * (c % kd)]);
+    __syncthreads();
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        c0[c] = y[c];
+        if (msid != sid) cm[c / kd + kd * (c % kd)] = -y[c];
+    }
+    T1Layout lay(s.q, kd);
+    const double* P1 = v.arena + s.t1[0] + lay.mat(M_PP);
+    const double* P2 = v.arena + s.t1[1] + lay.mat(M_PP);
+    for (int it = threadIdx.x; it < kd * kd; it += blockDim.x) {  // tmp[c][b] = sum_e y[c + kd e] P2[b][e]
+        const int c = it / kd, b = it - c * kd;
+        double acc = 0;
+        for (int e = 0; e < kd; ++e) acc = fma(y[c + kd * e], P2[b * kd + e], acc);
+        tmp[it] = acc;
+    }
+    __syncthreads();
+    double part = 0;
+    for (int m = threadIdx.x; m < K; m += blockDim.x) {  // y[(a,b)] sum_c P1[a][c] tmp[c][b]
+        const int b = m / kd, a = m - b * kd;
+        double z = 0;
+        for (int c = 0; c < kd; ++c) z = fma(P1[a * kd + c], tmp[c * kd + b], z);
+        part += y[m] * z;
+    }
+    part = warp_sum(part);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        norm_part[sid] = t;
+        norm_part[msid] = t;
+    }
+}
+
 // Per-instance normalisation of c0 (TISE with normalisation).
 __global__ void k_normalize_c0(SwrDeviceView v, const double* norm_part) {
     const int sid = blockIdx.x;
@@ -822,8 +876,8 @@ static inline unsigned div_up(long long a, long long b) { return (unsigned)((a +
 
 // Launches of an assembly besides the e-e block (3) and the Gauss-Jordan
 // panels/updates (2 per block column): tabulate, mat1d, orth, h_kron,
-// symmetrize, step_matrix, project, normalize_c0.
-extern const int kAssembleLaunchesFixed = 8;
+// symmetrize, step_matrix, project, anti_c0, normalize_c0.
+extern const int kAssembleLaunchesFixed = 9;
 
 cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, int max_kd, int max_K,
                             bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
@@ -859,6 +913,7 @@ cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, 
         }
     }
     k_project<<<v.n_sub, 256, 0, st>>>(v, d_norm_part);
+    k_anti_c0<<<v.n_sub, 256, 0, st>>>(v, d_norm_part);
     k_normalize_c0<<<v.n_sub, 256, 0, st>>>(v, d_norm_part);
     return cudaGetLastError();
 }

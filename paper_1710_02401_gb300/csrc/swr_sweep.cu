@@ -430,18 +430,45 @@ __global__ void k_energy_reduce(SwrDeviceView v, const double* part, double* ene
     dipole[i] = dip / den;
 }
 
+// Antisymmetric states (Appendix A): the lower subdomain (i1 > i2) of each
+// mirror pair is not solved; its iterates of the window are the mirror images
+// of the upper one's, y_sigma(i)^n = -swap(y_i^n) for n = 0..window (swap:
+// coefficient (a, b) -> (b, a)), filled before the traces, the exchange and
+// the energies read them.
+__global__ void k_anti_fill(SwrDeviceView v, const int* win) {
+    const int sid = blockIdx.y;
+    const SubDev& s = v.sub[sid];
+    const InstDev& in = v.inst[s.inst];
+    if (!in.anti || s.N != 2 || in.mode != SWR_MODE_TISE) return;
+    const int loc = sid - in.sub_base, i1 = loc % in.L, i2 = loc / in.L;
+    if (i1 <= i2) return;
+    const SubDev& ms = v.sub[in.sub_base + i2 + in.L * i1];
+    const int K = s.K, kd = s.kd;
+    const long long total = (long long)(win[s.inst] + 1) * K;
+    double* h = v.arena + s.hist;
+    const double* hm = v.arena + ms.hist;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long n = e / K;
+        const int c = (int)(e - n * K);
+        h[e] = -hm[n * K + c / kd + kd * (c % kd)];
+    }
+}
+
 // ------------------------------------------------------------- host driver
 
 static inline unsigned div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // Kernel launches per swr_step besides the window (reset, window, line traces,
-// gather, residual, residual reduce, energy, energy reduce).
+// gather, residual, residual reduce, energy, energy reduce; one more with
+// antisymmetric instances: the mirror fill).
 extern const int kStepLaunches = 8;
 
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
-                        int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax) {
+                        int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax,
+                        bool any_anti) {
     int nb = 64;
+    if (any_anti) k_anti_fill<<<dim3(nb, v.n_sub), 256, 0, st>>>(v, d_win);
     {
         const size_t base = ((size_t)lt_kmax + (size_t)lt_kdmax + 32 * (size_t)lt_kdmax) * sizeof(float2);
         const size_t tab = 2 * (size_t)lt_qmax * lt_kdmax * sizeof(float2);

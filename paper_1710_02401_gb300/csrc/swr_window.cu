@@ -255,6 +255,16 @@ __device__ inline int mirror_sid(const SwrDeviceView& v, const TaskCache& tc) {
     return in.sub_base + s / in.L + in.L * (s % in.L);
 }
 __device__ inline int swap_index(int c, int kd) { return c / kd + kd * (c % kd); }
+// The lower subdomain of a mirror pair has no tasks (its iterates are the
+// mirror images of the upper one's): the partials of an off-diagonal task of
+// an antisymmetric instance count twice in the instance's sums; the
+// projection onto the antisymmetric part is then needed on the diagonal only.
+__device__ inline double mirror_weight(const SwrDeviceView& v, const TaskCache& tc) {
+    return (v.inst[tc.inst].anti && mirror_sid(v, tc) != tc.sid) ? 2.0 : 1.0;
+}
+__device__ inline bool diagonal_anti(const SwrDeviceView& v, const TaskCache& tc) {
+    return v.inst[tc.inst].anti && mirror_sid(v, tc) == tc.sid;
+}
 
 // rows [r0, r0+nr) of z = (P1 (x) P2) y (N = 2) or P1 y (N = 1); y in shared
 // memory, P in shared or global memory.  Warp-parallel dot products (lanes over
@@ -517,7 +527,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_2ph(SweepArgs A) {
         const double* z0 = own(j, 2);
         for (int r = tid; r < nr; r += WIN_THREADS) acc += y0[r] * z0[r];
         acc = wblock_sum(acc, red);
-        if (tid == 0) A.part_s[t] = acc;
+        if (tid == 0) A.part_s[t] = acc * mirror_weight(v, tc);
     }
     target += gridDim.x;
     ++gen;
@@ -559,8 +569,9 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_2ph(SweepArgs A) {
             if (tid == 0 && tc.first) A.snorm[(long long)tc.inst * (cap + 1) + n] = s_n;
             if (n >= tc.maxs || !isfinite(s_n) || s_n <= 0.0) continue;  // closed in phase B
             if (load) {
-                // antisymmetric states: v <- (v - swap(v of the mirror subdomain)) / 2
-                const bool anti = v.inst[tc.inst].anti != 0;
+                // antisymmetric states: v <- (v - swap(v of the mirror subdomain)) / 2 on
+                // a diagonal subdomain (its own mirror)
+                const bool anti = diagonal_anti(v, tc);
                 const double *ynm = nullptr, *bnm = nullptr;
                 if (anti) {
                     const SubDev& ms = v.sub[mirror_sid(v, tc)];
@@ -599,7 +610,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_2ph(SweepArgs A) {
                 for (int r = tid; r < nr; r += WIN_THREADS)
                     acc += (y_n[r] * is_n - y_p[r] * is_p) * (z_n[r] * is_n - z_p[r] * is_p);
                 acc = wblock_sum(acc, red);
-                if (tid == 0) A.part_d[t] = acc;
+                if (tid == 0) A.part_d[t] = acc * mirror_weight(v, tc);
             } else {
                 __syncthreads();
             }
@@ -672,7 +683,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_2ph(SweepArgs A) {
             double acc = 0;
             for (int r = tid; r < nr; r += WIN_THREADS) acc += yslot[r] * zslot[r];
             acc = wblock_sum(acc, red);
-            if (tid == 0) A.part_s[t] = acc;
+            if (tid == 0) A.part_s[t] = acc * mirror_weight(v, tc);
         }
         __syncthreads();
         target += gridDim.x;
@@ -1387,9 +1398,10 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                     const double* U = v.arena + sd.work + (long long)(m & 1) * 2 * K;
                     const double* Wv = U + K;
                     const double* c0 = v.arena + tc.c0;
-                    // antisymmetric states: the products act on (y - swap(y of the mirror
-                    // subdomain)) / 2 and likewise b'; y itself is kept for the history and z
-                    const bool anti = v.inst[tc.inst].anti != 0;
+                    // antisymmetric states: on a diagonal subdomain (its own mirror) the
+                    // products act on (y - swap(y)) / 2 and likewise b'; y itself is kept
+                    // for the history and z
+                    const bool anti = diagonal_anti(v, tc);
                     const double *Um = nullptr, *Wm = nullptr, *c0m = nullptr, *bm = nullptr;
                     if (anti) {
                         const SubDev& ms = v.sub[mirror_sid(v, tc)];
@@ -1450,8 +1462,9 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                             a += red[i];
                             b += red[16 + i];
                         }
-                        A.part_s[t] = a;
-                        if (dn) A.part_d[t] = b;
+                        const double w = mirror_weight(v, tc);
+                        A.part_s[t] = a * w;
+                        if (dn) A.part_d[t] = b * w;
                     }
                 }
                 if (!str) continue;
