@@ -57,9 +57,9 @@ KERNEL_FUNCS["k_window_2ph<true>@batched"] = KERNEL_FUNCS["k_window_2ph<true>"]
 KERNEL_FUNCS["k_window_split@batched"] = KERNEL_FUNCS["k_window_split"]
 PROFILED_TRAFFIC = {
     "k_window_fused": ("123b4a784de2ee96", 329.5e6, "profiles/k_window_fused_tise_2e_16sd.md"),
-    "k_window_2ph<false>": ("36eacbc20ac4f33a", 278.4e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
-    "k_window_2ph<true>@batched": ("295b45653b3c50bc", 1.195, "profiles/k_window_2ph_df32_batched_uneven.md"),
-    "k_window_split@batched": ("c9b76ea5b5df2f56", 1.033, "profiles/k_window_split_batched_uneven.md"),
+    "k_window_2ph<false>": ("6fd9a352bcfedf25", 279.0e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
+    "k_window_2ph<true>@batched": ("cbd72ea8633a4ed0", 1.192, "profiles/k_window_2ph_df32_batched_uneven.md"),
+    "k_window_split@batched": ("b4d0cff880fcc2ac", 1.033, "profiles/k_window_split_batched_uneven.md"),
 }
 
 
@@ -117,7 +117,9 @@ def workload_config(name: str, inst) -> dict:
             "subdomains": inst.n_sub, "K_d": inst.K_d, "K": inst.K_d ** inst.n_elec,
             "nodes_per_coord": (inst.n_mid + 2) * inst.q_p, "dt": inst.dt, "mu": str(inst.mu),
             "tol": TOL, "kmax": KMAX, "l2": "flushed (256 MB write) before every step",
-            "parallelism": "replicas (one independent problem per GPU)"}
+            "parallelism": "replicas (one independent problem per GPU)",
+            **({"symmetry": "antisymmetric", "phi0_center": list(inst.phi0_center)}
+               if getattr(inst, "symmetry", "none") == "antisymmetric" else {})}
 
 
 class ClockSampler:
@@ -464,12 +466,19 @@ def main():
                     help="batched workload, mixed precision: window kernel before autotuning (0 automatic, 1 two-phase, "
                          "3 split)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic window plan (no swr_autotune)")
+    ap.add_argument("--antisymmetric", action="store_true",
+                    help="2-electron imaginary-time workloads: the lowest antisymmetric state (initial Gaussian "
+                         "centred at (0.8, -0.8)); the lower subdomain of each mirror pair is not solved")
     ap.add_argument("--sweep", action="store_true",
                     help="imaginary-time workloads: Schwarz convergence over a grid of time steps and Robin "
                          "constants, Robin and classical (Dirichlet) transmission; one JSON line")
     args = ap.parse_args()
     name = args.workload
     inst = workload(name)
+    if args.antisymmetric:
+        if name == BATCHED or inst.n_elec != 2 or inst.mode != "tise":
+            raise SystemExit("--antisymmetric takes a 2-electron imaginary-time workload")
+        inst = inst.replace(symmetry="antisymmetric", phi0_center=(0.8, -0.8))
     if name == BATCHED:
         inst = inst[:args.batch_instances]
         if args.max_steps > 0:
@@ -587,7 +596,8 @@ def main():
     elif args.precision == "mixed":
         # double-single matvec: ~12 FP32 operations per matrix element on the FP32 pipes
         peak = FP32_PEAK_TFLOPS / 6.0
-        kname = "k_window_fused" if main_run["plan"]["variant"] == S.WINDOW_FUSED else "k_window_2ph<true>"
+        kname = {S.WINDOW_FUSED: "k_window_fused", S.WINDOW_SPLIT: "k_window_split"}.get(
+            main_run["plan"]["variant"], "k_window_2ph<true>")
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": "measured FP32 FMA rate of this pool's GB300 (67.7 TFLOP/s) / 6: the "

@@ -1051,7 +1051,9 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
         if (!isfinite(c->res_h[i])) return fail(c, SWR_ENUMERIC, "non-finite residual in instance %zu", i);
         rmax = c->res_h[i] > rmax ? c->res_h[i] : rmax;
         wmax = c->win_h[i] > wmax ? c->win_h[i] : wmax;
-        solves += (long long)c->win_h[i] * c->inst[i].n_sub;
+        // antisymmetric states: the lower subdomain of a mirror pair is not solved
+        const int solved = c->inst[i].anti ? c->inst[i].L * (c->inst[i].L + 1) / 2 : c->inst[i].n_sub;
+        solves += (long long)c->win_h[i] * solved;
     }
     float ms = 0, wms = 0;
     CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
@@ -1065,6 +1067,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
         const double bel = c->tdse ? 16.0 : (c->variant == WIN_FUSED ? 16.0 : 8.0);
         for (size_t sid = 0; sid < c->sub.size(); ++sid) {
             const SubDev& sd = c->sub[sid];
+            if (c->inst[sd.inst].anti && sd.N == 2 && sd.idx[0] > sd.idx[1]) continue;  // mirror image, not solved
             const double K2 = (double)sd.K * sd.K;
             // real time: (1 + fixed-point iterations) complex matvecs with G0 per step
             const double mv = c->tdse ? c->cn_sweeps[sid] : (double)nsolve[sd.inst];
