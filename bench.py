@@ -612,7 +612,9 @@ def main():
     roof["traffic"] = traffic
     roof["traffic_source"] = src
     roof["window_ms_per_launch"] = w_ms / max(w_launch, 1)
-    roof["step_us"] = 1e3 * w_ms / max(1.0, cnt["solves"] / inst.n_sub)
+    # solved subdomains per step (antisymmetric states: one of each mirror pair)
+    n_solved = inst.L * (inst.L + 1) // 2 if getattr(inst, "symmetry", "none") == "antisymmetric" else inst.n_sub
+    roof["step_us"] = 1e3 * w_ms / max(1.0, cnt["solves"] / n_solved)
     launches = int(cnt["kernel_launches"])
 
     # end to end through the public API: setup from host descriptors, assembly,
