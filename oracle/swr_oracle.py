@@ -30,7 +30,7 @@ Schroedinger Equation"), in plain, slow numpy:
   reconstruction ...... Sec. 5.3 (average over the covering subdomains)
   residual ............ Sec. 6.2, Eq. residueRT and Sec. 6.3, Eq. residueIT
 
-Readings where the paper is silent or garbled (each listed in the design doc):
+Readings where the paper is silent or garbled:
   * weak form of -kappa*Lap with the Robin condition (d_n + mu) psi = g gives
     H~ = kappa (K + mu R) + V and a source +kappa*b (imaginary time) or
     -kappa*b (real time), kappa = 1/2 from H0 (Sec. 1.1);

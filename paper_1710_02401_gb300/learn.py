@@ -7,8 +7,8 @@ data (swr_trace_codec: orthonormal polynomials along each edge times in the
 step index), and the solve starts from the decoded prediction.  Training data
 come from the SWR solver itself, on the GPU; training runs on the GPU with
 the library's own forward/backward/Adam kernels.  The zero-guess solve stays
-the fallback and the judge: the residual that decides convergence is the
-same Res(k) of the plain method.
+the fallback and decides the prediction's error: the residual that decides
+convergence is the same Res(k) of the plain method.
 
 Every numerical step runs in libswr.so; this module only arranges the data
 (descriptors, the affine output standardisation folded into the last layer).
