@@ -68,8 +68,8 @@ typedef enum swr_launch_mode {
     SWR_LAUNCH_GRAPH = 0,      /* capture the iteration into a CUDA graph once
                                   per kind (parity of the trace buffers, first
                                   iteration) and replay it: one host launch per
-                                  iteration (if the driver refuses the capture,
-                                  the context launches directly; swr_window_plan
+                                  iteration (if the CUDA driver refuses the
+                                  capture, it launches directly; swr_window_plan
                                   reports which)                                */
     SWR_LAUNCH_DIRECT = 1      /* launch every kernel from the host             */
 } swr_launch_mode;

@@ -1014,7 +1014,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
     const int gp = c->parity, gf = c->k == 0 ? 1 : 0;
     if (c->prob.launch_mode == SWR_LAUNCH_GRAPH && !c->graph_failed && !c->gexec[gp][gf]) {
-        // a capture the driver refuses leaves the context on direct launches
+        // a capture the CUDA driver refuses leaves the context on direct launches
         if (capture_iteration(c, gp, gf) != cudaSuccess) {
             cudaGetLastError();
             c->graph_failed = true;
