@@ -111,16 +111,18 @@ typedef enum swr_tc {
                               constant mu; consistent up to O(1/mu)               */
 } swr_tc;
 
-/* Exchange symmetry of the sought state (Appendix A).  With
- * SWR_SYM_ANTISYMMETRIC (N = 2, imaginary time) every step acts on the
- * antisymmetric part of its input over mirror subdomains: with sigma(i) the
- * subdomain (i2, i1) of subdomain (i1, i2),
- *   v_i <- (v_i - swap(v_sigma(i))) / 2,   swap: coefficient (a, b) -> (b, a),
- * so that psi_sigma(i)(x2, x1) = -psi_i(x1, x2) holds at every step and the
- * iteration reaches the lowest antisymmetric (triplet) state.  Needs mirror
- * subdomains with the same K_d and delta, and an initial Gaussian whose
- * antisymmetric part is not zero (phi0_center off the diagonal); the fused
- * window variant is not available for such instances.                      */
+/* Exchange symmetry of the state (Appendix A).  With SWR_SYM_ANTISYMMETRIC
+ * (N = 2) the initial data is the antisymmetric part of the projected
+ * Gaussian and psi_sigma(i)(x2, x1) = -psi_i(x1, x2) holds at every step,
+ * sigma(i) the subdomain (i2, i1) of subdomain (i1, i2): only one subdomain
+ * of each mirror pair is stepped, the other filled in as its mirror image
+ * (swap: coefficient (a, b) -> (b, a), sign flipped).  In imaginary time the
+ * diagonal subdomains also act on the antisymmetric part of each step's
+ * input, (v - swap(v)) / 2, so the iteration reaches the lowest
+ * antisymmetric (triplet) state.  Needs mirror subdomains with the same K_d
+ * and delta, and an initial Gaussian whose antisymmetric part is not zero
+ * (phi0_center off the diagonal); the fused window variant is not available
+ * for such instances.                                                       */
 typedef enum swr_symmetry {
     SWR_SYM_NONE = 0,
     SWR_SYM_ANTISYMMETRIC = 1

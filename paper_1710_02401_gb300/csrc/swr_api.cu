@@ -231,8 +231,8 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
         if (in.symmetry != SWR_SYM_NONE && in.symmetry != SWR_SYM_ANTISYMMETRIC)
             return fail(c, SWR_EINVAL, "instance %d: unknown symmetry", i);
         if (in.symmetry == SWR_SYM_ANTISYMMETRIC) {
-            if (in.n_elec != 2 || in.mode != SWR_MODE_TISE)
-                return fail(c, SWR_EINVAL, "instance %d: antisymmetric states need N = 2 in imaginary time", i);
+            if (in.n_elec != 2)
+                return fail(c, SWR_EINVAL, "instance %d: antisymmetric states need N = 2", i);
             for (int s = 0; s < in.L * in.L; ++s) {
                 const int m = s / in.L + in.L * (s % in.L);
                 const int ks = in.K_d_per_sub ? in.K_d_per_sub[s] : in.K_d, km = in.K_d_per_sub ? in.K_d_per_sub[m] : in.K_d;

@@ -433,24 +433,24 @@ __global__ void k_energy_reduce(SwrDeviceView v, const double* part, double* ene
 // Antisymmetric states (Appendix A): the lower subdomain (i1 > i2) of each
 // mirror pair is not solved; its iterates of the window are the mirror images
 // of the upper one's, y_sigma(i)^n = -swap(y_i^n) for n = 0..window (swap:
-// coefficient (a, b) -> (b, a)), filled before the traces, the exchange and
-// the energies read them.
+// coefficient (a, b) -> (b, a); both planes of complex iterates), filled
+// before the traces, the exchange and the energies read them.
 __global__ void k_anti_fill(SwrDeviceView v, const int* win) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
     const InstDev& in = v.inst[s.inst];
-    if (!in.anti || s.N != 2 || in.mode != SWR_MODE_TISE) return;
+    if (!in.anti || s.N != 2) return;
     const int loc = sid - in.sub_base, i1 = loc % in.L, i2 = loc / in.L;
     if (i1 <= i2) return;
     const SubDev& ms = v.sub[in.sub_base + i2 + in.L * i1];
-    const int K = s.K, kd = s.kd;
-    const long long total = (long long)(win[s.inst] + 1) * K;
+    const int K = s.K, kd = s.kd, nch = in.mode == SWR_MODE_TDSE ? 2 : 1;
+    const long long total = (long long)(win[s.inst] + 1) * nch * K;
     double* h = v.arena + s.hist;
     const double* hm = v.arena + ms.hist;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const long long n = e / K;
-        const int c = (int)(e - n * K);
-        h[e] = -hm[n * K + c / kd + kd * (c % kd)];
+        const long long row = e / K;  // (step, plane)
+        const int c = (int)(e - row * K);
+        h[e] = -hm[row * K + c / kd + kd * (c % kd)];
     }
 }
 

@@ -49,6 +49,14 @@ __device__ inline double qx_row(const SubDev& s, const double* Xp1, const double
     return acc;
 }
 
+// Antisymmetric states: the lower subdomain (i1 > i2) of a mirror pair is not
+// stepped; its iterates are filled in as the mirror images of the upper one's
+// after the window.
+__device__ inline bool cn_mirror_skip(const SwrDeviceView& v, const SubDev& s) {
+    const InstDev& in = v.inst[s.inst];
+    return in.anti && s.N == 2 && s.idx[0] > s.idx[1];
+}
+
 struct CnBufs {
     long long r, u, x;   // per-subdomain planar vectors (offsets in doubles, 2K each)
 };
@@ -60,7 +68,7 @@ __global__ void k_cn_rhs(SwrDeviceView v, const long long* boff, const int* win_
     const InstDev& in = v.inst[s.inst];
     const int K = s.K, kd = s.kd;
     const int r0 = blockIdx.x * CN_ROWS;
-    if (r0 >= K) return;
+    if (r0 >= K || cn_mirror_skip(v, s)) return;
     extern __shared__ double sm[];
     double* c = sm;               // 2K
     double* X1 = sm + 2 * K;      // kd^2
@@ -107,7 +115,7 @@ __global__ void __launch_bounds__(256) k_cmv(SwrDeviceView v, const long long* b
     const SubDev& s = v.sub[sid];
     const int K = s.K;
     const int r0 = blockIdx.x * MV_ROWS;
-    if (r0 >= K || (need && m >= need[sid])) return;
+    if (r0 >= K || (need && m >= need[sid]) || cn_mirror_skip(v, s)) return;
     extern __shared__ double sm[];
     const double* U = v.arena + boff[3 * sid + 1];
     for (int e = threadIdx.x; e < 2 * K; e += blockDim.x) sm[e] = U[e];
@@ -141,7 +149,7 @@ __global__ void k_cn_update(SwrDeviceView v, const long long* boff, int n, const
     const InstDev& in = v.inst[s.inst];
     const int K = s.K, kd = s.kd;
     const int r0 = blockIdx.x * CN_ROWS;
-    if (r0 >= K || m >= need[sid]) return;
+    if (r0 >= K || m >= need[sid] || cn_mirror_skip(v, s)) return;
     extern __shared__ double sm[];
     double* x = sm;
     double* X1 = sm + 2 * K;
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(256) k_cmv_df32(SwrDeviceView v, const long lo
     const SubDev& s = v.sub[sid];
     const int K = s.K, ld = df32_ld(K);
     const int r0 = blockIdx.x * MV_ROWS;
-    if (r0 >= K || (need && m >= need[sid])) return;
+    if (r0 >= K || (need && m >= need[sid]) || cn_mirror_skip(v, s)) return;
     extern __shared__ float smf[];
     float* urh = smf;           // ld each
     float* url = smf + ld;
@@ -291,6 +299,7 @@ __global__ void k_split_c_df32(SwrDeviceView v) {
 __global__ void k_cn_finish(SwrDeviceView v, const long long* boff, int n) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
+    if (cn_mirror_skip(v, s)) return;
     const int K = s.K;
     const double* X = v.arena + boff[3 * sid + 2];
     const double* cn = v.arena + s.hist + (long long)n * 2 * K;

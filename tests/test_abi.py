@@ -192,7 +192,7 @@ def test_transmission_and_symmetry_requests_on_host(lib):
     assert status(anti, S.PREC_MIXED) == S.SWR_OK                              # split window
     assert status(anti, S.PREC_MIXED, S.WINDOW_FUSED) == S.SWR_EINVAL          # not the fused one
     assert status(P.tise_1d_two_subdomains().replace(symmetry="antisymmetric")) == S.SWR_EINVAL  # N = 1
-    assert status(P.small_tdse_2d().replace(symmetry="antisymmetric")) == S.SWR_EINVAL         # real time
+    assert status(P.small_tdse_2d().replace(symmetry="antisymmetric")) == S.SWR_OK             # real time too
     kd = [8, 9, 8, 9]  # subdomain (1, 0) and its mirror (0, 1) differ
     assert status(P.small_tise_2d(L=2, K_d=8).replace(K_d=kd, symmetry="antisymmetric")) == S.SWR_EINVAL
     assert status(P.small_tise_2d(L=2, K_d=8).replace(K_d=[8, 9, 9, 8], symmetry="antisymmetric")) == S.SWR_OK

@@ -189,6 +189,14 @@ def test_parity_antisymmetric_states(swr_mod, precision):
     assert 9 * s.window_plan()["tasks"] == 6 * sym.window_plan()["tasks"]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_parity_antisymmetric_real_time(swr_mod, precision):
+    # real time keeps the antisymmetry: one subdomain of each mirror pair is
+    # stepped, the other filled in as its mirror image after the window
+    inst = P.small_tdse_2d().replace(symmetry="antisymmetric", phi0_center=(0.8, -0.8))
+    _compare(swr_mod, inst, kmax=3, precision=precision)
+
+
 def test_antisymmetric_harmonic_pair_reaches_the_triplet_level(swr_mod):
     # two non-interacting electrons in a harmonic well: lowest antisymmetric
     # level 1/2 + 3/2 = 2 (the symmetric ground state is 1)
