@@ -16,9 +16,13 @@ from . import problems as P
 
 
 def instance_cost(inst: P.Instance) -> float:
-    """Bytes of step matrices one time step streams (sum of K^2 over subdomains)."""
+    """Bytes of step matrices one time step streams (sum of K^2 over the stepped
+    subdomains; an antisymmetric 2-electron instance steps only the subdomains
+    (i1, i2) with i1 <= i2, sid = i1 + L i2, the others being mirror images)."""
     kds = inst.K_d if isinstance(inst.K_d, (list, tuple)) else [inst.K_d] * inst.n_sub
-    return float(sum((kd ** inst.n_elec) ** 2 for kd in kds))
+    anti = getattr(inst, "symmetry", "none") == "antisymmetric" and inst.n_elec == 2
+    return float(sum((kd ** inst.n_elec) ** 2 for sid, kd in enumerate(kds)
+                     if not (anti and sid % inst.L > sid // inst.L)))
 
 
 def shard(instances: Sequence[P.Instance], rank: int, world: int) -> List[int]:

@@ -55,3 +55,14 @@ def test_shard_edge_cases():
     assert D.shard([], 0, 2) == []
     with pytest.raises(ValueError):
         D.shard(insts, 2, 2)
+
+
+def test_cost_of_antisymmetric_instances_counts_the_stepped_subdomains():
+    from paper_1710_02401_gb300 import dist as D
+    from paper_1710_02401_gb300 import problems as P
+    inst = P.small_tise_2d(L=3).replace(K_d=[6, 7, 8, 7, 6, 9, 8, 9, 5])  # mirror pairs (1,3), (2,6), (5,7) equal
+    sym = D.instance_cost(inst)
+    anti = D.instance_cost(inst.replace(symmetry="antisymmetric"))
+    K2 = [(kd * kd) ** 2 for kd in inst.K_d]
+    assert sym == sum(K2)
+    assert anti == K2[0] + K2[4] + K2[8] + K2[3] + K2[6] + K2[7]  # diagonal and upper (i1 <= i2) subdomains
