@@ -29,6 +29,7 @@ Schroedinger Equation"), in plain, slow numpy:
   inner NGF stop ...... Sec. 5.2 (||phi^{n+1} - phi^n|| <= delta)
   reconstruction ...... Sec. 5.3 (average over the covering subdomains)
   residual ............ Sec. 6.2, Eq. residueRT and Sec. 6.3, Eq. residueIT
+  interface mismatch .. Sec. 4.1, Eq. CVTOT and Sec. 4.2, Eq. CVTOT2
 
 Readings where the paper is silent or garbled:
   * weak form of -kappa*Lap with the Robin condition (d_n + mu) psi = g gives
@@ -46,6 +47,8 @@ Readings where the paper is silent or garbled:
     this reading the local Robin eigenproblem is a fixed point of the scheme;
   * Res(k)^2 = sum_n dt sum_i sum_{Gamma-nodes} w |u_i^(k) - u_i^(k-1)|^2,
     with u^(0) = 0, over the interior interfaces only;
+  * CVTOT(k)^2 = sum_n dt (sum_{(i,j)} ||psi_i^(k) - psi_j^(k)||_{Gamma_{i;j}})^2
+    over n = 1..W, Gamma_{i;j} = interface nodes of Omega_i in closure(Omega_j);
   * field e(t) = E0 sin^2(pi t/T) sin(omega t + phase) on [0, T], 0 after.
 
 Parity pins: see tests/test_oracle_pins.py (closed forms, invariants, brute
@@ -417,6 +420,7 @@ class IterRecord:
     k: int
     res: float
     n_win: int
+    cvtot: Optional[float] = None
     energy: Optional[float] = None
     norm2: Optional[float] = None
     dipole: Optional[float] = None
@@ -461,6 +465,53 @@ def reconstruct_at(inst, locs, coeffs, X):
         js = [j for j in range(inst.n_sub) if contains_closed(inst, j, x)]
         out[p] = sum(locs[j].basis.values(x[None, :])[0] @ coeffs[j] for j in js) / len(js)
     return out
+
+
+def schwarz_residual(locs, dt: float, u_hist, u_prev) -> float:
+    """Res(k) of Eq. residueIT (Sec. 6.3) / Eq. residueRT (Sec. 6.2): the
+    L2(0,T) norm in time of the sum over subdomains of the L2 norm on the
+    interior interfaces of u_i^(k) - u_i^(k-1).
+
+    u_hist[i]: (W+1, G_i) own traces of iteration k at steps 0..W; u_prev the
+    same for iteration k-1 (None for k = 1: u^(0) = 0).  Time integral by the
+    rectangle rule with weight dt at t_1..t_max(W, W'); a window shorter than
+    the other is held at its last value.  Interface integral by the surface
+    quadrature weights of the Gamma nodes."""
+    n_done = u_hist[0].shape[0] - 1
+    n_cmp = max(n_done, 0 if u_prev is None else u_prev[0].shape[0] - 1)
+    r2 = 0.0
+    for i, loc in enumerate(locs):
+        w = loc.gamma.w
+        for n in range(1, n_cmp + 1):
+            a = u_hist[i][min(n, n_done)]
+            b = np.zeros_like(a) if u_prev is None else u_prev[i][min(n, u_prev[i].shape[0] - 1)]
+            r2 += dt * float(np.sum(w * np.abs(a - b) ** 2))
+    return math.sqrt(r2)
+
+
+def interface_mismatch(locs, ops: "TraceOps", hist, dt: float) -> float:
+    """CVTOT of Eq. CVTOT (Sec. 4.1) and Eq. CVTOT2 (Sec. 4.2): at each time,
+    the sum over ordered pairs (i, j) of the L2(Gamma_{i;j}) norm of
+    psi_i^(k) - psi_j^(k), Gamma_{i;j} the part of the interior boundary of
+    Omega_i inside closure(Omega_j); then the L2(0,T) norm of that sum.
+
+    hist: iterates c^n of iteration k for n = 0..W (list over steps of lists
+    over subdomains; the normalised state in imaginary time).  Reading: the
+    same rectangle rule in time as Res(k) (weight dt at t_1..t_W), the surface
+    quadrature of the Gamma nodes on each Gamma_{i;j}.  Unlike Res(k) it does
+    not tend to 0: at the discrete fixed point psi_i and psi_j still differ on
+    Gamma_{i;j} by the discretisation error."""
+    total = 0.0
+    for n in range(1, len(hist)):
+        coeffs = hist[n]
+        c_n = 0.0
+        for i, (per_j, _cnt) in enumerate(ops.ops):
+            loc = locs[i]
+            for j, (rows, vals, _ders) in per_j.items():
+                diff = loc.own_vals[rows] @ coeffs[i] - vals @ coeffs[j]
+                c_n += math.sqrt(float(np.sum(loc.gamma.w[rows] * np.abs(diff) ** 2)))
+        total += dt * c_n * c_n
+    return math.sqrt(total)
 
 
 def assemble(inst) -> List[Local]:
@@ -581,16 +632,8 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
         g_hist_steps = [ops.robin_data(h) for h in hist_raw]
         g_hist = [np.array([g_hist_steps[n][i] for n in range(len(hist))]) for i in range(S)]
         # residual against the previous iteration (hold-last beyond a window)
-        n_cmp = max(n_done, 0 if u_prev is None else u_prev[0].shape[0] - 1)
-        r2 = 0.0
-        for i in range(S):
-            w = locs[i].gamma.w
-            for n in range(1, n_cmp + 1):
-                a = u_hist[i][min(n, n_done)]
-                b = np.zeros_like(a) if u_prev is None else u_prev[i][min(n, u_prev[i].shape[0] - 1)]
-                r2 += dt * float(np.sum(w * np.abs(a - b) ** 2))
-        res = math.sqrt(r2)
-        rec = IterRecord(k=k, res=res, n_win=n_done)
+        res = schwarz_residual(locs, dt, u_hist, u_prev)
+        rec = IterRecord(k=k, res=res, n_win=n_done, cvtot=interface_mismatch(locs, ops, hist, dt))
         if tdse:
             rec.norm2 = pou_norm2(locs, coeffs)
             rec.dipole = float(np.real(sum(np.vdot(c, l.Qchi @ c) for l, c in zip(locs, coeffs)))) / rec.norm2

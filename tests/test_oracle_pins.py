@@ -417,3 +417,105 @@ def test_real_time_keeps_antisymmetric_states_antisymmetric():
         b = r.locs[j].basis.values(X[:, ::-1]) @ r.coeffs[j]
         assert np.abs(a + b).max() <= 1e-8 * np.abs(a).max()
     assert r.records[-1].norm2 > 0.1
+
+
+# ------------------------------------------------ Res(k) and CVTOT (Sec. 4, 6)
+#
+# A 2 x 2 decomposition of [-4, 4]^2 (overlap 1, 11 Gaussians of exponent 2
+# per coordinate, centres 0.5 apart) where the Gaussian exp(-2 |x|^2) is a
+# basis function of every subdomain: it is projected exactly, and with no
+# kinetic term, no potential and no Robin source the implicit Euler step is
+# the identity, so every iterate of every Schwarz iteration is that Gaussian.
+# Interface integrals of it are erf closed forms.
+
+_PIN_DELTA = 2.0
+
+
+def _pin_instance(**kw):
+    base = P.Instance(n_elec=2, box=(-4.0, 4.0), L=2, overlap=1.0, K_d=11, delta=_PIN_DELTA, q_p=12, n_mid=3,
+                      nuclei=(), ee_coef=0.0, harmonic=0.0, kinetic=0.0, mu=10.0, mode=P.TISE,
+                      normalize=False, dt=0.37, n_steps=5, ngf_tol=0.0, phi0_gamma=_PIN_DELTA,
+                      phi0_center=(0.0, 0.0))
+    return base.replace(**kw) if kw else base
+
+
+def _edge_integral(p, lo, hi, d=_PIN_DELTA):
+    """int_lo^hi exp(-2 d (p^2 + x^2)) dx: |exp(-d |x|^2)|^2 along the line x_e = p."""
+    c = 2.0 * d
+    return math.exp(-c * p * p) * 0.5 * math.sqrt(math.pi / c) * (erf(math.sqrt(c) * hi) - erf(math.sqrt(c) * lo))
+
+
+def _pin_locs(inst):
+    locs = O.assemble(inst)
+    for l in locs:  # the raw Gaussians are kept (Cholesky accepted): basis functions are exact Gaussians
+        assert all(t is None for t in l.basis.T)
+    return locs
+
+
+def test_residual_closed_form_through_the_schwarz_loop():
+    inst = _pin_instance()
+    r = O.run_swr(inst, kmax=2, tol=0.0)
+    # every subdomain has two interior edges of length 5 at distance 0.5 from the origin
+    edge = _edge_integral(0.5, -4.5, 0.5)
+    want = math.sqrt(inst.n_steps * inst.dt * 8.0 * edge)
+    assert abs(r.records[0].res - want) <= 1e-12 * want, (r.records[0].res, want)
+    assert r.records[1].res <= 1e-12 * want  # the same iterates again
+    # every local solution is the same function; CVTOT sums per-pair norms of the
+    # rounding of c0 = A^-1 c~ (kappa(A) eps ~ 1e-13 per coefficient)
+    assert r.records[0].cvtot <= 1e-10 * want
+
+
+def test_residual_holds_the_shorter_window_at_its_last_value():
+    inst = _pin_instance()
+    locs = _pin_locs(inst)
+    u0 = [l.own_vals @ l.c0 for l in locs]  # exp(-2|x|^2) at each subdomain's interface nodes
+    edge8 = 8.0 * _edge_integral(0.5, -4.5, 0.5)
+    rng = np.random.default_rng(7)
+    dt = 0.23
+    for W, Wp in ((4, 7), (7, 3), (5, 5)):
+        f = rng.normal(size=W + 1)
+        g = rng.normal(size=Wp + 1)
+        u_k = [np.outer(f, u) for u in u0]
+        u_km1 = [np.outer(g, u) for u in u0]
+        want2 = edge8 * sum(dt * (f[min(n, W)] - g[min(n, Wp)]) ** 2 for n in range(1, max(W, Wp) + 1))
+        got = O.schwarz_residual(locs, dt, u_k, u_km1)
+        assert abs(got - math.sqrt(want2)) <= 1e-12 * math.sqrt(want2), (W, Wp, got, math.sqrt(want2))
+    # first iteration: u^(0) = 0
+    f = rng.normal(size=6)
+    got = O.schwarz_residual(locs, dt, [np.outer(f, u) for u in u0], None)
+    want = math.sqrt(edge8 * dt * float(np.sum(f[1:] ** 2)))
+    assert abs(got - want) <= 1e-12 * want
+
+
+def test_interface_mismatch_closed_form_of_pairwise_norms():
+    # psi_0 = f_n exp(-2|x|^2) on the lower-left subdomain, psi = 0 on the others:
+    # the mismatch on Gamma_{i;j} is psi_0 wherever 0 is one of the pair, so the
+    # pair norms are square roots of sums of edge integrals:
+    #   (0,(1,0)), (0,(0,1)), ((1,0),0), ((0,1),0): a full edge + a corner band
+    #   (0,(1,1)), ((1,1),0): two corner bands
+    inst = _pin_instance()
+    locs = _pin_locs(inst)
+    ops = O.TraceOps(inst, locs)
+    e0 = np.zeros(locs[0].basis.K)
+    e0[9 + 11 * 9] = 1.0  # centre (0, 0) of subdomain 0 (centres -4.5 .. 0.5)
+    rng = np.random.default_rng(11)
+    f = rng.normal(size=7)
+    hist = [[f[n] * e0] + [np.zeros(l.basis.K) for l in locs[1:]] for n in range(7)]
+    A = _edge_integral(0.5, -4.5, 0.5)
+    B = _edge_integral(0.5, -0.5, 0.5)
+    C = 4.0 * math.sqrt(A + B) + 2.0 * math.sqrt(2.0 * B)
+    dt = 0.41
+    want = C * math.sqrt(dt * float(np.sum(f[1:] ** 2)))
+    got = O.interface_mismatch(locs, ops, hist, dt)
+    assert abs(got - want) <= 1e-11 * want, (got, want)
+
+
+def test_interface_mismatch_stays_at_the_discretisation_error_when_res_vanishes():
+    # Eq. CVTOT2 measures psi_i - psi_j on the interfaces; at the converged
+    # Schwarz iterate those still differ by the discretisation error, while
+    # Res(k) (successive iterates) goes to 0
+    r = O.run_swr(P.harmonic_1d_two_subdomains(), kmax=50, tol=1e-10)
+    assert r.converged
+    c = [rec.cvtot for rec in r.records]
+    assert c[-1] > 1e3 * r.records[-1].res
+    assert abs(c[-1] - c[-2]) <= 1e-6 * c[-1]
