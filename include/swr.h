@@ -180,6 +180,11 @@ typedef struct swr_problem {
     int                 rows_per_task;   /* window row-task size: 0 (automatic) or
                                             8..256; swr_autotune may change it   */
     int                 launch_mode;     /* swr_launch_mode                        */
+    long long           spin_limit;      /* polls (about 64 ns each) before a device-side
+                                            wait of the window kernels gives up and
+                                            swr_step returns SWR_ETIMEOUT; 0 selects
+                                            the default 2^24 (about one second);
+                                            swr_set_spin_limit changes it later      */
 } swr_problem;
 
 typedef struct swr_ctx swr_ctx;
@@ -191,6 +196,7 @@ typedef struct swr_iter_report {
     int       window_max;        /* longest time window of this iteration          */
     long long subdomain_solves;  /* local step solves done in this iteration       */
     double    seconds;           /* device time of the iteration (CUDA events)     */
+    double    cvtot;             /* max over instances of CVTOT(k) (SWR_FIELD_CVTOT) */
 } swr_iter_report;
 
 typedef struct swr_report {
@@ -226,6 +232,13 @@ swr_status swr_step(swr_ctx* ctx, swr_iter_report* rep);
  * Returns SWR_ENOTCONV (report filled) when tol is not reached. */
 swr_status swr_iterate(swr_ctx* ctx, double tol, int kmax, swr_report* rep, double* res_history);
 
+/* Changes the number of polls after which a device-side wait of the window
+ * kernels gives up (swr_problem.spin_limit; 0 restores the default).  A step
+ * that gives up returns SWR_ETIMEOUT and leaves the Robin data of that
+ * iteration unusable: restore a checkpoint (swr_traces SET) before the next
+ * swr_step to continue from a known state.                                  */
+swr_status swr_set_spin_limit(swr_ctx* ctx, long long polls);
+
 /* Interface-trace window of the last iteration (checkpoint / warm start). */
 typedef enum swr_dir { SWR_GET = 0, SWR_SET = 1 } swr_dir;
 typedef struct swr_trace_view {
@@ -250,7 +263,7 @@ typedef enum swr_field {
     SWR_FIELD_TRACE_BYTES = 8,  /* size_t: bytes of the swr_traces window              */
     SWR_FIELD_NODE_COUNTS = 9,  /* int[3 * n_sub_total]: per subdomain (q, n_gamma, K) */
     SWR_FIELD_K_MAX = 10,       /* int: Schwarz iterations done so far                 */
-    SWR_FIELD_COUNTERS = 11     /* double[10], cumulative since swr_setup:
+    SWR_FIELD_COUNTERS = 11,    /* double[10], cumulative since swr_setup:
                                    [0] ms inside the time-window kernel (CUDA events on
                                        the context stream, one pair per launch),
                                    [1] launches of the time-window kernel,
@@ -264,6 +277,15 @@ typedef enum swr_field {
                                    [5] local step solves,
                                    [6] ms of swr_assemble (events), [7] ms of swr_step,
                                    [8] host->device bytes copied, [9] device->host bytes */
+    SWR_FIELD_CVTOT = 12        /* double[n_instances]: interface mismatch of the last
+                                   iteration, Eq. CVTOT (Sec. 4.1) / Eq. CVTOT2 (Sec. 4.2):
+                                   the L2 norm in time (rectangle rule, weight dt at
+                                   t_1..t_W) of the sum over ordered subdomain pairs (i, j)
+                                   of ||psi_i - psi_j||_{L2(Gamma_ij)}, Gamma_ij the
+                                   interface nodes of Omega_i inside closure(Omega_j), psi
+                                   the normalised state.  Unlike Res(k) it does not tend to
+                                   0: at the converged iterate it is the discretisation
+                                   mismatch of neighbouring local solutions              */
 } swr_field;
 swr_status swr_get(swr_ctx* ctx, int field, void* host, size_t bytes);
 
@@ -291,9 +313,10 @@ swr_status swr_trace_encode(swr_ctx* ctx, float* code_dev);
 swr_status swr_trace_decode_set(swr_ctx* ctx, const float* code_dev);
 
 /* Small BF16 multilayer perceptron trained with its own kernels (tanh hidden
- * layers, identity output, mean squared error, Adam); products on the tensor
- * cores (mma.sync m16n8k16, BF16 inputs, FP32 accumulation), FP32 master
- * weights.  Parameters: for each layer l, W_l [d_l x d_{l+1}] row-major then
+ * layers, identity output, mean squared error, Adam); products on the
+ * 5th-generation tensor cores (tcgen05.mma kind::f16, BF16 operands staged in
+ * shared memory, FP32 accumulator in tensor memory read back by tcgen05.ld),
+ * FP32 master weights.  Parameters: for each layer l, W_l [d_l x d_{l+1}] row-major then
  * b_l [d_{l+1}], d = (n_in, width x n_hidden, n_out).  x, y, t are DEVICE
  * arrays [batch x dim] row-major FP32.  Not part of the paper. */
 typedef struct swr_mlp swr_mlp;
@@ -322,8 +345,13 @@ const char* swr_mlp_last_error(const swr_mlp* mlp);
  * first call before any stream capture.  All calls share the array: calls
  * that overlap on the GPU (other streams, other contexts) race and must be
  * serialised by the caller.  Nothing in the array needs clearing: every call
- * overwrites all of the scratch it reads.  Synchronises the context stream.
- * Returns SWR_ESTATE before the first swr_step.  The result equals
+ * overwrites all of the scratch it reads.  The device address is cached per
+ * CUDA context: after cudaDeviceReset (or any other teardown of a device's
+ * primary context) the next call resolves it again in the new context.
+ * Synchronises the context stream.  Returns SWR_ESTATE unless a swr_step has
+ * completed since the last swr_assemble or swr_traces(SET) (a restored state
+ * has no residual of its own), or after a swr_step that failed; SWR_EINVAL
+ * when n differs from the number of instances.  The result equals
  * swr_get(SWR_FIELD_RES) of the same iteration. */
 swr_status swr_residual_noalloc(swr_ctx* ctx, double* res_host, size_t n);
 

@@ -33,7 +33,8 @@ extern const int kAssembleLaunchesFixed, kStepLaunches;
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
                         int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax,
-                        bool any_anti);
+                        bool any_anti, double* d_cv_part, double* d_cvtot);
+size_t cvtot_part_doubles(int n_inst);
 cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
                           int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
                           double* psi_out, const long long* psi_off, size_t smem);
@@ -49,7 +50,7 @@ using namespace swr;
 static const int GJ_NB_HOST = 32;     // Gauss-Jordan block (matches swr_assemble.cu)
 static const int RES_BLOCKS = 8;      // residual partial blocks per subdomain
 static const double ORTH_TAU_DEFAULT = 1e-12;  // basis reduction threshold when an instance gives 0
-static const long long SPIN_LIMIT = 1LL << 24;  // polls (x ~64 ns) before a barrier gives up
+static const long long SPIN_LIMIT = 1LL << 24;  // default polls (x ~64 ns) before a device-side wait gives up
 
 struct swr_ctx {
     std::string err;
@@ -111,6 +112,7 @@ struct swr_ctx {
     SplitQueue* d_queue = nullptr;
     int* d_qlist = nullptr;
     double *d_res_part = nullptr, *d_res = nullptr, *d_epart = nullptr, *d_energy = nullptr, *d_norm2 = nullptr;
+    double *d_cv_part = nullptr, *d_cvtot = nullptr;
     double* d_psi = nullptr;
     long long* d_psi_off = nullptr;
     cudaStream_t stream = nullptr;
@@ -118,9 +120,11 @@ struct swr_ctx {
     // state
     bool assembled = false;
     int k = 0, parity = 0;
+    bool step_done = false;       // a swr_step has completed since the last assembly or trace restore
+    long long spin_limit = SPIN_LIMIT;
     int grid = 0;
     size_t win_smem = 0;
-    std::vector<double> res_h, energy_h, norm2_h;
+    std::vector<double> res_h, energy_h, norm2_h, cvtot_h;
     std::vector<int> win_h, win_prev_h;
     std::vector<int> win_pp_h;  // windows of the iteration before the last one
     // counters (see SWR_FIELD_COUNTERS)
@@ -209,6 +213,7 @@ static void plan_cn_iterations(swr_ctx* c, int nmax) {
 
 static swr_status validate(swr_ctx* c, const swr_problem* p) {
     if (!p || p->n_instances < 1 || !p->instances) return fail(c, SWR_EINVAL, "empty problem");
+    if (p->spin_limit < 0) return fail(c, SWR_EINVAL, "spin_limit must be >= 0 (0: default)");
     int mode0 = p->instances[0].mode;
     for (int i = 0; i < p->n_instances; ++i) {
         const swr_instance& in = p->instances[i];
@@ -611,7 +616,8 @@ static void plan(swr_ctx* c) {
 struct AuxPlan {
     size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, cta0, tc, scal, alive, own,
         ctal, wfix, snorm, sums_s, sums_d,
-        n_active, win, win_prev, bar, queue, qlist, cnneed, res_part, res, epart, energy, norm2, dipole, boff, psi, psi_off, total;
+        n_active, win, win_prev, bar, queue, qlist, cnneed, res_part, res, cv_part, cvtot, epart, energy, norm2, dipole, boff,
+        psi, psi_off, total;
 };
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 static AuxPlan aux_plan(const swr_ctx* c) {
@@ -646,6 +652,8 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.qlist = o; o = al256(o + 2 * nt * sizeof(int));
     a.res_part = o; o = al256(o + ns * RES_BLOCKS * sizeof(double));
     a.res = o; o = al256(o + ni * sizeof(double));
+    a.cv_part = o; o = al256(o + cvtot_part_doubles((int)ni) * sizeof(double));
+    a.cvtot = o; o = al256(o + ni * sizeof(double));
     a.epart = o; o = al256(o + 3 * ns * sizeof(double));
     a.energy = o; o = al256(o + ni * sizeof(double));
     a.norm2 = o; o = al256(o + ni * sizeof(double));
@@ -795,6 +803,8 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->d_qlist = (int*)(b + a.qlist);
     c->d_res_part = (double*)(b + a.res_part);
     c->d_res = (double*)(b + a.res);
+    c->d_cv_part = (double*)(b + a.cv_part);
+    c->d_cvtot = (double*)(b + a.cvtot);
     c->d_epart = (double*)(b + a.epart);
     c->d_energy = (double*)(b + a.energy);
     c->d_norm2 = (double*)(b + a.norm2);
@@ -852,6 +862,8 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     if (c->grid > c->bps * c->nsm)
         return fail(c, SWR_EINVAL, "window grid of %d CTAs exceeds %d resident CTAs", c->grid, c->bps * c->nsm);
     c->res_h.assign(c->inst.size(), 0.0);
+    c->cvtot_h.assign(c->inst.size(), 0.0);
+    c->spin_limit = p->spin_limit > 0 ? p->spin_limit : SPIN_LIMIT;
     c->energy_h.assign(c->inst.size(), 0.0);
     c->norm2_h.assign(c->inst.size(), 0.0);
     c->win_h.assign(c->inst.size(), 0);
@@ -905,6 +917,8 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     c->parity = 0;
     CU(cudaMemsetAsync(c->d_win_prev, 0, c->inst.size() * sizeof(int), c->stream));
     c->win_prev_h.assign(c->inst.size(), 0);
+    c->win_pp_h.assign(c->inst.size(), 0);
+    c->step_done = false;
     return SWR_OK;
 }
 
@@ -940,7 +954,7 @@ static SweepArgs sweep_args(swr_ctx* c) {
     a.bar = c->d_bar;
     a.q = c->d_queue;
     a.q_list = c->d_qlist;
-    a.spin_limit = SPIN_LIMIT;
+    a.spin_limit = c->spin_limit;
     a.stage_floats = c->stage_floats;
     a.n_stages = c->n_stages;
     return a;
@@ -969,7 +983,8 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
     }
     if (e == cudaSuccess)
         e = launch_post(view(c), st, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
-                        c->d_res_part, RES_BLOCKS, c->d_res, c->cap, c->max_K, c->max_kd, c->max_q, c->any_anti);
+                        c->d_res_part, RES_BLOCKS, c->d_res, c->cap, c->max_K, c->max_kd, c->max_q, c->any_anti,
+                        c->d_cv_part, c->d_cvtot);
     if (e == cudaSuccess)
         e = launch_energy(view(c), st, c->d_win, c->d_snorm, c->cap, c->d_epart, c->d_energy, c->d_norm2,
                           c->d_dipole, c->d_psi, c->d_psi_off, c->energy_smem);
@@ -1011,6 +1026,7 @@ static cudaError_t capture_iteration(swr_ctx* c, int p, int f) {
 extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     if (!c) return fail(nullptr, SWR_EINVAL, "ctx is NULL");
     if (!c->assembled) return fail(c, SWR_ESTATE, "swr_step before swr_assemble");
+    c->step_done = false;  // set again once this iteration has completed without error
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
     const int gp = c->parity, gf = c->k == 0 ? 1 : 0;
     if (c->prob.launch_mode == SWR_LAUNCH_GRAPH && !c->graph_failed && !c->gexec[gp][gf]) {
@@ -1035,7 +1051,8 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     CU(cudaMemcpyAsync(c->energy_h.data(), c->d_energy, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(c->norm2_h.data(), c->d_norm2, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(c->dipole_h.data(), c->d_dipole, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    c->counters[9] += (double)(ni * (4 * sizeof(double) + sizeof(int)));
+    CU(cudaMemcpyAsync(c->cvtot_h.data(), c->d_cvtot, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    c->counters[9] += (double)(ni * (5 * sizeof(double) + sizeof(int)));
     swr_status st = check_err(c);
     if (st != SWR_OK) return st;
     // the current window becomes the previous one for the next iteration
@@ -1044,12 +1061,13 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     c->win_prev_h = c->win_h;
     c->k += 1;
     c->parity ^= 1;
-    double rmax = 0;
+    double rmax = 0, cmax = 0;
     int wmax = 0;
     long long solves = 0;
     for (size_t i = 0; i < ni; ++i) {
         if (!isfinite(c->res_h[i])) return fail(c, SWR_ENUMERIC, "non-finite residual in instance %zu", i);
         rmax = c->res_h[i] > rmax ? c->res_h[i] : rmax;
+        cmax = c->cvtot_h[i] > cmax ? c->cvtot_h[i] : cmax;
         wmax = c->win_h[i] > wmax ? c->win_h[i] : wmax;
         // antisymmetric states: the lower subdomain of a mirror pair is not solved
         const int solved = c->inst[i].anti ? c->inst[i].L * (c->inst[i].L + 1) / 2 : c->inst[i].n_sub;
@@ -1088,7 +1106,9 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
         rep->window_max = wmax;
         rep->subdomain_solves = solves;
         rep->seconds = ms * 1e-3;
+        rep->cvtot = cmax;
     }
+    c->step_done = true;
     return SWR_OK;
 }
 
@@ -1221,7 +1241,7 @@ extern "C" swr_status swr_field_bytes(swr_ctx* c, int field, size_t* bytes) {
     const size_t ni = c->inst.size(), ns = c->sub.size();
     const int cx = c->tdse ? 2 : 1;
     switch (field) {
-        case SWR_FIELD_ENERGY: case SWR_FIELD_NORM2: case SWR_FIELD_DIPOLE: case SWR_FIELD_RES:
+        case SWR_FIELD_ENERGY: case SWR_FIELD_NORM2: case SWR_FIELD_DIPOLE: case SWR_FIELD_RES: case SWR_FIELD_CVTOT:
             *bytes = ni * sizeof(double); return SWR_OK;
         case SWR_FIELD_WINDOW: *bytes = ni * sizeof(int); return SWR_OK;
         case SWR_FIELD_PSI_NODES: *bytes = (size_t)c->psi_total * cx * sizeof(double); return SWR_OK;
@@ -1252,6 +1272,7 @@ extern "C" swr_status swr_get(swr_ctx* c, int field, void* host, size_t bytes) {
         case SWR_FIELD_ENERGY: memcpy(host, c->energy_h.data(), need); return SWR_OK;
         case SWR_FIELD_NORM2: memcpy(host, c->norm2_h.data(), need); return SWR_OK;
         case SWR_FIELD_RES: memcpy(host, c->res_h.data(), need); return SWR_OK;
+        case SWR_FIELD_CVTOT: memcpy(host, c->cvtot_h.data(), need); return SWR_OK;
         case SWR_FIELD_WINDOW: memcpy(host, c->win_h.data(), need); return SWR_OK;
         case SWR_FIELD_DIPOLE: memcpy(host, c->dipole_h.data(), need); return SWR_OK;
         case SWR_FIELD_K_MAX: memcpy(host, &c->k, sizeof(int)); return SWR_OK;
@@ -1335,13 +1356,22 @@ extern "C" swr_status swr_traces(swr_ctx* c, int dir, swr_trace_view* view_) {
     CU(cudaMemcpyAsync(c->d_win_prev, c->win_prev_h.data(), ni * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     if (c->k == 0) c->k = 1;  // the next residual compares against the restored traces
+    c->step_done = false;     // the restored state has no residual of its own until the next swr_step
+    return SWR_OK;
+}
+
+extern "C" swr_status swr_set_spin_limit(swr_ctx* c, long long polls) {
+    if (!c) return fail(nullptr, SWR_EINVAL, "ctx is NULL");
+    if (polls < 0) return fail(c, SWR_EINVAL, "polls must be >= 0 (0: default)");
+    c->spin_limit = polls > 0 ? polls : SPIN_LIMIT;
+    drop_graphs(c);  // captured iterations carry the old limit in their kernel arguments
     return SWR_OK;
 }
 
 // Internal accessor for the allocation-free residual entry point (swr_noalloc.cu).
 namespace swr {
 bool residual_inputs(swr_ctx* c, ResidualInputs* r) {
-    if (!c || !c->assembled || c->k < 1) return false;
+    if (!c || !c->assembled || c->k < 1 || !c->step_done) return false;
     r->v = view(c);
     r->stream = c->stream;
     r->k = c->k;

@@ -6,6 +6,7 @@
 // window-length arrays and the per-instance result -- in one file-scope
 // __device__ array instead of the context's workspace.  It exists for callers
 // that must not allocate device memory at the point of the call.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <mutex>
 #include <stdio.h>
@@ -21,10 +22,46 @@ using namespace swr;
 
 static __device__ __align__(256) double g_noalloc_scratch[SWR_NOALLOC_SCRATCH_DOUBLES];
 
-// Device address of g_noalloc_scratch, resolved once per device (the host-side
-// name is only a stand-in and must never be passed to a kernel).
+// Device address of g_noalloc_scratch (the host-side name is only a stand-in
+// and must never be passed to a kernel), resolved once per device and CUDA
+// context: the unique id of the current context is kept beside the address,
+// so that after cudaDeviceReset (a new primary context) the address is
+// resolved again instead of reusing one from the destroyed context.  The
+// context id comes from the driver through the runtime's entry-point query
+// (no link dependency on the driver library).
 static std::mutex g_noalloc_mutex;
 static double* g_noalloc_ptr[64] = {nullptr};
+static unsigned long long g_noalloc_ctx[64] = {0};
+
+typedef CUresult (*PFN_ctx_get_current)(CUcontext*);
+typedef CUresult (*PFN_ctx_get_id)(CUcontext, unsigned long long*);
+
+// Unique id of the current CUDA context, 0 when it cannot be read.
+static unsigned long long current_context_id() {
+    static PFN_ctx_get_current get_current = nullptr;
+    static PFN_ctx_get_id get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_current = (PFN_ctx_get_current)f1;
+            get_id = (PFN_ctx_get_id)f2;
+        }
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 static cudaError_t noalloc_scratch_for_current_device(double** out) {
     int dev = 0;
@@ -32,11 +69,13 @@ static cudaError_t noalloc_scratch_for_current_device(double** out) {
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_noalloc_ptr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_noalloc_ptr[dev] = (double*)p;
+        g_noalloc_ctx[dev] = ctx;
     }
     *out = g_noalloc_ptr[dev];
     return cudaSuccess;
@@ -46,7 +85,8 @@ extern "C" swr_status swr_residual_noalloc(swr_ctx* ctx, double* res_host, size_
     if (!ctx || !res_host) return SWR_EINVAL;
     ResidualInputs r;
     if (!residual_inputs(ctx, &r)) {
-        set_error(ctx, "swr_residual_noalloc: no completed Schwarz iteration on this context");
+        set_error(ctx, "swr_residual_noalloc: no Schwarz iteration completed since the last assembly, trace "
+                       "restore or failed step");
         return SWR_ESTATE;
     }
     if (n != (size_t)r.n_inst) {
@@ -59,8 +99,8 @@ extern "C" swr_status swr_residual_noalloc(swr_ctx* ctx, double* res_host, size_
         char msg[200];
         snprintf(msg, sizeof(msg),
                  "swr_residual_noalloc: problem needs %lld scratch doubles, the static limit is %d "
-                 "(about %d subdomains)", need, SWR_NOALLOC_SCRATCH_DOUBLES,
-                 (SWR_NOALLOC_SCRATCH_DOUBLES - 2 * r.n_inst) / SWR_NOALLOC_RES_BLOCKS);
+                 "(at most %lld subdomains for %d instances)", need, SWR_NOALLOC_SCRATCH_DOUBLES,
+                 (SWR_NOALLOC_SCRATCH_DOUBLES - win_doubles - r.n_inst) / SWR_NOALLOC_RES_BLOCKS, r.n_inst);
         set_error(ctx, msg);
         return SWR_EINVAL;
     }

@@ -11,6 +11,8 @@
 
 namespace swr {
 
+#define WARPS_MAX 32
+
 __device__ inline double block_sum(double x, double* red) {
     x = warp_sum(x);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -334,6 +336,120 @@ __global__ void k_residual_reduce(SwrDeviceView v, const double* part, int nblk,
     if (threadIdx.x == 0) res[i] = sqrt(acc);
 }
 
+// CVTOT (Eq. CVTOT, Sec. 4.1; Eq. CVTOT2, Sec. 4.2) of one instance:
+// CVTOT^2 = sum_{n=1}^{W} dt C_n^2, C_n = sum over ordered pairs (i, j) of
+// ||psi_i - psi_j||_{L2(Gamma_{i;j})} at t_n, Gamma_{i;j} = the interface
+// nodes of Omega_i that lie in closure(Omega_j) (the contributors of the
+// averaged Robin data), psi the normalised state (y^n / s_n).  The pair
+// (i, j) is identified by the offset of j in the 3 x 3 block around i
+// (slot (j1 - i1 + 1) + 3 (j2 - i2 + 1)); each slot's node sum is reduced in a
+// fixed order, so the result is deterministic.  Grid (CV_BLOCKS, n_inst):
+// block b takes steps n = 1 + b, 1 + b + CV_BLOCKS, ...; its partial of
+// sum_n dt C_n^2 goes to part[inst * CV_BLOCKS + b].
+#define CV_BLOCKS 64
+__global__ void k_cvtot(SwrDeviceView v, const int* win, const double* snorm, int cap, double* part) {
+    const int ii = blockIdx.y;
+    const InstDev& in = v.inst[ii];
+    const int W = win[ii], nch = n_channels(in), L = in.L, qp = in.q_p;
+    __shared__ double red[9][WARPS_MAX];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double acc_t = 0;  // thread 0: sum over this block's steps of dt C_n^2
+    for (int n = 1 + blockIdx.x; n <= W; n += gridDim.x) {
+        const double sn = in.normalize ? snorm[(long long)ii * (cap + 1) + n] : 1.0;
+        double c_n = 0;
+        for (int sid = in.sub_base; sid < in.sub_base + in.n_sub; ++sid) {
+            const SubDev& s = v.sub[sid];
+            const int q = s.q, kd = s.kd;
+            T1Layout lay(q, kd);
+            double a[9];
+#pragma unroll
+            for (int sl = 0; sl < 9; ++sl) a[sl] = 0.0;
+            for (int node = threadIdx.x; node < s.ngam; node += blockDim.x) {
+                int slot, nt;
+                gamma_slot(s, node, slot, nt);
+                const int d = slot / 2, side = slot % 2;
+                const int lown = side ? 3 : 0;
+                double own[2] = {0, 0};
+                for (int ch = 0; ch < nch; ++ch) {
+                    const double* lo = v.arena + s.line + ((long long)n * nch + ch) * s.nline;
+                    own[ch] = (s.N == 1) ? lo[lown * 2 + 0] : lo[((d * 4 + lown) * 2 + 0) * q + nt];
+                }
+                const int kdn = s.idx[d];
+                const int across = kdn + (side ? 1 : -1);
+                if (s.N == 1) {
+                    const int j = in.sub_base + across;
+                    const int l = side ? 1 : 2;
+                    double e2 = 0;
+                    for (int ch = 0; ch < nch; ++ch) {
+                        const double* lj = v.arena + v.sub[j].line + ((long long)n * nch + ch) * v.sub[j].nline;
+                        const double df = own[ch] - lj[l * 2 + 0];
+                        e2 += df * df;
+                    }
+                    const int sl = across - kdn + 1;
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) a[t] += (t == sl) ? e2 : 0.0;
+                } else {
+                    const int o = 1 - d;
+                    const int ko = s.idx[o];
+                    const double w = v.arena[s.t1[o] + lay.w() + nt];
+                    const int pt = nt / qp, npan = in.n_mid + 2;
+                    int jo_list[3], shift[3], njo = 0;
+                    jo_list[njo] = ko; shift[njo++] = 0;
+                    if (pt == 0 && ko > 0) { jo_list[njo] = ko - 1; shift[njo++] = q - qp; }
+                    if (pt == npan - 1 && ko < L - 1) { jo_list[njo] = ko + 1; shift[njo++] = -(q - qp); }
+                    for (int jd_i = 0; jd_i < 2; ++jd_i) {
+                        const int jd = jd_i ? across : kdn;
+                        for (int t = 0; t < njo; ++t) {
+                            const int jo = jo_list[t];
+                            if (jd == kdn && jo == ko) continue;
+                            const int j1 = d == 0 ? jd : jo, j2 = d == 0 ? jo : jd;
+                            const int j = in.sub_base + j1 + L * j2;
+                            const int l = (jd == kdn) ? lown : (side ? 1 : 2);
+                            const int nj = nt + shift[t];
+                            double e2 = 0;
+                            for (int ch = 0; ch < nch; ++ch) {
+                                const double* lj = v.arena + v.sub[j].line + ((long long)n * nch + ch) * v.sub[j].nline;
+                                const double df = own[ch] - lj[((d * 4 + l) * 2 + 0) * q + nj];
+                                e2 += df * df;
+                            }
+                            const int sl = (j1 - s.idx[0] + 1) + 3 * (j2 - s.idx[1] + 1);
+#pragma unroll
+                            for (int u = 0; u < 9; ++u) a[u] += (u == sl) ? w * e2 : 0.0;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int sl = 0; sl < 9; ++sl) {
+                const double x = warp_sum(a[sl]);
+                if (lane == 0) red[sl][wid] = x;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int sl = 0; sl < 9; ++sl) {
+                    double t = 0;
+                    for (int u = 0; u < nw; ++u) t += red[sl][u];
+                    c_n += sqrt(t);
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double cs = c_n / sn;
+            acc_t += in.dt * cs * cs;
+        }
+    }
+    if (threadIdx.x == 0) part[(long long)ii * gridDim.x + blockIdx.x] = acc_t;
+}
+
+__global__ void k_cvtot_reduce(int n_inst, const double* part, int nblk, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    double acc = 0;
+    for (int b = 0; b < nblk; ++b) acc += part[(long long)i * nblk + b];
+    out[i] = sqrt(acc);
+}
+
 // Per subdomain at step W (normalised state): sums over the volume nodes of
 // w chi (kappa |grad psi|^2 + V |psi|^2), w chi |psi|^2 and w chi (x_1+..+x_N)|psi|^2,
 // and psi at the nodes (node p = q1 + q*q2; re, im interleaved in real time).
@@ -459,14 +575,14 @@ __global__ void k_anti_fill(SwrDeviceView v, const int* win) {
 static inline unsigned div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // Kernel launches per swr_step besides the window (reset, window, line traces,
-// gather, residual, residual reduce, energy, energy reduce; one more with
-// antisymmetric instances: the mirror fill).
-extern const int kStepLaunches = 8;
+// gather, residual, residual reduce, CVTOT, CVTOT reduce, energy, energy
+// reduce; one more with antisymmetric instances: the mirror fill).
+extern const int kStepLaunches = 10;
 
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
                         int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax,
-                        bool any_anti) {
+                        bool any_anti, double* d_cv_part, double* d_cvtot) {
     int nb = 64;
     if (any_anti) k_anti_fill<<<dim3(nb, v.n_sub), 256, 0, st>>>(v, d_win);
     {
@@ -485,8 +601,13 @@ cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_wi
     }
     k_residual<<<dim3(res_blocks, v.n_sub), 256, 0, st>>>(v, d_win, d_win_prev, parity, first_iter, d_res_part);
     k_residual_reduce<<<v.n_inst, 256, 0, st>>>(v, d_res_part, res_blocks, d_res);
+    k_cvtot<<<dim3(CV_BLOCKS, v.n_inst), 256, 0, st>>>(v, d_win, d_snorm, cap, d_cv_part);
+    k_cvtot_reduce<<<div_up(v.n_inst, 128), 128, 0, st>>>(v.n_inst, d_cv_part, CV_BLOCKS, d_cvtot);
     return cudaGetLastError();
 }
+
+// Partials of the CVTOT reduction per instance (doubles).
+size_t cvtot_part_doubles(int n_inst) { return (size_t)n_inst * CV_BLOCKS; }
 
 // Residual of one iteration into caller-chosen scratch (partials) and output.
 cudaError_t launch_residual(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,

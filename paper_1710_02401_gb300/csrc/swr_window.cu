@@ -1242,6 +1242,10 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NCW = WIN_THREADS / 32 - 1, CT = WIN_THREADS - 32;  // consumer warps, threads
     const long long wait_limit = A.spin_limit >> 4;
+    // the waits for this CTA's own bulk copies before it ends do not follow the
+    // caller's spin limit: a CTA must not exit while a copy still writes its
+    // shared memory, and a copy of a few KB completes within microseconds
+    const long long copy_limit = wait_limit > (1LL << 20) ? wait_limit : (1LL << 20);
     SplitQueue* q = A.q;
     unsigned target = 0, gen = 0;
     bool failed = false;  // a bounded wait gave up: the rest of the window skips its waits
@@ -1508,7 +1512,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
             // (bounded) for the last copy into each slot before the CTA ends
             if (tid == 0)
                 for (unsigned i = issued > NS ? issued - NS : 0; i < issued; ++i)
-                    mbar_wait(&full[i % NS], (i / NS) & 1u, wait_limit);
+                    mbar_wait(&full[i % NS], (i / NS) & 1u, copy_limit);
             __syncthreads();
             return;
         }

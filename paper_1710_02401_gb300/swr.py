@@ -28,7 +28,7 @@ SYM_NONE, SYM_ANTISYMMETRIC = 0, 1
 LAUNCH_GRAPH, LAUNCH_DIRECT = 0, 1
 GET, SET = 0, 1
 (FIELD_ENERGY, FIELD_NORM2, FIELD_DIPOLE, FIELD_RES, FIELD_WINDOW, FIELD_PSI_NODES, FIELD_OWN_TRACES,
- FIELD_ROBIN, FIELD_TRACE_BYTES, FIELD_NODE_COUNTS, FIELD_K_MAX, FIELD_COUNTERS) = range(12)
+ FIELD_ROBIN, FIELD_TRACE_BYTES, FIELD_NODE_COUNTS, FIELD_K_MAX, FIELD_COUNTERS, FIELD_CVTOT) = range(13)
 
 
 class swr_instance(C.Structure):
@@ -49,7 +49,8 @@ class swr_instance(C.Structure):
 class swr_problem(C.Structure):
     _fields_ = [("n_instances", C.c_int), ("instances", C.POINTER(swr_instance)), ("precision", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
-                ("window_variant", C.c_int), ("rows_per_task", C.c_int), ("launch_mode", C.c_int)]
+                ("window_variant", C.c_int), ("rows_per_task", C.c_int), ("launch_mode", C.c_int),
+                ("spin_limit", C.c_longlong)]
 
 
 class swr_tune_report(C.Structure):
@@ -61,7 +62,7 @@ class swr_tune_report(C.Structure):
 
 class swr_iter_report(C.Structure):
     _fields_ = [("k", C.c_int), ("res", C.c_double), ("window_max", C.c_int),
-                ("subdomain_solves", C.c_longlong), ("seconds", C.c_double)]
+                ("subdomain_solves", C.c_longlong), ("seconds", C.c_double), ("cvtot", C.c_double)]
 
 
 class swr_report(C.Structure):
@@ -77,7 +78,8 @@ EXPORTS = ["swr_workspace_size", "swr_setup", "swr_assemble", "swr_step", "swr_i
            "swr_get", "swr_field_bytes", "swr_trace_codec", "swr_trace_encode", "swr_trace_decode_set",
            "swr_mlp_create", "swr_mlp_param_count", "swr_mlp_set_params", "swr_mlp_get_params",
            "swr_mlp_forward", "swr_mlp_train_step", "swr_mlp_destroy", "swr_mlp_last_error",
-           "swr_residual_noalloc", "swr_autotune", "swr_window_plan", "swr_destroy", "swr_last_error"]
+           "swr_residual_noalloc", "swr_autotune", "swr_window_plan", "swr_set_spin_limit", "swr_destroy",
+           "swr_last_error"]
 
 _lib = None
 
@@ -100,6 +102,7 @@ def load_library(path: str = LIB_PATH):
     lib.swr_get.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]
     lib.swr_field_bytes.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]
     lib.swr_residual_noalloc.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.c_size_t]
+    lib.swr_set_spin_limit.argtypes = [C.c_void_p, C.c_longlong]
     lib.swr_autotune.argtypes = [C.c_void_p, C.c_int, C.POINTER(swr_tune_report)]
     lib.swr_window_plan.argtypes = [C.c_void_p, C.POINTER(swr_tune_report)]
     lib.swr_trace_codec.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
@@ -213,7 +216,7 @@ class SWR:
 
     def __init__(self, instances, precision: int = PREC_FP64, device: str = "cuda:0", stream=None,
                  use_torch_workspace: bool = True, window_variant: int = 0, rows_per_task: int = 0,
-                 launch_mode: int = 0):
+                 launch_mode: int = 0, spin_limit: int = 0):
         import torch
         self.lib = load_library()
         if isinstance(instances, P.Instance):
@@ -234,6 +237,7 @@ class SWR:
         prob.window_variant = int(window_variant)
         prob.rows_per_task = int(rows_per_task)
         prob.launch_mode = int(launch_mode)
+        prob.spin_limit = int(spin_limit)
         nbytes = C.c_size_t(0)
         self._check(self.lib.swr_workspace_size(C.byref(prob), C.byref(nbytes)), None)
         self.workspace = None
@@ -305,6 +309,10 @@ class SWR:
         self._check(self.lib.swr_get(self.ctx, field, out.ctypes.data_as(C.c_void_p), nb), self.ctx)
         return out
 
+    def set_spin_limit(self, polls: int) -> None:
+        """Polls before a device-side wait gives up (0: the default)."""
+        self._check(self.lib.swr_set_spin_limit(self.ctx, int(polls)), self.ctx)
+
     def residual_noalloc(self) -> np.ndarray:
         """Res(k) of the last iteration recomputed by the allocation-free entry point."""
         out = np.empty(len(self.instances), dtype=np.float64)
@@ -360,6 +368,10 @@ class SWR:
 
     def residual(self) -> np.ndarray:
         return self.get(FIELD_RES)
+
+    def cvtot(self) -> np.ndarray:
+        """Interface mismatch CVTOT(k) of the last iteration per instance (Eq. CVTOT / CVTOT2)."""
+        return self.get(FIELD_CVTOT)
 
     def window(self) -> np.ndarray:
         return self.get(FIELD_WINDOW, dtype=np.int32)

@@ -56,6 +56,7 @@ int main(void) {{
   F(swr_instance, delta_per_sub) F(swr_instance, x_nuc) F(swr_instance, mode) F(swr_instance, phi0_center)
   F(swr_instance, max_steps) F(swr_instance, orth_tau) F(swr_instance, tc) F(swr_problem, workspace_bytes) F(swr_iter_report, seconds)
   F(swr_problem, window_variant) F(swr_problem, rows_per_task) F(swr_problem, launch_mode)
+  F(swr_problem, spin_limit) F(swr_iter_report, cvtot)
   F(swr_tune_report, graph) F(swr_tune_report, seconds_default)
   return 0;
 }}
@@ -73,8 +74,9 @@ int main(void) {{
     assert int(got["swr_problem.workspace_bytes"]) == S.swr_problem.workspace_bytes.offset
     assert int(got["swr_iter_report.seconds"]) == S.swr_iter_report.seconds.offset
     assert int(got["swr_tune_report"]) == C.sizeof(S.swr_tune_report)
-    for key in ["window_variant", "rows_per_task", "launch_mode"]:
+    for key in ["window_variant", "rows_per_task", "launch_mode", "spin_limit"]:
         assert int(got[f"swr_problem.{key}"]) == getattr(S.swr_problem, key).offset, key
+    assert int(got["swr_iter_report.cvtot"]) == S.swr_iter_report.cvtot.offset
     assert int(got["swr_tune_report.seconds_default"]) == S.swr_tune_report.seconds_default.offset
     assert int(got["swr_tune_report.graph"]) == S.swr_tune_report.graph.offset
 
@@ -119,6 +121,9 @@ def test_workspace_size_and_validation_on_host(lib):
         assert len(lib.swr_last_error(None)) > 0
     empty = S.swr_problem()
     assert lib.swr_workspace_size(C.byref(empty), C.byref(n)) == S.SWR_EINVAL
+    neg = _problem([P.small_tise_2d()], keep)
+    neg.spin_limit = -1
+    assert lib.swr_workspace_size(C.byref(neg), C.byref(n)) == S.SWR_EINVAL
 
 
 def test_mixed_modes_rejected(lib):

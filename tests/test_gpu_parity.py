@@ -38,13 +38,16 @@ def swr_mod():
     return S
 
 
-def _run_gpu(S, inst, kmax, tol=0.0, precision=0):
+def _run_gpu(S, inst, kmax, tol=0.0, precision=0, cvtot=None):
     s = S.SWR(inst, precision=precision)
     s.assemble()
     res, wins, energies = [], [], []
     for _ in range(kmax):
         rep = s.step()
         res.append(rep.res)
+        if cvtot is not None:
+            cvtot.append(float(s.cvtot()[0]))
+            assert rep.cvtot == cvtot[-1]
         wins.append(int(s.window()[0]))
         if inst.mode == P.TDSE:
             energies.append((float(s.norm2()[0]), float(s.dipole()[0])))
@@ -65,11 +68,16 @@ REL_CANONICAL = 1e-7
 
 def _compare(S, inst, kmax, tol=0.0, rel=REL, precision=0):
     ref = O.run_swr(inst, kmax=kmax, tol=tol)
-    s, res, wins, energies = _run_gpu(S, inst, len(ref.records), tol, precision)
+    cv = []
+    s, res, wins, energies = _run_gpu(S, inst, len(ref.records), tol, precision, cvtot=cv)
     assert wins == [r.n_win for r in ref.records]
     r0 = max(r.res for r in ref.records)
     for a, r in zip(res, ref.records):
         assert abs(a - r.res) <= rel * r0, (a, r.res)
+    # interface mismatch (Eq. CVTOT / CVTOT2), absolute against its largest value
+    c0 = max(r.cvtot for r in ref.records)
+    for a, r in zip(cv, ref.records):
+        assert abs(a - r.cvtot) <= rel * c0, (a, r.cvtot)
     if inst.mode == P.TDSE:
         for (n2, dip), r in zip(energies, ref.records):
             assert abs(n2 - r.norm2) <= rel * abs(r.norm2), (n2, r.norm2)
