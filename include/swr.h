@@ -56,10 +56,22 @@ typedef enum swr_mode {
 
 typedef enum swr_precision {
     SWR_PREC_FP64 = 0,   /* plain FP64 everywhere                                */
-    SWR_PREC_MIXED = 1   /* step matrices stored as FP32 hi/lo pairs (four planes for
+    SWR_PREC_MIXED = 1,  /* step matrices stored as FP32 hi/lo pairs (four planes for
                             the complex real-time G0) with error-free FP32
                             accumulation: FP64-level accuracy on the FP32 pipes;
                             FP64 reductions, norms, orthogonalisation, inversion  */
+    SWR_PREC_FP32_REFINED = 2 /* the Schwarz iterations first run with the step
+                            matrices rounded to FP32 (only the hi plane of
+                            SWR_PREC_MIXED is read: 4 bytes per real element, 8
+                            per complex one; the products of the rounded matrix
+                            are still formed in double-single arithmetic, so each
+                            iteration is the FP64 iteration of a matrix perturbed
+                            by at most 2^-24 relative), then, once Res(k) <=
+                            swr_problem.refine_res or Res(k) stops falling, with
+                            the double-single matrices: the remaining iterations
+                            are the outer refinement that carries the iterate to
+                            the fixed point of the exact discrete problem.
+                            swr_iterate stops only on a refined iteration.      */
 } swr_precision;
 
 /* How swr_step launches the kernels of one Schwarz iteration.  Both run the
@@ -180,6 +192,11 @@ typedef struct swr_problem {
     int                 rows_per_task;   /* window row-task size: 0 (automatic) or
                                             8..256; swr_autotune may change it   */
     int                 launch_mode;     /* swr_launch_mode                        */
+    double              refine_res;      /* SWR_PREC_FP32_REFINED: Res(k) at or below which
+                                            the iteration switches to the double-single
+                                            step matrices; 0 selects 10 x the tolerance
+                                            inside swr_iterate, else 1e-7 x the largest
+                                            Res(k) so far                             */
     long long           spin_limit;      /* polls (about 64 ns each) before a device-side
                                             wait of the window kernels gives up and
                                             swr_step returns SWR_ETIMEOUT; 0 selects
@@ -197,6 +214,8 @@ typedef struct swr_iter_report {
     long long subdomain_solves;  /* local step solves done in this iteration       */
     double    seconds;           /* device time of the iteration (CUDA events)     */
     double    cvtot;             /* max over instances of CVTOT(k) (SWR_FIELD_CVTOT) */
+    int       fp32_matrices;     /* 1: this iteration used the FP32-rounded step
+                                    matrices (SWR_PREC_FP32_REFINED before the switch) */
 } swr_iter_report;
 
 typedef struct swr_report {
@@ -205,6 +224,8 @@ typedef struct swr_report {
     double    res_last;
     long long subdomain_solves;
     double    seconds;
+    int       fp32_iterations;   /* iterations run with the FP32-rounded step matrices
+                                    (SWR_PREC_FP32_REFINED)                          */
 } swr_report;
 
 /* Device bytes the context needs (so the caller can pass them in as
@@ -263,7 +284,7 @@ typedef enum swr_field {
     SWR_FIELD_TRACE_BYTES = 8,  /* size_t: bytes of the swr_traces window              */
     SWR_FIELD_NODE_COUNTS = 9,  /* int[3 * n_sub_total]: per subdomain (q, n_gamma, K) */
     SWR_FIELD_K_MAX = 10,       /* int: Schwarz iterations done so far                 */
-    SWR_FIELD_COUNTERS = 11,    /* double[10], cumulative since swr_setup:
+    SWR_FIELD_COUNTERS = 11,    /* double[11], cumulative since swr_setup:
                                    [0] ms inside the time-window kernel (CUDA events on
                                        the context stream, one pair per launch),
                                    [1] launches of the time-window kernel,
@@ -276,7 +297,13 @@ typedef enum swr_field {
                                        (step-matrix bytes read per local step solve),
                                    [5] local step solves,
                                    [6] ms of swr_assemble (events), [7] ms of swr_step,
-                                   [8] host->device bytes copied, [9] device->host bytes */
+                                   [8] host->device bytes copied, [9] device->host bytes,
+                                   [10] algorithmic step-matrix bytes of the window
+                                       kernels: per real matrix element 8 (the FP64
+                                       value or its FP32 hi/lo pair) or 4 (FP32-rounded
+                                       matrix), per complex one 16 or 8; K^2 elements
+                                       per local step solve (imaginary time) or per
+                                       matrix sweep (real time)                     */
     SWR_FIELD_CVTOT = 12        /* double[n_instances]: interface mismatch of the last
                                    iteration, Eq. CVTOT (Sec. 4.1) / Eq. CVTOT2 (Sec. 4.2):
                                    the L2 norm in time (rectangle rule, weight dt at

@@ -28,7 +28,7 @@ int window_rows_per_task_max();
 cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, int variant, bool df32);
 cudaError_t launch_split_df32(const SwrDeviceView& v, cudaStream_t st, int max_K, bool make_w);
 cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst, int variant, bool df32,
-                          cudaEvent_t ev_begin, cudaEvent_t ev_end);
+                          bool onep, cudaEvent_t ev_begin, cudaEvent_t ev_end);
 extern const int kAssembleLaunchesFixed, kStepLaunches;
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
@@ -41,7 +41,7 @@ cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_
 size_t energy_smem(const SubDev& s);
 cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const long long* d_boff, const int* d_win_prev,
                                int n_steps, const unsigned char* h_need, const unsigned char* d_need, int max_K,
-                               int max_kd, bool df32, long long* launches);
+                               int max_kd, bool df32, bool onep, long long* launches);
 cudaError_t launch_split_c_df32(const SwrDeviceView& v, cudaStream_t st, int max_K);
 }  // namespace swr
 
@@ -88,8 +88,8 @@ struct swr_ctx {
     int *d_cta_task0 = nullptr, *d_cta_list = nullptr;
     // launch of one Schwarz iteration: a CUDA graph per (parity, first iteration), captured once
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    long long g_win_launches[2][2] = {{0, 0}, {0, 0}};
+    cudaGraphExec_t gexec[2][2][2] = {};     // [parity][first iteration][FP32 matrices]
+    long long g_win_launches[2][2][2] = {};
     bool graph_failed = false;
     int* d_wfix = nullptr;          // real time: the fixed window of every instance
     TaskCache* d_tc = nullptr;
@@ -121,6 +121,9 @@ struct swr_ctx {
     bool assembled = false;
     int k = 0, parity = 0;
     bool step_done = false;       // a swr_step has completed since the last assembly or trace restore
+    bool refined = false;         // SWR_PREC_FP32_REFINED: switched to the double-single step matrices
+    double res_peak = 0.0, res_last = 0.0;  // largest and last Res(k) seen in the FP32 phase
+    double iterate_tol = 0.0;     // tolerance of the running swr_iterate (0 outside it)
     long long spin_limit = SPIN_LIMIT;
     int grid = 0;
     size_t win_smem = 0;
@@ -128,11 +131,15 @@ struct swr_ctx {
     std::vector<int> win_h, win_prev_h;
     std::vector<int> win_pp_h;  // windows of the iteration before the last one
     // counters (see SWR_FIELD_COUNTERS)
-    double counters[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double counters[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     cudaEvent_t evw0 = nullptr, evw1 = nullptr;
 };
 
 static std::string g_setup_err;
+
+// SWR_PREC_FP32_REFINED before its switch: the windows read only the hi plane
+// of the step matrices (the FP32-rounded G).
+static bool fp32_phase(const swr_ctx* c) { return c->prob.precision == SWR_PREC_FP32_REFINED && !c->refined; }
 
 static swr_status fail(swr_ctx* c, swr_status s, const char* fmt, ...) {
     char buf[512];
@@ -276,14 +283,17 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
             if (!(dl > 0)) return fail(c, SWR_EINVAL, "instance %d sub %d: delta must be > 0", i, s);
         }
     }
-    if (p->precision != SWR_PREC_FP64 && p->precision != SWR_PREC_MIXED)
+    if (p->precision != SWR_PREC_FP64 && p->precision != SWR_PREC_MIXED && p->precision != SWR_PREC_FP32_REFINED)
         return fail(c, SWR_EINVAL, "unknown precision");
+    if (!(p->refine_res >= 0.0)) return fail(c, SWR_EINVAL, "refine_res must be >= 0 (0: default)");
     if (p->window_variant < 0 || p->window_variant > SWR_WINDOW_SPLIT)
         return fail(c, SWR_EINVAL, "unknown window variant");
-    if (p->window_variant == SWR_WINDOW_FUSED && (p->precision != SWR_PREC_MIXED || mode0 != SWR_MODE_TISE))
+    if (p->window_variant == SWR_WINDOW_FUSED && (p->precision == SWR_PREC_FP64 || mode0 != SWR_MODE_TISE))
         return fail(c, SWR_EINVAL, "the fused window is the mixed-precision imaginary-time kernel");
-    if (p->window_variant == SWR_WINDOW_SPLIT && (p->precision != SWR_PREC_MIXED || mode0 != SWR_MODE_TISE))
+    if (p->window_variant == SWR_WINDOW_SPLIT && (p->precision == SWR_PREC_FP64 || mode0 != SWR_MODE_TISE))
         return fail(c, SWR_EINVAL, "the split window is the mixed-precision imaginary-time kernel");
+    if (p->window_variant == SWR_WINDOW_TWO_PHASE && p->precision == SWR_PREC_FP32_REFINED)
+        return fail(c, SWR_EINVAL, "SWR_PREC_FP32_REFINED runs the fused or the split window");
     if (p->launch_mode != SWR_LAUNCH_GRAPH && p->launch_mode != SWR_LAUNCH_DIRECT)
         return fail(c, SWR_EINVAL, "unknown launch mode");
     if (p->rows_per_task != 0 && (p->rows_per_task < 8 || p->rows_per_task > 256))
@@ -669,7 +679,7 @@ static AuxPlan aux_plan(const swr_ctx* c) {
 // Layout for the current device: the row tasks depend on the SM count and on
 // how many window CTAs fit per SM (two at most; 152 x 2 without a device).
 static bool plan_for_device(swr_ctx* c, const swr_problem* p) {
-    c->df32 = (p->precision == SWR_PREC_MIXED);
+    c->df32 = (p->precision != SWR_PREC_FP64);
     int dev = 0;
     bool have_dev = cudaGetDevice(&dev) == cudaSuccess &&
                     cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
@@ -919,6 +929,8 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     c->win_prev_h.assign(c->inst.size(), 0);
     c->win_pp_h.assign(c->inst.size(), 0);
     c->step_done = false;
+    c->refined = false;
+    c->res_peak = c->res_last = 0.0;
     return SWR_OK;
 }
 
@@ -973,13 +985,14 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
         if (e == cudaSuccess)
             e = launch_tdse_window(view(c), st, c->d_boff, c->d_win_prev, nmax, c->cn_need.data(), c->d_cn_need,
                                    c->max_K, c->max_kd,
-                                   c->df32, win_launches);
+                                   c->df32, fp32_phase(c), win_launches);
         if (e == cudaSuccess) e = record_event(c->evw1, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(c->d_win, c->d_wfix, c->inst.size() * sizeof(int), cudaMemcpyDeviceToDevice, st);
     } else {
         SweepArgs a = sweep_args(c);
-        e = launch_window(a, c->grid, c->win_smem, st, (int)c->inst.size(), c->variant, c->df32, c->evw0, c->evw1);
+        e = launch_window(a, c->grid, c->win_smem, st, (int)c->inst.size(), c->variant, c->df32, fp32_phase(c),
+                          c->evw0, c->evw1);
     }
     if (e == cudaSuccess)
         e = launch_post(view(c), st, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
@@ -994,15 +1007,16 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
 static void drop_graphs(swr_ctx* c) {
     for (int p = 0; p < 2; ++p)
         for (int f = 0; f < 2; ++f)
-            if (c->gexec[p][f]) {
-                cudaGraphExecDestroy(c->gexec[p][f]);
-                c->gexec[p][f] = nullptr;
-            }
+            for (int o = 0; o < 2; ++o)
+                if (c->gexec[p][f][o]) {
+                    cudaGraphExecDestroy(c->gexec[p][f][o]);
+                    c->gexec[p][f][o] = nullptr;
+                }
 }
 
 // Captures the iteration for the current (parity, first) once; later
 // iterations of the same kind replay it with one cudaGraphLaunch.
-static cudaError_t capture_iteration(swr_ctx* c, int p, int f) {
+static cudaError_t capture_iteration(swr_ctx* c, int p, int f, int o) {
     cudaError_t e = cudaSuccess;
     if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
@@ -1013,13 +1027,13 @@ static cudaError_t capture_iteration(swr_ctx* c, int p, int f) {
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(c->cap_stream, &g);
     if (er != cudaSuccess) e = er;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[p][f], g, 0ULL);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[p][f][o], g, 0ULL);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        c->gexec[p][f] = nullptr;
+        c->gexec[p][f][o] = nullptr;
         return e;
     }
-    c->g_win_launches[p][f] = wl;
+    c->g_win_launches[p][f][o] = wl;
     return cudaSuccess;
 }
 
@@ -1028,19 +1042,19 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     if (!c->assembled) return fail(c, SWR_ESTATE, "swr_step before swr_assemble");
     c->step_done = false;  // set again once this iteration has completed without error
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
-    const int gp = c->parity, gf = c->k == 0 ? 1 : 0;
-    if (c->prob.launch_mode == SWR_LAUNCH_GRAPH && !c->graph_failed && !c->gexec[gp][gf]) {
+    const int gp = c->parity, gf = c->k == 0 ? 1 : 0, go = fp32_phase(c) ? 1 : 0;
+    if (c->prob.launch_mode == SWR_LAUNCH_GRAPH && !c->graph_failed && !c->gexec[gp][gf][go]) {
         // a capture the CUDA driver refuses leaves the context on direct launches
-        if (capture_iteration(c, gp, gf) != cudaSuccess) {
+        if (capture_iteration(c, gp, gf, go) != cudaSuccess) {
             cudaGetLastError();
             c->graph_failed = true;
         }
     }
     CU(cudaEventRecord(c->ev0, c->stream));
     long long win_launches = 1;
-    if (c->gexec[gp][gf]) {
-        CU(cudaGraphLaunch(c->gexec[gp][gf], c->stream));
-        win_launches = c->g_win_launches[gp][gf];
+    if (c->gexec[gp][gf][go]) {
+        CU(cudaGraphLaunch(c->gexec[gp][gf][go], c->stream));
+        win_launches = c->g_win_launches[gp][gf][go];
     } else {
         CU(record_iteration(c, c->stream, &win_launches));
     }
@@ -1076,13 +1090,14 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     float ms = 0, wms = 0;
     CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     CU(cudaEventElapsedTime(&wms, c->evw0, c->evw1));
-    double flops = 0, bytes = 0;
+    double flops = 0, bytes = 0, bytes_alg = 0;
     {
         std::vector<int> nsolve(c->inst.size());
         for (size_t i = 0; i < ni; ++i) nsolve[i] = c->win_h[i];
         // bytes per matrix element: complex G0 16 (FP64 pair or four FP32 planes);
-        // real G 8 (FP64 or FP32 hi/lo); the fused variant also streams W (16)
-        const double bel = c->tdse ? 16.0 : (c->variant == WIN_FUSED ? 16.0 : 8.0);
+        // real G 8 (FP64 or FP32 hi/lo); the fused variant also streams W (16);
+        // half of each with the FP32-rounded matrices (hi planes only)
+        const double bel = (c->tdse ? 16.0 : (c->variant == WIN_FUSED ? 16.0 : 8.0)) * (go ? 0.5 : 1.0);
         for (size_t sid = 0; sid < c->sub.size(); ++sid) {
             const SubDev& sd = c->sub[sid];
             if (c->inst[sd.inst].anti && sd.N == 2 && sd.idx[0] > sd.idx[1]) continue;  // mirror image, not solved
@@ -1091,6 +1106,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
             const double mv = c->tdse ? c->cn_sweeps[sid] : (double)nsolve[sd.inst];
             flops += (c->tdse ? 8.0 : 2.0) * K2 * mv;
             bytes += bel * K2 * mv;
+            bytes_alg += (c->tdse ? 16.0 : 8.0) * (go ? 0.5 : 1.0) * K2 * mv;
         }
     }
     c->counters[0] += wms;
@@ -1100,6 +1116,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     c->counters[4] += bytes;
     c->counters[5] += (double)solves;
     c->counters[7] += ms;
+    c->counters[10] += bytes_alg;
     if (rep) {
         rep->k = c->k;
         rep->res = rmax;
@@ -1107,6 +1124,21 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
         rep->subdomain_solves = solves;
         rep->seconds = ms * 1e-3;
         rep->cvtot = cmax;
+        rep->fp32_matrices = go;
+    }
+    if (go) {
+        // the FP32 phase ends once Res(k) reaches the switch level, or when it has
+        // fallen far below its peak and stopped falling
+        c->res_peak = rmax > c->res_peak ? rmax : c->res_peak;
+        // default: ten times the tolerance of the running swr_iterate (iterations of the
+        // FP32-rounded problem below that only approach its own fixed point), else
+        // 1e-7 of the largest residual so far
+        const double thr = c->prob.refine_res > 0.0 ? c->prob.refine_res
+                           : c->iterate_tol > 0.0   ? 10.0 * c->iterate_tol
+                                                    : 1e-7 * c->res_peak;
+        const bool stalled = c->k >= 3 && rmax < 1e-3 * c->res_peak && rmax > 0.9 * c->res_last;
+        if (rmax <= thr || stalled) c->refined = true;  // graphs are kept per phase
+        c->res_last = rmax;
     }
     c->step_done = true;
     return SWR_OK;
@@ -1120,7 +1152,8 @@ static swr_status time_window_plan(swr_ctx* c, int steps, double* sec_per_step) 
     float best = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {
         CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
-        CU(launch_window(a, c->grid, c->win_smem, c->stream, (int)c->inst.size(), c->variant, c->df32, c->evw0,
+        CU(launch_window(a, c->grid, c->win_smem, c->stream, (int)c->inst.size(), c->variant, c->df32, fp32_phase(c),
+                         c->evw0,
                          c->evw1));
         c->counters[2] += 2;
         swr_status st = check_err(c);
@@ -1211,14 +1244,21 @@ extern "C" swr_status swr_iterate(swr_ctx* c, double tol, int kmax, swr_report* 
     memset(&r, 0, sizeof(r));
     for (int it = 0; it < kmax; ++it) {
         swr_iter_report ir;
+        c->iterate_tol = tol;
         swr_status st = swr_step(c, &ir);
+        c->iterate_tol = 0.0;
         if (st != SWR_OK) return st;
         if (hist) hist[it] = ir.res;
         r.iterations = it + 1;
         r.res_last = ir.res;
         r.subdomain_solves += ir.subdomain_solves;
         r.seconds += ir.seconds;
-        if (ir.res <= tol) {
+        r.fp32_iterations += ir.fp32_matrices;
+        if (ir.res <= tol && ir.fp32_matrices && !c->refined) {
+            c->refined = true;  // tolerance met with the FP32-rounded matrices: refine from here
+            continue;
+        }
+        if (ir.res <= tol && !ir.fp32_matrices) {
             r.converged = 1;
             break;
         }
@@ -1255,7 +1295,7 @@ extern "C" swr_status swr_field_bytes(swr_ctx* c, int field, size_t* bytes) {
         case SWR_FIELD_TRACE_BYTES: *bytes = sizeof(size_t); return SWR_OK;
         case SWR_FIELD_NODE_COUNTS: *bytes = 3 * ns * sizeof(int); return SWR_OK;
         case SWR_FIELD_K_MAX: *bytes = sizeof(int); return SWR_OK;
-        case SWR_FIELD_COUNTERS: *bytes = 10 * sizeof(double); return SWR_OK;
+        case SWR_FIELD_COUNTERS: *bytes = 11 * sizeof(double); return SWR_OK;
     }
     return fail(c, SWR_EINVAL, "unknown field %d", field);
 }

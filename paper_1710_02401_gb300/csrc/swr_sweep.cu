@@ -342,29 +342,31 @@ __global__ void k_residual_reduce(SwrDeviceView v, const double* part, int nblk,
 // nodes of Omega_i that lie in closure(Omega_j) (the contributors of the
 // averaged Robin data), psi the normalised state (y^n / s_n).  The pair
 // (i, j) is identified by the offset of j in the 3 x 3 block around i
-// (slot (j1 - i1 + 1) + 3 (j2 - i2 + 1)); each slot's node sum is reduced in a
-// fixed order, so the result is deterministic.  Grid (CV_BLOCKS, n_inst):
-// block b takes steps n = 1 + b, 1 + b + CV_BLOCKS, ...; its partial of
-// sum_n dt C_n^2 goes to part[inst * CV_BLOCKS + b].
-#define CV_BLOCKS 64
-__global__ void k_cvtot(SwrDeviceView v, const int* win, const double* snorm, int cap, double* part) {
+// (slot (j1 - i1 + 1) + 3 (j2 - i2 + 1)).  Grid (CV_BLOCKS, n_inst): block b
+// takes steps n = 1 + b, 1 + b + CV_BLOCKS, ...; within a step, warp w takes
+// the subdomains w, w + 8, ... (lanes over interface nodes, one register
+// accumulator per slot, shuffle sums), and the warps' sums of C_i are added
+// in warp order: a fixed order, so the result is deterministic.  The block's
+// partial of sum_n dt C_n^2 goes to part[inst * CV_BLOCKS + b].
+#define CV_BLOCKS 512
+__global__ void __launch_bounds__(256) k_cvtot(SwrDeviceView v, const int* win, const double* snorm, int cap,
+                                               double* part) {
     const int ii = blockIdx.y;
     const InstDev& in = v.inst[ii];
     const int W = win[ii], nch = n_channels(in), L = in.L, qp = in.q_p;
-    __shared__ double red[9][WARPS_MAX];
+    __shared__ double wsum[WARPS_MAX];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double acc_t = 0;  // thread 0: sum over this block's steps of dt C_n^2
     for (int n = 1 + blockIdx.x; n <= W; n += gridDim.x) {
-        const double sn = in.normalize ? snorm[(long long)ii * (cap + 1) + n] : 1.0;
-        double c_n = 0;
-        for (int sid = in.sub_base; sid < in.sub_base + in.n_sub; ++sid) {
-            const SubDev& s = v.sub[sid];
+        double c_w = 0;  // this warp's sum of C_i over its subdomains
+        for (int loc = wid; loc < in.n_sub; loc += nw) {
+            const SubDev& s = v.sub[in.sub_base + loc];
             const int q = s.q, kd = s.kd;
             T1Layout lay(q, kd);
             double a[9];
 #pragma unroll
             for (int sl = 0; sl < 9; ++sl) a[sl] = 0.0;
-            for (int node = threadIdx.x; node < s.ngam; node += blockDim.x) {
+            for (int node = lane; node < s.ngam; node += 32) {
                 int slot, nt;
                 gamma_slot(s, node, slot, nt);
                 const int d = slot / 2, side = slot % 2;
@@ -419,25 +421,20 @@ __global__ void k_cvtot(SwrDeviceView v, const int* win, const double* snorm, in
                     }
                 }
             }
+            double c_i = 0;
 #pragma unroll
-            for (int sl = 0; sl < 9; ++sl) {
-                const double x = warp_sum(a[sl]);
-                if (lane == 0) red[sl][wid] = x;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                for (int sl = 0; sl < 9; ++sl) {
-                    double t = 0;
-                    for (int u = 0; u < nw; ++u) t += red[sl][u];
-                    c_n += sqrt(t);
-                }
-            }
-            __syncthreads();
+            for (int sl = 0; sl < 9; ++sl) c_i += sqrt(warp_sum(a[sl]));
+            c_w += c_i;
         }
+        if (lane == 0) wsum[wid] = c_w;
+        __syncthreads();
         if (threadIdx.x == 0) {
-            const double cs = c_n / sn;
+            double c_n = 0;
+            for (int u = 0; u < nw; ++u) c_n += wsum[u];
+            const double cs = c_n / (in.normalize ? snorm[(long long)ii * (cap + 1) + n] : 1.0);
             acc_t += in.dt * cs * cs;
         }
+        __syncthreads();
     }
     if (threadIdx.x == 0) part[(long long)ii * gridDim.x + blockIdx.x] = acc_t;
 }

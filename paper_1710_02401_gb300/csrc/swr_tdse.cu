@@ -193,7 +193,10 @@ __device__ inline void ds_mac(float& ah, float& al, float gh, float gl, float xh
 // rows of ld = df32_ld(K) columns (zero-padded, 16-byte aligned): complex
 // double-single matvec, FP64-level accuracy on the FP32 pipes.  Each warp
 // takes two rows at a time with 16-byte loads of every plane, so that eight
-// independent 512-byte requests per warp are in flight.
+// independent 512-byte requests per warp are in flight.  ONEP: only the hi
+// planes are read (the FP32-rounded G0 of SWR_PREC_FP32_REFINED before its
+// switch, 8 bytes per complex element), their lo terms taken as 0.
+template <bool ONEP>
 __global__ void __launch_bounds__(256) k_cmv_df32(SwrDeviceView v, const long long* boff, const unsigned char* need,
                                                   int m) {
     const int sid = blockIdx.y;
@@ -235,10 +238,11 @@ __global__ void __launch_bounds__(256) k_cmv_df32(SwrDeviceView v, const long lo
             for (int i = 0; i < 2; ++i) {
                 if (i < nrow) {
                     const long long o = (long long)(rb + i) * ld + c;
+                    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
                     const float4 grh = *reinterpret_cast<const float4*>(Grh + o);
-                    const float4 grl = *reinterpret_cast<const float4*>(Grl + o);
+                    const float4 grl = ONEP ? zero4 : *reinterpret_cast<const float4*>(Grl + o);
                     const float4 gih = *reinterpret_cast<const float4*>(Gih + o);
-                    const float4 gil = *reinterpret_cast<const float4*>(Gil + o);
+                    const float4 gil = ONEP ? zero4 : *reinterpret_cast<const float4*>(Gil + o);
 #define CMV_TERM(f)                                                   \
     ds_mac(reh[i], rel[i], grh.f, grl.f, xrh.f, xrl.f);               \
     ds_mac(reh[i], rel[i], -gih.f, -gil.f, xih.f, xil.f);             \
@@ -331,7 +335,7 @@ cudaError_t launch_split_c_df32(const SwrDeviceView& v, cudaStream_t st, int max
 
 cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const long long* d_boff, const int* d_win_prev,
                                int n_steps, const unsigned char* h_need, const unsigned char* d_need, int max_K,
-                               int max_kd, bool df32, long long* launches) {
+                               int max_kd, bool df32, bool onep, long long* launches) {
     const size_t sm_el = (2 * (size_t)max_K + 2 * (size_t)max_kd * max_kd) * sizeof(double);
     const size_t sm_mv = 2 * (size_t)df32_ld(max_K) * sizeof(double);
     static bool attr_done = false;
@@ -339,7 +343,8 @@ cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const lo
         cudaFuncSetAttribute(k_cn_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         cudaFuncSetAttribute(k_cn_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         cudaFuncSetAttribute(k_cmv, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        cudaFuncSetAttribute(k_cmv_df32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_cmv_df32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_cmv_df32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         attr_done = true;
     }
     const dim3 ge(div_up(max_K, CN_ROWS), v.n_sub), gm(div_up(max_K, MV_ROWS), v.n_sub), gf(div_up(2 * max_K, 256), v.n_sub);
@@ -351,11 +356,13 @@ cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const lo
         int iters = 0;
         for (int s = 0; s < v.n_sub; ++s) iters = h_need[(size_t)n * v.n_sub + s] > iters ? h_need[(size_t)n * v.n_sub + s] : iters;
         k_cn_rhs<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, d_win_prev, n);
-        if (df32) k_cmv_df32<<<gm, 256, sm_mv, st>>>(v, d_boff, nullptr, 0);
+        if (df32 && onep) k_cmv_df32<true><<<gm, 256, sm_mv, st>>>(v, d_boff, nullptr, 0);
+        else if (df32) k_cmv_df32<false><<<gm, 256, sm_mv, st>>>(v, d_boff, nullptr, 0);
         else k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff, nullptr, 0);
         for (int m = 0; m < iters; ++m) {
             k_cn_update<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, n, nd, m);
-            if (df32) k_cmv_df32<<<gm, 256, sm_mv, st>>>(v, d_boff, nd, m);
+            if (df32 && onep) k_cmv_df32<true><<<gm, 256, sm_mv, st>>>(v, d_boff, nd, m);
+            else if (df32) k_cmv_df32<false><<<gm, 256, sm_mv, st>>>(v, d_boff, nd, m);
             else k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff, nd, m);
         }
         k_cn_finish<<<gf, 256, 0, st>>>(v, d_boff, n);

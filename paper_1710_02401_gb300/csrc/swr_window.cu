@@ -714,6 +714,9 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_2ph(SweepArgs A) {
 // Shared-memory task state only (at most WIN_TPC tasks per CTA).
 // Dynamic shared memory: vs[kmax] doubles | vf[kmax] float2 | tmp[rows_max + 2 kdmax]
 // doubles | P[tasks_per_cta][2][kdmax^2] doubles | G_hi rows (floats, when resident).
+// ONEP: only the hi planes of G and W are read (the FP32-rounded step matrix
+// of SWR_PREC_FP32_REFINED before its switch), their lo terms taken as 0.
+template <bool ONEP>
 __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
     extern __shared__ double sm[];
     __shared__ double red[33];
@@ -891,10 +894,11 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
                         if (i < nrow) {
                             const long long o = (long long)(rb + i) * ld + c;
                             const float* ghp = gres ? Gsm + (long long)(rb + i - tc.r0) * ld + c : Ghg + o;
+                            const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
                             const float4 g0 = *reinterpret_cast<const float4*>(ghp);
-                            const float4 g1 = *reinterpret_cast<const float4*>(Gl + o);
+                            const float4 g1 = ONEP ? zero4 : *reinterpret_cast<const float4*>(Gl + o);
                             const float4 w0 = *reinterpret_cast<const float4*>(Wh + o);
-                            const float4 w1 = *reinterpret_cast<const float4*>(Wl + o);
+                            const float4 w1 = ONEP ? zero4 : *reinterpret_cast<const float4*>(Wl + o);
                             df32_acc(yh[i], yl[i], g0.x, g1.x, xa.x, xa.y);
                             df32_acc(zh[i], zl[i], w0.x, w1.x, xa.x, xa.y);
                             df32_acc(yh[i], yl[i], g0.y, g1.y, xa.z, xa.w);
@@ -1015,10 +1019,10 @@ __device__ inline bool mbar_wait(const unsigned long long* bar, unsigned par, lo
     return false;
 }
 
-// Rows per stage for rows of ld floats: a power of two <= 32 with both planes in
-// stage_floats.
-__device__ inline int split_stage_rows(int ld, int stage_floats) {
-    const int r = stage_floats / (2 * ld);
+// Rows per stage for rows of ld floats: a power of two <= 32 with `planes`
+// planes (2: hi and lo; 1: hi only) in stage_floats.
+__device__ inline int split_stage_rows(int ld, int stage_floats, int planes = 2) {
+    const int r = stage_floats / (planes * ld);
     return r >= 32 ? 32 : r >= 16 ? 16 : r >= 8 ? 8 : r >= 4 ? 4 : r >= 2 ? 2 : 1;
 }
 
@@ -1167,12 +1171,12 @@ __device__ void z_rows_group(const TaskCache& tc, const double* P1g, const doubl
 }
 
 // One double-single chunk of 4 columns of a staged row into (yh, yl) and,
-// with HASB, (wh, wl).
-template <bool HASB>
+// with HASB, (wh, wl); ONEP: the row's lo plane is absent (taken as 0).
+template <bool HASB, bool ONEP>
 __device__ inline void split_chunk(const float* sh, const float* sl, const float2* vf, const float2* bf, int c,
                                    float& yh, float& yl, float& wh, float& wl) {
     const float4 g0 = *reinterpret_cast<const float4*>(sh + c);
-    const float4 g1 = *reinterpret_cast<const float4*>(sl + c);
+    const float4 g1 = ONEP ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(sl + c);
     const float4 xa = *reinterpret_cast<const float4*>(vf + c);
     const float4 xb = *reinterpret_cast<const float4*>(vf + c + 2);
     df32_acc(yh, yl, g0.x, g1.x, xa.x, xa.y);
@@ -1200,16 +1204,16 @@ __device__ inline void ds_add(float& h, float& l, float oh, float ol) {
 // One staged row by one warp: lanes over groups of 4 columns, two accumulator
 // pairs per product (alternate column groups), shuffle sum; the row's values of
 // G y and G b to all lanes.
-template <bool HASB>
+template <bool HASB, bool ONEP>
 __device__ inline void split_row(const float* sh, const float* sl, const float2* vf, const float2* bf, int ld,
                                  int lane, double& y, double& w) {
     float yh0 = 0.f, yl0 = 0.f, wh0 = 0.f, wl0 = 0.f, yh1 = 0.f, yl1 = 0.f, wh1 = 0.f, wl1 = 0.f;
     int c = lane * 4;
     for (; c + 128 < ld; c += 256) {
-        split_chunk<HASB>(sh, sl, vf, bf, c, yh0, yl0, wh0, wl0);
-        split_chunk<HASB>(sh, sl, vf, bf, c + 128, yh1, yl1, wh1, wl1);
+        split_chunk<HASB, ONEP>(sh, sl, vf, bf, c, yh0, yl0, wh0, wl0);
+        split_chunk<HASB, ONEP>(sh, sl, vf, bf, c + 128, yh1, yl1, wh1, wl1);
     }
-    if (c < ld) split_chunk<HASB>(sh, sl, vf, bf, c, yh0, yl0, wh0, wl0);
+    if (c < ld) split_chunk<HASB, ONEP>(sh, sl, vf, bf, c, yh0, yl0, wh0, wl0);
     ds_add(yh0, yl0, yh1, yl1);
     if (HASB) ds_add(wh0, wl0, wh1, wl1);
 #pragma unroll
@@ -1221,6 +1225,10 @@ __device__ inline void split_row(const float* sh, const float* sl, const float2*
     w = HASB ? (double)wh0 + (double)wl0 : 0.0;
 }
 
+// ONEP: only the hi plane of G is staged (the FP32-rounded step matrix of
+// SWR_PREC_FP32_REFINED before its switch): one bulk copy per stage, twice the
+// rows per stage, the lo terms taken as 0.
+template <bool ONEP>
 __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
     extern __shared__ double sm[];
     __shared__ double red[33];
@@ -1346,7 +1354,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                     push(2 * t + (str ? 1 : 0));
                     if (!str) continue;
                     // the task's stages: rows [rb, rb + rs) of both planes per stage
-                    const int ld = df32_ld(tc.K), rs = split_stage_rows(ld, SC);
+                    const int ld = df32_ld(tc.K), rs = split_stage_rows(ld, SC, ONEP ? 1 : 2);
                     const float* Gh = (const float*)(v.arena + tc.Gf);
                     const long long plane = (long long)tc.K * ld;
                     for (int rb = tc.r0; rb < tc.r0 + tc.nr; rb += rs) {
@@ -1356,18 +1364,19 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                         const unsigned bytes = (unsigned)nrow * ld * 4u, mb = smem_u32(&full[s]);
                         float* dst = ring + (size_t)s * SC;
                         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
-                                     "r"(2u * bytes)
+                                     "r"((ONEP ? 1u : 2u) * bytes)
                                      : "memory");
                         asm volatile(
                             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
                             "[%3];" ::"r"(smem_u32(dst)),
                             "l"(Gh + (long long)rb * ld), "r"(bytes), "r"(mb)
                             : "memory");
-                        asm volatile(
-                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-                            "[%3];" ::"r"(smem_u32(dst + rs * ld)),
-                            "l"(Gh + plane + (long long)rb * ld), "r"(bytes), "r"(mb)
-                            : "memory");
+                        if (!ONEP)
+                            asm volatile(
+                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                                "[%3];" ::"r"(smem_u32(dst + rs * ld)),
+                                "l"(Gh + plane + (long long)rb * ld), "r"(bytes), "r"(mb)
+                                : "memory");
                         ++issued;
                     }
                 }
@@ -1475,7 +1484,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                 // rows of u^{m+1} = G y^m and w^{m+1} = G (kappa dt b'^{m+1}) from the
                 // staged rows: row r0 + o of the task to consumer warp o mod 7, whole
                 // rows per warp, no block barrier between stages
-                const int rs = split_stage_rows(ld, SC);
+                const int rs = split_stage_rows(ld, SC, ONEP ? 1 : 2);
                 double* Un = v.arena + sd.work + (long long)((m + 1) & 1) * 2 * K;
                 double* Wn = Un + K;
                 const bool hasb = bsrc != nullptr;
@@ -1487,8 +1496,12 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                     int r = ((cw - (rb - tc.r0)) % NCW + NCW) % NCW;
                     for (; r < nrow; r += NCW) {
                         double y, w;
-                        if (hasb) split_row<true>(stage + (size_t)r * ld, stage + (size_t)(rs + r) * ld, vf, bf, ld, lane, y, w);
-                        else split_row<false>(stage + (size_t)r * ld, stage + (size_t)(rs + r) * ld, vf, bf, ld, lane, y, w);
+                        if (hasb)
+                            split_row<true, ONEP>(stage + (size_t)r * ld, stage + (size_t)(rs + r) * ld, vf, bf, ld,
+                                                  lane, y, w);
+                        else
+                            split_row<false, ONEP>(stage + (size_t)r * ld, stage + (size_t)(rs + r) * ld, vf, bf, ld,
+                                                   lane, y, w);
                         if (lane == 0) {
                             Un[rb + r] = y;
                             Wn[rb + r] = w;
@@ -1621,17 +1634,28 @@ size_t window_smem_split(int kmax, int kdmax, int rows_max, int stage_floats, in
 int window_tasks_per_cta_max() { return WIN_TPC; }
 int window_rows_per_task_max() { return WIN_RB; }
 
-static const void* window_kernel(int variant, bool df32) {
-    if (variant == WIN_FUSED) return (const void*)k_window_fused;
-    if (variant == WIN_SPLIT) return (const void*)k_window_split;
+static const void* window_kernel(int variant, bool df32, bool onep) {
+    if (variant == WIN_FUSED) return onep ? (const void*)k_window_fused<true> : (const void*)k_window_fused<false>;
+    if (variant == WIN_SPLIT) return onep ? (const void*)k_window_split<true> : (const void*)k_window_split<false>;
     return df32 ? (const void*)k_window_2ph<true> : (const void*)k_window_2ph<false>;
 }
 
+// Resident CTAs per SM of the window kernel: the smaller of its two instantiations
+// (both planes, hi plane only) where the variant has both.
 cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, int variant, bool df32) {
-    const void* f = window_kernel(variant, df32);
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, WIN_THREADS, smem);
+    int best = 1 << 30;
+    for (int o = 0; o < 2; ++o) {
+        if (o == 1 && variant != WIN_FUSED && variant != WIN_SPLIT) break;
+        const void* f = window_kernel(variant, df32, o == 1);
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, WIN_THREADS, smem);
+        if (e != cudaSuccess) return e;
+        best = b < best ? b : best;
+    }
+    *blocks_per_sm = best;
+    return cudaSuccess;
 }
 
 cudaError_t launch_split_df32(const SwrDeviceView& v, cudaStream_t st, int max_K, bool make_w) {
@@ -1646,12 +1670,13 @@ cudaError_t launch_split_df32(const SwrDeviceView& v, cudaStream_t st, int max_K
 }
 
 cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, int n_inst, int variant, bool df32,
-                          cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+                          bool onep, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
     k_window_reset<<<1, 32, 0, st>>>(a, n_inst);
     cudaError_t e = record_event(ev_begin, st);
     if (e != cudaSuccess) return e;
     void* params[] = {&a};
-    e = cudaLaunchCooperativeKernel(window_kernel(variant, df32), dim3(grid), dim3(WIN_THREADS), params, smem, st);
+    e = cudaLaunchCooperativeKernel(window_kernel(variant, df32, onep), dim3(grid), dim3(WIN_THREADS), params, smem,
+                                    st);
     if (e != cudaSuccess) return e;
     return record_event(ev_end, st);
 }

@@ -143,3 +143,47 @@ def compare(model: Model, instances, tol=1e-8, kmax=60):
     _, zero, _ = solve(instances, tol, kmax)
     _, learned, _ = solve(instances, tol, kmax, init_codes=predict_codes(model, instances))
     return zero, learned
+
+
+def compare_timed(model: Model, instances, tol=1e-8, kmax=60, repeats=3):
+    """Wall time of the batched solve to Res <= tol of every instance, from
+    zero traces and from the learned guess (descriptor upload, MLP inference
+    and decoding of the codes into Robin data and sources included), best of
+    `repeats`; setup and assembly of the context are inside both timings."""
+    import time
+    import torch
+
+    def timed(learned: bool):
+        best, out = float("inf"), None
+        for _ in range(repeats):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = S.SWR(list(instances))
+            s.assemble()
+            s.trace_codec(CODE_S, CODE_T)
+            t_inf = 0.0
+            if learned:
+                ti = time.perf_counter()
+                s.trace_decode_set(predict_codes(model, instances))
+                torch.cuda.synchronize()
+                t_inf = time.perf_counter() - ti
+            n = len(instances)
+            done = np.full(n, kmax + 1)
+            for k in range(1, kmax + 1):
+                s.step()
+                r = s.residual()
+                done[(r <= tol) & (done > kmax)] = k
+                if np.all(done <= kmax):
+                    break
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            s.close()
+            if dt < best:
+                best, out = dt, (done, t_inf)
+        return best, out[0], out[1]
+
+    t_zero, it_zero, _ = timed(False)
+    t_learned, it_learned, t_inf = timed(True)
+    return {"seconds_zero_guess": t_zero, "seconds_learned": t_learned, "seconds_inference_decode": t_inf,
+            "iterations_zero_guess": float(np.mean(it_zero)), "iterations_learned": float(np.mean(it_learned)),
+            "batch_iterations_zero_guess": int(np.max(it_zero)), "batch_iterations_learned": int(np.max(it_learned))}

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libswr.so")
 SWR_OK, SWR_EINVAL, SWR_ENOMEM, SWR_ECUDA, SWR_ESINGULAR, SWR_ENUMERIC, SWR_ENOTCONV, SWR_ETIMEOUT, SWR_ESTATE = range(9)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENUMERIC", "ENOTCONV", "ETIMEOUT", "ESTATE"]
 MODE_TISE, MODE_TDSE = 0, 1
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_FP32_REFINED = 0, 1, 2
 WINDOW_AUTO, WINDOW_TWO_PHASE, WINDOW_FUSED, WINDOW_SPLIT = 0, 1, 2, 3
 TC_ROBIN, TC_DIRICHLET = 0, 1
 SYM_NONE, SYM_ANTISYMMETRIC = 0, 1
@@ -50,7 +50,7 @@ class swr_problem(C.Structure):
     _fields_ = [("n_instances", C.c_int), ("instances", C.POINTER(swr_instance)), ("precision", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
                 ("window_variant", C.c_int), ("rows_per_task", C.c_int), ("launch_mode", C.c_int),
-                ("spin_limit", C.c_longlong)]
+                ("refine_res", C.c_double), ("spin_limit", C.c_longlong)]
 
 
 class swr_tune_report(C.Structure):
@@ -62,12 +62,13 @@ class swr_tune_report(C.Structure):
 
 class swr_iter_report(C.Structure):
     _fields_ = [("k", C.c_int), ("res", C.c_double), ("window_max", C.c_int),
-                ("subdomain_solves", C.c_longlong), ("seconds", C.c_double), ("cvtot", C.c_double)]
+                ("subdomain_solves", C.c_longlong), ("seconds", C.c_double), ("cvtot", C.c_double),
+                ("fp32_matrices", C.c_int)]
 
 
 class swr_report(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("res_last", C.c_double),
-                ("subdomain_solves", C.c_longlong), ("seconds", C.c_double)]
+                ("subdomain_solves", C.c_longlong), ("seconds", C.c_double), ("fp32_iterations", C.c_int)]
 
 
 class swr_trace_view(C.Structure):
@@ -216,7 +217,7 @@ class SWR:
 
     def __init__(self, instances, precision: int = PREC_FP64, device: str = "cuda:0", stream=None,
                  use_torch_workspace: bool = True, window_variant: int = 0, rows_per_task: int = 0,
-                 launch_mode: int = 0, spin_limit: int = 0):
+                 launch_mode: int = 0, spin_limit: int = 0, refine_res: float = 0.0):
         import torch
         self.lib = load_library()
         if isinstance(instances, P.Instance):
@@ -238,6 +239,7 @@ class SWR:
         prob.rows_per_task = int(rows_per_task)
         prob.launch_mode = int(launch_mode)
         prob.spin_limit = int(spin_limit)
+        prob.refine_res = float(refine_res)
         nbytes = C.c_size_t(0)
         self._check(self.lib.swr_workspace_size(C.byref(prob), C.byref(nbytes)), None)
         self.workspace = None
@@ -360,7 +362,7 @@ class SWR:
     def counters(self) -> dict:
         c = self.get(FIELD_COUNTERS)
         keys = ["window_ms", "window_launches", "kernel_launches", "window_flops", "window_bytes",
-                "solves", "assemble_ms", "step_ms", "h2d_bytes", "d2h_bytes"]
+                "solves", "assemble_ms", "step_ms", "h2d_bytes", "d2h_bytes", "window_bytes_alg"]
         return dict(zip(keys, (float(x) for x in c)))
 
     def energy(self) -> np.ndarray:

@@ -56,7 +56,8 @@ int main(void) {{
   F(swr_instance, delta_per_sub) F(swr_instance, x_nuc) F(swr_instance, mode) F(swr_instance, phi0_center)
   F(swr_instance, max_steps) F(swr_instance, orth_tau) F(swr_instance, tc) F(swr_problem, workspace_bytes) F(swr_iter_report, seconds)
   F(swr_problem, window_variant) F(swr_problem, rows_per_task) F(swr_problem, launch_mode)
-  F(swr_problem, spin_limit) F(swr_iter_report, cvtot)
+  F(swr_problem, spin_limit) F(swr_iter_report, cvtot) F(swr_problem, refine_res) F(swr_iter_report, fp32_matrices)
+  F(swr_report, fp32_iterations)
   F(swr_tune_report, graph) F(swr_tune_report, seconds_default)
   return 0;
 }}
@@ -74,9 +75,11 @@ int main(void) {{
     assert int(got["swr_problem.workspace_bytes"]) == S.swr_problem.workspace_bytes.offset
     assert int(got["swr_iter_report.seconds"]) == S.swr_iter_report.seconds.offset
     assert int(got["swr_tune_report"]) == C.sizeof(S.swr_tune_report)
-    for key in ["window_variant", "rows_per_task", "launch_mode", "spin_limit"]:
+    for key in ["window_variant", "rows_per_task", "launch_mode", "spin_limit", "refine_res"]:
         assert int(got[f"swr_problem.{key}"]) == getattr(S.swr_problem, key).offset, key
-    assert int(got["swr_iter_report.cvtot"]) == S.swr_iter_report.cvtot.offset
+    for key in ["cvtot", "fp32_matrices"]:
+        assert int(got[f"swr_iter_report.{key}"]) == getattr(S.swr_iter_report, key).offset, key
+    assert int(got["swr_report.fp32_iterations"]) == S.swr_report.fp32_iterations.offset
     assert int(got["swr_tune_report.seconds_default"]) == S.swr_tune_report.seconds_default.offset
     assert int(got["swr_tune_report.graph"]) == S.swr_tune_report.graph.offset
 
@@ -124,6 +127,9 @@ def test_workspace_size_and_validation_on_host(lib):
     neg = _problem([P.small_tise_2d()], keep)
     neg.spin_limit = -1
     assert lib.swr_workspace_size(C.byref(neg), C.byref(n)) == S.SWR_EINVAL
+    neg = _problem([P.small_tise_2d()], keep)
+    neg.refine_res = -1.0
+    assert lib.swr_workspace_size(C.byref(neg), C.byref(n)) == S.SWR_EINVAL
 
 
 def test_mixed_modes_rejected(lib):
@@ -149,6 +155,11 @@ def test_window_plan_requests_on_host(lib):
         (S.WINDOW_SPLIT, 0, S.PREC_MIXED, True),
         (S.WINDOW_SPLIT, 256, S.PREC_MIXED, True),   # task state in global memory: any task size
         (S.WINDOW_SPLIT, 0, S.PREC_FP64, False),     # the split kernel is the mixed one
+        (S.WINDOW_SPLIT, 0, S.PREC_FP32_REFINED, True),
+        (S.WINDOW_FUSED, 0, S.PREC_FP32_REFINED, True),
+        (0, 0, S.PREC_FP32_REFINED, True),
+        (S.WINDOW_TWO_PHASE, 0, S.PREC_FP32_REFINED, False),  # reads both planes: no FP32 phase
+        (0, 0, 3, False),
         (4, 0, S.PREC_MIXED, False),
         (0, 4, S.PREC_FP64, False),
         (0, 257, S.PREC_FP64, False),

@@ -34,22 +34,27 @@ def S():
 
 
 def _steps(s, n):
-    res, wins, en = [], [], []
+    res, wins, en, cv = [], [], [], []
     for _ in range(n):
         s.step()
         res.append(s.residual().copy())
         wins.append(s.window().copy())
         en.append(s.energy().copy())
+        cv.append(s.cvtot().copy())
+    _steps.cvtot = np.array(cv)
     return np.array(res), np.array(wins), np.array(en)
 
 
-def _check(res, wins, en, refs):
+def _check(res, wins, en, refs, cv=None):
+    cv = _steps.cvtot if cv is None else cv
     for i, ref in enumerate(refs):
         rmax = max(r.res for r in ref.records)
+        cmax = max(r.cvtot for r in ref.records)
         for k, r in enumerate(ref.records):
             assert wins[k][i] == r.n_win, (i, k)
             assert abs(res[k][i] - r.res) <= REL * rmax, (i, k, res[k][i], r.res)
             assert abs(en[k][i] - r.energy) <= REL * abs(r.energy), (i, k, en[k][i], r.energy)
+            assert abs(cv[k][i] - r.cvtot) <= REL * cmax, (i, k, cv[k][i], r.cvtot)
 
 
 PLAN_INST = P.small_tise_2d(K_d=16, q_p=8, n_mid=3)  # 9 subdomains, K = 256

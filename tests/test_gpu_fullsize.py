@@ -1,0 +1,161 @@
+"""GPU parity at the sizes the product runs, against stored oracle values.
+
+The expected values in tests/golden/*.npz were written by
+tests/golden/make_golden.py, which calls only the FP64 CPU oracle:
+
+* tise_2e_16sd_k3: the 2-electron ground-state workload at full size (4 x 4
+  subdomains, K = 576), first three Schwarz iterations; compared through the
+  plans the benchmark runs: the fused double-single window (G_hi rows resident
+  in shared memory), the split double-single window (rows streamed by bulk
+  copies) and the FP64 two-phase window;
+* tdse_2e_k1024_4sd: the real-time workload's subdomain shape (K = 1024
+  complex) on 2 x 2 subdomains, 20 Crank-Nicolson steps, two iterations;
+  FP64 complex matvec and the four-plane double-single one;
+* batched_k1024: three instances of the uneven batch in one launch, two of
+  them with K = 1024 two-electron subdomains (split window stages of 66 KB),
+  two iterations.
+
+Compared per Schwarz iteration: window lengths (exact), Res(k) and CVTOT(k)
+(absolute against 1e-10 of their largest value), energies or norm and dipole
+(1e-10 relative); for the last iteration the own traces and Robin data at
+every interface node of the stored steps plus seeded samples over the whole
+window, and psi at every 7th volume node, against 1e-10 of the largest
+magnitude (Robin data included).  The largest measured differences are
+printed.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1710_02401_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = os.path.join(HERE, "golden")
+REL = 1e-10
+REL_ROBIN = 1e-10
+
+
+@pytest.fixture(scope="module")
+def S():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_02401_gb300 import build as B
+    B.build()
+    from paper_1710_02401_gb300 import swr as S_
+    return S_
+
+
+def _case(name):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(GOLD, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    insts, kmax = mg.case_instances(name)
+    path = os.path.join(GOLD, name + ".npz")
+    if not os.path.exists(path):
+        pytest.fail(f"missing stored values {path}: run tests/golden/make_golden.py {name}")
+    return insts, kmax, dict(np.load(path))
+
+
+def _check(S, name, precision, variant=0, expect_variant=None):
+    insts, kmax, G = _case(name)
+    s = S.SWR(insts, precision=precision, window_variant=variant)
+    s.assemble()
+    plan = s.window_plan()
+    if expect_variant is not None:
+        assert plan["variant"] == expect_variant, plan
+    ni = len(insts)
+    hist = {k: [] for k in ("win", "res", "cvtot", "energy", "norm2", "dipole")}
+    for _ in range(kmax):
+        s.step()
+        hist["win"].append(s.window().astype(np.int64))
+        hist["res"].append(s.residual())
+        hist["cvtot"].append(s.cvtot())
+        if insts[0].mode == P.TDSE:
+            hist["norm2"].append(s.norm2())
+            hist["dipole"].append(s.dipole())
+        else:
+            hist["energy"].append(s.energy())
+    u_all, g_all, psi_all = s.own_traces(), s.robin_data(), s.psi_nodes()
+    worst = {}
+
+    def note(key, val):
+        worst[key] = max(worst.get(key, 0.0), float(val))
+
+    sub0 = 0
+    for ii, inst in enumerate(insts):
+        p = f"i{ii}_"
+        win = np.array([h[ii] for h in hist["win"]])
+        assert win.tolist() == G[p + "win"].tolist(), (name, ii, win, G[p + "win"])
+        for key in ("res", "cvtot"):
+            got = np.array([h[ii] for h in hist[key]])
+            ref = G[p + key]
+            err = np.abs(got - ref).max() / ref.max()
+            note(key, err)
+            assert err <= REL, (name, ii, key, got, ref)
+        if inst.mode == P.TDSE:
+            for key in ("norm2", "dipole"):
+                got = np.array([h[ii] for h in hist[key]])
+                ref = G[p + key]
+                err = (np.abs(got - ref) / np.maximum(np.abs(ref), 1.0 if key == "dipole" else 0.0)).max()
+                note(key, err)
+                assert err <= REL, (name, ii, key, got, ref)
+        else:
+            got = np.array([h[ii] for h in hist["energy"]])
+            ref = G[p + "energy"]
+            err = (np.abs(got - ref) / np.abs(ref)).max()
+            note("energy", err)
+            assert err <= REL, (name, ii, got, ref)
+        st = G[p + "steps"]
+        umax = max(np.abs(G[p + f"u{i}"]).max() for i in range(inst.n_sub) if G[p + f"u{i}"].size)
+        gmax = max(np.abs(G[p + f"g{i}"]).max() for i in range(inst.n_sub) if G[p + f"g{i}"].size)
+        pmax = max(np.abs(G[p + f"psi{i}"]).max() for i in range(inst.n_sub))
+        for i in range(inst.n_sub):
+            u, g, psi = u_all[sub0 + i], g_all[sub0 + i], psi_all[sub0 + i]
+            if G[p + f"u{i}"].size:
+                eu = np.abs(u[st] - G[p + f"u{i}"]).max() / umax
+                eg = np.abs(g[st] - G[p + f"g{i}"]).max() / gmax
+                note("own_traces", eu)
+                note("robin", eg)
+                assert eu <= REL, (name, ii, i, eu)
+                assert eg <= REL_ROBIN, (name, ii, i, eg)
+            ep = np.abs(psi[::int(G["psi_stride"])] - G[p + f"psi{i}"]).max() / pmax
+            note("psi", ep)
+            assert ep <= REL, (name, ii, i, ep)
+        idx = G[p + "smp_idx"]
+        su = np.array([u_all[sub0 + i][n, k] for i, n, k in idx])
+        sg = np.array([g_all[sub0 + i][n, k] for i, n, k in idx])
+        eu = np.abs(su - G[p + "smp_u"]).max() / umax
+        eg = np.abs(sg - G[p + "smp_g"]).max() / gmax
+        note("own_traces", eu)
+        note("robin", eg)
+        assert eu <= REL and eg <= REL_ROBIN, (name, ii, eu, eg)
+        sub0 += inst.n_sub
+    print(f"\n{name} precision={precision} plan={plan}: largest relative differences "
+          + ", ".join(f"{k} {v:.2e}" for k, v in sorted(worst.items())))
+
+
+def test_fullsize_ground_state_fused_double_single(S):
+    _check(S, "tise_2e_16sd_k3", S.PREC_MIXED, 0, expect_variant=S.WINDOW_FUSED)
+
+
+def test_fullsize_ground_state_split_double_single(S):
+    _check(S, "tise_2e_16sd_k3", S.PREC_MIXED, S.WINDOW_SPLIT, expect_variant=S.WINDOW_SPLIT)
+
+
+def test_fullsize_ground_state_fp64(S):
+    _check(S, "tise_2e_16sd_k3", S.PREC_FP64, 0, expect_variant=S.WINDOW_TWO_PHASE)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_fullsize_real_time_k1024(S, precision):
+    _check(S, "tdse_2e_k1024_4sd", precision)
+
+
+@pytest.mark.parametrize("precision,variant", [(1, 3), (1, 0), (0, 0)], ids=["split", "mixed-auto", "fp64"])
+def test_fullsize_batched_k1024(S, precision, variant):
+    _check(S, "batched_k1024", precision, variant)

@@ -109,3 +109,10 @@ def test_learned_guess_saves_schwarz_iterations(mods):
     zero, learned = Lrn.compare(model, test)
     assert np.all(zero <= 60) and np.all(learned <= 61)
     assert learned.mean() < zero.mean()
+    # wall time at the same Res <= 1e-8 for every instance, inference and
+    # decoding of the guess included
+    t = Lrn.compare_timed(model, test)
+    print(f"\nlearned guess: {t}")
+    assert t["batch_iterations_learned"] <= t["batch_iterations_zero_guess"]
+    assert t["seconds_inference_decode"] < 0.1 * t["seconds_learned"]
+    assert t["seconds_learned"] < t["seconds_zero_guess"]

@@ -11,10 +11,14 @@ FP64 tolerance: 1e-10 relative on energies and node values (the workloads'
 bases have kappa(A) <= 1e9, so two backward-stable FP64 solves of the same
 discrete problem agree to ~kappa*eps ~ 1e-7 in coefficients but to ~1e-12 in
 the basis-invariant values); Res(k) is a difference of successive iterates,
-so it is compared absolutely against 1e-10 of the largest residual.  The
-Robin data hold normal derivatives at the subdomain edge, where the
-projected initial data of a sharp-edged basis carry ~10x more rounding
-(measured 1.3e-10 at t = 0): they are compared at 1e-9.
+so it is compared absolutely against 1e-10 of the largest residual; the
+Robin data likewise, except in the heat-equation case: there the initial
+Gaussian (exp(-0.2 x^2) on subdomains of width 11) is poorly represented near
+the subdomain edges, the L2 projection does not control the normal
+derivative at the edge, and the projected coefficients carry kappa(A) eps =
+2e6 x 2.2e-16 = 4.4e-10 of relative rounding in both implementations (LU in
+the raw basis here, the Cholesky-orthonormalised basis there): measured
+1.3e-10 at t = 0, compared at 1e-9.
 """
 import numpy as np
 import pytest
@@ -58,7 +62,7 @@ def _run_gpu(S, inst, kmax, tol=0.0, precision=0, cvtot=None):
     return s, res, wins, energies
 
 
-REL_ROBIN = 1e-9
+REL_ROBIN_PROJECTED_EDGE = 1e-9
 # canonical orthogonalisation: the kept eigenvectors down to ~1e-11 lambda_max
 # are determined only to eps lambda_max / (eigenvalue gap) in direction (Jacobi
 # on the GPU, LAPACK in the oracle); basis-invariant results agree to ~2e-8
@@ -66,7 +70,7 @@ REL_ROBIN = 1e-9
 REL_CANONICAL = 1e-7
 
 
-def _compare(S, inst, kmax, tol=0.0, rel=REL, precision=0):
+def _compare(S, inst, kmax, tol=0.0, rel=REL, precision=0, rel_robin=None):
     ref = O.run_swr(inst, kmax=kmax, tol=tol)
     cv = []
     s, res, wins, energies = _run_gpu(S, inst, len(ref.records), tol, precision, cvtot=cv)
@@ -94,13 +98,18 @@ def _compare(S, inst, kmax, tol=0.0, rel=REL, precision=0):
     for i in range(inst.n_sub):
         assert u[i].shape == ref.own_traces[i].shape
         assert np.abs(u[i] - ref.own_traces[i]).max() <= rel * umax
-        assert np.abs(g[i] - ref.robin[i]).max() <= max(REL_ROBIN, rel) * gmax
+        assert np.abs(g[i] - ref.robin[i]).max() <= (rel_robin or rel) * gmax
     # psi at every volume node of every subdomain
     psi = s.psi_nodes()
     pref = [O.psi_at_nodes(ref.locs[i], ref.coeffs[i]) for i in range(inst.n_sub)]
     pmax = max(np.abs(p).max() for p in pref)
     for i in range(inst.n_sub):
         assert np.abs(psi[i] - pref[i]).max() <= rel * pmax
+    eu = max(np.abs(u[i] - ref.own_traces[i]).max() for i in range(inst.n_sub) if u[i].size) / umax
+    eg = max(np.abs(g[i] - ref.robin[i]).max() for i in range(inst.n_sub) if g[i].size) / gmax
+    ep = max(np.abs(psi[i] - pref[i]).max() for i in range(inst.n_sub)) / pmax
+    print(f"\n[parity] N={inst.n_elec} L={inst.L} K_d={inst.K_d} mode={inst.mode} precision={precision}: "
+          f"own traces {eu:.2e}, Robin data {eg:.2e}, psi {ep:.2e}")
     return s, ref
 
 
@@ -155,7 +164,7 @@ def test_parity_heat_fixed_window(swr_mod):
                       q_p=10, n_mid=5, nuclei=(), ee_coef=0.0, kinetic=1.0, mu=1.0,
                       mode=P.TISE, normalize=False, dt=0.1, n_steps=10, ngf_tol=0.0,
                       phi0_gamma=0.2)
-    _compare(swr_mod, inst, kmax=5)
+    _compare(swr_mod, inst, kmax=5, rel_robin=REL_ROBIN_PROJECTED_EDGE)
 
 
 def test_parity_real_time_one_electron(swr_mod):
