@@ -421,6 +421,10 @@ class IterRecord:
     res: float
     n_win: int
     cvtot: Optional[float] = None
+    # ||c^{n} - c^{n-1}||_chi of the inner NGF stop test (Sec. 5.2) at the last
+    # steps of the window: {n: value} for n = n_win - 1, n_win (imaginary time with
+    # the stop test only)
+    stop_values: Optional[dict] = None
     energy: Optional[float] = None
     norm2: Optional[float] = None
     dipole: Optional[float] = None
@@ -592,6 +596,7 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
         hist_raw = [coeffs]      # iterates before normalisation (solution at t_n^-)
         n_win = fixed if fixed > 0 else inst.max_steps
         n_done = 0
+        stop_q = {}
         for n in range(n_win):
             new = []
             if tdse:
@@ -622,7 +627,10 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
             coeffs = new
             hist.append(coeffs)
             if fixed == 0 and not tdse:
-                if math.sqrt(max(0.0, pou_norm2(locs, diff))) <= inst.ngf_tol:
+                q = math.sqrt(max(0.0, pou_norm2(locs, diff)))
+                stop_q[n_done] = q
+                stop_q.pop(n_done - 2, None)
+                if q <= inst.ngf_tol:
                     break
         # traces of this iteration for all steps 0..n_done
         u_hist = [np.array([locs[i].own_vals @ h[i] for h in hist]) for i in range(S)]
@@ -633,7 +641,8 @@ def run_swr(inst, kmax: int = 50, tol: float = 1e-8, locs: Optional[List[Local]]
         g_hist = [np.array([g_hist_steps[n][i] for n in range(len(hist))]) for i in range(S)]
         # residual against the previous iteration (hold-last beyond a window)
         res = schwarz_residual(locs, dt, u_hist, u_prev)
-        rec = IterRecord(k=k, res=res, n_win=n_done, cvtot=interface_mismatch(locs, ops, hist, dt))
+        rec = IterRecord(k=k, res=res, n_win=n_done, cvtot=interface_mismatch(locs, ops, hist, dt),
+                         stop_values=dict(stop_q) if stop_q else None)
         if tdse:
             rec.norm2 = pou_norm2(locs, coeffs)
             rec.dipole = float(np.real(sum(np.vdot(c, l.Qchi @ c) for l, c in zip(locs, coeffs)))) / rec.norm2

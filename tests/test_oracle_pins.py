@@ -519,3 +519,14 @@ def test_interface_mismatch_stays_at_the_discretisation_error_when_res_vanishes(
     c = [rec.cvtot for rec in r.records]
     assert c[-1] > 1e3 * r.records[-1].res
     assert abs(c[-1] - c[-2]) <= 1e-6 * c[-1]
+
+
+def test_recorded_ngf_stop_values_bracket_the_tolerance():
+    # Sec. 5.2: the window ends at the first step whose ||c^n - c^(n-1)|| is at
+    # most delta; the recorded values of its last two steps straddle delta
+    inst = P.small_tise_2d(L=2, K_d=6, q_p=6, n_mid=2)
+    r = O.run_swr(inst, kmax=2, tol=0.0)
+    for rec in r.records:
+        W = rec.n_win
+        assert set(rec.stop_values) == {W - 1, W}
+        assert rec.stop_values[W] <= inst.ngf_tol < rec.stop_values[W - 1]
