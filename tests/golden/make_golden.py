@@ -19,9 +19,10 @@ Cases (one .npz each, beside this script):
                       seeded 512-instance uneven batch, two Schwarz iterations
 
 Stored per Schwarz iteration: window length, Res(k), CVTOT(k), energy (or
-norm^2 and dipole in real time).  For the last iteration: the own traces u_i
-and the Robin data g_i at every interface node of the steps listed in
-`steps`, plus `n_samples` seeded (subdomain, step, node) samples over the
+norm^2 and dipole in real time), and in imaginary time the NGF stop
+quantity ||c^n - c^(n-1)|| of the window's last two steps (stop_prev,
+stop_last).  For the last iteration: the own traces u_i and the Robin data
+g_i at every interface node of the steps listed in `steps`, plus `n_samples` seeded (subdomain, step, node) samples over the
 whole window; psi at every `psi_stride`-th volume node.
 """
 from __future__ import annotations
@@ -75,6 +76,9 @@ def run_case(name):
         out[p + "win"] = np.array([rec.n_win for rec in r.records], dtype=np.int64)
         out[p + "res"] = np.array([rec.res for rec in r.records])
         out[p + "cvtot"] = np.array([rec.cvtot for rec in r.records])
+        if r.records[0].stop_values:
+            out[p + "stop_prev"] = np.array([rec.stop_values[rec.n_win - 1] for rec in r.records])
+            out[p + "stop_last"] = np.array([rec.stop_values[rec.n_win] for rec in r.records])
         if inst.mode == P.TDSE:
             out[p + "norm2"] = np.array([rec.norm2 for rec in r.records])
             out[p + "dipole"] = np.array([rec.dipole for rec in r.records])
