@@ -469,6 +469,7 @@ def extra_real_time(args, env):
         out[pn] = {"value": rep.subdomain_solves / (ms * 1e-3), "unit": "subdomain solves/s",
                    "ms_per_schwarz_iteration": ms, "window_ms": w_ms, "fp32_matrices": rep.fp32_matrices,
                    "norm2": float(s.norm2()[0]), "dipole": float(s.dipole()[0]),
+                   "tensor_contractions": s.window_plan()["tensor_contractions"],
                    "roofline": {"kernel": "k_cmv_df32 + Crank-Nicolson element-wise kernels" if pn != "fp64"
                                 else "k_cmv + Crank-Nicolson element-wise kernels", "bound": "hbm",
                                 "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
@@ -479,6 +480,33 @@ def extra_real_time(args, env):
     out[args.precision]["speedup_vs_fp64"] = out[args.precision]["value"] / out["fp64"]["value"]
     out["note"] = "second Schwarz iteration (the first is the warm-up), 1000 Crank-Nicolson steps, L2 flushed"
     return out
+
+
+def run_assembly(args, S, reps=3):
+    """swr_assemble timed with CUDA events (library counter), best of `reps`
+    after one warm-up, for both contraction paths."""
+    import torch
+    rows = []
+    for wname in ("tdse_2e_64sd", "tise_2e_16sd"):
+        inst = workload(wname)
+        for pname, path in (("fp64", S.CONTRACT_FP64), ("tensor", S.CONTRACT_TENSOR)):
+            s = S.SWR(inst, precision=S.PREC_MIXED, contraction_path=path)
+            s.assemble()
+            best = float("inf")
+            for _ in range(reps):
+                c0 = s.counters()["assemble_ms"]
+                s.assemble()
+                best = min(best, s.counters()["assemble_ms"] - c0)
+            rows.append({"workload": wname, "contraction": pname, "assemble_ms": best,
+                         "subdomains": inst.n_sub, "K": inst.K_d ** inst.n_elec})
+            s.close()
+            torch.cuda.synchronize()
+    out = {"metric": "swr_assemble time (FP64 vs tensor-core contractions)", "unit": "ms",
+           "higher_is_better": False, "data": "synthetic", "rows": rows}
+    for w in ("tdse_2e_64sd", "tise_2e_16sd"):
+        a = [r["assemble_ms"] for r in rows if r["workload"] == w]
+        out[f"speedup_{w}"] = a[0] / a[1]
+    print(json.dumps(out))
 
 
 def run_learned(args, n_train=160, n_test=24):
@@ -587,6 +615,10 @@ def main():
                     help="learned initial traces: train the BF16 MLP on GPU-generated converged traces of the "
                          "reduced real-time family, then time held-out solves to Res <= 1e-8 from zero traces and "
                          "from the learned guess (inference and decoding included); one JSON line")
+    ap.add_argument("--assembly", action="store_true",
+                    help="time swr_assemble (quadrature, local matrices, orthonormalisation, e-e block, step-matrix "
+                         "inversion) with the FP64 and the tensor-core contractions on the real-time 64-subdomain and "
+                         "the 2-electron ground-state workloads; one JSON line")
     ap.add_argument("--sweep", action="store_true",
                     help="imaginary-time workloads: Schwarz convergence over a grid of time steps and Robin "
                          "constants, Robin and classical (Dirichlet) transmission; one JSON line")
@@ -629,6 +661,12 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
+    if args.assembly:
+        if rank == 0:
+            run_assembly(args, S)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     if args.learned:
         if rank == 0:
             run_learned(args)
@@ -645,7 +683,8 @@ def main():
     def timed(prec_name, steps, warmup, sample_clocks):
         """W untimed + K timed steps (assemble + iterate to Res <= TOL), CUDA
         events on the library's stream, L2 flushed before every step."""
-        s = S.SWR(inst, precision=prec_of[prec_name], device=str(dev), stream=stream)
+        s = S.SWR(inst, precision=prec_of[prec_name], device=str(dev), stream=stream,
+                  window_variant=args.window_variant if prec_name != "fp64" else 0)
         tune = None
         if inst.mode == "tise" and not args.no_autotune:
             s.assemble()
@@ -724,7 +763,8 @@ def main():
         alu = {"achieved": tflops, "peak": FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS / 6.0,
                "unit": "TFLOP/s", "algorithmic": "8 K^2 FP64-equivalent flops per complex sweep"}
     else:
-        kname = {S.WINDOW_FUSED: "k_window_fused", S.WINDOW_SPLIT: "k_window_split"}.get(
+        kname = {S.WINDOW_FUSED: "k_window_fused", S.WINDOW_SPLIT: "k_window_split",
+                 S.WINDOW_RESIDENT: "k_window_resident"}.get(
             main_run["plan"]["variant"], "k_window_2ph<true>" if args.precision != "fp64" else "k_window_2ph<false>")
         alg = (f"{bpe} of the step-matrix inverse per element, K^2 elements per local step solve (the "
                "factor-apply); the 2-electron workload's 42.5 MB of step matrices stay in L2, so the kernel is "
@@ -740,6 +780,9 @@ def main():
     roof["traffic"] = traffic
     roof["traffic_source"] = src
     roof["window_ms_per_launch"] = w_ms / max(w_launch, 1)
+    n_it = max(1, sum(r.iterations for r in reps))
+    roof["post_window_ms_per_iteration"] = (cnt["step_ms"] - w_ms) / n_it
+    roof["assemble_ms_per_step"] = cnt["assemble_ms"] / max(1, args.steps)
     # solved subdomains per step (antisymmetric states: one of each mirror pair)
     n_solved = inst.L * (inst.L + 1) // 2 if getattr(inst, "symmetry", "none") == "antisymmetric" else inst.n_sub
     roof["step_us"] = 1e3 * w_ms / max(1.0, cnt["solves"] / n_solved)
@@ -789,13 +832,15 @@ def main():
         "schwarz_iterations": [r.iterations for r in reps], "converged": all(r.converged for r in reps),
         "res_last": [r.res_last for r in reps],
         "energy": float(s.energy()[0]),
+        "cvtot": float(s.cvtot()[0]),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "subdomain solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": main_run["clocks"],
-        "window_plan": {k: main_run["plan"][k] for k in ("variant", "rows_per_task", "tasks", "ctas", "graph")},
+        "window_plan": {k: main_run["plan"][k] for k in ("variant", "rows_per_task", "tasks", "ctas", "graph",
+                                                         "tensor_contractions")},
     }
     if main_run["tune"] is not None:
         out["window_plan"]["autotune_us_per_step"] = {"chosen": 1e6 * main_run["tune"]["seconds_per_step"],

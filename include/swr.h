@@ -101,7 +101,7 @@ typedef enum swr_window_variant {
                                   W = (Pp (x) Pp) G precomputed, one grid barrier
                                   per step (16 bytes per element); at most 4 row
                                   tasks of at most 64 rows per CTA               */
-    SWR_WINDOW_SPLIT = 3       /* mixed precision only: u = G y^n and
+    SWR_WINDOW_SPLIT = 3,      /* mixed precision only: u = G y^n and
                                   w = G (kappa dt b') in one pass over G before
                                   s_n is known, y^{n+1} = u / s_n + w formed after
                                   the next barrier: one grid barrier per step,
@@ -109,7 +109,34 @@ typedef enum swr_window_variant {
                                   in global memory); the stop on the NGF
                                   tolerance is decided one step later and the
                                   extra step dropped                             */
+    SWR_WINDOW_RESIDENT = 4    /* mixed precision only, no antisymmetric
+                                  instances: the split recursion with static
+                                  tasks (at most 4 of at most 64 rows per CTA)
+                                  whose G_hi rows stay in shared memory for the
+                                  whole window: a step reads only G_lo from L2
+                                  (nothing with the FP32-rounded matrices), no W;
+                                  one grid barrier per step                      */
 } swr_window_variant;
+
+/* Where swr_assemble runs its two dense contractions: the e-e block of the
+ * local Hamiltonians (Sec. 5.1: B^T diag(w V_ee) B, sum-factorised into two
+ * products per subdomain) and the rank-32 trailing updates of the blocked
+ * Gauss-Jordan inversion of the step matrices (Sec. 5.4 step 2: the local
+ * systems I + dt H' and I + i dt/2 H').  Either in FP64 on the FP64 pipe, or
+ * on the 5th-generation tensor cores with FP64 emulated by exact BF16 slices:
+ * every operand row / column scaled by a power of two and cut into integer
+ * slices that BF16 holds exactly (9 slices of 7 bits for the inversion's
+ * 32-long inner products, 11 of 6 bits for the e-e products' inner length up
+ * to 384), one FP32 tensor-memory accumulator per slice level (exact sums),
+ * levels combined in FP64: the dropped terms stay below 2^-63 (inversion) or
+ * 2^-66 (e-e) of the largest operand products times the inner length.     */
+typedef enum swr_contraction {
+    SWR_CONTRACT_AUTO = 0,     /* tensor cores when every subdomain has K >= 768
+                                  (measured: 1.8x the FP64 assembly at K = 1024,
+                                  0.8x at K = 576), else FP64                     */
+    SWR_CONTRACT_FP64 = 1,     /* FP64 products                                   */
+    SWR_CONTRACT_TENSOR = 2    /* tensor-core products                            */
+} swr_contraction;
 
 /* Transmission condition (Sec. 4, "Selection of the transmission
  * conditions"): the data g_i each subdomain takes from its covering
@@ -202,6 +229,11 @@ typedef struct swr_problem {
                                             swr_step returns SWR_ETIMEOUT; 0 selects
                                             the default 2^24 (about one second);
                                             swr_set_spin_limit changes it later      */
+    int                 contraction_path; /* swr_contraction                       */
+    int                 cvtot_each_iteration; /* 1: every swr_step computes CVTOT
+                                            (SWR_FIELD_CVTOT) and reports it in
+                                            swr_iter_report.cvtot; 0: swr_get computes
+                                            it for the last iteration on request   */
 } swr_problem;
 
 typedef struct swr_ctx swr_ctx;
@@ -213,7 +245,8 @@ typedef struct swr_iter_report {
     int       window_max;        /* longest time window of this iteration          */
     long long subdomain_solves;  /* local step solves done in this iteration       */
     double    seconds;           /* device time of the iteration (CUDA events)     */
-    double    cvtot;             /* max over instances of CVTOT(k) (SWR_FIELD_CVTOT) */
+    double    cvtot;             /* max over instances of CVTOT(k) (SWR_FIELD_CVTOT)
+                                    with cvtot_each_iteration, else -1            */
     int       fp32_matrices;     /* 1: this iteration used the FP32-rounded step
                                     matrices (SWR_PREC_FP32_REFINED before the switch) */
 } swr_iter_report;
@@ -312,7 +345,10 @@ typedef enum swr_field {
                                    interface nodes of Omega_i inside closure(Omega_j), psi
                                    the normalised state.  Unlike Res(k) it does not tend to
                                    0: at the converged iterate it is the discretisation
-                                   mismatch of neighbouring local solutions              */
+                                   mismatch of neighbouring local solutions.  Computed
+                                   on this request from the last iteration's line traces
+                                   (they stay until the next swr_step), or in every
+                                   iteration with swr_problem.cvtot_each_iteration      */
 } swr_field;
 swr_status swr_get(swr_ctx* ctx, int field, void* host, size_t bytes);
 
@@ -403,11 +439,13 @@ typedef struct swr_tune_report {
     int    graph;            /* 1: iterations replay a captured CUDA graph      */
     double seconds_per_step; /* best time per window step                       */
     double seconds_default;  /* time per step of the plan before tuning         */
+    int    tensor_contractions; /* 1: assembly runs the Gauss-Jordan updates and
+                                   e-e products on the tensor cores             */
 } swr_tune_report;
 swr_status swr_autotune(swr_ctx* ctx, int steps, swr_tune_report* out);
 
 /* The window plan in use (variant, rows_per_task, tasks, ctas,
- * task_state_global, graph; the timing fields are zero).  variant is 0 for
+ * task_state_global, graph, tensor_contractions; the timing fields are zero).  variant is 0 for
  * real-time problems, whose steps are launched from the host.               */
 swr_status swr_window_plan(const swr_ctx* ctx, swr_tune_report* out);
 

@@ -18,11 +18,18 @@
 #include "swr_internal.cuh"
 
 namespace swr {
+struct TgState;
 cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, int max_kd, int max_K,
                             bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
-                            const GemmJob* d_jobs2, double* d_norm_part);
+                            const GemmJob* d_jobs2, double* d_norm_part, const TgState* tg);
+size_t tg_scratch_bytes(const int* Ks, const int* qs, const int* kds, const int* nel, int n_sub, bool cplx_data,
+                        bool any_ee);
+cudaError_t tg_setup(TgState** out, void* base, const int* Ks, const int* qs, const int* kds, const int* nel, int n_sub,
+                     bool cplx_data, bool any_ee, cudaStream_t st);
+void tg_release(TgState* g);
 size_t window_smem(int kmax, int kdmax, int rows_max, int tasks_in_smem, long long g_resident_floats);
 size_t window_smem_split(int kmax, int kdmax, int rows_max, int stage_floats, int n_stages);
+size_t window_smem_resident(int kmax, int kdmax, int rows_max, int tasks_in_smem, long long g_resident_floats);
 int window_tasks_per_cta_max();
 int window_rows_per_task_max();
 cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, int variant, bool df32);
@@ -33,8 +40,10 @@ extern const int kAssembleLaunchesFixed, kStepLaunches;
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
                         int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax,
-                        bool any_anti, double* d_cv_part, double* d_cvtot);
+                        bool any_anti, double* d_cv_part, double* d_cvtot, bool with_cvtot);
 size_t cvtot_part_doubles(int n_inst);
+cudaError_t launch_cvtot(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm, int cap,
+                         double* d_cv_part, double* d_cvtot);
 cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm,
                           int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
                           double* psi_out, const long long* psi_off, size_t smem);
@@ -113,6 +122,7 @@ struct swr_ctx {
     int* d_qlist = nullptr;
     double *d_res_part = nullptr, *d_res = nullptr, *d_epart = nullptr, *d_energy = nullptr, *d_norm2 = nullptr;
     double *d_cv_part = nullptr, *d_cvtot = nullptr;
+    bool cvtot_valid = false;     // cvtot_h holds the CVTOT of the last iteration
     double* d_psi = nullptr;
     long long* d_psi_off = nullptr;
     cudaStream_t stream = nullptr;
@@ -121,6 +131,9 @@ struct swr_ctx {
     bool assembled = false;
     int k = 0, parity = 0;
     bool step_done = false;       // a swr_step has completed since the last assembly or trace restore
+    bool use_tg = false;          // Gauss-Jordan trailing updates on the tensor cores
+    TgState* tg = nullptr;
+    void* d_tg = nullptr;
     bool refined = false;         // SWR_PREC_FP32_REFINED: switched to the double-single step matrices
     double res_peak = 0.0, res_last = 0.0;  // largest and last Res(k) seen in the FP32 phase
     double iterate_tol = 0.0;     // tolerance of the running swr_iterate (0 outside it)
@@ -286,8 +299,12 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
     if (p->precision != SWR_PREC_FP64 && p->precision != SWR_PREC_MIXED && p->precision != SWR_PREC_FP32_REFINED)
         return fail(c, SWR_EINVAL, "unknown precision");
     if (!(p->refine_res >= 0.0)) return fail(c, SWR_EINVAL, "refine_res must be >= 0 (0: default)");
-    if (p->window_variant < 0 || p->window_variant > SWR_WINDOW_SPLIT)
+    if (p->contraction_path < SWR_CONTRACT_AUTO || p->contraction_path > SWR_CONTRACT_TENSOR)
+        return fail(c, SWR_EINVAL, "unknown contraction_path");
+    if (p->window_variant < 0 || p->window_variant > SWR_WINDOW_RESIDENT)
         return fail(c, SWR_EINVAL, "unknown window variant");
+    if (p->window_variant == SWR_WINDOW_RESIDENT && (p->precision == SWR_PREC_FP64 || mode0 != SWR_MODE_TISE))
+        return fail(c, SWR_EINVAL, "the resident window is a mixed-precision imaginary-time kernel");
     if (p->window_variant == SWR_WINDOW_FUSED && (p->precision == SWR_PREC_FP64 || mode0 != SWR_MODE_TISE))
         return fail(c, SWR_EINVAL, "the fused window is the mixed-precision imaginary-time kernel");
     if (p->window_variant == SWR_WINDOW_SPLIT && (p->precision == SWR_PREC_FP64 || mode0 != SWR_MODE_TISE))
@@ -418,11 +435,14 @@ static bool plan_window(swr_ctx* c, int variant_req, int rows_req, bool have_dev
             variant = (c->df32 && c->has_w && fits) ? WIN_FUSED : c->df32 && !c->tdse ? WIN_SPLIT : WIN_TWO_PHASE;
         if (variant == WIN_FUSED && (!c->df32 || !c->has_w || !fits)) return false;
         if (variant == WIN_SPLIT && !c->df32) return false;
+        if (variant == WIN_RESIDENT && (!c->df32 || c->tdse || c->any_anti || !fits)) return false;
         c->variant = variant;
         c->many = (fits && variant != WIN_SPLIT) ? 0 : 1;  // the split kernel keeps task state in global memory
         const long long gres_floats = (long long)c->max_rows * df32_ld(c->max_K);
-        c->g_resident = variant == WIN_FUSED && c->tasks_per_cta == 1 &&
-                        window_smem(c->max_K, c->max_kd, c->max_rows, 1, gres_floats) <= 110 * 1024;
+        c->g_resident = (variant == WIN_FUSED && c->tasks_per_cta == 1 &&
+                         window_smem(c->max_K, c->max_kd, c->max_rows, 1, gres_floats) <= 110 * 1024) ||
+                        (variant == WIN_RESIDENT && c->tasks_per_cta == 1 &&
+                         window_smem_resident(c->max_K, c->max_kd, c->max_rows, 1, gres_floats) <= 110 * 1024);
         if (variant == WIN_SPLIT) {
             // stages of 4 rows of the widest subdomain (both planes), fewer rows when
             // the shared memory of per_sm CTAs per SM would not hold two of them
@@ -433,6 +453,9 @@ static bool plan_window(swr_ctx* c, int variant_req, int rows_req, bool have_dev
                 if (window_smem_split(c->max_K, c->max_kd, c->max_rows, c->stage_floats, c->n_stages) <= budget) break;
             }
             c->win_smem = window_smem_split(c->max_K, c->max_kd, c->max_rows, c->stage_floats, c->n_stages);
+        } else if (variant == WIN_RESIDENT) {
+            c->win_smem = window_smem_resident(c->max_K, c->max_kd, c->max_rows, c->tasks_per_cta,
+                                               c->g_resident ? gres_floats : 0);
         } else {
             c->win_smem = window_smem(c->max_K, c->max_kd, c->max_rows, c->many ? 1 : c->tasks_per_cta,
                                       c->g_resident ? gres_floats : 0);
@@ -627,7 +650,7 @@ struct AuxPlan {
     size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, cta0, tc, scal, alive, own,
         ctal, wfix, snorm, sums_s, sums_d,
         n_active, win, win_prev, bar, queue, qlist, cnneed, res_part, res, cv_part, cvtot, epart, energy, norm2, dipole, boff,
-        psi, psi_off, total;
+        psi, psi_off, tg, total;
 };
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 static AuxPlan aux_plan(const swr_ctx* c) {
@@ -672,6 +695,17 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.cnneed = o; o = al256(o + c->cn_need.size() + 1);
     a.psi = o; o = al256(o + (size_t)c->psi_total * sizeof(double) * (c->tdse ? 2 : 1));
     a.psi_off = o; o = al256(o + ns * sizeof(long long));
+    a.tg = o;
+    if (c->use_tg) {
+        std::vector<int> Ks(ns), qs(ns), kds(ns), nel(ns);
+        for (size_t s = 0; s < ns; ++s) {
+            Ks[s] = c->sub[s].K;
+            qs[s] = c->sub[s].q;
+            kds[s] = c->sub[s].kd;
+            nel[s] = c->sub[s].N;
+        }
+        o = al256(o + tg_scratch_bytes(Ks.data(), qs.data(), kds.data(), nel.data(), (int)ns, c->tdse, c->any_ee));
+    }
     a.total = o;
     return a;
 }
@@ -688,6 +722,11 @@ static bool plan_for_device(swr_ctx* c, const swr_problem* p) {
         c->nsm = 152;
     }
     plan(c);  // descriptors and arena
+    // automatic: the tensor-core contractions where they measured faster, when
+    // every subdomain has K >= 768 (K = 1024: 1.8x the FP64 assembly; K = 576: 0.8x)
+    bool all_large = !c->sub.empty();
+    for (const SubDev& sd : c->sub) all_large = all_large && sd.K >= 768;
+    c->use_tg = p->contraction_path == SWR_CONTRACT_TENSOR || (p->contraction_path == SWR_CONTRACT_AUTO && all_large);
     c->tasks_cap = task_capacity(c);
     c->any_ngf_stop = false;
     for (const InstDev& d : c->inst)
@@ -823,6 +862,19 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->d_cn_need = (unsigned char*)(b + a.cnneed);
     c->d_psi = (double*)(b + a.psi);
     c->d_psi_off = (long long*)(b + a.psi_off);
+    if (c->use_tg) {
+        const size_t ns = c->sub.size();
+        std::vector<int> Ks(ns), qs(ns), kds(ns), nel(ns);
+        for (size_t s = 0; s < ns; ++s) {
+            Ks[s] = c->sub[s].K;
+            qs[s] = c->sub[s].q;
+            kds[s] = c->sub[s].kd;
+            nel[s] = c->sub[s].N;
+        }
+        c->d_tg = (void*)(b + a.tg);
+        CU(tg_setup(&c->tg, c->d_tg, Ks.data(), qs.data(), kds.data(), nel.data(), (int)ns, c->tdse, c->any_ee,
+                    c->stream));
+    }
     // GEMM jobs of the sum-factorised e-e block
     std::vector<GemmJob> j1(c->sub.size()), j2(c->sub.size());
     for (size_t s = 0; s < c->sub.size(); ++s) {
@@ -911,7 +963,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream));
     CU(cudaEventRecord(c->ev0, c->stream));
     CU(launch_assemble(view(c), c->stream, c->max_q, c->max_kd, c->max_K, c->any_ee, c->tdse, !c->tdse,
-                       c->d_jobs1, c->d_jobs2, c->d_norm_part));
+                       c->d_jobs1, c->d_jobs2, c->d_norm_part, c->tg));
     if (c->df32 && !c->tdse) CU(launch_split_df32(view(c), c->stream, c->max_K, c->has_w));
     if (c->df32 && c->tdse) CU(launch_split_c_df32(view(c), c->stream, c->max_K));
     CU(cudaEventRecord(c->ev1, c->stream));
@@ -920,7 +972,8 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     float ams = 0;
     CU(cudaEventElapsedTime(&ams, c->ev0, c->ev1));
     c->counters[6] += ams;
-    c->counters[2] += kAssembleLaunchesFixed + (c->any_ee ? 3 : 0) + 2 * ((c->max_K + GJ_NB_HOST - 1) / GJ_NB_HOST) +
+    c->counters[2] += kAssembleLaunchesFixed + (c->any_ee ? (c->tg ? 7 : 3) : 0) +
+                      (c->tg ? 4 : 2) * ((c->max_K + GJ_NB_HOST - 1) / GJ_NB_HOST) +
                       (c->df32 ? (c->tdse || !c->has_w ? 1 : 2) : 0);
     c->assembled = true;
     c->k = 0;
@@ -997,7 +1050,7 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
     if (e == cudaSuccess)
         e = launch_post(view(c), st, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
                         c->d_res_part, RES_BLOCKS, c->d_res, c->cap, c->max_K, c->max_kd, c->max_q, c->any_anti,
-                        c->d_cv_part, c->d_cvtot);
+                        c->d_cv_part, c->d_cvtot, c->prob.cvtot_each_iteration != 0);
     if (e == cudaSuccess)
         e = launch_energy(view(c), st, c->d_win, c->d_snorm, c->cap, c->d_epart, c->d_energy, c->d_norm2,
                           c->d_dipole, c->d_psi, c->d_psi_off, c->energy_smem);
@@ -1065,10 +1118,12 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     CU(cudaMemcpyAsync(c->energy_h.data(), c->d_energy, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(c->norm2_h.data(), c->d_norm2, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(c->dipole_h.data(), c->d_dipole, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(c->cvtot_h.data(), c->d_cvtot, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    c->counters[9] += (double)(ni * (5 * sizeof(double) + sizeof(int)));
+    if (c->prob.cvtot_each_iteration)
+        CU(cudaMemcpyAsync(c->cvtot_h.data(), c->d_cvtot, ni * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    c->counters[9] += (double)(ni * ((c->prob.cvtot_each_iteration ? 5 : 4) * sizeof(double) + sizeof(int)));
     swr_status st = check_err(c);
     if (st != SWR_OK) return st;
+    c->cvtot_valid = c->prob.cvtot_each_iteration != 0;
     // the current window becomes the previous one for the next iteration
     CU(cudaMemcpyAsync(c->d_win_prev, c->d_win, ni * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
     c->win_pp_h = c->win_prev_h;
@@ -1081,7 +1136,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     for (size_t i = 0; i < ni; ++i) {
         if (!isfinite(c->res_h[i])) return fail(c, SWR_ENUMERIC, "non-finite residual in instance %zu", i);
         rmax = c->res_h[i] > rmax ? c->res_h[i] : rmax;
-        cmax = c->cvtot_h[i] > cmax ? c->cvtot_h[i] : cmax;
+        if (c->cvtot_valid) cmax = c->cvtot_h[i] > cmax ? c->cvtot_h[i] : cmax;
         wmax = c->win_h[i] > wmax ? c->win_h[i] : wmax;
         // antisymmetric states: the lower subdomain of a mirror pair is not solved
         const int solved = c->inst[i].anti ? c->inst[i].L * (c->inst[i].L + 1) / 2 : c->inst[i].n_sub;
@@ -1111,7 +1166,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     }
     c->counters[0] += wms;
     c->counters[1] += 1;
-    c->counters[2] += kStepLaunches - 1 + win_launches + (c->any_anti ? 1 : 0);
+    c->counters[2] += kStepLaunches - 1 + win_launches + (c->any_anti ? 1 : 0) + (c->prob.cvtot_each_iteration ? 2 : 0);
     c->counters[3] += flops;
     c->counters[4] += bytes;
     c->counters[5] += (double)solves;
@@ -1123,7 +1178,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
         rep->window_max = wmax;
         rep->subdomain_solves = solves;
         rep->seconds = ms * 1e-3;
-        rep->cvtot = cmax;
+        rep->cvtot = c->cvtot_valid ? cmax : -1.0;
         rep->fp32_matrices = go;
     }
     if (go) {
@@ -1175,6 +1230,7 @@ extern "C" swr_status swr_window_plan(const swr_ctx* c, swr_tune_report* out) {
     out->ctas = c->grid;
     out->task_state_global = c->many;
     out->graph = (c->prob.launch_mode == SWR_LAUNCH_GRAPH && !c->graph_failed) ? 1 : 0;
+    out->tensor_contractions = c->use_tg ? 1 : 0;
     return SWR_OK;
 }
 
@@ -1189,10 +1245,11 @@ extern "C" swr_status swr_autotune(swr_ctx* c, int steps, swr_tune_report* out) 
     std::vector<Cand> cands;
     cands.push_back({c->prob.window_variant, c->prob.rows_per_task});  // the plan before tuning
     const int rows_list[] = {0, 16, 32, 64, 128, 256};
-    const int variants[] = {WIN_TWO_PHASE, WIN_FUSED, WIN_SPLIT};
+    const int variants[] = {WIN_TWO_PHASE, WIN_FUSED, WIN_SPLIT, WIN_RESIDENT};
     for (int v : variants) {
         if (v == WIN_FUSED && !(c->df32 && c->has_w)) continue;
-        if (v == WIN_SPLIT && !c->df32) continue;
+        if ((v == WIN_SPLIT || v == WIN_RESIDENT) && !c->df32) continue;
+        if (v == WIN_TWO_PHASE && c->prob.precision == SWR_PREC_FP32_REFINED) continue;  // reads both planes
         for (int r : rows_list) cands.push_back({v, r});
     }
     std::vector<std::vector<int>> seen;  // (variant, tasks, grid, rows target) of the plans timed
@@ -1312,7 +1369,18 @@ extern "C" swr_status swr_get(swr_ctx* c, int field, void* host, size_t bytes) {
         case SWR_FIELD_ENERGY: memcpy(host, c->energy_h.data(), need); return SWR_OK;
         case SWR_FIELD_NORM2: memcpy(host, c->norm2_h.data(), need); return SWR_OK;
         case SWR_FIELD_RES: memcpy(host, c->res_h.data(), need); return SWR_OK;
-        case SWR_FIELD_CVTOT: memcpy(host, c->cvtot_h.data(), need); return SWR_OK;
+        case SWR_FIELD_CVTOT:
+            if (c->k == 0) return fail(c, SWR_ESTATE, "no iteration done yet");
+            if (!c->cvtot_valid) {
+                CU(launch_cvtot(view(c), c->stream, c->d_win, c->d_snorm, c->cap, c->d_cv_part, c->d_cvtot));
+                CU(cudaMemcpyAsync(c->cvtot_h.data(), c->d_cvtot, need, cudaMemcpyDeviceToHost, c->stream));
+                CU(cudaStreamSynchronize(c->stream));
+                c->counters[2] += 2;
+                c->counters[9] += (double)need;
+                c->cvtot_valid = true;
+            }
+            memcpy(host, c->cvtot_h.data(), need);
+            return SWR_OK;
         case SWR_FIELD_WINDOW: memcpy(host, c->win_h.data(), need); return SWR_OK;
         case SWR_FIELD_DIPOLE: memcpy(host, c->dipole_h.data(), need); return SWR_OK;
         case SWR_FIELD_K_MAX: memcpy(host, &c->k, sizeof(int)); return SWR_OK;
@@ -1458,6 +1526,7 @@ void codec_release(const swr_ctx* c);
 extern "C" void swr_destroy(swr_ctx* c) {
     if (!c) return;
     codec_release(c);
+    if (c->tg) tg_release(c->tg);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     if (c->ev0) cudaEventDestroy(c->ev0);

@@ -879,9 +879,16 @@ static inline unsigned div_up(long long a, long long b) { return (unsigned)((a +
 // symmetrize, step_matrix, project, anti_c0, normalize_c0.
 extern const int kAssembleLaunchesFixed = 9;
 
+struct TgState;
+cudaError_t tg_update(const TgState* g, const SwrDeviceView& v, cudaStream_t st, int kb, int max_K);
+bool tg_has_ee(const TgState* g);
+cudaError_t te_products(const TgState* g, const SwrDeviceView& v, cudaStream_t st, const GemmJob* d_jobs1,
+                        const GemmJob* d_jobs2);
+
+// tg: the tensor-core Gauss-Jordan state (swr_tcgj.cu) or null for the FP64 updates.
 cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, int max_kd, int max_K,
                             bool any_ee, bool any_tdse, bool any_tise, const GemmJob* d_jobs1,
-                            const GemmJob* d_jobs2, double* d_norm_part) {
+                            const GemmJob* d_jobs2, double* d_norm_part, const TgState* tg) {
     dim3 g2(v.n_sub, 2);
     k_tabulate<<<g2, 256, 0, st>>>(v);
     k_mat1d<<<g2, 256, 0, st>>>(v);
@@ -890,11 +897,17 @@ cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, 
     k_orth<<<g2, 256, sm, st>>>(v);
     if (any_ee) {
         k_ee_operands<<<dim3(v.n_sub, 16), 256, 0, st>>>(v);
-        int kd2 = max_kd * max_kd;
-        // Mee = Wv (q x q) * P2 (q x kd^2)
-        k_dgemm<<<dim3(div_up(kd2, GT), div_up(max_q, GT), v.n_sub), 256, 0, st>>>(v, d_jobs1);
-        // V'ee[(a,c),(b,e)] = P1^T (kd^2 x q) * Mee (q x kd^2), scattered into H'
-        k_dgemm<<<dim3(div_up(kd2, GT), div_up(kd2, GT), v.n_sub), 256, 0, st>>>(v, d_jobs2);
+        if (tg_has_ee(tg)) {
+            // the same two products on the tensor cores (FP64 emulated by BF16 slices)
+            cudaError_t e = te_products(tg, v, st, d_jobs1, d_jobs2);
+            if (e != cudaSuccess) return e;
+        } else {
+            int kd2 = max_kd * max_kd;
+            // Mee = Wv (q x q) * P2 (q x kd^2)
+            k_dgemm<<<dim3(div_up(kd2, GT), div_up(max_q, GT), v.n_sub), 256, 0, st>>>(v, d_jobs1);
+            // V'ee[(a,c),(b,e)] = P1^T (kd^2 x q) * Mee (q x kd^2), scattered into H'
+            k_dgemm<<<dim3(div_up(kd2, GT), div_up(kd2, GT), v.n_sub), 256, 0, st>>>(v, d_jobs2);
+        }
     }
     dim3 ge(div_up((long long)max_K * max_K, 256 * 8), v.n_sub);
     k_h_kron<<<ge, 256, 0, st>>>(v, any_ee ? 1 : 0);
@@ -905,11 +918,21 @@ cudaError_t launch_assemble(const SwrDeviceView& v, cudaStream_t st, int max_q, 
         if (any_tdse) {
             dim3 gu(div_up(max_K, 32), div_up(max_K, 32), v.n_sub);
             k_gj_panel<cplx><<<v.n_sub, 256, 0, st>>>(v, kb);
-            k_gj_update<cplx><<<gu, 256, 0, st>>>(v, kb);
+            if (tg) {
+                cudaError_t e = tg_update(tg, v, st, kb, max_K);
+                if (e != cudaSuccess) return e;
+            } else {
+                k_gj_update<cplx><<<gu, 256, 0, st>>>(v, kb);
+            }
         } else {
             dim3 gu(div_up(max_K, 64), div_up(max_K, 64), v.n_sub);
             k_gj_panel<double><<<v.n_sub, 256, 0, st>>>(v, kb);
-            k_gj_update<double><<<gu, 256, 0, st>>>(v, kb);
+            if (tg) {
+                cudaError_t e = tg_update(tg, v, st, kb, max_K);
+                if (e != cudaSuccess) return e;
+            } else {
+                k_gj_update<double><<<gu, 256, 0, st>>>(v, kb);
+            }
         }
     }
     k_project<<<v.n_sub, 256, 0, st>>>(v, d_norm_part);

@@ -202,7 +202,7 @@ struct TaskCache {
 };
 
 // Window kernel variants.
-enum WindowVariant { WIN_TWO_PHASE = 1, WIN_FUSED = 2, WIN_SPLIT = 3 };
+enum WindowVariant { WIN_TWO_PHASE = 1, WIN_FUSED = 2, WIN_SPLIT = 3, WIN_RESIDENT = 4 };
 
 // Event record that becomes an event-record node of the graph under stream
 // capture (external record) and is a plain record otherwise.

@@ -572,14 +572,15 @@ __global__ void k_anti_fill(SwrDeviceView v, const int* win) {
 static inline unsigned div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // Kernel launches per swr_step besides the window (reset, window, line traces,
-// gather, residual, residual reduce, CVTOT, CVTOT reduce, energy, energy
-// reduce; one more with antisymmetric instances: the mirror fill).
-extern const int kStepLaunches = 10;
+// gather, residual, residual reduce, energy, energy reduce; two more with
+// CVTOT in every iteration, one more with antisymmetric instances: the mirror
+// fill).
+extern const int kStepLaunches = 8;
 
 cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                         const double* d_snorm, int cap, int parity, int first_iter, double* d_res_part,
                         int res_blocks, double* d_res, int max_cap_hint, int lt_kmax, int lt_kdmax, int lt_qmax,
-                        bool any_anti, double* d_cv_part, double* d_cvtot) {
+                        bool any_anti, double* d_cv_part, double* d_cvtot, bool with_cvtot) {
     int nb = 64;
     if (any_anti) k_anti_fill<<<dim3(nb, v.n_sub), 256, 0, st>>>(v, d_win);
     {
@@ -598,6 +599,17 @@ cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_wi
     }
     k_residual<<<dim3(res_blocks, v.n_sub), 256, 0, st>>>(v, d_win, d_win_prev, parity, first_iter, d_res_part);
     k_residual_reduce<<<v.n_inst, 256, 0, st>>>(v, d_res_part, res_blocks, d_res);
+    if (with_cvtot) {
+        k_cvtot<<<dim3(CV_BLOCKS, v.n_inst), 256, 0, st>>>(v, d_win, d_snorm, cap, d_cv_part);
+        k_cvtot_reduce<<<div_up(v.n_inst, 128), 128, 0, st>>>(v.n_inst, d_cv_part, CV_BLOCKS, d_cvtot);
+    }
+    return cudaGetLastError();
+}
+
+// CVTOT of the last iteration on request (its line traces, windows and
+// normalisations are still in place until the next swr_step).
+cudaError_t launch_cvtot(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const double* d_snorm, int cap,
+                         double* d_cv_part, double* d_cvtot) {
     k_cvtot<<<dim3(CV_BLOCKS, v.n_inst), 256, 0, st>>>(v, d_win, d_snorm, cap, d_cv_part);
     k_cvtot_reduce<<<div_up(v.n_inst, 128), 128, 0, st>>>(v.n_inst, d_cv_part, CV_BLOCKS, d_cvtot);
     return cudaGetLastError();

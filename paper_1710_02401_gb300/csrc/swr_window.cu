@@ -971,6 +971,257 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_fused(SweepArgs A) {
     }
 }
 
+// ------------------------------------------------ resident single-plane window
+//
+// The split recursion (u^{m+1} = G y^m and w^{m+1} = G (kappa dt b'^{m+1}) in
+// one pass over G, y^{m+1} = u^{m+1} / s_m + w^{m+1} formed after the barrier,
+// the NGF stop decided one step later) with the fused window's static tasks:
+// every CTA keeps its tasks and the G_hi rows of its (single) task resident
+// in shared memory for the whole window, so a step reads from L2 only the
+// G_lo plane of its rows (nothing in the FP32 phase, ONEP), the u and w of its
+// subdomain and the partials; no W = (Pp (x) Pp) G.  One release-only grid
+// barrier per step; each CTA sums its instances' partials itself, in a fixed
+// order.  At most WIN_TPC tasks of at most WIN_RB rows per CTA.
+// Dynamic shared memory: vs[kmax4] doubles | vf[kmax4] float2 | bf[kmax4] float2
+// | tmp[rows_max + 2 kdmax] | Psm[tasks][2][kdmax^2] | (16-byte aligned) G_hi rows.
+template <bool ONEP>
+__global__ void __launch_bounds__(WIN_THREADS, 2) k_window_resident(SweepArgs A) {
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    __shared__ TaskCache tcs[WIN_TPC];
+    __shared__ double own[WIN_TPC][6][WIN_RB];  // y slots 0..2, z slots 3..5 (ring of 3, by step)
+    __shared__ double is1_sm[WIN_TPC], is2_sm[WIN_TPC];  // 1/s_{m-1}, 1/s_{m-2} of the task's instance
+    __shared__ int alive[WIN_TPC];
+    __shared__ int s_stop;
+    __shared__ double s2_sm[WIN_TPC], d2_sm[WIN_TPC];  // s_{m-1}^2 and D_{m-2} of each task's instance
+    long long pofs = 0;
+    int go = 1;
+    const SwrDeviceView& v = A.v;
+    const int t_begin = A.cta_task0[blockIdx.x];
+    const int ntk = A.cta_task0[blockIdx.x + 1] - t_begin;
+    const int cap = A.cap;
+    const int kmax = df32_ld(A.kmax), kdmax = A.kdmax;
+    double* vs = sm;
+    float2* vf = (float2*)(sm + kmax);
+    float2* bf = (float2*)(sm + 2 * kmax);
+    double* tmp = sm + 3 * kmax;
+    double* Psm = tmp + A.rows_max + 2 * kdmax;
+    float* Gsm = (float*)(Psm + (long long)A.tasks_per_cta * 2 * kdmax * kdmax + (A.rows_max & 1));
+    const bool gres = A.g_resident != 0;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = WIN_THREADS / 32;
+    unsigned target = 0, gen = 0;
+
+    for (int j = 0; j < ntk; ++j) {
+        const int t = A.cta_list[t_begin + j];
+        if (tid == 0) {
+            tcs[j] = make_task_cache(A, t);
+            alive[j] = 1;
+            is1_sm[j] = 1.0;
+            is2_sm[j] = 1.0;
+        }
+        __syncthreads();
+        const TaskCache& tc = tcs[j];
+        double* P1 = Psm + (long long)j * 2 * kdmax * kdmax;
+        double* P2 = P1 + (long long)kdmax * kdmax;
+        for (int e = tid; e < tc.kd * tc.kd; e += WIN_THREADS) {
+            P1[e] = v.arena[tc.p1 + e];
+            P2[e] = v.arena[tc.p2 + e];
+        }
+        if (gres) {
+            const float* Gh = (const float*)(v.arena + tc.Gf);
+            const long long ld = df32_ld(tc.K);
+            for (long long e = tid; e < (long long)tc.nr * ld; e += WIN_THREADS) Gsm[e] = Gh[(long long)tc.r0 * ld + e];
+        }
+    }
+    __syncthreads();
+    auto task_sums = [&]() {
+        for (int j = 0; j < ntk; ++j) {
+            const int i = tcs[j].inst;
+            if (j > 0 && tcs[j - 1].inst == i) {
+                if (tid == 0) {
+                    s2_sm[j] = s2_sm[j - 1];
+                    d2_sm[j] = d2_sm[j - 1];
+                }
+                continue;
+            }
+            block_sums2(A.part_s + pofs, A.part_d + pofs, A.inst_task0[i], A.inst_task0[i + 1], red, &s2_sm[j],
+                        &d2_sm[j]);
+        }
+        __syncthreads();
+        pofs = pofs ? 0 : A.n_tasks;
+    };
+
+    for (int m = 0;; ++m) {
+        for (int j = 0; j < ntk; ++j) {
+            __syncthreads();
+            if (!alive[j]) continue;
+            const TaskCache& tc = tcs[j];
+            const int K = tc.K, nr = tc.nr, ld = df32_ld(K);
+            const int t = A.cta_list[t_begin + j];
+            const SubDev& sd = v.sub[tc.sid];
+            if (tid == 0) {
+                int stop = 0;
+                if (m >= 1) {
+                    // the plain algorithm's stop at n = m-2 (D_{m-2}), else at n = m-1
+                    // (cap, or s_{m-1} not positive and finite)
+                    const double s2 = tc.normalize ? s2_sm[j] : 1.0;
+                    const double is1 = tc.normalize ? rsqrt(s2) : 1.0;
+                    const double s1 = tc.normalize ? s2 * is1 : 1.0;
+                    int win = 0;
+                    const bool bad = !isfinite(s1) || s1 <= 0.0;
+                    if (m >= 3 && tc.ngf_stop && sqrt(fmax(d2_sm[j], 0.0)) <= tc.ngf_tol) {
+                        stop = 1;
+                        win = m - 2;
+                    } else if (m - 1 >= tc.maxs || bad) {
+                        stop = 1;
+                        win = m - 1;
+                    }
+                    if (tc.first) A.snorm[(long long)tc.inst * (cap + 1) + m - 1] = s1;
+                    if (stop) {
+                        alive[j] = 0;
+                        if (tc.first) {
+                            A.win[tc.inst] = win;
+                            if (bad) atomicOr(v.err, SWR_ERR_NUMERIC);
+                            __threadfence();
+                            atomicSub(A.n_active, 1);
+                        }
+                    } else {
+                        is2_sm[j] = is1_sm[j];
+                        is1_sm[j] = is1;
+                    }
+                }
+                s_stop = stop;
+            }
+            __syncthreads();
+            if (s_stop) continue;
+            const double is1 = is1_sm[j], is2 = is2_sm[j];
+            // full y^m = u^m / s_{m-1} + w^m of the subdomain (y^0 = c0) and kappa dt b'^{m+1}
+            const int wp = A.win_prev[tc.inst];
+            const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(m + 1, wp) * K : nullptr;
+            {
+                const double* U = v.arena + sd.work + (long long)(m & 1) * 2 * K;
+                const double* Wv = U + K;
+                const double* c0 = v.arena + tc.c0;
+                for (int c = tid; c < ld; c += WIN_THREADS) {
+                    if (c < K) {
+                        const double y = m == 0 ? c0[c] : __ldcg(U + c) * is1 + __ldcg(Wv + c);
+                        vs[c] = y;
+                        vf[c] = ds_split(y);
+                        bf[c] = bsrc ? ds_split(tc.kdt * bsrc[c]) : make_float2(0.f, 0.f);
+                    } else {
+                        vf[c] = make_float2(0.f, 0.f);
+                        bf[c] = make_float2(0.f, 0.f);
+                    }
+                }
+            }
+            __syncthreads();
+            double* ym = own[j][m % 3];
+            double* hrow = v.arena + tc.hist + (long long)m * K;
+            for (int r = tid; r < nr; r += WIN_THREADS) {
+                ym[r] = vs[tc.r0 + r];
+                hrow[tc.r0 + r] = vs[tc.r0 + r];
+            }
+            double* P1 = Psm + (long long)j * 2 * kdmax * kdmax;
+            double* P2 = P1 + (long long)kdmax * kdmax;
+            double* zm = own[j][3 + m % 3];
+            z_rows_sm(tc, P1, P2, vs, zm, tmp);  // ends with a block barrier
+            // partials: s_m^2 (own rows of y^m . z^m) and D_{m-1} = ||c^{m-1} - c^{m-2}||_chi^2
+            {
+                const bool dn = m >= 2 && tc.ngf_stop;
+                const double* y1 = own[j][(m + 2) % 3];
+                const double* y2 = own[j][(m + 1) % 3];
+                const double* z1 = own[j][3 + (m + 2) % 3];
+                const double* z2 = own[j][3 + (m + 1) % 3];
+                double acc = 0, accd = 0;
+                for (int r = tid; r < nr; r += WIN_THREADS) {
+                    acc += ym[r] * zm[r];
+                    if (dn) accd += (y1[r] * is1 - y2[r] * is2) * (z1[r] * is1 - z2[r] * is2);
+                }
+                acc = warp_sum(acc);
+                accd = warp_sum(accd);
+                if (lane == 0) {
+                    red[warp] = acc;
+                    red[16 + warp] = accd;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    double a = 0, b = 0;
+                    for (int i = 0; i < nw; ++i) {
+                        a += red[i];
+                        b += red[16 + i];
+                    }
+                    A.part_s[pofs + t] = a;
+                    if (dn) A.part_d[pofs + t] = b;
+                }
+            }
+            if (m >= tc.maxs) continue;  // no step beyond the cap
+            // rows of u^{m+1} = G y^m and w^{m+1} = G (kappa dt b'^{m+1}): two rows per
+            // warp at a time, G_hi from shared memory (or L2), G_lo from L2 (ONEP: none)
+            double* Un = v.arena + sd.work + (long long)((m + 1) & 1) * 2 * K;
+            double* Wn = Un + K;
+            const float* Ghg = (const float*)(v.arena + tc.Gf);
+            const float* Gl = Ghg + (long long)K * ld;
+            const bool hasb = bsrc != nullptr;
+            for (int rb = tc.r0 + 2 * warp; rb < tc.r0 + nr; rb += 2 * nw) {
+                const int nrow = min(2, tc.r0 + nr - rb);
+                float yh[2] = {0.f, 0.f}, yl[2] = {0.f, 0.f}, wh[2] = {0.f, 0.f}, wl[2] = {0.f, 0.f};
+                for (int c = lane * 4; c < ld; c += 128) {
+                    const float4 xa = *reinterpret_cast<const float4*>(vf + c);
+                    const float4 xb = *reinterpret_cast<const float4*>(vf + c + 2);
+                    const float4 ba = *reinterpret_cast<const float4*>(bf + c);
+                    const float4 bb = *reinterpret_cast<const float4*>(bf + c + 2);
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        if (i < nrow) {
+                            const long long o = (long long)(rb + i) * ld + c;
+                            const float* ghp = gres ? Gsm + (long long)(rb + i - tc.r0) * ld + c : Ghg + o;
+                            const float4 g0 = *reinterpret_cast<const float4*>(ghp);
+                            const float4 g1 = ONEP ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                   : *reinterpret_cast<const float4*>(Gl + o);
+                            df32_acc(yh[i], yl[i], g0.x, g1.x, xa.x, xa.y);
+                            df32_acc(yh[i], yl[i], g0.y, g1.y, xa.z, xa.w);
+                            df32_acc(yh[i], yl[i], g0.z, g1.z, xb.x, xb.y);
+                            df32_acc(yh[i], yl[i], g0.w, g1.w, xb.z, xb.w);
+                            if (hasb) {
+                                df32_acc(wh[i], wl[i], g0.x, g1.x, ba.x, ba.y);
+                                df32_acc(wh[i], wl[i], g0.y, g1.y, ba.z, ba.w);
+                                df32_acc(wh[i], wl[i], g0.z, g1.z, bb.x, bb.y);
+                                df32_acc(wh[i], wl[i], g0.w, g1.w, bb.z, bb.w);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        float sh, eh;
+                        float oh = __shfl_xor_sync(0xffffffffu, yh[i], o), ol = __shfl_xor_sync(0xffffffffu, yl[i], o);
+                        two_sum(yh[i], oh, sh, eh);
+                        yh[i] = sh;
+                        yl[i] = yl[i] + ol + eh;
+                        oh = __shfl_xor_sync(0xffffffffu, wh[i], o);
+                        ol = __shfl_xor_sync(0xffffffffu, wl[i], o);
+                        two_sum(wh[i], oh, sh, eh);
+                        wh[i] = sh;
+                        wl[i] = wl[i] + ol + eh;
+                    }
+                    if (lane == 0 && i < nrow) {
+                        Un[rb + i] = (double)yh[i] + (double)yl[i];
+                        Wn[rb + i] = (double)wh[i] + (double)wl[i];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        target += gridDim.x;
+        ++gen;
+        if (!release_barrier(&A.bar->count, &A.bar->gen, target, gen, v.err, A.spin_limit, A.n_active, &go)) return;
+        if (!go) return;
+        task_sums();
+    }
+}
+
 // ------------------------------------------------------- single-barrier window
 //
 // Mixed precision, batches of any size, ONE reduce-barrier per step, G streamed
@@ -1631,10 +1882,20 @@ size_t window_smem_split(int kmax, int kdmax, int rows_max, int stage_floats, in
            (size_t)n_stages * stage_floats * sizeof(float);
 }
 
+// Resident window: vs, vf, bf (3 kmax4 doubles), tmp, the tasks' Kronecker
+// factors and the resident G_hi rows.
+size_t window_smem_resident(int kmax, int kdmax, int rows_max, int tasks_in_smem, long long g_resident_floats) {
+    return (3 * (size_t)df32_ld(kmax) + (size_t)rows_max + 2 * (size_t)kdmax +
+            (size_t)tasks_in_smem * 2 * kdmax * kdmax + 1) * sizeof(double) +
+           (size_t)g_resident_floats * sizeof(float);
+}
+
 int window_tasks_per_cta_max() { return WIN_TPC; }
 int window_rows_per_task_max() { return WIN_RB; }
 
 static const void* window_kernel(int variant, bool df32, bool onep) {
+    if (variant == WIN_RESIDENT)
+        return onep ? (const void*)k_window_resident<true> : (const void*)k_window_resident<false>;
     if (variant == WIN_FUSED) return onep ? (const void*)k_window_fused<true> : (const void*)k_window_fused<false>;
     if (variant == WIN_SPLIT) return onep ? (const void*)k_window_split<true> : (const void*)k_window_split<false>;
     return df32 ? (const void*)k_window_2ph<true> : (const void*)k_window_2ph<false>;
@@ -1645,7 +1906,7 @@ static const void* window_kernel(int variant, bool df32, bool onep) {
 cudaError_t window_occupancy(int* blocks_per_sm, size_t smem, int variant, bool df32) {
     int best = 1 << 30;
     for (int o = 0; o < 2; ++o) {
-        if (o == 1 && variant != WIN_FUSED && variant != WIN_SPLIT) break;
+        if (o == 1 && variant != WIN_FUSED && variant != WIN_SPLIT && variant != WIN_RESIDENT) break;
         const void* f = window_kernel(variant, df32, o == 1);
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -22,10 +22,11 @@ SWR_OK, SWR_EINVAL, SWR_ENOMEM, SWR_ECUDA, SWR_ESINGULAR, SWR_ENUMERIC, SWR_ENOT
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENUMERIC", "ENOTCONV", "ETIMEOUT", "ESTATE"]
 MODE_TISE, MODE_TDSE = 0, 1
 PREC_FP64, PREC_MIXED, PREC_FP32_REFINED = 0, 1, 2
-WINDOW_AUTO, WINDOW_TWO_PHASE, WINDOW_FUSED, WINDOW_SPLIT = 0, 1, 2, 3
+WINDOW_AUTO, WINDOW_TWO_PHASE, WINDOW_FUSED, WINDOW_SPLIT, WINDOW_RESIDENT = 0, 1, 2, 3, 4
 TC_ROBIN, TC_DIRICHLET = 0, 1
 SYM_NONE, SYM_ANTISYMMETRIC = 0, 1
 LAUNCH_GRAPH, LAUNCH_DIRECT = 0, 1
+CONTRACT_AUTO, CONTRACT_FP64, CONTRACT_TENSOR = 0, 1, 2
 GET, SET = 0, 1
 (FIELD_ENERGY, FIELD_NORM2, FIELD_DIPOLE, FIELD_RES, FIELD_WINDOW, FIELD_PSI_NODES, FIELD_OWN_TRACES,
  FIELD_ROBIN, FIELD_TRACE_BYTES, FIELD_NODE_COUNTS, FIELD_K_MAX, FIELD_COUNTERS, FIELD_CVTOT) = range(13)
@@ -50,14 +51,15 @@ class swr_problem(C.Structure):
     _fields_ = [("n_instances", C.c_int), ("instances", C.POINTER(swr_instance)), ("precision", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
                 ("window_variant", C.c_int), ("rows_per_task", C.c_int), ("launch_mode", C.c_int),
-                ("refine_res", C.c_double), ("spin_limit", C.c_longlong)]
+                ("refine_res", C.c_double), ("spin_limit", C.c_longlong), ("contraction_path", C.c_int),
+                ("cvtot_each_iteration", C.c_int)]
 
 
 class swr_tune_report(C.Structure):
     _fields_ = [("variant", C.c_int), ("rows_per_task", C.c_int), ("tasks", C.c_int), ("ctas", C.c_int),
                 ("task_state_global", C.c_int), ("candidates", C.c_int), ("graph", C.c_int),
                 ("seconds_per_step", C.c_double),
-                ("seconds_default", C.c_double)]
+                ("seconds_default", C.c_double), ("tensor_contractions", C.c_int)]
 
 
 class swr_iter_report(C.Structure):
@@ -217,7 +219,8 @@ class SWR:
 
     def __init__(self, instances, precision: int = PREC_FP64, device: str = "cuda:0", stream=None,
                  use_torch_workspace: bool = True, window_variant: int = 0, rows_per_task: int = 0,
-                 launch_mode: int = 0, spin_limit: int = 0, refine_res: float = 0.0):
+                 launch_mode: int = 0, spin_limit: int = 0, refine_res: float = 0.0, contraction_path: int = 0,
+                 cvtot_each_iteration: bool = False):
         import torch
         self.lib = load_library()
         if isinstance(instances, P.Instance):
@@ -240,6 +243,8 @@ class SWR:
         prob.launch_mode = int(launch_mode)
         prob.spin_limit = int(spin_limit)
         prob.refine_res = float(refine_res)
+        prob.contraction_path = int(contraction_path)
+        prob.cvtot_each_iteration = 1 if cvtot_each_iteration else 0
         nbytes = C.c_size_t(0)
         self._check(self.lib.swr_workspace_size(C.byref(prob), C.byref(nbytes)), None)
         self.workspace = None

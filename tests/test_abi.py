@@ -57,8 +57,8 @@ int main(void) {{
   F(swr_instance, max_steps) F(swr_instance, orth_tau) F(swr_instance, tc) F(swr_problem, workspace_bytes) F(swr_iter_report, seconds)
   F(swr_problem, window_variant) F(swr_problem, rows_per_task) F(swr_problem, launch_mode)
   F(swr_problem, spin_limit) F(swr_iter_report, cvtot) F(swr_problem, refine_res) F(swr_iter_report, fp32_matrices)
-  F(swr_report, fp32_iterations)
-  F(swr_tune_report, graph) F(swr_tune_report, seconds_default)
+  F(swr_report, fp32_iterations) F(swr_problem, contraction_path) F(swr_problem, cvtot_each_iteration)
+  F(swr_tune_report, graph) F(swr_tune_report, seconds_default) F(swr_tune_report, tensor_contractions)
   return 0;
 }}
 ''')
@@ -75,13 +75,15 @@ int main(void) {{
     assert int(got["swr_problem.workspace_bytes"]) == S.swr_problem.workspace_bytes.offset
     assert int(got["swr_iter_report.seconds"]) == S.swr_iter_report.seconds.offset
     assert int(got["swr_tune_report"]) == C.sizeof(S.swr_tune_report)
-    for key in ["window_variant", "rows_per_task", "launch_mode", "spin_limit", "refine_res"]:
+    for key in ["window_variant", "rows_per_task", "launch_mode", "spin_limit", "refine_res", "contraction_path",
+                "cvtot_each_iteration"]:
         assert int(got[f"swr_problem.{key}"]) == getattr(S.swr_problem, key).offset, key
     for key in ["cvtot", "fp32_matrices"]:
         assert int(got[f"swr_iter_report.{key}"]) == getattr(S.swr_iter_report, key).offset, key
     assert int(got["swr_report.fp32_iterations"]) == S.swr_report.fp32_iterations.offset
     assert int(got["swr_tune_report.seconds_default"]) == S.swr_tune_report.seconds_default.offset
     assert int(got["swr_tune_report.graph"]) == S.swr_tune_report.graph.offset
+    assert int(got["swr_tune_report.tensor_contractions"]) == S.swr_tune_report.tensor_contractions.offset
 
 
 def _problem(insts, keep):
@@ -130,6 +132,15 @@ def test_workspace_size_and_validation_on_host(lib):
     neg = _problem([P.small_tise_2d()], keep)
     neg.refine_res = -1.0
     assert lib.swr_workspace_size(C.byref(neg), C.byref(n)) == S.SWR_EINVAL
+    neg = _problem([P.small_tise_2d()], keep)
+    neg.contraction_path = 3
+    assert lib.swr_workspace_size(C.byref(neg), C.byref(n)) == S.SWR_EINVAL
+    # the tensor-core inverse needs slice scratch: a larger workspace
+    tc = _problem([P.small_tise_2d()], keep)
+    tc.contraction_path = S.CONTRACT_TENSOR
+    n_tc = C.c_size_t(0)
+    assert lib.swr_workspace_size(C.byref(tc), C.byref(n_tc)) == S.SWR_OK
+    assert n_tc.value > n.value
 
 
 def test_mixed_modes_rejected(lib):
@@ -159,8 +170,12 @@ def test_window_plan_requests_on_host(lib):
         (S.WINDOW_FUSED, 0, S.PREC_FP32_REFINED, True),
         (0, 0, S.PREC_FP32_REFINED, True),
         (S.WINDOW_TWO_PHASE, 0, S.PREC_FP32_REFINED, False),  # reads both planes: no FP32 phase
+        (S.WINDOW_RESIDENT, 0, S.PREC_MIXED, True),
+        (S.WINDOW_RESIDENT, 0, S.PREC_FP32_REFINED, True),
+        (S.WINDOW_RESIDENT, 0, S.PREC_FP64, False),    # the resident kernel is a mixed one
+        (S.WINDOW_RESIDENT, 256, S.PREC_MIXED, False),  # 256-row tasks do not fit its shared memory
+        (5, 0, S.PREC_MIXED, False),
         (0, 0, 3, False),
-        (4, 0, S.PREC_MIXED, False),
         (0, 4, S.PREC_FP64, False),
         (0, 257, S.PREC_FP64, False),
     ]:
@@ -207,6 +222,7 @@ def test_transmission_and_symmetry_requests_on_host(lib):
     assert status(anti) == S.SWR_OK
     assert status(anti, S.PREC_MIXED) == S.SWR_OK                              # split window
     assert status(anti, S.PREC_MIXED, S.WINDOW_FUSED) == S.SWR_EINVAL          # not the fused one
+    assert status(anti, S.PREC_MIXED, S.WINDOW_RESIDENT) == S.SWR_EINVAL       # nor the resident one
     assert status(P.tise_1d_two_subdomains().replace(symmetry="antisymmetric")) == S.SWR_EINVAL  # N = 1
     assert status(P.small_tdse_2d().replace(symmetry="antisymmetric")) == S.SWR_OK             # real time too
     kd = [8, 9, 8, 9]  # subdomain (1, 0) and its mirror (0, 1) differ

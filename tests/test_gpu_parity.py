@@ -42,16 +42,17 @@ def swr_mod():
     return S
 
 
-def _run_gpu(S, inst, kmax, tol=0.0, precision=0, cvtot=None):
-    s = S.SWR(inst, precision=precision)
+def _run_gpu(S, inst, kmax, tol=0.0, precision=0, cvtot=None, contraction_path=0, cvtot_each_iteration=False):
+    s = S.SWR(inst, precision=precision, contraction_path=contraction_path,
+              cvtot_each_iteration=cvtot_each_iteration)
     s.assemble()
     res, wins, energies = [], [], []
     for _ in range(kmax):
         rep = s.step()
         res.append(rep.res)
         if cvtot is not None:
-            cvtot.append(float(s.cvtot()[0]))
-            assert rep.cvtot == cvtot[-1]
+            cvtot.append(float(s.cvtot()[0]))  # on request, or from the iteration itself
+            assert rep.cvtot == (cvtot[-1] if cvtot_each_iteration else -1.0)
         wins.append(int(s.window()[0]))
         if inst.mode == P.TDSE:
             energies.append((float(s.norm2()[0]), float(s.dipole()[0])))
@@ -70,10 +71,12 @@ REL_ROBIN_PROJECTED_EDGE = 1e-9
 REL_CANONICAL = 1e-7
 
 
-def _compare(S, inst, kmax, tol=0.0, rel=REL, precision=0, rel_robin=None):
+def _compare(S, inst, kmax, tol=0.0, rel=REL, precision=0, rel_robin=None, contraction_path=0,
+             cvtot_each_iteration=False):
     ref = O.run_swr(inst, kmax=kmax, tol=tol)
     cv = []
-    s, res, wins, energies = _run_gpu(S, inst, len(ref.records), tol, precision, cvtot=cv)
+    s, res, wins, energies = _run_gpu(S, inst, len(ref.records), tol, precision, cvtot=cv,
+                                      contraction_path=contraction_path, cvtot_each_iteration=cvtot_each_iteration)
     assert wins == [r.n_win for r in ref.records]
     r0 = max(r.res for r in ref.records)
     for a, r in zip(res, ref.records):
@@ -135,6 +138,22 @@ def test_parity_mixed_precision_one_electron(swr_mod):
 
 def test_parity_mixed_precision_two_electrons_3x3(swr_mod):
     _compare(swr_mod, P.small_tise_2d(), kmax=6, precision=swr_mod.PREC_MIXED)
+
+
+def test_parity_cvtot_in_every_iteration(swr_mod):
+    # CVTOT inside each swr_step (captured with the iteration) and reported in its report
+    _compare(swr_mod, P.small_tise_2d(), kmax=4, cvtot_each_iteration=True)
+    _compare(swr_mod, P.small_tdse_2d(), kmax=3, precision=swr_mod.PREC_MIXED, cvtot_each_iteration=True)
+
+
+@pytest.mark.parametrize("make", [lambda: P.small_tise_2d(), lambda: P.small_tdse_2d(),
+                                  lambda: P.small_tise_2d(L=2, K_d=7, q_p=6, n_mid=2).replace(
+                                      K_d=[7, 9, 8, 6], delta=[1.3, 2.1, 1.7, 1.1])],
+                         ids=["real", "complex", "uneven"])
+def test_parity_tensor_core_inverse(swr_mod, make):
+    # Gauss-Jordan trailing updates on the tensor cores (FP64 emulated by BF16
+    # slices): ragged tiles (K = 100 and K = 36..81 in 128 x 32 tiles)
+    _compare(swr_mod, make(), kmax=3, contraction_path=swr_mod.CONTRACT_TENSOR)
 
 
 def test_parity_two_electrons_uneven_kd_and_no_ee(swr_mod):
