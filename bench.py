@@ -60,6 +60,7 @@ KERNEL_FUNCS["k_window_split"] = ["mbar_wait", "split_stage_rows", "reduce_barri
                                   "df32_acc", "k_window_split"]
 KERNEL_FUNCS["k_window_2ph<true>@batched"] = KERNEL_FUNCS["k_window_2ph<true>"]
 KERNEL_FUNCS["k_window_split@batched"] = KERNEL_FUNCS["k_window_split"]
+KERNEL_FUNCS["k_window_cluster"] = ["ds_split_int", "cl_rsqrt", "k_window_cluster"]
 PROFILED_TRAFFIC = {
     "k_window_fused": ("123b4a784de2ee96", 329.5e6, "profiles/k_window_fused_tise_2e_16sd.md"),
     "k_window_2ph<false>": ("6fd9a352bcfedf25", 279.0e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
@@ -72,7 +73,8 @@ def kernel_source_hash(kernel):
     """sha256 prefix of the text of the functions `kernel` is built from."""
     import hashlib
     import re
-    src = open(os.path.join(ROOT, "paper_1710_02401_gb300", "csrc", "swr_window.cu")).read()
+    csrc = os.path.join(ROOT, "paper_1710_02401_gb300", "csrc")
+    src = open(os.path.join(csrc, "swr_window.cu")).read() + open(os.path.join(csrc, "swr_cluster.cu")).read()
     h = hashlib.sha256()
     for fn in KERNEL_FUNCS[kernel]:
         m = re.search(r"^[^\n]*\b" + re.escape(fn) + r"\(.*?^}\n", src, re.M | re.S)
@@ -764,11 +766,17 @@ def main():
                "unit": "TFLOP/s", "algorithmic": "8 K^2 FP64-equivalent flops per complex sweep"}
     else:
         kname = {S.WINDOW_FUSED: "k_window_fused", S.WINDOW_SPLIT: "k_window_split",
-                 S.WINDOW_RESIDENT: "k_window_resident"}.get(
+                 S.WINDOW_RESIDENT: "k_window_resident", S.WINDOW_CLUSTER: "k_window_cluster"}.get(
             main_run["plan"]["variant"], "k_window_2ph<true>" if args.precision != "fp64" else "k_window_2ph<false>")
-        alg = (f"{bpe} of the step-matrix inverse per element, K^2 elements per local step solve (the "
-               "factor-apply); the 2-electron workload's 42.5 MB of step matrices stay in L2, so the kernel is "
-               "bounded by its per-step grid barrier and L2 latency, not by HBM")
+        if kname == "k_window_cluster":
+            alg = (f"{bpe} of the step-matrix inverse per element, K^2 elements per local step solve (the "
+                   "factor-apply); the cluster window keeps every subdomain's 2.65 MB of step matrix on chip "
+                   "(G_hi in shared memory, G_lo in tensor memory) for the whole window, so these bytes are read "
+                   "from SRAM and the fraction is the algorithmic rate against the HBM copy peak, not DRAM traffic")
+        else:
+            alg = (f"{bpe} of the step-matrix inverse per element, K^2 elements per local step solve (the "
+                   "factor-apply); the 2-electron workload's 42.5 MB of step matrices stay in L2, so the kernel is "
+                   "bounded by its per-step grid barrier and L2 latency, not by HBM")
         alu = {"achieved": tflops, "peak": FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS / 6.0,
                "unit": "TFLOP/s", "algorithmic": "2 K^2 FP64-equivalent flops per local step solve",
                "peak_source": "FP64 FMA rate (1.01 TFLOP/s) or FP32 FMA rate / 6 (67.7 TFLOP/s / 6: a double-single "

@@ -90,8 +90,9 @@ typedef enum swr_launch_mode {
  * compute the same step; they differ in how the per-step normalisation is
  * synchronised, and so in summation order (results agree to rounding).      */
 typedef enum swr_window_variant {
-    SWR_WINDOW_AUTO = 0,       /* mixed precision: fused when it fits, else
-                                  split; FP64: two-phase                         */
+    SWR_WINDOW_AUTO = 0,       /* mixed precision: cluster when it fits (and no
+                                  row target is given), else fused when it fits,
+                                  else split; FP64: two-phase                    */
     SWR_WINDOW_TWO_PHASE = 1,  /* y = G v, grid barrier, z = (Pp (x) Pp) y, grid
                                   barrier: G read once per step (8 bytes per
                                   element in both precisions); any batch size
@@ -109,13 +110,23 @@ typedef enum swr_window_variant {
                                   in global memory); the stop on the NGF
                                   tolerance is decided one step later and the
                                   extra step dropped                             */
-    SWR_WINDOW_RESIDENT = 4    /* mixed precision only, no antisymmetric
+    SWR_WINDOW_RESIDENT = 4,   /* mixed precision only, no antisymmetric
                                   instances: the split recursion with static
                                   tasks (at most 4 of at most 64 rows per CTA)
                                   whose G_hi rows stay in shared memory for the
                                   whole window: a step reads only G_lo from L2
                                   (nothing with the FP32-rounded matrices), no W;
                                   one grid barrier per step                      */
+    SWR_WINDOW_CLUSTER = 5     /* mixed precision only, no antisymmetric
+                                  instances, K <= 768: one thread-block cluster
+                                  (one CTA per SM) per subdomain; each CTA keeps
+                                  its rows of G on chip for the whole window
+                                  (G_hi in shared memory, G_lo in tensor memory),
+                                  y^n moves between the CTAs of a cluster through
+                                  distributed shared memory, one cluster barrier
+                                  per step and one arrival counter per instance
+                                  for s_n (no grid barrier); needs every
+                                  subdomain's cluster resident at once          */
 } swr_window_variant;
 
 /* Where swr_assemble runs its two dense contractions: the e-e block of the

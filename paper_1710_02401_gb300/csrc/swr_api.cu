@@ -80,6 +80,9 @@ struct swr_ctx {
     int stage_floats = 0;           // split window: floats per stage of staged rows
     size_t energy_smem = 0;         // dynamic shared memory of the energy / node-value kernel
     int n_stages = 0;               // split window: stages in the ring
+    int cl_size = 0, tmem_cols = 0; // cluster window: CTAs per cluster, tensor-memory columns per CTA
+    unsigned long long* d_clslots = nullptr;  // cluster window: tagged partials [2][tasks][4]
+    int cl_hs = 0;                  // cluster window: G_hi elements per thread in shared memory
     int cn_iters = 0;
     std::vector<long long> boff;  // real time: per subdomain r, u, x work vectors
     long long* d_boff = nullptr;
@@ -301,8 +304,10 @@ static swr_status validate(swr_ctx* c, const swr_problem* p) {
     if (!(p->refine_res >= 0.0)) return fail(c, SWR_EINVAL, "refine_res must be >= 0 (0: default)");
     if (p->contraction_path < SWR_CONTRACT_AUTO || p->contraction_path > SWR_CONTRACT_TENSOR)
         return fail(c, SWR_EINVAL, "unknown contraction_path");
-    if (p->window_variant < 0 || p->window_variant > SWR_WINDOW_RESIDENT)
+    if (p->window_variant < 0 || p->window_variant > SWR_WINDOW_CLUSTER)
         return fail(c, SWR_EINVAL, "unknown window variant");
+    if (p->window_variant == SWR_WINDOW_CLUSTER && (p->precision == SWR_PREC_FP64 || mode0 != SWR_MODE_TISE))
+        return fail(c, SWR_EINVAL, "the cluster window is a mixed-precision imaginary-time kernel");
     if (p->window_variant == SWR_WINDOW_RESIDENT && (p->precision == SWR_PREC_FP64 || mode0 != SWR_MODE_TISE))
         return fail(c, SWR_EINVAL, "the resident window is a mixed-precision imaginary-time kernel");
     if (p->window_variant == SWR_WINDOW_FUSED && (p->precision == SWR_PREC_FP64 || mode0 != SWR_MODE_TISE))
@@ -423,8 +428,98 @@ static long long task_capacity(const swr_ctx* c) {
 // automatic): the tasks, whether their state fits shared memory, the dynamic
 // shared memory and the CTAs per SM.  Returns false when the request cannot be
 // met (fused variant without W, or fused with task state in global memory).
+// Cluster window plan: one cluster of cs CTAs (one CTA per SM) per subdomain,
+// the rows of each subdomain split evenly over its cluster.  cs is the largest
+// size with at most 16 CTAs, at least ROWS_MIN rows per CTA and ns * cs <= SMs
+// whose rows fit shared and tensor memory and of which the device holds all ns
+// clusters at once (a row request gives cs = ceil(max K / rows)).
+static bool plan_cluster(swr_ctx* c, int rows_req, bool have_dev) {
+    if (!c->df32 || c->tdse || c->any_anti) return false;
+    const int nsm = c->nsm > 0 ? c->nsm : 152;
+    const int ns = (int)c->sub.size();
+    if (ns < 1 || ns > nsm) return false;
+    int kmin = 1 << 30;
+    for (const SubDev& s : c->sub) kmin = s.K < kmin ? s.K : kmin;
+    int cs = nsm / ns;
+    if (cs > 16) cs = 16;
+    if (cs > kmin / ROWS_MIN) cs = kmin / ROWS_MIN;
+    if (rows_req > 0) {
+        const int want = (c->max_K + rows_req - 1) / rows_req;
+        if (want > cs) return false;
+        cs = want;
+    }
+    for (; cs >= 1; --cs) {
+        const int rows = (c->max_K + cs - 1) / cs;
+        const int hs = cluster_hi_smem(c->max_K, c->max_kd, rows);
+        const int cols = cluster_tmem_cols(c->max_K, rows, hs);
+        if (cols == 0) return false;  // fewer CTAs per cluster only lengthen the rows
+        const size_t smem = window_smem_cluster(c->max_K, c->max_kd, rows, hs);
+        if (have_dev) {
+            int ncl = 0;
+            if (cluster_occupancy(&ncl, rows, smem, cs, ns * cs) != cudaSuccess) {
+                cudaGetLastError();
+                ncl = 0;
+            }
+            if (ncl < ns) {
+                if (rows_req > 0) return false;
+                continue;
+            }
+        }
+        c->tasks.clear();
+        c->inst_task0.clear();
+        c->cta_task0.assign(1, 0);
+        c->cta_list.clear();
+        c->max_rows = 0;
+        long long own = 0;
+        int cur_inst = -1;
+        for (size_t sid = 0; sid < c->sub.size(); ++sid) {
+            const SubDev& s = c->sub[sid];
+            while (cur_inst < s.inst) {
+                c->inst_task0.push_back((int)c->tasks.size());
+                ++cur_inst;
+            }
+            for (int j = 0; j < cs; ++j) {
+                Task t;
+                t.sid = (int)sid;
+                t.r0 = (int)((long long)j * s.K / cs);
+                t.r1 = (int)((long long)(j + 1) * s.K / cs);
+                t.inst = s.inst;
+                t.own = own;
+                own += 6LL * (t.r1 - t.r0);
+                if (t.r1 - t.r0 > c->max_rows) c->max_rows = t.r1 - t.r0;
+                c->cta_list.push_back((int)c->tasks.size());
+                c->tasks.push_back(t);
+                c->cta_task0.push_back((int)c->tasks.size());
+            }
+        }
+        while (cur_inst < (int)c->inst.size()) {
+            c->inst_task0.push_back((int)c->tasks.size());
+            ++cur_inst;
+        }
+        c->own_total = own;
+        c->grid = (int)c->tasks.size();
+        c->tasks_per_cta = 1;
+        c->rows_target = c->max_rows;
+        c->variant = WIN_CLUSTER;
+        c->many = 0;
+        c->g_resident = false;
+        c->cl_size = cs;
+        c->cl_hs = cluster_hi_smem(c->max_K, c->max_kd, c->max_rows);
+        c->tmem_cols = cluster_tmem_cols(c->max_K, c->max_rows, c->cl_hs);
+        c->win_smem = window_smem_cluster(c->max_K, c->max_kd, c->max_rows, c->cl_hs);
+        c->bps = 1;
+        return true;
+    }
+    return false;
+}
+
 static bool plan_window(swr_ctx* c, int variant_req, int rows_req, bool have_dev) {
     const int nsm = c->nsm > 0 ? c->nsm : 152;
+    if (variant_req == WIN_CLUSTER) return plan_cluster(c, rows_req, have_dev);
+    // automatic plan: the cluster window wherever it fits (mixed precision,
+    // imaginary time, every subdomain's rows on chip, one resident cluster per
+    // subdomain), else the fused, split or two-phase window below
+    if (variant_req == 0 && rows_req == 0 && plan_cluster(c, 0, have_dev)) return true;
     for (int per_sm = 2; per_sm >= 1; --per_sm) {
         plan_tasks(c, rows_req, per_sm * nsm, variant_req == WIN_SPLIT);
         if (variant_req == 0 && c->df32 && !c->tdse && !c->has_w) plan_tasks(c, rows_req, per_sm * nsm, true);
@@ -649,7 +744,7 @@ static void plan(swr_ctx* c) {
 struct AuxPlan {
     size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, cta0, tc, scal, alive, own,
         ctal, wfix, snorm, sums_s, sums_d,
-        n_active, win, win_prev, bar, queue, qlist, cnneed, res_part, res, cv_part, cvtot, epart, energy, norm2, dipole, boff,
+        n_active, win, win_prev, bar, queue, qlist, clslots, cnneed, res_part, res, cv_part, cvtot, epart, energy, norm2, dipole, boff,
         psi, psi_off, tg, total;
 };
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -683,6 +778,7 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.bar = o; o = al256(o + sizeof(GridBarrier));
     a.queue = o; o = al256(o + sizeof(SplitQueue));
     a.qlist = o; o = al256(o + 2 * nt * sizeof(int));
+    a.clslots = o; o = al256(o + 8 * nt * sizeof(unsigned long long));
     a.res_part = o; o = al256(o + ns * RES_BLOCKS * sizeof(double));
     a.res = o; o = al256(o + ni * sizeof(double));
     a.cv_part = o; o = al256(o + cvtot_part_doubles((int)ni) * sizeof(double));
@@ -734,6 +830,14 @@ static bool plan_for_device(swr_ctx* c, const swr_problem* p) {
     return plan_window(c, p->window_variant, p->rows_per_task, have_dev);
 }
 
+// The requested window plan cannot run the problem.
+static swr_status plan_failure() {
+    return fail(nullptr, SWR_EINVAL, "the requested window plan cannot run this problem (fused: mixed precision, at "
+                "most %d row tasks of at most %d rows per CTA; cluster: mixed precision, no antisymmetric instance, "
+                "every subdomain's rows on chip and one cluster per subdomain resident at once)",
+                window_tasks_per_cta_max(), window_rows_per_task_max());
+}
+
 static swr_status copy_problem(swr_ctx* c, const swr_problem* p) {
     c->prob = *p;
     c->inst_h.assign(p->instances, p->instances + p->n_instances);
@@ -783,8 +887,7 @@ extern "C" swr_status swr_workspace_size(const swr_problem* p, size_t* bytes) {
     swr_ctx tmp;
     copy_problem(&tmp, p);
     if (!plan_for_device(&tmp, p))
-        return fail(nullptr, SWR_EINVAL, "the fused window needs mixed precision and at most %d row tasks of at most "
-                    "%d rows per CTA", window_tasks_per_cta_max(), window_rows_per_task_max());
+        return plan_failure();
     *bytes = aux_plan(&tmp).total;
     return SWR_OK;
 }
@@ -798,8 +901,7 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     copy_problem(c, p);
     if (!plan_for_device(c, p)) {
         delete c;
-        return fail(nullptr, SWR_EINVAL, "the fused window needs mixed precision and at most %d row tasks of at most "
-                    "%d rows per CTA", window_tasks_per_cta_max(), window_rows_per_task_max());
+        return plan_failure();
     }
     AuxPlan a = aux_plan(c);
     c->stream = (cudaStream_t)p->stream;
@@ -848,6 +950,7 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->d_win = (int*)(b + a.win);
     c->d_win_prev = (int*)(b + a.win_prev);
     c->d_bar = (GridBarrier*)(b + a.bar);
+    c->d_clslots = (unsigned long long*)(b + a.clslots);
     c->d_queue = (SplitQueue*)(b + a.queue);
     c->d_qlist = (int*)(b + a.qlist);
     c->d_res_part = (double*)(b + a.res_part);
@@ -1022,6 +1125,10 @@ static SweepArgs sweep_args(swr_ctx* c) {
     a.spin_limit = c->spin_limit;
     a.stage_floats = c->stage_floats;
     a.n_stages = c->n_stages;
+    a.cl_slots = c->variant == WIN_CLUSTER ? c->d_clslots : nullptr;  // zeroed by the reset before each window
+    a.tmem_cols = c->tmem_cols;
+    a.cl_size = c->cl_size;
+    a.cl_hs = c->cl_hs;
     return a;
 }
 
@@ -1245,10 +1352,11 @@ extern "C" swr_status swr_autotune(swr_ctx* c, int steps, swr_tune_report* out) 
     std::vector<Cand> cands;
     cands.push_back({c->prob.window_variant, c->prob.rows_per_task});  // the plan before tuning
     const int rows_list[] = {0, 16, 32, 64, 128, 256};
-    const int variants[] = {WIN_TWO_PHASE, WIN_FUSED, WIN_SPLIT, WIN_RESIDENT};
+    const int variants[] = {WIN_TWO_PHASE, WIN_FUSED, WIN_SPLIT, WIN_RESIDENT, WIN_CLUSTER};
     for (int v : variants) {
         if (v == WIN_FUSED && !(c->df32 && c->has_w)) continue;
-        if ((v == WIN_SPLIT || v == WIN_RESIDENT) && !c->df32) continue;
+        if ((v == WIN_SPLIT || v == WIN_RESIDENT || v == WIN_CLUSTER) && !c->df32) continue;
+        if (v == WIN_CLUSTER && c->any_anti) continue;
         if (v == WIN_TWO_PHASE && c->prob.precision == SWR_PREC_FP32_REFINED) continue;  // reads both planes
         for (int r : rows_list) cands.push_back({v, r});
     }

@@ -202,7 +202,7 @@ struct TaskCache {
 };
 
 // Window kernel variants.
-enum WindowVariant { WIN_TWO_PHASE = 1, WIN_FUSED = 2, WIN_SPLIT = 3, WIN_RESIDENT = 4 };
+enum WindowVariant { WIN_TWO_PHASE = 1, WIN_FUSED = 2, WIN_SPLIT = 3, WIN_RESIDENT = 4, WIN_CLUSTER = 5 };
 
 // Event record that becomes an event-record node of the graph under stream
 // capture (external record) and is a plain record otherwise.
@@ -244,7 +244,48 @@ struct SweepArgs {
     int n_stages;               // split window: stages in the ring (2..8)
     SplitQueue* q;              // split window: work queue counters
     int* q_list;                // split window: [2][n_tasks] task lists by step parity
+    unsigned long long* cl_slots;  // cluster window: [2][n_tasks][4] tagged partials (step parity, task)
+    int tmem_cols;              // cluster window: tensor-memory columns per CTA (power of two, 0: none)
+    int cl_size;                // cluster window: CTAs per cluster (one subdomain each)
+    int cl_hs;                  // cluster window: G_hi elements per thread in shared memory (rest: tensor memory)
 };
+
+// Constants of task t, gathered once per window.
+__device__ inline TaskCache make_task_cache(const SweepArgs& A, int t) {
+    const Task tk = A.tasks[t];
+    const SubDev& s = A.v.sub[tk.sid];
+    const InstDev& in = A.v.inst[tk.inst];
+    TaskCache c;
+    c.inst = tk.inst;
+    c.sid = tk.sid;
+    c.r0 = tk.r0;
+    c.nr = tk.r1 - tk.r0;
+    c.K = s.K;
+    c.kd = s.kd;
+    c.N = s.N;
+    c.t0 = A.inst_task0[tk.inst];
+    c.first = (t == c.t0);
+    c.maxs = in.window_cap > 0 ? in.window_cap : in.max_steps;
+    c.ngf_stop = (in.window_cap == 0 && in.ngf_tol > 0.0);
+    if (A.tune_steps > 0) {
+        c.maxs = min(c.maxs, A.tune_steps);
+        c.ngf_stop = 0;
+    }
+    c.normalize = in.normalize;
+    c.hist = s.hist;
+    c.bvec = s.bvec;
+    c.Gm = s.Gm;
+    c.Gf = s.Gf;
+    c.Wf = s.Wf;
+    c.c0 = s.c0;
+    T1Layout lay(s.q, s.kd);
+    c.p1 = s.t1[0] + lay.mat(M_PP);
+    c.p2 = s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_PP);
+    c.own = tk.own;
+    c.kdt = in.kappa * in.dt;
+    c.ngf_tol = in.ngf_tol;
+    return c;
+}
 
 // What the allocation-free residual entry point needs from a context.
 struct ResidualInputs {
@@ -255,6 +296,14 @@ struct ResidualInputs {
     const int* win_before; // host, windows of the iteration before it
 };
 bool residual_inputs(swr_ctx* c, ResidualInputs* r);
+// Cluster window (swr_cluster.cu): dynamic shared memory, tensor-memory
+// columns per CTA (0: does not fit), clusters of cs CTAs the device holds at
+// once, and the launch.
+size_t window_smem_cluster(int kmax, int kdmax, int rows_max, int hs);
+int cluster_hi_smem(int kmax, int kdmax, int rows_max);
+int cluster_tmem_cols(int kmax, int rows_max, int hs);
+cudaError_t cluster_occupancy(int* clusters, int rows_max, size_t smem, int cs, int grid);
+cudaError_t launch_cluster_window(SweepArgs& a, int grid, int cs, size_t smem, cudaStream_t st, bool onep);
 void set_error(swr_ctx* c, const char* msg);
 cudaError_t launch_residual(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                             int parity, int first_iter, double* d_part, int res_blocks, double* d_res);

@@ -209,42 +209,6 @@ __device__ inline void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-__device__ inline TaskCache make_task_cache(const SweepArgs& A, int t) {
-    const Task tk = A.tasks[t];
-    const SubDev& s = A.v.sub[tk.sid];
-    const InstDev& in = A.v.inst[tk.inst];
-    TaskCache c;
-    c.inst = tk.inst;
-    c.sid = tk.sid;
-    c.r0 = tk.r0;
-    c.nr = tk.r1 - tk.r0;
-    c.K = s.K;
-    c.kd = s.kd;
-    c.N = s.N;
-    c.t0 = A.inst_task0[tk.inst];
-    c.first = (t == c.t0);
-    c.maxs = in.window_cap > 0 ? in.window_cap : in.max_steps;
-    c.ngf_stop = (in.window_cap == 0 && in.ngf_tol > 0.0);
-    if (A.tune_steps > 0) {
-        c.maxs = min(c.maxs, A.tune_steps);
-        c.ngf_stop = 0;
-    }
-    c.normalize = in.normalize;
-    c.hist = s.hist;
-    c.bvec = s.bvec;
-    c.Gm = s.Gm;
-    c.Gf = s.Gf;
-    c.Wf = s.Wf;
-    c.c0 = s.c0;
-    T1Layout lay(s.q, s.kd);
-    c.p1 = s.t1[0] + lay.mat(M_PP);
-    c.p2 = s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_PP);
-    c.own = tk.own;
-    c.kdt = in.kappa * in.dt;
-    c.ngf_tol = in.ngf_tol;
-    return c;
-}
-
 // Antisymmetric states (Appendix A): the mirror subdomain (i2, i1) of the
 // task's subdomain (i1, i2), and the index of coefficient (a, b) -> (b, a)
 // (index a + kd b: the orthonormal per-coordinate functions of an interval
@@ -1791,6 +1755,8 @@ __global__ void k_window_reset(SweepArgs A, int n_inst) {
         A.q->claim[0] = A.q->claim[1] = 0;
         A.q->count[0] = A.q->count[1] = 0;
     }
+    if (blockIdx.x == 0 && A.cl_slots)
+        for (int i = threadIdx.x; i < 8 * A.n_tasks; i += blockDim.x) A.cl_slots[i] = 0ULL;
 }
 
 // Split of the FP64 step-matrix inverse into FP32 pairs (mixed precision).
@@ -1935,9 +1901,13 @@ cudaError_t launch_window(SweepArgs& a, int grid, size_t smem, cudaStream_t st, 
     k_window_reset<<<1, 32, 0, st>>>(a, n_inst);
     cudaError_t e = record_event(ev_begin, st);
     if (e != cudaSuccess) return e;
-    void* params[] = {&a};
-    e = cudaLaunchCooperativeKernel(window_kernel(variant, df32, onep), dim3(grid), dim3(WIN_THREADS), params, smem,
-                                    st);
+    if (variant == WIN_CLUSTER) {
+        e = launch_cluster_window(a, grid, a.cl_size, smem, st, onep);
+    } else {
+        void* params[] = {&a};
+        e = cudaLaunchCooperativeKernel(window_kernel(variant, df32, onep), dim3(grid), dim3(WIN_THREADS), params,
+                                        smem, st);
+    }
     if (e != cudaSuccess) return e;
     return record_event(ev_end, st);
 }

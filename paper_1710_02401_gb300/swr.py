@@ -22,7 +22,7 @@ SWR_OK, SWR_EINVAL, SWR_ENOMEM, SWR_ECUDA, SWR_ESINGULAR, SWR_ENUMERIC, SWR_ENOT
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESINGULAR", "ENUMERIC", "ENOTCONV", "ETIMEOUT", "ESTATE"]
 MODE_TISE, MODE_TDSE = 0, 1
 PREC_FP64, PREC_MIXED, PREC_FP32_REFINED = 0, 1, 2
-WINDOW_AUTO, WINDOW_TWO_PHASE, WINDOW_FUSED, WINDOW_SPLIT, WINDOW_RESIDENT = 0, 1, 2, 3, 4
+WINDOW_AUTO, WINDOW_TWO_PHASE, WINDOW_FUSED, WINDOW_SPLIT, WINDOW_RESIDENT, WINDOW_CLUSTER = 0, 1, 2, 3, 4, 5
 TC_ROBIN, TC_DIRICHLET = 0, 1
 SYM_NONE, SYM_ANTISYMMETRIC = 0, 1
 LAUNCH_GRAPH, LAUNCH_DIRECT = 0, 1

@@ -174,7 +174,10 @@ def test_window_plan_requests_on_host(lib):
         (S.WINDOW_RESIDENT, 0, S.PREC_FP32_REFINED, True),
         (S.WINDOW_RESIDENT, 0, S.PREC_FP64, False),    # the resident kernel is a mixed one
         (S.WINDOW_RESIDENT, 256, S.PREC_MIXED, False),  # 256-row tasks do not fit its shared memory
-        (5, 0, S.PREC_MIXED, False),
+        (S.WINDOW_CLUSTER, 0, S.PREC_MIXED, True),
+        (S.WINDOW_CLUSTER, 0, S.PREC_FP32_REFINED, True),
+        (S.WINDOW_CLUSTER, 0, S.PREC_FP64, False),     # the cluster kernel is a mixed one
+        (6, 0, S.PREC_MIXED, False),
         (0, 0, 3, False),
         (0, 4, S.PREC_FP64, False),
         (0, 257, S.PREC_FP64, False),
@@ -201,6 +204,12 @@ def test_window_plan_requests_on_host(lib):
     ps = _problem([P.small_tdse_2d()], keep)
     ps.precision, ps.window_variant = S.PREC_MIXED, S.WINDOW_SPLIT
     assert lib.swr_workspace_size(C.byref(ps), C.byref(n)) == S.SWR_EINVAL  # imaginary time only
+    ps.window_variant = S.WINDOW_CLUSTER
+    assert lib.swr_workspace_size(C.byref(ps), C.byref(n)) == S.SWR_EINVAL
+    # the cluster plan needs one SM per CTA and one cluster per subdomain: a
+    # 512-instance batch has more subdomains than the device has SMs
+    pb.window_variant = S.WINDOW_CLUSTER
+    assert lib.swr_workspace_size(C.byref(pb), C.byref(n)) == S.SWR_EINVAL
 
 
 def test_transmission_and_symmetry_requests_on_host(lib):
@@ -223,6 +232,7 @@ def test_transmission_and_symmetry_requests_on_host(lib):
     assert status(anti, S.PREC_MIXED) == S.SWR_OK                              # split window
     assert status(anti, S.PREC_MIXED, S.WINDOW_FUSED) == S.SWR_EINVAL          # not the fused one
     assert status(anti, S.PREC_MIXED, S.WINDOW_RESIDENT) == S.SWR_EINVAL       # nor the resident one
+    assert status(anti, S.PREC_MIXED, S.WINDOW_CLUSTER) == S.SWR_EINVAL        # nor the cluster one
     assert status(P.tise_1d_two_subdomains().replace(symmetry="antisymmetric")) == S.SWR_EINVAL  # N = 1
     assert status(P.small_tdse_2d().replace(symmetry="antisymmetric")) == S.SWR_OK             # real time too
     kd = [8, 9, 8, 9]  # subdomain (1, 0) and its mirror (0, 1) differ

@@ -49,7 +49,8 @@ def _bvec_offset(s, inst, sub):
     return off + 8 * cap1 * max(int(counts[sub][1]), 1) * nch
 
 
-@pytest.mark.parametrize("precision,variant", [(0, 1), (1, 2)], ids=["fp64-two-phase", "mixed-fused"])
+@pytest.mark.parametrize("precision,variant", [(0, 1), (1, 2), (1, 5)], ids=["fp64-two-phase", "mixed-fused",
+                                                                            "mixed-cluster"])
 def test_barrier_timeout_is_reported_and_the_context_recovers(S, precision, variant):
     inst = P.small_tise_2d()
     ref = S.SWR(inst, precision=precision, window_variant=variant)

@@ -170,7 +170,13 @@ def _check(S, name, precision, variant=0, expect_variant=None, contraction_path=
 
 
 def test_fullsize_ground_state_fused_double_single(S):
-    _check(S, "tise_2e_16sd_k3", S.PREC_MIXED, 0, expect_variant=S.WINDOW_FUSED)
+    _check(S, "tise_2e_16sd_k3", S.PREC_MIXED, S.WINDOW_FUSED, expect_variant=S.WINDOW_FUSED)
+
+
+def test_fullsize_ground_state_automatic_plan_is_the_cluster_window(S):
+    insts, _, _ = _case("tise_2e_16sd_k3")
+    s = S.SWR(insts, precision=S.PREC_MIXED)
+    assert s.window_plan()["variant"] == S.WINDOW_CLUSTER
 
 
 def test_fullsize_ground_state_split_double_single(S):
@@ -179,6 +185,12 @@ def test_fullsize_ground_state_split_double_single(S):
 
 def test_fullsize_ground_state_resident_double_single(S):
     _check(S, "tise_2e_16sd_k3", S.PREC_MIXED, S.WINDOW_RESIDENT, expect_variant=S.WINDOW_RESIDENT)
+
+
+def test_fullsize_ground_state_cluster(S):
+    # one cluster per subdomain, K = 576 rows on chip (G_hi in shared memory,
+    # G_lo in tensor memory)
+    _check(S, "tise_2e_16sd_k3", S.PREC_MIXED, S.WINDOW_CLUSTER, expect_variant=S.WINDOW_CLUSTER)
 
 
 def test_fullsize_ground_state_fp64(S):

@@ -42,9 +42,10 @@ def swr_mod():
     return S
 
 
-def _run_gpu(S, inst, kmax, tol=0.0, precision=0, cvtot=None, contraction_path=0, cvtot_each_iteration=False):
+def _run_gpu(S, inst, kmax, tol=0.0, precision=0, cvtot=None, contraction_path=0, cvtot_each_iteration=False,
+             window_variant=0):
     s = S.SWR(inst, precision=precision, contraction_path=contraction_path,
-              cvtot_each_iteration=cvtot_each_iteration)
+              cvtot_each_iteration=cvtot_each_iteration, window_variant=window_variant)
     s.assemble()
     res, wins, energies = [], [], []
     for _ in range(kmax):
@@ -72,11 +73,12 @@ REL_CANONICAL = 1e-7
 
 
 def _compare(S, inst, kmax, tol=0.0, rel=REL, precision=0, rel_robin=None, contraction_path=0,
-             cvtot_each_iteration=False):
+             cvtot_each_iteration=False, window_variant=0):
     ref = O.run_swr(inst, kmax=kmax, tol=tol)
     cv = []
     s, res, wins, energies = _run_gpu(S, inst, len(ref.records), tol, precision, cvtot=cv,
-                                      contraction_path=contraction_path, cvtot_each_iteration=cvtot_each_iteration)
+                                      contraction_path=contraction_path, cvtot_each_iteration=cvtot_each_iteration,
+                                      window_variant=window_variant)
     assert wins == [r.n_win for r in ref.records]
     r0 = max(r.res for r in ref.records)
     for a, r in zip(res, ref.records):
@@ -154,6 +156,54 @@ def test_parity_tensor_core_inverse(swr_mod, make):
     # Gauss-Jordan trailing updates on the tensor cores (FP64 emulated by BF16
     # slices): ragged tiles (K = 100 and K = 36..81 in 128 x 32 tiles)
     _compare(swr_mod, make(), kmax=3, contraction_path=swr_mod.CONTRACT_TENSOR)
+
+
+@pytest.mark.parametrize("make,kmax,tol,rel_robin", [
+    (lambda: P.tise_1d_two_subdomains(), 50, 1e-8, None),
+    (lambda: P.small_tise_2d(), 6, 0.0, None),
+    (lambda: P.small_tise_2d(L=2, K_d=7, q_p=6, n_mid=2).replace(K_d=[7, 9, 8, 6], delta=[1.3, 2.1, 1.7, 1.1],
+                                                                ee_coef=0.0), 4, 0.0, None),
+    (lambda: P.small_tise_2d().replace(tc="dirichlet", mu=50.0), 4, 0.0, None),
+    (lambda: P.Instance(n_elec=1, box=(-15.0, 15.0), L=3, overlap=1.0, K_d=40, delta=4.0, q_p=10, n_mid=5,
+                        nuclei=(), ee_coef=0.0, kinetic=1.0, mu=1.0, mode=P.TISE, normalize=False, dt=0.1,
+                        n_steps=10, ngf_tol=0.0, phi0_gamma=0.2), 5, 0.0, REL_ROBIN_PROJECTED_EDGE)],
+    ids=["one-electron", "two-electrons-3x3", "uneven-no-ee", "classical", "heat-fixed-window"])
+def test_parity_cluster_window(swr_mod, make, kmax, tol, rel_robin):
+    # one thread-block cluster per subdomain, step-matrix rows on chip (G_hi in
+    # shared memory, G_lo in tensor memory), y^n exchanged through distributed
+    # shared memory: the same results as the oracle at the same bar
+    S = swr_mod
+    s, _ = _compare(S, make(), kmax=kmax, tol=tol, precision=S.PREC_MIXED, rel_robin=rel_robin,
+                    window_variant=S.WINDOW_CLUSTER)
+    plan = s.window_plan()
+    assert plan["variant"] == S.WINDOW_CLUSTER and plan["ctas"] == plan["tasks"], plan
+    assert plan["tasks"] % s.instances[0].n_sub == 0  # one cluster of equal size per subdomain
+
+
+def test_parity_batched_instances_cluster_window(swr_mod):
+    # three instances, each with its own arrival counter; their windows end at
+    # different steps and the clusters of one never wait for another's
+    S = swr_mod
+    insts = [P.small_tise_2d(L=2, K_d=6, q_p=6, n_mid=2),
+             P.tise_1d_two_subdomains().replace(L=3, K_d=20, delta=2.0),
+             P.small_tise_2d(L=2, K_d=7, q_p=6, n_mid=2).replace(nuclei=((0.3, 2.0),), mu=4.0)]
+    s = S.SWR(insts, precision=S.PREC_MIXED, window_variant=S.WINDOW_CLUSTER)
+    s.assemble()
+    assert s.window_plan()["variant"] == S.WINDOW_CLUSTER
+    kmax = 3
+    gres, gwin = [], []
+    for _ in range(kmax):
+        s.step()
+        gres.append(s.residual().copy())
+        gwin.append(s.window().copy())
+    gE = s.energy()
+    for i, inst in enumerate(insts):
+        ref = O.run_swr(inst, kmax=kmax, tol=0.0)
+        assert [int(w[i]) for w in gwin] == [r.n_win for r in ref.records]
+        assert abs(gE[i] - ref.records[-1].energy) <= REL * abs(ref.records[-1].energy)
+        rmax = max(r.res for r in ref.records)
+        for k in range(kmax):
+            assert abs(gres[k][i] - ref.records[k].res) <= REL * rmax
 
 
 def test_parity_two_electrons_uneven_kd_and_no_ee(swr_mod):

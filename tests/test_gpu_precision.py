@@ -70,7 +70,8 @@ def _run(S, inst, variant=0, refine_res=0.0, stop_at_switch=False, kmax=200):
 
 
 CASES = [("one-electron", P.tise_1d_two_subdomains, 0), ("two-electron-fused", P.small_tise_2d, 0),
-         ("two-electron-split", P.small_tise_2d, 3), ("two-electron-resident", P.small_tise_2d, 4)]
+         ("two-electron-split", P.small_tise_2d, 3), ("two-electron-resident", P.small_tise_2d, 4),
+         ("two-electron-cluster", P.small_tise_2d, 5)]
 
 
 @pytest.mark.parametrize("name,make,variant", CASES, ids=[c[0] for c in CASES])
