@@ -50,8 +50,9 @@ Readings where the paper is silent, garbled or not usable in 1-D:
   * the LSDs of Omega_{i,j} (x1 in D_i, x2 in D_j, index i + L j): pairs
     (l, p) of orbital indices, l < p when i = j (a determinant of one orbital
     with itself vanishes), every pair otherwise, ordered by
-    lambda_l^i + lambda_p^j (ties by l, then p), the first K kept (the paper
-    selects K LSDs among the candidate determinants without giving the rule);
+    lambda_l^i + lambda_p^j (sums within 1e-9 relative count as ties, broken by
+    l, then p), the first K kept (the paper selects K LSDs among the
+    candidate determinants without giving the rule);
   * x_b, eps_b and V_inf are not given for the tests: x_b = |D_i|/2 (the
     barrier at half height on the edge of D_i, the orbitals not null there),
     eps_b = 0.4, V_inf = 100; with these the neighbour inner products of
@@ -264,14 +265,33 @@ def two_electron(p: LsdProblem, orbs: Sequence[Orbitals], idx: Sequence[int]) ->
     return E.reshape(n, n, n, n)
 
 
+TIE = 1e-9  # orbital-energy sums this close (relative) count as equal
+
+
 def lsd_pairs(p: LsdProblem, orbs: Sequence[Orbitals], i: int, j: int) -> List[Tuple[int, int]]:
     """The K determinants of Omega_{i,j} (reading above): (l, p) with the
-    orbital phi_l^i in the first slot and phi_p^j in the second."""
+    orbital phi_l^i in the first slot and phi_p^j in the second, ranked by
+    lambda_l^i + lambda_p^j; sums within TIE (relative) are ties, broken by
+    (l, p) (mirror-image subdomains have equal spectra, so exact ties occur
+    and rounding must not order them)."""
     cand = [(l, q) for l in range(p.M) for q in range(p.M) if (i != j or l < q)]
-    cand.sort(key=lambda t: (orbs[i].lam[t[0]] + orbs[j].lam[t[1]], t[0], t[1]))
     if len(cand) < p.K:
         raise ValueError(f"Omega_({i},{j}) has {len(cand)} candidate determinants, fewer than K = {p.K}")
-    return cand[: p.K]
+    e = [orbs[i].lam[l] + orbs[j].lam[q] for (l, q) in cand]
+
+    def before(u, v):
+        d = e[u] - e[v]
+        if abs(d) <= TIE * (1.0 + abs(e[u]) + abs(e[v])):
+            return cand[u] < cand[v]
+        return d < 0.0
+
+    rank = [sum(1 for v in range(len(cand)) if v != u and before(v, u)) for u in range(len(cand))]
+    if sorted(rank) != list(range(len(cand))):
+        raise ValueError(f"Omega_({i},{j}): the tie rule does not order the candidates")
+    out = [None] * len(cand)
+    for u, r in enumerate(rank):
+        out[r] = cand[u]
+    return out[: p.K]
 
 
 def lsd_gram(p: LsdProblem, oe: OneElectron, pa, ia: Tuple[int, int], pb, ib: Tuple[int, int]) -> np.ndarray:
