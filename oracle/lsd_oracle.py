@@ -53,6 +53,9 @@ Readings where the paper is silent, garbled or not usable in 1-D:
     lambda_l^i + lambda_p^j (sums within 1e-9 relative count as ties, broken by
     l, then p), the first K kept (the paper selects K LSDs among the
     candidate determinants without giving the rule);
+  * Test 1's K = N_phi (N_phi + 1) / 2 = 45 determinants per subdomain with
+    N_phi = 9: a diagonal subdomain needs l < p, and 45 = C(10, 2), so the
+    default takes M = 10 orbitals per 1-D subdomain and K = 45;
   * x_b, eps_b and V_inf are not given for the tests: x_b = |D_i|/2 (the
     barrier at half height on the edge of D_i, the orbitals not null there),
     eps_b = 0.4, V_inf = 100; with these the neighbour inner products of
@@ -83,7 +86,7 @@ class LsdProblem:
     eta_ee: float = 0.5
     ee_coef: float = 1.0
     harmonic: float = 0.0           # + harmonic x^2 / 2 in the one-electron potential
-    M: int = 9                      # local orbitals per 1-D subdomain
+    M: int = 10                     # local orbitals per 1-D subdomain
     K: int = 45                     # LSDs per 2-D subdomain
     kd: int = 40                    # Gaussians of one orbital basis
     delta: float = 0.0              # Gaussian exponent (0: spacing rule)
