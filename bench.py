@@ -487,6 +487,30 @@ def extra_real_time(args, env):
     return out
 
 
+def run_lsd(args, S, reps=3):
+    """swr_lsd_build at the paper's Test 1 sizes: wall time of the whole call
+    (allocation, device work, copies back), best of `reps` after a warm-up,
+    and Table 1's inner products of the central subdomain's first four
+    determinants with themselves and with the first two of the next subdomain
+    in x1."""
+    kw = dict(M=10, K=45, kd=40)
+    S.lsd_build(**kw)
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        g = S.lsd_build(**kw)
+        best = min(best, time.perf_counter() - t0)
+    c = 2 + 5 * 2
+    out = {"metric": "swr_lsd_build wall time (Test 1 sizes)", "value": best, "unit": "s", "higher_is_better": False,
+           "data": "synthetic", "config": {"L": 5, "box": [-8.0, 8.0], "overlap": 0.32, "orbitals_per_subdomain": 10,
+                                            "determinants_per_subdomain": 45, "gaussians_per_orbital_basis": 40,
+                                            "nuclei": [[-0.5, 1.0], [0.5, 1.0]]},
+           "orbital_energies_central": [float(x) for x in g["lam"][2]],
+           "table1_vv_offdiag_max": float(abs(g["S_lsd"][c][:4, :4] - __import__("numpy").eye(4)).max()),
+           "table1_vw": [[float(x) for x in row] for row in g["G_next"][c][:4, :2]]}
+    print(json.dumps(out))
+
+
 def run_assembly(args, S, reps=3):
     """swr_assemble timed with CUDA events (library counter), best of `reps`
     after one warm-up, for both contraction paths."""
@@ -624,6 +648,10 @@ def main():
                     help="time swr_assemble (quadrature, local matrices, orthonormalisation, e-e block, step-matrix "
                          "inversion) with the FP64 and the tensor-core contractions on the real-time 64-subdomain and "
                          "the 2-electron ground-state workloads; one JSON line")
+    ap.add_argument("--lsd", action="store_true",
+                    help="local orbitals and local Slater determinants at the paper's Test 1 sizes (L = 5, 10 orbitals "
+                         "per subdomain, 45 determinants per subdomain): time of swr_lsd_build (best of three) and "
+                         "Table 1's inner products; one JSON line")
     ap.add_argument("--sweep", action="store_true",
                     help="imaginary-time workloads: Schwarz convergence over a grid of time steps and Robin "
                          "constants, Robin and classical (Dirichlet) transmission; one JSON line")
@@ -669,6 +697,12 @@ def main():
     if args.assembly:
         if rank == 0:
             run_assembly(args, S)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.lsd:
+        if rank == 0:
+            run_lsd(args, S)
         if world > 1:
             dist.destroy_process_group()
         return

@@ -460,6 +460,71 @@ swr_status swr_autotune(swr_ctx* ctx, int steps, swr_tune_report* out);
  * real-time problems, whose steps are launched from the host.               */
 swr_status swr_window_plan(const swr_ctx* ctx, swr_tune_report* out);
 
+/* ------------------------------------------------------------------------
+ * Local orbitals and local Slater determinants: the paper's second basis
+ * family (Sec. 3.2 "Local orbital construction" with the barrier potential
+ * of Eq. BARPOT; Eq. LSD; Appendix A "Discrete local Hamiltonian
+ * construction with local Slater's determinants"; Sec. 7 Test 1, Table 1).
+ *
+ * The line [box_lo, box_hi] is cut into L subdomains D_i of width
+ * H + overlap (H = (box_hi - box_lo) / L, centre x_ci = box_lo + (i + 1/2) H).
+ * In each D_i the M lowest eigenpairs of
+ *   1/2 int a phi' psi' + int (V_en + V_b) phi psi = lambda int phi psi,
+ *   V_b = v_inf s(|x - x_ci| - x_b),  a = 1 - s,  x_b = xb_factor (H + overlap),
+ * s the C^2 step rising over [x_b - eps_b/2, x_b + eps_b/2], V_en soft-Coulomb
+ * nuclei (-Z / sqrt((x - x_A)^2 + eta_en^2)) plus harmonic x^2 / 2, are
+ * computed in a basis of kd Gaussians exp(-delta (x - alpha_k)^2), alpha_k
+ * equally spaced on [x_ci - x_b, x_ci + x_b] (delta = 0: 1 / (2 h^2), h their
+ * spacing), with composite Gauss-Legendre rules (q_p nodes per panel of width
+ * <= panel).  Each orbital's sign makes int phi exp(0.37 (x - x_ci)) dx > 0.
+ * The 2-D subdomain Omega_{i,j} (x1 in D_i, x2 in D_j, index i + L j) takes
+ * the K determinants
+ *   v = (phi_l^i(x1) phi_p^j(x2) - phi_l^i(x2) phi_p^j(x1)) / sqrt(2)
+ * of lowest lambda_l^i + lambda_p^j (l < p when i = j; sums within 1e-9
+ * relative are ties, broken by (l, p)).  All integrals run over the whole
+ * line; the e-e interaction is ee_coef / sqrt((x1 - x2)^2 + eta_ee^2).
+ * Everything is computed on the device in FP64 (one call; the device memory
+ * it needs is allocated and freed inside).                                  */
+typedef struct swr_lsd_problem {
+    double box_lo, box_hi;
+    int    L;                  /* 1-D subdomains, 1..16                         */
+    double overlap;            /* overlap width of neighbouring D_i, >= 0       */
+    int    n_nuclei;           /* 0..3                                          */
+    double x_nuc[3], Z_nuc[3];
+    double eta_en, eta_ee;     /* soft-Coulomb parameters (> 0)                 */
+    double ee_coef;            /* e-e strength                                  */
+    double harmonic;           /* harmonic term in V_en                         */
+    int    M;                  /* orbitals per subdomain, 1..kd                 */
+    int    K;                  /* determinants per Omega, 1..M (M - 1) / 2      */
+    int    kd;                 /* Gaussians per orbital basis, 2..64            */
+    double delta;              /* Gaussian exponent, 0: 1 / (2 h^2)             */
+    double xb_factor;          /* x_b = xb_factor |D_i|, > 0                    */
+    double eps_b;              /* width of the barrier's rise, > 0              */
+    double v_inf;              /* barrier height, >= 0                          */
+    int    q_p;                /* Gauss-Legendre nodes per panel, 2..16         */
+    double panel;              /* panel width, > 0                              */
+} swr_lsd_problem;
+
+/* Caller-owned host buffers, row-major; orbital a = i M + l.                */
+typedef struct swr_lsd_result {
+    double* lam;               /* [L][M] lambda_l^i, ascending per subdomain    */
+    double* coef;              /* [L][kd][M] Gaussian coefficients of phi_l^i    */
+    double* S1;                /* [L M][L M] <phi_a, phi_b>                      */
+    double* h1;                /* [L M][L M] 1/2 <phi_a', phi_b'> + <phi_a|V_en|phi_b> */
+    double* J1;                /* [L M][L M] <phi_a|x|phi_b>                     */
+    int*    pairs;             /* [L L][K][2] (l, p) of every determinant        */
+    double* S_lsd;             /* [L L][K][K] Gram of the determinants of Omega  */
+    double* H_lsd;             /* [L L][K][K] H0 between them                    */
+    double* G_next;            /* [L L][K][K] <v of Omega_{i,j}, v of Omega_{i+1,j}>
+                                  (zero for i = L - 1)                          */
+} swr_lsd_result;
+
+/* Builds everything above.  SWR_EINVAL for an invalid problem or a NULL
+ * buffer, SWR_ENOMEM when the device memory cannot be had, SWR_ESINGULAR when
+ * an orbital basis overlap is not positive definite, SWR_ECUDA on a runtime
+ * error; details in swr_last_error(NULL).                                   */
+swr_status swr_lsd_build(const swr_lsd_problem* p, swr_lsd_result* out);
+
 void        swr_destroy(swr_ctx* ctx);
 const char* swr_last_error(const swr_ctx* ctx);
 

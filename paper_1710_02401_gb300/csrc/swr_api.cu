@@ -153,6 +153,11 @@ struct swr_ctx {
 
 static std::string g_setup_err;
 
+// Error text of calls without a context (swr_last_error(NULL)).
+namespace swr {
+void set_setup_error(const char* msg) { g_setup_err = msg; }
+}  // namespace swr
+
 // SWR_PREC_FP32_REFINED before its switch: the windows read only the hi plane
 // of the step matrices (the FP32-rounded G).
 static bool fp32_phase(const swr_ctx* c) { return c->prob.precision == SWR_PREC_FP32_REFINED && !c->refined; }

@@ -305,6 +305,7 @@ int cluster_tmem_cols(int kmax, int rows_max, int hs);
 cudaError_t cluster_occupancy(int* clusters, int rows_max, size_t smem, int cs, int grid);
 cudaError_t launch_cluster_window(SweepArgs& a, int grid, int cs, size_t smem, cudaStream_t st, bool onep);
 void set_error(swr_ctx* c, const char* msg);
+void set_setup_error(const char* msg);
 cudaError_t launch_residual(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                             int parity, int first_iter, double* d_part, int res_blocks, double* d_res);
 }  // namespace swr

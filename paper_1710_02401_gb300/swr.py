@@ -77,12 +77,24 @@ class swr_trace_view(C.Structure):
     _fields_ = [("host", C.c_void_p), ("bytes", C.c_size_t)]
 
 
+class swr_lsd_problem(C.Structure):
+    _fields_ = [("box_lo", C.c_double), ("box_hi", C.c_double), ("L", C.c_int), ("overlap", C.c_double),
+                ("n_nuclei", C.c_int), ("x_nuc", C.c_double * 3), ("Z_nuc", C.c_double * 3),
+                ("eta_en", C.c_double), ("eta_ee", C.c_double), ("ee_coef", C.c_double), ("harmonic", C.c_double),
+                ("M", C.c_int), ("K", C.c_int), ("kd", C.c_int), ("delta", C.c_double), ("xb_factor", C.c_double),
+                ("eps_b", C.c_double), ("v_inf", C.c_double), ("q_p", C.c_int), ("panel", C.c_double)]
+
+
+class swr_lsd_result(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("lam", "coef", "S1", "h1", "J1", "pairs", "S_lsd", "H_lsd", "G_next")]
+
+
 EXPORTS = ["swr_workspace_size", "swr_setup", "swr_assemble", "swr_step", "swr_iterate", "swr_traces",
            "swr_get", "swr_field_bytes", "swr_trace_codec", "swr_trace_encode", "swr_trace_decode_set",
            "swr_mlp_create", "swr_mlp_param_count", "swr_mlp_set_params", "swr_mlp_get_params",
            "swr_mlp_forward", "swr_mlp_train_step", "swr_mlp_destroy", "swr_mlp_last_error",
            "swr_residual_noalloc", "swr_autotune", "swr_window_plan", "swr_set_spin_limit", "swr_destroy",
-           "swr_last_error"]
+           "swr_last_error", "swr_lsd_build"]
 
 _lib = None
 
@@ -496,3 +508,33 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+def lsd_build(box=(-8.0, 8.0), L=5, overlap=0.32, nuclei=((-0.5, 1.0), (0.5, 1.0)), eta_en=0.5, eta_ee=0.5,
+              ee_coef=1.0, harmonic=0.0, M=10, K=45, kd=40, delta=0.0, xb_factor=0.5, eps_b=0.4, v_inf=100.0,
+              q_p=12, panel=0.2) -> dict:
+    """Local orbitals and local Slater determinants (swr_lsd_build): orbital
+    energies and coefficients, one-electron integrals, and per 2-D subdomain
+    the determinants' (l, p), Gram, H0 and Gram against the next subdomain in
+    x1.  Argument meaning as in include/swr.h."""
+    lib = load_library()
+    lib.swr_lsd_build.argtypes = [C.POINTER(swr_lsd_problem), C.POINTER(swr_lsd_result)]
+    lib.swr_lsd_build.restype = C.c_int
+    p = swr_lsd_problem()
+    p.box_lo, p.box_hi, p.L, p.overlap = float(box[0]), float(box[1]), int(L), float(overlap)
+    p.n_nuclei = len(nuclei)
+    for a, (x, z) in enumerate(nuclei):
+        p.x_nuc[a], p.Z_nuc[a] = float(x), float(z)
+    p.eta_en, p.eta_ee, p.ee_coef, p.harmonic = float(eta_en), float(eta_ee), float(ee_coef), float(harmonic)
+    p.M, p.K, p.kd, p.delta = int(M), int(K), int(kd), float(delta)
+    p.xb_factor, p.eps_b, p.v_inf, p.q_p, p.panel = float(xb_factor), float(eps_b), float(v_inf), int(q_p), float(panel)
+    LM = L * M
+    out = {"lam": np.zeros((L, M)), "coef": np.zeros((L, kd, M)), "S1": np.zeros((LM, LM)),
+           "h1": np.zeros((LM, LM)), "J1": np.zeros((LM, LM)), "pairs": np.zeros((L * L, K, 2), dtype=np.int32),
+           "S_lsd": np.zeros((L * L, K, K)), "H_lsd": np.zeros((L * L, K, K)), "G_next": np.zeros((L * L, K, K))}
+    r = swr_lsd_result(*[out[k].ctypes.data for k, _ in swr_lsd_result._fields_])
+    st = lib.swr_lsd_build(C.byref(p), C.byref(r))
+    if st != SWR_OK:
+        msg = lib.swr_last_error(None)
+        raise SWRError(st, msg.decode() if msg else "")
+    return out

@@ -59,6 +59,11 @@ int main(void) {{
   F(swr_problem, spin_limit) F(swr_iter_report, cvtot) F(swr_problem, refine_res) F(swr_iter_report, fp32_matrices)
   F(swr_report, fp32_iterations) F(swr_problem, contraction_path) F(swr_problem, cvtot_each_iteration)
   F(swr_tune_report, graph) F(swr_tune_report, seconds_default) F(swr_tune_report, tensor_contractions)
+  printf("swr_lsd_problem %zu\\n", sizeof(swr_lsd_problem));
+  printf("swr_lsd_result %zu\\n", sizeof(swr_lsd_result));
+  F(swr_lsd_problem, L) F(swr_lsd_problem, overlap) F(swr_lsd_problem, x_nuc) F(swr_lsd_problem, M)
+  F(swr_lsd_problem, kd) F(swr_lsd_problem, delta) F(swr_lsd_problem, q_p) F(swr_lsd_problem, panel)
+  F(swr_lsd_result, pairs) F(swr_lsd_result, G_next)
   return 0;
 }}
 ''')
@@ -84,6 +89,12 @@ int main(void) {{
     assert int(got["swr_tune_report.seconds_default"]) == S.swr_tune_report.seconds_default.offset
     assert int(got["swr_tune_report.graph"]) == S.swr_tune_report.graph.offset
     assert int(got["swr_tune_report.tensor_contractions"]) == S.swr_tune_report.tensor_contractions.offset
+    assert int(got["swr_lsd_problem"]) == C.sizeof(S.swr_lsd_problem)
+    assert int(got["swr_lsd_result"]) == C.sizeof(S.swr_lsd_result)
+    for key in ["L", "overlap", "x_nuc", "M", "kd", "delta", "q_p", "panel"]:
+        assert int(got[f"swr_lsd_problem.{key}"]) == getattr(S.swr_lsd_problem, key).offset, key
+    for key in ["pairs", "G_next"]:
+        assert int(got[f"swr_lsd_result.{key}"]) == getattr(S.swr_lsd_result, key).offset, key
 
 
 def _problem(insts, keep):
