@@ -81,58 +81,6 @@ __device__ inline void cl_red_release(unsigned* p) {
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(p) : "memory");
 }
 
-// ---------------------------------------------------- double-single helpers
-__device__ inline void cl_two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-__device__ inline float2 cl_norm(float h, float l) {
-    const float s = h + l;
-    return make_float2(s, l - (s - h));
-}
-__device__ inline float2 cl_add(float2 a, float2 b) {
-    float s, e;
-    cl_two_sum(a.x, b.x, s, e);
-    return cl_norm(s, e + (a.y + b.y));
-}
-__device__ inline float2 cl_mul(float2 a, float2 b) {
-    const float p = a.x * b.x;
-    float e = fmaf(a.x, b.x, -p);
-    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
-    return cl_norm(p, e);
-}
-__device__ inline float2 cl_neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ inline float2 cl_shfl_add(float2 a, int o) {
-    return cl_add(a, make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o)));
-}
-__device__ inline double cl_to_double(float2 a) { return (double)a.x + (double)a.y; }
-
-// Split of a double into a double-single pair on the integer pipes: hi = x
-// truncated to 24 significant bits, lo = the remainder truncated to 24 bits,
-// |x - hi - lo| <= 2^-46 |x|.  |x| < 2^-100 gives (0, 0); NaN, infinities and
-// |x| >= 2^128 take the FP64 conversion (and propagate).
-__device__ inline float2 ds_split_int(double x) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((u >> 52) & 0x7ffULL) - 1023;
-    if (e < -100) return make_float2(0.f, 0.f);
-    if (e > 127) return make_float2((float)x, 0.f);
-    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
-    const unsigned long long mant = u & 0xFFFFFFFFFFFFFULL;
-    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29));
-    const unsigned long long r = mant & 0x1FFFFFFFULL;  // the 29 bits below hi
-    float lo = 0.f;
-    if (r != 0) {
-        const int p = 63 - __clzll((long long)r);  // leading bit of r, 0..28
-        const int le = e - 52 + p;                 // its binary exponent
-        if (le >= -126) {
-            const unsigned m = p >= 23 ? (unsigned)(r >> (p - 23)) : (unsigned)(r << (23 - p));
-            lo = __uint_as_float(sign | ((unsigned)(le + 127) << 23) | (m & 0x7FFFFFu));
-        }
-    }
-    return make_float2(hi, lo);
-}
-
 // Matrix-vector layout of one CTA: warp w owns the column segment
 // [w sw, (w+1) sw) of its rows, lane l the rows l + 32 k (k < rpl), so a thread
 // holds rpl x sw elements (index e = k sw + j); sw is a multiple of 4 with
@@ -185,8 +133,8 @@ __device__ inline float2 cl_rsqrt(float2 a) {
     float2 y = make_float2(rsqrtf(a.x), 0.f);
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
-        const float2 r = cl_add(make_float2(1.f, 0.f), cl_neg(cl_mul(a, cl_mul(y, y))));
-        y = cl_add(y, cl_mul(y, make_float2(0.5f * r.x, 0.5f * r.y)));
+        const float2 r = dsp_add(make_float2(1.f, 0.f), dsp_neg(dsp_mul(a, dsp_mul(y, y))));
+        y = dsp_add(y, dsp_mul(y, make_float2(0.5f * r.x, 0.5f * r.y)));
     }
     return y;
 }
@@ -309,8 +257,8 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
                         const float2* p2 = P2 + (b0 + bb) * kd;
                         for (int e = g; e < kd; e += 4) ds_fma(acc.x, acc.y, yn[c + kd * e], p2[e]);
                     }
-                    acc = cl_shfl_add(acc, 1);
-                    acc = cl_shfl_add(acc, 2);
+                    acc = dsp_shfl_add(acc, 1);
+                    acc = dsp_shfl_add(acc, 2);
                     if (it < items && g == 0) tmp[it] = acc;
                 }
                 asm volatile("bar.sync 1, %0;" ::"n"(CL_THREADS - 32) : "memory");
@@ -323,9 +271,9 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
                         const float2* tb = tmp + (b - b0) * kd;
                         for (int c = g; c < kd; c += 8) ds_fma(acc.x, acc.y, p1[c], tb[c]);
                     }
-                    acc = cl_shfl_add(acc, 1);
-                    acc = cl_shfl_add(acc, 2);
-                    acc = cl_shfl_add(acc, 4);
+                    acc = dsp_shfl_add(acc, 1);
+                    acc = dsp_shfl_add(acc, 2);
+                    acc = dsp_shfl_add(acc, 4);
                     if (i < nr && g == 0) zo_n[i] = acc;
                 }
             } else {
@@ -336,9 +284,9 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
                         const float2* p1 = P1 + (r0 + i) * kd;
                         for (int c = g; c < kd; c += 8) ds_fma(acc.x, acc.y, p1[c], yn[c]);
                     }
-                    acc = cl_shfl_add(acc, 1);
-                    acc = cl_shfl_add(acc, 2);
-                    acc = cl_shfl_add(acc, 4);
+                    acc = dsp_shfl_add(acc, 1);
+                    acc = dsp_shfl_add(acc, 2);
+                    acc = dsp_shfl_add(acc, 4);
                     if (i < nr && g == 0) zo_n[i] = acc;
                 }
             }
@@ -347,29 +295,29 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
             // y1 is1 - y2 is2 = is1 (y1 - y2) + y2 (is1 - is2): the differences of
             // nearby iterates are formed before any rounding of the products
             const float2 is1 = s_is[0], is2 = s_is[1];
-            const float2 dis = cl_add(is1, cl_neg(is2));
+            const float2 dis = dsp_add(is1, dsp_neg(is2));
             const float2* y1 = yown + (size_t)((n + 2) % 3) * nrm;
             const float2* y2 = yown + (size_t)((n + 1) % 3) * nrm;
             const float2* z1 = zown + (size_t)((n + 2) % 3) * nrm;
             const float2* z2 = zown + (size_t)((n + 1) % 3) * nrm;
             float2 acc = make_float2(0.f, 0.f);
             for (int i = lane; i < nr; i += 32) {
-                const float2 d = cl_add(cl_mul(is1, cl_add(y1[i], cl_neg(y2[i]))), cl_mul(y2[i], dis));
-                const float2 e = cl_add(cl_mul(is1, cl_add(z1[i], cl_neg(z2[i]))), cl_mul(z2[i], dis));
-                acc = cl_add(acc, cl_mul(d, e));
+                const float2 d = dsp_add(dsp_mul(is1, dsp_add(y1[i], dsp_neg(y2[i]))), dsp_mul(y2[i], dis));
+                const float2 e = dsp_add(dsp_mul(is1, dsp_add(z1[i], dsp_neg(z2[i]))), dsp_mul(z2[i], dis));
+                acc = dsp_add(acc, dsp_mul(d, e));
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc = cl_shfl_add(acc, o);
+            for (int o = 16; o > 0; o >>= 1) acc = dsp_shfl_add(acc, o);
             if (lane == 0) s_dpart = acc;
         }
         __syncthreads();
         // ---- partial of s_n^2 (own rows), published with the partial of D_{n-1}
         {
             float2 acc = make_float2(0.f, 0.f);
-            for (int i = tid; i < nr; i += CL_THREADS) acc = cl_add(acc, cl_mul(yo_n[i], zo_n[i]));
+            for (int i = tid; i < nr; i += CL_THREADS) acc = dsp_add(acc, dsp_mul(yo_n[i], zo_n[i]));
             if (tid < ((nr + 31) & ~31)) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc = cl_shfl_add(acc, o);
+                for (int o = 16; o > 0; o >>= 1) acc = dsp_shfl_add(acc, o);
                 if (lane == 0) red2[warp] = acc;
             }
         }
@@ -379,7 +327,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
         const bool dprev = n >= 2 && stop_rule;
         if (tid == 0) {
             float2 a = make_float2(0.f, 0.f);
-            for (int w = 0; w < (nr + 31) / 32 && w < CL_WARPS; ++w) a = cl_add(a, red2[w]);
+            for (int w = 0; w < (nr + 31) / 32 && w < CL_WARPS; ++w) a = dsp_add(a, red2[w]);
             const float2 d = dprev ? s_dpart : make_float2(0.f, 0.f);
             unsigned long long* my = slots + (size_t)t * 4;
             cl_st_relaxed(my + 0, cl_tagged(a.x, tag));
@@ -420,23 +368,23 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
                     }
                 }
                 // slot order: lane-strided partial sums, combined below in lane order
-                ss = cl_add(ss, ps);
-                sd = cl_add(sd, pd);
+                ss = dsp_add(ss, ps);
+                sd = dsp_add(sd, pd);
             }
             if (__any_sync(0xffffffffu, !ok)) {
                 if (lane == 0) s_fail = 1;
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                ss = cl_shfl_add(ss, o);
-                sd = cl_shfl_add(sd, o);
+                ss = dsp_shfl_add(ss, o);
+                sd = dsp_shfl_add(sd, o);
             }
             if (lane == 0) {
                 // ---- decisions of step n (those of the other window kernels)
                 int stop = s_fail;
                 if (!stop) {
                     const float2 isn = tc.normalize ? cl_rsqrt(ss) : make_float2(1.f, 0.f);
-                    const float2 sn = tc.normalize ? cl_mul(ss, isn) : make_float2(1.f, 0.f);
+                    const float2 sn = tc.normalize ? dsp_mul(ss, isn) : make_float2(1.f, 0.f);
                     const bool bad = !(isfinite(sn.x) && sn.x > 0.f);
                     if (dprev && sd.x + sd.y <= tol2.x + tol2.y) {
                         stop = 1;  // window ends at n - 1
@@ -455,21 +403,21 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
             // ---- meanwhile: kappa dt b'^{n+1} into v (integer-pipe split), history row n
             if (wp > 0) {
                 const double* bsrc = v.arena + tc.bvec + (long long)min(n + 1, wp) * K;
-                for (int c = tid - 32; c < K; c += CL_THREADS - 32) vf[c] = cl_mul(ds_split_int(bsrc[c]), kdt2);
+                for (int c = tid - 32; c < K; c += CL_THREADS - 32) vf[c] = dsp_mul(dsp_split_int(bsrc[c]), kdt2);
             } else {
                 for (int c = tid - 32; c < K; c += CL_THREADS - 32) vf[c] = make_float2(0.f, 0.f);
             }
             if (n >= 1) {
                 double* hrow = v.arena + tc.hist + (long long)n * K;
-                for (int i = tid - 32; i < nr; i += CL_THREADS - 32) hrow[r0 + i] = cl_to_double(yo_n[i]);
+                for (int i = tid - 32; i < nr; i += CL_THREADS - 32) hrow[r0 + i] = dsp_to_double(yo_n[i]);
             }
         }
         __syncthreads();
         if (!s_stop) {
-            if (tc.first && tid == CL_THREADS - 1) A.snorm[(long long)tc.inst * (A.cap + 1) + n] = cl_to_double(s_sn);
+            if (tc.first && tid == CL_THREADS - 1) A.snorm[(long long)tc.inst * (A.cap + 1) + n] = dsp_to_double(s_sn);
             // ---- v = y^n / s_n + kappa dt b'^{n+1}
             const float2 isf = s_is[0];
-            for (int c = tid; c < K; c += CL_THREADS) vf[c] = cl_add(cl_mul(yn[c], isf), vf[c]);
+            for (int c = tid; c < K; c += CL_THREADS) vf[c] = dsp_add(dsp_mul(yn[c], isf), vf[c]);
             __syncthreads();
             // ---- own rows of y^{n+1} = G v: each thread its rpl rows over its
             //      warp's column segment (v broadcast from shared memory), chunks
@@ -539,7 +487,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
                 for (int k = 0; k < RPL; ++k)
                     if (k < rpl)
                         segp[((size_t)k * CL_WARPS + warp) * 32 + lane] =
-                            cl_add(make_float2(ah[k], al[k]), make_float2(bh[k], bl[k]));
+                            dsp_add(make_float2(ah[k], al[k]), make_float2(bh[k], bl[k]));
             }
             __syncthreads();
             // ---- row sums over the 16 segments (4 threads per row, fixed order),
@@ -552,10 +500,10 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
                     if (i < nr) {
                         const float2* sp = segp + ((size_t)(i >> 5) * CL_WARPS) * 32 + (i & 31);
 #pragma unroll
-                        for (int w = p; w < CL_WARPS; w += 4) y = cl_add(y, sp[(size_t)w * 32]);
+                        for (int w = p; w < CL_WARPS; w += 4) y = dsp_add(y, sp[(size_t)w * 32]);
                     }
-                    y = cl_shfl_add(y, 1);
-                    y = cl_shfl_add(y, 2);
+                    y = dsp_shfl_add(y, 1);
+                    y = dsp_shfl_add(y, 2);
                     if (i < nr && p == 0)
                         for (unsigned r = 0; r < CS; ++r) cl_store2(ynext + r0 + i, r, y.x, y.y);
                 }
@@ -563,7 +511,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
         } else {
             if (tid == 0 && tc.first && !s_fail) {
                 // the window length and the normalisation of the last step
-                A.snorm[(long long)tc.inst * (A.cap + 1) + n] = cl_to_double(s_sn);
+                A.snorm[(long long)tc.inst * (A.cap + 1) + n] = dsp_to_double(s_sn);
                 A.win[tc.inst] = s_wend;
                 if (!(isfinite(s_sn.x) && s_sn.x > 0.f)) atomicOr(v.err, SWR_ERR_NUMERIC);
                 __threadfence();

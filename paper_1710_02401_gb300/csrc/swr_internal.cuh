@@ -158,6 +158,59 @@ __device__ inline void ds_fma(float& h, float& l, float2 a, float2 b) {
     l += (err + e) + fmaf(a.x, b.y, a.y * b.x);
 }
 
+// Double-single pairs (h, l) as float2 on the FP32 pipes: error-free sum and
+// product of the leading terms, renormalised results.
+__device__ inline void dsp_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ inline float2 dsp_norm(float h, float l) {
+    const float s = h + l;
+    return make_float2(s, l - (s - h));
+}
+__device__ inline float2 dsp_add(float2 a, float2 b) {
+    float s, e;
+    dsp_two_sum(a.x, b.x, s, e);
+    return dsp_norm(s, e + (a.y + b.y));
+}
+__device__ inline float2 dsp_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    return dsp_norm(p, e);
+}
+__device__ inline float2 dsp_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ inline float2 dsp_shfl_add(float2 a, int o) {
+    return dsp_add(a, make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o)));
+}
+__device__ inline double dsp_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+// Split of a double into a double-single pair on the integer pipes: hi = x
+// truncated to 24 significant bits, lo = the remainder truncated to 24 bits,
+// |x - hi - lo| <= 2^-46 |x|.  |x| < 2^-100 gives (0, 0); NaN, infinities and
+// |x| >= 2^128 take the FP64 conversion (and propagate).
+__device__ inline float2 dsp_split_int(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((u >> 52) & 0x7ffULL) - 1023;
+    if (e < -100) return make_float2(0.f, 0.f);
+    if (e > 127) return make_float2((float)x, 0.f);
+    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+    const unsigned long long mant = u & 0xFFFFFFFFFFFFFULL;
+    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29));
+    const unsigned long long r = mant & 0x1FFFFFFFULL;  // the 29 bits below hi
+    float lo = 0.f;
+    if (r != 0) {
+        const int p = 63 - __clzll((long long)r);  // leading bit of r, 0..28
+        const int le = e - 52 + p;                 // its binary exponent
+        if (le >= -126) {
+            const unsigned m = p >= 23 ? (unsigned)(r >> (p - 23)) : (unsigned)(r << (23 - p));
+            lo = __uint_as_float(sign | ((unsigned)(le + 127) << 23) | (m & 0x7FFFFFu));
+        }
+    }
+    return make_float2(hi, lo);
+}
+
 __device__ inline double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -1385,6 +1385,67 @@ __device__ void z_rows_group(const TaskCache& tc, const double* P1g, const doubl
     split_cbar();
 }
 
+// Rows [r0, r0+nr) of z = (P1 (x) P2) y (N = 2) or P1 y (N = 1) in
+// double-single for the consumer group (CT threads from ct): y as pairs in
+// shared memory, the Kronecker factors staged as pairs (split on the integer
+// pipes), tmp[bb][c] = sum_e Y[c][e] P2[b0+bb][e] with 4 threads per entry,
+// z[(a, b)] = sum_c P1[a][c] tmp[b-b0][c] with 8 threads per row; z to FP64.
+__device__ void z_rows_group_ds(const TaskCache& tc, const double* P1g, const double* P2g, const float2* ys, double* z,
+                                float2* tmp, float2* Ps, int ct, int CT) {
+    const int kd = tc.kd, r0 = tc.r0, nr = tc.nr, kk = kd * kd;
+    float2* P1 = Ps;
+    float2* P2 = Ps + kk;
+    for (int e = ct; e < kk; e += CT) {
+        P1[e] = dsp_split_int(P1g[e]);
+        if (tc.N == 2) P2[e] = dsp_split_int(P2g[e]);
+    }
+    split_cbar();
+    if (tc.N == 2) {
+        const int b0 = r0 / kd, nb = (r0 + nr - 1) / kd - b0 + 1, items = nb * kd;
+        for (int base = 0; base < items; base += CT / 4) {
+            const int it = base + (ct >> 2), g = ct & 3;
+            float2 acc = make_float2(0.f, 0.f);
+            if (it < items) {
+                const int bb = it / kd, c = it - bb * kd;
+                const float2* p2 = P2 + (b0 + bb) * kd;
+                for (int e = g; e < kd; e += 4) ds_fma(acc.x, acc.y, ys[c + kd * e], p2[e]);
+            }
+            acc = dsp_shfl_add(acc, 1);
+            acc = dsp_shfl_add(acc, 2);
+            if (it < items && g == 0) tmp[it] = acc;
+        }
+        split_cbar();
+        for (int base = 0; base < nr; base += CT / 8) {
+            const int i = base + (ct >> 3), g = ct & 7;
+            float2 acc = make_float2(0.f, 0.f);
+            if (i < nr) {
+                const int r = r0 + i, b = r / kd, a = r - b * kd;
+                const float2* p1 = P1 + a * kd;
+                const float2* tb = tmp + (b - b0) * kd;
+                for (int c = g; c < kd; c += 8) ds_fma(acc.x, acc.y, p1[c], tb[c]);
+            }
+            acc = dsp_shfl_add(acc, 1);
+            acc = dsp_shfl_add(acc, 2);
+            acc = dsp_shfl_add(acc, 4);
+            if (i < nr && g == 0) z[i] = dsp_to_double(acc);
+        }
+    } else {
+        for (int base = 0; base < nr; base += CT / 8) {
+            const int i = base + (ct >> 3), g = ct & 7;
+            float2 acc = make_float2(0.f, 0.f);
+            if (i < nr) {
+                const float2* p1 = P1 + (r0 + i) * kd;
+                for (int c = g; c < kd; c += 8) ds_fma(acc.x, acc.y, p1[c], ys[c]);
+            }
+            acc = dsp_shfl_add(acc, 1);
+            acc = dsp_shfl_add(acc, 2);
+            acc = dsp_shfl_add(acc, 4);
+            if (i < nr && g == 0) z[i] = dsp_to_double(acc);
+        }
+    }
+    split_cbar();
+}
+
 // One double-single chunk of 4 columns of a staged row into (yh, yl) and,
 // with HASB, (wh, wl); ONEP: the row's lo plane is absent (taken as 0).
 template <bool HASB, bool ONEP>
@@ -1421,7 +1482,7 @@ __device__ inline void ds_add(float& h, float& l, float oh, float ol) {
 // G y and G b to all lanes.
 template <bool HASB, bool ONEP>
 __device__ inline void split_row(const float* sh, const float* sl, const float2* vf, const float2* bf, int ld,
-                                 int lane, double& y, double& w) {
+                                 int lane, float2& y, float2& w) {
     float yh0 = 0.f, yl0 = 0.f, wh0 = 0.f, wl0 = 0.f, yh1 = 0.f, yl1 = 0.f, wh1 = 0.f, wl1 = 0.f;
     int c = lane * 4;
     for (; c + 128 < ld; c += 256) {
@@ -1436,8 +1497,8 @@ __device__ inline void split_row(const float* sh, const float* sl, const float2*
         ds_add(yh0, yl0, __shfl_xor_sync(0xffffffffu, yh0, o), __shfl_xor_sync(0xffffffffu, yl0, o));
         if (HASB) ds_add(wh0, wl0, __shfl_xor_sync(0xffffffffu, wh0, o), __shfl_xor_sync(0xffffffffu, wl0, o));
     }
-    y = (double)yh0 + (double)yl0;
-    w = HASB ? (double)wh0 + (double)wl0 : 0.0;
+    y = dsp_norm(yh0, yl0);
+    w = HASB ? dsp_norm(wh0, wl0) : make_float2(0.f, 0.f);
 }
 
 // ONEP: only the hi plane of G is staged (the FP32-rounded step matrix of
@@ -1619,38 +1680,51 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                 const SubDev& sd = v.sub[tc.sid];
                 const int wp = A.win_prev[tc.inst];
                 const double* bsrc = (wp > 0) ? v.arena + tc.bvec + (long long)min(m + 1, wp) * K : nullptr;
-                // full y^m = u^m / s_{m-1} + w^m (y^0 = c0), and kappa dt b'^{m+1}
+                // full y^m = u^m / s_{m-1} + w^m (y^0 = c0) and kappa dt b'^{m+1} as
+                // double-single pairs on the FP32 and integer pipes (u, w are
+                // stored as pairs; the FP64 unit of this part is slow)
                 const double is1 = m >= 1 ? __ldcg(sc1 + ni + tc.inst) : 1.0;
                 const double is2 = m >= 2 ? __ldcg(sc2 + ni + tc.inst) : 1.0;
+                float2* ys2 = reinterpret_cast<float2*>(vs);  // y^m as pairs (the matvec input is vf)
                 {
-                    const double* U = v.arena + sd.work + (long long)(m & 1) * 2 * K;
-                    const double* Wv = U + K;
+                    const float2 isf = ds_split(is1), kdt2 = ds_split(tc.kdt);
+                    const float2* U = reinterpret_cast<const float2*>(v.arena + sd.work + (long long)(m & 1) * 2 * K);
+                    const float2* Wv = U + K;
                     const double* c0 = v.arena + tc.c0;
                     // antisymmetric states: on a diagonal subdomain (its own mirror) the
                     // products act on (y - swap(y)) / 2 and likewise b'; y itself is kept
                     // for the history and z
                     const bool anti = diagonal_anti(v, tc);
-                    const double *Um = nullptr, *Wm = nullptr, *c0m = nullptr, *bm = nullptr;
+                    const float2 *Um = nullptr, *Wm = nullptr;
+                    const double *c0m = nullptr, *bm = nullptr;
                     if (anti) {
                         const SubDev& ms = v.sub[mirror_sid(v, tc)];
-                        Um = v.arena + ms.work + (long long)(m & 1) * 2 * K;
+                        Um = reinterpret_cast<const float2*>(v.arena + ms.work + (long long)(m & 1) * 2 * K);
                         Wm = Um + K;
                         c0m = v.arena + ms.c0;
                         if (bsrc) bm = v.arena + ms.bvec + (long long)min(m + 1, wp) * K;
                     }
+                    const float2 half = make_float2(0.5f, 0.f);
                     for (int c = ct; c < ld; c += CT) {
                         if (c < K) {
-                            const double y = m == 0 ? c0[c] : __ldcg(U + c) * is1 + __ldcg(Wv + c);
-                            double yp = y, bp = bsrc ? bsrc[c] : 0.0;
+                            auto ld2 = [](const float2* p) {
+                                const unsigned long long u = __ldcg(reinterpret_cast<const unsigned long long*>(p));
+                                return make_float2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
+                            };
+                            const float2 y = m == 0 ? dsp_split_int(c0[c]) : dsp_add(dsp_mul(ld2(U + c), isf), ld2(Wv + c));
+                            float2 yp = y, bp = bsrc ? dsp_split_int(bsrc[c]) : make_float2(0.f, 0.f);
                             if (anti) {
                                 const int sc = swap_index(c, tc.kd);
-                                yp = 0.5 * (y - (m == 0 ? c0m[sc] : __ldcg(Um + sc) * is1 + __ldcg(Wm + sc)));
-                                if (bsrc) bp = 0.5 * (bp - __ldcg(bm + sc));
+                                const float2 ym_ = m == 0 ? dsp_split_int(c0m[sc])
+                                                          : dsp_add(dsp_mul(ld2(Um + sc), isf), ld2(Wm + sc));
+                                yp = dsp_mul(half, dsp_add(y, dsp_neg(ym_)));
+                                if (bsrc) bp = dsp_mul(half, dsp_add(bp, dsp_neg(dsp_split_int(__ldcg(bm + sc)))));
                             }
-                            vs[c] = y;
-                            vf[c] = ds_split(yp);
-                            bf[c] = bsrc ? ds_split(tc.kdt * bp) : make_float2(0.f, 0.f);
+                            ys2[c] = y;
+                            vf[c] = yp;
+                            bf[c] = bsrc ? dsp_mul(kdt2, bp) : make_float2(0.f, 0.f);
                         } else {
+                            ys2[c] = make_float2(0.f, 0.f);
                             vf[c] = make_float2(0.f, 0.f);
                             bf[c] = make_float2(0.f, 0.f);
                         }
@@ -1660,11 +1734,13 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                 double* ym = own(tc, m % 3);
                 double* hrow = v.arena + tc.hist + (long long)m * K;
                 for (int r = ct; r < nr; r += CT) {
-                    ym[r] = vs[tc.r0 + r];
-                    hrow[tc.r0 + r] = vs[tc.r0 + r];
+                    const double yd = m == 0 ? v.arena[tc.c0 + tc.r0 + r] : dsp_to_double(ys2[tc.r0 + r]);
+                    ym[r] = yd;
+                    hrow[tc.r0 + r] = yd;
                 }
                 double* zm = own(tc, 3 + m % 3);
-                z_rows_group(tc, v.arena + tc.p1, v.arena + tc.p2, vs, zm, tmp, Ps, ct, CT);
+                z_rows_group_ds(tc, v.arena + tc.p1, v.arena + tc.p2, ys2, zm, reinterpret_cast<float2*>(tmp),
+                                reinterpret_cast<float2*>(Ps), ct, CT);
                 // partials: s_m^2 (own rows of y^m . z^m) and D_{m-1}
                 {
                     const bool dn = m >= 2 && tc.ngf_stop;
@@ -1700,8 +1776,8 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                 // staged rows: row r0 + o of the task to consumer warp o mod 7, whole
                 // rows per warp, no block barrier between stages
                 const int rs = split_stage_rows(ld, SC, ONEP ? 1 : 2);
-                double* Un = v.arena + sd.work + (long long)((m + 1) & 1) * 2 * K;
-                double* Wn = Un + K;
+                float2* Un = reinterpret_cast<float2*>(v.arena + sd.work + (long long)((m + 1) & 1) * 2 * K);
+                float2* Wn = Un + K;
                 const bool hasb = bsrc != nullptr;
                 for (int rb = tc.r0; rb < tc.r0 + nr; rb += rs) {
                     const int nrow = min(rs, tc.r0 + nr - rb);
@@ -1710,7 +1786,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                     const float* stage = ring + (size_t)s * SC;
                     int r = ((cw - (rb - tc.r0)) % NCW + NCW) % NCW;
                     for (; r < nrow; r += NCW) {
-                        double y, w;
+                        float2 y, w;
                         if (hasb)
                             split_row<true, ONEP>(stage + (size_t)r * ld, stage + (size_t)(rs + r) * ld, vf, bf, ld,
                                                   lane, y, w);
