@@ -788,7 +788,7 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.res = o; o = al256(o + ni * sizeof(double));
     a.cv_part = o; o = al256(o + cvtot_part_doubles((int)ni) * sizeof(double));
     a.cvtot = o; o = al256(o + ni * sizeof(double));
-    a.epart = o; o = al256(o + 3 * ns * sizeof(double));
+    a.epart = o; o = al256(o + 3 * ns * ENERGY_BLOCKS * sizeof(double));
     a.energy = o; o = al256(o + ni * sizeof(double));
     a.norm2 = o; o = al256(o + ni * sizeof(double));
     a.dipole = o; o = al256(o + ni * sizeof(double));

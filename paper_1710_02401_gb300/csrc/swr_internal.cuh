@@ -359,6 +359,8 @@ cudaError_t cluster_occupancy(int* clusters, int rows_max, size_t smem, int cs, 
 cudaError_t launch_cluster_window(SweepArgs& a, int grid, int cs, size_t smem, cudaStream_t st, bool onep);
 void set_error(swr_ctx* c, const char* msg);
 void set_setup_error(const char* msg);
+// Blocks per subdomain of the energy kernel (partials [n_sub][ENERGY_BLOCKS][3]).
+#define ENERGY_BLOCKS 16
 cudaError_t launch_residual(const SwrDeviceView& v, cudaStream_t st, const int* d_win, const int* d_win_prev,
                             int parity, int first_iter, double* d_part, int res_blocks, double* d_res);
 }  // namespace swr

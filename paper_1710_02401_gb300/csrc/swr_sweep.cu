@@ -450,9 +450,14 @@ __global__ void k_cvtot_reduce(int n_inst, const double* part, int nblk, double*
 // Per subdomain at step W (normalised state): sums over the volume nodes of
 // w chi (kappa |grad psi|^2 + V |psi|^2), w chi |psi|^2 and w chi (x_1+..+x_N)|psi|^2,
 // and psi at the nodes (node p = q1 + q*q2; re, im interleaved in real time).
+// Energy partials of one subdomain split over ENERGY_BLOCKS blocks: block b
+// takes the quadrature nodes of the last coordinate in
+// [b q / ENERGY_BLOCKS, (b+1) q / ENERGY_BLOCKS) (and, N = 2, only the columns
+// of the first contraction those nodes need); partial (sid, b) at
+// part[3 (sid ENERGY_BLOCKS + b)].
 __global__ void k_energy(SwrDeviceView v, const int* win, const double* snorm, int cap, double* part,
                          double* psi_out, const long long* psi_off) {
-    const int sid = blockIdx.x;
+    const int sid = blockIdx.y, blk = blockIdx.x;
     const SubDev& s = v.sub[sid];
     const InstDev& in = v.inst[s.inst];
     const int W = win[s.inst], nch = n_channels(in);
@@ -471,7 +476,8 @@ __global__ void k_energy(SwrDeviceView v, const int* win, const double* snorm, i
         for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c] = y[c] / sn;
         __syncthreads();
         if (s.N == 1) {
-            for (int n = threadIdx.x; n < q; n += blockDim.x) {
+            const int n_lo = blk * q / ENERGY_BLOCKS, n_hi = (blk + 1) * q / ENERGY_BLOCKS;
+            for (int n = n_lo + threadIdx.x; n < n_hi; n += blockDim.x) {
                 double p = 0, dp = 0;
                 for (int a = 0; a < kd; ++a) {
                     p += T0[lay.B() + n * kd + a] * ys[a];
@@ -485,8 +491,9 @@ __global__ void k_energy(SwrDeviceView v, const int* win, const double* snorm, i
             }
         } else {
             const double* T1 = v.arena + s.t1[1];
-            for (int e = threadIdx.x; e < kd * q; e += blockDim.x) {
-                int a = e / q, n2 = e % q;
+            const int n2_lo = blk * q / ENERGY_BLOCKS, n2_hi = (blk + 1) * q / ENERGY_BLOCKS, nw = n2_hi - n2_lo;
+            for (int e = threadIdx.x; e < kd * nw; e += blockDim.x) {
+                int a = e / nw, n2 = n2_lo + e % nw;
                 double acc = 0, accd = 0;
                 for (int b = 0; b < kd; ++b) {
                     double c = ys[a + kd * b];
@@ -497,14 +504,14 @@ __global__ void k_energy(SwrDeviceView v, const int* win, const double* snorm, i
                 G1d[e] = accd;
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+            for (int e = n2_lo * q + threadIdx.x; e < n2_hi * q; e += blockDim.x) {
                 int n2 = e / q, n1 = e % q;
                 double p = 0, d1 = 0, d2 = 0;
                 for (int a = 0; a < kd; ++a) {
                     double b1 = T0[lay.B() + n1 * kd + a];
-                    p += b1 * G1[a * q + n2];
-                    d1 += T0[lay.D() + n1 * kd + a] * G1[a * q + n2];
-                    d2 += b1 * G1d[a * q + n2];
+                    p += b1 * G1[a * nw + (n2 - n2_lo)];
+                    d1 += T0[lay.D() + n1 * kd + a] * G1[a * nw + (n2 - n2_lo)];
+                    d2 += b1 * G1d[a * nw + (n2 - n2_lo)];
                 }
                 double x1 = T0[lay.x() + n1], x2 = T1[lay.x() + n2];
                 double r = x1 - x2;
@@ -522,9 +529,10 @@ __global__ void k_energy(SwrDeviceView v, const int* win, const double* snorm, i
     den = block_sum(den, red);
     dip = block_sum(dip, red);
     if (threadIdx.x == 0) {
-        part[3 * sid] = num;
-        part[3 * sid + 1] = den;
-        part[3 * sid + 2] = dip;
+        const long long o = 3LL * ((long long)sid * ENERGY_BLOCKS + blk);
+        part[o] = num;
+        part[o + 1] = den;
+        part[o + 2] = dip;
     }
 }
 
@@ -533,11 +541,13 @@ __global__ void k_energy_reduce(SwrDeviceView v, const double* part, double* ene
     if (i >= v.n_inst) return;
     const InstDev& in = v.inst[i];
     double num = 0, den = 0, dip = 0;
-    for (int j = 0; j < in.n_sub; ++j) {
-        num += part[3 * (in.sub_base + j)];
-        den += part[3 * (in.sub_base + j) + 1];
-        dip += part[3 * (in.sub_base + j) + 2];
-    }
+    for (int j = 0; j < in.n_sub; ++j)
+        for (int b = 0; b < ENERGY_BLOCKS; ++b) {
+            const long long o = 3LL * ((long long)(in.sub_base + j) * ENERGY_BLOCKS + b);
+            num += part[o];
+            den += part[o + 1];
+            dip += part[o + 2];
+        }
     energy[i] = num / den;
     norm2[i] = den;
     dipole[i] = dip / den;
@@ -636,7 +646,7 @@ cudaError_t launch_energy(const SwrDeviceView& v, cudaStream_t st, const int* d_
                           int cap, double* d_part, double* d_energy, double* d_norm2, double* d_dipole,
                           double* psi_out, const long long* psi_off, size_t smem) {
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_energy<<<v.n_sub, 256, smem, st>>>(v, d_win, d_snorm, cap, d_part, psi_out, psi_off);
+    k_energy<<<dim3(ENERGY_BLOCKS, v.n_sub), 256, smem, st>>>(v, d_win, d_snorm, cap, d_part, psi_out, psi_off);
     k_energy_reduce<<<div_up(v.n_inst, 128), 128, 0, st>>>(v, d_part, d_energy, d_norm2, d_dipole);
     return cudaGetLastError();
 }
