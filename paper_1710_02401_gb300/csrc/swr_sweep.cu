@@ -95,7 +95,7 @@ __global__ void k_line_traces(SwrDeviceView v, const int* win, int cap, int kmax
             }
             continue;
         }
-        for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c + c / kd] = ds_split(y[c]);  // (a, b) at a + (kd+1) b
+        for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c + c / kd] = dsp_split_int(y[c]);  // (a, b) at a + (kd+1) b
         __syncthreads();
         for (int e = threadIdx.x; e < 16 * kd; e += blockDim.x) {
             const int combo = e / kd, m = e % kd;
@@ -143,9 +143,10 @@ __device__ inline void gamma_slot(const SubDev& s, int node, int& slot, int& nt)
 
 // Averaged Robin data g_i and own traces u_i at the interface nodes of every
 // subdomain for steps 0..W, and the Robin source b'_i of the next iteration.
-// The tangential sums of b' run over the weighted node tables
-// WB_d[t][m] = w_t B_d[t][m], staged once per CTA in shared memory when they
-// fit (`staged`), each sum split into GATHER_SPLIT chunks added in a fixed order.
+// The tangential sums of b' run in double-single on the FP32 pipes over the
+// weighted node tables WB_d[t][m] = w_t B_d[t][m], staged once per CTA in
+// shared memory as pairs when they fit (`staged`), each sum split into
+// GATHER_SPLIT chunks added in a fixed order; b' is written in FP64.
 #define GATHER_SPLIT 4
 __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, int cap, int parity, int staged) {
     const int sid = blockIdx.y;
@@ -154,20 +155,27 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
     const int W = win[s.inst], nch = n_channels(in);
     const int kd = s.kd, q = s.q, K = s.K, L = in.L, qp = in.q_p;
     T1Layout lay(q, kd);
-    __shared__ double gs[2][4 * 384];
-    __shared__ double hsum[4][64];
-    __shared__ double hpart[GATHER_SPLIT][4][64];
-    extern __shared__ double wbs[];  // [2][q][kd] (staged)
-    if (staged && s.N == 2) {
-        for (int e = threadIdx.x; e < 2 * q * kd; e += blockDim.x) {
-            const int d = e / (q * kd), rest = e % (q * kd), t = rest / kd;
-            const double* To = v.arena + s.t1[d];
-            wbs[e] = To[lay.w() + t] * To[lay.B() + rest];
+    __shared__ float2 gs2[2][4 * 384];  // Robin data of the step as pairs (b' sums)
+    __shared__ float2 hsum[4][64];
+    __shared__ float2 hpart[GATHER_SPLIT][4][64];
+    __shared__ float2 lvt[2][2][64];     // Lv rows l = 0, 3 of both coordinates as pairs
+    extern __shared__ float2 wbs[];      // [2][q][kd] (staged)
+    if (s.N == 2) {
+        if (staged)
+            for (int e = threadIdx.x; e < 2 * q * kd; e += blockDim.x) {
+                const int d = e / (q * kd), rest = e % (q * kd), t = rest / kd;
+                const double* To = v.arena + s.t1[d];
+                wbs[e] = dsp_split_int(To[lay.w() + t] * To[lay.B() + rest]);
+            }
+        for (int e = threadIdx.x; e < 2 * 2 * kd; e += blockDim.x) {
+            const int d = e / (2 * kd), li = (e / kd) & 1, a = e % kd;
+            lvt[d][li][a] = dsp_split_int(v.arena[s.t1[d] + lay.Lv() + (li ? 3 : 0) * kd + a]);
         }
         __syncthreads();
     }
     for (int n = blockIdx.x; n <= W; n += gridDim.x) {
         const double sn = in.normalize ? snorm[(long long)s.inst * (cap + 1) + n] : 1.0;
+        const double isn = 1.0 / sn;  // one division per step, not per node
         for (int node = threadIdx.x; node < s.ngam; node += blockDim.x) {
             int slot, nt;
             gamma_slot(s, node, slot, nt);
@@ -219,7 +227,8 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
                     }
                 }
             }
-            const double inv = 1.0 / (double)cnt;
+            // 1/cnt for the contributor counts that occur (1 to 3: constants)
+            const double inv = cnt == 1 ? 1.0 : cnt == 2 ? 0.5 : cnt == 3 ? 1.0 / 3.0 : 1.0 / (double)cnt;
             // g = (n.grad + mu) psi_j averaged (Robin), or mu psi_j (classical SWR by
             // penalty); complex mu mixes the planes
             const double sd = in.tc == SWR_TC_DIRICHLET ? 0.0 : sig;
@@ -227,9 +236,9 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
             double gim = (sd * der[1] + in.mu_re * val[1] + in.mu_im * val[0]) * inv;
             for (int ch = 0; ch < nch; ++ch) {
                 const double gv = ch ? gim : gre;
-                v.arena[s.u[parity] + ((long long)n * nch + ch) * s.ngam + node] = own[ch] / sn;
+                v.arena[s.u[parity] + ((long long)n * nch + ch) * s.ngam + node] = own[ch] * isn;
                 v.arena[s.g + ((long long)n * nch + ch) * s.ngam + node] = gv;
-                gs[ch][node] = gv;
+                gs2[ch][node] = dsp_split_int(gv);
             }
         }
         __syncthreads();
@@ -243,7 +252,8 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
                     for (int sl = 0; sl < 2; ++sl) {
                         if (s.gam_off[sl] < 0) continue;
                         int l = sl ? 3 : 0;
-                        acc += gs[ch][s.gam_off[sl]] * T[lay.Lv() + l * kd + a];
+                        acc += v.arena[s.g + ((long long)n * nch + ch) * s.ngam + s.gam_off[sl]] *
+                               T[lay.Lv() + l * kd + a];
                     }
                     bdst[a] = acc;
                 }
@@ -251,39 +261,39 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
                 const int chunk = (q + GATHER_SPLIT - 1) / GATHER_SPLIT;
                 for (int e = threadIdx.x; e < GATHER_SPLIT * 4 * kd; e += blockDim.x) {
                     const int part = e / (4 * kd), rest = e % (4 * kd), sl = rest / kd, m = rest % kd;
-                    double acc = 0;
+                    float2 acc = make_float2(0.f, 0.f);
                     if (s.gam_off[sl] >= 0) {
                         const int d = sl / 2, t0 = part * chunk, t1 = min(q, t0 + chunk);
-                        const double* gv = gs[ch] + s.gam_off[sl];
+                        const float2* gv = gs2[ch] + s.gam_off[sl];
                         if (staged) {
-                            const double* wb = wbs + (long long)(1 - d) * q * kd;
-                            for (int t = t0; t < t1; ++t) acc += gv[t] * wb[t * kd + m];
+                            const float2* wb = wbs + (long long)(1 - d) * q * kd;
+                            for (int t = t0; t < t1; ++t) ds_fma(acc.x, acc.y, gv[t], wb[t * kd + m]);
                         } else {
                             const double* To = v.arena + s.t1[1 - d];
-                            for (int t = t0; t < t1; ++t) acc += gv[t] * (To[lay.w() + t] * To[lay.B() + t * kd + m]);
+                            for (int t = t0; t < t1; ++t)
+                                ds_fma(acc.x, acc.y, gv[t], dsp_split_int(To[lay.w() + t] * To[lay.B() + t * kd + m]));
                         }
                     }
-                    hpart[part][sl][m] = acc;
+                    hpart[part][sl][m] = dsp_norm(acc.x, acc.y);
                 }
                 __syncthreads();
                 for (int e = threadIdx.x; e < 4 * kd; e += blockDim.x) {
                     const int sl = e / kd, m = e % kd;
-                    double acc = 0;
-                    for (int part = 0; part < GATHER_SPLIT; ++part) acc += hpart[part][sl][m];
+                    float2 acc = make_float2(0.f, 0.f);
+                    for (int part = 0; part < GATHER_SPLIT; ++part) acc = dsp_add(acc, hpart[part][sl][m]);
                     hsum[sl][m] = acc;
                 }
                 __syncthreads();
                 for (int e = threadIdx.x; e < K; e += blockDim.x) {
                     int a = e % kd, b = e / kd;
-                    double acc = 0;
+                    float2 acc = make_float2(0.f, 0.f);
                     for (int sl = 0; sl < 4; ++sl) {
                         if (s.gam_off[sl] < 0) continue;
-                        int d = sl / 2, l = (sl % 2) ? 3 : 0;
-                        const double* Td = v.arena + s.t1[d];
-                        if (d == 0) acc += Td[lay.Lv() + l * kd + a] * hsum[sl][b];
-                        else acc += hsum[sl][a] * Td[lay.Lv() + l * kd + b];
+                        const int d = sl / 2, li = sl % 2;
+                        if (d == 0) ds_fma(acc.x, acc.y, lvt[0][li][a], hsum[sl][b]);
+                        else ds_fma(acc.x, acc.y, hsum[sl][a], lvt[1][li][b]);
                     }
-                    bdst[e] = acc;
+                    bdst[e] = dsp_to_double(acc);
                 }
             }
             __syncthreads();
@@ -602,7 +612,7 @@ cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_wi
         k_line_traces<<<dim3(nb, v.n_sub), 256, sm, st>>>(v, d_win, cap, lt_kmax, lt_kdmax, lt_qmax, staged);
     }
     {
-        const size_t tab = 2 * (size_t)lt_qmax * lt_kdmax * sizeof(double);
+        const size_t tab = 2 * (size_t)lt_qmax * lt_kdmax * sizeof(float2);
         const int staged = tab <= 96 * 1024;
         if (staged) cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab);
         k_gather<<<dim3(nb, v.n_sub), 256, staged ? tab : 0, st>>>(v, d_win, d_snorm, cap, parity, staged);
