@@ -443,6 +443,7 @@ static bool plan_cluster(swr_ctx* c, int rows_req, bool have_dev) {
     const int nsm = c->nsm > 0 ? c->nsm : 152;
     const int ns = (int)c->sub.size();
     if (ns < 1 || ns > nsm) return false;
+    if (nsm > 160) return false;  // the kernel polls at most 160 slots per instance
     int kmin = 1 << 30;
     for (const SubDev& s : c->sub) kmin = s.K < kmin ? s.K : kmin;
     int cs = nsm / ns;

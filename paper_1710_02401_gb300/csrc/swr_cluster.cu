@@ -42,6 +42,7 @@ namespace swr {
 #define CL_THREADS 512
 #define CL_WARPS (CL_THREADS / 32)
 #define CL_SMEM_MIN (120 * 1024)  // at least this much shared memory: one CTA per SM
+#define CL_POLL 5                  // slots polled per lane: instances of at most 160 CTAs
 #define CL_SMEM_MAX (226 * 1024)  // dynamic shared memory budget per CTA
 
 __device__ inline unsigned cl_smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -143,6 +144,7 @@ template <int RPL, bool ONEP>
 __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
     extern __shared__ __align__(16) unsigned char cl_sm[];
     __shared__ float2 red2[CL_WARPS];
+    __shared__ float2 s_poll[CL_POLL][32][2];  // polled partials (s^2, D) per lane and slot
     __shared__ float2 s_is[2];    // 1/s_n, 1/s_{n-1} (after the decisions of step n)
     __shared__ float2 s_dpart;    // partial of D_{n-1} from this CTA's rows
     __shared__ float2 s_sn;       // s_n
@@ -340,36 +342,56 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
             //      polls per slot), summed in slot order, the same bits in every CTA
             float2 ss = make_float2(0.f, 0.f), sd = make_float2(0.f, 0.f);
             bool ok = true;
-            for (int base = t0; base < t1; base += 32) {
-                const int j = base + lane;
-                float2 ps = make_float2(0.f, 0.f), pd = make_float2(0.f, 0.f);
-                if (j < t1 && ok) {
-                    const unsigned long long* w = slots + (size_t)j * 4;
-                    long long it = 0;
-                    for (;;) {
-                        unsigned long long w0, w1, w2, w3;
-                        cl_ld2_relaxed(w, w0, w1);
-                        cl_ld2_relaxed(w + 2, w2, w3);
-                        if ((unsigned)(w0 >> 32) == tag && (unsigned)(w1 >> 32) == tag &&
-                            (unsigned)(w2 >> 32) == tag && (unsigned)(w3 >> 32) == tag) {
-                            ps = make_float2(cl_untag(w0), cl_untag(w1));
-                            pd = make_float2(cl_untag(w2), cl_untag(w3));
-                            break;
+            // lane l owns the slots t0 + l + 32 u (u < CL_POLL); each round issues the
+            // loads of all its slots still missing (in groups of three), so the wait
+            // after the last arrival is one L2 round trip, not one per slot
+            unsigned todo = 0;
+#pragma unroll
+            for (int u = 0; u < CL_POLL; ++u) {
+                s_poll[u][lane][0] = s_poll[u][lane][1] = make_float2(0.f, 0.f);
+                if (t0 + lane + 32 * u < t1) todo |= 1u << u;
+            }
+            long long it = 0;
+            while (todo && ok) {
+                // loads in flight together for groups of at most 3 slots (registers)
+#pragma unroll
+                for (int g0 = 0; g0 < CL_POLL; g0 += 3) {
+                    unsigned long long w[3][4];
+#pragma unroll
+                    for (int du = 0; du < 3; ++du) {
+                        const int u = g0 + du;
+                        if (u < CL_POLL && (todo & (1u << u))) {
+                            const unsigned long long* wp_ = slots + (size_t)(t0 + lane + 32 * u) * 4;
+                            cl_ld2_relaxed(wp_, w[du][0], w[du][1]);
+                            cl_ld2_relaxed(wp_ + 2, w[du][2], w[du][3]);
                         }
-                        if (++it > A.spin_limit) {
-                            atomicOr(v.err, SWR_ERR_TIMEOUT);
-                            ok = false;
-                            break;
-                        }
-                        if ((it & 255) == 0 && *(volatile int*)v.err) {
-                            ok = false;
-                            break;
+                    }
+#pragma unroll
+                    for (int du = 0; du < 3; ++du) {
+                        const int u = g0 + du;
+                        if (u < CL_POLL && (todo & (1u << u)) && (unsigned)(w[du][0] >> 32) == tag &&
+                            (unsigned)(w[du][1] >> 32) == tag && (unsigned)(w[du][2] >> 32) == tag &&
+                            (unsigned)(w[du][3] >> 32) == tag) {
+                            s_poll[u][lane][0] = make_float2(cl_untag(w[du][0]), cl_untag(w[du][1]));
+                            s_poll[u][lane][1] = make_float2(cl_untag(w[du][2]), cl_untag(w[du][3]));
+                            todo &= ~(1u << u);
                         }
                     }
                 }
-                // slot order: lane-strided partial sums, combined below in lane order
-                ss = dsp_add(ss, ps);
-                sd = dsp_add(sd, pd);
+                if (todo) {
+                    if (++it > A.spin_limit) {
+                        atomicOr(v.err, SWR_ERR_TIMEOUT);
+                        ok = false;
+                    } else if ((it & 255) == 0 && *(volatile int*)v.err) {
+                        ok = false;
+                    }
+                }
+            }
+            // slot order: lane-strided partial sums, combined below in lane order
+#pragma unroll
+            for (int u = 0; u < CL_POLL; ++u) {
+                ss = dsp_add(ss, s_poll[u][lane][0]);
+                sd = dsp_add(sd, s_poll[u][lane][1]);
             }
             if (__any_sync(0xffffffffu, !ok)) {
                 if (lane == 0) s_fail = 1;
@@ -520,8 +542,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
             // this CTA leaves after the barrier: so does every CTA of its cluster
             if (tid < (int)CS) cl_store_int(&cl_flag[n & 1], (unsigned)tid, 1);
         }
-        __syncthreads();
-        cl_sync();
+        cl_sync();  // also a barrier of this CTA's threads
         // one read for the whole CTA; the entry is cleared for step n+2 before
         // this CTA arrives at the next barrier (no peer writes it before that)
         if (tid == 0) {
