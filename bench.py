@@ -487,6 +487,29 @@ def extra_real_time(args, env):
     return out
 
 
+def run_real_time_converge(args, S, kmax=80):
+    """The real-time 64-subdomain workload from assembly to Res <= 1e-8:
+    CUDA-synchronised wall time of assemble + iterate, the iteration count
+    and the residual of every iteration."""
+    import torch
+    inst = workload("tdse_2e_64sd")
+    s = S.SWR(inst, precision=prec_code(S, args.precision))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.assemble()
+    rep, hist = s.iterate(TOL, kmax)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    out = {"metric": "real-time workload to Res <= 1e-8 (wall time, assembly included)", "value": wall, "unit": "s",
+           "higher_is_better": False, "data": "synthetic", "precision": args.precision,
+           "config": workload_config("tdse_2e_64sd", inst), "converged": bool(rep.converged),
+           "schwarz_iterations": rep.iterations, "res_history": [float(x) for x in hist],
+           "subdomain_solves": rep.subdomain_solves, "solves_per_s": rep.subdomain_solves / wall,
+           "norm2": float(s.norm2()[0]), "dipole": float(s.dipole()[0])}
+    s.close()
+    print(json.dumps(out))
+
+
 def run_lsd(args, S, reps=3):
     """swr_lsd_build at the paper's Test 1 sizes: wall time of the whole call
     (allocation, device work, copies back), best of `reps` after a warm-up,
@@ -648,6 +671,10 @@ def main():
                     help="time swr_assemble (quadrature, local matrices, orthonormalisation, e-e block, step-matrix "
                          "inversion) with the FP64 and the tensor-core contractions on the real-time 64-subdomain and "
                          "the 2-electron ground-state workloads; one JSON line")
+    ap.add_argument("--real-time-converge", action="store_true",
+                    help="the 64-subdomain real-time workload (K = 1024 complex, 1000 Crank-Nicolson steps) iterated "
+                         "to Res <= 1e-8 in the headline precision: wall time, Schwarz iterations, residual history, "
+                         "final norm and dipole; one JSON line")
     ap.add_argument("--lsd", action="store_true",
                     help="local orbitals and local Slater determinants at the paper's Test 1 sizes (L = 5, 10 orbitals "
                          "per subdomain, 45 determinants per subdomain): time of swr_lsd_build (best of three) and "
@@ -697,6 +724,12 @@ def main():
     if args.assembly:
         if rank == 0:
             run_assembly(args, S)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.real_time_converge:
+        if rank == 0:
+            run_real_time_converge(args, S)
         if world > 1:
             dist.destroy_process_group()
         return
