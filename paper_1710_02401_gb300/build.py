@@ -20,7 +20,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libswr.so")
 SOURCES = ["swr_api.cu", "swr_assemble.cu", "swr_sweep.cu", "swr_window.cu", "swr_tdse.cu", "swr_codec.cu",
            "swr_mlp.cu", "swr_noalloc.cu", "swr_tcgj.cu",
-           "swr_cluster.cu", "swr_lsd.cu"]
+           "swr_cluster.cu", "swr_lsd.cu", "swr_robin.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

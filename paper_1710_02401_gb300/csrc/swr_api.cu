@@ -95,6 +95,8 @@ struct swr_ctx {
     // window plan: kernel variant, row-task target, CTA ranges, task state in global memory
     int variant = WIN_TWO_PHASE, rows_target = 0, many = 0;
     bool has_w = false;             // W = (Pp (x) Pp) G allocated (fused variant possible)
+    bool robin_w = false;           // Robin response GE, H, W allocated (cluster window possible)
+    int max_J = 0;                  // Robin response: largest column count of GE
     std::vector<int> cta_task0, cta_list;
     long long tasks_cap = 0;        // capacity of the task arrays (row target 8)
     int *d_cta_task0 = nullptr, *d_cta_list = nullptr;
@@ -439,7 +441,7 @@ static long long task_capacity(const swr_ctx* c) {
 // whose rows fit shared and tensor memory and of which the device holds all ns
 // clusters at once (a row request gives cs = ceil(max K / rows)).
 static bool plan_cluster(swr_ctx* c, int rows_req, bool have_dev) {
-    if (!c->df32 || c->tdse || c->any_anti) return false;
+    if (!c->df32 || c->tdse || c->any_anti || !c->robin_w) return false;
     const int nsm = c->nsm > 0 ? c->nsm : 152;
     const int ns = (int)c->sub.size();
     if (ns < 1 || ns > nsm) return false;
@@ -706,6 +708,7 @@ static void plan(swr_ctx* c) {
             }
             s.Gf = 0;
             s.Wf = 0;
+            s.GE = s.Hr = s.Wr = 0;
             c->psi_off.push_back(po);
             po += (d.N == 2) ? (long long)q * q : q;
             if (K > c->max_K) c->max_K = K;
@@ -726,8 +729,27 @@ static void plan(swr_ctx* c) {
                    (c->tasks_per_cta <= window_tasks_per_cta_max() && c->max_rows <= window_rows_per_task_max() &&
                     window_smem(c->max_K, c->max_kd, c->max_rows, c->tasks_per_cta, 0) <= WIN_SMEM_TASKS_MAX);
     }
+    // the Robin response of the cluster window (w^n = kappa dt G b'^n for every
+    // step, swr_robin.cu): where that window can run (mixed precision,
+    // imaginary time, no antisymmetric instance, at most one subdomain per SM)
+    {
+        const int nsm = c->nsm > 0 ? c->nsm : 152;
+        bool small_kd = true;
+        for (const SubDev& s : c->sub) small_kd = small_kd && (s.N == 1 || s.kd <= 64);
+        c->robin_w = c->df32 && !c->tdse && !c->any_anti && small_kd && !c->sub.empty() &&
+                     (int)c->sub.size() <= nsm && nsm <= 160 &&
+                     (p.window_variant == 0 || p.window_variant == WIN_CLUSTER);
+    }
+    c->max_J = 0;
     for (SubDev& s : c->sub) {
         const long long K = s.K;
+        if (c->robin_w) {
+            const long long J = robin_columns(s);
+            s.GE = off; off = align32(off + K * (J > 0 ? J : 1));
+            s.Hr = off; off = align32(off + (long long)(c->cap + 1) * (J > 0 ? J : 1));
+            s.Wr = off; off = align32(off + (long long)(c->cap + 1) * df32_ld((int)K));
+            if (J > c->max_J) c->max_J = (int)J;
+        }
         if (c->df32 && c->tdse) {
             s.Gf = off; off = align32(off + 2LL * K * df32_ld((int)K));  // four FP32 planes of the complex G0 [K][ld]
         } else if (c->df32) {
@@ -1075,6 +1097,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
                        c->d_jobs1, c->d_jobs2, c->d_norm_part, c->tg));
     if (c->df32 && !c->tdse) CU(launch_split_df32(view(c), c->stream, c->max_K, c->has_w));
     if (c->df32 && c->tdse) CU(launch_split_c_df32(view(c), c->stream, c->max_K));
+    if (c->robin_w && c->max_J > 0) CU(launch_robin_ge(view(c), c->stream, c->max_K, c->max_J));
     CU(cudaEventRecord(c->ev1, c->stream));
     swr_status st = check_err(c);
     if (st != SWR_OK) return st;
@@ -1083,7 +1106,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
     c->counters[6] += ams;
     c->counters[2] += kAssembleLaunchesFixed + (c->any_ee ? (c->tg ? 7 : 3) : 0) +
                       (c->tg ? 4 : 2) * ((c->max_K + GJ_NB_HOST - 1) / GJ_NB_HOST) +
-                      (c->df32 ? (c->tdse || !c->has_w ? 1 : 2) : 0);
+                      (c->df32 ? (c->tdse || !c->has_w ? 1 : 2) : 0) + (c->robin_w && c->max_J > 0 ? 1 : 0);
     c->assembled = true;
     c->k = 0;
     c->parity = 0;
@@ -1157,8 +1180,11 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
             e = cudaMemcpyAsync(c->d_win, c->d_wfix, c->inst.size() * sizeof(int), cudaMemcpyDeviceToDevice, st);
     } else {
         SweepArgs a = sweep_args(c);
-        e = launch_window(a, c->grid, c->win_smem, st, (int)c->inst.size(), c->variant, c->df32, fp32_phase(c),
-                          c->evw0, c->evw1);
+        // the cluster window takes the Robin response of every step from memory
+        if (c->variant == WIN_CLUSTER) e = launch_robin_w(view(c), st, c->d_win_prev, c->max_K, c->nsm > 0 ? c->nsm : 152);
+        if (e == cudaSuccess)
+            e = launch_window(a, c->grid, c->win_smem, st, (int)c->inst.size(), c->variant, c->df32, fp32_phase(c),
+                              c->evw0, c->evw1);
     }
     if (e == cudaSuccess)
         e = launch_post(view(c), st, c->d_win, c->d_win_prev, c->d_snorm, c->cap, c->parity, c->k == 0 ? 1 : 0,
@@ -1279,7 +1305,8 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     }
     c->counters[0] += wms;
     c->counters[1] += 1;
-    c->counters[2] += kStepLaunches - 1 + win_launches + (c->any_anti ? 1 : 0) + (c->prob.cvtot_each_iteration ? 2 : 0);
+    c->counters[2] += kStepLaunches - 1 + win_launches + (c->any_anti ? 1 : 0) + (c->prob.cvtot_each_iteration ? 2 : 0) +
+                      (!c->tdse && c->variant == WIN_CLUSTER ? 2 : 0);
     c->counters[3] += flops;
     c->counters[4] += bytes;
     c->counters[5] += (double)solves;
@@ -1362,7 +1389,7 @@ extern "C" swr_status swr_autotune(swr_ctx* c, int steps, swr_tune_report* out) 
     for (int v : variants) {
         if (v == WIN_FUSED && !(c->df32 && c->has_w)) continue;
         if ((v == WIN_SPLIT || v == WIN_RESIDENT || v == WIN_CLUSTER) && !c->df32) continue;
-        if (v == WIN_CLUSTER && c->any_anti) continue;
+        if (v == WIN_CLUSTER && (c->any_anti || !c->robin_w)) continue;
         if (v == WIN_TWO_PHASE && c->prob.precision == SWR_PREC_FP32_REFINED) continue;  // reads both planes
         for (int r : rows_list) cands.push_back({v, r});
     }

@@ -18,14 +18,16 @@
 //      the partial of s_n^2; it is published together with the partial of
 //      D_{n-1} = ||c^{n-1} - c^{n-2}||^2 computed at step n-1, and the
 //      instance's arrival counter is incremented (release);
-//   3. while the counter fills: kappa dt b'^{n+1} is split into double-single
-//      on the integer pipes (the FP64 unit of this part is slow);
+//   3. while the counter fills: own rows of u = G y^n (the product does not
+//      wait for s_n: y^{n+1} = G (y^n / s_n + kappa dt b'^{n+1})
+//      = u / s_n + w^{n+1}, with w^{n+1} = kappa dt G b'^{n+1} formed for every
+//      step before the window, swr_robin.cu);
 //   4. the instance sums (same order, same bits in every CTA) and the
 //      decisions of the other window kernels: stop at n-1 on D_{n-1} <= tol^2,
 //      at n on the cap or a non-positive s_n;
-//   5. v = y^n / s_n + kappa dt b'^{n+1} in double-single, own rows of
-//      y^{n+1} = G v to the history and into every CTA of the cluster, and the
-//      partial of D_n from the own rows (FP64, as the other kernels);
+//   5. own rows of y^{n+1} = u / s_n + w^{n+1} in double-single into every CTA
+//      of the cluster (the history row and the partial of D_n follow from
+//      them at step n+1);
 //   6. cluster barrier.
 // There is no grid barrier: the clusters of one instance meet only at its
 // counter, those of different instances never wait on each other.  Every
@@ -92,12 +94,12 @@ __host__ __device__ inline int cluster_sw(int K) { return 4 * ((df32_ld(K) + 63)
 __host__ __device__ inline int cluster_rpl(int rows) { return (rows + 31) / 32; }
 
 // Shared memory of one CTA (bytes) before the G_hi elements: y^n double
-// buffer | v | P1, P2 | Kronecker scratch | own rows of y and z (3 steps each)
-// | segment partials [rpl][16][32] (double-single pairs).
+// buffer | P1, P2 | Kronecker scratch | own rows of y and z (3 steps each)
+// | own rows of w^{n+1} | segment partials [rpl][16][32] (double-single pairs).
 __host__ __device__ inline int cluster_vlen(int kmax) { return 16 * cluster_sw(kmax); }
 __host__ __device__ inline size_t cluster_smem_vectors(int kmax, int kdmax, int rows_max) {
     const size_t ld = (size_t)cluster_vlen(kmax);  // y and v padded to 16 segments, zero past K
-    return (3 * ld + 2 * (size_t)kdmax * kdmax + (size_t)rows_max + 2 * (size_t)kdmax + 6 * (size_t)rows_max +
+    return (2 * ld + 2 * (size_t)kdmax * kdmax + (size_t)rows_max + 2 * (size_t)kdmax + 7 * (size_t)rows_max +
             (size_t)cluster_rpl(rows_max) * CL_THREADS) *
            sizeof(float2);
 }
@@ -166,13 +168,13 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
     const int ldm = cluster_vlen(A.kmax), kdm = A.kdmax, nrm = A.rows_max;
     float* Gsm = (float*)cl_sm;                           // [16][hsm/4][32][4]
     float2* ybuf = (float2*)(Gsm + (size_t)hsm * CL_THREADS);  // [2][ldm]
-    float2* vf = ybuf + 2 * ldm;
-    float2* P1 = vf + ldm;
+    float2* P1 = ybuf + 2 * ldm;
     float2* P2 = P1 + kdm * kdm;
     float2* tmp = P2 + kdm * kdm;        // [nrm + 2 kdm]
     float2* yown = tmp + nrm + 2 * kdm;  // [3][nrm]
     float2* zown = yown + 3 * nrm;       // [3][nrm]
-    float2* segp = zown + 3 * nrm;       // [rpl][16][32] segment partials
+    float2* wown = zown + 3 * nrm;       // [nrm] own rows of w^{n+1}
+    float2* segp = wown + nrm;           // [rpl][16][32] segment partials
     const unsigned q = (unsigned)warp & 3u;  // tensor-memory lane quarter of this warp
     const float* Ghg = (const float*)(v.arena + tc.Gf);
     const float* Glg = Ghg + (size_t)K * ld;
@@ -227,12 +229,14 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
         for (int c = tid; c < ldm; c += CL_THREADS) {
             ybuf[c] = c < K ? ds_split(c0[c]) : make_float2(0.f, 0.f);
             ybuf[ldm + c] = make_float2(0.f, 0.f);
-            vf[c] = make_float2(0.f, 0.f);
         }
         for (int i = tid; i < nr; i += CL_THREADS) h0[r0 + i] = c0[r0 + i];
     }
-    const float2 kdt2 = ds_split(tc.kdt);
     const int wp = A.win_prev[tc.inst];
+    // w^n = kappa dt G b'^n of the previous iteration's Robin data, rows of ldw
+    const float2* Wg = reinterpret_cast<const float2*>(v.arena + v.sub[tc.sid].Wr);
+    const int ldw = df32_ld(K);
+    const int wi = tid - 32;  // threads 32.. carry the own rows of w^{n+1} through the step
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     cl_sync();  // every CTA of the cluster initialised before the first remote store
@@ -242,6 +246,14 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
         const float2* yn = ybuf + (size_t)(n & 1) * ldm;
         float2* yo_n = yown + (size_t)(n % 3) * nrm;
         float2* zo_n = zown + (size_t)(n % 3) * nrm;
+        // own row of w^{n+1} (held beyond the previous window at its last step),
+        // loaded now and used after the product
+        float2 wreg = make_float2(0.f, 0.f);
+        if (wp > 0 && wi >= 0 && wi < nr) {
+            const unsigned long long u =
+                __ldcg(reinterpret_cast<const unsigned long long*>(Wg + (long long)min(n + 1, wp) * ldw + r0 + wi));
+            wreg = make_float2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
+        }
         // ---- phase A: own rows of y^n and z^n = (Pp (x) Pp) y^n (double-single,
         //      warps 0..14: tmp[bb][c] = sum_e Y[c][e] P2[b0+bb][e] with 4 threads
         //      per entry, z[(a, b)] = sum_c P1[a][c] tmp[b-b0][c] with 8 per row);
@@ -337,6 +349,78 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
             cl_st_relaxed(my + 2, cl_tagged(d.x, tag));
             cl_st_relaxed(my + 3, cl_tagged(d.y, tag));
         }
+        // ---- own rows of u = G y^n (s_n is not needed yet): each thread its
+        //      rpl rows over its warp's column segment (y^n broadcast from
+        //      shared memory), chunks of 4 columns, the next chunk's
+        //      tensor-memory loads in flight while the current one is used
+        {
+            const int cb = warp * sw, tlo = (warp >> 2) * ne, thi = 4 * ne + (warp >> 2) * ht;
+            float ah[RPL], al[RPL];
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) ah[k] = al[k] = 0.f;
+            // two statically named register buffers (a runtime buffer index
+            // would put them in local memory)
+            unsigned loA[RPL][4], thA[RPL][4], loB[RPL][4], thB[RPL][4];
+            auto issue = [&](int j0, unsigned (&lo)[RPL][4], unsigned (&th)[RPL][4]) {
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    if (k < rpl) {
+                        const int e = k * sw + j0;
+                        if (!ONEP) cl_tld4(tmem, q, tlo + e, lo[k]);
+                        if (e >= hs) cl_tld4(tmem, q, thi + (e - hs), th[k]);
+                    }
+                }
+            };
+            // a second accumulator set for the odd chunks: two independent
+            // chains per row
+            float bh[RPL], bl[RPL];
+#pragma unroll
+            for (int k = 0; k < RPL; ++k) bh[k] = bl[k] = 0.f;
+            auto use = [&](int j0, const unsigned (&lo)[RPL][4], const unsigned (&th)[RPL][4], float (&ah)[RPL],
+                           float (&al)[RPL]) {
+                const float4 va = *reinterpret_cast<const float4*>(yn + cb + j0);
+                const float4 vb = *reinterpret_cast<const float4*>(yn + cb + j0 + 2);
+#pragma unroll
+                for (int k = 0; k < RPL; ++k) {
+                    if (k < rpl) {
+                        const int e = k * sw + j0;
+                        float4 g;
+                        if (e < hs)
+                            g = *reinterpret_cast<const float4*>(
+                                Gsm + (((size_t)warp * (hsm >> 2) + (e >> 2)) * 32 + lane) * 4);
+                        else
+                            g = make_float4(__uint_as_float(th[k][0]), __uint_as_float(th[k][1]),
+                                            __uint_as_float(th[k][2]), __uint_as_float(th[k][3]));
+                        const float l0 = ONEP ? 0.f : __uint_as_float(lo[k][0]);
+                        const float l1 = ONEP ? 0.f : __uint_as_float(lo[k][1]);
+                        const float l2 = ONEP ? 0.f : __uint_as_float(lo[k][2]);
+                        const float l3 = ONEP ? 0.f : __uint_as_float(lo[k][3]);
+                        ds_fma(ah[k], al[k], make_float2(g.x, l0), make_float2(va.x, va.y));
+                        ds_fma(ah[k], al[k], make_float2(g.y, l1), make_float2(va.z, va.w));
+                        ds_fma(ah[k], al[k], make_float2(g.z, l2), make_float2(vb.x, vb.y));
+                        ds_fma(ah[k], al[k], make_float2(g.w, l3), make_float2(vb.z, vb.w));
+                    }
+                }
+            };
+            issue(0, loA, thA);
+            for (int j0 = 0; j0 < sw; j0 += 8) {
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (j0 + 4 < sw) issue(j0 + 4, loB, thB);
+                use(j0, loA, thA, ah, al);
+                if (j0 + 4 < sw) {
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (j0 + 8 < sw) issue(j0 + 8, loA, thA);
+                    use(j0 + 4, loB, thB, bh, bl);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RPL; ++k)
+                if (k < rpl)
+                    segp[((size_t)k * CL_WARPS + warp) * 32 + lane] =
+                        dsp_add(make_float2(ah[k], al[k]), make_float2(bh[k], bl[k]));
+        }
+        if (wi >= 0 && wi < nr) wown[wi] = wreg;
+        __syncthreads();
         if (warp == 0) {
             // ---- the instance's partials: every word tagged with this step (bounded
             //      polls per slot), summed in slot order, the same bits in every CTA
@@ -421,99 +505,17 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
                 }
                 s_stop = stop;
             }
-        } else {
-            // ---- meanwhile: kappa dt b'^{n+1} into v (integer-pipe split), history row n
-            if (wp > 0) {
-                const double* bsrc = v.arena + tc.bvec + (long long)min(n + 1, wp) * K;
-                for (int c = tid - 32; c < K; c += CL_THREADS - 32) vf[c] = dsp_mul(dsp_split_int(bsrc[c]), kdt2);
-            } else {
-                for (int c = tid - 32; c < K; c += CL_THREADS - 32) vf[c] = make_float2(0.f, 0.f);
-            }
-            if (n >= 1) {
-                double* hrow = v.arena + tc.hist + (long long)n * K;
-                for (int i = tid - 32; i < nr; i += CL_THREADS - 32) hrow[r0 + i] = dsp_to_double(yo_n[i]);
-            }
+        } else if (n >= 1) {
+            // ---- meanwhile: history row n
+            double* hrow = v.arena + tc.hist + (long long)n * K;
+            for (int i = tid - 32; i < nr; i += CL_THREADS - 32) hrow[r0 + i] = dsp_to_double(yo_n[i]);
         }
         __syncthreads();
         if (!s_stop) {
             if (tc.first && tid == CL_THREADS - 1) A.snorm[(long long)tc.inst * (A.cap + 1) + n] = dsp_to_double(s_sn);
-            // ---- v = y^n / s_n + kappa dt b'^{n+1}
             const float2 isf = s_is[0];
-            for (int c = tid; c < K; c += CL_THREADS) vf[c] = dsp_add(dsp_mul(yn[c], isf), vf[c]);
-            __syncthreads();
-            // ---- own rows of y^{n+1} = G v: each thread its rpl rows over its
-            //      warp's column segment (v broadcast from shared memory), chunks
-            //      of 4 columns, the next chunk's tensor-memory loads in flight
-            //      while the current one is used
-            {
-                const int cb = warp * sw, tlo = (warp >> 2) * ne, thi = 4 * ne + (warp >> 2) * ht;
-                float ah[RPL], al[RPL];
-#pragma unroll
-                for (int k = 0; k < RPL; ++k) ah[k] = al[k] = 0.f;
-                // two statically named register buffers (a runtime buffer index
-                // would put them in local memory)
-                unsigned loA[RPL][4], thA[RPL][4], loB[RPL][4], thB[RPL][4];
-                auto issue = [&](int j0, unsigned (&lo)[RPL][4], unsigned (&th)[RPL][4]) {
-#pragma unroll
-                    for (int k = 0; k < RPL; ++k) {
-                        if (k < rpl) {
-                            const int e = k * sw + j0;
-                            if (!ONEP) cl_tld4(tmem, q, tlo + e, lo[k]);
-                            if (e >= hs) cl_tld4(tmem, q, thi + (e - hs), th[k]);
-                        }
-                    }
-                };
-                // a second accumulator set for the odd chunks: two independent
-                // chains per row
-                float bh[RPL], bl[RPL];
-#pragma unroll
-                for (int k = 0; k < RPL; ++k) bh[k] = bl[k] = 0.f;
-                auto use = [&](int j0, const unsigned (&lo)[RPL][4], const unsigned (&th)[RPL][4], float (&ah)[RPL],
-                               float (&al)[RPL]) {
-                    const float4 va = *reinterpret_cast<const float4*>(vf + cb + j0);
-                    const float4 vb = *reinterpret_cast<const float4*>(vf + cb + j0 + 2);
-#pragma unroll
-                    for (int k = 0; k < RPL; ++k) {
-                        if (k < rpl) {
-                            const int e = k * sw + j0;
-                            float4 g;
-                            if (e < hs)
-                                g = *reinterpret_cast<const float4*>(
-                                    Gsm + (((size_t)warp * (hsm >> 2) + (e >> 2)) * 32 + lane) * 4);
-                            else
-                                g = make_float4(__uint_as_float(th[k][0]), __uint_as_float(th[k][1]),
-                                                __uint_as_float(th[k][2]), __uint_as_float(th[k][3]));
-                            const float l0 = ONEP ? 0.f : __uint_as_float(lo[k][0]);
-                            const float l1 = ONEP ? 0.f : __uint_as_float(lo[k][1]);
-                            const float l2 = ONEP ? 0.f : __uint_as_float(lo[k][2]);
-                            const float l3 = ONEP ? 0.f : __uint_as_float(lo[k][3]);
-                            ds_fma(ah[k], al[k], make_float2(g.x, l0), make_float2(va.x, va.y));
-                            ds_fma(ah[k], al[k], make_float2(g.y, l1), make_float2(va.z, va.w));
-                            ds_fma(ah[k], al[k], make_float2(g.z, l2), make_float2(vb.x, vb.y));
-                            ds_fma(ah[k], al[k], make_float2(g.w, l3), make_float2(vb.z, vb.w));
-                        }
-                    }
-                };
-                issue(0, loA, thA);
-                for (int j0 = 0; j0 < sw; j0 += 8) {
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (j0 + 4 < sw) issue(j0 + 4, loB, thB);
-                    use(j0, loA, thA, ah, al);
-                    if (j0 + 4 < sw) {
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (j0 + 8 < sw) issue(j0 + 8, loA, thA);
-                        use(j0 + 4, loB, thB, bh, bl);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < RPL; ++k)
-                    if (k < rpl)
-                        segp[((size_t)k * CL_WARPS + warp) * 32 + lane] =
-                            dsp_add(make_float2(ah[k], al[k]), make_float2(bh[k], bl[k]));
-            }
-            __syncthreads();
             // ---- row sums over the 16 segments (4 threads per row, fixed order),
-            //      y^{n+1} rows into every CTA of the cluster
+            //      y^{n+1} = u / s_n + w^{n+1} into every CTA of the cluster
             {
                 float2* ynext = ybuf + (size_t)((n + 1) & 1) * ldm;
                 for (int base = 0; base < 4 * nr; base += CL_THREADS) {
@@ -526,8 +528,10 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_window_cluster(SweepArgs A) {
                     }
                     y = dsp_shfl_add(y, 1);
                     y = dsp_shfl_add(y, 2);
-                    if (i < nr && p == 0)
+                    if (i < nr && p == 0) {
+                        y = dsp_add(dsp_mul(y, isf), wown[i]);
                         for (unsigned r = 0; r < CS; ++r) cl_store2(ynext + r0 + i, r, y.x, y.y);
+                    }
                 }
             }
         } else {

@@ -60,6 +60,9 @@ struct SubDev {
     long long work;               // scratch for assembly (see swr_assemble.cu)
     long long Gf;                 // mixed precision: G as FP32 pairs (G_hi [K*K] then G_lo [K*K])
     long long Wf;                 // mixed precision: W = (Pp (x) Pp) G as FP32 pairs
+    long long GE;                 // Robin response (swr_robin.cu): G times the edge-load columns, K x J pairs
+    long long Hr;                 // Robin response: (cap+1) x J tangential sums of b' per step (pairs)
+    long long Wr;                 // Robin response: (cap+1) x df32_ld(K) pairs, w^n = kappa dt G b'^n
     int nline;                    // values per step in `line`
 };
 
@@ -357,6 +360,11 @@ int cluster_hi_smem(int kmax, int kdmax, int rows_max);
 int cluster_tmem_cols(int kmax, int rows_max, int hs);
 cudaError_t cluster_occupancy(int* clusters, int rows_max, size_t smem, int cs, int grid);
 cudaError_t launch_cluster_window(SweepArgs& a, int grid, int cs, size_t smem, cudaStream_t st, bool onep);
+// Robin response w^n = kappa dt G b'^n (swr_robin.cu): columns of GE per
+// subdomain, GE at assembly, H and W before each cluster window.
+int robin_columns(const SubDev& s);
+cudaError_t launch_robin_ge(const SwrDeviceView& v, cudaStream_t st, int max_K, int max_J);
+cudaError_t launch_robin_w(const SwrDeviceView& v, cudaStream_t st, const int* d_win_prev, int max_K, int nsm);
 void set_error(swr_ctx* c, const char* msg);
 void set_setup_error(const char* msg);
 // Blocks per subdomain of the energy kernel (partials [n_sub][ENERGY_BLOCKS][3]).

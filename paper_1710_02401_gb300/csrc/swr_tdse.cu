@@ -34,7 +34,10 @@ __device__ inline double field_e(const InstDev& in, double t) {
     return in.E0 * s * s * sin(in.omega * t + in.phase);
 }
 
-// (Q' x)[r] for rows r of one subdomain, x planar channel in shared memory.
+// (Q' x)[r] for rows r of one subdomain, x planar channel in shared memory:
+// FP64 for the plain FP64 path; for the mixed path factors and x as
+// double-single pairs (the products on the FP32 pipes: this part's FP64 unit
+// spends tens of microseconds per launch on them).
 __device__ inline double qx_row(const SubDev& s, const double* Xp1, const double* Xp2, const double* x, int r) {
     const int kd = s.kd;
     if (s.N == 1) {
@@ -47,6 +50,18 @@ __device__ inline double qx_row(const SubDev& s, const double* Xp1, const double
     for (int c = 0; c < kd; ++c) acc += Xp1[a * kd + c] * x[c + kd * b];
     for (int e = 0; e < kd; ++e) acc += Xp2[b * kd + e] * x[a + kd * e];
     return acc;
+}
+__device__ inline double qx_row(const SubDev& s, const float2* Xp1, const float2* Xp2, const float2* x, int r) {
+    const int kd = s.kd;
+    float h = 0.f, l = 0.f;
+    if (s.N == 1) {
+        for (int c = 0; c < kd; ++c) ds_fma(h, l, Xp1[r * kd + c], x[c]);
+        return dsp_to_double(dsp_norm(h, l));
+    }
+    const int a = r % kd, b = r / kd;
+    for (int c = 0; c < kd; ++c) ds_fma(h, l, Xp1[a * kd + c], x[c + kd * b]);
+    for (int e = 0; e < kd; ++e) ds_fma(h, l, Xp2[b * kd + e], x[a + kd * e]);
+    return dsp_to_double(dsp_norm(h, l));
 }
 
 // Antisymmetric states: the lower subdomain (i1 > i2) of a mirror pair is not
@@ -61,7 +76,16 @@ struct CnBufs {
     long long r, u, x;   // per-subdomain planar vectors (offsets in doubles, 2K each)
 };
 
+// Shared-memory element of the element-wise kernels: FP64, or a double-single
+// pair on the mixed path.
+template <bool DS> struct CnElem { typedef double T; };
+template <> struct CnElem<true> { typedef float2 T; };
+template <bool DS> __device__ inline typename CnElem<DS>::T cn_elem(double x);
+template <> __device__ inline double cn_elem<false>(double x) { return x; }
+template <> __device__ inline float2 cn_elem<true>(double x) { return dsp_split_int(x); }
+
 // r = 2c^n + i dth Q' c^n + i hk (b^{n+1} + b^n);  u = r
+template <bool DS>
 __global__ void k_cn_rhs(SwrDeviceView v, const long long* boff, const int* win_prev, int n) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
@@ -69,18 +93,19 @@ __global__ void k_cn_rhs(SwrDeviceView v, const long long* boff, const int* win_
     const int K = s.K, kd = s.kd;
     const int r0 = blockIdx.x * CN_ROWS;
     if (r0 >= K || cn_mirror_skip(v, s)) return;
-    extern __shared__ double sm[];
-    double* c = sm;               // 2K
-    double* X1 = sm + 2 * K;      // kd^2
-    double* X2 = X1 + kd * kd;    // kd^2
+    typedef typename CnElem<DS>::T E;
+    extern __shared__ double sm_raw[];
+    E* c = reinterpret_cast<E*>(sm_raw);  // 2K
+    E* X1 = c + 2 * K;                     // kd^2
+    E* X2 = X1 + kd * kd;                  // kd^2
     T1Layout lay(s.q, kd);
     const double* cn = v.arena + s.hist + (long long)n * 2 * K;
-    for (int e = threadIdx.x; e < 2 * K; e += CN_THREADS) c[e] = cn[e];
+    for (int e = threadIdx.x; e < 2 * K; e += CN_THREADS) c[e] = cn_elem<DS>(cn[e]);
     const double* X1g = v.arena + s.t1[0] + lay.mat(M_XP);
     const double* X2g = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_XP);
     for (int e = threadIdx.x; e < kd * kd; e += CN_THREADS) {
-        X1[e] = X1g[e];
-        X2[e] = X2g[e];
+        X1[e] = cn_elem<DS>(X1g[e]);
+        X2[e] = cn_elem<DS>(X2g[e]);
     }
     __syncthreads();
     const double th0 = 0.5 * in.dt * field_e(in, n * in.dt), th1 = 0.5 * in.dt * field_e(in, (n + 1) * in.dt);
@@ -97,8 +122,8 @@ __global__ void k_cn_rhs(SwrDeviceView v, const long long* boff, const int* win_
             bre = b1[r] + b0[r];
             bim = b1[K + r] + b0[K + r];
         }
-        const double rre = 2.0 * c[r] - dth * qim - hk * bim;
-        const double rim = 2.0 * c[K + r] + dth * qre + hk * bre;
+        const double rre = 2.0 * cn[r] - dth * qim - hk * bim;
+        const double rim = 2.0 * cn[K + r] + dth * qre + hk * bre;
         R[r] = rre;
         R[K + r] = rim;
         U[r] = rre;
@@ -143,6 +168,7 @@ __global__ void __launch_bounds__(256) k_cmv(SwrDeviceView v, const long long* b
 
 // u = r - i theta_{n+1} Q' x  (fixed-point iteration m; the subdomains that
 // need no more than m iterations at this step are skipped)
+template <bool DS>
 __global__ void k_cn_update(SwrDeviceView v, const long long* boff, int n, const unsigned char* need, int m) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
@@ -150,18 +176,19 @@ __global__ void k_cn_update(SwrDeviceView v, const long long* boff, int n, const
     const int K = s.K, kd = s.kd;
     const int r0 = blockIdx.x * CN_ROWS;
     if (r0 >= K || m >= need[sid] || cn_mirror_skip(v, s)) return;
-    extern __shared__ double sm[];
-    double* x = sm;
-    double* X1 = sm + 2 * K;
-    double* X2 = X1 + kd * kd;
+    typedef typename CnElem<DS>::T E;
+    extern __shared__ double sm_raw[];
+    E* x = reinterpret_cast<E*>(sm_raw);
+    E* X1 = x + 2 * K;
+    E* X2 = X1 + kd * kd;
     T1Layout lay(s.q, kd);
     const double* Xg = v.arena + boff[3 * sid + 2];
-    for (int e = threadIdx.x; e < 2 * K; e += CN_THREADS) x[e] = Xg[e];
+    for (int e = threadIdx.x; e < 2 * K; e += CN_THREADS) x[e] = cn_elem<DS>(Xg[e]);
     const double* X1g = v.arena + s.t1[0] + lay.mat(M_XP);
     const double* X2g = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_XP);
     for (int e = threadIdx.x; e < kd * kd; e += CN_THREADS) {
-        X1[e] = X1g[e];
-        X2[e] = X2g[e];
+        X1[e] = cn_elem<DS>(X1g[e]);
+        X2[e] = cn_elem<DS>(X2g[e]);
     }
     __syncthreads();
     const double th1 = 0.5 * in.dt * field_e(in, (n + 1) * in.dt);
@@ -340,8 +367,10 @@ cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const lo
     const size_t sm_mv = 2 * (size_t)df32_ld(max_K) * sizeof(double);
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_cn_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        cudaFuncSetAttribute(k_cn_update, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_cn_rhs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_cn_rhs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_cn_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_cn_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         cudaFuncSetAttribute(k_cmv, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         cudaFuncSetAttribute(k_cmv_df32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         cudaFuncSetAttribute(k_cmv_df32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -355,12 +384,14 @@ cudaError_t launch_tdse_window(const SwrDeviceView& v, cudaStream_t st, const lo
         const unsigned char* nd = d_need + (size_t)n * v.n_sub;
         int iters = 0;
         for (int s = 0; s < v.n_sub; ++s) iters = h_need[(size_t)n * v.n_sub + s] > iters ? h_need[(size_t)n * v.n_sub + s] : iters;
-        k_cn_rhs<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, d_win_prev, n);
+        if (df32) k_cn_rhs<true><<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, d_win_prev, n);
+        else k_cn_rhs<false><<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, d_win_prev, n);
         if (df32 && onep) k_cmv_df32<true><<<gm, 256, sm_mv, st>>>(v, d_boff, nullptr, 0);
         else if (df32) k_cmv_df32<false><<<gm, 256, sm_mv, st>>>(v, d_boff, nullptr, 0);
         else k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff, nullptr, 0);
         for (int m = 0; m < iters; ++m) {
-            k_cn_update<<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, n, nd, m);
+            if (df32) k_cn_update<true><<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, n, nd, m);
+            else k_cn_update<false><<<ge, CN_THREADS, sm_el, st>>>(v, d_boff, n, nd, m);
             if (df32 && onep) k_cmv_df32<true><<<gm, 256, sm_mv, st>>>(v, d_boff, nd, m);
             else if (df32) k_cmv_df32<false><<<gm, 256, sm_mv, st>>>(v, d_boff, nd, m);
             else k_cmv<<<gm, 256, sm_mv, st>>>(v, d_boff, nd, m);

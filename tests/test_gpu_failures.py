@@ -2,7 +2,8 @@
 
 * SWR_ETIMEOUT: the device-side waits of the window kernels are bounded by a
   per-problem poll limit; a limit of one poll makes the grid barriers of a
-  normal window give up.  Every CTA returns (the limit bounds each wait, and
+  normal window give up (the cluster window on a problem whose subdomains
+  differ in size, where some CTAs wait at every step).  Every CTA returns (the limit bounds each wait, and
   a CTA that finds the error flag set stops waiting), the host reads the
   status, and the context stays usable: with the default limit restored and
   the checkpoint of the previous iteration put back, the next step
@@ -49,10 +50,21 @@ def _bvec_offset(s, inst, sub):
     return off + 8 * cap1 * max(int(counts[sub][1]), 1) * nch
 
 
+def _uneven_cluster_instance():
+    """Four subdomains, one of them with a 4 x 4 basis against 16 x 16 for
+    the others.  The cluster window forms G y^n before it waits for the
+    partials of s_n, so with even subdomains every partial is usually there
+    at the first poll; here the small subdomain's CTAs reach the poll far
+    ahead of the others' partials at every step."""
+    base = P.small_tise_2d(L=2, q_p=8, n_mid=3)
+    kds = [16, 16, 16, 4]
+    return base.replace(K_d=kds, delta=[P.spacing_rule_delta(base.box, 2, base.overlap, k) for k in kds])
+
+
 @pytest.mark.parametrize("precision,variant", [(0, 1), (1, 2), (1, 5)], ids=["fp64-two-phase", "mixed-fused",
                                                                             "mixed-cluster"])
 def test_barrier_timeout_is_reported_and_the_context_recovers(S, precision, variant):
-    inst = P.small_tise_2d()
+    inst = _uneven_cluster_instance() if variant == 5 else P.small_tise_2d()
     ref = S.SWR(inst, precision=precision, window_variant=variant)
     ref.assemble()
     ref.step()
