@@ -60,7 +60,7 @@ KERNEL_FUNCS["k_window_split"] = ["mbar_wait", "split_stage_rows", "reduce_barri
                                   "df32_acc", "k_window_split"]
 KERNEL_FUNCS["k_window_2ph<true>@batched"] = KERNEL_FUNCS["k_window_2ph<true>"]
 KERNEL_FUNCS["k_window_split@batched"] = KERNEL_FUNCS["k_window_split"]
-KERNEL_FUNCS["k_window_cluster"] = ["ds_split_int", "cl_rsqrt", "k_window_cluster"]
+KERNEL_FUNCS["k_window_cluster"] = ["cl_rsqrt", "k_window_cluster"]
 PROFILED_TRAFFIC = {
     "k_window_fused": ("123b4a784de2ee96", 329.5e6, "profiles/k_window_fused_tise_2e_16sd.md"),
     "k_window_2ph<false>": ("6fd9a352bcfedf25", 279.0e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
@@ -68,7 +68,7 @@ PROFILED_TRAFFIC = {
     "k_window_split@batched": ("b4d0cff880fcc2ac", 1.033, "profiles/k_window_split_batched_uneven.md"),
     # the captured launch is a 1723-step window; the traffic is the history rows and
     # Robin sources, proportional to the window length like the algorithmic bytes
-    "k_window_cluster": ("1747f3752e76cc83", 259.97e6, "profiles/k_window_cluster_tise_2e_16sd.md"),
+    "k_window_cluster": ("01d810867459c710", 259.04e6, "profiles/k_window_cluster_tise_2e_16sd.md"),
 }
 
 

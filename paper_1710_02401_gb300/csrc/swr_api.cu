@@ -1097,7 +1097,7 @@ extern "C" swr_status swr_assemble(swr_ctx* c) {
                        c->d_jobs1, c->d_jobs2, c->d_norm_part, c->tg));
     if (c->df32 && !c->tdse) CU(launch_split_df32(view(c), c->stream, c->max_K, c->has_w));
     if (c->df32 && c->tdse) CU(launch_split_c_df32(view(c), c->stream, c->max_K));
-    if (c->robin_w && c->max_J > 0) CU(launch_robin_ge(view(c), c->stream, c->max_K, c->max_J));
+    if (c->robin_w) CU(launch_robin_ge(view(c), c->stream, c->max_K, c->max_J));
     CU(cudaEventRecord(c->ev1, c->stream));
     swr_status st = check_err(c);
     if (st != SWR_OK) return st;
@@ -1181,7 +1181,11 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
     } else {
         SweepArgs a = sweep_args(c);
         // the cluster window takes the Robin response of every step from memory
-        if (c->variant == WIN_CLUSTER) e = launch_robin_w(view(c), st, c->d_win_prev, c->max_K, c->nsm > 0 ? c->nsm : 152);
+        if (c->variant == WIN_CLUSTER) {
+            int kd2 = 0;
+            for (const SubDev& sd : c->sub) kd2 = (sd.N == 2 && sd.kd > kd2) ? sd.kd : kd2;
+            e = launch_robin_w(view(c), st, c->d_win_prev, kd2, c->nsm > 0 ? c->nsm : 152);
+        }
         if (e == cudaSuccess)
             e = launch_window(a, c->grid, c->win_smem, st, (int)c->inst.size(), c->variant, c->df32, fp32_phase(c),
                               c->evw0, c->evw1);

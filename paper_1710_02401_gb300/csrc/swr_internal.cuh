@@ -364,7 +364,7 @@ cudaError_t launch_cluster_window(SweepArgs& a, int grid, int cs, size_t smem, c
 // subdomain, GE at assembly, H and W before each cluster window.
 int robin_columns(const SubDev& s);
 cudaError_t launch_robin_ge(const SwrDeviceView& v, cudaStream_t st, int max_K, int max_J);
-cudaError_t launch_robin_w(const SwrDeviceView& v, cudaStream_t st, const int* d_win_prev, int max_K, int nsm);
+cudaError_t launch_robin_w(const SwrDeviceView& v, cudaStream_t st, const int* d_win_prev, int kd2, int nsm);
 void set_error(swr_ctx* c, const char* msg);
 void set_setup_error(const char* msg);
 // Blocks per subdomain of the energy kernel (partials [n_sub][ENERGY_BLOCKS][3]).

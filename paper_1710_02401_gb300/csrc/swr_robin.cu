@@ -111,112 +111,139 @@ __device__ inline void gram_inverse(const double* const* vec, int n, int kd, dou
 }
 
 // H[n] (pairs, J per step) from the stored b'^n, n = 0..n_prev, by the
-// gauge-fixed decomposition above.  Steps strided over blockIdx.x.
-__global__ void __launch_bounds__(RB_THREADS) k_robin_h(SwrDeviceView v, const int* win_prev) {
+// gauge-fixed decomposition above, in double-single on the FP32 pipes (this
+// part's FP64 unit would make it as long as the product that follows).  One
+// warp per step, steps strided over the warps of the grid; the per-subdomain
+// constants (edge vectors, inverse Gram matrices) are staged once per CTA.
+// Dynamic shared memory: per warp the step's b' as a kd x kd matrix with
+// column stride kd + 1 (conflict-free column walks).
+#define RH_MAXKD 64
+__global__ void k_robin_h(SwrDeviceView v, const int* win_prev) {
     const SubDev& s = v.sub[blockIdx.y];
     const int wp = win_prev[s.inst];
     const int K = s.K, kd = s.kd, J = robin_cols(s);
-    if (wp <= 0 || J == 0 || (int)blockIdx.x > wp) return;
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wp <= 0 || J == 0 || (int)blockIdx.x * nw > wp) return;
     int blk[4];
     robin_slots(s, blk);
-    __shared__ const double* U[2];
-    __shared__ const double* V[2];
+    __shared__ float2 U2[2][RH_MAXKD], V2[2][RH_MAXKD];
+    __shared__ float2 GUi2[4], GVi2[4];
     __shared__ int slU[2], slV[2], p, q;
-    __shared__ double GUi[4], GVi[4];
-    __shared__ double Ys[64][2], UY[2][2];
-    __shared__ double Qs[2][64];
-    extern __shared__ double Bm[];  // K
+    __shared__ float2 Ysw[8][RH_MAXKD][2], Qsw[8][2][RH_MAXKD], UYw[8][4];
+    extern __shared__ float2 Bw[];  // [nw][kd (kd + 1)] (two electrons)
     if (threadIdx.x == 0) {
-        p = q = 0;
+        const double* U[2] = {nullptr, nullptr};
+        const double* V[2] = {nullptr, nullptr};
+        int pp = 0, qq = 0;
         for (int sl = 0; sl < 4; ++sl) {
             if (blk[sl] < 0) continue;
             if (sl < 2) {
-                slU[p] = sl;
-                U[p++] = robin_edge(v, s, sl);
+                slU[pp] = sl;
+                U[pp++] = robin_edge(v, s, sl);
             } else {
-                slV[q] = sl;
-                V[q++] = robin_edge(v, s, sl);
+                slV[qq] = sl;
+                V[qq++] = robin_edge(v, s, sl);
             }
         }
-        gram_inverse(U, p, kd, GUi);
-        gram_inverse(V, q, kd, GVi);
+        double gu[4] = {0, 0, 0, 0}, gv[4] = {0, 0, 0, 0};
+        gram_inverse(U, pp, kd, gu);
+        gram_inverse(V, qq, kd, gv);
+        for (int i = 0; i < 4; ++i) {
+            GUi2[i] = dsp_split_int(gu[i]);
+            GVi2[i] = dsp_split_int(gv[i]);
+        }
+        p = pp;
+        q = qq;
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < 2 * kd; e += blockDim.x) {
+        const int i = e / kd, a = e - i * kd;
+        if (i < p) U2[i][a] = dsp_split_int(robin_edge(v, s, slU[i])[a]);
+        if (i < q) V2[i][a] = dsp_split_int(robin_edge(v, s, slV[i])[a]);
+    }
+    __syncthreads();
+    const int ldb = kd + 1;
+    float2* Bm = Bw + (size_t)warp * kd * ldb;
+    float2 (*Ys)[2] = Ysw[warp];
+    float2 (*Qs)[RH_MAXKD] = Qsw[warp];
+    float2* UY = UYw[warp];
     float2* H = reinterpret_cast<float2*>(v.arena + s.Hr);
-    for (int n = blockIdx.x; n <= wp; n += gridDim.x) {
+    for (int n = blockIdx.x * nw + warp; n <= wp; n += gridDim.x * nw) {
         const double* b = v.arena + s.bvec + (long long)n * K;
         float2* h = H + (long long)n * J;
         if (s.N == 1) {
             // h = (U^T U)^{-1} U^T b'
-            if (threadIdx.x < 32) {
-                double t[2] = {0, 0};
-                for (int i = 0; i < p; ++i) {
-                    double acc = 0;
-                    for (int a = threadIdx.x; a < kd; a += 32) acc = fma(U[i][a], b[a], acc);
-                    t[i] = warp_sum(acc);
-                }
-                if (threadIdx.x < p) {
-                    const int i = threadIdx.x;
-                    double x = 0;
-                    for (int k = 0; k < p; ++k) x = fma(GUi[i * p + k], t[k], x);
-                    h[blk[slU[i]]] = dsp_split_int(x);
-                }
+            float2 t[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            for (int i = 0; i < p; ++i) {
+                float th = 0.f, tl = 0.f;
+                for (int a = lane; a < kd; a += 32) ds_fma(th, tl, U2[i][a], dsp_split_int(b[a]));
+                float2 acc = dsp_norm(th, tl);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc = dsp_shfl_add(acc, o);
+                t[i] = acc;
+            }
+            if (lane < p) {
+                float2 x = make_float2(0.f, 0.f);
+                for (int k = 0; k < p; ++k) x = dsp_add(x, dsp_mul(GUi2[lane * p + k], t[k]));
+                h[blk[slU[lane]]] = x;
             }
             continue;
         }
-        for (int e = threadIdx.x; e < K; e += RB_THREADS) Bm[e] = b[e];
-        __syncthreads();
-        // Y = B V (V^T V)^{-1}: B[a][bb] = b'[a + kd bb]
-        for (int it = threadIdx.x; it < kd * q; it += RB_THREADS) {
+        for (int e = lane; e < K; e += 32) {
+            const int bb = e / kd, a = e - bb * kd;
+            Bm[a + ldb * bb] = dsp_split_int(b[e]);
+        }
+        __syncwarp();
+        // (B V)[a][t] and Q = U^T B
+        for (int it = lane; it < kd * q; it += 32) {
             const int a = it / q, t = it - a * q;
-            double acc = 0;
-            for (int bb = 0; bb < kd; ++bb) acc = fma(Bm[a + kd * bb], V[t][bb], acc);
-            Ys[a][t] = acc;  // (B V)[a][t], scaled below
+            float hh = 0.f, ll = 0.f;
+            for (int bb = 0; bb < kd; ++bb) ds_fma(hh, ll, Bm[a + ldb * bb], V2[t][bb]);
+            Ys[a][t] = dsp_norm(hh, ll);
         }
-        // Q = U^T B
-        for (int it = threadIdx.x; it < kd * p; it += RB_THREADS) {
+        for (int it = lane; it < kd * p; it += 32) {
             const int t = it / kd, bb = it - t * kd;
-            double acc = 0;
-            for (int a = 0; a < kd; ++a) acc = fma(U[t][a], Bm[a + kd * bb], acc);
-            Qs[t][bb] = acc;
+            float hh = 0.f, ll = 0.f;
+            for (int a = 0; a < kd; ++a) ds_fma(hh, ll, U2[t][a], Bm[a + ldb * bb]);
+            Qs[t][bb] = dsp_norm(hh, ll);
         }
-        __syncthreads();
-        if (threadIdx.x < kd) {
-            const int a = threadIdx.x;
-            double y[2] = {0, 0};
-            for (int sidx = 0; sidx < q; ++sidx)
-                for (int t = 0; t < q; ++t) y[sidx] = fma(Ys[a][t], GVi[t * q + sidx], y[sidx]);
-            for (int sidx = 0; sidx < q; ++sidx) Ys[a][sidx] = y[sidx];  // row a is this thread's alone
+        __syncwarp();
+        // Y = (B V) (V^T V)^{-1}: every lane its own rows a
+        for (int a = lane; a < kd; a += 32) {
+            float2 y[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            for (int si = 0; si < q; ++si)
+                for (int t = 0; t < q; ++t) y[si] = dsp_add(y[si], dsp_mul(Ys[a][t], GVi2[t * q + si]));
+            for (int si = 0; si < q; ++si) Ys[a][si] = y[si];
         }
-        __syncthreads();
+        __syncwarp();
         // U^T Y (p x q)
-        if (threadIdx.x < p * q) {
-            const int t = threadIdx.x / q, u = threadIdx.x - t * q;
-            double acc = 0;
-            for (int a = 0; a < kd; ++a) acc = fma(U[t][a], Ys[a][u], acc);
-            UY[t][u] = acc;
+        if (lane < p * q) {
+            const int t = lane / q, u = lane - t * q;
+            float hh = 0.f, ll = 0.f;
+            for (int a = 0; a < kd; ++a) ds_fma(hh, ll, U2[t][a], Ys[a][u]);
+            UY[t * 2 + u] = dsp_norm(hh, ll);
         }
-        __syncthreads();
+        __syncwarp();
         // h: X^T = (U^T U)^{-1} (U^T B - (U^T Y) V^T) for coordinate-0 slots, Y for coordinate 1
-        for (int it = threadIdx.x; it < kd * (p + q); it += RB_THREADS) {
-            const int sidx = it / kd, m = it - sidx * kd;
-            double x;
+        for (int it = lane; it < kd * (p + q); it += 32) {
+            const int si = it / kd, m = it - si * kd;
+            float2 x;
             int sl;
-            if (sidx < p) {
-                x = 0;
+            if (si < p) {
+                x = make_float2(0.f, 0.f);
                 for (int t = 0; t < p; ++t) {
-                    double r = Qs[t][m];
-                    for (int u = 0; u < q; ++u) r = fma(-UY[t][u], V[u][m], r);
-                    x = fma(GUi[sidx * p + t], r, x);
+                    float rh = Qs[t][m].x, rl = Qs[t][m].y;
+                    for (int u = 0; u < q; ++u) ds_fma(rh, rl, dsp_neg(UY[t * 2 + u]), V2[u][m]);
+                    x = dsp_add(x, dsp_mul(GUi2[si * p + t], dsp_norm(rh, rl)));
                 }
-                sl = slU[sidx];
+                sl = slU[si];
             } else {
-                x = Ys[m][sidx - p];
-                sl = slV[sidx - p];
+                x = Ys[m][si - p];
+                sl = slV[si - p];
             }
-            h[blk[sl] * kd + m] = dsp_split_int(x);
+            h[blk[sl] * kd + m] = x;
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -239,7 +266,8 @@ __global__ void __launch_bounds__(RB_THREADS) k_robin_w(SwrDeviceView v, const i
             first[sid] = t;
             const SubDev& s = v.sub[sid];
             const int wp = win_prev[s.inst];
-            if (wp > 0 && robin_cols(s) > 0) t += ((s.K + RW_T - 1) / RW_T) * ((wp + RW_T) / RW_T);
+            // subdomains without an interior edge get zeros (no inner products)
+            if (wp > 0) t += ((s.K + RW_T - 1) / RW_T) * ((wp + RW_T) / RW_T);
         }
         first[v.n_sub < RW_MAXSUB ? v.n_sub : RW_MAXSUB] = t;
     }
@@ -310,22 +338,30 @@ __global__ void __launch_bounds__(RB_THREADS) k_robin_w(SwrDeviceView v, const i
 static inline unsigned rb_div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // GE of every subdomain (assembly, after the step-matrix inverse).
+// Also raises the dynamic shared-memory cap of k_robin_h to the most its
+// launches ask for (160 KB beside its static arrays), here at assembly and not
+// inside a captured iteration.
 cudaError_t launch_robin_ge(const SwrDeviceView& v, cudaStream_t st, int max_K, int max_J) {
-    k_robin_ge<<<dim3(rb_div_up((long long)max_K * max_J, RB_THREADS), v.n_sub), RB_THREADS, 0, st>>>(v);
+    cudaError_t e = cudaFuncSetAttribute(k_robin_h, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    if (max_J > 0) k_robin_ge<<<dim3(rb_div_up((long long)max_K * max_J, RB_THREADS), v.n_sub), RB_THREADS, 0, st>>>(v);
     return cudaGetLastError();
 }
 
 // H and W of every subdomain for the coming window (before it is launched);
 // the grids do not depend on the window lengths, which the kernels read on
-// the device (a captured iteration replays them unchanged).
-cudaError_t launch_robin_w(const SwrDeviceView& v, cudaStream_t st, const int* d_win_prev, int max_K, int nsm) {
-    const size_t sm = (size_t)max_K * sizeof(double);
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_robin_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+// the device (a captured iteration replays them unchanged).  kd2: the largest
+// kd of the two-electron subdomains (0 when there are none).
+cudaError_t launch_robin_w(const SwrDeviceView& v, cudaStream_t st, const int* d_win_prev, int kd2, int nsm) {
+    int nw = 8;
+    size_t sm = 0;
+    if (kd2 > 0) {
+        const size_t per_warp = (size_t)kd2 * (kd2 + 1) * sizeof(float2);
+        while (nw > 1 && nw * per_warp > 160 * 1024) --nw;
+        sm = nw * per_warp;
     }
     const int per = (2 * nsm + v.n_sub - 1) / v.n_sub;
-    k_robin_h<<<dim3(per > 0 ? per : 1, v.n_sub), RB_THREADS, sm, st>>>(v, d_win_prev);
+    k_robin_h<<<dim3(per > 0 ? per : 1, v.n_sub), 32 * nw, sm, st>>>(v, d_win_prev);
     k_robin_w<<<4 * nsm, RB_THREADS, 0, st>>>(v, d_win_prev);
     return cudaGetLastError();
 }

@@ -107,8 +107,15 @@ __global__ void k_cn_rhs(SwrDeviceView v, const long long* boff, const int* win_
         X1[e] = cn_elem<DS>(X1g[e]);
         X2[e] = cn_elem<DS>(X2g[e]);
     }
+    // the field at t_n and t_{n+1}: once per CTA (the FP64 sines of every
+    // thread would take most of the launch on this part's FP64 unit)
+    __shared__ double s_th[2];
+    if (threadIdx.x == 0) {
+        s_th[0] = 0.5 * in.dt * field_e(in, n * in.dt);
+        s_th[1] = 0.5 * in.dt * field_e(in, (n + 1) * in.dt);
+    }
     __syncthreads();
-    const double th0 = 0.5 * in.dt * field_e(in, n * in.dt), th1 = 0.5 * in.dt * field_e(in, (n + 1) * in.dt);
+    const double th0 = s_th[0], th1 = s_th[1];
     const double dth = th1 - th0, hk = 0.5 * in.dt * in.kappa;
     const int wp = win_prev[s.inst];
     const double* b1 = (wp > 0) ? v.arena + s.bvec + (long long)min(n + 1, wp) * 2 * K : nullptr;
@@ -190,8 +197,10 @@ __global__ void k_cn_update(SwrDeviceView v, const long long* boff, int n, const
         X1[e] = cn_elem<DS>(X1g[e]);
         X2[e] = cn_elem<DS>(X2g[e]);
     }
+    __shared__ double s_th1;
+    if (threadIdx.x == 0) s_th1 = 0.5 * in.dt * field_e(in, (n + 1) * in.dt);  // once per CTA
     __syncthreads();
-    const double th1 = 0.5 * in.dt * field_e(in, (n + 1) * in.dt);
+    const double th1 = s_th1;
     const double* R = v.arena + boff[3 * sid + 0];
     double* U = v.arena + boff[3 * sid + 1];
     for (int r = r0 + threadIdx.x; r < min(K, r0 + CN_ROWS); r += CN_THREADS) {

@@ -206,6 +206,35 @@ def test_parity_batched_instances_cluster_window(swr_mod):
             assert abs(gres[k][i] - ref.records[k].res) <= REL * rmax
 
 
+def test_parity_cluster_window_with_a_single_subdomain_instance(swr_mod):
+    # a one-subdomain instance has no interior edge (no Robin source, no
+    # columns in the precomputed Robin response): its window must see zeros
+    # where the other instance's clusters see w^n = kappa dt G b'^n
+    S = swr_mod
+    insts = [P.small_tise_2d(L=2, K_d=6, q_p=6, n_mid=2), P.small_tise_2d(L=1, K_d=6, q_p=6, n_mid=2)]
+    s = S.SWR(insts, precision=S.PREC_MIXED, window_variant=S.WINDOW_CLUSTER)
+    s.assemble()
+    assert s.window_plan()["variant"] == S.WINDOW_CLUSTER
+    kmax = 3
+    gres, gE, gwin = [], [], []
+    for _ in range(kmax):
+        s.step()
+        gres.append(s.residual().copy())
+        gE.append(s.energy().copy())
+        gwin.append(s.window().copy())
+    ref = O.run_swr(insts[0], kmax=kmax, tol=0.0)
+    assert [int(w[0]) for w in gwin] == [r.n_win for r in ref.records]
+    rmax = max(r.res for r in ref.records)
+    for k in range(kmax):
+        assert abs(gres[k][0] - ref.records[k].res) <= REL * rmax
+        assert abs(gE[k][0] - ref.records[k].energy) <= REL * abs(ref.records[k].energy)
+    one = O.run_swr(insts[1], kmax=1, tol=0.0).records[0]
+    for k in range(kmax):  # the same single-domain window every iteration
+        assert int(gwin[k][1]) == one.n_win
+        assert abs(gE[k][1] - one.energy) <= REL * abs(one.energy)
+        assert gres[k][1] == 0.0
+
+
 def test_parity_two_electrons_uneven_kd_and_no_ee(swr_mod):
     inst = P.small_tise_2d(L=2, K_d=7, q_p=6, n_mid=2).replace(
         K_d=[7, 9, 8, 6], delta=[1.3, 2.1, 1.7, 1.1], ee_coef=0.0)
