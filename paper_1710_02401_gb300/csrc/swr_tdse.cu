@@ -25,7 +25,7 @@
 namespace swr {
 
 #define CN_THREADS 256
-#define CN_ROWS 64   // rows per CTA of the element-wise kernels
+#define CN_ROWS 256  // rows per CTA of the element-wise kernels (one per thread)
 #define MV_ROWS 32   // rows per CTA of the complex matvec
 
 __device__ inline double field_e(const InstDev& in, double t) {
@@ -34,32 +34,34 @@ __device__ inline double field_e(const InstDev& in, double t) {
     return in.E0 * s * s * sin(in.omega * t + in.phase);
 }
 
-// (Q' x)[r] for rows r of one subdomain, x planar channel in shared memory:
-// FP64 for the plain FP64 path; for the mixed path factors and x as
-// double-single pairs (the products on the FP32 pipes: this part's FP64 unit
-// spends tens of microseconds per launch on them).
-__device__ inline double qx_row(const SubDev& s, const double* Xp1, const double* Xp2, const double* x, int r) {
+// (Q' x)[r] for rows r of one subdomain, x planar channel in shared memory,
+// the first coordinate's factor transposed (X1t[c kd + a] = Xp1[a][c]: the
+// lanes of a warp, consecutive rows, read consecutive words): FP64 for the
+// plain FP64 path; for the mixed path factors and x as double-single pairs
+// (the products on the FP32 pipes: this part's FP64 unit spends tens of
+// microseconds per launch on them).
+__device__ inline double qx_row(const SubDev& s, const double* X1t, const double* Xp2, const double* x, int r) {
     const int kd = s.kd;
     if (s.N == 1) {
         double acc = 0;
-        for (int c = 0; c < kd; ++c) acc += Xp1[r * kd + c] * x[c];
+        for (int c = 0; c < kd; ++c) acc += X1t[c * kd + r] * x[c];
         return acc;
     }
     const int a = r % kd, b = r / kd;
     double acc = 0;
-    for (int c = 0; c < kd; ++c) acc += Xp1[a * kd + c] * x[c + kd * b];
+    for (int c = 0; c < kd; ++c) acc += X1t[c * kd + a] * x[c + kd * b];
     for (int e = 0; e < kd; ++e) acc += Xp2[b * kd + e] * x[a + kd * e];
     return acc;
 }
-__device__ inline double qx_row(const SubDev& s, const float2* Xp1, const float2* Xp2, const float2* x, int r) {
+__device__ inline double qx_row(const SubDev& s, const float2* X1t, const float2* Xp2, const float2* x, int r) {
     const int kd = s.kd;
     float h = 0.f, l = 0.f;
     if (s.N == 1) {
-        for (int c = 0; c < kd; ++c) ds_fma(h, l, Xp1[r * kd + c], x[c]);
+        for (int c = 0; c < kd; ++c) ds_fma(h, l, X1t[c * kd + r], x[c]);
         return dsp_to_double(dsp_norm(h, l));
     }
     const int a = r % kd, b = r / kd;
-    for (int c = 0; c < kd; ++c) ds_fma(h, l, Xp1[a * kd + c], x[c + kd * b]);
+    for (int c = 0; c < kd; ++c) ds_fma(h, l, X1t[c * kd + a], x[c + kd * b]);
     for (int e = 0; e < kd; ++e) ds_fma(h, l, Xp2[b * kd + e], x[a + kd * e]);
     return dsp_to_double(dsp_norm(h, l));
 }
@@ -84,6 +86,25 @@ template <bool DS> __device__ inline typename CnElem<DS>::T cn_elem(double x);
 template <> __device__ inline double cn_elem<false>(double x) { return x; }
 template <> __device__ inline float2 cn_elem<true>(double x) { return dsp_split_int(x); }
 
+// dst[e] (TR: dst[(e % kd) kd + e / kd]) = src[e] for e < n, by the whole
+// CTA: eight loads per thread in flight before the first store.
+template <bool DS, bool TR>
+__device__ inline void cn_stage(typename CnElem<DS>::T* dst, const double* src, int n, int kd) {
+    for (int base = threadIdx.x; base < n; base += 8 * CN_THREADS) {
+        double t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = base + u * CN_THREADS;
+            t[u] = e < n ? src[e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = base + u * CN_THREADS;
+            if (e < n) dst[TR ? (e % kd) * kd + e / kd : e] = cn_elem<DS>(t[u]);
+        }
+    }
+}
+
 // r = 2c^n + i dth Q' c^n + i hk (b^{n+1} + b^n);  u = r
 template <bool DS>
 __global__ void k_cn_rhs(SwrDeviceView v, const long long* boff, const int* win_prev, int n) {
@@ -96,17 +117,13 @@ __global__ void k_cn_rhs(SwrDeviceView v, const long long* boff, const int* win_
     typedef typename CnElem<DS>::T E;
     extern __shared__ double sm_raw[];
     E* c = reinterpret_cast<E*>(sm_raw);  // 2K
-    E* X1 = c + 2 * K;                     // kd^2
+    E* X1 = c + 2 * K;                     // kd^2, transposed
     E* X2 = X1 + kd * kd;                  // kd^2
     T1Layout lay(s.q, kd);
     const double* cn = v.arena + s.hist + (long long)n * 2 * K;
-    for (int e = threadIdx.x; e < 2 * K; e += CN_THREADS) c[e] = cn_elem<DS>(cn[e]);
-    const double* X1g = v.arena + s.t1[0] + lay.mat(M_XP);
-    const double* X2g = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_XP);
-    for (int e = threadIdx.x; e < kd * kd; e += CN_THREADS) {
-        X1[e] = cn_elem<DS>(X1g[e]);
-        X2[e] = cn_elem<DS>(X2g[e]);
-    }
+    cn_stage<DS, false>(c, cn, 2 * K, kd);
+    cn_stage<DS, true>(X1, v.arena + s.t1[0] + lay.mat(M_XP), kd * kd, kd);
+    cn_stage<DS, false>(X2, v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_XP), kd * kd, kd);
     // the field at t_n and t_{n+1}: once per CTA (the FP64 sines of every
     // thread would take most of the launch on this part's FP64 unit)
     __shared__ double s_th[2];
@@ -190,13 +207,9 @@ __global__ void k_cn_update(SwrDeviceView v, const long long* boff, int n, const
     E* X2 = X1 + kd * kd;
     T1Layout lay(s.q, kd);
     const double* Xg = v.arena + boff[3 * sid + 2];
-    for (int e = threadIdx.x; e < 2 * K; e += CN_THREADS) x[e] = cn_elem<DS>(Xg[e]);
-    const double* X1g = v.arena + s.t1[0] + lay.mat(M_XP);
-    const double* X2g = v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_XP);
-    for (int e = threadIdx.x; e < kd * kd; e += CN_THREADS) {
-        X1[e] = cn_elem<DS>(X1g[e]);
-        X2[e] = cn_elem<DS>(X2g[e]);
-    }
+    cn_stage<DS, false>(x, Xg, 2 * K, kd);
+    cn_stage<DS, true>(X1, v.arena + s.t1[0] + lay.mat(M_XP), kd * kd, kd);
+    cn_stage<DS, false>(X2, v.arena + s.t1[s.N == 2 ? 1 : 0] + lay.mat(M_XP), kd * kd, kd);
     __shared__ double s_th1;
     if (threadIdx.x == 0) s_th1 = 0.5 * in.dt * field_e(in, (n + 1) * in.dt);  // once per CTA
     __syncthreads();
