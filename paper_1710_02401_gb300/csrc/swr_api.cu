@@ -57,7 +57,7 @@ cudaError_t launch_split_c_df32(const SwrDeviceView& v, cudaStream_t st, int max
 using namespace swr;
 
 static const int GJ_NB_HOST = 32;     // Gauss-Jordan block (matches swr_assemble.cu)
-static const int RES_BLOCKS = 8;      // residual partial blocks per subdomain
+static const int RES_BLOCKS = 32;     // residual partial blocks per subdomain
 static const double ORTH_TAU_DEFAULT = 1e-12;  // basis reduction threshold when an instance gives 0
 static const long long SPIN_LIMIT = 1LL << 24;  // default polls (x ~64 ns) before a device-side wait gives up
 

@@ -148,18 +148,23 @@ __device__ inline void gamma_slot(const SubDev& s, int node, int& slot, int& nt)
 // shared memory as pairs when they fit (`staged`), each sum split into
 // GATHER_SPLIT chunks added in a fixed order; b' is written in FP64.
 #define GATHER_SPLIT 4
-__global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, int cap, int parity, int staged) {
+__global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, int cap, int parity, int staged,
+                         int gsz) {
     const int sid = blockIdx.y;
     const SubDev& s = v.sub[sid];
     const InstDev& in = v.inst[s.inst];
     const int W = win[s.inst], nch = n_channels(in);
     const int kd = s.kd, q = s.q, K = s.K, L = in.L, qp = in.q_p;
     T1Layout lay(q, kd);
-    __shared__ float2 gs2[2][4 * 384];  // Robin data of the step as pairs (b' sums)
     __shared__ float2 hsum[4][64];
     __shared__ float2 hpart[GATHER_SPLIT][4][64];
     __shared__ float2 lvt[2][2][64];     // Lv rows l = 0, 3 of both coordinates as pairs
-    extern __shared__ float2 wbs[];      // [2][q][kd] (staged)
+    // dynamic: the step's Robin data as pairs for the b' sums [2][gsz] (gsz >= the
+    // interface nodes of any subdomain), then the staged tables [2][q][kd]; sized
+    // to the problem so that several CTAs share an SM
+    extern __shared__ float2 gdyn[];
+    float2* gs2 = gdyn;
+    float2* wbs = gdyn + 2 * gsz;
     if (s.N == 2) {
         if (staged)
             for (int e = threadIdx.x; e < 2 * q * kd; e += blockDim.x) {
@@ -174,8 +179,12 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
         __syncthreads();
     }
     for (int n = blockIdx.x; n <= W; n += gridDim.x) {
-        const double sn = in.normalize ? snorm[(long long)s.inst * (cap + 1) + n] : 1.0;
-        const double isn = 1.0 / sn;  // one division per step, not per node
+        // one FP64 division per step and CTA (per thread it would keep this
+        // part's FP64 unit busy for a good share of the kernel)
+        __shared__ double s_isn;
+        if (threadIdx.x == 0) s_isn = 1.0 / (in.normalize ? snorm[(long long)s.inst * (cap + 1) + n] : 1.0);
+        __syncthreads();
+        const double isn = s_isn;
         for (int node = threadIdx.x; node < s.ngam; node += blockDim.x) {
             int slot, nt;
             gamma_slot(s, node, slot, nt);
@@ -238,7 +247,7 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
                 const double gv = ch ? gim : gre;
                 v.arena[s.u[parity] + ((long long)n * nch + ch) * s.ngam + node] = own[ch] * isn;
                 v.arena[s.g + ((long long)n * nch + ch) * s.ngam + node] = gv;
-                gs2[ch][node] = dsp_split_int(gv);
+                gs2[ch * gsz + node] = dsp_split_int(gv);
             }
         }
         __syncthreads();
@@ -264,7 +273,7 @@ __global__ void k_gather(SwrDeviceView v, const int* win, const double* snorm, i
                     float2 acc = make_float2(0.f, 0.f);
                     if (s.gam_off[sl] >= 0) {
                         const int d = sl / 2, t0 = part * chunk, t1 = min(q, t0 + chunk);
-                        const float2* gv = gs2[ch] + s.gam_off[sl];
+                        const float2* gv = gs2 + ch * gsz + s.gam_off[sl];
                         if (staged) {
                             const float2* wb = wbs + (long long)(1 - d) * q * kd;
                             for (int t = t0; t < t1; ++t) ds_fma(acc.x, acc.y, gv[t], wb[t * kd + m]);
@@ -315,9 +324,11 @@ __global__ void k_residual(SwrDeviceView v, const int* win, const int* win_prev,
     T1Layout lay(q, kd);
     __shared__ double red[33];
     double acc = 0;
-    for (long long e = threadIdx.x + (long long)blockIdx.x * blockDim.x; e < (long long)Nn * s.ngam;
-         e += (long long)blockDim.x * gridDim.x) {
-        int n = 1 + (int)(e / s.ngam), node = (int)(e % s.ngam);
+    // 32-bit indices (Nn * ngam stays far below 2^31: windows of at most a few
+    // thousand steps, at most 4 q interface nodes)
+    const int total = Nn * s.ngam, ng = s.ngam;
+    for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < total; e += blockDim.x * gridDim.x) {
+        const int n = 1 + e / ng, node = e - (n - 1) * ng;
         double w = 1.0;
         if (s.N == 2) {
             int slot, nt;
@@ -609,13 +620,19 @@ cudaError_t launch_post(const SwrDeviceView& v, cudaStream_t st, const int* d_wi
         const int staged = base + tab <= 96 * 1024;
         const size_t sm = base + (staged ? tab : 0);
         if (sm > 48 * 1024) cudaFuncSetAttribute(k_line_traces, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_line_traces, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         k_line_traces<<<dim3(nb, v.n_sub), 256, sm, st>>>(v, d_win, cap, lt_kmax, lt_kdmax, lt_qmax, staged);
     }
     {
+        const int gsz = 4 * lt_qmax;  // interface nodes of a subdomain: at most 4 edges of q
+        const size_t gbytes = 2 * (size_t)gsz * sizeof(float2);
         const size_t tab = 2 * (size_t)lt_qmax * lt_kdmax * sizeof(float2);
         const int staged = tab <= 96 * 1024;
-        if (staged) cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab);
-        k_gather<<<dim3(nb, v.n_sub), 256, staged ? tab : 0, st>>>(v, d_win, d_snorm, cap, parity, staged);
+        const size_t sm = gbytes + (staged ? tab : 0);
+        if (sm > 48 * 1024) cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_gather, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        k_gather<<<dim3(nb, v.n_sub), 256, sm, st>>>(v, d_win, d_snorm, cap, parity, staged, gsz);
     }
     k_residual<<<dim3(res_blocks, v.n_sub), 256, 0, st>>>(v, d_win, d_win_prev, parity, first_iter, d_res_part);
     k_residual_reduce<<<v.n_inst, 256, 0, st>>>(v, d_res_part, res_blocks, d_res);
