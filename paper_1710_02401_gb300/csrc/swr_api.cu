@@ -89,6 +89,7 @@ struct swr_ctx {
     std::vector<unsigned char> cn_need;  // real time: fixed-point iterations [step][subdomain]
     std::vector<double> cn_sweeps;       // real time: matvecs with G0 per subdomain over the whole window
     unsigned char* d_cn_need = nullptr;
+    int* d_rtiles = nullptr;        // Robin response: first product tile of every subdomain
     double* d_dipole = nullptr;
     std::vector<double> dipole_h;
     int nsm = 0, bps = 0, tasks_per_cta = 1, max_rows = 0;
@@ -729,16 +730,14 @@ static void plan(swr_ctx* c) {
                    (c->tasks_per_cta <= window_tasks_per_cta_max() && c->max_rows <= window_rows_per_task_max() &&
                     window_smem(c->max_K, c->max_kd, c->max_rows, c->tasks_per_cta, 0) <= WIN_SMEM_TASKS_MAX);
     }
-    // the Robin response of the cluster window (w^n = kappa dt G b'^n for every
-    // step, swr_robin.cu): where that window can run (mixed precision,
-    // imaginary time, no antisymmetric instance, at most one subdomain per SM)
+    // the Robin response w^n = kappa dt G b'^n of every step (swr_robin.cu),
+    // read by the cluster and split windows: mixed precision, imaginary time,
+    // no antisymmetric instance
     {
-        const int nsm = c->nsm > 0 ? c->nsm : 152;
         bool small_kd = true;
         for (const SubDev& s : c->sub) small_kd = small_kd && (s.N == 1 || s.kd <= 64);
         c->robin_w = c->df32 && !c->tdse && !c->any_anti && small_kd && !c->sub.empty() &&
-                     (int)c->sub.size() <= nsm && nsm <= 160 &&
-                     (p.window_variant == 0 || p.window_variant == WIN_CLUSTER);
+                     (p.window_variant == 0 || p.window_variant == WIN_CLUSTER || p.window_variant == WIN_SPLIT);
     }
     c->max_J = 0;
     for (SubDev& s : c->sub) {
@@ -772,7 +771,7 @@ static void plan(swr_ctx* c) {
 struct AuxPlan {
     size_t inst, sub, err, jobs1, jobs2, norm_part, tasks, task0, part_s, part_d, cta0, tc, scal, alive, own,
         ctal, wfix, snorm, sums_s, sums_d,
-        n_active, win, win_prev, bar, queue, qlist, clslots, cnneed, res_part, res, cv_part, cvtot, epart, energy, norm2, dipole, boff,
+        n_active, win, win_prev, bar, queue, qlist, clslots, cnneed, rtiles, res_part, res, cv_part, cvtot, epart, energy, norm2, dipole, boff,
         psi, psi_off, tg, total;
 };
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -817,6 +816,7 @@ static AuxPlan aux_plan(const swr_ctx* c) {
     a.dipole = o; o = al256(o + ni * sizeof(double));
     a.boff = o; o = al256(o + (c->boff.size() + 1) * sizeof(long long));
     a.cnneed = o; o = al256(o + c->cn_need.size() + 1);
+    a.rtiles = o; o = al256(o + (ns + 1) * sizeof(int));
     a.psi = o; o = al256(o + (size_t)c->psi_total * sizeof(double) * (c->tdse ? 2 : 1));
     a.psi_off = o; o = al256(o + ns * sizeof(long long));
     a.tg = o;
@@ -991,6 +991,7 @@ extern "C" swr_status swr_setup(const swr_problem* p, swr_ctx** out) {
     c->d_dipole = (double*)(b + a.dipole);
     c->d_boff = (long long*)(b + a.boff);
     c->d_cn_need = (unsigned char*)(b + a.cnneed);
+    c->d_rtiles = (int*)(b + a.rtiles);
     c->d_psi = (double*)(b + a.psi);
     c->d_psi_off = (long long*)(b + a.psi_off);
     if (c->use_tg) {
@@ -1158,6 +1159,7 @@ static SweepArgs sweep_args(swr_ctx* c) {
     a.tmem_cols = c->tmem_cols;
     a.cl_size = c->cl_size;
     a.cl_hs = c->cl_hs;
+    a.robin_w = c->robin_w && c->variant == WIN_SPLIT ? 1 : 0;
     return a;
 }
 
@@ -1181,10 +1183,10 @@ static cudaError_t record_iteration(swr_ctx* c, cudaStream_t st, long long* win_
     } else {
         SweepArgs a = sweep_args(c);
         // the cluster window takes the Robin response of every step from memory
-        if (c->variant == WIN_CLUSTER) {
+        if (c->robin_w && (c->variant == WIN_CLUSTER || c->variant == WIN_SPLIT)) {
             int kd2 = 0;
             for (const SubDev& sd : c->sub) kd2 = (sd.N == 2 && sd.kd > kd2) ? sd.kd : kd2;
-            e = launch_robin_w(view(c), st, c->d_win_prev, kd2, c->nsm > 0 ? c->nsm : 152);
+            e = launch_robin_w(view(c), st, c->d_win_prev, kd2, c->nsm > 0 ? c->nsm : 152, c->d_rtiles);
         }
         if (e == cudaSuccess)
             e = launch_window(a, c->grid, c->win_smem, st, (int)c->inst.size(), c->variant, c->df32, fp32_phase(c),
@@ -1310,7 +1312,7 @@ extern "C" swr_status swr_step(swr_ctx* c, swr_iter_report* rep) {
     c->counters[0] += wms;
     c->counters[1] += 1;
     c->counters[2] += kStepLaunches - 1 + win_launches + (c->any_anti ? 1 : 0) + (c->prob.cvtot_each_iteration ? 2 : 0) +
-                      (!c->tdse && c->variant == WIN_CLUSTER ? 2 : 0);
+                      (!c->tdse && c->robin_w && (c->variant == WIN_CLUSTER || c->variant == WIN_SPLIT) ? 3 : 0);
     c->counters[3] += flops;
     c->counters[4] += bytes;
     c->counters[5] += (double)solves;

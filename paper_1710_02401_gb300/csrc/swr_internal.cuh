@@ -304,6 +304,7 @@ struct SweepArgs {
     int tmem_cols;              // cluster window: tensor-memory columns per CTA (power of two, 0: none)
     int cl_size;                // cluster window: CTAs per cluster (one subdomain each)
     int cl_hs;                  // cluster window: G_hi elements per thread in shared memory (rest: tensor memory)
+    int robin_w;                // the Robin response w^n = kappa dt G b'^n is precomputed (split window: one product)
 };
 
 // Constants of task t, gathered once per window.
@@ -364,7 +365,8 @@ cudaError_t launch_cluster_window(SweepArgs& a, int grid, int cs, size_t smem, c
 // subdomain, GE at assembly, H and W before each cluster window.
 int robin_columns(const SubDev& s);
 cudaError_t launch_robin_ge(const SwrDeviceView& v, cudaStream_t st, int max_K, int max_J);
-cudaError_t launch_robin_w(const SwrDeviceView& v, cudaStream_t st, const int* d_win_prev, int kd2, int nsm);
+cudaError_t launch_robin_w(const SwrDeviceView& v, cudaStream_t st, const int* d_win_prev, int kd2, int nsm,
+                           int* d_tiles);
 void set_error(swr_ctx* c, const char* msg);
 void set_setup_error(const char* msg);
 // Blocks per subdomain of the energy kernel (partials [n_sub][ENERGY_BLOCKS][3]).

@@ -249,34 +249,27 @@ __global__ void k_robin_h(SwrDeviceView v, const int* win_prev) {
 
 // W[n][r] = kappa dt sum_j GE[r][j] H[n][j] (pairs, rows of ldw = df32_ld(K)),
 // n = 0..n_prev, tiles of 64 rows x 64 steps of all subdomains numbered in
-// one sequence and strided over the grid (balanced whatever the subdomain
-// count); each thread 4 rows x 4 steps, inner chunks of 16 columns staged in
-// shared memory (rows padded by two pairs), 32-byte stores of 4 consecutive rows.
+// one sequence (tiles[sid] the first tile of subdomain sid, tiles[n_sub] the
+// total, from k_robin_tiles) and strided over the grid, balanced whatever the
+// subdomain count; each thread 4 rows x 4 steps, inner chunks of 16 columns
+// staged in shared memory (rows padded by two pairs), 32-byte stores of 4
+// consecutive rows.
 #define RW_T 64
 #define RW_C 16
 #define RW_P (RW_T + 2)
-#define RW_MAXSUB 160
-__global__ void __launch_bounds__(RB_THREADS) k_robin_w(SwrDeviceView v, const int* win_prev) {
+__global__ void __launch_bounds__(RB_THREADS) k_robin_w(SwrDeviceView v, const int* win_prev, const int* tiles) {
     __shared__ __align__(16) float2 As[RW_C][RW_P];
     __shared__ __align__(16) float2 Bs[RW_C][RW_P];
-    __shared__ int first[RW_MAXSUB + 1];  // first global tile of each subdomain
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int sid = 0; sid < v.n_sub && sid < RW_MAXSUB; ++sid) {
-            first[sid] = t;
-            const SubDev& s = v.sub[sid];
-            const int wp = win_prev[s.inst];
-            // subdomains without an interior edge get zeros (no inner products)
-            if (wp > 0) t += ((s.K + RW_T - 1) / RW_T) * ((wp + RW_T) / RW_T);
-        }
-        first[v.n_sub < RW_MAXSUB ? v.n_sub : RW_MAXSUB] = t;
-    }
-    __syncthreads();
-    const int nsub = v.n_sub < RW_MAXSUB ? v.n_sub : RW_MAXSUB;
+    const int total = tiles[v.n_sub];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // rows tx*4.., steps ty*4..
-    for (int g = blockIdx.x; g < first[nsub]; g += gridDim.x) {
-        int sid = 0;
-        while (first[sid + 1] <= g) ++sid;
+    for (int g = blockIdx.x; g < total; g += gridDim.x) {
+        int lo = 0, hi = v.n_sub;  // the subdomain: tiles[sid] <= g < tiles[sid + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tiles[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        const int sid = lo;
         const SubDev& s = v.sub[sid];
         const InstDev& in = v.inst[s.inst];
         const int wp = win_prev[s.inst];
@@ -285,7 +278,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_robin_w(SwrDeviceView v, const i
         const float2* H = reinterpret_cast<const float2*>(v.arena + s.Hr);
         float2* W = reinterpret_cast<float2*>(v.arena + s.Wr);
         const float2 kdt = dsp_split_int(in.kappa * in.dt);
-        const int tr = (K + RW_T - 1) / RW_T, tile = g - first[sid];
+        const int tr = (K + RW_T - 1) / RW_T, tile = g - tiles[sid];
         const int r0 = (tile % tr) * RW_T, n0 = (tile / tr) * RW_T;
         float ah[4][4], al[4][4];
 #pragma unroll
@@ -335,6 +328,41 @@ __global__ void __launch_bounds__(RB_THREADS) k_robin_w(SwrDeviceView v, const i
     }
 }
 
+// tiles[sid] = the first tile of subdomain sid in the product's sequence
+// (64 x 64 tiles of K rows by n_prev + 1 steps; subdomains without an
+// interior edge get their zeros the same way), tiles[n_sub] = the total: an
+// exclusive scan by one CTA over contiguous runs of subdomains.
+__global__ void k_robin_tiles(SwrDeviceView v, const int* win_prev, int* tiles) {
+    __shared__ int part[1024];
+    const int ns = v.n_sub, per = (ns + blockDim.x - 1) / blockDim.x;
+    const int s0 = threadIdx.x * per, s1 = min(ns, s0 + per);
+    int sum = 0;
+    for (int sid = s0; sid < s1; ++sid) {
+        const SubDev& s = v.sub[sid];
+        const int wp = win_prev[s.inst];
+        if (wp > 0) sum += ((s.K + RW_T - 1) / RW_T) * ((wp + RW_T) / RW_T);
+    }
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const int x = part[t];
+            part[t] = acc;
+            acc += x;
+        }
+        tiles[ns] = acc;
+    }
+    __syncthreads();
+    int acc = part[threadIdx.x];
+    for (int sid = s0; sid < s1; ++sid) {
+        tiles[sid] = acc;
+        const SubDev& s = v.sub[sid];
+        const int wp = win_prev[s.inst];
+        if (wp > 0) acc += ((s.K + RW_T - 1) / RW_T) * ((wp + RW_T) / RW_T);
+    }
+}
+
 static inline unsigned rb_div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // GE of every subdomain (assembly, after the step-matrix inverse).
@@ -352,7 +380,8 @@ cudaError_t launch_robin_ge(const SwrDeviceView& v, cudaStream_t st, int max_K, 
 // the grids do not depend on the window lengths, which the kernels read on
 // the device (a captured iteration replays them unchanged).  kd2: the largest
 // kd of the two-electron subdomains (0 when there are none).
-cudaError_t launch_robin_w(const SwrDeviceView& v, cudaStream_t st, const int* d_win_prev, int kd2, int nsm) {
+cudaError_t launch_robin_w(const SwrDeviceView& v, cudaStream_t st, const int* d_win_prev, int kd2, int nsm,
+                           int* d_tiles) {
     int nw = 8;
     size_t sm = 0;
     if (kd2 > 0) {
@@ -362,7 +391,8 @@ cudaError_t launch_robin_w(const SwrDeviceView& v, cudaStream_t st, const int* d
     }
     const int per = (2 * nsm + v.n_sub - 1) / v.n_sub;
     k_robin_h<<<dim3(per > 0 ? per : 1, v.n_sub), 32 * nw, sm, st>>>(v, d_win_prev);
-    k_robin_w<<<4 * nsm, RB_THREADS, 0, st>>>(v, d_win_prev);
+    k_robin_tiles<<<1, 1024, 0, st>>>(v, d_win_prev, d_tiles);
+    k_robin_w<<<4 * nsm, RB_THREADS, 0, st>>>(v, d_win_prev, d_tiles);
     return cudaGetLastError();
 }
 

@@ -97,33 +97,60 @@ __global__ void k_line_traces(SwrDeviceView v, const int* win, int cap, int kmax
         }
         for (int c = threadIdx.x; c < K; c += blockDim.x) ys[c + c / kd] = dsp_split_int(y[c]);  // (a, b) at a + (kd+1) b
         __syncthreads();
-        for (int e = threadIdx.x; e < 16 * kd; e += blockDim.x) {
-            const int combo = e / kd, m = e % kd;
-            const int d = combo / 8, lk = combo % 8;  // lk = 2 l + kind
-            const float2* Lr = Lt + (d * 8 + lk) * kd;
-            float h = 0.f, lo = 0.f;
+        // two combinations (lines 2p and 2p+1 of one coordinate) per thread: the
+        // Y element loaded once for both, two independent chains
+        for (int e = threadIdx.x; e < 8 * kd; e += blockDim.x) {
+            const int pc = e / kd, m = e - pc * kd;
+            const int d = pc / 4;
+            const float2* L0 = Lt + (2 * pc) * kd;
+            const float2* L1 = L0 + kd;
+            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
             if (d == 0) {  // r[b] = sum_a L1[a] Y[a][b]
-                for (int a = 0; a < kd; ++a) ds_fma(h, lo, Lr[a], ys[a + (kd + 1) * m]);
+#pragma unroll 4
+                for (int a = 0; a < kd; ++a) {
+                    const float2 yv = ys[a + (kd + 1) * m];
+                    ds_fma(h0, l0, L0[a], yv);
+                    ds_fma(h1, l1, L1[a], yv);
+                }
             } else {       // r[a] = sum_b Y[a][b] L2[b]
-                for (int b = 0; b < kd; ++b) ds_fma(h, lo, Lr[b], ys[m + (kd + 1) * b]);
+#pragma unroll 4
+                for (int b = 0; b < kd; ++b) {
+                    const float2 yv = ys[m + (kd + 1) * b];
+                    ds_fma(h0, l0, L0[b], yv);
+                    ds_fma(h1, l1, L1[b], yv);
+                }
             }
-            const float hs = h + lo;  // renormalised pair
-            r[e] = make_float2(hs, lo - (hs - h));
+            float hs = h0 + l0;  // renormalised pairs
+            r[(2 * pc) * kd + m] = make_float2(hs, l0 - (hs - h0));
+            hs = h1 + l1;
+            r[(2 * pc + 1) * kd + m] = make_float2(hs, l1 - (hs - h1));
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < 16 * q; e += blockDim.x) {
-            const int combo = e / q, node = e % q;
-            const int d = combo / 8;
-            const float2* rc = r + combo * kd;
-            float h = 0.f, lo = 0.f;
+        // two combinations of one coordinate per thread against one node row
+        for (int e = threadIdx.x; e < 8 * q; e += blockDim.x) {
+            const int pc = e / q, node = e - pc * q;
+            const int d = pc / 4;
+            const float2* rc0 = r + (2 * pc) * kd;
+            const float2* rc1 = rc0 + kd;
+            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
             if (staged) {
                 const float2* Bo = Bt + (1 - d) * kd * q + node;
-                for (int m = 0; m < kd; ++m) ds_fma(h, lo, Bo[m * q], rc[m]);
+#pragma unroll 4
+                for (int m = 0; m < kd; ++m) {
+                    const float2 bv = Bo[m * q];
+                    ds_fma(h0, l0, bv, rc0[m]);
+                    ds_fma(h1, l1, bv, rc1[m]);
+                }
             } else {
                 const double* Bo = v.arena + s.t1[1 - d] + lay.B() + (long long)node * kd;
-                for (int m = 0; m < kd; ++m) ds_fma(h, lo, ds_split(Bo[m]), rc[m]);
+                for (int m = 0; m < kd; ++m) {
+                    const float2 bv = ds_split(Bo[m]);
+                    ds_fma(h0, l0, bv, rc0[m]);
+                    ds_fma(h1, l1, bv, rc1[m]);
+                }
             }
-            out[combo * q + node] = (double)h + (double)lo;
+            out[(2 * pc) * q + node] = (double)h0 + (double)l0;
+            out[(2 * pc + 1) * q + node] = (double)h1 + (double)l1;
         }
         __syncthreads();
     }

@@ -1689,7 +1689,14 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                 {
                     const float2 isf = ds_split(is1), kdt2 = ds_split(tc.kdt);
                     const float2* U = reinterpret_cast<const float2*>(v.arena + sd.work + (long long)(m & 1) * 2 * K);
+                    // w^m: formed by this kernel at step m - 1 (G times kappa dt b'^m), or
+                    // read from the Robin response precomputed for every step
+                    // (swr_robin.cu; no antisymmetric instance then), zero
+                    // without Robin data
                     const float2* Wv = U + K;
+                    const float2* Wpre = nullptr;
+                    if (A.robin_w && m >= 1 && wp > 0)
+                        Wpre = reinterpret_cast<const float2*>(v.arena + sd.Wr) + (long long)min(m, wp) * ld;
                     const double* c0 = v.arena + tc.c0;
                     // antisymmetric states: on a diagonal subdomain (its own mirror) the
                     // products act on (y - swap(y)) / 2 and likewise b'; y itself is kept
@@ -1711,8 +1718,9 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                                 const unsigned long long u = __ldcg(reinterpret_cast<const unsigned long long*>(p));
                                 return make_float2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
                             };
-                            const float2 y = m == 0 ? dsp_split_int(c0[c]) : dsp_add(dsp_mul(ld2(U + c), isf), ld2(Wv + c));
-                            float2 yp = y, bp = bsrc ? dsp_split_int(bsrc[c]) : make_float2(0.f, 0.f);
+                            const float2 wm = A.robin_w ? (Wpre ? ld2(Wpre + c) : make_float2(0.f, 0.f)) : ld2(Wv + c);
+                            const float2 y = m == 0 ? dsp_split_int(c0[c]) : dsp_add(dsp_mul(ld2(U + c), isf), wm);
+                            float2 yp = y, bp = (bsrc && !A.robin_w) ? dsp_split_int(bsrc[c]) : make_float2(0.f, 0.f);
                             if (anti) {
                                 const int sc = swap_index(c, tc.kd);
                                 const float2 ym_ = m == 0 ? dsp_split_int(c0m[sc])
@@ -1722,7 +1730,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                             }
                             ys2[c] = y;
                             vf[c] = yp;
-                            bf[c] = bsrc ? dsp_mul(kdt2, bp) : make_float2(0.f, 0.f);
+                            bf[c] = (bsrc && !A.robin_w) ? dsp_mul(kdt2, bp) : make_float2(0.f, 0.f);
                         } else {
                             ys2[c] = make_float2(0.f, 0.f);
                             vf[c] = make_float2(0.f, 0.f);
@@ -1778,7 +1786,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                 const int rs = split_stage_rows(ld, SC, ONEP ? 1 : 2);
                 float2* Un = reinterpret_cast<float2*>(v.arena + sd.work + (long long)((m + 1) & 1) * 2 * K);
                 float2* Wn = Un + K;
-                const bool hasb = bsrc != nullptr;
+                const bool hasb = bsrc != nullptr && !A.robin_w;  // else u = G y^m only
                 for (int rb = tc.r0; rb < tc.r0 + nr; rb += rs) {
                     const int nrow = min(rs, tc.r0 + nr - rb);
                     const unsigned s = used % NS;
