@@ -561,32 +561,44 @@ def run_assembly(args, S, reps=3):
     print(json.dumps(out))
 
 
-def run_learned(args, n_train=160, n_test=24):
-    """Learned initial traces on the reduced real-time family: GPU data
-    generation, training with the library's MLP kernels, and the held-out
-    comparison at equal residual."""
+LEARNED_FAMILIES = {
+    "small": ("learned_trace_family", "learned_trace_family (2 electrons, [-6,6]^2, 2x2 subdomains, 8x8 Gaussians, "
+                                      "40 Crank-Nicolson steps, random nuclei, softening and field phase)"),
+    "16sd": ("learned_trace_family_16sd", "learned_trace_family_16sd (2 electrons, [-10,10]^2, 4x4 subdomains with "
+                                          "the 64-subdomain real-time workload's core width 5 and overlap 0.5, 10x10 "
+                                          "Gaussians, 100 Crank-Nicolson steps, random nuclei, charges, softening "
+                                          "and field phase)"),
+}
+
+
+def run_learned(args):
+    """Learned initial traces: GPU data generation, training with the
+    library's MLP kernels, and the held-out comparison at equal residual."""
+    import numpy as np
+    import torch
     from paper_1710_02401_gb300 import learn as Lrn
     from paper_1710_02401_gb300 import problems as P
-    import torch
+    fam_fn, fam_desc = LEARNED_FAMILIES[args.learned_family]
+    family = getattr(P, fam_fn)
+    n_train, n_test = args.learned_train, args.learned_test
     t0 = time.perf_counter()
-    x, y, done = Lrn.gather_training_set(P.learned_trace_family(n_train, seed=21))
+    x, y, done = Lrn.gather_training_set(family(n_train, seed=21))
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    model, losses = Lrn.train(x, y, steps=1500)
+    model, losses = Lrn.train(x, y, steps=args.learned_steps)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    r = Lrn.compare_timed(model, P.learned_trace_family(n_test, seed=99))
+    r = Lrn.compare_timed(model, family(n_test, seed=99))
     print(json.dumps({"metric": "Schwarz time-to-1e-8 from the learned initial traces vs zero traces",
                       "unit": "s", "higher_is_better": False, "value": r["seconds_learned"],
                       "baseline_zero_guess_s": r["seconds_zero_guess"],
                       "speedup": r["seconds_zero_guess"] / r["seconds_learned"], **r,
                       "training": {"instances": n_train, "subdomains": int(x.shape[0]), "data_seconds": t_data,
-                                   "train_seconds": t_train, "adam_steps": 1500, "loss_first": losses[0],
-                                   "loss_last": losses[-1]},
-                      "config": {"workload": "learned_trace_family (2 electrons, [-6,6]^2, 2x2 subdomains, 8x8 "
-                                             "Gaussians, 40 Crank-Nicolson steps, random nuclei, softening and "
-                                             "field phase)", "held_out_instances": n_test, "tol": 1e-8},
+                                   "train_seconds": t_train, "adam_steps": args.learned_steps,
+                                   "loss_first": losses[0], "loss_last": losses[-1],
+                                   "training_iterations_zero_guess_mean": float(np.mean(done))},
+                      "config": {"workload": fam_desc, "held_out_instances": n_test, "tol": 1e-8},
                       "data": "synthetic"}))
 
 
@@ -663,6 +675,12 @@ def main():
     ap.add_argument("--antisymmetric", action="store_true",
                     help="2-electron imaginary-time workloads: the lowest antisymmetric state (initial Gaussian "
                          "centred at (0.8, -0.8)); the lower subdomain of each mirror pair is not solved")
+    ap.add_argument("--learned-family", default="small", choices=["small", "16sd"],
+                    help="--learned: the instance family (small: 2x2 subdomains, 40 steps; 16sd: 4x4 subdomains "
+                         "of the real-time workload's geometry, 100 steps)")
+    ap.add_argument("--learned-train", type=int, default=160, help="--learned: training instances")
+    ap.add_argument("--learned-test", type=int, default=24, help="--learned: held-out instances")
+    ap.add_argument("--learned-steps", type=int, default=1500, help="--learned: Adam steps")
     ap.add_argument("--learned", action="store_true",
                     help="learned initial traces: train the BF16 MLP on GPU-generated converged traces of the "
                          "reduced real-time family, then time held-out solves to Res <= 1e-8 from zero traces and "

@@ -247,3 +247,26 @@ def learned_trace_family(n_instances: int, seed: int = 5) -> List[Instance]:
                             nuclei=nuc, eta_en=eps, eta_ee=eps, ee_coef=1.0, mu=-10j, mode=TDSE,
                             dt=0.01, n_steps=40, field=(0.5, 0.4, 8.0, phase), phi0_gamma=1.0))
     return out
+
+
+
+def learned_trace_family_16sd(n_instances: int, seed: int = 7) -> List[Instance]:
+    """Seeded real-time problems for the learned initial traces with the
+    64-subdomain real-time workload's subdomain geometry (cores of width 5,
+    overlap 0.5) on a 4 x 4 grid: 2 electrons, [-10,10]^2, 10 x 10 Gaussians
+    per subdomain, 100 Crank-Nicolson steps (dt = 0.01), mu = -10i, field
+    0.5 sin^2(pi t) sin(8 t + phase) with phase ~ U[0, 2 pi); 1 or 2 nuclei
+    at U[-2, 2] with Z in {1, 2, 3}; softening ~ U[0.3, 1]."""
+    rng = random.Random(seed)
+    box, L, ov, kd = (-10.0, 10.0), 4, 0.5, 10
+    out = []
+    for _ in range(n_instances):
+        P = rng.choice((1, 2))
+        nuc = tuple((rng.uniform(-2.0, 2.0), float(rng.choice((1, 2, 3)))) for _ in range(P))
+        eps = rng.uniform(0.3, 1.0)
+        phase = rng.uniform(0.0, 2.0 * math.pi)
+        out.append(Instance(n_elec=2, box=box, L=L, overlap=ov, K_d=kd,
+                            delta=spacing_rule_delta(box, L, ov, kd), q_p=8, n_mid=mid_panels(box, L, ov),
+                            nuclei=nuc, eta_en=eps, eta_ee=eps, ee_coef=1.0, mu=-10j, mode=TDSE,
+                            dt=0.01, n_steps=100, field=(0.5, 1.0, 8.0, phase), phi0_gamma=1.0))
+    return out
