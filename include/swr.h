@@ -102,10 +102,13 @@ typedef enum swr_window_variant {
                                   W = (Pp (x) Pp) G precomputed, one grid barrier
                                   per step (16 bytes per element); at most 4 row
                                   tasks of at most 64 rows per CTA               */
-    SWR_WINDOW_SPLIT = 3,      /* mixed precision only: u = G y^n and
-                                  w = G (kappa dt b') in one pass over G before
-                                  s_n is known, y^{n+1} = u / s_n + w formed after
-                                  the next barrier: one grid barrier per step,
+    SWR_WINDOW_SPLIT = 3,      /* mixed precision only: u = G y^n in one pass
+                                  over G before s_n is known, y^{n+1} = u / s_n
+                                  + w formed after the next barrier, with
+                                  w = kappa dt G b' read from the Robin response
+                                  formed before the window for every step (with
+                                  antisymmetric instances: formed in the same
+                                  pass over G); one grid barrier per step,
                                   8 bytes per element, any batch size (task state
                                   in global memory); the stop on the NGF
                                   tolerance is decided one step later and the
@@ -125,8 +128,11 @@ typedef enum swr_window_variant {
                                   y^n moves between the CTAs of a cluster through
                                   distributed shared memory, one cluster barrier
                                   per step and one arrival counter per instance
-                                  for s_n (no grid barrier); needs every
-                                  subdomain's cluster resident at once          */
+                                  for s_n (no grid barrier), the product G y^n
+                                  formed while s_n is reduced and w = kappa dt
+                                  G b' read from the Robin response formed before
+                                  the window; needs every subdomain's cluster
+                                  resident at once                              */
 } swr_window_variant;
 
 /* Where swr_assemble runs its two dense contractions: the e-e block of the
