@@ -734,8 +734,9 @@ static void plan(swr_ctx* c) {
     // read by the cluster and split windows: mixed precision, imaginary time,
     // no antisymmetric instance
     {
+        // (the decomposition kernel stages edge vectors of at most 64 values)
         bool small_kd = true;
-        for (const SubDev& s : c->sub) small_kd = small_kd && (s.N == 1 || s.kd <= 64);
+        for (const SubDev& s : c->sub) small_kd = small_kd && s.kd <= 64;
         c->robin_w = c->df32 && !c->tdse && !c->any_anti && small_kd && !c->sub.empty() &&
                      (p.window_variant == 0 || p.window_variant == WIN_CLUSTER || p.window_variant == WIN_SPLIT);
     }

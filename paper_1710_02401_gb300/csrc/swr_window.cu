@@ -1570,6 +1570,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                 auto push = [&](int val) {
                     const unsigned s = pushed % SPLIT_FIFO;
                     if (pushed >= SPLIT_FIFO) wait(&fe[s], (pushed / SPLIT_FIFO - 1) & 1u);
+                    if (failed) return;  // a wait gave up: the consumers leave on their own bounded waits
                     fifo[s] = val;
                     mbar_arrive(&ff[s]);
                     ++pushed;
@@ -1579,6 +1580,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                 unsigned a_pos = 0;
                 int a_t = -1, a_par = 0;
                 for (;;) {
+                    if (failed) break;  // a wait gave up: claim and issue nothing more
                     // next task of step m: guided chunks of the step's list
                     if (c_next == c_end) {
                         const unsigned n = m == 0 ? (unsigned)nt : __ldcg(&q->count[m & 1]);
@@ -1636,6 +1638,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 2) k_window_split(SweepArgs A) {
                     for (int rb = tc.r0; rb < tc.r0 + tc.nr; rb += rs) {
                         const unsigned s = issued % NS;
                         if (issued >= NS) wait(&empty[s], (issued / NS - 1) & 1u);
+                        if (failed) break;  // never a copy into a slot whose release was not seen
                         const int nrow = min(rs, tc.r0 + tc.nr - rb);
                         const unsigned bytes = (unsigned)nrow * ld * 4u, mb = smem_u32(&full[s]);
                         float* dst = ring + (size_t)s * SC;
