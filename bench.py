@@ -65,7 +65,7 @@ PROFILED_TRAFFIC = {
     "k_window_fused": ("123b4a784de2ee96", 329.5e6, "profiles/k_window_fused_tise_2e_16sd.md"),
     "k_window_2ph<false>": ("6fd9a352bcfedf25", 279.0e6, "profiles/k_window_2ph_fp64_tise_2e_16sd.md"),
     "k_window_2ph<true>@batched": ("cbd72ea8633a4ed0", 1.192, "profiles/k_window_2ph_df32_batched_uneven.md"),
-    "k_window_split@batched": ("951237c2e2359605", 1.030, "profiles/k_window_split_batched_uneven.md"),
+    "k_window_split@batched": ("e908166e69fb5910", 1.030, "profiles/k_window_split_batched_uneven.md"),
     # the captured launch is a 1723-step window; the traffic is the history rows and
     # Robin sources, proportional to the window length like the algorithmic bytes
     "k_window_cluster": ("01d810867459c710", 259.04e6, "profiles/k_window_cluster_tise_2e_16sd.md"),
