@@ -14,7 +14,7 @@
 // The Hermitian part of M0 is I - (dt/2) kappa mu_im R' >= I for mu_im <= 0,
 // so ||G0|| <= 1 and the fixed point contracts with
 // rho <= (dt/2) max|e| max_{Omega_i}|x_1 + ... + x_N|; the host chooses the
-// iteration count from rho so that rho^(m+1) <= 1e-17.
+// iteration count from rho so that rho^(m+1) <= 1e-15.
 //
 // Complex vectors are planar: [re block K][im block K].  G0 is interleaved
 // (re, im) per element as the Gauss-Jordan inversion leaves it.
